@@ -1,0 +1,354 @@
+"""Throughput bench of the GB300 SND hot path.
+
+Workload: one full Northern Cross beam - 1024 channels over 400-416 MHz, dt = 0.138 ms,
+2048 trial DMs over 0-2000 pc cm^-3, uint8 filterbank streamed in 16384-sample chunks,
+seeded synthetic noise with 200 injected bursts. A step streams 16 chunks (2^18 samples)
+through the whole path (encoder -> SND tree -> matched filter -> candidates) in each of the
+three modes (binary, graded, float; branching 8, Supplementary Table S1 operating points);
+the three plans keep streaming across steps, so every timed chunk emits 16384 samples per
+DM row. Metric: DM-trial samples per second (DM rows x emitted plane samples / time).
+
+Multi-GPU: beams are independent, so N ranks run N beam replicas with no collective
+(weak scaling); value = all ranks' DM-samples / the slowest rank's time.
+
+--impl reference runs the FP64 CPU oracle (the only other implementation of this method
+here) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+W = synth.NC1024
+MODES = (("binary", 0), ("graded", 1), ("float", 2))
+BRANCHING = 8
+TREE_BYTES_PER_DM_SAMPLE = W.nchan / W.ndm + 4.0  # uint8 input read once + int32 plane written once
+DATA_NOTE = "synthetic: seeded rint(N(128,16)) uint8 noise + 200 injected dispersed bursts"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_from_profile(src_hash: str):
+    """DRAM bytes per tree launch from the committed ncu summary, if it was taken on this
+    exact tree kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_tree_nc1024_2048dm.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("bench_key:"):
+            k, _, v = line[len("bench_key:"):].strip().partition("=")
+            vals[k.strip()] = v.strip()
+    if vals.get("tree_source_sha1") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _tree_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("tree.cu", "snd_internal.h"):
+        with open(os.path.join(ROOT, "paper_2606_15361_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------------------
+
+def oracle_sample(chunks, rows: int):
+    """Time the FP64 oracle on a bounded sample of the workload: the steady-state chunk
+    (index 2) of every mode, encoder over all channels, SND tree + matched filter on the
+    first `rows` DM rows. Returns (DM-samples, seconds, description)."""
+    from oracle import delays as od
+    from oracle import encoder as oe
+    from oracle import mf as om
+    from oracle import stream as ost
+    from oracle import tree as ot
+    freqs, dms = W.freqs(), W.dms()
+    tab = od.delay_table(freqs, synth.NC_DT, dms)
+    D = int(tab.max())
+    widths = [om.row_widths(freqs, synth.NC_DT, d, 0.1) for d in dms[:rows]]
+    t0 = time.perf_counter()
+    work = 0
+    for name, m in MODES:
+        cfg = ost.defaults(m, branching=BRANCHING)
+        x = np.concatenate([oe.encode_chunk(chunks[i], cfg.enc_theta)[0] for i in range(3)], axis=1)
+        e_prev = 2 * W.chunk - D
+        y = ot.snd_rows(x, 0, tab, range(rows), e_prev, W.chunk, m, cfg.cluster, cfg.branching,
+                        cfg.k_leaf, cfg.k_internal, cfg.cap)
+        floor = cfg.sigma_min if m == 0 else None
+        for r in range(rows):
+            om.row_mf(y[r], W.chunk - 1023, widths[r], cfg.det_theta, floor)
+        work += rows * W.chunk
+    dt = time.perf_counter() - t0
+    return work, dt, (f"FP64 numpy oracle, 1 chunk x 3 modes: encoder on all 1024 channels, "
+                      f"tree + matched filter on {rows} of 2048 DM rows")
+
+
+def run_reference(args, rank, world):
+    out = {"impl": "reference", "metric": "DM-trial samples/s", "unit": "DM-samples/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA_NOTE}
+    if rank != 0:
+        return None
+    chunks = [W.chunk_data(i) for i in range(3)]
+    for _ in range(args.warmup):
+        oracle_sample(chunks, 1)
+    work = 0
+    secs = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        w_, s_, desc = oracle_sample(chunks, args.ref_rows)
+        work += w_
+        secs += s_
+    v = work / secs
+    out.update({"value": v, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+                "config": {"workload": "nc1024_2048dm: 1024 ch 400-416 MHz, dt 0.138 ms, 2048 DMs 0-2000, "
+                                       "16384-sample chunks, B=8, binary+graded+float",
+                           "sample": desc},
+                "cpu_baseline": {"value": v, "unit": "DM-samples/s", "cores": 1, "kind": "oracle", "sample": desc},
+                "e2e": {"value": v, "unit": "DM-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2606_15361_gb300 as g
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    host_chunks = [W.chunk_data(i) for i in range(W.nchunks)]
+    dchunks = [torch.from_numpy(c).to(dev) for c in host_chunks]                  # 268 MB > L2
+    pinned = [torch.from_numpy(c).pin_memory() for c in host_chunks]
+    freqs, dms = W.freqs(), W.dms()
+    plans = {name: g.Plan(freqs, synth.NC_DT, dms, BRANCHING, m, g.options(m, max_chunk=W.chunk), device=dev)
+             for name, m in MODES}
+    stream = torch.cuda.current_stream(dev)
+
+    def step(host: bool):
+        for name, _ in MODES:
+            p = plans[name]
+            for i in range(W.nchunks):
+                if host:
+                    p.execute_host(pinned[i])
+                else:
+                    p.execute(dchunks[i])
+
+    def sync():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+
+    # warm-up (also fills the rings: from then on every chunk emits W.chunk samples per row)
+    for _ in range(max(args.warmup, 1)):
+        step(False)
+    for p in plans.values():
+        p.candidates(check=False)
+    sync()
+    launches0 = {n: p.stats().kernel_launches for n, p in plans.items()}
+    for p in plans.values():
+        p.profile(True)
+        p.profile_read()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(False)
+    ev1.record(stream)
+    sync()
+    ms_dev = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = {n: p.profile_read() for n, p in plans.items()}
+    for p in plans.values():
+        p.profile(False)
+    launches = sum(p.stats().kernel_launches - launches0[n] for n, p in plans.items())
+    ncands = sum(len(p.candidates(check=False)[0]) for p in plans.values())
+
+    # end to end: pinned host chunks copied inside the C-ABI call, candidates read back
+    for p in plans.values():
+        p.candidates(check=False)
+    sync()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    d2h = 0
+    for _ in range(args.steps):
+        step(True)
+        for p in plans.values():
+            c, _ = p.candidates(check=False)
+            d2h += c.nbytes + 8
+    ev1.record(stream)
+    sync()
+    ms_e2e = max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
+
+    per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
+    t = torch.tensor([ms_dev, ms_e2e], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_dev, ms_e2e = float(t[0]), float(t[1])
+    value = per_step * args.steps * world / (ms_dev / 1e3)
+    e2e = per_step * args.steps * world / (ms_e2e / 1e3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+
+    peaks, src = _peaks()
+    tree_ms = sum(prof[n]["tree"][0] for n in prof)
+    tree_n = sum(prof[n]["tree"][1] for n in prof)
+    tree_launch_ms = tree_ms / max(tree_n, 1)
+    units = W.chunk * W.ndm
+    achieved = TREE_BYTES_PER_DM_SAMPLE * units / (tree_launch_ms / 1e3) / 1e9
+    per_mode = {}
+    for n in prof:
+        st = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof[n].items()}
+        tms = prof[n]["tree"][0] / max(prof[n]["tree"][1], 1)
+        per_mode[n] = {"stage_ms_per_chunk": st,
+                       "tree_gdm_samples_per_s": round(units / (tms / 1e3) / 1e9, 2),
+                       "tree_hbm_frac": round(TREE_BYTES_PER_DM_SAMPLE * units / (tms / 1e3) / 1e9 /
+                                              peaks["hbm_gbs"], 4),
+                       "pipeline_gdm_samples_per_s": round(units / (sum(v[0] for v in prof[n].values()) /
+                                                                    max(prof[n]["tree"][1], 1) / 1e3) / 1e9, 2)}
+    traffic = _traffic_from_profile(_tree_source_hash())
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        work, secs, desc = oracle_sample(host_chunks[:3], args.ref_rows)
+        cpu = {"value": work / secs, "unit": "DM-samples/s", "cores": 1, "kind": "oracle", "sample": desc}
+    realtime_beams = e2e / (W.ndm / synth.NC_DT) / len(MODES)
+    return {
+        "metric": "DM-trial samples/s", "value": value, "unit": "DM-samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u1/int32",
+        "data": DATA_NOTE,
+        "config": {"workload": "nc1024_2048dm: 1024 ch 400-416 MHz, dt 0.138 ms, 2048 DMs 0-2000 pc/cm3, "
+                               "16 x 16384-sample chunks per step, B=8, modes binary+graded+float (Table S1)",
+                   "branching": BRANCHING, "chunk": W.chunk, "chunks_per_step": W.nchunks,
+                   "l2": "inputs larger than L2 (16 chunks = 268 MB uint8 per step, 129 MB L2)",
+                   "parallelism": f"beam replicas x{world}"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "k_tree (SND tree, all modes, average launch)",
+                     "peak_source": src, "algorithmic_bytes_per_dm_sample": TREE_BYTES_PER_DM_SAMPLE},
+        "per_mode": per_mode,
+        "e2e": {"value": e2e, "unit": "DM-samples/s",
+                "h2d_bytes_per_step": len(MODES) * W.nchunks * W.chunk * W.nchan,
+                "d2h_bytes_per_step": int(d2h / max(args.steps, 1))},
+        "realtime_beams_per_mode": realtime_beams,
+        "candidates_in_timed_steps": ncands,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_gpu(args, rank, world, local_rank)
+    if res is not None and rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

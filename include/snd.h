@@ -1,0 +1,209 @@
+/*
+ * snd.h - C ABI of the GB300 Spiking Neural Dedispersion (SND) hot path.
+ *
+ * The library searches a streamed uint8 filterbank for dispersed pulses:
+ *   delta encoder  -> SND delay-and-add tree -> DM-scaled boxcar matched filter
+ *   -> threshold, 9x9 closing, 8-connected labelling -> candidate list
+ * (arXiv 2606.15361, Methods: "Pipeline overview", "Input encoding", "The Spiking
+ * Neural Dedispersion algorithm", "Matched filtering", "Candidate detection").
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: SND_OK (0) on success, a negative snd_status_t otherwise. No C++
+ *    exception crosses this boundary. An error raised while a plan is executing is
+ *    sticky: later calls on that plan return it until snd_destroy.
+ *  - "device" pointers are CUDA global-memory pointers of the current device; "host"
+ *    pointers are ordinary CPU memory (pinned memory makes snd_execute_host faster).
+ *  - stream is a cudaStream_t passed as void* (0 = the legacy default stream).
+ *  - A plan is not re-entrant: one stream at a time per plan. Distinct plans may run
+ *    concurrently on distinct streams and workspaces.
+ *  - The library allocates no device memory. All device state lives in a
+ *    caller-owned workspace (snd_workspace_size / snd_bind_workspace).
+ */
+#ifndef SND_H
+#define SND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SND_OK = 0,
+  SND_ERR_ARG = -1,          /* invalid argument (null pointer, size, option range) */
+  SND_ERR_FREQ_ORDER = -2,   /* channel frequencies not finite, positive, distinct */
+  SND_ERR_DM = -3,           /* a trial DM is negative or not finite */
+  SND_ERR_WORKSPACE = -4,    /* workspace missing, too small or misaligned */
+  SND_ERR_CHUNK = -5,        /* nsamp <= 0 or > max_chunk */
+  SND_ERR_CUDA = -6,         /* a CUDA runtime call failed */
+  SND_ERR_STATE = -7,        /* call not valid in the plan's current state */
+  SND_ERR_TIMEOUT = -8,      /* a bounded device-side loop gave up */
+  SND_ERR_OVERFLOW = -9,     /* a fixed-capacity device list overflowed (results dropped) */
+  SND_ERR_NOMEM = -10,       /* host allocation failed */
+  SND_ERR_UNSUPPORTED = -11  /* configuration outside what the GPU kernels implement */
+} snd_status_t;
+
+/* Tree activation modes (Methods, "Tree activation modes"). */
+typedef enum {
+  SND_MODE_BINARY = 0,  /* Mode A: node = 1[count >= K] (K_L at leaves, K_I above) */
+  SND_MODE_GRADED = 1,  /* Mode B: node = min(sum, N) at every node, root included */
+  SND_MODE_FLOAT = 2    /* Mode C: node = sum; root divided by sqrt(N_f) */
+} snd_mode_t;
+
+typedef struct snd_plan_s* snd_plan_t;
+
+/* Option flag: evaluate the tree with the slow scalar verification kernel (one thread per
+ * DM-sample, integer counts from the full delay table) instead of the tiled bit-sliced
+ * kernel. Results are identical; it exists to cross-check the fast kernel. */
+#define SND_FLAG_REFERENCE_TREE 1
+
+/*
+ * Options. Fill with snd_options_init(mode, &o) (Supplementary Table S1 operating point
+ * for that mode) and then override fields; values are used as given.
+ */
+typedef struct {
+  int32_t cluster_size;     /* C, leaf cluster size, 1..7 (Table S1: 4) */
+  int32_t k_leaf;           /* K_L, binary leaf quorum, 1..8 (Table S1: 2); other modes ignore */
+  int32_t k_internal;       /* K_I, binary internal quorum, 1..8 (Table S1: 2) */
+  int32_t graded_cap;       /* N, graded cap, 1..255 (Table S1: 255) */
+  double enc_theta;         /* theta, encoder threshold in sigma (1.5 binary/float, 0.75 graded) */
+  double det_theta;         /* Theta, detection S/N threshold, > 0 (Table S1: 7.0) */
+  double sigma_min;         /* sigma floor of the matched filter, binary mode only (0.20) */
+  double mf_alpha;          /* alpha of the width rule (Methods, "Matched filtering": 0.1) */
+  int32_t closing_size;     /* closing element side, odd, 1..31 (9) */
+  int32_t n_min_pixels;     /* islands with fewer closed-mask pixels are dropped (10) */
+  int32_t max_chunk;        /* largest nsamp accepted by snd_execute (default 32768) */
+  int32_t cand_capacity;    /* candidates held on the device between snd_candidates calls */
+  int32_t cell_capacity;    /* mask cells with S/N kept per matched-filter block */
+  int32_t run_capacity;     /* closed-mask runs per matched-filter block */
+  int32_t flags;            /* 0, or SND_FLAG_REFERENCE_TREE */
+} snd_options_t;
+
+/* One detection (Methods, "Candidate detection": one candidate per island, peak pixel). */
+typedef struct {
+  int32_t dm_index;   /* row of the trial-DM grid */
+  float dm;           /* dm_grid[dm_index] */
+  int64_t t;          /* stream sample index (time of arrival at the top of the band) */
+  float snr;          /* peak S/N (FP64 matched filter, rounded to float) */
+  int32_t width;      /* boxcar width of the peak, samples */
+  int32_t npix;       /* pixels of the island in the closed mask */
+  int32_t reserved;
+} snd_candidate_t;
+
+typedef struct {
+  int32_t nchan, ndm, mode, branching, cluster_size;
+  int32_t max_delay;               /* D = max delta_c(d), samples */
+  int32_t nlevels;                 /* tree levels including the leaves */
+  int32_t nodes_per_level[24];     /* structural nodes per level (leaves first) */
+  int64_t unique_per_level[24];    /* distinct node patterns per level (neuron count) */
+  double adds_per_dm_sample;       /* additions per DM-sample with pattern sharing */
+  int32_t wmax;                    /* largest boxcar width over the DM grid */
+  int32_t ring_words;              /* bit-ring words per channel (one copy) */
+  int64_t hist_mem_bytes;          /* Eq. hist_mem for this single band and mode */
+  size_t workspace_bytes;
+  int64_t samples_in;              /* samples consumed so far */
+  int64_t emitted;                 /* E: plane samples emitted per row so far */
+  int64_t scored;                  /* F: start times scored by the matched filter so far */
+  int32_t candidates_pending;      /* -1 unless synchronised by snd_candidates */
+  int32_t tree_tile_dms;           /* DM rows per tree CTA */
+  int32_t tree_tile_words;         /* 32-sample words per tree CTA */
+  int32_t tree_group_leaves;       /* leaves staged per shared-memory round */
+  int32_t tree_smem_bytes;         /* dynamic shared memory of the tree kernel */
+  int32_t max_patterns_per_group;
+  int64_t kernel_launches;         /* CUDA kernels enqueued by this plan since binding */
+} snd_plan_stats_t;
+
+/* Pipeline stages timed by snd_profile / snd_profile_read. */
+enum { SND_STAGE_ENCODE = 0, SND_STAGE_TREE = 1, SND_STAGE_MF = 2, SND_STAGE_CANDIDATES = 3, SND_NUM_STAGES = 4 };
+
+/* Fill *o with the Supplementary Table S1 operating point of `mode`. */
+int snd_options_init(snd_mode_t mode, snd_options_t* o);
+
+/*
+ * Build a plan (host only; no CUDA call).
+ *   freqs_mhz[nchan]  channel-centre frequencies, MHz, any order, distinct, > 0
+ *   dt_s              sample interval, seconds, > 0
+ *   dm_grid[ndm]      trial DMs, pc cm^-3, finite and >= 0, any order, duplicates allowed
+ *   branching         B >= 2 (Methods, "Tree levels")
+ * Delays: delta_c(d) = floor(K d (f_c^-2 - f_ref^-2)/dt + 1/2), K = 4.148808e3 MHz^2 s,
+ * f_ref = highest frequency (Methods, "Incoherent dedispersion").
+ * snd_plan uses the Table S1 options of `mode`. *out receives the plan (NULL on error).
+ */
+int snd_plan(const double* freqs_mhz, int32_t nchan, double dt_s, const double* dm_grid,
+             int32_t ndm, int32_t branching, snd_mode_t mode, snd_plan_t* out);
+int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s, const double* dm_grid,
+                int32_t ndm, int32_t branching, snd_mode_t mode, const snd_options_t* opts,
+                snd_plan_t* out);
+
+/* Bytes of device workspace the plan needs (0 for a NULL plan). */
+size_t snd_workspace_size(snd_plan_t plan);
+
+/*
+ * Bind a device workspace of at least snd_workspace_size bytes, 256-byte aligned, and reset
+ * the stream state (stream time back to 0). The caller owns the memory and must keep it
+ * alive until snd_destroy or the next bind. Uploads the plan's device tables and clears the
+ * workspace with work enqueued on `stream` (no host synchronisation).
+ */
+int snd_bind_workspace(snd_plan_t plan, void* d_workspace, size_t bytes, void* stream);
+
+/*
+ * Process the next chunk of the stream (Methods, "Pipeline overview").
+ *   d_chunk      device uint8[nsamp][nchan] (time-major, SIGPROC order), read only;
+ *                must stay valid until the stream passes this call
+ *   nsamp        1..max_chunk samples
+ *   stream       all work is enqueued on it; no host synchronisation
+ *   d_plane_out  optional device output [ndm][*nemit_out] row-major: int32 root values
+ *                (binary 0/1, graded 0..N) or float32 (float mode, counts/sqrt(N_f)) for the
+ *                newly emitted samples [E_prev, E_new); NULL to skip
+ *   nemit_out    optional host int32: E_new - E_prev, the emitted samples per row, where
+ *                E = max(0, samples consumed - D) (every emitted sample has full history)
+ * Candidates found by this call accumulate on the device until snd_candidates.
+ */
+int snd_execute(snd_plan_t plan, const uint8_t* d_chunk, int32_t nsamp, void* stream,
+                void* d_plane_out, int32_t* nemit_out);
+
+/*
+ * Same as snd_execute for a HOST chunk: copies h_chunk into the workspace's staging area
+ * (cudaMemcpyAsync on `stream`) and then runs the path. h_chunk must stay unchanged until
+ * the stream passes the copy; page-locked memory makes the copy asynchronous.
+ */
+int snd_execute_host(snd_plan_t plan, const uint8_t* h_chunk, int32_t nsamp, void* stream,
+                     void* d_plane_out, int32_t* nemit_out);
+
+/*
+ * Synchronise the plan's last stream, copy the candidates accumulated since the previous
+ * call to host_out (at most cap; sorted by (t, dm_index)), report their count in *n_out
+ * and clear the device list. Returns SND_ERR_OVERFLOW (after copying what was kept) when
+ * a device capacity overflowed since the last call, SND_ERR_TIMEOUT when a bounded device
+ * loop gave up.
+ */
+int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_t cap, int32_t* n_out);
+
+/* Plan statistics (host only; stream counters are those of the last enqueued call). */
+int snd_plan_stats(snd_plan_t plan, snd_plan_stats_t* out);
+
+/* Copy the plan's integer delay table int32[ndm][nchan] to host memory (n >= ndm*nchan). */
+int snd_delay_table(snd_plan_t plan, int32_t* host_out, int64_t n);
+
+/*
+ * Per-stage device timing. enable != 0 makes every following snd_execute record a CUDA
+ * event pair around each stage on the execution stream (events are created on first use
+ * and kept by the plan); enable == 0 stops recording. snd_profile_read synchronises the
+ * recorded events, writes the summed milliseconds and the number of timed launches of each
+ * stage into ms_out[SND_NUM_STAGES] and count_out[SND_NUM_STAGES] (either may be NULL), and
+ * clears the record.
+ */
+int snd_profile(snd_plan_t plan, int enable);
+int snd_profile_read(snd_plan_t plan, double* ms_out, int64_t* count_out);
+
+/* Release the plan's host memory. The workspace is the caller's. NULL is ignored. */
+void snd_destroy(snd_plan_t plan);
+
+/* Static description of a status code. */
+const char* snd_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SND_H */

@@ -1,0 +1,235 @@
+"""Python binding of the GB300 SND library (``libsnd.so``, C ABI in ``include/snd.h``).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA kernels.
+PyTorch supplies device memory (the workspace, chunks and planes) and streams. Importing
+this module loads the in-tree library and fails loudly if it has not been built; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsnd.so")
+
+MODE_BINARY, MODE_GRADED, MODE_FLOAT = 0, 1, 2
+FLAG_REFERENCE_TREE = 1
+
+STATUS = {
+    0: "SND_OK", -1: "SND_ERR_ARG", -2: "SND_ERR_FREQ_ORDER", -3: "SND_ERR_DM",
+    -4: "SND_ERR_WORKSPACE", -5: "SND_ERR_CHUNK", -6: "SND_ERR_CUDA", -7: "SND_ERR_STATE",
+    -8: "SND_ERR_TIMEOUT", -9: "SND_ERR_OVERFLOW", -10: "SND_ERR_NOMEM", -11: "SND_ERR_UNSUPPORTED",
+}
+ERR = {v: k for k, v in STATUS.items()}
+
+
+class SndOptions(ctypes.Structure):
+    _fields_ = [
+        ("cluster_size", ctypes.c_int32), ("k_leaf", ctypes.c_int32), ("k_internal", ctypes.c_int32),
+        ("graded_cap", ctypes.c_int32), ("enc_theta", ctypes.c_double), ("det_theta", ctypes.c_double),
+        ("sigma_min", ctypes.c_double), ("mf_alpha", ctypes.c_double), ("closing_size", ctypes.c_int32),
+        ("n_min_pixels", ctypes.c_int32), ("max_chunk", ctypes.c_int32), ("cand_capacity", ctypes.c_int32),
+        ("cell_capacity", ctypes.c_int32), ("run_capacity", ctypes.c_int32), ("flags", ctypes.c_int32),
+    ]
+
+
+class SndCandidate(ctypes.Structure):
+    _fields_ = [("dm_index", ctypes.c_int32), ("dm", ctypes.c_float), ("t", ctypes.c_int64),
+                ("snr", ctypes.c_float), ("width", ctypes.c_int32), ("npix", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SndPlanStats(ctypes.Structure):
+    _fields_ = [
+        ("nchan", ctypes.c_int32), ("ndm", ctypes.c_int32), ("mode", ctypes.c_int32),
+        ("branching", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("max_delay", ctypes.c_int32),
+        ("nlevels", ctypes.c_int32), ("nodes_per_level", ctypes.c_int32 * 24),
+        ("unique_per_level", ctypes.c_int64 * 24), ("adds_per_dm_sample", ctypes.c_double),
+        ("wmax", ctypes.c_int32), ("ring_words", ctypes.c_int32), ("hist_mem_bytes", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_size_t), ("samples_in", ctypes.c_int64), ("emitted", ctypes.c_int64),
+        ("scored", ctypes.c_int64), ("candidates_pending", ctypes.c_int32), ("tree_tile_dms", ctypes.c_int32),
+        ("tree_tile_words", ctypes.c_int32), ("tree_group_leaves", ctypes.c_int32),
+        ("tree_smem_bytes", ctypes.c_int32), ("max_patterns_per_group", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+
+CANDIDATE_DTYPE = np.dtype([("dm_index", "<i4"), ("dm", "<f4"), ("t", "<i8"), ("snr", "<f4"),
+                            ("width", "<i4"), ("npix", "<i4"), ("reserved", "<i4")])
+assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(SndCandidate) == 32
+
+EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", "snd_bind_workspace",
+           "snd_execute", "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table",
+           "snd_profile", "snd_profile_read", "snd_destroy", "snd_error_string")
+STAGES = ("encode", "tree", "mf", "candidates")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsnd.so not built at {LIB_PATH}: run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D, SZ, V = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                             ctypes.c_size_t, ctypes.c_void_p)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.snd_options_init.argtypes = [I32, ctypes.POINTER(SndOptions)]
+    lib.snd_plan.argtypes = [dp, I32, D, dp, I32, I32, I32, ctypes.POINTER(P)]
+    lib.snd_plan_ex.argtypes = [dp, I32, D, dp, I32, I32, I32, ctypes.POINTER(SndOptions), ctypes.POINTER(P)]
+    lib.snd_workspace_size.argtypes = [P]
+    lib.snd_workspace_size.restype = SZ
+    lib.snd_bind_workspace.argtypes = [P, V, SZ, V]
+    lib.snd_execute.argtypes = [P, V, I32, V, V, ctypes.POINTER(I32)]
+    lib.snd_execute_host.argtypes = [P, V, I32, V, V, ctypes.POINTER(I32)]
+    lib.snd_candidates.argtypes = [P, ctypes.POINTER(SndCandidate), I32, ctypes.POINTER(I32)]
+    lib.snd_plan_stats.argtypes = [P, ctypes.POINTER(SndPlanStats)]
+    lib.snd_delay_table.argtypes = [P, ctypes.POINTER(ctypes.c_int32), I64]
+    lib.snd_profile.argtypes = [P, ctypes.c_int]
+    lib.snd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    lib.snd_destroy.argtypes = [P]
+    lib.snd_destroy.restype = None
+    lib.snd_error_string.argtypes = [ctypes.c_int]
+    lib.snd_error_string.restype = ctypes.c_char_p
+    for name in ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_bind_workspace", "snd_execute",
+                 "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table", "snd_profile",
+                 "snd_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+class SndError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib.snd_error_string(code).decode()
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({msg})")
+
+
+def _check(code: int, where: str) -> int:
+    if code != 0:
+        raise SndError(code, where)
+    return code
+
+
+def options(mode: int, **kw) -> SndOptions:
+    o = SndOptions()
+    _check(lib.snd_options_init(mode, ctypes.byref(o)), "snd_options_init")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Plan:
+    """One SND plan (snd_plan_ex) plus a torch-allocated device workspace."""
+
+    def __init__(self, freqs, dt: float, dms, branching: int, mode: int, opts: SndOptions | None = None,
+                 bind: bool = True, device=None, stream=None):
+        self.freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+        self.dms = np.ascontiguousarray(dms, dtype=np.float64)
+        self.dt = float(dt)
+        self.mode = int(mode)
+        self.nchan = self.freqs.size
+        self.ndm = self.dms.size
+        self.opts = opts if opts is not None else options(mode)
+        h = ctypes.c_void_p()
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(lib.snd_plan_ex(self.freqs.ctypes.data_as(dp), self.nchan, self.dt, self.dms.ctypes.data_as(dp),
+                               self.ndm, int(branching), self.mode, ctypes.byref(self.opts), ctypes.byref(h)),
+               "snd_plan_ex")
+        self.handle = h
+        self.workspace = None
+        if bind:
+            self.bind(device=device, stream=stream)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.snd_destroy(h)
+            self.handle = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib.snd_workspace_size(self.handle))
+
+    def bind(self, device=None, stream=None, workspace=None):
+        import torch
+        n = self.workspace_bytes
+        if workspace is None:
+            workspace = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+        ptr = workspace.data_ptr()
+        off = (-ptr) % 256
+        self.workspace = workspace
+        _check(lib.snd_bind_workspace(self.handle, ctypes.c_void_p(ptr + off), n, _stream_ptr(stream)),
+               "snd_bind_workspace")
+
+    def execute(self, chunk, plane_out=None, stream=None) -> int:
+        """chunk: device uint8 tensor [nsamp][nchan]; plane_out: optional device tensor
+        [ndm][nemit] (int32, or float32 in float mode). Returns nemit."""
+        assert chunk.is_cuda and chunk.dtype.itemsize == 1 and chunk.is_contiguous()
+        nsamp = int(chunk.shape[0])
+        ne = ctypes.c_int32(0)
+        out = ctypes.c_void_p(plane_out.data_ptr()) if plane_out is not None else None
+        _check(lib.snd_execute(self.handle, ctypes.c_void_p(chunk.data_ptr()), nsamp, _stream_ptr(stream), out,
+                               ctypes.byref(ne)), "snd_execute")
+        return int(ne.value)
+
+    def execute_host(self, chunk, plane_out=None, stream=None) -> int:
+        """chunk: host uint8 array/tensor [nsamp][nchan] (pinned for an asynchronous copy)."""
+        if hasattr(chunk, "data_ptr"):
+            ptr, nsamp = chunk.data_ptr(), int(chunk.shape[0])
+        else:
+            chunk = np.ascontiguousarray(chunk, dtype=np.uint8)
+            ptr, nsamp = chunk.ctypes.data, chunk.shape[0]
+        ne = ctypes.c_int32(0)
+        out = ctypes.c_void_p(plane_out.data_ptr()) if plane_out is not None else None
+        _check(lib.snd_execute_host(self.handle, ctypes.c_void_p(ptr), nsamp, _stream_ptr(stream), out,
+                                    ctypes.byref(ne)), "snd_execute_host")
+        return int(ne.value)
+
+    def nemit_next(self, nsamp: int) -> int:
+        s = self.stats()
+        return max(0, s.samples_in + nsamp - s.max_delay) - s.emitted
+
+    def candidates(self, cap: int | None = None, check: bool = True):
+        """Synchronise and return (structured numpy array of candidates, status)."""
+        cap = int(self.opts.cand_capacity if cap is None else cap)
+        buf = (SndCandidate * max(cap, 1))()
+        n = ctypes.c_int32(0)
+        rc = lib.snd_candidates(self.handle, buf, cap, ctypes.byref(n))
+        if check:
+            _check(rc, "snd_candidates")
+        arr = np.frombuffer(bytes(buf)[: n.value * CANDIDATE_DTYPE.itemsize], dtype=CANDIDATE_DTYPE).copy()
+        return arr, rc
+
+    def stats(self) -> SndPlanStats:
+        s = SndPlanStats()
+        _check(lib.snd_plan_stats(self.handle, ctypes.byref(s)), "snd_plan_stats")
+        return s
+
+    def profile(self, enable: bool = True):
+        _check(lib.snd_profile(self.handle, int(enable)), "snd_profile")
+
+    def profile_read(self) -> dict:
+        """{stage: (milliseconds summed, timed launches)} since the last read."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_int64 * 4)()
+        _check(lib.snd_profile_read(self.handle, ms, cnt), "snd_profile_read")
+        return {STAGES[i]: (ms[i], cnt[i]) for i in range(4)}
+
+    def delay_table(self) -> np.ndarray:
+        out = np.zeros((self.ndm, self.nchan), dtype=np.int32)
+        _check(lib.snd_delay_table(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), out.size),
+               "snd_delay_table")
+        return out

@@ -1,0 +1,358 @@
+// Candidate detection (Methods, "Candidate detection"): threshold mask -> square binary
+// closing -> 8-connected labelling -> islands of at least N_min pixels -> one candidate per
+// island at its peak pixel.
+//
+//  * Closing (side 2r+1): dilation with outside = 0, then erosion with outside = 1, each
+//    done separably (rows, then DM columns) on the bit-packed mask, 32 samples per word.
+//  * Labelling works on runs of set bits of the closed mask. Runs are counted and written
+//    per row (deterministic order: row-major), runs of adjacent rows that touch under
+//    8-connectivity (s_j <= e_i and s_i <= e_j, ends exclusive) are united in a lock-free
+//    union-find whose root is the smallest run index, and island sizes are summed per root.
+//  * Peak: each original-mask cell finds its run and raises its island's 64-bit key
+//    (S/N float bits << 32 | ~cell index) with atomicMax: larger S/N wins, ties go to the
+//    smaller cell index = smaller DM row, then smaller t.
+//  * The block's candidates are ranked by (t, DM index) and appended to the plan's list.
+// Every data-dependent loop is bounded; a bound that is hit sets a status bit instead of
+// spinning.
+
+#include "snd_internal.h"
+
+namespace snd {
+namespace {
+
+constexpr int kGridStride = 152 * 4;
+
+__global__ void k_close_h(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int mw, int nb,
+                          int r, int erode) {
+  const int d = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nbw = (nb + 31) >> 5;
+  if (q >= nbw) return;
+  const uint32_t outside = erode ? 0xFFFFFFFFu : 0u;
+  const uint32_t tailvalid = (nb & 31) ? ((1u << (nb & 31)) - 1u) : 0xFFFFFFFFu;
+  auto word = [&](int qq) -> uint32_t {
+    if (qq < 0 || qq >= nbw) return outside;
+    uint32_t w = in[static_cast<size_t>(d) * mw + qq];
+    if (qq == nbw - 1) w = erode ? (w | ~tailvalid) : (w & tailvalid);
+    return w;
+  };
+  const uint32_t a = word(q - 1), b = word(q), c = word(q + 1);
+  uint32_t acc = b;
+  for (int k = 1; k <= r; ++k) {
+    const uint32_t right = __funnelshift_r(b, c, k);  // bit t <- bit t+k
+    const uint32_t left = __funnelshift_l(a, b, k);   // bit t <- bit t-k
+    acc = erode ? (acc & right & left) : (acc | right | left);
+  }
+  if (q == nbw - 1) acc &= tailvalid;
+  out[static_cast<size_t>(d) * mw + q] = acc;
+}
+
+__global__ void k_close_v(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int ndm, int mw,
+                          int nb, int r, int erode) {
+  const int d = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nbw = (nb + 31) >> 5;
+  if (q >= nbw) return;
+  uint32_t acc = erode ? 0xFFFFFFFFu : 0u;
+  for (int j = -r; j <= r; ++j) {
+    const int dd = d + j;
+    if (dd < 0 || dd >= ndm) continue;  // outside: 1 for erosion, 0 for dilation (no-ops)
+    const uint32_t w = in[static_cast<size_t>(dd) * mw + q];
+    acc = erode ? (acc & w) : (acc | w);
+  }
+  if (q == nbw - 1 && (nb & 31)) acc &= (1u << (nb & 31)) - 1u;
+  out[static_cast<size_t>(d) * mw + q] = acc;
+}
+
+// One warp per row: number of runs (run starts) of the closed mask.
+__global__ void k_run_count(const uint32_t* __restrict__ m, int ndm, int mw, int nb, int32_t* row_runs) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= ndm) return;
+  const int nbw = (nb + 31) >> 5;
+  const uint32_t* row = m + static_cast<size_t>(warp) * mw;
+  int cnt = 0;
+  for (int q0 = 0; q0 < nbw; q0 += 32) {
+    const int q = q0 + lane;
+    const uint32_t w = q < nbw ? row[q] : 0u;
+    const uint32_t prev = q > 0 && q - 1 < nbw ? row[q - 1] : 0u;
+    cnt += __popc(w & ~((w << 1) | (prev >> 31)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
+  if (lane == 0) row_runs[warp] = cnt;
+}
+
+// Single CTA: exclusive scan of the per-row run counts; total -> counters[kCntRuns].
+__global__ void k_scan_rows(int32_t* row_runs, int ndm, uint32_t* counters, int run_cap) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int per = (ndm + 1023) / 1024;
+  const int lo = min(ndm, tid * per), hi = min(ndm, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += row_runs[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int i = 0; i < 1024; ++i) {
+      const int v = part[i];
+      part[i] = acc;
+      acc += v;
+    }
+    row_runs[ndm] = acc;
+    counters[kCntRuns] = static_cast<uint32_t>(acc);
+    if (acc > run_cap) atomicOr(&counters[kCntStatus], kStatusRunOverflow);
+  }
+  __syncthreads();
+  int acc = part[tid];
+  for (int i = lo; i < hi; ++i) {
+    const int v = row_runs[i];
+    row_runs[i] = acc;
+    acc += v;
+  }
+}
+
+// One warp per row: write runs [start, end) in order, initialise union-find state.
+__global__ void k_run_write(const uint32_t* __restrict__ m, int ndm, int mw, int nb, const int32_t* row_runs,
+                            int32_t* run_start, int32_t* run_end, int32_t* run_row, int32_t* parent,
+                            int32_t* npix, unsigned long long* peak, int32_t* pwidth, int run_cap) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= ndm) return;
+  if (row_runs[ndm] > run_cap) return;
+  const int nbw = (nb + 31) >> 5;
+  const uint32_t* row = m + static_cast<size_t>(warp) * mw;
+  int base_s = row_runs[warp], base_e = row_runs[warp];
+  for (int q0 = 0; q0 < nbw; q0 += 32) {
+    const int q = q0 + lane;
+    const uint32_t w = q < nbw ? row[q] : 0u;
+    const uint32_t prev = (q > 0 && q - 1 < nbw) ? row[q - 1] : 0u;
+    const uint32_t next = (q + 1 < nbw) ? row[q + 1] : 0u;
+    uint32_t st = w & ~((w << 1) | (prev >> 31));
+    uint32_t en = w & ~((w >> 1) | (next << 31));
+    const int ns = __popc(st), ne = __popc(en);
+    int is = ns, ie = ne;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int us = __shfl_up_sync(0xFFFFFFFFu, is, o);
+      const int ue = __shfl_up_sync(0xFFFFFFFFu, ie, o);
+      if (lane >= o) {
+        is += us;
+        ie += ue;
+      }
+    }
+    int ps = base_s + is - ns, pe = base_e + ie - ne;
+    while (st) {
+      const int b = __ffs(st) - 1;
+      st &= st - 1;
+      run_start[ps] = q * 32 + b;
+      run_row[ps] = warp;
+      parent[ps] = ps;
+      npix[ps] = 0;
+      peak[ps] = 0ull;
+      pwidth[ps] = 0;
+      ++ps;
+    }
+    while (en) {
+      const int b = __ffs(en) - 1;
+      en &= en - 1;
+      run_end[pe++] = q * 32 + b + 1;
+    }
+    base_s += __shfl_sync(0xFFFFFFFFu, is, 31);
+    base_e += __shfl_sync(0xFFFFFFFFu, ie, 31);
+  }
+}
+
+__device__ __forceinline__ int find_root(const int32_t* parent, int x, uint32_t* status) {
+  const volatile int32_t* vp = parent;
+  for (int it = 0; it < (1 << 20); ++it) {
+    const int p = vp[x];
+    if (p == x) return x;
+    x = p;
+  }
+  atomicOr(status, kStatusUnionTimeout);
+  return x;
+}
+
+__device__ __forceinline__ void unite(int32_t* parent, int a, int b, uint32_t* status) {
+  for (int it = 0; it < 4096; ++it) {
+    a = find_root(parent, a, status);
+    b = find_root(parent, b, status);
+    if (a == b) return;
+    if (a < b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    if (atomicCAS(&parent[a], a, b) == a) return;
+  }
+  atomicOr(status, kStatusUnionTimeout);
+}
+
+__device__ __forceinline__ int runs_total(const int32_t* row_runs, int ndm, int run_cap) {
+  const int n = row_runs[ndm];
+  return n > run_cap ? -1 : n;
+}
+
+__global__ void k_union(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
+                        const int32_t* run_end, const int32_t* run_row, int32_t* parent, uint32_t* counters) {
+  const int n = runs_total(row_runs, ndm, run_cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = run_row[i];
+    if (d == 0) continue;
+    const int s = run_start[i], e = run_end[i];
+    int lo = row_runs[d - 1], hi = row_runs[d];
+    // first run of the row above with end >= s
+    int a = lo, b = hi;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (run_end[mid] >= s) b = mid; else a = mid + 1;
+    }
+    for (int j = a; j < hi && run_start[j] <= e; ++j) unite(parent, i, j, &counters[kCntStatus]);
+  }
+}
+
+__global__ void k_flatten(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
+                          const int32_t* run_end, int32_t* parent, int32_t* npix, uint32_t* counters) {
+  const int n = runs_total(row_runs, ndm, run_cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int r = find_root(parent, i, &counters[kCntStatus]);
+    parent[i] = r;
+    atomicAdd(&npix[r], run_end[i] - run_start[i]);
+  }
+}
+
+// Run of row d that contains column t, or -1.
+__device__ __forceinline__ int run_of(const int32_t* row_runs, const int32_t* run_start, const int32_t* run_end,
+                                      int d, int t) {
+  const int lo = row_runs[d], hi = row_runs[d + 1];
+  int a = lo - 1, b = hi - 1;  // last run with start <= t lies in [a, b]; a == lo - 1: none
+  while (a < b) {
+    const int mid = (a + b + 1) >> 1;
+    if (run_start[mid] <= t) a = mid; else b = mid - 1;
+  }
+  if (a < lo || run_end[a] <= t) return -1;
+  return a;
+}
+
+__global__ void k_peak(const MfCell* cells, uint32_t* counters, int cell_cap, int nb, const int32_t* row_runs,
+                       int ndm, int run_cap, const int32_t* run_start, const int32_t* run_end,
+                       const int32_t* parent, unsigned long long* peak, int32_t* pwidth, int pass) {
+  if (runs_total(row_runs, ndm, run_cap) < 0) return;
+  const int nc = min(static_cast<int>(counters[kCntCells]), cell_cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const MfCell c = cells[i];
+    const int d = static_cast<int>(c.cell / static_cast<uint32_t>(nb));
+    const int t = static_cast<int>(c.cell - static_cast<uint32_t>(d) * static_cast<uint32_t>(nb));
+    const int run = run_of(row_runs, run_start, run_end, d, t);
+    if (run < 0) {
+      atomicOr(&counters[kCntStatus], kStatusBounds);
+      continue;
+    }
+    const int root = parent[run];
+    const unsigned long long key =
+        (static_cast<unsigned long long>(__float_as_uint(c.snr)) << 32) | (0xFFFFFFFFull - c.cell);
+    if (pass == 0) {
+      atomicMax(&peak[root], key);
+    } else if (peak[root] == key) {
+      pwidth[root] = c.width;
+    }
+  }
+}
+
+__global__ void k_emit(const int32_t* row_runs, int ndm, int run_cap, const int32_t* parent, const int32_t* npix,
+                       const unsigned long long* peak, const int32_t* pwidth, int nb, int n_min,
+                       long long f_prev, const float* dm_f32, snd_candidate_t* bcand, int cand_cap,
+                       uint32_t* counters) {
+  const int n = runs_total(row_runs, ndm, run_cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (parent[i] != i || npix[i] < n_min || peak[i] == 0ull) continue;
+    const uint32_t cell = 0xFFFFFFFFu - static_cast<uint32_t>(peak[i] & 0xFFFFFFFFull);
+    const int d = static_cast<int>(cell / static_cast<uint32_t>(nb));
+    const int t = static_cast<int>(cell - static_cast<uint32_t>(d) * static_cast<uint32_t>(nb));
+    const uint32_t idx = atomicAdd(&counters[kCntBlockCands], 1u);
+    if (idx >= static_cast<uint32_t>(cand_cap)) {
+      atomicOr(&counters[kCntStatus], kStatusBlockCandOverflow);
+      continue;
+    }
+    snd_candidate_t c;
+    c.dm_index = d;
+    c.dm = dm_f32[d];
+    c.t = f_prev + t;
+    c.snr = __uint_as_float(static_cast<uint32_t>(peak[i] >> 32));
+    c.width = pwidth[i];
+    c.npix = npix[i];
+    c.reserved = 0;
+    bcand[idx] = c;
+  }
+}
+
+// Rank every block candidate by (t, dm_index) (keys are distinct: one peak pixel per island)
+// and place it after the candidates already held.
+__global__ void k_rank_append(const snd_candidate_t* bcand, snd_candidate_t* cand, uint32_t* counters,
+                              int cand_cap) {
+  const int n = min(static_cast<int>(counters[kCntBlockCands]), cand_cap);
+  const int base = static_cast<int>(counters[kCntCands]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const snd_candidate_t ci = bcand[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const snd_candidate_t cj = bcand[j];
+      rank += (cj.t < ci.t) || (cj.t == ci.t && cj.dm_index < ci.dm_index);
+    }
+    const int pos = base + rank;
+    if (pos < cand_cap) {
+      cand[pos] = ci;
+    } else {
+      atomicOr(&counters[kCntStatus], kStatusCandOverflow);
+    }
+  }
+}
+
+__global__ void k_bump(uint32_t* counters, int cand_cap) {
+  const int n = min(static_cast<int>(counters[kCntBlockCands]), cand_cap);
+  const int tot = static_cast<int>(counters[kCntCands]) + n;
+  counters[kCntCands] = static_cast<uint32_t>(min(tot, cand_cap));
+}
+
+}  // namespace
+
+cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  const DevPtrs& dp = p.dp;
+  const int r = p.closing / 2;
+  const int nbw = (nb + 31) / 32;
+  dim3 blk(128), grd((nbw + 127) / 128, p.ndm);
+  if (r > 0) {
+    p.launches += 4;
+    k_close_h<<<grd, blk, 0, s>>>(dp.mask, dp.mask2, p.mw, nb, r, 0);
+    k_close_v<<<grd, blk, 0, s>>>(dp.mask2, dp.mask3, p.ndm, p.mw, nb, r, 0);
+    k_close_h<<<grd, blk, 0, s>>>(dp.mask3, dp.mask2, p.mw, nb, r, 1);
+    k_close_v<<<grd, blk, 0, s>>>(dp.mask2, dp.mask3, p.ndm, p.mw, nb, r, 1);
+  } else {
+    cudaMemcpyAsync(dp.mask3, dp.mask, sizeof(uint32_t) * static_cast<size_t>(p.ndm) * p.mw,
+                    cudaMemcpyDeviceToDevice, s);
+  }
+  const int wblocks = (p.ndm * 32 + 255) / 256;
+  k_run_count<<<wblocks, 256, 0, s>>>(dp.mask3, p.ndm, p.mw, nb, dp.row_runs);
+  k_scan_rows<<<1, 1024, 0, s>>>(dp.row_runs, p.ndm, dp.counters, p.run_cap);
+  k_run_write<<<wblocks, 256, 0, s>>>(dp.mask3, p.ndm, p.mw, nb, dp.row_runs, dp.run_start, dp.run_end,
+                                      dp.run_row, dp.parent, dp.npix, dp.peak, dp.pwidth, p.run_cap);
+  k_union<<<kGridStride, 256, 0, s>>>(dp.row_runs, p.ndm, p.run_cap, dp.run_start, dp.run_end, dp.run_row,
+                                      dp.parent, dp.counters);
+  k_flatten<<<kGridStride, 256, 0, s>>>(dp.row_runs, p.ndm, p.run_cap, dp.run_start, dp.run_end, dp.parent,
+                                        dp.npix, dp.counters);
+  k_peak<<<kGridStride, 256, 0, s>>>(dp.cells, dp.counters, p.cell_cap, nb, dp.row_runs, p.ndm, p.run_cap,
+                                     dp.run_start, dp.run_end, dp.parent, dp.peak, dp.pwidth, 0);
+  k_peak<<<kGridStride, 256, 0, s>>>(dp.cells, dp.counters, p.cell_cap, nb, dp.row_runs, p.ndm, p.run_cap,
+                                     dp.run_start, dp.run_end, dp.parent, dp.peak, dp.pwidth, 1);
+  k_emit<<<kGridStride, 256, 0, s>>>(dp.row_runs, p.ndm, p.run_cap, dp.parent, dp.npix, dp.peak, dp.pwidth, nb,
+                                     p.n_min, f_prev, dp.dm_f32, dp.bcand, p.cand_cap, dp.counters);
+  k_rank_append<<<kGridStride, 256, 0, s>>>(dp.bcand, dp.cand, dp.counters, p.cand_cap);
+  k_bump<<<1, 1, 0, s>>>(dp.counters, p.cand_cap);
+  p.launches += 11;
+  return cudaGetLastError();
+}
+
+}  // namespace snd

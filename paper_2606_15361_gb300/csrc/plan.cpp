@@ -1,0 +1,551 @@
+// Host side of the SND library: options, plan construction, statistics, error strings.
+//
+// Plan construction follows Methods, "The Spiking Neural Dedispersion algorithm":
+// integer delays per channel and trial DM, leaf clusters of C contiguous channels,
+// B-ary levels above them, and enumeration of the distinct integer-delay patterns of
+// every node. The GPU evaluates the tree from the leaf patterns (see tree.cu); the
+// deeper-level pattern counts are kept as plan statistics (neuron counts, additions per
+// DM-sample, Eq. hist_mem).
+//
+// This file must be compiled without floating-point contraction (-ffp-contract=off):
+// the delay rounding and the width rule are FP64 decisions with a fixed operation order.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "snd_internal.h"
+
+using snd::Plan;
+
+namespace {
+
+constexpr double kDm = 4.148808e3;  // MHz^2 s pc^-1 cm^3
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct VecHash {
+  size_t operator()(const std::vector<int32_t>& v) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int32_t x : v) {
+      h ^= static_cast<uint32_t>(x);
+      h *= 1099511628211ull;
+    }
+    return static_cast<size_t>(h ^ (h >> 29));
+  }
+};
+
+int choose_tree_geometry(Plan& p);
+
+}  // namespace
+
+extern "C" int snd_options_init(snd_mode_t mode, snd_options_t* o) {
+  if (!o) return SND_ERR_ARG;
+  if (mode != SND_MODE_BINARY && mode != SND_MODE_GRADED && mode != SND_MODE_FLOAT)
+    return SND_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  // Supplementary Table S1 operating points; C = 4 from its SND-tree block.
+  o->cluster_size = 4;
+  o->k_leaf = 2;
+  o->k_internal = 2;
+  o->graded_cap = 255;
+  o->enc_theta = (mode == SND_MODE_GRADED) ? 0.75 : 1.5;
+  o->det_theta = 7.0;
+  o->sigma_min = 0.20;
+  o->mf_alpha = 0.1;  // Methods, "Matched filtering"
+  o->closing_size = 9;
+  o->n_min_pixels = 10;
+  o->max_chunk = 32768;
+  o->cand_capacity = 65536;
+  o->cell_capacity = 1 << 20;
+  o->run_capacity = 1 << 21;
+  o->flags = 0;
+  return SND_OK;
+}
+
+namespace snd {
+
+int build_plan(Plan& p) {
+  const int nchan = p.nchan, ndm = p.ndm, C = p.C, B = p.B;
+  // --- delays (Methods, "Incoherent dedispersion") ---
+  std::vector<double> inv2(nchan);
+  for (int c = 0; c < nchan; ++c) inv2[c] = 1.0 / (p.freqs[c] * p.freqs[c]);
+  p.ref_chan = 0;
+  p.min_chan = 0;
+  for (int c = 1; c < nchan; ++c) {
+    if (p.freqs[c] > p.freqs[p.ref_chan]) p.ref_chan = c;
+    if (p.freqs[c] < p.freqs[p.min_chan]) p.min_chan = c;
+  }
+  p.delays.assign(static_cast<size_t>(ndm) * nchan, 0);
+  int64_t dmax = 0;
+  for (int d = 0; d < ndm; ++d) {
+    const double kd = kDm * p.dms[d];
+    for (int c = 0; c < nchan; ++c) {
+      const double x = (kd * (inv2[c] - inv2[p.ref_chan])) / p.dt;
+      const double r = std::floor(x + 0.5);
+      if (!(r >= 0.0) || r > 1.0e9) return SND_ERR_DM;
+      p.delays[static_cast<size_t>(d) * nchan + c] = static_cast<int32_t>(r);
+      dmax = std::max<int64_t>(dmax, static_cast<int64_t>(r));
+    }
+  }
+  p.D = static_cast<int>(dmax);
+
+  // --- boxcar widths (Methods, "Matched filtering") ---
+  p.width_mask.assign(ndm, 0);
+  p.wmax = 1;
+  for (int d = 0; d < ndm; ++d) {
+    const double sweep = ((kDm * p.dms[d]) * (inv2[p.min_chan] - inv2[p.ref_chan])) / p.dt;
+    const double lim = p.mf_alpha * sweep;
+    uint16_t m = 0x000F;  // 1, 2, 4, 8
+    for (int j = 4; j < kNumWidthSlots; ++j)
+      if (static_cast<double>(1 << j) <= lim) m |= static_cast<uint16_t>(1u << j);
+    p.width_mask[d] = m;
+    for (int j = 0; j < kNumWidthSlots; ++j)
+      if (m & (1u << j)) p.wmax = std::max(p.wmax, 1 << j);
+  }
+
+  // --- tree levels (Methods, "Leaf clusters" / "Tree levels") ---
+  p.level_nodes.clear();
+  p.level_nodes.push_back((nchan + C - 1) / C);
+  while (p.level_nodes.back() > 1) p.level_nodes.push_back((p.level_nodes.back() + B - 1) / B);
+  p.nlev = static_cast<int>(p.level_nodes.size());
+  if (p.nlev > kMaxLevels) return SND_ERR_UNSUPPORTED;
+  p.nleaves = p.level_nodes[0];
+  const int NL = p.nleaves;
+
+  // channel range and reference channel of every node, level by level
+  std::vector<std::vector<int>> node_lo(p.nlev), node_hi(p.nlev), node_ref(p.nlev);
+  for (int l = 0; l < p.nlev; ++l) {
+    const int n = p.level_nodes[l];
+    node_lo[l].resize(n);
+    node_hi[l].resize(n);
+    node_ref[l].resize(n);
+    for (int i = 0; i < n; ++i) {
+      int lo, hi;
+      if (l == 0) {
+        lo = i * C;
+        hi = std::min(nchan, lo + C);
+      } else {
+        lo = node_lo[l - 1][i * B];
+        hi = node_hi[l - 1][std::min(p.level_nodes[l - 1], (i + 1) * B) - 1];
+      }
+      node_lo[l][i] = lo;
+      node_hi[l][i] = hi;
+      int r = lo;
+      for (int c = lo + 1; c < hi; ++c)
+        if (p.freqs[c] > p.freqs[r]) r = c;
+      node_ref[l][i] = r;
+    }
+  }
+
+  // --- leaf patterns: distinct relative delays delta_c(d) - delta_ref(d) per leaf ---
+  p.leaf_pid.assign(static_cast<size_t>(ndm) * NL, 0);
+  std::vector<int32_t> leaf_loc(static_cast<size_t>(ndm) * NL, 0);  // id local to the leaf
+  p.pat_rel.clear();
+  p.npat = 0;
+  std::vector<int> leaf_npat(NL, 0);
+  int64_t din = 0;
+  {
+    std::vector<int32_t> key(C);
+    for (int k = 0; k < NL; ++k) {
+      std::unordered_map<std::vector<int32_t>, int, VecHash> ids;
+      const int base = p.npat;
+      const int lo = node_lo[0][k], hi = node_hi[0][k], r = node_ref[0][k];
+      for (int d = 0; d < ndm; ++d) {
+        const int32_t* row = &p.delays[static_cast<size_t>(d) * nchan];
+        std::fill(key.begin(), key.end(), 0);
+        for (int c = lo; c < hi; ++c) {
+          key[c - lo] = row[c] - row[r];
+          din = std::max<int64_t>(din, key[c - lo]);
+        }
+        auto it = ids.find(key);
+        int id;
+        if (it == ids.end()) {
+          id = p.npat++;
+          ids.emplace(key, id);
+          p.pat_rel.insert(p.pat_rel.end(), key.begin(), key.end());
+          leaf_npat[k]++;
+        } else {
+          id = it->second;
+        }
+        p.leaf_pid[static_cast<size_t>(d) * NL + k] = id;
+        leaf_loc[static_cast<size_t>(d) * NL + k] = id - base;
+      }
+    }
+  }
+
+  // --- statistics: distinct patterns at every level, additions, Eq. hist_mem ---
+  {
+    p.level_unique.assign(p.nlev, 0);
+    double adds = 0.0;
+    const int bits_out = (p.mode == SND_MODE_BINARY) ? 1 : (p.mode == SND_MODE_GRADED ? 8 : 32);
+    double hist_bits_bytes = std::ceil(static_cast<double>(nchan) * static_cast<double>(din) / 8.0);
+    // node pattern ids of the level below, [ndm][n]
+    std::vector<int32_t> below(leaf_loc);
+    std::vector<int> below_count(leaf_npat);
+    for (int k = 0; k < NL; ++k) {
+      p.level_unique[0] += leaf_npat[k];
+      adds += static_cast<double>(leaf_npat[k]) * (node_hi[0][k] - node_lo[0][k] - 1);
+    }
+    for (int l = 0; l < p.nlev; ++l) {
+      const int n = p.level_nodes[l];
+      // ring depth d_{n,m}: largest shift the parent requests from node n in pattern m
+      if (l + 1 < p.nlev) {
+        for (int i = 0; i < n; ++i) {
+          const int par = i / B;
+          std::vector<int64_t> depth(below_count[i], 0);
+          for (int d = 0; d < ndm; ++d) {
+            const int32_t* row = &p.delays[static_cast<size_t>(d) * nchan];
+            const int64_t sh = row[node_ref[l][i]] - row[node_ref[l + 1][par]];
+            int32_t m = below[static_cast<size_t>(d) * n + i];
+            depth[m] = std::max(depth[m], sh);
+          }
+          for (int64_t dd : depth)
+            hist_bits_bytes += std::ceil(static_cast<double>(dd) * bits_out / 8.0);
+        }
+      }
+      if (l + 1 >= p.nlev) break;
+      const int np = p.level_nodes[l + 1];
+      std::vector<int32_t> cur(static_cast<size_t>(ndm) * np, 0);
+      std::vector<int> cur_count(np, 0);
+      for (int j = 0; j < np; ++j) {
+        const int c0 = j * B, c1 = std::min(n, (j + 1) * B);
+        std::unordered_map<std::vector<int32_t>, int, VecHash> ids;
+        std::vector<int32_t> key(2 * (c1 - c0));
+        for (int d = 0; d < ndm; ++d) {
+          const int32_t* row = &p.delays[static_cast<size_t>(d) * nchan];
+          for (int i = c0; i < c1; ++i) {
+            key[2 * (i - c0)] = below[static_cast<size_t>(d) * n + i];
+            key[2 * (i - c0) + 1] = row[node_ref[l][i]] - row[node_ref[l + 1][j]];
+          }
+          auto it = ids.find(key);
+          int id;
+          if (it == ids.end()) {
+            id = cur_count[j]++;
+            ids.emplace(key, id);
+          } else {
+            id = it->second;
+          }
+          cur[static_cast<size_t>(d) * np + j] = id;
+        }
+        p.level_unique[l + 1] += cur_count[j];
+        adds += static_cast<double>(cur_count[j]) * (c1 - c0 - 1);
+      }
+      below.swap(cur);
+      below_count.swap(cur_count);
+    }
+    p.adds_per_dm_sample = adds / ndm;
+    p.hist_mem_bytes = static_cast<int64_t>(hist_bits_bytes);
+  }
+
+  // --- DM tiles: distinct leaf patterns per (tile, leaf), per-DM index and shift ---
+  int rc = choose_tree_geometry(p);
+  if (rc) return rc;
+
+  // --- ring, plane ring and workspace layout ---
+  const TreeGeom& g = p.geom;
+  const int maxw_chunk = (p.max_chunk + 31) / 32;
+  // words reachable from one emitted block: delay + chunk + tile padding + funnel partner
+  p.R = (p.D >> 5) + maxw_chunk + g.span + 8;
+  p.Lp = static_cast<int>(align_up(static_cast<size_t>(p.wmax) - 1 + p.max_chunk + 96, 32));
+  p.mw = (p.Lp + 31) / 32;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  p.off.ring = take(sizeof(uint32_t) * static_cast<size_t>(nchan) * 2 * p.R);
+  p.off.hist = take(sizeof(uint32_t) * static_cast<size_t>(nchan) * 256);
+  p.off.levels = take(sizeof(int32_t) * nchan);
+  p.off.plane = take(sizeof(int32_t) * static_cast<size_t>(ndm) * p.Lp);
+  p.off.mask = take(sizeof(uint32_t) * static_cast<size_t>(ndm) * p.mw);
+  p.off.mask2 = take(sizeof(uint32_t) * static_cast<size_t>(ndm) * p.mw);
+  p.off.mask3 = take(sizeof(uint32_t) * static_cast<size_t>(ndm) * p.mw);
+  p.off.cells = take(sizeof(MfCell) * static_cast<size_t>(p.cell_cap));
+  p.off.counters = take(sizeof(uint32_t) * kCntSlots);
+  p.off.row_runs = take(sizeof(int32_t) * (static_cast<size_t>(ndm) + 1));
+  p.off.run_start = take(sizeof(int32_t) * static_cast<size_t>(p.run_cap));
+  p.off.run_end = take(sizeof(int32_t) * static_cast<size_t>(p.run_cap));
+  p.off.run_row = take(sizeof(int32_t) * static_cast<size_t>(p.run_cap));
+  p.off.parent = take(sizeof(int32_t) * static_cast<size_t>(p.run_cap));
+  p.off.npix = take(sizeof(int32_t) * static_cast<size_t>(p.run_cap));
+  p.off.peak = take(sizeof(unsigned long long) * static_cast<size_t>(p.run_cap));
+  p.off.pwidth = take(sizeof(int32_t) * static_cast<size_t>(p.run_cap));
+  p.off.bcand = take(sizeof(snd_candidate_t) * static_cast<size_t>(p.cand_cap));
+  p.off.cand = take(sizeof(snd_candidate_t) * static_cast<size_t>(p.cand_cap));
+  p.off.staging = take(static_cast<size_t>(p.max_chunk) * nchan);
+  p.off.width_mask = take(sizeof(uint16_t) * ndm);
+  p.off.dm_f32 = take(sizeof(float) * ndm);
+  p.off.tp_off = take(sizeof(int32_t) * p.tp_off.size());
+  p.off.tp_pid = take(sizeof(int32_t) * std::max<size_t>(1, p.tp_pid.size()));
+  p.off.tp_smin = take(sizeof(int32_t) * std::max<size_t>(1, p.tp_smin.size()));
+  p.off.tp_leaf = take(sizeof(int32_t) * std::max<size_t>(1, p.tp_leaf.size()));
+  p.off.dl_lp = take(p.dl_lp.size());
+  p.off.dl_sh = take(sizeof(int32_t) * p.dl_sh.size());
+  p.off.pat_rel = take(sizeof(int32_t) * std::max<size_t>(1, p.pat_rel.size()));
+  p.off.delays = take(sizeof(int32_t) * p.delays.size());
+  p.ws_bytes = o;
+  return SND_OK;
+}
+
+}  // namespace snd
+
+namespace {
+
+// Tree kernel geometry: DM rows per CTA (one warp each), 32-sample words per lane, and
+// how many leaves are staged per shared-memory round so that the staged leaf-pattern
+// series fit the shared-memory budget.
+int choose_tree_geometry(Plan& p) {
+  snd::TreeGeom& g = p.geom;
+  const int ndm = p.ndm, NL = p.nleaves;
+  g.dms_per_cta = 8;
+  g.kw = snd::tree_kw(p.mode, p.nlev, p.KL > p.KI ? p.KL : p.KI);
+  g.tile_words = 32 * g.kw;
+  g.planes = (p.mode == SND_MODE_BINARY) ? 1 : 3;
+  g.ndm_tiles = (ndm + g.dms_per_cta - 1) / g.dms_per_cta;
+
+  p.tp_off.assign(static_cast<size_t>(g.ndm_tiles) * NL + 1, 0);
+  p.tp_pid.clear();
+  p.tp_smin.clear();
+  p.tp_leaf.clear();
+  p.dl_lp.assign(static_cast<size_t>(ndm) * NL, 0);
+  p.dl_sh.assign(static_cast<size_t>(ndm) * NL, 0);
+  int64_t dspread = 0;
+  std::vector<int> npat_tl(static_cast<size_t>(g.ndm_tiles) * NL, 0);
+  for (int t = 0; t < g.ndm_tiles; ++t) {
+    const int d0 = t * g.dms_per_cta, d1 = std::min(ndm, d0 + g.dms_per_cta);
+    for (int k = 0; k < NL; ++k) {
+      // reference channel of the leaf: highest frequency among its channels
+      int r = k * p.C;
+      for (int c = k * p.C + 1; c < std::min(p.nchan, (k + 1) * p.C); ++c)
+        if (p.freqs[c] > p.freqs[r]) r = c;
+      const size_t at = static_cast<size_t>(t) * NL + k;
+      p.tp_off[at] = static_cast<int32_t>(p.tp_pid.size());
+      std::vector<int32_t> pids, smin, smax;
+      for (int d = d0; d < d1; ++d) {
+        const int32_t pid = p.leaf_pid[static_cast<size_t>(d) * NL + k];
+        const int32_t sh = p.delays[static_cast<size_t>(d) * p.nchan + r];
+        int idx = -1;
+        for (size_t i = 0; i < pids.size(); ++i)
+          if (pids[i] == pid) idx = static_cast<int>(i);
+        if (idx < 0) {
+          idx = static_cast<int>(pids.size());
+          pids.push_back(pid);
+          smin.push_back(sh);
+          smax.push_back(sh);
+        } else {
+          smin[idx] = std::min(smin[idx], sh);
+          smax[idx] = std::max(smax[idx], sh);
+        }
+        p.dl_lp[static_cast<size_t>(d) * NL + k] = static_cast<uint8_t>(idx);
+        p.dl_sh[static_cast<size_t>(d) * NL + k] = sh;
+      }
+      for (size_t i = 0; i < pids.size(); ++i) {
+        p.tp_pid.push_back(pids[i]);
+        p.tp_smin.push_back(smin[i]);
+        p.tp_leaf.push_back(k);
+        dspread = std::max<int64_t>(dspread, static_cast<int64_t>(smax[i]) - smin[i]);
+      }
+      npat_tl[at] = static_cast<int>(pids.size());
+    }
+  }
+  p.tp_off.back() = static_cast<int32_t>(p.tp_pid.size());
+  g.span = g.tile_words + static_cast<int>(dspread >> 5) + 2;
+
+  // largest group that fits the budget
+  const int budget = 64 * 1024;
+  int best = 1, best_pat = 0;
+  for (int G = 1; G <= NL; ++G) {
+    int mp = 0;
+    for (int t = 0; t < g.ndm_tiles; ++t)
+      for (int k0 = 0; k0 < NL; k0 += G) {
+        int s = 0;
+        for (int k = k0; k < std::min(NL, k0 + G); ++k) s += npat_tl[static_cast<size_t>(t) * NL + k];
+        mp = std::max(mp, s);
+      }
+    // series + meta + per-entry ring offsets/shifts (C each) + entry leaf
+    const int64_t bytes = static_cast<int64_t>(mp) * g.planes * g.span * 4 +
+                          static_cast<int64_t>(g.dms_per_cta) * G * 4 +
+                          static_cast<int64_t>(mp) * (2 * p.C + 1) * 4;
+    if (G == 1 || bytes <= budget) {
+      best = G;
+      best_pat = mp;
+      g.smem_bytes = static_cast<int>(bytes);
+    }
+    if (bytes > budget) break;
+    if (G >= 64) break;
+  }
+  g.group_leaves = best;
+  g.max_pat_group = best_pat;
+  if (g.smem_bytes > 200 * 1024) return SND_ERR_UNSUPPORTED;
+  return SND_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
+                           const double* dm_grid, int32_t ndm, int32_t branching, snd_mode_t mode,
+                           const snd_options_t* opts, snd_plan_t* out) {
+  if (out) *out = nullptr;
+  if (!out || !freqs_mhz || !dm_grid || nchan < 1 || ndm < 1 || branching < 2 || branching > 64)
+    return SND_ERR_ARG;
+  if (mode != SND_MODE_BINARY && mode != SND_MODE_GRADED && mode != SND_MODE_FLOAT) return SND_ERR_ARG;
+  if (!finite_pos(dt_s)) return SND_ERR_ARG;
+  if (nchan > 65536 || ndm > 65536) return SND_ERR_UNSUPPORTED;
+  snd_options_t o;
+  if (opts) {
+    o = *opts;
+  } else {
+    snd_options_init(mode, &o);
+  }
+  if (o.flags & ~SND_FLAG_REFERENCE_TREE) return SND_ERR_ARG;
+  if (o.cluster_size < 1 || o.cluster_size > 7) return SND_ERR_UNSUPPORTED;
+  if (mode == SND_MODE_BINARY && (o.k_leaf < 1 || o.k_leaf > 8 || o.k_internal < 1 || o.k_internal > 8))
+    return SND_ERR_UNSUPPORTED;
+  if (mode == SND_MODE_GRADED && (o.graded_cap < 1 || o.graded_cap > 255)) return SND_ERR_UNSUPPORTED;
+  if (!std::isfinite(o.enc_theta) || !finite_pos(o.det_theta) || !std::isfinite(o.sigma_min) ||
+      o.sigma_min < 0.0 || !std::isfinite(o.mf_alpha) || o.mf_alpha < 0.0)
+    return SND_ERR_ARG;
+  if (o.closing_size < 1 || o.closing_size > 31 || (o.closing_size & 1) == 0) return SND_ERR_ARG;
+  if (o.n_min_pixels < 1 || o.max_chunk < 1 || o.max_chunk > (1 << 22) || o.cand_capacity < 1 ||
+      o.cell_capacity < 1 || o.run_capacity < 1)
+    return SND_ERR_ARG;
+  for (int c = 0; c < nchan; ++c)
+    if (!finite_pos(freqs_mhz[c])) return SND_ERR_FREQ_ORDER;
+  {
+    std::vector<double> f(freqs_mhz, freqs_mhz + nchan);
+    std::sort(f.begin(), f.end());
+    for (int c = 1; c < nchan; ++c)
+      if (f[c] == f[c - 1]) return SND_ERR_FREQ_ORDER;
+  }
+  for (int d = 0; d < ndm; ++d)
+    if (!std::isfinite(dm_grid[d]) || dm_grid[d] < 0.0) return SND_ERR_DM;
+
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return SND_ERR_NOMEM;
+  try {
+    p->nchan = nchan;
+    p->ndm = ndm;
+    p->mode = mode;
+    p->B = branching;
+    p->C = o.cluster_size;
+    p->KL = o.k_leaf;
+    p->KI = o.k_internal;
+    p->N = o.graded_cap;
+    p->dt = dt_s;
+    p->enc_theta = o.enc_theta;
+    p->det_theta = o.det_theta;
+    p->sigma_min = o.sigma_min;
+    p->mf_alpha = o.mf_alpha;
+    p->closing = o.closing_size;
+    p->n_min = o.n_min_pixels;
+    p->max_chunk = o.max_chunk;
+    p->cand_cap = o.cand_capacity;
+    p->cell_cap = o.cell_capacity;
+    p->run_cap = o.run_capacity;
+    p->flags = o.flags;
+    p->freqs.assign(freqs_mhz, freqs_mhz + nchan);
+    p->dms.assign(dm_grid, dm_grid + ndm);
+    int rc = snd::build_plan(*p);
+    if (rc) {
+      delete p;
+      return rc;
+    }
+    // the matched filter stages one row segment (Wmax - 1 + chunk samples) in shared memory;
+    // cell indices (row * nb + t) must fit 32 bits
+    if ((static_cast<int64_t>(p->wmax) + p->max_chunk) * 4 + 4096 > 227 * 1024 ||
+        static_cast<int64_t>(ndm) * p->Lp >= (int64_t(1) << 32)) {
+      delete p;
+      return SND_ERR_UNSUPPORTED;
+    }
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return SND_ERR_NOMEM;
+  } catch (...) {
+    delete p;
+    return SND_ERR_ARG;
+  }
+  *out = reinterpret_cast<snd_plan_t>(p);
+  return SND_OK;
+}
+
+extern "C" int snd_plan(const double* freqs_mhz, int32_t nchan, double dt_s, const double* dm_grid,
+                        int32_t ndm, int32_t branching, snd_mode_t mode, snd_plan_t* out) {
+  return snd_plan_ex(freqs_mhz, nchan, dt_s, dm_grid, ndm, branching, mode, nullptr, out);
+}
+
+extern "C" size_t snd_workspace_size(snd_plan_t plan) {
+  if (!plan) return 0;
+  return reinterpret_cast<Plan*>(plan)->ws_bytes;
+}
+
+extern "C" int snd_plan_stats(snd_plan_t plan, snd_plan_stats_t* s) {
+  if (!plan || !s) return SND_ERR_ARG;
+  const Plan& p = *reinterpret_cast<Plan*>(plan);
+  std::memset(s, 0, sizeof(*s));
+  s->nchan = p.nchan;
+  s->ndm = p.ndm;
+  s->mode = p.mode;
+  s->branching = p.B;
+  s->cluster_size = p.C;
+  s->max_delay = p.D;
+  s->nlevels = p.nlev;
+  for (int l = 0; l < p.nlev && l < 24; ++l) {
+    s->nodes_per_level[l] = p.level_nodes[l];
+    s->unique_per_level[l] = p.level_unique[l];
+  }
+  s->adds_per_dm_sample = p.adds_per_dm_sample;
+  s->wmax = p.wmax;
+  s->ring_words = p.R;
+  s->hist_mem_bytes = p.hist_mem_bytes;
+  s->workspace_bytes = p.ws_bytes;
+  s->samples_in = p.T;
+  s->emitted = p.E;
+  s->scored = p.F;
+  s->candidates_pending = p.pending_host;
+  s->tree_tile_dms = p.geom.dms_per_cta;
+  s->tree_tile_words = p.geom.tile_words;
+  s->tree_group_leaves = p.geom.group_leaves;
+  s->tree_smem_bytes = p.geom.smem_bytes;
+  s->max_patterns_per_group = p.geom.max_pat_group;
+  s->kernel_launches = p.launches;
+  return SND_OK;
+}
+
+extern "C" int snd_delay_table(snd_plan_t plan, int32_t* host_out, int64_t n) {
+  if (!plan || !host_out) return SND_ERR_ARG;
+  const Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (n < static_cast<int64_t>(p.delays.size())) return SND_ERR_ARG;
+  std::memcpy(host_out, p.delays.data(), p.delays.size() * sizeof(int32_t));
+  return SND_OK;
+}
+
+extern "C" void snd_destroy(snd_plan_t plan) {
+  if (!plan) return;
+  delete reinterpret_cast<Plan*>(plan);
+}
+
+extern "C" const char* snd_error_string(int status) {
+  switch (status) {
+    case SND_OK: return "ok";
+    case SND_ERR_ARG: return "invalid argument";
+    case SND_ERR_FREQ_ORDER: return "channel frequencies must be finite, positive and distinct";
+    case SND_ERR_DM: return "trial DMs must be finite and non-negative";
+    case SND_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case SND_ERR_CHUNK: return "chunk length outside 1..max_chunk";
+    case SND_ERR_CUDA: return "CUDA runtime error";
+    case SND_ERR_STATE: return "call not valid in the plan's current state";
+    case SND_ERR_TIMEOUT: return "bounded device loop gave up";
+    case SND_ERR_OVERFLOW: return "device list capacity overflowed";
+    case SND_ERR_NOMEM: return "host allocation failed";
+    case SND_ERR_UNSUPPORTED: return "configuration not supported by the GPU kernels";
+    default: return "unknown status";
+  }
+}

@@ -1,0 +1,238 @@
+// Stream runtime of the SND library: workspace binding, per-chunk launch sequence on the
+// caller's stream, and the candidate read-back. Streaming follows Methods, "Pipeline
+// overview", in ring-buffer form: after a chunk the plane samples [E_prev, E_new) with
+// E = max(0, samples consumed - D) are emitted (each has its full delay history), and the
+// matched filter scores start times [F_prev, F_new) with F = max(0, E - (Wmax - 1)).
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "snd_internal.h"
+
+using snd::Plan;
+
+namespace {
+
+int fail(Plan& p, int code) {
+  if (!p.sticky) p.sticky = code;
+  return code;
+}
+
+template <typename T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+template <typename T>
+cudaError_t upload(void* base, size_t off, const std::vector<T>& v, cudaStream_t s) {
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(at<T>(base, off), v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t mark(Plan& p, cudaStream_t s, size_t* slot) {
+  if (p.ev_used == p.ev_pool.size()) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    p.ev_pool.push_back(ev);
+  }
+  *slot = p.ev_used++;
+  return cudaEventRecord(p.ev_pool[*slot], s);
+}
+
+// Run one stage, bracketed by an event pair when profiling.
+template <typename F>
+cudaError_t stage(Plan& p, int id, cudaStream_t s, F&& f) {
+  if (!p.profiling) return f();
+  size_t a = 0, b = 0;
+  cudaError_t e = mark(p, s, &a);
+  if (e == cudaSuccess) e = f();
+  if (e == cudaSuccess) e = mark(p, s, &b);
+  if (e == cudaSuccess) p.ev_marks.push_back({id, {a, b}});
+  return e;
+}
+
+int run_chunk(Plan& p, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s, void* d_plane_out,
+              int32_t* nemit_out) {
+  const int64_t e_prev = p.E;
+  const int64_t e_new = std::max<int64_t>(0, p.T + nsamp - p.D);
+  const int64_t f_prev = p.F;
+  const int64_t f_new = std::max<int64_t>(0, e_new - (p.wmax - 1));
+  const int nb = static_cast<int>(f_new - f_prev);
+  cudaError_t e = stage(p, SND_STAGE_ENCODE, s, [&] { return snd::launch_encode(p, d_chunk, nsamp, s); });
+  if (e == cudaSuccess && e_new > e_prev)
+    e = stage(p, SND_STAGE_TREE, s, [&] { return snd::launch_tree(p, e_prev, e_new, s); });
+  if (e == cudaSuccess && nb > 0)
+    e = cudaMemsetAsync(p.dp.counters, 0, sizeof(uint32_t) * (snd::kCntBlockCands + 1), s);
+  if (e == cudaSuccess && (nb > 0 || (d_plane_out && e_new > e_prev)))
+    e = stage(p, SND_STAGE_MF, s, [&] { return snd::launch_mf(p, e_prev, e_new, f_prev, f_new, d_plane_out, s); });
+  if (e == cudaSuccess && nb > 0)
+    e = stage(p, SND_STAGE_CANDIDATES, s, [&] { return snd::launch_candidates(p, f_prev, nb, s); });
+  if (e != cudaSuccess) return fail(p, SND_ERR_CUDA);
+  p.T += nsamp;
+  p.E = e_new;
+  p.F = f_new;
+  p.last_stream = s;
+  p.pending_host = -1;
+  if (nemit_out) *nemit_out = static_cast<int32_t>(e_new - e_prev);
+  return SND_OK;
+}
+
+}  // namespace
+
+extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, void* stream) {
+  if (!plan) return SND_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (!d_ws || bytes < p.ws_bytes || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return SND_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  snd::DevPtrs& dp = p.dp;
+  const auto& o = p.off;
+  dp.ring = at<uint32_t>(d_ws, o.ring);
+  dp.hist = at<uint32_t>(d_ws, o.hist);
+  dp.levels = at<int32_t>(d_ws, o.levels);
+  dp.plane = at<int32_t>(d_ws, o.plane);
+  dp.mask = at<uint32_t>(d_ws, o.mask);
+  dp.mask2 = at<uint32_t>(d_ws, o.mask2);
+  dp.mask3 = at<uint32_t>(d_ws, o.mask3);
+  dp.cells = at<snd::MfCell>(d_ws, o.cells);
+  dp.counters = at<uint32_t>(d_ws, o.counters);
+  dp.row_runs = at<int32_t>(d_ws, o.row_runs);
+  dp.run_start = at<int32_t>(d_ws, o.run_start);
+  dp.run_end = at<int32_t>(d_ws, o.run_end);
+  dp.run_row = at<int32_t>(d_ws, o.run_row);
+  dp.parent = at<int32_t>(d_ws, o.parent);
+  dp.npix = at<int32_t>(d_ws, o.npix);
+  dp.peak = at<unsigned long long>(d_ws, o.peak);
+  dp.pwidth = at<int32_t>(d_ws, o.pwidth);
+  dp.bcand = at<snd_candidate_t>(d_ws, o.bcand);
+  dp.cand = at<snd_candidate_t>(d_ws, o.cand);
+  dp.staging = at<uint8_t>(d_ws, o.staging);
+  dp.width_mask = at<uint16_t>(d_ws, o.width_mask);
+  dp.dm_f32 = at<float>(d_ws, o.dm_f32);
+  dp.tp_off = at<int32_t>(d_ws, o.tp_off);
+  dp.tp_pid = at<int32_t>(d_ws, o.tp_pid);
+  dp.tp_smin = at<int32_t>(d_ws, o.tp_smin);
+  dp.tp_leaf = at<int32_t>(d_ws, o.tp_leaf);
+  dp.dl_lp = at<uint8_t>(d_ws, o.dl_lp);
+  dp.dl_sh = at<int32_t>(d_ws, o.dl_sh);
+  dp.pat_rel = at<int32_t>(d_ws, o.pat_rel);
+  dp.delays = at<int32_t>(d_ws, o.delays);
+  std::vector<float> dmf(p.dms.begin(), p.dms.end());
+  cudaError_t e = cudaMemsetAsync(d_ws, 0, p.ws_bytes, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.width_mask, p.width_mask, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.dm_f32, dmf, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.tp_off, p.tp_off, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.tp_pid, p.tp_pid, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.tp_smin, p.tp_smin, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.tp_leaf, p.tp_leaf, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.dl_lp, p.dl_lp, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.dl_sh, p.dl_sh, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.pat_rel, p.pat_rel, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.delays, p.delays, s);
+  if (e != cudaSuccess) {
+    p.bound = false;
+    return SND_ERR_CUDA;
+  }
+  p.ws = d_ws;
+  p.ws_have = bytes;
+  p.bound = true;
+  p.last_stream = s;
+  p.T = p.E = p.F = 0;
+  p.sticky = 0;
+  p.pending_host = 0;
+  p.launches = 0;
+  p.ev_used = 0;
+  p.ev_marks.clear();
+  return SND_OK;
+}
+
+extern "C" int snd_profile(snd_plan_t plan, int enable) {
+  if (!plan) return SND_ERR_ARG;
+  reinterpret_cast<Plan*>(plan)->profiling = enable != 0;
+  return SND_OK;
+}
+
+extern "C" int snd_profile_read(snd_plan_t plan, double* ms_out, int64_t* count_out) {
+  if (!plan) return SND_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  double ms[SND_NUM_STAGES] = {0, 0, 0, 0};
+  int64_t cnt[SND_NUM_STAGES] = {0, 0, 0, 0};
+  int rc = SND_OK;
+  for (const auto& m : p.ev_marks) {
+    float t = 0.f;
+    if (cudaEventSynchronize(p.ev_pool[m.second.second]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, p.ev_pool[m.second.first], p.ev_pool[m.second.second]) != cudaSuccess) {
+      rc = SND_ERR_CUDA;
+      break;
+    }
+    ms[m.first] += t;
+    cnt[m.first] += 1;
+  }
+  p.ev_marks.clear();
+  p.ev_used = 0;
+  for (int i = 0; i < SND_NUM_STAGES; ++i) {
+    if (ms_out) ms_out[i] = ms[i];
+    if (count_out) count_out[i] = cnt[i];
+  }
+  return rc;
+}
+
+snd::Plan::~Plan() {
+  for (cudaEvent_t ev : ev_pool) cudaEventDestroy(ev);
+}
+
+extern "C" int snd_execute(snd_plan_t plan, const uint8_t* d_chunk, int32_t nsamp, void* stream,
+                           void* d_plane_out, int32_t* nemit_out) {
+  if (!plan) return SND_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (p.sticky) return p.sticky;
+  if (!p.bound) return SND_ERR_STATE;
+  if (!d_chunk) return SND_ERR_ARG;
+  if (nsamp < 1 || nsamp > p.max_chunk) return SND_ERR_CHUNK;
+  return run_chunk(p, d_chunk, nsamp, static_cast<cudaStream_t>(stream), d_plane_out, nemit_out);
+}
+
+extern "C" int snd_execute_host(snd_plan_t plan, const uint8_t* h_chunk, int32_t nsamp, void* stream,
+                                void* d_plane_out, int32_t* nemit_out) {
+  if (!plan) return SND_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (p.sticky) return p.sticky;
+  if (!p.bound) return SND_ERR_STATE;
+  if (!h_chunk) return SND_ERR_ARG;
+  if (nsamp < 1 || nsamp > p.max_chunk) return SND_ERR_CHUNK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = static_cast<size_t>(nsamp) * p.nchan;
+  if (cudaMemcpyAsync(p.dp.staging, h_chunk, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(p, SND_ERR_CUDA);
+  return run_chunk(p, p.dp.staging, nsamp, s, d_plane_out, nemit_out);
+}
+
+extern "C" int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_t cap, int32_t* n_out) {
+  if (n_out) *n_out = 0;
+  if (!plan || !n_out || cap < 0 || (cap > 0 && !host_out)) return SND_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (!p.bound) return SND_ERR_STATE;
+  if (p.sticky) return p.sticky;
+  if (cudaStreamSynchronize(p.last_stream) != cudaSuccess) return fail(p, SND_ERR_CUDA);
+  uint32_t cnt[snd::kCntSlots];
+  if (cudaMemcpy(cnt, p.dp.counters, sizeof(cnt), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(p, SND_ERR_CUDA);
+  const int n = static_cast<int>(cnt[snd::kCntCands]);
+  const int take = n < cap ? n : cap;
+  if (take > 0 &&
+      cudaMemcpy(host_out, p.dp.cand, sizeof(snd_candidate_t) * take, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(p, SND_ERR_CUDA);
+  uint32_t zero[2] = {0, 0};
+  if (cudaMemcpy(p.dp.counters + snd::kCntCands, zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(p, SND_ERR_CUDA);
+  *n_out = take;
+  p.pending_host = 0;
+  const uint32_t st = cnt[snd::kCntStatus];
+  if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout)) return SND_ERR_TIMEOUT;
+  if (st & (snd::kStatusCellOverflow | snd::kStatusRunOverflow | snd::kStatusCandOverflow |
+            snd::kStatusBlockCandOverflow | snd::kStatusBounds))
+    return SND_ERR_OVERFLOW;
+  if (n > cap) return SND_ERR_OVERFLOW;
+  return SND_OK;
+}

@@ -1,0 +1,170 @@
+// Internal declarations shared by the host runtime and the CUDA kernels of the SND library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/snd.h"
+
+namespace snd {
+
+constexpr int kMaxLevels = 24;     // tree levels (leaves included) supported by the plan
+constexpr int kNumWidthSlots = 11; // widths 1,2,4,...,1024 -> bit j of a row's width mask = 2^j
+constexpr int kTreeThreadsPerDm = 32;
+constexpr int kFlagReferenceTree = SND_FLAG_REFERENCE_TREE;
+
+// Device status word bits (written by kernels, read by snd_candidates).
+enum : uint32_t {
+  kStatusCellOverflow = 1u << 0,
+  kStatusRunOverflow = 1u << 1,
+  kStatusCandOverflow = 1u << 2,
+  kStatusBlockCandOverflow = 1u << 3,
+  kStatusTauTimeout = 1u << 4,
+  kStatusUnionTimeout = 1u << 5,
+  kStatusBounds = 1u << 6,
+};
+
+// One matched-filter cell kept for peak selection.
+struct MfCell {
+  uint32_t cell;   // row * nb + t (t relative to the block start)
+  float snr;       // S/N rounded to float
+  int32_t width;   // boxcar width of the cell's maximum
+};
+
+// Tree kernel geometry (chosen on the host).
+struct TreeGeom {
+  int dms_per_cta;     // DM rows per CTA (one warp each)
+  int kw;              // 32-sample words per lane
+  int tile_words;      // 32 * kw
+  int group_leaves;    // leaves staged per shared-memory round
+  int span;            // words of one staged leaf-pattern series (per plane)
+  int max_pat_group;   // max pattern entries in one group of one DM tile
+  int planes;          // planes of a leaf value (1 binary, 3 graded/float)
+  int smem_bytes;      // dynamic shared memory per CTA
+  int ndm_tiles;
+};
+
+// Device pointers inside the bound workspace.
+struct DevPtrs {
+  uint32_t* ring;          // [nchan][2R] bit ring (mirrored)
+  uint32_t* hist;          // [256][nchan]
+  int32_t* levels;         // [nchan] encoder level u_c (256 = never)
+  int32_t* plane;          // [ndm][Lp] root values by absolute time modulo Lp
+  uint32_t* mask;          // [ndm][mw] matched-filter mask of the current block
+  uint32_t* mask2;         // [ndm][mw] closing scratch
+  uint32_t* mask3;         // [ndm][mw] closed mask
+  MfCell* cells;           // [cell_cap]
+  uint32_t* counters;      // [16] misc counters (cells, runs, block cands, cands, status ...)
+  int32_t* row_runs;       // [ndm + 1] run offsets per row (exclusive scan)
+  int32_t* run_start;      // [run_cap]
+  int32_t* run_end;        // [run_cap]
+  int32_t* run_row;        // [run_cap]
+  int32_t* parent;         // [run_cap]
+  int32_t* npix;           // [run_cap]
+  unsigned long long* peak;// [run_cap]
+  int32_t* pwidth;         // [run_cap] width of the island's peak cell
+  snd_candidate_t* bcand;  // [cand_cap] candidates of the current block (unsorted)
+  snd_candidate_t* cand;   // [cand_cap] accumulated sorted candidates
+  uint8_t* staging;        // [max_chunk * nchan] host-chunk staging
+  // plan tables
+  uint16_t* width_mask;    // [ndm]
+  float* dm_f32;           // [ndm]
+  int32_t* tp_off;         // [ndm_tiles * nleaves + 1]
+  int32_t* tp_pid;         // [ntp] global pattern id of each (tile, leaf) entry
+  int32_t* tp_smin;        // [ntp]
+  int32_t* tp_leaf;        // [ntp] leaf of each entry
+  uint8_t* dl_lp;          // [ndm * nleaves] tile-local pattern index
+  int32_t* dl_sh;          // [ndm * nleaves] leaf shift = delta_ref(leaf)(d)
+  int32_t* pat_rel;        // [npat * C] relative delays of each pattern's channels
+  int32_t* delays;         // [ndm * nchan] full delay table (reference kernel, tests)
+};
+
+// Counter slots.
+enum {
+  kCntCells = 0,
+  kCntRuns = 1,
+  kCntBlockCands = 2,
+  kCntCands = 3,
+  kCntStatus = 4,
+  kCntSlots = 16
+};
+
+struct Plan {
+  // configuration
+  int nchan = 0, ndm = 0, mode = 0, B = 2, C = 4, KL = 2, KI = 2, N = 255;
+  double dt = 0, enc_theta = 1.5, det_theta = 7.0, sigma_min = 0.2, mf_alpha = 0.1;
+  int closing = 9, n_min = 10, max_chunk = 32768, cand_cap = 65536, cell_cap = 1 << 20,
+      run_cap = 1 << 21, flags = 0;
+  std::vector<double> freqs, dms;
+
+  // derived
+  int ref_chan = 0, min_chan = 0;
+  int D = 0;
+  std::vector<int32_t> delays;          // [ndm][nchan]
+  std::vector<uint16_t> width_mask;     // [ndm]
+  int wmax = 1;
+  int nlev = 1;
+  std::vector<int> level_nodes;         // nodes per level (leaves first)
+  std::vector<int64_t> level_unique;    // distinct patterns per level
+  double adds_per_dm_sample = 0;
+  int64_t hist_mem_bytes = 0;
+  int nleaves = 0;
+
+  // leaf patterns and tiles
+  int npat = 0;
+  std::vector<int32_t> pat_rel;         // [npat][C]
+  std::vector<int32_t> leaf_pid;        // [ndm][nleaves]
+  std::vector<int32_t> tp_off, tp_pid, tp_smin, tp_leaf;
+  std::vector<uint8_t> dl_lp;
+  std::vector<int32_t> dl_sh;
+  TreeGeom geom{};
+
+  // sizes
+  int R = 0;           // ring words per copy
+  int Lp = 0;          // plane ring columns (multiple of 32)
+  int mw = 0;          // mask words per row
+  size_t ws_bytes = 0;
+  struct Off {
+    size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
+        run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, width_mask, dm_f32, tp_off,
+        tp_pid, tp_smin, tp_leaf, dl_lp, dl_sh, pat_rel, delays;
+  } off{};
+
+  // binding and stream state
+  void* ws = nullptr;
+  size_t ws_have = 0;
+  DevPtrs dp{};
+  bool bound = false;
+  cudaStream_t last_stream = nullptr;
+  int64_t T = 0;   // samples consumed
+  int64_t E = 0;   // emitted plane samples
+  int64_t F = 0;   // scored start times
+  int sticky = 0;
+  int pending_host = -1;
+  mutable int64_t launches = 0;  // kernels enqueued since binding
+
+  // per-stage timing (snd_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;       // created on demand, reused
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;  // (stage, (start, stop))
+  ~Plan();
+};
+
+// plan.cpp
+int build_plan(Plan& p);
+
+// kernels (launchers), each returns cudaGetLastError() of its launch and adds the number
+// of kernels it enqueued to p.launches
+cudaError_t launch_encode(const Plan& p, const uint8_t* d_chunk, int nsamp, cudaStream_t s);
+cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream_t s);
+cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64_t f_new,
+                      void* d_plane_out, cudaStream_t s);
+cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_t s);
+int tree_kw(int mode, int nlev, int kmax);  // 32-sample words per lane of k_tree
+
+}  // namespace snd
