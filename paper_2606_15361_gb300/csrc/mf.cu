@@ -47,22 +47,35 @@ __device__ __forceinline__ double snr_of(long long s, double mu_w, double den) {
 }
 
 __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
-  extern __shared__ __align__(16) int32_t y[];  // len + 1 entries
+  // smem: the row segment, 4 words of front pad (aligned staging) and tail pad
+  extern __shared__ __align__(16) int32_t smem[];
+  int32_t* y = smem + 4;
   __shared__ long long red1[kMfThreads / 32], red2[kMfThreads / 32];
   __shared__ int tau[kNumWidthSlots];
   __shared__ double smu, ssig;
   __shared__ int s_ok;
-  __shared__ uint32_t s_carry;
   __shared__ uint32_t wsum[kMfThreads / 32];
   const int d = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int NWARP = kMfThreads / 32;
   const int len = static_cast<int>(a.e_new - a.f_prev);
-  const int32_t* src = a.plane + static_cast<size_t>(d) * a.Lp;
-  const int c0 = static_cast<int>(a.f_prev % a.Lp);
-  for (int i = tid; i < len; i += kMfThreads) {
-    int c = c0 + i;
-    if (c >= a.Lp) c -= a.Lp;
-    y[i] = src[c];
+  // 1. stage ring columns [f_prev, e_new) of row d with 16-byte loads (Lp % 4 == 0, so an
+  //    aligned group of four columns never straddles the ring's wrap point)
+  {
+    const int32_t* src = a.plane + static_cast<size_t>(d) * a.Lp;
+    const int c0 = static_cast<int>(a.f_prev % a.Lp);
+    const int r0 = c0 & 3;
+    const int ngroups = (len + r0 + 3) >> 2;
+    for (int k = tid; k < ngroups; k += kMfThreads) {
+      int c = c0 - r0 + 4 * k;
+      if (c >= a.Lp) c -= a.Lp;
+      const int4 v = __ldg(reinterpret_cast<const int4*>(src + c));
+      int32_t* dst = y + 4 * k - r0;
+      dst[0] = v.x;
+      dst[1] = v.y;
+      dst[2] = v.z;
+      dst[3] = v.w;
+    }
   }
   __syncthreads();
   // caller's plane: the newly emitted samples [E_prev, E_new)
@@ -78,7 +91,7 @@ __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
   }
   const int nb = a.nb;
   if (nb <= 0) return;
-  // exact integer sums over the block's start times
+  // 2. exact integer sums over the block's start times
   long long s1 = 0, s2 = 0;
   for (int i = tid; i < nb; i += kMfThreads) {
     const long long v = y[i];
@@ -94,11 +107,30 @@ __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
     red1[wid] = s1;
     red2[wid] = s2;
   }
+  __syncthreads();  // every warp has read the raw values before the in-place scan
+  // 3. warp-segmented exclusive scan in place (uint32 wrap-around keeps window sums exact)
+  const int seg = ((len + NWARP * 32 - 1) / (NWARP * 32)) * 32;
+  const int lo = min(len, wid * seg), hi = min(len, lo + seg);
+  uint32_t carry = 0;
+  for (int base = lo; base < hi; base += 32) {
+    const int i = base + lane;
+    const uint32_t v = (i < hi) ? static_cast<uint32_t>(y[i]) : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (i < hi) y[i] = static_cast<int32_t>(carry + incl - v);
+    carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+  }
+  if (lane == 0) wsum[wid] = carry;
   __syncthreads();
   const uint32_t wm = a.width_mask[d];
-  if (tid == 0) {
+  if (wid == 0) {
+    // row statistics (FP64, fixed order) and, lane j, the integer threshold of width 2^j
     long long t1 = 0, t2 = 0;
-    for (int w = 0; w < kMfThreads / 32; ++w) {
+    for (int w = 0; w < NWARP; ++w) {
       t1 += red1[w];
       t2 += red2[w];
     }
@@ -107,55 +139,39 @@ __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
     const double var = __dsub_rn(__ddiv_rn(static_cast<double>(t2), n), __dmul_rn(mu, mu));
     double sig = var > 0.0 ? __dsqrt_rn(var) : 0.0;
     if (a.binary && sig < a.sigma_min) sig = a.sigma_min;
-    smu = mu;
-    ssig = sig;
-    s_ok = sig > 0.0;
-    if (s_ok) {
-      for (int j = 0; j < kNumWidthSlots; ++j) {
-        if (!((wm >> j) & 1)) continue;
-        const double w = static_cast<double>(1 << j);
-        const double mu_w = __dmul_rn(mu, w);
-        const double den = __dmul_rn(sig, __dsqrt_rn(w));
-        double est = ceil(__dadd_rn(mu_w, __dmul_rn(a.theta, den)));
-        if (est < 0.0) est = 0.0;
-        if (est > 2147483000.0) est = 2147483000.0;
-        long long s = static_cast<long long>(est);
-        int down = 0, up = 0;
-        while (s > 0 && down < 64 && snr_of(s - 1, mu_w, den) >= a.theta) {
-          --s;
-          ++down;
-        }
-        while (up < 64 && snr_of(s, mu_w, den) < a.theta) {
-          ++s;
-          ++up;
-        }
-        if (down == 64 || up == 64) atomicOr(&a.counters[kCntStatus], kStatusTauTimeout);
-        tau[j] = static_cast<int>(s);
+    if (lane == 0) {
+      smu = mu;
+      ssig = sig;
+      s_ok = sig > 0.0;
+    }
+    if (sig > 0.0 && lane < kNumWidthSlots && ((wm >> lane) & 1)) {
+      const double w = static_cast<double>(1 << lane);
+      const double mu_w = __dmul_rn(mu, w);
+      const double den = __dmul_rn(sig, __dsqrt_rn(w));
+      double est = ceil(__dadd_rn(mu_w, __dmul_rn(a.theta, den)));
+      if (est < 0.0) est = 0.0;
+      if (est > 2147483000.0) est = 2147483000.0;
+      long long sv = static_cast<long long>(est);
+      int down = 0, up = 0;
+      while (sv > 0 && down < 64 && snr_of(sv - 1, mu_w, den) >= a.theta) {
+        --sv;
+        ++down;
       }
+      while (up < 64 && snr_of(sv, mu_w, den) < a.theta) {
+        ++sv;
+        ++up;
+      }
+      if (down == 64 || up == 64) atomicOr(&a.counters[kCntStatus], kStatusTauTimeout);
+      tau[lane] = static_cast<int>(sv);
     }
   }
-  // in-place exclusive prefix sums (uint32 wrap-around: window differences stay exact)
-  uint32_t carry = 0;
-  for (int base = 0; base < len; base += kMfThreads) {
-    const int i = base + tid;
-    const uint32_t v = (i < len) ? static_cast<uint32_t>(y[i]) : 0u;
-    uint32_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    uint32_t woff = 0;
-    for (int w = 0; w < wid; ++w) woff += wsum[w];
-    if (i < len) y[i] = static_cast<int32_t>(carry + woff + incl - v);
-    if (tid == kMfThreads - 1) s_carry = carry + woff + incl;
-    __syncthreads();
-    carry = s_carry;
-    __syncthreads();
+  {
+    uint32_t off = 0;
+    for (int w = 0; w < wid; ++w) off += wsum[w];
+    if (off)
+      for (int i = lo + lane; i < hi; i += 32) y[i] = static_cast<int32_t>(static_cast<uint32_t>(y[i]) + off);
+    if (wid == NWARP - 1 && lane == 0) y[len] = static_cast<int32_t>(off + carry);
   }
-  if (tid == 0) y[len] = static_cast<int32_t>(carry);
   __syncthreads();
   const int nbw = (nb + 31) >> 5;
   uint32_t* mrow = a.mask + static_cast<size_t>(d) * a.mw;
@@ -163,19 +179,19 @@ __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
     for (int q = tid; q < nbw; q += kMfThreads) mrow[q] = 0;
     return;
   }
+  int tw[kNumWidthSlots];
+#pragma unroll
+  for (int j = 0; j < kNumWidthSlots; ++j) tw[j] = ((wm >> j) & 1) ? tau[j] : 0x7FFFFFFF;
   const double mu = smu, sig = ssig;
   const uint32_t* P = reinterpret_cast<const uint32_t*>(y);
-  for (int q = wid; q < nbw; q += kMfThreads / 32) {
+  for (int q = wid; q < nbw; q += NWARP) {
     const int t = q * 32 + lane;
     bool hit = false;
     if (t < nb) {
       const uint32_t p0 = P[t];
 #pragma unroll
       for (int j = 0; j < kNumWidthSlots; ++j) {
-        if ((wm >> j) & 1) {
-          const int S = static_cast<int>(P[t + (1 << j)] - p0);
-          hit |= S >= tau[j];
-        }
+        if ((wm >> j) & 1) hit |= static_cast<int>(P[t + (1 << j)] - p0) >= tw[j];
       }
     }
     const uint32_t word = __ballot_sync(0xFFFFFFFFu, hit);
@@ -236,7 +252,7 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
   a.plane_out = nemit > 0 ? d_plane_out : nullptr;
   a.nemit = nemit;
   const int len = static_cast<int>(e_new - f_prev);
-  const int smem = (len + 1) * 4;
+  const int smem = (len + 12) * 4;  // 4 words of front pad, prefix total and staging overrun
   cudaError_t e = cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   k_mf<<<p.ndm, kMfThreads, smem, s>>>(a);

@@ -250,7 +250,7 @@ int build_plan(Plan& p) {
   const TreeGeom& g = p.geom;
   const int maxw_chunk = (p.max_chunk + 31) / 32;
   // words reachable from one emitted block: delay + chunk + tile padding + funnel partner
-  p.R = (p.D >> 5) + maxw_chunk + g.span + 8;
+  p.R = (p.D >> 5) + maxw_chunk + g.cspan + 8;
   p.Lp = static_cast<int>(align_up(static_cast<size_t>(p.wmax) - 1 + p.max_chunk + 96, 32));
   p.mw = (p.Lp + 31) / 32;
   size_t o = 0;
@@ -288,6 +288,7 @@ int build_plan(Plan& p) {
   p.off.dl_lp = take(p.dl_lp.size());
   p.off.dl_sh = take(sizeof(int32_t) * p.dl_sh.size());
   p.off.pat_rel = take(sizeof(int32_t) * std::max<size_t>(1, p.pat_rel.size()));
+  p.off.tile_wb = take(sizeof(int32_t) * p.tile_wb.size());
   p.off.delays = take(sizeof(int32_t) * p.delays.size());
   p.ws_bytes = o;
   return SND_OK;
@@ -297,14 +298,17 @@ int build_plan(Plan& p) {
 
 namespace {
 
-// Tree kernel geometry: DM rows per CTA (one warp each), 32-sample words per lane, and
-// how many leaves are staged per shared-memory round so that the staged leaf-pattern
-// series fit the shared-memory budget.
+// Tree kernel geometry: DMs per CTA, output words per CTA, the per-(tile, leaf) lists of
+// distinct leaf patterns, the staged window sizes, and how many leaves (a multiple of B) are
+// staged per shared-memory round so that a CTA fits the shared-memory budget.
 int choose_tree_geometry(Plan& p) {
   snd::TreeGeom& g = p.geom;
-  const int ndm = p.ndm, NL = p.nleaves;
-  g.dms_per_cta = 8;
-  g.kw = snd::tree_kw(p.mode, p.nlev, p.KL > p.KI ? p.KL : p.KI);
+  const int ndm = p.ndm, NL = p.nleaves, nchan = p.nchan;
+  const snd::TreeShape sh = snd::tree_shape(p.mode, p.nlev, p.KL > p.KI ? p.KL : p.KI);
+  g.warps = sh.warps;
+  g.dpw = sh.dpw;
+  g.kw = sh.kw;
+  g.dms_per_cta = sh.warps * sh.dpw;
   g.tile_words = 32 * g.kw;
   g.planes = (p.mode == SND_MODE_BINARY) ? 1 : 3;
   g.ndm_tiles = (ndm + g.dms_per_cta - 1) / g.dms_per_cta;
@@ -315,52 +319,63 @@ int choose_tree_geometry(Plan& p) {
   p.tp_leaf.clear();
   p.dl_lp.assign(static_cast<size_t>(ndm) * NL, 0);
   p.dl_sh.assign(static_cast<size_t>(ndm) * NL, 0);
-  int64_t dspread = 0;
+  p.tile_wb.assign(static_cast<size_t>(g.ndm_tiles) * nchan, 0);
+  int64_t sspread = 0, cspread = 0;
   std::vector<int> npat_tl(static_cast<size_t>(g.ndm_tiles) * NL, 0);
   for (int t = 0; t < g.ndm_tiles; ++t) {
     const int d0 = t * g.dms_per_cta, d1 = std::min(ndm, d0 + g.dms_per_cta);
+    for (int c = 0; c < nchan; ++c) {
+      int32_t lo = p.delays[static_cast<size_t>(d0) * nchan + c], hi = lo;
+      for (int d = d0 + 1; d < d1; ++d) {
+        lo = std::min(lo, p.delays[static_cast<size_t>(d) * nchan + c]);
+        hi = std::max(hi, p.delays[static_cast<size_t>(d) * nchan + c]);
+      }
+      p.tile_wb[static_cast<size_t>(t) * nchan + c] = std::max(lo - 31, 0) >> 5;
+      cspread = std::max<int64_t>(cspread, static_cast<int64_t>(hi) - lo);
+    }
     for (int k = 0; k < NL; ++k) {
       // reference channel of the leaf: highest frequency among its channels
       int r = k * p.C;
-      for (int c = k * p.C + 1; c < std::min(p.nchan, (k + 1) * p.C); ++c)
+      for (int c = k * p.C + 1; c < std::min(nchan, (k + 1) * p.C); ++c)
         if (p.freqs[c] > p.freqs[r]) r = c;
       const size_t at = static_cast<size_t>(t) * NL + k;
       p.tp_off[at] = static_cast<int32_t>(p.tp_pid.size());
       std::vector<int32_t> pids, smin, smax;
       for (int d = d0; d < d1; ++d) {
         const int32_t pid = p.leaf_pid[static_cast<size_t>(d) * NL + k];
-        const int32_t sh = p.delays[static_cast<size_t>(d) * p.nchan + r];
+        const int32_t s = p.delays[static_cast<size_t>(d) * nchan + r];
         int idx = -1;
         for (size_t i = 0; i < pids.size(); ++i)
           if (pids[i] == pid) idx = static_cast<int>(i);
         if (idx < 0) {
           idx = static_cast<int>(pids.size());
           pids.push_back(pid);
-          smin.push_back(sh);
-          smax.push_back(sh);
+          smin.push_back(s);
+          smax.push_back(s);
         } else {
-          smin[idx] = std::min(smin[idx], sh);
-          smax[idx] = std::max(smax[idx], sh);
+          smin[idx] = std::min(smin[idx], s);
+          smax[idx] = std::max(smax[idx], s);
         }
         p.dl_lp[static_cast<size_t>(d) * NL + k] = static_cast<uint8_t>(idx);
-        p.dl_sh[static_cast<size_t>(d) * NL + k] = sh;
+        p.dl_sh[static_cast<size_t>(d) * NL + k] = s;
       }
       for (size_t i = 0; i < pids.size(); ++i) {
         p.tp_pid.push_back(pids[i]);
         p.tp_smin.push_back(smin[i]);
         p.tp_leaf.push_back(k);
-        dspread = std::max<int64_t>(dspread, static_cast<int64_t>(smax[i]) - smin[i]);
+        sspread = std::max<int64_t>(sspread, static_cast<int64_t>(smax[i]) - smin[i]);
       }
       npat_tl[at] = static_cast<int>(pids.size());
     }
   }
   p.tp_off.back() = static_cast<int32_t>(p.tp_pid.size());
-  g.span = g.tile_words + static_cast<int>(dspread >> 5) + 2;
+  // series word j covers leaf samples [32*(smin>>5) + 32 j, +32): a DM with shift s reads
+  // words (s>>5)-(smin>>5) + w and +1 for w < tile_words
+  g.span = g.tile_words + static_cast<int>(sspread >> 5) + 2;
+  // channel c of entry (smin, rel) is read at window words ((32(smin>>5)+rel)>>5) - wb_c + j (+1)
+  g.cspan = g.span + static_cast<int>((cspread + 31) >> 5) + 2;
 
-  // largest group that fits the budget
-  const int budget = 64 * 1024;
-  int best = 1, best_pat = 0;
-  for (int G = 1; G <= NL; ++G) {
+  auto smem_for = [&](int G, int* mp_out) {
     int mp = 0;
     for (int t = 0; t < g.ndm_tiles; ++t)
       for (int k0 = 0; k0 < NL; k0 += G) {
@@ -368,21 +383,28 @@ int choose_tree_geometry(Plan& p) {
         for (int k = k0; k < std::min(NL, k0 + G); ++k) s += npat_tl[static_cast<size_t>(t) * NL + k];
         mp = std::max(mp, s);
       }
-    // series + meta + per-entry ring offsets/shifts (C each) + entry leaf
-    const int64_t bytes = static_cast<int64_t>(mp) * g.planes * g.span * 4 +
-                          static_cast<int64_t>(g.dms_per_cta) * G * 4 +
-                          static_cast<int64_t>(mp) * (2 * p.C + 1) * 4;
-    if (G == 1 || bytes <= budget) {
-      best = G;
-      best_pat = mp;
-      g.smem_bytes = static_cast<int>(bytes);
-    }
-    if (bytes > budget) break;
-    if (G >= 64) break;
+    *mp_out = mp;
+    // series as word pairs (2 words per series word), windows, meta, entry info
+    const int64_t words = static_cast<int64_t>(G) * p.C * g.cspan + 2 * static_cast<int64_t>(mp) * g.planes * g.span +
+                          static_cast<int64_t>(g.dms_per_cta) * G + static_cast<int64_t>(mp) * (p.C + 1);
+    return words * 4;
+  };
+  const int64_t budget = 100 * 1024;
+  const int unit = (p.nlev == 1) ? 1 : std::min(p.B, NL);
+  int G = unit, mp = 0;
+  int64_t bytes = smem_for(G, &mp);
+  for (int m = 2; unit * m <= NL + unit - 1 && unit * (m - 1) < NL; ++m) {
+    int mp2 = 0;
+    const int64_t b2 = smem_for(unit * m, &mp2);
+    if (b2 > budget) break;
+    G = unit * m;
+    mp = mp2;
+    bytes = b2;
   }
-  g.group_leaves = best;
-  g.max_pat_group = best_pat;
-  if (g.smem_bytes > 200 * 1024) return SND_ERR_UNSUPPORTED;
+  g.group_leaves = G;
+  g.max_pat_group = mp;
+  g.smem_bytes = static_cast<int>(bytes);
+  if (bytes > 220 * 1024) return SND_ERR_UNSUPPORTED;
   return SND_OK;
 }
 

@@ -117,6 +117,7 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.dl_lp = at<uint8_t>(d_ws, o.dl_lp);
   dp.dl_sh = at<int32_t>(d_ws, o.dl_sh);
   dp.pat_rel = at<int32_t>(d_ws, o.pat_rel);
+  dp.tile_wb = at<int32_t>(d_ws, o.tile_wb);
   dp.delays = at<int32_t>(d_ws, o.delays);
   std::vector<float> dmf(p.dms.begin(), p.dms.end());
   cudaError_t e = cudaMemsetAsync(d_ws, 0, p.ws_bytes, s);
@@ -129,6 +130,7 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   if (e == cudaSuccess) e = upload(d_ws, o.dl_lp, p.dl_lp, s);
   if (e == cudaSuccess) e = upload(d_ws, o.dl_sh, p.dl_sh, s);
   if (e == cudaSuccess) e = upload(d_ws, o.pat_rel, p.pat_rel, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.tile_wb, p.tile_wb, s);
   if (e == cudaSuccess) e = upload(d_ws, o.delays, p.delays, s);
   if (e != cudaSuccess) {
     p.bound = false;

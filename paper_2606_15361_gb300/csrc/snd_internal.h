@@ -35,13 +35,21 @@ struct MfCell {
   int32_t width;   // boxcar width of the cell's maximum
 };
 
+// Tree kernel shape: warps per CTA, trial DMs per warp, 32-sample words per lane.
+struct TreeShape {
+  int warps, dpw, kw;
+};
+
 // Tree kernel geometry (chosen on the host).
 struct TreeGeom {
-  int dms_per_cta;     // DM rows per CTA (one warp each)
+  int warps;           // warps per CTA
+  int dpw;             // trial DMs per warp
   int kw;              // 32-sample words per lane
-  int tile_words;      // 32 * kw
-  int group_leaves;    // leaves staged per shared-memory round
+  int dms_per_cta;     // warps * dpw
+  int tile_words;      // largest output words per CTA (32 * kw)
+  int group_leaves;    // leaves staged per shared-memory round (a multiple of B)
   int span;            // words of one staged leaf-pattern series (per plane)
+  int cspan;           // words of one staged channel window
   int max_pat_group;   // max pattern entries in one group of one DM tile
   int planes;          // planes of a leaf value (1 binary, 3 graded/float)
   int smem_bytes;      // dynamic shared memory per CTA
@@ -80,6 +88,7 @@ struct DevPtrs {
   uint8_t* dl_lp;          // [ndm * nleaves] tile-local pattern index
   int32_t* dl_sh;          // [ndm * nleaves] leaf shift = delta_ref(leaf)(d)
   int32_t* pat_rel;        // [npat * C] relative delays of each pattern's channels
+  int32_t* tile_wb;        // [ndm_tiles * nchan] first staged ring word per channel (tile-relative)
   int32_t* delays;         // [ndm * nchan] full delay table (reference kernel, tests)
 };
 
@@ -121,6 +130,7 @@ struct Plan {
   std::vector<int32_t> tp_off, tp_pid, tp_smin, tp_leaf;
   std::vector<uint8_t> dl_lp;
   std::vector<int32_t> dl_sh;
+  std::vector<int32_t> tile_wb;
   TreeGeom geom{};
 
   // sizes
@@ -131,7 +141,7 @@ struct Plan {
   struct Off {
     size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
         run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, width_mask, dm_f32, tp_off,
-        tp_pid, tp_smin, tp_leaf, dl_lp, dl_sh, pat_rel, delays;
+        tp_pid, tp_smin, tp_leaf, dl_lp, dl_sh, pat_rel, tile_wb, delays;
   } off{};
 
   // binding and stream state
@@ -165,6 +175,6 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
 cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64_t f_new,
                       void* d_plane_out, cudaStream_t s);
 cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_t s);
-int tree_kw(int mode, int nlev, int kmax);  // 32-sample words per lane of k_tree
+TreeShape tree_shape(int mode, int nlev, int kmax);  // k_tree launch shape
 
 }  // namespace snd

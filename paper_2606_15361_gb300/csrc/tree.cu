@@ -41,7 +41,11 @@ struct TreeArgs {
   const uint8_t* dl_lp;
   const int32_t* dl_sh;
   const int32_t* pat_rel;
-  int G, span, maxpat;
+  const int32_t* tile_wb;  // [ndm_tiles][nchan] first staged ring word of each channel, relative to the tile
+  int G, span, cspan, maxpat;
+  int tile_words;   // output words per CTA (<= 32*KW)
+  int plain1;       // graded: the cap cannot bind inside a level-1 node
+  int span_extra;   // leaf-series words beyond tile_words
   long long word0;  // absolute index of the first output word
   int nwords;       // output words of this call
   int32_t* plane;
@@ -128,44 +132,66 @@ __device__ __forceinline__ void store_bits(int32_t* dst, uint32_t v) {
 
 constexpr int kBinary = SND_MODE_BINARY, kGraded = SND_MODE_GRADED, kFloat = SND_MODE_FLOAT;
 
-// Per-thread tree state for MODE.
-template <int MODE, int MAXL, int KW, int TH>
-struct TreeState;
+// Bit-sliced count of up to 7 one-bit inputs (3 planes). NC is the compile-time channel
+// bound: NC = 4 for clusters of exactly four channels, 8 for the generic (predicated) path.
+template <int NC>
+__device__ __forceinline__ void count7(const uint32_t* x, int cs, uint32_t* c) {
+  c[0] = c[1] = c[2] = 0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    if (NC != 8 || i < cs) {
+      const uint32_t k0 = c[0] & x[i];
+      c[0] ^= x[i];
+      const uint32_t k1 = c[1] & k0;
+      c[1] ^= k0;
+      c[2] |= k1;
+    }
+  }
+}
 
-template <int MAXL, int KW, int TH>
-struct TreeState<kBinary, MAXL, KW, TH> {
+// Per-warp tree state: DPW trial DMs x KW words per lane. Level 1 is accumulated per node
+// (all of its leaves in one go); levels >= 2 keep one accumulator per open node.
+template <int MODE, int MAXL, int KW, int TH, int DPW>
+struct Tree;
+
+// Mode A: thermometer codes, acc[..][i] = 1[count >= i+1].
+template <int MAXL, int KW, int TH, int DPW>
+struct Tree<kBinary, MAXL, KW, TH, DPW> {
   static constexpr int kLeafPlanes = 1;
-  // acc[l][j][i] = 1[count of level-l node (word j) >= i + 1]  (thermometer code)
-  uint32_t acc[MAXL][KW][TH];
-  uint32_t root[KW];
-  // one-hot word masks selecting the K_I plane (a runtime-indexed select would push the
-  // accumulators to local memory)
-  uint32_t ksel[TH];
+  uint32_t acc[MAXL][DPW][KW][TH];
+  uint32_t root[DPW][KW];
+  uint32_t ksel[TH];  // one-hot masks selecting the K_I plane (keeps acc in registers)
   int cnt[MAXL], node[MAXL], fan[MAXL];
+
   __device__ __forceinline__ void init(const TreeArgs& a) {
 #pragma unroll
     for (int i = 0; i < TH; ++i) ksel[i] = (i == a.KI - 1) ? 0xFFFFFFFFu : 0u;
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
 #pragma unroll
-      for (int j = 0; j < KW; ++j)
+      for (int d = 0; d < DPW; ++d)
 #pragma unroll
-        for (int i = 0; i < TH; ++i) acc[l][j][i] = 0;
+        for (int j = 0; j < KW; ++j)
+#pragma unroll
+          for (int i = 0; i < TH; ++i) acc[l][d][j][i] = 0;
       cnt[l] = 0;
       node[l] = 0;
-      fan[l] = (l >= 1 && l < a.nlev) ? min(a.B, a.level_nodes[l - 1]) : 1;
+      fan[l] = (l >= 2 && l < a.nlev) ? min(a.B, a.level_nodes[l - 1]) : 1;
     }
 #pragma unroll
-    for (int j = 0; j < KW; ++j) root[j] = 0;
+    for (int d = 0; d < DPW; ++d)
+#pragma unroll
+      for (int j = 0; j < KW; ++j) root[d][j] = 0;
   }
-  // leaf value from its channel bits (binary: quorum K_L over the cluster)
+  // leaf: quorum K_L over the cluster's channel bits
+  template <int NC>
   __device__ __forceinline__ static void leaf(const TreeArgs& a, const uint32_t* x, int cs, uint32_t* out) {
-    uint32_t t[TH];
+    uint32_t t[TH];  // TH >= K_L
 #pragma unroll
     for (int i = 0; i < TH; ++i) t[i] = 0;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if (c < cs) {
+    for (int c = 0; c < NC; ++c) {
+      if (NC != 8 || c < cs) {
 #pragma unroll
         for (int i = TH - 1; i > 0; --i) t[i] |= t[i - 1] & x[c];
         t[0] |= x[c];
@@ -176,228 +202,307 @@ struct TreeState<kBinary, MAXL, KW, TH> {
     for (int i = 0; i < TH; ++i) r |= t[i] & ((i == a.KL - 1) ? 0xFFFFFFFFu : 0u);
     out[0] = r;
   }
-  __device__ __forceinline__ void push(const TreeArgs& a, uint32_t (*v)[1]) {
-    if (a.nlev == 1) {
+  // level-1 node accumulator for one DM
+  struct Node {
+    uint32_t t[KW][TH];
+  };
+  __device__ __forceinline__ static void node_clear(Node& n) {
 #pragma unroll
-      for (int j = 0; j < KW; ++j) root[j] = v[j][0];
+    for (int j = 0; j < KW; ++j)
+#pragma unroll
+      for (int i = 0; i < TH; ++i) n.t[j][i] = 0;
+  }
+  __device__ __forceinline__ static void node_add(Node& n, int j, const uint32_t* v) {
+#pragma unroll
+    for (int i = TH - 1; i > 0; --i) n.t[j][i] |= n.t[j][i - 1] & v[0];
+    n.t[j][0] |= v[0];
+  }
+  __device__ __forceinline__ uint32_t select_k(const uint32_t* t) const {
+    uint32_t r = 0;
+#pragma unroll
+    for (int i = 0; i < TH; ++i) r |= t[i] & ksel[i];
+    return r;
+  }
+  // all DMs of the warp finished level-1 node n: push their values up
+  __device__ __forceinline__ void push_nodes(const TreeArgs& a, Node (&nd)[DPW]) {
+    uint32_t cur[DPW][KW];
+#pragma unroll
+    for (int d = 0; d < DPW; ++d)
+#pragma unroll
+      for (int j = 0; j < KW; ++j) cur[d][j] = select_k(nd[d].t[j]);
+    if (a.nlev == 2) {
+#pragma unroll
+      for (int d = 0; d < DPW; ++d)
+#pragma unroll
+        for (int j = 0; j < KW; ++j) root[d][j] = cur[d][j];
       return;
     }
-    uint32_t cur[KW];
 #pragma unroll
-    for (int j = 0; j < KW; ++j) cur[j] = v[j][0];
-#pragma unroll
-    for (int l = 1; l < MAXL; ++l) {
+    for (int l = 2; l < MAXL; ++l) {
       if (l >= a.nlev) break;
 #pragma unroll
-      for (int j = 0; j < KW; ++j) {
+      for (int d = 0; d < DPW; ++d)
 #pragma unroll
-        for (int i = TH - 1; i > 0; --i) acc[l][j][i] |= acc[l][j][i - 1] & cur[j];
-        acc[l][j][0] |= cur[j];
-      }
+        for (int j = 0; j < KW; ++j) {
+#pragma unroll
+          for (int i = TH - 1; i > 0; --i) acc[l][d][j][i] |= acc[l][d][j][i - 1] & cur[d][j];
+          acc[l][d][j][0] |= cur[d][j];
+        }
       if (++cnt[l] < fan[l]) break;
 #pragma unroll
-      for (int j = 0; j < KW; ++j) {
-        uint32_t r = 0;
+      for (int d = 0; d < DPW; ++d)
 #pragma unroll
-        for (int i = 0; i < TH; ++i) {
-          r |= acc[l][j][i] & ksel[i];
-          acc[l][j][i] = 0;
+        for (int j = 0; j < KW; ++j) {
+          cur[d][j] = select_k(acc[l][d][j]);
+#pragma unroll
+          for (int i = 0; i < TH; ++i) acc[l][d][j][i] = 0;
         }
-        cur[j] = r;
-      }
       cnt[l] = 0;
       ++node[l];
       fan[l] = min(a.B, a.level_nodes[l - 1] - a.B * node[l]);
       if (l == a.nlev - 1) {
 #pragma unroll
-        for (int j = 0; j < KW; ++j) root[j] = cur[j];
+        for (int d = 0; d < DPW; ++d)
+#pragma unroll
+          for (int j = 0; j < KW; ++j) root[d][j] = cur[d][j];
       }
     }
   }
-  __device__ __forceinline__ void store(int32_t* dst, int j) const { store_bits(dst, root[j]); }
+  __device__ __forceinline__ void set_root_leaf(int d, int j, const uint32_t* v) { root[d][j] = v[0]; }
+  __device__ __forceinline__ void finish() {}
+  __device__ __forceinline__ void store(int32_t* dst, int d, int j) const { store_bits(dst, root[d][j]); }
 };
 
-template <int MAXL, int KW, int TH>
-struct TreeState<kGraded, MAXL, KW, TH> {
+// Mode B: saturating 8-plane counters, min(sum, N) at every node.
+template <int MAXL, int KW, int TH, int DPW>
+struct Tree<kGraded, MAXL, KW, TH, DPW> {
   static constexpr int kLeafPlanes = 3;
-  uint32_t acc[MAXL][KW][8];
-  uint32_t root[KW][8];
+  uint32_t acc[MAXL][DPW][KW][8];
+  uint32_t root[DPW][KW][8];
   int cnt[MAXL], node[MAXL], fan[MAXL];
+
   __device__ __forceinline__ void init(const TreeArgs& a) {
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
 #pragma unroll
-      for (int j = 0; j < KW; ++j)
+      for (int d = 0; d < DPW; ++d)
 #pragma unroll
-        for (int p = 0; p < 8; ++p) acc[l][j][p] = 0;
+        for (int j = 0; j < KW; ++j)
+#pragma unroll
+          for (int p = 0; p < 8; ++p) acc[l][d][j][p] = 0;
       cnt[l] = 0;
       node[l] = 0;
-      fan[l] = (l >= 1 && l < a.nlev) ? min(a.B, a.level_nodes[l - 1]) : 1;
+      fan[l] = (l >= 2 && l < a.nlev) ? min(a.B, a.level_nodes[l - 1]) : 1;
     }
+#pragma unroll
+    for (int d = 0; d < DPW; ++d)
+#pragma unroll
+      for (int j = 0; j < KW; ++j)
+#pragma unroll
+        for (int p = 0; p < 8; ++p) root[d][j][p] = 0;
+  }
+  template <int NC>
+  __device__ __forceinline__ static void leaf(const TreeArgs& a, const uint32_t* x, int cs, uint32_t* out) {
+    count7<NC>(x, cs, out);
+    if (a.N < 7) clamp_planes<3>(out, 0u, a.N);
+  }
+  struct Node {
+    uint32_t p[KW][8];
+  };
+  __device__ __forceinline__ static void node_clear(Node& n) {
 #pragma unroll
     for (int j = 0; j < KW; ++j)
 #pragma unroll
-      for (int p = 0; p < 8; ++p) root[j][p] = 0;
+      for (int p = 0; p < 8; ++p) n.p[j][p] = 0;
   }
-  __device__ __forceinline__ static void leaf(const TreeArgs& a, const uint32_t* x, int cs, uint32_t* out) {
-    uint32_t c[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i < cs) {
-        const uint32_t k0 = c[0] & x[i];
-        c[0] ^= x[i];
-        const uint32_t k1 = c[1] & k0;
-        c[1] ^= k0;
-        c[2] |= k1;
-      }
-    }
-    if (a.N < 7) clamp_planes<3>(c, 0u, a.N);
-    out[0] = c[0];
-    out[1] = c[1];
-    out[2] = c[2];
-  }
-  __device__ __forceinline__ void push(const TreeArgs& a, uint32_t (*v)[3]) {
-    uint32_t cur[KW][8];
-#pragma unroll
-    for (int j = 0; j < KW; ++j) {
-#pragma unroll
-      for (int p = 0; p < 8; ++p) cur[j][p] = (p < 3) ? v[j][p < 3 ? p : 0] : 0u;
-    }
-    if (a.nlev == 1) {
-#pragma unroll
-      for (int j = 0; j < KW; ++j)
-#pragma unroll
-        for (int p = 0; p < 8; ++p) root[j][p] = cur[j][p];
+  // level-1 node: add a 3-plane leaf value. When B*min(C,N) <= min(N, 63) the cap cannot
+  // bind inside a level-1 node and the sum fits 6 planes (plain add); otherwise saturate.
+  __device__ __forceinline__ static void node_add_sat(Node& n, int j, const uint32_t* v, int N, bool plain) {
+    if (plain) {
+      add_planes<6, 3>(n.p[j], v);
       return;
     }
+    const uint32_t over = add_planes<8, 3>(n.p[j], v);
+    if (N == 255) {
 #pragma unroll
-    for (int l = 1; l < MAXL; ++l) {
-      if (l >= a.nlev) break;
+      for (int p = 0; p < 8; ++p) n.p[j][p] |= over;
+    } else {
+      clamp_planes<8>(n.p[j], over, N);
+    }
+  }
+  __device__ __forceinline__ static void add_sat8(uint32_t* acc, const uint32_t* v, int N) {
+    const uint32_t over = add_planes<8, 8>(acc, v);
+    if (N == 255) {
 #pragma unroll
-      for (int j = 0; j < KW; ++j) {
-        // min(min(a+b,N)+c,N) = min(a+b+c,N) for non-negative values: saturate per child
-        const uint32_t over = add_planes<8, 8>(acc[l][j], cur[j]);
-        if (a.N == 255) {
+      for (int p = 0; p < 8; ++p) acc[p] |= over;
+    } else {
+      clamp_planes<8>(acc, over, N);
+    }
+  }
+  __device__ __forceinline__ void push_nodes(const TreeArgs& a, Node (&nd)[DPW]) {
+    if (a.nlev == 2) {
 #pragma unroll
-          for (int p = 0; p < 8; ++p) acc[l][j][p] |= over;
-        } else {
-          clamp_planes<8>(acc[l][j], over, a.N);
-        }
-      }
-      if (++cnt[l] < fan[l]) break;
+      for (int d = 0; d < DPW; ++d)
+#pragma unroll
+        for (int j = 0; j < KW; ++j)
+#pragma unroll
+          for (int p = 0; p < 8; ++p) root[d][j][p] = nd[d].p[j][p];
+      return;
+    }
+    uint32_t cur[DPW][KW][8];
+#pragma unroll
+    for (int d = 0; d < DPW; ++d)
 #pragma unroll
       for (int j = 0; j < KW; ++j)
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          cur[j][p] = acc[l][j][p];
-          acc[l][j][p] = 0;
-        }
+        for (int p = 0; p < 8; ++p) cur[d][j][p] = nd[d].p[j][p];
+#pragma unroll
+    for (int l = 2; l < MAXL; ++l) {
+      if (l >= a.nlev) break;
+#pragma unroll
+      for (int d = 0; d < DPW; ++d)
+#pragma unroll
+        for (int j = 0; j < KW; ++j) add_sat8(acc[l][d][j], cur[d][j], a.N);
+      if (++cnt[l] < fan[l]) break;
+#pragma unroll
+      for (int d = 0; d < DPW; ++d)
+#pragma unroll
+        for (int j = 0; j < KW; ++j)
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            cur[d][j][p] = acc[l][d][j][p];
+            acc[l][d][j][p] = 0;
+          }
       cnt[l] = 0;
       ++node[l];
       fan[l] = min(a.B, a.level_nodes[l - 1] - a.B * node[l]);
       if (l == a.nlev - 1) {
 #pragma unroll
-        for (int j = 0; j < KW; ++j)
+        for (int d = 0; d < DPW; ++d)
 #pragma unroll
-          for (int p = 0; p < 8; ++p) root[j][p] = cur[j][p];
+          for (int j = 0; j < KW; ++j)
+#pragma unroll
+            for (int p = 0; p < 8; ++p) root[d][j][p] = cur[d][j][p];
       }
     }
   }
-  __device__ __forceinline__ void store(int32_t* dst, int j) const { store_word<8>(dst, root[j]); }
+  __device__ __forceinline__ void set_root_leaf(int d, int j, const uint32_t* v) {
+#pragma unroll
+    for (int p = 0; p < 8; ++p) root[d][j][p] = (p < 3) ? v[p < 3 ? p : 0] : 0u;
+  }
+  __device__ __forceinline__ void finish() {}
+  __device__ __forceinline__ void store(int32_t* dst, int d, int j) const { store_word<8>(dst, root[d][j]); }
 };
 
-template <int MAXL, int KW, int TH>
-struct TreeState<kFloat, MAXL, KW, TH> {
-  // Mode C has no per-node rule, so the root count is the sum of all leaf counts: a small
-  // 6-plane counter (flushed every 9 leaves, <= 63) feeding a 16-plane counter.
+// Mode C: no node rule, so the root count is the sum of all leaf counts: a 6-plane counter
+// per DM (flushed every 9 leaves, <= 63) feeding a 16-plane counter.
+template <int MAXL, int KW, int TH, int DPW>
+struct Tree<kFloat, MAXL, KW, TH, DPW> {
   static constexpr int kLeafPlanes = 3;
-  uint32_t small[KW][6];
-  uint32_t big[KW][16];
+  uint32_t small[DPW][KW][6];
+  uint32_t big[DPW][KW][16];
   int nsmall;
   __device__ __forceinline__ void init(const TreeArgs&) {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
+    for (int d = 0; d < DPW; ++d)
 #pragma unroll
-      for (int p = 0; p < 6; ++p) small[j][p] = 0;
+      for (int j = 0; j < KW; ++j) {
 #pragma unroll
-      for (int p = 0; p < 16; ++p) big[j][p] = 0;
-    }
+        for (int p = 0; p < 6; ++p) small[d][j][p] = 0;
+#pragma unroll
+        for (int p = 0; p < 16; ++p) big[d][j][p] = 0;
+      }
     nsmall = 0;
   }
+  template <int NC>
   __device__ __forceinline__ static void leaf(const TreeArgs&, const uint32_t* x, int cs, uint32_t* out) {
-    uint32_t c[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i < cs) {
-        const uint32_t k0 = c[0] & x[i];
-        c[0] ^= x[i];
-        const uint32_t k1 = c[1] & k0;
-        c[1] ^= k0;
-        c[2] |= k1;
-      }
-    }
-    out[0] = c[0];
-    out[1] = c[1];
-    out[2] = c[2];
+    count7<NC>(x, cs, out);
+  }
+  __device__ __forceinline__ void add_leaf(int d, int j, const uint32_t* v) { add_planes<6, 3>(small[d][j], v); }
+  __device__ __forceinline__ void leaves_done(int n) {
+    nsmall += n;
+    if (nsmall >= 9) flush();
   }
   __device__ __forceinline__ void flush() {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-      add_planes<16, 6>(big[j], small[j]);
+    for (int d = 0; d < DPW; ++d)
 #pragma unroll
-      for (int p = 0; p < 6; ++p) small[j][p] = 0;
-    }
+      for (int j = 0; j < KW; ++j) {
+        add_planes<16, 6>(big[d][j], small[d][j]);
+#pragma unroll
+        for (int p = 0; p < 6; ++p) small[d][j][p] = 0;
+      }
     nsmall = 0;
   }
-  __device__ __forceinline__ void push(const TreeArgs&, uint32_t (*v)[3]) {
-#pragma unroll
-    for (int j = 0; j < KW; ++j) add_planes<6, 3>(small[j], v[j]);
-    if (++nsmall == 9) flush();
-  }
   __device__ __forceinline__ void finish() { flush(); }
-  __device__ __forceinline__ void store(int32_t* dst, int j) const { store_word<16>(dst, big[j]); }
+  __device__ __forceinline__ void store(int32_t* dst, int d, int j) const { store_word<16>(dst, big[d][j]); }
 };
 
-template <int MODE, int MAXL, int KW, int TH>
-__global__ void __launch_bounds__(256) k_tree(TreeArgs a) {
-  using State = TreeState<MODE, MAXL, KW, TH>;
-  constexpr int PL = State::kLeafPlanes;
+// k_tree: CTA = NW warps x DPW trial DMs each (DT = NW*DPW consecutive DMs) x tile_words
+// output words. Per group of G leaves (a multiple of B, so level-1 nodes never straddle):
+//   1. stage the group's channel windows from the mirrored bit ring into shared memory;
+//   2. phase 1: one warp per distinct (leaf, pattern) entry, lanes over words: evaluate the
+//      leaf's series once (the paper's unique leaf neuron for this DM tile);
+//   3. phase 2: every warp gathers, for each of its DMs and each level-1 node of the group,
+//      the node's leaf values at the DM's own leaf shifts (one funnel shift per plane and
+//      word) and pushes the finished node values up the tree.
+template <int MODE, int MAXL, int KW, int TH, int DPW, int CT>
+__global__ void __launch_bounds__(512, (MODE == kBinary && TH == 2) ? 2 : 1) k_tree(TreeArgs a) {
+  using T = Tree<MODE, MAXL, KW, TH, DPW>;
+  constexpr int PL = T::kLeafPlanes;
+  constexpr int NC = CT ? CT : 8;  // channels per leaf iterated at compile time
   extern __shared__ __align__(16) uint32_t sm[];
-  const int DT = blockDim.y;
+  const int NW = blockDim.y;
+  const int DT = NW * DPW;
   const int lane = threadIdx.x, wd = threadIdx.y;
-  const int tid = wd * 32 + lane, nthr = 32 * DT;
-  constexpr int TW = 32 * KW;
+  const int tid = wd * 32 + lane, nthr = 32 * NW;
   const int tile = blockIdx.y;
-  const long long aw0 = a.word0 + static_cast<long long>(blockIdx.x) * TW;
+  const long long aw0 = a.word0 + static_cast<long long>(blockIdx.x) * a.tile_words;
   const int awp = static_cast<int>(aw0 % a.R);
-  const int drow = tile * DT + wd;
-  const int d = min(drow, a.ndm - 1);
-  const int NL = a.nleaves, C = a.C, G = a.G, span = a.span;
+  const int NL = a.nleaves, C = a.C, G = a.G, span = a.span, cspan = a.cspan;
+  const int span_eff = min(span, a.tile_words + a.span_extra);
 
-  uint32_t* series = sm;                                                   // maxpat*PL*span
-  uint32_t* meta = series + static_cast<size_t>(a.maxpat) * PL * span;     // DT*G
-  int* eoff = reinterpret_cast<int*>(meta + DT * G);                        // maxpat*C
-  int* esh = eoff + a.maxpat * C;                                           // maxpat*C
-  int* eleaf = esh + a.maxpat * C;                                          // maxpat
+  // leaf series are stored as word pairs (w[j], w[j+1]) so a gather is one 64-bit load
+  uint2* ser = reinterpret_cast<uint2*>(sm);                                 // maxpat*PL*span
+  uint32_t* win = sm + 2 * a.maxpat * PL * span;                             // G*C*cspan
+  uint32_t* meta = win + G * C * cspan;                                      // DT*G
+  uint32_t* epk = meta + DT * G;                                             // maxpat*C
+  int* eleaf = reinterpret_cast<int*>(epk + a.maxpat * C);                    // maxpat
 
-  State st;
+  T st;
   st.init(a);
+  const bool plain1 = a.plain1 != 0;
 
   for (int g0 = 0; g0 < NL; g0 += G) {
     const int g1 = min(NL, g0 + G);
     const int ng = g1 - g0;
+    const int c_lo = g0 * C, c_hi = min(a.nchan, g1 * C);
     const int ebase = a.tp_off[tile * NL + g0];
     const int ne = a.tp_off[tile * NL + g1] - ebase;
-    for (int i = tid; i < ne; i += nthr) {
-      const int pid = a.tp_pid[ebase + i];
-      const int smin = a.tp_smin[ebase + i];
-      eleaf[i] = a.tp_leaf[ebase + i];
+    // 1. channel windows: absolute words aw0 + wb_c + [0, cspan)
+    for (int cl = wd; cl < c_hi - c_lo; cl += NW) {
+      const int c = c_lo + cl;
+      const uint32_t* row = a.ring + static_cast<size_t>(c) * 2 * a.R + awp + a.tile_wb[tile * a.nchan + c];
+      uint32_t* dst = win + cl * cspan;
+      for (int j = lane; j < cspan; j += 32) dst[j] = __ldg(row + j);
+    }
+    // entry info: window-relative word offset and shift of every channel of every entry
+    for (int e = tid; e < ne; e += nthr) {
+      const int pid = a.tp_pid[ebase + e];
+      const int smin = a.tp_smin[ebase + e];
+      const int k = a.tp_leaf[ebase + e];
+      eleaf[e] = k - g0;
       for (int ci = 0; ci < C; ++ci) {
-        const int rel = a.pat_rel[pid * C + ci];
-        eoff[i * C + ci] = (smin >> 5) + (rel >> 5);
-        esh[i * C + ci] = rel & 31;
+        const int c = k * C + ci;
+        uint32_t pk = 0;
+        if (c < a.nchan) {
+          const int q = 32 * (smin >> 5) + a.pat_rel[pid * C + ci];
+          pk = (static_cast<uint32_t>((q >> 5) - a.tile_wb[tile * a.nchan + c]) << 5) | static_cast<uint32_t>(q & 31);
+        }
+        epk[e * C + ci] = pk;
       }
     }
+    // per (DM, leaf): series word offset and bit shift
     for (int i = tid; i < DT * ng; i += nthr) {
       const int dl = i / ng, kl = i - dl * ng;
       const int dd = min(tile * DT + dl, a.ndm - 1);
@@ -409,56 +514,128 @@ __global__ void __launch_bounds__(256) k_tree(TreeArgs a) {
       meta[dl * G + kl] = (static_cast<uint32_t>(e * PL * span + j0) << 5) | static_cast<uint32_t>(s & 31);
     }
     __syncthreads();
-    // phase 1: distinct (leaf, pattern) series of this group
-    for (int it = tid; it < ne * span; it += nthr) {
-      const int e = it / span, j = it - e * span;
-      const int c0 = eleaf[e] * C;
-      const int cs = min(C, a.nchan - c0);
-      uint32_t x[8];
+    // 2. phase 1: distinct (leaf, pattern) series, one (entry, 32-word chunk) per warp step
+    {
+      const int nch = (span_eff + 31) >> 5;
+      for (int it = wd; it < ne * nch; it += NW) {
+        const int e = it / nch;
+        const int j = ((it - e * nch) << 5) + lane;
+        const int kl = eleaf[e];
+        const int cs = CT ? CT : min(C, a.nchan - (g0 + kl) * C);
+        const uint32_t* wbase = win + kl * C * cspan;
+        if (j < span_eff) {
+          uint32_t x[NC];
 #pragma unroll
-      for (int ci = 0; ci < 8; ++ci) {
-        if (ci < cs) {
-          const uint32_t* row = a.ring + static_cast<size_t>(c0 + ci) * 2 * a.R;
-          const int ph = awp + eoff[e * C + ci] + j;
-          x[ci] = funnel(__ldg(row + ph), __ldg(row + ph + 1), esh[e * C + ci]);
-        } else {
-          x[ci] = 0;
+          for (int ci = 0; ci < NC; ++ci) {
+            if (CT || ci < cs) {
+              const uint32_t pk = epk[e * C + ci];
+              const uint32_t* w = wbase + ci * cspan + (pk >> 5) + j;
+              x[ci] = funnel(w[0], w[1], pk & 31);
+            } else {
+              x[ci] = 0;
+            }
+          }
+          uint32_t v[PL];
+          T::template leaf<NC>(a, x, cs, v);
+          uint2* out = ser + e * PL * span;
+#pragma unroll
+          for (int p = 0; p < PL; ++p) {
+            out[p * span + j].x = v[p];
+            if (j > 0) out[p * span + j - 1].y = v[p];
+          }
         }
       }
-      uint32_t v[PL];
-      State::leaf(a, x, cs, v);
-#pragma unroll
-      for (int p = 0; p < PL; ++p) series[(e * PL + p) * span + j] = v[p];
     }
     __syncthreads();
-    // phase 2: every DM gathers its leaf values and pushes them up its tree
-    for (int kl = 0; kl < ng; ++kl) {
-      const uint32_t m = meta[wd * G + kl];
-      const int off = static_cast<int>(m >> 5);
-      const int sh = static_cast<int>(m & 31);
-      uint32_t v[KW][PL];
+    // 3. phase 2
+    if constexpr (MODE == kFloat) {
+      for (int kl = 0; kl < ng; ++kl) {
 #pragma unroll
-      for (int jw = 0; jw < KW; ++jw) {
-        const int w = lane + 32 * jw;
+        for (int d = 0; d < DPW; ++d) {
+          const uint32_t m = meta[(wd * DPW + d) * G + kl];
+          const uint2* base = ser + (m >> 5);
+          const int sh = m & 31;
 #pragma unroll
-        for (int p = 0; p < PL; ++p) {
-          const uint32_t* s = series + off + p * span + w;
-          v[jw][p] = funnel(s[0], s[1], sh);
+          for (int jw = 0; jw < KW; ++jw) {
+            const int w = lane + 32 * jw;
+            uint32_t v[PL];
+#pragma unroll
+            for (int p = 0; p < PL; ++p) {
+              const uint2 q = base[p * span + w];
+              v[p] = funnel(q.x, q.y, sh);
+            }
+            st.add_leaf(d, jw, v);
+          }
+        }
+        st.leaves_done(1);
+      }
+    } else {
+      if (a.nlev == 1) {
+        // a single leaf is the root
+#pragma unroll
+        for (int d = 0; d < DPW; ++d) {
+          const uint32_t m = meta[(wd * DPW + d) * G];
+          const uint2* base = ser + (m >> 5);
+#pragma unroll
+          for (int jw = 0; jw < KW; ++jw) {
+            const int w = lane + 32 * jw;
+            uint32_t v[PL];
+#pragma unroll
+            for (int p = 0; p < PL; ++p) {
+              const uint2 q = base[p * span + w];
+              v[p] = funnel(q.x, q.y, m & 31);
+            }
+            st.set_root_leaf(d, jw, v);
+          }
+        }
+      } else {
+        for (int k0 = g0; k0 < g1; k0 += a.B) {
+          const int k1 = min(g1, k0 + a.B);
+          typename T::Node nd[DPW];
+#pragma unroll
+          for (int d = 0; d < DPW; ++d) {
+            T::node_clear(nd[d]);
+            for (int k = k0; k < k1; ++k) {
+              const uint32_t m = meta[(wd * DPW + d) * G + (k - g0)];
+              const uint2* base = ser + (m >> 5);
+              const int sh = m & 31;
+#pragma unroll
+              for (int jw = 0; jw < KW; ++jw) {
+                const int w = lane + 32 * jw;
+                uint32_t v[PL];
+#pragma unroll
+                for (int p = 0; p < PL; ++p) {
+                  const uint2 q = base[p * span + w];
+                  v[p] = funnel(q.x, q.y, sh);
+                }
+                if constexpr (MODE == kBinary) {
+                  T::node_add(nd[d], jw, v);
+                } else {
+                  T::node_add_sat(nd[d], jw, v, a.N, plain1);
+                }
+              }
+            }
+          }
+          st.push_nodes(a, nd);
         }
       }
-      st.push(a, v);
     }
     __syncthreads();
   }
-  if constexpr (MODE == kFloat) st.finish();
-  if (drow >= a.ndm) return;
+  st.finish();
   const int lw = a.Lp >> 5;
 #pragma unroll
-  for (int jw = 0; jw < KW; ++jw) {
-    const long long aw = aw0 + lane + 32 * jw;
-    if (aw - a.word0 >= a.nwords) continue;
-    const int col = static_cast<int>(aw % lw) * 32;
-    st.store(a.plane + static_cast<size_t>(d) * a.Lp + col, jw);
+  for (int d = 0; d < DPW; ++d) {
+    const int drow = tile * DT + wd * DPW + d;
+    if (drow >= a.ndm) continue;
+#pragma unroll
+    for (int jw = 0; jw < KW; ++jw) {
+      const int w = lane + 32 * jw;
+      const long long aw = aw0 + w;
+      if (w >= a.tile_words || aw - a.word0 >= a.nwords) continue;
+      const int col = static_cast<int>(aw % lw) * 32;
+      st.store(a.plane + static_cast<size_t>(drow) * a.Lp + col, d, jw);
+    }
   }
 }
 
@@ -512,29 +689,32 @@ __global__ void k_tree_ref(RefArgs a) {
   a.plane[static_cast<size_t>(d) * a.Lp + static_cast<int>(t % a.Lp)] = root;
 }
 
-template <int MODE, int MAXL, int KW, int TH>
+template <int MODE, int MAXL, int KW, int TH, int DPW>
 cudaError_t run_tree(const TreeArgs& a, dim3 grid, dim3 block, int smem, cudaStream_t s) {
-  auto kern = k_tree<MODE, MAXL, KW, TH>;
+  auto kern = (a.C == 4 && a.nchan % 4 == 0) ? k_tree<MODE, MAXL, KW, TH, DPW, 4> : k_tree<MODE, MAXL, KW, TH, DPW, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int MODE, int KW, int TH>
-cudaError_t dispatch_levels(const Plan& p, const TreeArgs& a, dim3 grid, dim3 block, int smem,
-                            cudaStream_t s) {
-  if (p.nlev <= 4) return run_tree<MODE, 4, KW, TH>(a, grid, block, smem, s);
-  if (p.nlev <= 8) return run_tree<MODE, 8, KW, TH>(a, grid, block, smem, s);
-  return run_tree<MODE, 16, KW, TH>(a, grid, block, smem, s);
-}
-
 }  // namespace
 
-int tree_kw(int mode, int nlev, int kmax) {
+// Kernel shape for a mode and tree depth: {warps per CTA, DMs per warp, words per lane}.
+// Chosen so the per-thread accumulators (levels x DMs x words x planes) stay in registers.
+TreeShape tree_shape(int mode, int nlev, int kmax) {
   const int maxl = nlev <= 4 ? 4 : (nlev <= 8 ? 8 : 16);
-  const int per_level = (mode == SND_MODE_BINARY) ? (kmax <= 2 ? 2 : 8) : (mode == SND_MODE_GRADED ? 8 : 0);
-  return (maxl * per_level * 2 <= 64) ? 2 : 1;
+  if (mode == SND_MODE_BINARY) {
+    const int regs = maxl * (kmax <= 2 ? 2 : 8);  // accumulator words per (DM, word)
+    if (regs * 4 <= 48) return {16, 2, 2};
+    if (regs * 2 <= 48) return {16, 2, 1};
+    return {16, 1, 1};
+  }
+  if (mode == SND_MODE_GRADED) {
+    if (maxl * 8 * 2 <= 64) return {16, 2, 1};
+    return {16, 1, 1};
+  }
+  return {16, 2, 1};
 }
 
 cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream_t s) {
@@ -586,32 +766,47 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
   a.dl_lp = dp.dl_lp;
   a.dl_sh = dp.dl_sh;
   a.pat_rel = dp.pat_rel;
-  a.G = p.geom.group_leaves;
-  a.span = p.geom.span;
-  a.maxpat = p.geom.max_pat_group;
+  a.tile_wb = dp.tile_wb;
+  const TreeGeom& g = p.geom;
+  a.G = g.group_leaves;
+  a.span = g.span;
+  a.cspan = g.cspan;
+  a.maxpat = g.max_pat_group;
+  a.span_extra = g.span - g.tile_words;
+  {
+    const int lmax = p.B * (p.C < p.N ? p.C : p.N);
+    a.plain1 = (lmax <= p.N && lmax <= 63) ? 1 : 0;
+  }
   a.word0 = e_prev >> 5;
   a.nwords = static_cast<int>(((e_new - 1) >> 5) - (e_prev >> 5) + 1);
+  // spread the words evenly over the fewest tiles of at most tile_words
+  const int ntiles = (a.nwords + g.tile_words - 1) / g.tile_words;
+  a.tile_words = (a.nwords + ntiles - 1) / ntiles;
   a.plane = dp.plane;
   a.Lp = p.Lp;
-  const TreeGeom& g = p.geom;
-  dim3 block(32, g.dms_per_cta);
-  dim3 grid((a.nwords + g.tile_words - 1) / g.tile_words, g.ndm_tiles);
+  dim3 block(32, g.warps);
+  dim3 grid(ntiles, g.ndm_tiles);
   const int smem = g.smem_bytes;
   p.launches += 1;
+  // instantiations follow tree_shape(): the accumulators of every open level stay in registers
+  const int kmax = p.KL > p.KI ? p.KL : p.KI;
+  const int maxl = p.nlev <= 4 ? 4 : (p.nlev <= 8 ? 8 : 16);
   if (p.mode == SND_MODE_BINARY) {
-    const int kmax = p.KL > p.KI ? p.KL : p.KI;
     if (kmax <= 2) {
-      if (g.kw == 1) return dispatch_levels<kBinary, 1, 2>(p, a, grid, block, smem, s);
-      return dispatch_levels<kBinary, 2, 2>(p, a, grid, block, smem, s);
+      if (maxl == 4) return run_tree<kBinary, 4, 2, 2, 2>(a, grid, block, smem, s);
+      if (maxl == 8) return run_tree<kBinary, 8, 1, 2, 2>(a, grid, block, smem, s);
+      return run_tree<kBinary, 16, 1, 2, 1>(a, grid, block, smem, s);
     }
-    if (g.kw == 1) return dispatch_levels<kBinary, 1, 8>(p, a, grid, block, smem, s);
-    return dispatch_levels<kBinary, 2, 8>(p, a, grid, block, smem, s);
+    if (maxl == 4) return run_tree<kBinary, 4, 1, 8, 1>(a, grid, block, smem, s);
+    if (maxl == 8) return run_tree<kBinary, 8, 1, 8, 1>(a, grid, block, smem, s);
+    return run_tree<kBinary, 16, 1, 8, 1>(a, grid, block, smem, s);
   }
   if (p.mode == SND_MODE_GRADED) {
-    if (g.kw == 1) return dispatch_levels<kGraded, 1, 1>(p, a, grid, block, smem, s);
-    return dispatch_levels<kGraded, 2, 1>(p, a, grid, block, smem, s);
+    if (maxl == 4) return run_tree<kGraded, 4, 1, 1, 2>(a, grid, block, smem, s);
+    if (maxl == 8) return run_tree<kGraded, 8, 1, 1, 1>(a, grid, block, smem, s);
+    return run_tree<kGraded, 16, 1, 1, 1>(a, grid, block, smem, s);
   }
-  return run_tree<kFloat, 4, 2, 1>(a, grid, block, smem, s);
+  return run_tree<kFloat, 4, 1, 1, 2>(a, grid, block, smem, s);
 }
 
 }  // namespace snd
