@@ -197,6 +197,23 @@ int snd_delay_table(snd_plan_t plan, int32_t* host_out, int64_t n);
 int snd_profile(snd_plan_t plan, int enable);
 int snd_profile_read(snd_plan_t plan, double* ms_out, int64_t* count_out);
 
+/*
+ * Encoder without device allocation (the paper has no counterpart: this is a convenience for
+ * callers that cannot allocate device memory, e.g. code running where cudaMalloc is not
+ * allowed or plugins that are handed only pre-allocated buffers). Encodes one chunk on its
+ * own (statistics over this chunk, samples counted from its first row) exactly as
+ * snd_execute's encoder does:
+ *   d_chunk     device uint8[nsamp][nchan], read only
+ *   theta       encoder threshold in sigma (snd_options_t.enc_theta)
+ *   d_bits_out  device uint32[nchan][ceil(nsamp/32)]: bit i of word w is x_c(32 w + i)
+ * Needs no workspace: its histogram scratch is a static device array sized for at most 4096
+ * channels (nchan > 4096 returns SND_ERR_UNSUPPORTED). The first call on a device looks the
+ * array up and must come before any stream capture. Calls on one device share the array, so
+ * calls that overlap on the GPU race; serialise them. No allocation is made.
+ */
+int snd_encode_static(const uint8_t* d_chunk, int32_t nsamp, int32_t nchan, double theta, uint32_t* d_bits_out,
+                      void* stream);
+
 /* Release the plan's host memory. The workspace is the caller's. NULL is ignored. */
 void snd_destroy(snd_plan_t plan);
 

@@ -63,7 +63,7 @@ assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(SndCandidate) == 32
 
 EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", "snd_bind_workspace",
            "snd_execute", "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table",
-           "snd_profile", "snd_profile_read", "snd_destroy", "snd_error_string")
+           "snd_profile", "snd_profile_read", "snd_encode_static", "snd_destroy", "snd_error_string")
 STAGES = ("encode", "tree", "mf", "candidates")
 
 
@@ -87,13 +87,14 @@ def _load():
     lib.snd_delay_table.argtypes = [P, ctypes.POINTER(ctypes.c_int32), I64]
     lib.snd_profile.argtypes = [P, ctypes.c_int]
     lib.snd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    lib.snd_encode_static.argtypes = [V, I32, I32, D, V, V]
     lib.snd_destroy.argtypes = [P]
     lib.snd_destroy.restype = None
     lib.snd_error_string.argtypes = [ctypes.c_int]
     lib.snd_error_string.restype = ctypes.c_char_p
     for name in ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_bind_workspace", "snd_execute",
                  "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table", "snd_profile",
-                 "snd_profile_read"):
+                 "snd_profile_read", "snd_encode_static"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
