@@ -40,21 +40,34 @@ __global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk,
     const int v = i >> 5, l = i & 31;
     const int cc = blockIdx.x * 32 + l;
     const uint32_t n = h[v][l];
-    if (cc < nchan && n) atomicAdd(&hist[static_cast<size_t>(v) * nchan + cc], n);
+    if (cc < nchan && n) atomicAdd(&hist[static_cast<size_t>(cc) * 256 + v], n);
   }
 }
 
-__global__ void k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
-                         int32_t* __restrict__ levels) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per channel; lane l holds bins l, l+32, ..., l+224. Integer sums are exact; the
+// FP64 steps run on lane 0 in the fixed order above. For integer v, v < lo <=> v < ceil(lo)
+// and v > hi <=> v > floor(hi), and the smallest integer above thr is floor(thr) + 1, so the
+// clip bounds and the level are exact integer decisions.
+__global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
+                                                int32_t* __restrict__ levels) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (c >= nchan) return;
-  // hist is [256][nchan]: consecutive threads read consecutive words
-  uint32_t* h = hist + c;
+  uint32_t* h = hist + static_cast<size_t>(c) * 256;
+  long long n[8];
   long long s1 = 0, s2 = 0;
-  for (int v = 0; v < 256; ++v) {
-    const long long n = h[static_cast<size_t>(v) * nchan];
-    s1 += n * v;
-    s2 += n * v * v;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int v = lane + 32 * k;
+    n[k] = h[v];
+    h[v] = 0;  // ready for the next chunk
+    s1 += n[k] * v;
+    s2 += n[k] * v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+    s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
   }
   const double nf = static_cast<double>(nsamp);
   const double mu0 = __ddiv_rn(static_cast<double>(s1), nf);
@@ -62,21 +75,29 @@ __global__ void k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, doub
   const double sig0 = var0 > 0.0 ? __dsqrt_rn(var0) : 0.0;
   const double lo = __dsub_rn(mu0, __dmul_rn(5.0, sig0));
   const double hi = __dadd_rn(mu0, __dmul_rn(5.0, sig0));
+  const int ilo = static_cast<int>(fmin(fmax(ceil(lo), -1.0), 257.0));    // in range: v >= ilo
+  const int ihi = static_cast<int>(fmin(fmax(floor(hi), -1.0), 257.0));   //           v <= ihi
   long long s1in = 0, s2in = 0, nlo = 0, nhi = 0;
-  for (int v = 0; v < 256; ++v) {
-    const long long n = h[static_cast<size_t>(v) * nchan];
-    h[static_cast<size_t>(v) * nchan] = 0;  // ready for the next chunk
-    if (n == 0) continue;
-    const double fv = static_cast<double>(v);
-    if (fv < lo) {
-      nlo += n;
-    } else if (fv > hi) {
-      nhi += n;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int v = lane + 32 * k;
+    if (v < ilo) {
+      nlo += n[k];
+    } else if (v > ihi) {
+      nhi += n[k];
     } else {
-      s1in += n * v;
-      s2in += n * v * v;
+      s1in += n[k] * v;
+      s2in += n[k] * v * v;
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1in += __shfl_xor_sync(0xFFFFFFFFu, s1in, o);
+    s2in += __shfl_xor_sync(0xFFFFFFFFu, s2in, o);
+    nlo += __shfl_xor_sync(0xFFFFFFFFu, nlo, o);
+    nhi += __shfl_xor_sync(0xFFFFFFFFu, nhi, o);
+  }
+  if (lane != 0) return;
   const double s1c = __dadd_rn(__dadd_rn(static_cast<double>(s1in), __dmul_rn(static_cast<double>(nlo), lo)),
                                __dmul_rn(static_cast<double>(nhi), hi));
   const double s2c =
@@ -88,11 +109,10 @@ __global__ void k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, doub
   int u = 256;
   if (sig > 0.0) {
     const double thr = __dadd_rn(mu, __dmul_rn(theta, sig));
-    for (int v = 0; v < 256; ++v) {
-      if (static_cast<double>(v) > thr) {
-        u = v;
-        break;
-      }
+    if (thr < 0.0) {
+      u = 0;
+    } else if (thr < 255.0) {
+      u = static_cast<int>(floor(thr)) + 1;
     }
   }
   levels[c] = u;
@@ -129,19 +149,65 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ chunk,
   row[phys + R] = w;
 }
 
+// Warp per (ring word, 32 channels): lane l holds sample 32*aw + l and loads its 32 channel
+// bytes with two 16-byte loads; one ballot per channel turns the 32 comparisons into that
+// channel's spike word. Requires nchan % 32 == 0 and a 16-byte aligned chunk.
+__global__ void __launch_bounds__(256) k_pack32(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
+                                                const int32_t* __restrict__ levels, long long t0, long long word0,
+                                                int nwords, uint32_t* __restrict__ ring, int R) {
+  const int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ncb = nchan >> 5;
+  if (task >= nwords * ncb) return;
+  const int q = task / ncb, cb = task - q * ncb;
+  const int c0 = cb * 32;
+  const long long aw = word0 + q;
+  const long long r = aw * 32 + lane - t0;
+  const bool valid = r >= 0 && r < nsamp;
+  uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
+  if (valid) {
+    const uint4* src = reinterpret_cast<const uint4*>(chunk + static_cast<size_t>(r) * nchan + c0);
+    b0 = __ldg(src);
+    b1 = __ldg(src + 1);
+  }
+  const uint32_t wv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  const int my_u = levels[c0 + lane];
+  uint32_t mine = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int u = __shfl_sync(0xFFFFFFFFu, my_u, j);
+    const int v = static_cast<int>((wv[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+    const uint32_t word = __ballot_sync(0xFFFFFFFFu, valid && v >= u);
+    if (lane == j) mine = word;
+  }
+  const long long s0 = aw * 32;
+  const uint32_t keep = (s0 < t0) ? ((1u << static_cast<int>(t0 - s0)) - 1u) : 0u;
+  const int phys = static_cast<int>(aw % R);
+  uint32_t* row = ring + static_cast<size_t>(c0 + lane) * 2 * R;
+  const uint32_t w = (row[phys] & keep) | mine;
+  row[phys] = w;
+  row[phys + R] = w;
+}
+
 }  // namespace
 
 cudaError_t launch_encode(const Plan& p, const uint8_t* d_chunk, int nsamp, cudaStream_t s) {
   const DevPtrs& dp = p.dp;
   dim3 hb(32, 8), hg((p.nchan + 31) / 32, (nsamp + kHistRowsPerBlock - 1) / kHistRowsPerBlock);
   k_hist<<<hg, hb, 0, s>>>(d_chunk, nsamp, p.nchan, dp.hist);
-  k_levels<<<(p.nchan + 127) / 128, 128, 0, s>>>(dp.hist, p.nchan, nsamp, p.enc_theta, dp.levels);
+  k_levels<<<(p.nchan * 32 + 255) / 256, 256, 0, s>>>(dp.hist, p.nchan, nsamp, p.enc_theta, dp.levels);
   const long long t0 = p.T;
   const long long w0 = t0 >> 5;
   const long long w1 = (t0 + nsamp - 1) >> 5;
   const int nwords = static_cast<int>(w1 - w0 + 1);
-  dim3 pb(32, 8), pg((p.nchan + 31) / 32, (nwords + 7) / 8);
-  k_pack<<<pg, pb, 0, s>>>(d_chunk, nsamp, p.nchan, dp.levels, t0, w0, nwords, dp.ring, p.R);
+  if (p.nchan % 32 == 0 && (reinterpret_cast<uintptr_t>(d_chunk) & 15u) == 0) {
+    const long long tasks = static_cast<long long>(nwords) * (p.nchan / 32);
+    k_pack32<<<static_cast<unsigned>((tasks * 32 + 255) / 256), 256, 0, s>>>(d_chunk, nsamp, p.nchan, dp.levels, t0,
+                                                                           w0, nwords, dp.ring, p.R);
+  } else {
+    dim3 pb(32, 8), pg((p.nchan + 31) / 32, (nwords + 7) / 8);
+    k_pack<<<pg, pb, 0, s>>>(d_chunk, nsamp, p.nchan, dp.levels, t0, w0, nwords, dp.ring, p.R);
+  }
   p.launches += 3;
   return cudaGetLastError();
 }

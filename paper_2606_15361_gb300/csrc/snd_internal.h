@@ -59,7 +59,7 @@ struct TreeGeom {
 // Device pointers inside the bound workspace.
 struct DevPtrs {
   uint32_t* ring;          // [nchan][2R] bit ring (mirrored)
-  uint32_t* hist;          // [256][nchan]
+  uint32_t* hist;          // [nchan][256]
   int32_t* levels;         // [nchan] encoder level u_c (256 = never)
   int32_t* plane;          // [ndm][Lp] root values by absolute time modulo Lp
   uint32_t* mask;          // [ndm][mw] matched-filter mask of the current block

@@ -394,49 +394,53 @@ struct Tree<kGraded, MAXL, KW, TH, DPW> {
   __device__ __forceinline__ void store(int32_t* dst, int d, int j) const { store_word<8>(dst, root[d][j]); }
 };
 
-// Mode C: no node rule, so the root count is the sum of all leaf counts: a 6-plane counter
-// per DM (flushed every 9 leaves, <= 63) feeding a 16-plane counter.
+// Mode C: no node rule, so the root count is the sum of all leaf counts: node sums of up to
+// eight leaves (6 planes) are added into a 16-plane counter per (DM, word).
 template <int MAXL, int KW, int TH, int DPW>
 struct Tree<kFloat, MAXL, KW, TH, DPW> {
   static constexpr int kLeafPlanes = 3;
-  uint32_t small[DPW][KW][6];
-  uint32_t big[DPW][KW][16];
-  int nsmall;
+  uint32_t root[DPW][KW][16];
   __device__ __forceinline__ void init(const TreeArgs&) {
 #pragma unroll
     for (int d = 0; d < DPW; ++d)
 #pragma unroll
-      for (int j = 0; j < KW; ++j) {
+      for (int j = 0; j < KW; ++j)
 #pragma unroll
-        for (int p = 0; p < 6; ++p) small[d][j][p] = 0;
-#pragma unroll
-        for (int p = 0; p < 16; ++p) big[d][j][p] = 0;
-      }
-    nsmall = 0;
+        for (int p = 0; p < 16; ++p) root[d][j][p] = 0;
   }
   template <int NC>
   __device__ __forceinline__ static void leaf(const TreeArgs&, const uint32_t* x, int cs, uint32_t* out) {
     count7<NC>(x, cs, out);
   }
-  __device__ __forceinline__ void add_leaf(int d, int j, const uint32_t* v) { add_planes<6, 3>(small[d][j], v); }
-  __device__ __forceinline__ void leaves_done(int n) {
-    nsmall += n;
-    if (nsmall >= 9) flush();
-  }
-  __device__ __forceinline__ void flush() {
-#pragma unroll
-    for (int d = 0; d < DPW; ++d)
-#pragma unroll
-      for (int j = 0; j < KW; ++j) {
-        add_planes<16, 6>(big[d][j], small[d][j]);
-#pragma unroll
-        for (int p = 0; p < 6; ++p) small[d][j][p] = 0;
-      }
-    nsmall = 0;
-  }
-  __device__ __forceinline__ void finish() { flush(); }
-  __device__ __forceinline__ void store(int32_t* dst, int d, int j) const { store_word<16>(dst, big[d][j]); }
+  struct Node {};  // float needs no per-node state
+  __device__ __forceinline__ void add_node(int d, int j, const uint32_t* s6) { add_planes<16, 6>(root[d][j], s6); }
+  __device__ __forceinline__ void finish() {}
+  __device__ __forceinline__ void store(int32_t* dst, int d, int j) const { store_word<16>(dst, root[d][j]); }
 };
+
+// z[0..N] = x[0..N) + y[0..N) (ripple carry; N+1 planes out)
+template <int N>
+__device__ __forceinline__ void add2(const uint32_t* x, const uint32_t* y, uint32_t* z) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const uint32_t a = x[i], b = y[i];
+    z[i] = a ^ b ^ c;
+    c = (a & b) | (c & (a ^ b));
+  }
+  z[N] = c;
+}
+
+// Sum of eight 3-plane values by a pairwise adder tree (3+3 -> 4, 4+4 -> 5, 5+5 -> 6 planes):
+// about 50 logic operations instead of ~96 for eight sequential adds into a 6-plane counter.
+__device__ __forceinline__ void sum8(const uint32_t (&v)[8][3], uint32_t* out6) {
+  uint32_t a[4][4], b[2][5];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) add2<3>(v[2 * i], v[2 * i + 1], a[i]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) add2<4>(a[2 * i], a[2 * i + 1], b[i]);
+  add2<5>(b[0], b[1], out6);
+}
 
 // k_tree: CTA = NW warps x DPW trial DMs each (DT = NW*DPW consecutive DMs) x tile_words
 // output words. Per group of G leaves (a multiple of B, so level-1 nodes never straddle):
@@ -514,60 +518,115 @@ __global__ void __launch_bounds__(512, (MODE == kBinary && TH == 2) ? 2 : 1) k_t
       meta[dl * G + kl] = (static_cast<uint32_t>(e * PL * span + j0) << 5) | static_cast<uint32_t>(s & 31);
     }
     __syncthreads();
-    // 2. phase 1: distinct (leaf, pattern) series, one (entry, 32-word chunk) per warp step
-    {
-      const int nch = (span_eff + 31) >> 5;
-      for (int it = wd; it < ne * nch; it += NW) {
-        const int e = it / nch;
-        const int j = ((it - e * nch) << 5) + lane;
-        const int kl = eleaf[e];
-        const int cs = CT ? CT : min(C, a.nchan - (g0 + kl) * C);
-        const uint32_t* wbase = win + kl * C * cspan;
-        if (j < span_eff) {
-          uint32_t x[NC];
+    // 2. phase 1: distinct (leaf, pattern) series, one entry per warp, lanes over words
+    for (int e = wd; e < ne; e += NW) {
+      const int kl = eleaf[e];
+      const int cs = CT ? CT : min(C, a.nchan - (g0 + kl) * C);
+      uint32_t pk[NC];
+      const uint32_t* wch[NC];
 #pragma unroll
-          for (int ci = 0; ci < NC; ++ci) {
-            if (CT || ci < cs) {
-              const uint32_t pk = epk[e * C + ci];
-              const uint32_t* w = wbase + ci * cspan + (pk >> 5) + j;
-              x[ci] = funnel(w[0], w[1], pk & 31);
-            } else {
-              x[ci] = 0;
-            }
-          }
-          uint32_t v[PL];
-          T::template leaf<NC>(a, x, cs, v);
-          uint2* out = ser + e * PL * span;
+      for (int ci = 0; ci < NC; ++ci) {
+        pk[ci] = (CT || ci < cs) ? epk[e * C + ci] : 0u;
+        wch[ci] = win + (kl * C + ci) * cspan + (pk[ci] >> 5);
+      }
+      uint2* out = ser + e * PL * span;
+      for (int j = lane; j < span_eff; j += 32) {
+        uint32_t x[NC];
 #pragma unroll
-          for (int p = 0; p < PL; ++p) {
-            out[p * span + j].x = v[p];
-            if (j > 0) out[p * span + j - 1].y = v[p];
-          }
+        for (int ci = 0; ci < NC; ++ci)
+          x[ci] = (CT || ci < cs) ? funnel(wch[ci][j], wch[ci][j + 1], pk[ci] & 31) : 0u;
+        uint32_t v[PL];
+        T::template leaf<NC>(a, x, cs, v);
+#pragma unroll
+        for (int p = 0; p < PL; ++p) {
+          out[p * span + j].x = v[p];
+          if (j > 0) out[p * span + j - 1].y = v[p];
         }
       }
     }
     __syncthreads();
     // 3. phase 2
-    if constexpr (MODE == kFloat) {
-      for (int kl = 0; kl < ng; ++kl) {
+    if constexpr (MODE != kBinary) {
+      if (MODE == kGraded && a.nlev == 1) {
+        // a single leaf is the root
 #pragma unroll
         for (int d = 0; d < DPW; ++d) {
-          const uint32_t m = meta[(wd * DPW + d) * G + kl];
+          const uint32_t m = meta[(wd * DPW + d) * G];
           const uint2* base = ser + (m >> 5);
-          const int sh = m & 31;
 #pragma unroll
           for (int jw = 0; jw < KW; ++jw) {
-            const int w = lane + 32 * jw;
             uint32_t v[PL];
 #pragma unroll
             for (int p = 0; p < PL; ++p) {
-              const uint2 q = base[p * span + w];
-              v[p] = funnel(q.x, q.y, sh);
+              const uint2 q = base[p * span + lane + 32 * jw];
+              v[p] = funnel(q.x, q.y, m & 31);
             }
-            st.add_leaf(d, jw, v);
+            if constexpr (MODE == kGraded) st.set_root_leaf(d, jw, v);
           }
         }
-        st.leaves_done(1);
+      } else {
+        // float groups leaves by eight (its result does not depend on the tree); graded
+        // follows the level-1 nodes of B leaves
+        const int nstep = (MODE == kFloat) ? 8 : a.B;
+        const bool plain = (MODE == kFloat) || plain1;
+        for (int k0 = g0; k0 < g1; k0 += nstep) {
+          const int n = min(g1, k0 + nstep) - k0;
+          typename T::Node nd[DPW];
+#pragma unroll
+          for (int d = 0; d < DPW; ++d) {
+            const uint32_t* mrow = meta + (wd * DPW + d) * G + (k0 - g0);
+#pragma unroll
+            for (int jw = 0; jw < KW; ++jw) {
+              const int w = lane + 32 * jw;
+              uint32_t s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+              if (plain && n == 8) {
+                uint32_t v[8][3];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  const uint32_t m = mrow[i];
+                  const uint2* base = ser + (m >> 5);
+#pragma unroll
+                  for (int p = 0; p < 3; ++p) {
+                    const uint2 q = base[p * span + w];
+                    v[i][p] = funnel(q.x, q.y, m & 31);
+                  }
+                }
+                sum8(v, s8);
+              } else {
+                for (int i = 0; i < n; ++i) {
+                  const uint32_t m = mrow[i];
+                  const uint2* base = ser + (m >> 5);
+                  uint32_t v[3];
+#pragma unroll
+                  for (int p = 0; p < 3; ++p) {
+                    const uint2 q = base[p * span + w];
+                    v[p] = funnel(q.x, q.y, m & 31);
+                  }
+                  if (plain) {
+                    add_planes<6, 3>(s8, v);
+                  } else {
+                    const uint32_t over = add_planes<8, 3>(s8, v);
+                    if constexpr (MODE == kGraded) {
+                      if (a.N == 255) {
+#pragma unroll
+                        for (int p = 0; p < 8; ++p) s8[p] |= over;
+                      } else {
+                        clamp_planes<8>(s8, over, a.N);
+                      }
+                    }
+                  }
+                }
+              }
+              if constexpr (MODE == kFloat) {
+                st.add_node(d, jw, s8);
+              } else {
+#pragma unroll
+                for (int p = 0; p < 8; ++p) nd[d].p[jw][p] = s8[p];
+              }
+            }
+          }
+          if constexpr (MODE == kGraded) st.push_nodes(a, nd);
+        }
       }
     } else {
       if (a.nlev == 1) {
