@@ -282,12 +282,9 @@ int build_plan(Plan& p) {
   p.off.width_mask = take(sizeof(uint16_t) * ndm);
   p.off.dm_f32 = take(sizeof(float) * ndm);
   p.off.tp_off = take(sizeof(int32_t) * p.tp_off.size());
-  p.off.tp_pid = take(sizeof(int32_t) * std::max<size_t>(1, p.tp_pid.size()));
-  p.off.tp_smin = take(sizeof(int32_t) * std::max<size_t>(1, p.tp_smin.size()));
-  p.off.tp_leaf = take(sizeof(int32_t) * std::max<size_t>(1, p.tp_leaf.size()));
-  p.off.dl_lp = take(p.dl_lp.size());
-  p.off.dl_sh = take(sizeof(int32_t) * p.dl_sh.size());
-  p.off.pat_rel = take(sizeof(int32_t) * std::max<size_t>(1, p.pat_rel.size()));
+  p.off.gepk = take(sizeof(uint32_t) * std::max<size_t>(1, p.gepk.size()));
+  p.off.gleaf = take(sizeof(int32_t) * std::max<size_t>(1, p.gleaf.size()));
+  p.off.gmeta = take(sizeof(uint32_t) * p.gmeta.size());
   p.off.tile_wb = take(sizeof(int32_t) * p.tile_wb.size());
   p.off.delays = take(sizeof(int32_t) * p.delays.size());
   p.ws_bytes = o;
@@ -384,9 +381,10 @@ int choose_tree_geometry(Plan& p) {
         mp = std::max(mp, s);
       }
     *mp_out = mp;
-    // series as word pairs (2 words per series word), windows, meta, entry info
-    const int64_t words = static_cast<int64_t>(G) * p.C * g.cspan + 2 * static_cast<int64_t>(mp) * g.planes * g.span +
-                          static_cast<int64_t>(g.dms_per_cta) * G + static_cast<int64_t>(mp) * (p.C + 1);
+    // series as word pairs + two staging buffers (windows, meta, entry offsets and leaves)
+    const int64_t buf = (static_cast<int64_t>(G) * p.C * g.cspan + static_cast<int64_t>(g.dms_per_cta) * G +
+                         static_cast<int64_t>(mp) * (p.C + 1) + 3) & ~int64_t(3);
+    const int64_t words = 2 * static_cast<int64_t>(mp) * g.planes * g.span + 2 * buf;
     return words * 4;
   };
   const int64_t budget = 100 * 1024;
@@ -405,6 +403,43 @@ int choose_tree_geometry(Plan& p) {
   g.max_pat_group = mp;
   g.smem_bytes = static_cast<int>(bytes);
   if (bytes > 220 * 1024) return SND_ERR_UNSUPPORTED;
+
+  // Precomputed staging offsets, so a CTA only copies tables:
+  //  gepk[entry][ci]: channel ci of entry (smin, rel) is read at staged-window word
+  //    ((32*(smin>>5) + rel) >> 5) - wb_c (+ j, + 1) with bit shift rel & 31;
+  //  gleaf[entry]: its leaf relative to the first leaf of its group;
+  //  gmeta[d][k]: DM d gathers leaf k from series word ((e*planes*span + j0) << 5 | s & 31),
+  //    e = the entry's index within its group, j0 = (s>>5) - (smin>>5), s = the leaf shift.
+  const size_t ntp = p.tp_pid.size();
+  p.gepk.assign(ntp * p.C, 0);
+  p.gleaf.assign(ntp, 0);
+  for (int t = 0; t < g.ndm_tiles; ++t)
+    for (int k = 0; k < NL; ++k)
+      for (int32_t e = p.tp_off[static_cast<size_t>(t) * NL + k]; e < p.tp_off[static_cast<size_t>(t) * NL + k + 1];
+           ++e) {
+        const int pid = p.tp_pid[e], smin = p.tp_smin[e];
+        p.gleaf[e] = k - (k / G) * G;
+        for (int ci = 0; ci < p.C; ++ci) {
+          const int c = k * p.C + ci;
+          if (c >= nchan) continue;
+          const int q = 32 * (smin >> 5) + p.pat_rel[static_cast<size_t>(pid) * p.C + ci];
+          const int eoff = (q >> 5) - p.tile_wb[static_cast<size_t>(t) * nchan + c];
+          p.gepk[e * p.C + ci] = (static_cast<uint32_t>(eoff) << 5) | static_cast<uint32_t>(q & 31);
+        }
+      }
+  p.gmeta.assign(static_cast<size_t>(ndm) * NL, 0);
+  for (int d = 0; d < ndm; ++d) {
+    const int t = d / g.dms_per_cta;
+    for (int k = 0; k < NL; ++k) {
+      const size_t at = static_cast<size_t>(d) * NL + k;
+      const int g0 = (k / G) * G;
+      const int ebase = p.tp_off[static_cast<size_t>(t) * NL + g0];
+      const int eg = p.tp_off[static_cast<size_t>(t) * NL + k] + p.dl_lp[at];  // global entry index
+      const int s = p.dl_sh[at];
+      const int j0 = (s >> 5) - (p.tp_smin[eg] >> 5);
+      p.gmeta[at] = (static_cast<uint32_t>((eg - ebase) * g.planes * g.span + j0) << 5) | static_cast<uint32_t>(s & 31);
+    }
+  }
   return SND_OK;
 }
 

@@ -111,12 +111,9 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.width_mask = at<uint16_t>(d_ws, o.width_mask);
   dp.dm_f32 = at<float>(d_ws, o.dm_f32);
   dp.tp_off = at<int32_t>(d_ws, o.tp_off);
-  dp.tp_pid = at<int32_t>(d_ws, o.tp_pid);
-  dp.tp_smin = at<int32_t>(d_ws, o.tp_smin);
-  dp.tp_leaf = at<int32_t>(d_ws, o.tp_leaf);
-  dp.dl_lp = at<uint8_t>(d_ws, o.dl_lp);
-  dp.dl_sh = at<int32_t>(d_ws, o.dl_sh);
-  dp.pat_rel = at<int32_t>(d_ws, o.pat_rel);
+  dp.gepk = at<uint32_t>(d_ws, o.gepk);
+  dp.gleaf = at<int32_t>(d_ws, o.gleaf);
+  dp.gmeta = at<uint32_t>(d_ws, o.gmeta);
   dp.tile_wb = at<int32_t>(d_ws, o.tile_wb);
   dp.delays = at<int32_t>(d_ws, o.delays);
   std::vector<float> dmf(p.dms.begin(), p.dms.end());
@@ -124,12 +121,9 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   if (e == cudaSuccess) e = upload(d_ws, o.width_mask, p.width_mask, s);
   if (e == cudaSuccess) e = upload(d_ws, o.dm_f32, dmf, s);
   if (e == cudaSuccess) e = upload(d_ws, o.tp_off, p.tp_off, s);
-  if (e == cudaSuccess) e = upload(d_ws, o.tp_pid, p.tp_pid, s);
-  if (e == cudaSuccess) e = upload(d_ws, o.tp_smin, p.tp_smin, s);
-  if (e == cudaSuccess) e = upload(d_ws, o.tp_leaf, p.tp_leaf, s);
-  if (e == cudaSuccess) e = upload(d_ws, o.dl_lp, p.dl_lp, s);
-  if (e == cudaSuccess) e = upload(d_ws, o.dl_sh, p.dl_sh, s);
-  if (e == cudaSuccess) e = upload(d_ws, o.pat_rel, p.pat_rel, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.gepk, p.gepk, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.gleaf, p.gleaf, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.gmeta, p.gmeta, s);
   if (e == cudaSuccess) e = upload(d_ws, o.tile_wb, p.tile_wb, s);
   if (e == cudaSuccess) e = upload(d_ws, o.delays, p.delays, s);
   if (e != cudaSuccess) {

@@ -82,12 +82,9 @@ struct DevPtrs {
   uint16_t* width_mask;    // [ndm]
   float* dm_f32;           // [ndm]
   int32_t* tp_off;         // [ndm_tiles * nleaves + 1]
-  int32_t* tp_pid;         // [ntp] global pattern id of each (tile, leaf) entry
-  int32_t* tp_smin;        // [ntp]
-  int32_t* tp_leaf;        // [ntp] leaf of each entry
-  uint8_t* dl_lp;          // [ndm * nleaves] tile-local pattern index
-  int32_t* dl_sh;          // [ndm * nleaves] leaf shift = delta_ref(leaf)(d)
-  int32_t* pat_rel;        // [npat * C] relative delays of each pattern's channels
+  uint32_t* gepk;          // [ntp * C] staged-window word offset << 5 | shift per entry channel
+  int32_t* gleaf;          // [ntp] leaf of each entry relative to its group
+  uint32_t* gmeta;         // [ndm * nleaves] series word offset << 5 | shift per (DM, leaf)
   int32_t* tile_wb;        // [ndm_tiles * nchan] first staged ring word per channel (tile-relative)
   int32_t* delays;         // [ndm * nchan] full delay table (reference kernel, tests)
 };
@@ -131,6 +128,8 @@ struct Plan {
   std::vector<uint8_t> dl_lp;
   std::vector<int32_t> dl_sh;
   std::vector<int32_t> tile_wb;
+  std::vector<uint32_t> gepk, gmeta;  // precomputed staging offsets (see choose_tree_geometry)
+  std::vector<int32_t> gleaf;
   TreeGeom geom{};
 
   // sizes
@@ -141,7 +140,7 @@ struct Plan {
   struct Off {
     size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
         run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, width_mask, dm_f32, tp_off,
-        tp_pid, tp_smin, tp_leaf, dl_lp, dl_sh, pat_rel, tile_wb, delays;
+        gepk, gleaf, gmeta, tile_wb, delays;
   } off{};
 
   // binding and stream state

@@ -24,6 +24,8 @@
 //  * Leaves are processed in groups sized to the shared-memory budget; the per-DM tree
 //    state (one accumulator per open level) stays in registers across groups.
 
+#include <cuda_pipeline.h>
+
 #include "snd_internal.h"
 
 namespace snd {
@@ -34,13 +36,10 @@ struct TreeArgs {
   int R, nchan, ndm, nleaves;
   int C, B, KL, KI, N, nlev;
   int level_nodes[kMaxLevels];
-  const int32_t* tp_off;
-  const int32_t* tp_pid;
-  const int32_t* tp_smin;
-  const int32_t* tp_leaf;
-  const uint8_t* dl_lp;
-  const int32_t* dl_sh;
-  const int32_t* pat_rel;
+  const int32_t* tp_off;   // [ndm_tiles * nleaves + 1] first (tile, leaf) entry of each leaf
+  const uint32_t* gepk;    // [entries][C] window word offset << 5 | bit shift of each entry channel
+  const int32_t* gleaf;    // [entries] leaf of each entry, relative to its group's first leaf
+  const uint32_t* gmeta;   // [ndm][nleaves] series word offset << 5 | bit shift of (DM, leaf)
   const int32_t* tile_wb;  // [ndm_tiles][nchan] first staged ring word of each channel, relative to the tile
   int G, span, cspan, maxpat;
   int tile_words;   // output words per CTA (<= 32*KW)
@@ -467,56 +466,61 @@ __global__ void __launch_bounds__(512, (MODE == kBinary && TH == 2) ? 2 : 1) k_t
   const int span_eff = min(span, a.tile_words + a.span_extra);
 
   // leaf series are stored as word pairs (w[j], w[j+1]) so a gather is one 64-bit load
-  uint2* ser = reinterpret_cast<uint2*>(sm);                                 // maxpat*PL*span
-  uint32_t* win = sm + 2 * a.maxpat * PL * span;                             // G*C*cspan
-  uint32_t* meta = win + G * C * cspan;                                      // DT*G
-  uint32_t* epk = meta + DT * G;                                             // maxpat*C
-  int* eleaf = reinterpret_cast<int*>(epk + a.maxpat * C);                    // maxpat
+  // shared memory: leaf series (word pairs) + two staging buffers, each holding one group's
+  // channel windows, per-(DM, leaf) offsets and per-entry channel offsets/leaves; the next
+  // group's buffer is filled with cp.async while the current group computes
+  uint2* ser = reinterpret_cast<uint2*>(sm);                                 // maxpat*PL*span pairs
+  const int win_w = G * C * cspan, meta_w = DT * G, epk_w = a.maxpat * C;
+  const int buf_w = (win_w + meta_w + epk_w + a.maxpat + 3) & ~3;
+  uint32_t* bufs = sm + 2 * a.maxpat * PL * span;
 
   T st;
   st.init(a);
   const bool plain1 = a.plain1 != 0;
 
-  for (int g0 = 0; g0 < NL; g0 += G) {
+  auto prefetch = [&](int g0, int b) {
     const int g1 = min(NL, g0 + G);
     const int ng = g1 - g0;
     const int c_lo = g0 * C, c_hi = min(a.nchan, g1 * C);
     const int ebase = a.tp_off[tile * NL + g0];
     const int ne = a.tp_off[tile * NL + g1] - ebase;
-    // 1. channel windows: absolute words aw0 + wb_c + [0, cspan)
+    uint32_t* win = bufs + b * buf_w;
+    uint32_t* meta = win + win_w;
+    uint32_t* epk = meta + meta_w;
+    uint32_t* eleaf = epk + epk_w;
     for (int cl = wd; cl < c_hi - c_lo; cl += NW) {
       const int c = c_lo + cl;
       const uint32_t* row = a.ring + static_cast<size_t>(c) * 2 * a.R + awp + a.tile_wb[tile * a.nchan + c];
-      uint32_t* dst = win + cl * cspan;
-      for (int j = lane; j < cspan; j += 32) dst[j] = __ldg(row + j);
+      for (int j = lane; j < cspan; j += 32) __pipeline_memcpy_async(win + cl * cspan + j, row + j, 4);
     }
-    // entry info: window-relative word offset and shift of every channel of every entry
-    for (int e = tid; e < ne; e += nthr) {
-      const int pid = a.tp_pid[ebase + e];
-      const int smin = a.tp_smin[ebase + e];
-      const int k = a.tp_leaf[ebase + e];
-      eleaf[e] = k - g0;
-      for (int ci = 0; ci < C; ++ci) {
-        const int c = k * C + ci;
-        uint32_t pk = 0;
-        if (c < a.nchan) {
-          const int q = 32 * (smin >> 5) + a.pat_rel[pid * C + ci];
-          pk = (static_cast<uint32_t>((q >> 5) - a.tile_wb[tile * a.nchan + c]) << 5) | static_cast<uint32_t>(q & 31);
-        }
-        epk[e * C + ci] = pk;
-      }
+    for (int dl = wd; dl < DT; dl += NW) {
+      const uint32_t* src = a.gmeta + static_cast<size_t>(min(tile * DT + dl, a.ndm - 1)) * NL + g0;
+      for (int kl = lane; kl < ng; kl += 32) __pipeline_memcpy_async(meta + dl * G + kl, src + kl, 4);
     }
-    // per (DM, leaf): series word offset and bit shift
-    for (int i = tid; i < DT * ng; i += nthr) {
-      const int dl = i / ng, kl = i - dl * ng;
-      const int dd = min(tile * DT + dl, a.ndm - 1);
-      const int k = g0 + kl;
-      const size_t at = static_cast<size_t>(dd) * NL + k;
-      const int s = a.dl_sh[at];
-      const int e = a.tp_off[tile * NL + k] - ebase + a.dl_lp[at];
-      const int j0 = (s >> 5) - (a.tp_smin[ebase + e] >> 5);
-      meta[dl * G + kl] = (static_cast<uint32_t>(e * PL * span + j0) << 5) | static_cast<uint32_t>(s & 31);
+    for (int i = tid; i < ne * C; i += nthr)
+      __pipeline_memcpy_async(epk + i, a.gepk + static_cast<size_t>(ebase) * C + i, 4);
+    for (int i = tid; i < ne; i += nthr) __pipeline_memcpy_async(eleaf + i, a.gleaf + ebase + i, 4);
+    __pipeline_commit();
+  };
+
+  prefetch(0, 0);
+  for (int g0 = 0, gi = 0; g0 < NL; g0 += G, ++gi) {
+    const int g1 = min(NL, g0 + G);
+    const int ng = g1 - g0;
+    const int ebase = a.tp_off[tile * NL + g0];
+    const int ne = a.tp_off[tile * NL + g1] - ebase;
+    const int b = gi & 1;
+    if (g1 < NL) {
+      prefetch(g1, b ^ 1);
+      __pipeline_wait_prior(1);
+    } else {
+      __pipeline_wait_prior(0);
     }
+    const uint32_t* win = bufs + b * buf_w;
+    const uint32_t* meta = win + win_w;
+    const uint32_t* epk = meta + meta_w;
+    const int* eleaf = reinterpret_cast<const int*>(epk + epk_w);
+    (void)ng;
     __syncthreads();
     // 2. phase 1: distinct (leaf, pattern) series, one entry per warp, lanes over words
     for (int e = wd; e < ne; e += NW) {
@@ -752,6 +756,7 @@ template <int MODE, int MAXL, int KW, int TH, int DPW>
 cudaError_t run_tree(const TreeArgs& a, dim3 grid, dim3 block, int smem, cudaStream_t s) {
   auto kern = (a.C == 4 && a.nchan % 4 == 0) ? k_tree<MODE, MAXL, KW, TH, DPW, 4> : k_tree<MODE, MAXL, KW, TH, DPW, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
@@ -819,12 +824,9 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
   a.nlev = p.nlev;
   for (int l = 0; l < kMaxLevels; ++l) a.level_nodes[l] = l < p.nlev ? p.level_nodes[l] : 1;
   a.tp_off = dp.tp_off;
-  a.tp_pid = dp.tp_pid;
-  a.tp_smin = dp.tp_smin;
-  a.tp_leaf = dp.tp_leaf;
-  a.dl_lp = dp.dl_lp;
-  a.dl_sh = dp.dl_sh;
-  a.pat_rel = dp.pat_rel;
+  a.gepk = dp.gepk;
+  a.gleaf = dp.gleaf;
+  a.gmeta = dp.gmeta;
   a.tile_wb = dp.tile_wb;
   const TreeGeom& g = p.geom;
   a.G = g.group_leaves;
