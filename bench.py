@@ -330,6 +330,21 @@ def run_gpu(args, rank, world, local_rank):
     }
 
 
+def drive(mode_name: str, nchunks: int, branching: int):
+    """Run one plan of the workload over `nchunks` chunks, untimed (for profiler captures:
+    the tree kernel's second launch is the first steady-state chunk)."""
+    import torch
+    import paper_2606_15361_gb300 as g
+    m = dict(MODES)[mode_name]
+    chunks = [torch.from_numpy(W.chunk_data(i)).cuda() for i in range(nchunks)]
+    plan = g.Plan(W.freqs(), synth.NC_DT, W.dms(), branching, m, g.options(m, max_chunk=W.chunk))
+    for c in chunks:
+        plan.execute(c)
+    torch.cuda.synchronize()
+    _, rc = plan.candidates(check=False)
+    print(json.dumps({"drive": mode_name, "chunks": nchunks, "branching": branching, "status": rc}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,7 +353,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--drive", choices=[m for m, _ in MODES], help="profiling driver: one plan, no timing")
+    ap.add_argument("--chunks", type=int, default=3)
+    ap.add_argument("--branching", type=int, default=BRANCHING)
     args = ap.parse_args()
+    if args.drive:
+        drive(args.drive, args.chunks, args.branching)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -46,10 +46,10 @@ __device__ __forceinline__ double snr_of(long long s, double mu_w, double den) {
   return __ddiv_rn(__dsub_rn(static_cast<double>(s), mu_w), den);
 }
 
-__global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
-  // smem: the row segment, 4 words of front pad (aligned staging) and tail pad
+__global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
+  // smem: the row segment, placed so that every aligned group of four ring columns lands
+  // on a 16-byte boundary (one 128-bit store per group), with pads on both sides
   extern __shared__ __align__(16) int32_t smem[];
-  int32_t* y = smem + 4;
   __shared__ long long red1[kMfThreads / 32], red2[kMfThreads / 32];
   __shared__ int tau[kNumWidthSlots];
   __shared__ double smu, ssig;
@@ -59,22 +59,19 @@ __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int NWARP = kMfThreads / 32;
   const int len = static_cast<int>(a.e_new - a.f_prev);
-  // 1. stage ring columns [f_prev, e_new) of row d with 16-byte loads (Lp % 4 == 0, so an
-  //    aligned group of four columns never straddles the ring's wrap point)
+  const int c0 = static_cast<int>(a.f_prev % a.Lp);
+  const int r0 = c0 & 3;
+  int32_t* y = smem + 4 + r0;  // y[i] = ring column c0 + i
+  // 1. stage ring columns [f_prev, e_new) of row d with 16-byte loads and stores (Lp % 4 == 0,
+  //    so an aligned group of four columns never straddles the ring's wrap point)
   {
     const int32_t* src = a.plane + static_cast<size_t>(d) * a.Lp;
-    const int c0 = static_cast<int>(a.f_prev % a.Lp);
-    const int r0 = c0 & 3;
     const int ngroups = (len + r0 + 3) >> 2;
+    int4* dst = reinterpret_cast<int4*>(smem + 4);
     for (int k = tid; k < ngroups; k += kMfThreads) {
       int c = c0 - r0 + 4 * k;
       if (c >= a.Lp) c -= a.Lp;
-      const int4 v = __ldg(reinterpret_cast<const int4*>(src + c));
-      int32_t* dst = y + 4 * k - r0;
-      dst[0] = v.x;
-      dst[1] = v.y;
-      dst[2] = v.z;
-      dst[3] = v.w;
+      dst[k] = __ldg(reinterpret_cast<const int4*>(src + c));
     }
   }
   __syncthreads();
@@ -91,30 +88,21 @@ __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
   }
   const int nb = a.nb;
   if (nb <= 0) return;
-  // 2. exact integer sums over the block's start times
-  long long s1 = 0, s2 = 0;
-  for (int i = tid; i < nb; i += kMfThreads) {
-    const long long v = y[i];
-    s1 += v;
-    s2 += v * v;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_down_sync(0xFFFFFFFFu, s1, o);
-    s2 += __shfl_down_sync(0xFFFFFFFFu, s2, o);
-  }
-  if (lane == 0) {
-    red1[wid] = s1;
-    red2[wid] = s2;
-  }
-  __syncthreads();  // every warp has read the raw values before the in-place scan
-  // 3. warp-segmented exclusive scan in place (uint32 wrap-around keeps window sums exact)
+  __syncthreads();  // the caller's copy has read the raw values before the in-place scan
+  // 2. warp-segmented exclusive scan in place (uint32 wrap-around keeps window sums exact),
+  //    with the exact integer sums over the block's start times taken on the way
   const int seg = ((len + NWARP * 32 - 1) / (NWARP * 32)) * 32;
   const int lo = min(len, wid * seg), hi = min(len, lo + seg);
   uint32_t carry = 0;
+  long long s1 = 0, s2 = 0;
   for (int base = lo; base < hi; base += 32) {
     const int i = base + lane;
     const uint32_t v = (i < hi) ? static_cast<uint32_t>(y[i]) : 0u;
+    if (i < nb) {
+      const long long vv = static_cast<int32_t>(v);
+      s1 += vv;
+      s2 += vv * vv;
+    }
     uint32_t incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -125,6 +113,15 @@ __global__ void __launch_bounds__(kMfThreads) k_mf(MfArgs a) {
     carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
   }
   if (lane == 0) wsum[wid] = carry;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_down_sync(0xFFFFFFFFu, s1, o);
+    s2 += __shfl_down_sync(0xFFFFFFFFu, s2, o);
+  }
+  if (lane == 0) {
+    red1[wid] = s1;
+    red2[wid] = s2;
+  }
   __syncthreads();
   const uint32_t wm = a.width_mask[d];
   if (wid == 0) {
@@ -252,7 +249,7 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
   a.plane_out = nemit > 0 ? d_plane_out : nullptr;
   a.nemit = nemit;
   const int len = static_cast<int>(e_new - f_prev);
-  const int smem = (len + 12) * 4;  // 4 words of front pad, prefix total and staging overrun
+  const int smem = (len + 16) * 4;  // front pad (4 + up to 3), prefix total and staging overrun
   cudaError_t e = cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   k_mf<<<p.ndm, kMfThreads, smem, s>>>(a);
