@@ -132,6 +132,22 @@ def _tree_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
+def reduce_max(values, dist=None, device=None):
+    """Max over ranks of per-rank timings (the slowest rank sets the whole-job time)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, ms: float) -> float:
+    """Units processed by all ranks (weak scaling: each rank its own beam replica) per second
+    of the slowest rank."""
+    return units_per_rank_step * steps * world / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------------------
@@ -271,12 +287,9 @@ def run_gpu(args, rank, world, local_rank):
     ms_e2e = max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
 
     per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
-    t = torch.tensor([ms_dev, ms_e2e], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_dev, ms_e2e = float(t[0]), float(t[1])
-    value = per_step * args.steps * world / (ms_dev / 1e3)
-    e2e = per_step * args.steps * world / (ms_e2e / 1e3)
+    ms_dev, ms_e2e = reduce_max([ms_dev, ms_e2e], dist, dev)
+    value = whole_job_rate(per_step, args.steps, world, ms_dev)
+    e2e = whole_job_rate(per_step, args.steps, world, ms_e2e)
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -450,7 +450,8 @@ __device__ __forceinline__ void sum8(const uint32_t (&v)[8][3], uint32_t* out6) 
 //      the node's leaf values at the DM's own leaf shifts (one funnel shift per plane and
 //      word) and pushes the finished node values up the tree.
 template <int MODE, int MAXL, int KW, int TH, int DPW, int CT>
-__global__ void __launch_bounds__(512, (MODE == kBinary && TH == 2) ? 2 : 1) k_tree(TreeArgs a) {
+__global__ void __launch_bounds__((MODE != kBinary && DPW == 1 && MAXL == 4) ? 1024 : 512,
+                                  (MODE == kBinary && TH == 2) ? 2 : 1) k_tree(TreeArgs a) {
   using T = Tree<MODE, MAXL, KW, TH, DPW>;
   constexpr int PL = T::kLeafPlanes;
   constexpr int NC = CT ? CT : 8;  // channels per leaf iterated at compile time
@@ -774,11 +775,13 @@ TreeShape tree_shape(int mode, int nlev, int kmax) {
     if (regs * 2 <= 48) return {16, 2, 1};
     return {16, 1, 1};
   }
+  // graded / float: 32 warps x 1 DM (1024 threads, <= 64 registers) keeps 32-DM tiles at
+  // twice the warps per SM of 16 warps x 2 DMs
   if (mode == SND_MODE_GRADED) {
-    if (maxl * 8 * 2 <= 64) return {16, 2, 1};
+    if (maxl <= 4) return {32, 1, 1};
     return {16, 1, 1};
   }
-  return {16, 2, 1};
+  return {32, 1, 1};
 }
 
 cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream_t s) {
@@ -863,11 +866,11 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
     return run_tree<kBinary, 16, 1, 8, 1>(a, grid, block, smem, s);
   }
   if (p.mode == SND_MODE_GRADED) {
-    if (maxl == 4) return run_tree<kGraded, 4, 1, 1, 2>(a, grid, block, smem, s);
+    if (maxl == 4) return run_tree<kGraded, 4, 1, 1, 1>(a, grid, block, smem, s);
     if (maxl == 8) return run_tree<kGraded, 8, 1, 1, 1>(a, grid, block, smem, s);
     return run_tree<kGraded, 16, 1, 1, 1>(a, grid, block, smem, s);
   }
-  return run_tree<kFloat, 4, 1, 1, 2>(a, grid, block, smem, s);
+  return run_tree<kFloat, 4, 1, 1, 1>(a, grid, block, smem, s);
 }
 
 }  // namespace snd
