@@ -217,6 +217,48 @@ int snd_encode_static(const uint8_t* d_chunk, int32_t nsamp, int32_t nchan, doub
 /* Release the plan's host memory. The workspace is the caller's. NULL is ignored. */
 void snd_destroy(snd_plan_t plan);
 
+/*
+ * Multi-rate search (Methods, "Multi-rate extension"; Eq. scrunch). Each trial DM d runs at
+ * the scrunch factor S(d) = the largest power of two, at most s_max, with
+ * S*dt <= K d df / f_c^3 (df = |f_1 - f_0|, f_c = (max f + min f)/2, MHz). The DMs that share
+ * one S form a band, searched by its own plan (same mode, options and branching) at sample
+ * interval S*dt on the chunk averaged over S samples, (sum + S/2)/S per channel in uint8.
+ * Band candidates are reported in native units (t * S, width * S) with the global DM index
+ * and merged by single linkage: candidates within 20 pc cm^-3 and 200 ms of one another
+ * (through any chain) form one cluster, reported by its largest S/N (ties: smaller DM index,
+ * then smaller t), the list sorted by (t, dm_index).
+ *   opts       options of every band (NULL: Table S1 of `mode`); each band plan gets
+ *              max_chunk / S as its own max_chunk. opts->max_chunk must be a multiple of the
+ *              largest S in use (else SND_ERR_ARG)
+ *   s_max      largest scrunch factor, a power of two in 1..1024
+ * Errors: SND_ERR_ARG, SND_ERR_DM, SND_ERR_NOMEM and whatever snd_plan_ex returns for a band.
+ */
+typedef struct snd_multirate_s* snd_multirate_t;
+int snd_multirate_plan(const double* freqs_mhz, int32_t nchan, double dt_s, const double* dm_grid, int32_t ndm,
+                       int32_t branching, snd_mode_t mode, const snd_options_t* opts, int32_t s_max,
+                       snd_multirate_t* out);
+/* Number of bands and, for the first `cap`, their scrunch factors and DM counts (either array
+   may be NULL). Bands come in increasing S; a band's DMs keep the grid order. */
+int snd_multirate_info(snd_multirate_t mr, int32_t* nbands, int32_t* scrunch, int32_t* band_ndm, int32_t cap);
+/* The plan of band `band` (owned by `mr`: do not bind, execute or destroy it; statistics and
+   profiling calls are allowed). */
+int snd_multirate_band_plan(snd_multirate_t mr, int32_t band, snd_plan_t* out);
+/* Device workspace bytes: every band plan's workspace, scrunch staging and the merge lists. */
+size_t snd_multirate_workspace_size(snd_multirate_t mr);
+/* Bind a 256-byte aligned workspace and reset every band's stream state; synchronises `stream`. */
+int snd_multirate_bind_workspace(snd_multirate_t mr, void* d_workspace, size_t bytes, void* stream);
+/* Next chunk, device uint8[nsamp][nchan]; nsamp a multiple of the largest S in use, at most
+   max_chunk (else SND_ERR_CHUNK). Enqueued on `stream`, no host synchronisation. */
+int snd_multirate_execute(snd_multirate_t mr, const uint8_t* d_chunk, int32_t nsamp, void* stream);
+/* Same for a host chunk, copied into the workspace first (cudaMemcpyAsync on `stream`). */
+int snd_multirate_execute_host(snd_multirate_t mr, const uint8_t* h_chunk, int32_t nsamp, void* stream);
+/* Merge the candidates of all bands found since the previous call (on the GPU), copy at most
+   cap of them to host_out and clear the band lists; synchronises. SND_ERR_OVERFLOW and
+   SND_ERR_TIMEOUT as for snd_candidates. */
+int snd_multirate_candidates(snd_multirate_t mr, snd_candidate_t* host_out, int32_t cap, int32_t* n_out);
+/* Release the band plans and host memory; NULL is ignored. */
+void snd_multirate_destroy(snd_multirate_t mr);
+
 /* Static description of a status code. */
 const char* snd_error_string(int status);
 

@@ -63,7 +63,10 @@ assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(SndCandidate) == 32
 
 EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", "snd_bind_workspace",
            "snd_execute", "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table",
-           "snd_profile", "snd_profile_read", "snd_encode_static", "snd_destroy", "snd_error_string")
+           "snd_profile", "snd_profile_read", "snd_encode_static", "snd_destroy", "snd_error_string",
+           "snd_multirate_plan", "snd_multirate_info", "snd_multirate_band_plan", "snd_multirate_workspace_size",
+           "snd_multirate_bind_workspace", "snd_multirate_execute", "snd_multirate_execute_host",
+           "snd_multirate_candidates", "snd_multirate_destroy")
 STAGES = ("encode", "tree", "mf", "candidates")
 
 
@@ -92,9 +95,24 @@ def _load():
     lib.snd_destroy.restype = None
     lib.snd_error_string.argtypes = [ctypes.c_int]
     lib.snd_error_string.restype = ctypes.c_char_p
+    ip = ctypes.POINTER(I32)
+    lib.snd_multirate_plan.argtypes = [dp, I32, D, dp, I32, I32, I32, ctypes.POINTER(SndOptions), I32,
+                                       ctypes.POINTER(P)]
+    lib.snd_multirate_info.argtypes = [P, ip, ip, ip, I32]
+    lib.snd_multirate_band_plan.argtypes = [P, I32, ctypes.POINTER(P)]
+    lib.snd_multirate_workspace_size.argtypes = [P]
+    lib.snd_multirate_workspace_size.restype = SZ
+    lib.snd_multirate_bind_workspace.argtypes = [P, V, SZ, V]
+    lib.snd_multirate_execute.argtypes = [P, V, I32, V]
+    lib.snd_multirate_execute_host.argtypes = [P, V, I32, V]
+    lib.snd_multirate_candidates.argtypes = [P, ctypes.POINTER(SndCandidate), I32, ip]
+    lib.snd_multirate_destroy.argtypes = [P]
+    lib.snd_multirate_destroy.restype = None
     for name in ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_bind_workspace", "snd_execute",
                  "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table", "snd_profile",
-                 "snd_profile_read", "snd_encode_static"):
+                 "snd_profile_read", "snd_encode_static", "snd_multirate_plan", "snd_multirate_info",
+                 "snd_multirate_band_plan", "snd_multirate_bind_workspace", "snd_multirate_execute",
+                 "snd_multirate_execute_host", "snd_multirate_candidates"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -156,7 +174,7 @@ class Plan:
 
     def __del__(self):
         h = getattr(self, "handle", None)
-        if h is not None and h.value:
+        if h is not None and h.value and getattr(self, "_owned", True):
             lib.snd_destroy(h)
             self.handle = None
 
@@ -234,3 +252,96 @@ class Plan:
         _check(lib.snd_delay_table(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), out.size),
                "snd_delay_table")
         return out
+
+
+class _BandPlan(Plan):
+    """A band plan owned by a MultiRatePlan: statistics, profiling and the delay table only."""
+
+    def __init__(self, handle, freqs, dt, dms, mode, opts):
+        self.freqs, self.dms, self.dt, self.mode = freqs, dms, dt, mode
+        self.nchan, self.ndm, self.opts = freqs.size, dms.size, opts
+        self.handle = handle
+        self._owned = False
+        self.workspace = None
+
+
+class MultiRatePlan:
+    """Multi-rate search (snd_multirate_*): one plan per scrunch band, candidates merged on the GPU."""
+
+    def __init__(self, freqs, dt: float, dms, branching: int, mode: int, opts: SndOptions | None = None,
+                 s_max: int = 64, bind: bool = True, device=None, stream=None):
+        self.freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+        self.dms = np.ascontiguousarray(dms, dtype=np.float64)
+        self.dt = float(dt)
+        self.mode = int(mode)
+        self.nchan = self.freqs.size
+        self.opts = opts if opts is not None else options(mode)
+        h = ctypes.c_void_p()
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(lib.snd_multirate_plan(self.freqs.ctypes.data_as(dp), self.nchan, self.dt,
+                                      self.dms.ctypes.data_as(dp), self.dms.size, int(branching), self.mode,
+                                      ctypes.byref(self.opts), int(s_max), ctypes.byref(h)), "snd_multirate_plan")
+        self.handle = h
+        nb = ctypes.c_int32(0)
+        _check(lib.snd_multirate_info(h, ctypes.byref(nb), None, None, 0), "snd_multirate_info")
+        sc = (ctypes.c_int32 * max(nb.value, 1))()
+        nd = (ctypes.c_int32 * max(nb.value, 1))()
+        _check(lib.snd_multirate_info(h, ctypes.byref(nb), sc, nd, nb.value), "snd_multirate_info")
+        self.scrunch = [int(sc[i]) for i in range(nb.value)]
+        self.band_ndm = [int(nd[i]) for i in range(nb.value)]
+        self.workspace = None
+        if bind:
+            self.bind(device=device, stream=stream)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.snd_multirate_destroy(h)
+            self.handle = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib.snd_multirate_workspace_size(self.handle))
+
+    def band_plan(self, i: int) -> Plan:
+        """Borrowed view of band i's plan (stats, profile, delay table)."""
+        h = ctypes.c_void_p()
+        _check(lib.snd_multirate_band_plan(self.handle, int(i), ctypes.byref(h)), "snd_multirate_band_plan")
+        s = self.scrunch[i]
+        return _BandPlan(h, self.freqs, self.dt * s, np.zeros(self.band_ndm[i]), self.mode, self.opts)
+
+    def bind(self, device=None, stream=None, workspace=None):
+        import torch
+        n = self.workspace_bytes
+        if workspace is None:
+            workspace = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+        ptr = workspace.data_ptr()
+        off = (-ptr) % 256
+        self.workspace = workspace
+        _check(lib.snd_multirate_bind_workspace(self.handle, ctypes.c_void_p(ptr + off), n, _stream_ptr(stream)),
+               "snd_multirate_bind_workspace")
+
+    def execute(self, chunk, stream=None):
+        assert chunk.is_cuda and chunk.dtype.itemsize == 1 and chunk.is_contiguous()
+        _check(lib.snd_multirate_execute(self.handle, ctypes.c_void_p(chunk.data_ptr()), int(chunk.shape[0]),
+                                         _stream_ptr(stream)), "snd_multirate_execute")
+
+    def execute_host(self, chunk, stream=None):
+        if hasattr(chunk, "data_ptr"):
+            ptr, nsamp = chunk.data_ptr(), int(chunk.shape[0])
+        else:
+            chunk = np.ascontiguousarray(chunk, dtype=np.uint8)
+            ptr, nsamp = chunk.ctypes.data, chunk.shape[0]
+        _check(lib.snd_multirate_execute_host(self.handle, ctypes.c_void_p(ptr), nsamp, _stream_ptr(stream)),
+               "snd_multirate_execute_host")
+
+    def candidates(self, cap: int | None = None, check: bool = True):
+        """Merged candidates since the last call: (structured numpy array, status)."""
+        cap = int(self.opts.cand_capacity * len(self.scrunch) if cap is None else cap)
+        buf = (SndCandidate * max(cap, 1))()
+        n = ctypes.c_int32(0)
+        rc = lib.snd_multirate_candidates(self.handle, buf, cap, ctypes.byref(n))
+        if check:
+            _check(rc, "snd_multirate_candidates")
+        arr = np.frombuffer(bytes(buf)[: n.value * CANDIDATE_DTYPE.itemsize], dtype=CANDIDATE_DTYPE).copy()
+        return arr, rc

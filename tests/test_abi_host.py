@@ -114,3 +114,51 @@ def test_delay_table_matches_oracle_unsorted(snd):
     d = rng.uniform(0, 300, 33)
     p = snd.Plan(f, 2.56e-4, d, 3, snd.MODE_GRADED, bind=False)
     assert (p.delay_table() == delays.delay_table(f, 2.56e-4, d)).all()
+
+
+def _mr_rc(snd, freqs, dms, s_max=64, mode=1, **kw):
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    d = np.ascontiguousarray(dms, dtype=np.float64)
+    o = snd.options(mode, **kw)
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = snd.lib.snd_multirate_plan(f.ctypes.data_as(dp), f.size, 1.38e-4, d.ctypes.data_as(dp), d.size, 2, mode,
+                                    ctypes.byref(o), s_max, ctypes.byref(h))
+    if rc == 0:
+        snd.lib.snd_multirate_destroy(h)
+    else:
+        assert not h.value
+    return rc
+
+
+def test_multirate_plan_bands_match_oracle(snd):
+    """Band split (Eq. scrunch) of the library equals the oracle's, for several grids and caps."""
+    from oracle import delays as odelays
+    from oracle import multirate as omr
+    for nchan, dms, s_max in [(64, synth.dm_grid(128, 100.0), 64), (1024, synth.dm_grid(2048, 2000.0), 16),
+                              (1024, synth.dm_grid(2048, 2000.0), 4), (256, np.array([3.0, 900.0, 0.0, 450.0]), 64)]:
+        f = synth.channel_freqs(nchan)
+        m = snd.MultiRatePlan(f, 1.38e-4, dms, 2, snd.MODE_GRADED, s_max=s_max, bind=False)
+        exp = omr.bands(f, 1.38e-4, dms, s_max)
+        assert m.scrunch == [s for s, _ in exp]
+        assert m.band_ndm == [len(i) for _, i in exp]
+        for b, (s, idx) in enumerate(exp):
+            bp = m.band_plan(b)
+            st = bp.stats()
+            assert st.ndm == len(idx)
+            # the band runs its DM subset at sample interval S*dt
+            assert (bp.delay_table() == odelays.delay_table(f, s * 1.38e-4, np.asarray(dms)[idx])).all()
+        assert m.workspace_bytes > 0
+
+
+def test_multirate_plan_argument_errors(snd):
+    f = synth.channel_freqs(64)
+    d = synth.dm_grid(128, 100.0)
+    E = snd.ERR
+    assert _mr_rc(snd, f, d) == 0
+    assert _mr_rc(snd, f, d, s_max=3) == E["SND_ERR_ARG"]
+    assert _mr_rc(snd, f, d, s_max=0) == E["SND_ERR_ARG"]
+    assert _mr_rc(snd, f, d, s_max=2048) == E["SND_ERR_ARG"]
+    assert _mr_rc(snd, f, np.array([1.0, -2.0])) == E["SND_ERR_DM"]
+    # max_chunk must be a multiple of the largest scrunch factor in use
+    assert _mr_rc(snd, f, d, max_chunk=16384 + 1) == E["SND_ERR_ARG"]
