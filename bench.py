@@ -212,6 +212,39 @@ def run_reference(args, rank, world):
 # GPU arm
 # ----------------------------------------------------------------------------------------
 
+def multirate_rate(g, args, dev, stream, dchunks, freqs, dms, mode=("graded", 1), s_max=16):
+    """Multi-rate search of the same beam (graded mode, bands up to S = 16 as in Table S1),
+    timed beside the single-rate plan of the same mode: native DM-samples per second."""
+    import torch
+    m = g.MultiRatePlan(freqs, synth.NC_DT, dms, BRANCHING, mode[1], g.options(mode[1], max_chunk=W.chunk),
+                        s_max=s_max, device=dev)
+    single = g.Plan(freqs, synth.NC_DT, dms, BRANCHING, mode[1], g.options(mode[1], max_chunk=W.chunk), device=dev)
+    steps = max(1, min(args.steps, 5))
+    out = {"mode": mode[0], "s_max": s_max, "bands": [[s, n] for s, n in zip(m.scrunch, m.band_ndm)]}
+    for name, run in (("multirate", lambda c: m.execute(c)), ("single_rate", lambda c: single.execute(c))):
+        for _ in range(max(args.warmup, 1)):
+            for c in dchunks:
+                run(c)
+        (m if name == "multirate" else single).candidates(check=False)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            for c in dchunks:
+                run(c)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / steps
+        out[name] = {"ms_per_step": ms, "dm_samples_per_s": W.nchunks * W.chunk * W.ndm / (ms / 1e3)}
+    t0 = time.perf_counter()
+    c, _ = m.candidates(check=False)
+    out["merge_ms"] = 1e3 * (time.perf_counter() - t0)
+    out["merged_candidates"] = int(len(c))
+    out["speedup"] = out["single_rate"]["ms_per_step"] / out["multirate"]["ms_per_step"]
+    out["note"] = "step = 16 chunks of 16384 native samples; merge (candidate read) timed once, host clock"
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2606_15361_gb300 as g
@@ -286,6 +319,8 @@ def run_gpu(args, rank, world, local_rank):
     sync()
     ms_e2e = max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
 
+    mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if rank == 0 else None
+
     per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
     ms_dev, ms_e2e = reduce_max([ms_dev, ms_e2e], dist, dev)
     value = whole_job_rate(per_step, args.steps, world, ms_dev)
@@ -337,6 +372,7 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": len(MODES) * W.nchunks * W.chunk * W.nchan,
                 "d2h_bytes_per_step": int(d2h / max(args.steps, 1))},
         "realtime_beams_per_mode": realtime_beams,
+        "multirate": mr,
         "candidates_in_timed_steps": ncands,
         "cpu_baseline": cpu,
         "clocks": clk,
