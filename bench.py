@@ -245,6 +245,31 @@ def multirate_rate(g, args, dev, stream, dchunks, freqs, dms, mode=("graded", 1)
     return out
 
 
+def zfloat_rate(g, args, dev, dchunks, freqs, dms):
+    """Labelled-payload Mode C (precision study) on the same beam: the tree with FP16 and with
+    FP32 partial-sum storage, timed per chunk by the stage events (plane only)."""
+    out = {}
+    steps = max(1, min(args.steps, 3))
+    for name, flag in (("fp16", g.FLAG_FP16_PARTIALS), ("fp32", 0)):
+        p = g.Plan(freqs, synth.NC_DT, dms, BRANCHING, g.MODE_ZFLOAT,
+                   g.options(g.MODE_ZFLOAT, max_chunk=W.chunk, flags=flag), device=dev)
+        for _ in range(max(args.warmup, 1)):
+            for c in dchunks:
+                p.execute(c)
+        p.profile(True)
+        p.profile_read()
+        for _ in range(steps):
+            for c in dchunks:
+                p.execute(c)
+        prof = p.profile_read()
+        p.profile(False)
+        tms = prof["tree"][0] / max(prof["tree"][1], 1)
+        ems = prof["encode"][0] / max(prof["encode"][1], 1)
+        out[name] = {"tree_ms_per_chunk": round(tms, 4), "encode_ms_per_chunk": round(ems, 4),
+                     "tree_gdm_samples_per_s": round(W.chunk * W.ndm / (tms / 1e3) / 1e9, 2)}
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2606_15361_gb300 as g
@@ -320,6 +345,7 @@ def run_gpu(args, rank, world, local_rank):
     ms_e2e = max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
 
     mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if rank == 0 else None
+    zf = zfloat_rate(g, args, dev, dchunks, freqs, dms) if rank == 0 else None
 
     per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
     ms_dev, ms_e2e = reduce_max([ms_dev, ms_e2e], dist, dev)
@@ -373,6 +399,7 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(d2h / max(args.steps, 1))},
         "realtime_beams_per_mode": realtime_beams,
         "multirate": mr,
+        "zfloat_precision_study": zf,
         "candidates_in_timed_steps": ncands,
         "cpu_baseline": cpu,
         "clocks": clk,

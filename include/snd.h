@@ -48,7 +48,14 @@ typedef enum {
 typedef enum {
   SND_MODE_BINARY = 0,  /* Mode A: node = 1[count >= K] (K_L at leaves, K_I above) */
   SND_MODE_GRADED = 1,  /* Mode B: node = min(sum, N) at every node, root included */
-  SND_MODE_FLOAT = 2    /* Mode C: node = sum; root divided by sqrt(N_f) */
+  SND_MODE_FLOAT = 2,   /* Mode C: node = sum; root divided by sqrt(N_f) */
+  /* Mode C with the labelled payload x_c(t) = z_c(t) * 1[P_c(t) >= u_c], z = (P - mu_c)/sigma_c
+     (the encoder's clipped per-chunk statistics), for the float-mode precision study: every
+     node below the root is stored in FP32, or FP16 with SND_FLAG_FP16_PARTIALS, before its
+     parent adds it in FP32, children in index order; the FP32 root times fp32(1/sqrt(N_f)) is
+     the plane. Produces the float32 plane only: the matched filter and candidate stages do not
+     run (snd_candidates returns none). */
+  SND_MODE_ZFLOAT = 3
 } snd_mode_t;
 
 typedef struct snd_plan_s* snd_plan_t;
@@ -57,6 +64,9 @@ typedef struct snd_plan_s* snd_plan_t;
  * DM-sample, integer counts from the full delay table) instead of the tiled bit-sliced
  * kernel. Results are identical; it exists to cross-check the fast kernel. */
 #define SND_FLAG_REFERENCE_TREE 1
+/* Option flag (SND_MODE_ZFLOAT only): store the payload and every partial sum below the root
+ * in FP16 (round to nearest even) instead of FP32; accumulation stays FP32. */
+#define SND_FLAG_FP16_PARTIALS 2
 
 /*
  * Options. Fill with snd_options_init(mode, &o) (Supplementary Table S1 operating point
@@ -77,7 +87,7 @@ typedef struct {
   int32_t cand_capacity;    /* candidates held on the device between snd_candidates calls */
   int32_t cell_capacity;    /* mask cells with S/N kept per matched-filter block */
   int32_t run_capacity;     /* closed-mask runs per matched-filter block */
-  int32_t flags;            /* 0, or SND_FLAG_REFERENCE_TREE */
+  int32_t flags;            /* 0, SND_FLAG_REFERENCE_TREE, or SND_FLAG_FP16_PARTIALS (zfloat) */
 } snd_options_t;
 
 /* One detection (Methods, "Candidate detection": one candidate per island, peak pixel). */
@@ -154,8 +164,9 @@ int snd_bind_workspace(snd_plan_t plan, void* d_workspace, size_t bytes, void* s
  *   nsamp        1..max_chunk samples
  *   stream       all work is enqueued on it; no host synchronisation
  *   d_plane_out  optional device output [ndm][*nemit_out] row-major: int32 root values
- *                (binary 0/1, graded 0..N) or float32 (float mode, counts/sqrt(N_f)) for the
- *                newly emitted samples [E_prev, E_new); NULL to skip
+ *                (binary 0/1, graded 0..N) or float32 (float mode, counts/sqrt(N_f); zfloat,
+ *                the labelled-payload plane) for the newly emitted samples [E_prev, E_new);
+ *                NULL to skip
  *   nemit_out    optional host int32: E_new - E_prev, the emitted samples per row, where
  *                E = max(0, samples consumed - D) (every emitted sample has full history)
  * Candidates found by this call accumulate on the device until snd_candidates.

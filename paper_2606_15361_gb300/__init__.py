@@ -15,8 +15,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsnd.so")
 
-MODE_BINARY, MODE_GRADED, MODE_FLOAT = 0, 1, 2
+MODE_BINARY, MODE_GRADED, MODE_FLOAT, MODE_ZFLOAT = 0, 1, 2, 3
 FLAG_REFERENCE_TREE = 1
+FLAG_FP16_PARTIALS = 2
 
 STATUS = {
     0: "SND_OK", -1: "SND_ERR_ARG", -2: "SND_ERR_FREQ_ORDER", -3: "SND_ERR_DM",

@@ -12,6 +12,8 @@
 // physical word (a>>5) mod R and again at R + that (the mirror lets any window of < R words
 // be read contiguously).
 
+#include <cuda_fp16.h>
+
 #include "snd_internal.h"
 
 namespace snd {
@@ -48,8 +50,10 @@ __global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk,
 // FP64 steps run on lane 0 in the fixed order above. For integer v, v < lo <=> v < ceil(lo)
 // and v > hi <=> v > floor(hi), and the smallest integer above thr is floor(thr) + 1, so the
 // clip bounds and the level are exact integer decisions.
+// With ztab set (labelled payload), every lane also writes the payload of its 8 values,
+// z = (v - mu)/sigma in FP64 for v >= u (0 below), rounded once to FP16 (zfp16) or FP32.
 __global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
-                                                int32_t* __restrict__ levels) {
+                                                int32_t* __restrict__ levels, void* __restrict__ ztab, int zfp16) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= nchan) return;
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int
     nlo += __shfl_xor_sync(0xFFFFFFFFu, nlo, o);
     nhi += __shfl_xor_sync(0xFFFFFFFFu, nhi, o);
   }
-  if (lane != 0) return;
+  // every lane holds the same reduced sums, so every lane evaluates the same FP64 recipe
   const double s1c = __dadd_rn(__dadd_rn(static_cast<double>(s1in), __dmul_rn(static_cast<double>(nlo), lo)),
                                __dmul_rn(static_cast<double>(nhi), hi));
   const double s2c =
@@ -115,7 +119,46 @@ __global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int
       u = static_cast<int>(floor(thr)) + 1;
     }
   }
-  levels[c] = u;
+  if (lane == 0) levels[c] = u;
+  if (ztab) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int v = lane + 32 * k;
+      const double z = (v >= u) ? __ddiv_rn(__dsub_rn(static_cast<double>(v), mu), sig) : 0.0;
+      if (zfp16) {
+        static_cast<__half*>(ztab)[static_cast<size_t>(c) * 256 + v] = __double2half(z);
+      } else {
+        static_cast<float*>(ztab)[static_cast<size_t>(c) * 256 + v] = __double2float_rn(z);
+      }
+    }
+  }
+}
+
+// Labelled payload into the ring: zring[c][(t0 + r) mod Rz] = ztab[c][P_c(r)]. A CTA
+// transposes 32 channels x 256 samples through shared memory, so both the chunk reads and
+// the ring writes are contiguous runs; the 32 payload tables it uses stay in L1.
+template <typename ST>
+__global__ void __launch_bounds__(256) k_pack_z(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
+                                                const ST* __restrict__ ztab, long long t0, ST* __restrict__ zring,
+                                                int Rz) {
+  __shared__ ST tile[32][257];
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 256;
+  const int c = c0 + lane;
+  for (int rl = wy; rl < 256; rl += 8) {
+    const int r = r0 + rl;
+    if (r < nsamp && c < nchan)
+      tile[lane][rl] = __ldg(ztab + static_cast<size_t>(c) * 256 + chunk[static_cast<size_t>(r) * nchan + c]);
+  }
+  __syncthreads();
+  for (int cl = wy; cl < 32; cl += 8) {
+    if (c0 + cl >= nchan) break;
+    ST* row = zring + static_cast<size_t>(c0 + cl) * Rz;
+    for (int rl = lane; rl < 256; rl += 32) {
+      const int r = r0 + rl;
+      if (r < nsamp) row[static_cast<int>((t0 + r) % Rz)] = tile[cl][rl];
+    }
+  }
 }
 
 // One thread per (channel, ring word). Lanes run over channels, so each row read is a
@@ -195,8 +238,22 @@ cudaError_t launch_encode(const Plan& p, const uint8_t* d_chunk, int nsamp, cuda
   const DevPtrs& dp = p.dp;
   dim3 hb(32, 8), hg((p.nchan + 31) / 32, (nsamp + kHistRowsPerBlock - 1) / kHistRowsPerBlock);
   k_hist<<<hg, hb, 0, s>>>(d_chunk, nsamp, p.nchan, dp.hist);
-  k_levels<<<(p.nchan * 32 + 255) / 256, 256, 0, s>>>(dp.hist, p.nchan, nsamp, p.enc_theta, dp.levels);
+  const bool z = p.mode == SND_MODE_ZFLOAT;
+  k_levels<<<(p.nchan * 32 + 255) / 256, 256, 0, s>>>(dp.hist, p.nchan, nsamp, p.enc_theta, dp.levels,
+                                                      z ? dp.ztab : nullptr, p.zgeom.fp16);
   const long long t0 = p.T;
+  if (z) {
+    dim3 zb(32, 8), zg((p.nchan + 31) / 32, (nsamp + 255) / 256);
+    if (p.zgeom.fp16) {
+      k_pack_z<__half><<<zg, zb, 0, s>>>(d_chunk, nsamp, p.nchan, static_cast<const __half*>(dp.ztab), t0,
+                                         static_cast<__half*>(dp.zring), p.zgeom.Rz);
+    } else {
+      k_pack_z<float><<<zg, zb, 0, s>>>(d_chunk, nsamp, p.nchan, static_cast<const float*>(dp.ztab), t0,
+                                        static_cast<float*>(dp.zring), p.zgeom.Rz);
+    }
+    p.launches += 3;
+    return cudaGetLastError();
+  }
   const long long w0 = t0 >> 5;
   const long long w1 = (t0 + nsamp - 1) >> 5;
   const int nwords = static_cast<int>(w1 - w0 + 1);

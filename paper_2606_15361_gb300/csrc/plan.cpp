@@ -40,12 +40,13 @@ struct VecHash {
 };
 
 int choose_tree_geometry(Plan& p);
+int choose_ztree_geometry(Plan& p);
 
 }  // namespace
 
 extern "C" int snd_options_init(snd_mode_t mode, snd_options_t* o) {
   if (!o) return SND_ERR_ARG;
-  if (mode != SND_MODE_BINARY && mode != SND_MODE_GRADED && mode != SND_MODE_FLOAT)
+  if (mode != SND_MODE_BINARY && mode != SND_MODE_GRADED && mode != SND_MODE_FLOAT && mode != SND_MODE_ZFLOAT)
     return SND_ERR_ARG;
   std::memset(o, 0, sizeof(*o));
   // Supplementary Table S1 operating points; C = 4 from its SND-tree block.
@@ -182,7 +183,10 @@ int build_plan(Plan& p) {
   {
     p.level_unique.assign(p.nlev, 0);
     double adds = 0.0;
-    const int bits_out = (p.mode == SND_MODE_BINARY) ? 1 : (p.mode == SND_MODE_GRADED ? 8 : 32);
+    const int bits_out = (p.mode == SND_MODE_BINARY)   ? 1
+                         : (p.mode == SND_MODE_GRADED) ? 8
+                         : (p.mode == SND_MODE_ZFLOAT && (p.flags & SND_FLAG_FP16_PARTIALS)) ? 16
+                                                       : 32;
     double hist_bits_bytes = std::ceil(static_cast<double>(nchan) * static_cast<double>(din) / 8.0);
     // node pattern ids of the level below, [ndm][n]
     std::vector<int32_t> below(leaf_loc);
@@ -242,8 +246,9 @@ int build_plan(Plan& p) {
     p.hist_mem_bytes = static_cast<int64_t>(hist_bits_bytes);
   }
 
-  // --- DM tiles: distinct leaf patterns per (tile, leaf), per-DM index and shift ---
-  int rc = choose_tree_geometry(p);
+  // --- DM tiles: distinct leaf patterns per (tile, leaf), per-DM index and shift, for the
+  // bit-sliced tree; the labelled-payload tree has tiles of its own (and no bit ring use) ---
+  int rc = (p.mode == SND_MODE_ZFLOAT) ? choose_ztree_geometry(p) : choose_tree_geometry(p);
   if (rc) return rc;
 
   // --- ring, plane ring and workspace layout ---
@@ -287,6 +292,12 @@ int build_plan(Plan& p) {
   p.off.gmeta = take(sizeof(uint32_t) * p.gmeta.size());
   p.off.tile_wb = take(sizeof(int32_t) * p.tile_wb.size());
   p.off.delays = take(sizeof(int32_t) * p.delays.size());
+  if (p.mode == SND_MODE_ZFLOAT) {
+    const size_t es = p.zgeom.fp16 ? 2 : 4;
+    p.off.zring = take(es * static_cast<size_t>(nchan) * p.zgeom.Rz);
+    p.off.ztab = take(es * static_cast<size_t>(nchan) * 256);
+    p.off.zwb = take(sizeof(int32_t) * p.zwb.size());
+  }
   p.ws_bytes = o;
   return SND_OK;
 }
@@ -443,6 +454,54 @@ int choose_tree_geometry(Plan& p) {
   return SND_OK;
 }
 
+// Labelled-payload tree geometry: DMs per CTA, samples per CTA (32 lanes x samples per
+// lane, fewer samples for deeper trees so the per-level partial sums stay in registers), the
+// first staged sample of each channel per DM tile (its smallest delay over the tile) and the
+// widest staged window, leaves staged per shared-memory round, and the payload ring length.
+int choose_ztree_geometry(Plan& p) {
+  snd::ZGeom& z = p.zgeom;
+  const int ndm = p.ndm, nchan = p.nchan, NL = p.nleaves;
+  if (p.nlev > 16) return SND_ERR_UNSUPPORTED;
+  z.fp16 = (p.flags & SND_FLAG_FP16_PARTIALS) ? 1 : 0;
+  z.maxl = p.nlev <= 4 ? 4 : (p.nlev <= 8 ? 8 : 16);
+  z.spt = z.maxl == 4 ? 8 : (z.maxl == 8 ? 4 : 2);
+  z.dms_per_cta = 16;
+  z.tile_samples = 32 * z.spt;
+  z.ndm_tiles = (ndm + z.dms_per_cta - 1) / z.dms_per_cta;
+  p.zwb.assign(static_cast<size_t>(z.ndm_tiles) * nchan, 0);
+  int64_t spread = 0;
+  for (int t = 0; t < z.ndm_tiles; ++t) {
+    const int d0 = t * z.dms_per_cta, d1 = std::min(ndm, d0 + z.dms_per_cta);
+    for (int c = 0; c < nchan; ++c) {
+      int32_t lo = p.delays[static_cast<size_t>(d0) * nchan + c], hi = lo;
+      for (int d = d0 + 1; d < d1; ++d) {
+        lo = std::min(lo, p.delays[static_cast<size_t>(d) * nchan + c]);
+        hi = std::max(hi, p.delays[static_cast<size_t>(d) * nchan + c]);
+      }
+      p.zwb[static_cast<size_t>(t) * nchan + c] = lo;
+      spread = std::max<int64_t>(spread, static_cast<int64_t>(hi) - lo);
+    }
+  }
+  if (spread > (1 << 20)) return SND_ERR_UNSUPPORTED;
+  const int es = z.fp16 ? 2 : 4;
+  z.win = static_cast<int>(align_up(static_cast<size_t>(z.tile_samples + spread), 8));
+  // per staged channel: its window and the tile's DM offsets into it
+  const int64_t per_chan = static_cast<int64_t>(z.win) * es + 4 * z.dms_per_cta;
+  const int64_t budget = 72 * 1024;
+  int G = static_cast<int>(budget / (per_chan * p.C));
+  if (G < 1) {
+    G = 1;
+    if (per_chan * p.C > 200 * 1024) return SND_ERR_UNSUPPORTED;
+  }
+  z.group_leaves = std::min(G, NL);
+  const int gc = z.group_leaves * p.C;
+  z.smem_bytes = static_cast<int>(align_up(static_cast<size_t>(gc) * z.win * es, 16) +
+                                  static_cast<size_t>(4) * z.dms_per_cta * gc);
+  // every emitted sample reads [E_prev, T_new): at most D + max_chunk samples back
+  z.Rz = static_cast<int>(align_up(static_cast<size_t>(p.D) + p.max_chunk + 64, 8));
+  return SND_OK;
+}
+
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
@@ -453,7 +512,8 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
   if (out) *out = nullptr;
   if (!out || !freqs_mhz || !dm_grid || nchan < 1 || ndm < 1 || branching < 2 || branching > 64)
     return SND_ERR_ARG;
-  if (mode != SND_MODE_BINARY && mode != SND_MODE_GRADED && mode != SND_MODE_FLOAT) return SND_ERR_ARG;
+  if (mode != SND_MODE_BINARY && mode != SND_MODE_GRADED && mode != SND_MODE_FLOAT && mode != SND_MODE_ZFLOAT)
+    return SND_ERR_ARG;
   if (!finite_pos(dt_s)) return SND_ERR_ARG;
   if (nchan > 65536 || ndm > 65536) return SND_ERR_UNSUPPORTED;
   snd_options_t o;
@@ -462,7 +522,9 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
   } else {
     snd_options_init(mode, &o);
   }
-  if (o.flags & ~SND_FLAG_REFERENCE_TREE) return SND_ERR_ARG;
+  if (o.flags & ~(SND_FLAG_REFERENCE_TREE | SND_FLAG_FP16_PARTIALS)) return SND_ERR_ARG;
+  if ((o.flags & SND_FLAG_FP16_PARTIALS) && mode != SND_MODE_ZFLOAT) return SND_ERR_ARG;
+  if ((o.flags & SND_FLAG_REFERENCE_TREE) && mode == SND_MODE_ZFLOAT) return SND_ERR_UNSUPPORTED;
   if (o.cluster_size < 1 || o.cluster_size > 7) return SND_ERR_UNSUPPORTED;
   if (mode == SND_MODE_BINARY && (o.k_leaf < 1 || o.k_leaf > 8 || o.k_internal < 1 || o.k_internal > 8))
     return SND_ERR_UNSUPPORTED;
@@ -571,6 +633,12 @@ extern "C" int snd_plan_stats(snd_plan_t plan, snd_plan_stats_t* s) {
   s->tree_tile_words = p.geom.tile_words;
   s->tree_group_leaves = p.geom.group_leaves;
   s->tree_smem_bytes = p.geom.smem_bytes;
+  if (p.mode == SND_MODE_ZFLOAT) {
+    s->tree_tile_dms = p.zgeom.dms_per_cta;
+    s->tree_tile_words = p.zgeom.tile_samples / 32;
+    s->tree_group_leaves = p.zgeom.group_leaves;
+    s->tree_smem_bytes = p.zgeom.smem_bytes;
+  }
   s->max_patterns_per_group = p.geom.max_pat_group;
   s->kernel_launches = p.launches;
   return SND_OK;

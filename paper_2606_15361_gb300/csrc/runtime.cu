@@ -61,6 +61,18 @@ int run_chunk(Plan& p, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s, vo
   const int64_t f_new = std::max<int64_t>(0, e_new - (p.wmax - 1));
   const int nb = static_cast<int>(f_new - f_prev);
   cudaError_t e = stage(p, SND_STAGE_ENCODE, s, [&] { return snd::launch_encode(p, d_chunk, nsamp, s); });
+  if (p.mode == SND_MODE_ZFLOAT) {
+    // labelled-payload plane only: no matched filter or candidates
+    if (e == cudaSuccess && e_new > e_prev)
+      e = stage(p, SND_STAGE_TREE, s, [&] { return snd::launch_tree_z(p, e_prev, e_new, d_plane_out, s); });
+    if (e != cudaSuccess) return fail(p, SND_ERR_CUDA);
+    p.T += nsamp;
+    p.E = e_new;
+    p.last_stream = s;
+    p.pending_host = -1;
+    if (nemit_out) *nemit_out = static_cast<int32_t>(e_new - e_prev);
+    return SND_OK;
+  }
   if (e == cudaSuccess && e_new > e_prev)
     e = stage(p, SND_STAGE_TREE, s, [&] { return snd::launch_tree(p, e_prev, e_new, s); });
   if (e == cudaSuccess && nb > 0)
@@ -116,6 +128,10 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.gmeta = at<uint32_t>(d_ws, o.gmeta);
   dp.tile_wb = at<int32_t>(d_ws, o.tile_wb);
   dp.delays = at<int32_t>(d_ws, o.delays);
+  const bool z = p.mode == SND_MODE_ZFLOAT;
+  dp.zring = z ? at<void>(d_ws, o.zring) : nullptr;
+  dp.ztab = z ? at<void>(d_ws, o.ztab) : nullptr;
+  dp.zwb = z ? at<int32_t>(d_ws, o.zwb) : nullptr;
   std::vector<float> dmf(p.dms.begin(), p.dms.end());
   cudaError_t e = cudaMemsetAsync(d_ws, 0, p.ws_bytes, s);
   if (e == cudaSuccess) e = upload(d_ws, o.width_mask, p.width_mask, s);
@@ -126,6 +142,7 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   if (e == cudaSuccess) e = upload(d_ws, o.gmeta, p.gmeta, s);
   if (e == cudaSuccess) e = upload(d_ws, o.tile_wb, p.tile_wb, s);
   if (e == cudaSuccess) e = upload(d_ws, o.delays, p.delays, s);
+  if (e == cudaSuccess && z) e = upload(d_ws, o.zwb, p.zwb, s);
   if (e != cudaSuccess) {
     p.bound = false;
     return SND_ERR_CUDA;

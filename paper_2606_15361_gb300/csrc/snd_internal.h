@@ -56,6 +56,20 @@ struct TreeGeom {
   int ndm_tiles;
 };
 
+// Labelled-payload (zfloat) tree geometry (chosen on the host).
+struct ZGeom {
+  int fp16;           // payload and partial sums stored in FP16 (else FP32)
+  int maxl;           // level capacity of the kernel instantiation (4, 8, 16)
+  int spt;            // output samples per lane
+  int dms_per_cta;    // DM rows per CTA (one warp each)
+  int tile_samples;   // output samples per CTA (32 * spt)
+  int ndm_tiles;
+  int win;            // staged payload samples per channel
+  int group_leaves;   // leaves staged per shared-memory round
+  int smem_bytes;
+  int Rz;             // payload ring samples per channel
+};
+
 // Device pointers inside the bound workspace.
 struct DevPtrs {
   uint32_t* ring;          // [nchan][2R] bit ring (mirrored)
@@ -87,6 +101,9 @@ struct DevPtrs {
   uint32_t* gmeta;         // [ndm * nleaves] series word offset << 5 | shift per (DM, leaf)
   int32_t* tile_wb;        // [ndm_tiles * nchan] first staged ring word per channel (tile-relative)
   int32_t* delays;         // [ndm * nchan] full delay table (reference kernel, tests)
+  void* zring;             // zfloat: [nchan][Rz] payload ring (half or float), sample a at a mod Rz
+  void* ztab;              // zfloat: [nchan][256] payload of each uint8 value (0 below the level)
+  int32_t* zwb;            // zfloat: [ndm_tiles][nchan] first staged sample offset per channel
 };
 
 // Counter slots.
@@ -131,6 +148,8 @@ struct Plan {
   std::vector<uint32_t> gepk, gmeta;  // precomputed staging offsets (see choose_tree_geometry)
   std::vector<int32_t> gleaf;
   TreeGeom geom{};
+  ZGeom zgeom{};
+  std::vector<int32_t> zwb;
 
   // sizes
   int R = 0;           // ring words per copy
@@ -140,7 +159,7 @@ struct Plan {
   struct Off {
     size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
         run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, width_mask, dm_f32, tp_off,
-        gepk, gleaf, gmeta, tile_wb, delays;
+        gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb;
   } off{};
 
   // binding and stream state
@@ -175,5 +194,6 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
                       void* d_plane_out, cudaStream_t s);
 cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_t s);
 TreeShape tree_shape(int mode, int nlev, int kmax);  // k_tree launch shape
+cudaError_t launch_tree_z(const Plan& p, int64_t e_prev, int64_t e_new, void* d_plane_out, cudaStream_t s);
 
 }  // namespace snd

@@ -162,3 +162,23 @@ def test_multirate_plan_argument_errors(snd):
     assert _mr_rc(snd, f, np.array([1.0, -2.0])) == E["SND_ERR_DM"]
     # max_chunk must be a multiple of the largest scrunch factor in use
     assert _mr_rc(snd, f, d, max_chunk=16384 + 1) == E["SND_ERR_ARG"]
+
+
+def test_zfloat_flags_and_stats(snd):
+    f = synth.channel_freqs(64)
+    d = synth.dm_grid(128, 100.0)
+    E = snd.ERR
+    assert _plan_rc(snd, f, d, mode=snd.MODE_ZFLOAT) == 0
+    assert _plan_rc(snd, f, d, mode=snd.MODE_ZFLOAT, opts=snd.options(snd.MODE_ZFLOAT, flags=2)) == 0
+    # FP16 storage is a zfloat option; the reference kernel does not evaluate zfloat
+    assert _plan_rc(snd, f, d, mode=snd.MODE_FLOAT, opts=snd.options(snd.MODE_FLOAT, flags=2)) == E["SND_ERR_ARG"]
+    assert _plan_rc(snd, f, d, mode=snd.MODE_ZFLOAT,
+                    opts=snd.options(snd.MODE_ZFLOAT, flags=1)) == E["SND_ERR_UNSUPPORTED"]
+    assert _plan_rc(snd, f, d, mode=4, opts=snd.options(snd.MODE_FLOAT)) == E["SND_ERR_ARG"]
+    p16 = snd.Plan(f, 1.38e-4, d, 2, snd.MODE_ZFLOAT, snd.options(snd.MODE_ZFLOAT, flags=2), bind=False)
+    p32 = snd.Plan(f, 1.38e-4, d, 2, snd.MODE_ZFLOAT, bind=False)
+    s16, s32 = p16.stats(), p32.stats()
+    assert s16.tree_tile_dms == 16 and s16.tree_smem_bytes <= 72 * 1024 + 4096
+    # FP16 storage halves the per-node history of Eq. hist_mem relative to FP32
+    assert s16.hist_mem_bytes < s32.hist_mem_bytes
+    assert p16.workspace_bytes < p32.workspace_bytes
