@@ -273,6 +273,66 @@ void snd_multirate_destroy(snd_multirate_t mr);
 /* Static description of a status code. */
 const char* snd_error_string(int status);
 
+/*
+ * Learned candidate sifter (the paper leaves a learned classifier to future work,
+ * "Discussion"; the plain threshold-and-clustering sifter above stays the default and the
+ * reference). A CNN classifies 64-DM x 256-sample snippets of the float plane around
+ * candidates: three 3x3 convolutions (16/32/64 channels, zero padding 1, bias, ReLU), each
+ * followed by 2x2 max pooling, then fc 16384 -> 128 (ReLU) and fc 128 -> 1 (the logit of
+ * "astrophysical"). Loss: mean binary cross-entropy. Parameters: one FP32 vector of
+ * snd_sifter_num_params() values, in the order W1[16][1][3][3], b1[16], W2[32][16][3][3],
+ * b2[32], W3[64][32][3][3], b3[64], Wf1[128][16384] (features c*256 + y*32 + x), bf1[128],
+ * Wf2[128], bf2[1]. Convolutions and fc1 run as BF16 tensor-core GEMMs with FP32
+ * accumulation (forward and backward); training uses Adam (beta 0.9 / 0.999, eps 1e-8).
+ * Snippets are FP32 [n][64][256]; labels FP32 0/1 [n]. All device pointers; calls enqueue
+ * on `stream` (snd_sifter_gradients and snd_sifter_status synchronise it).
+ */
+typedef struct snd_sifter_s* snd_sifter_t;
+/* Host only. max_batch: largest n of any call (1..65536); training != 0 also sizes the
+   backward and optimizer buffers; seed: He-uniform initial weights (zero biases). */
+int snd_sifter_create(int32_t max_batch, int32_t training, uint64_t seed, snd_sifter_t* out);
+int64_t snd_sifter_num_params(void);
+size_t snd_sifter_workspace_size(snd_sifter_t sf);
+/* Bind a 256-byte aligned device workspace and upload the initial parameters (synchronises). */
+int snd_sifter_bind_workspace(snd_sifter_t sf, void* d_workspace, size_t bytes, void* stream);
+/* Replace the parameters from host memory (n = snd_sifter_num_params()); resets Adam. */
+int snd_sifter_set_params(snd_sifter_t sf, const float* host_params, int64_t n, void* stream);
+int snd_sifter_get_params(snd_sifter_t sf, float* host_params, int64_t n);
+/* Logits d_logits[n] of snippets d_x[n][64][256]. */
+int snd_sifter_forward(snd_sifter_t sf, const float* d_x, int32_t n, float* d_logits, void* stream);
+/* Loss (d_loss[1]) and its gradient with respect to every parameter (d_grads, num_params
+   floats) on n labelled snippets, without an update (training plans only). Either output
+   may be NULL. Synchronises; SND_ERR_TIMEOUT if a bounded device wait gave up. */
+int snd_sifter_gradients(snd_sifter_t sf, const float* d_x, const float* d_y, int32_t n, float* d_grads,
+                         float* d_loss, void* stream);
+/* One Adam step of learning rate lr on n labelled snippets; d_loss (optional) receives the
+   step's loss before the update. */
+int snd_sifter_train_step(snd_sifter_t sf, const float* d_x, const float* d_y, int32_t n, float lr, float* d_loss,
+                          void* stream);
+/* Synchronise and report the device error word (SND_ERR_TIMEOUT) or a sticky error. */
+int snd_sifter_status(snd_sifter_t sf);
+/* CUDA kernels enqueued by this sifter so far. */
+int64_t snd_sifter_launches(snd_sifter_t sf);
+void snd_sifter_destroy(snd_sifter_t sf);
+
+/*
+ * Snippet extraction: d_out[i][64][256] = the float plane d_plane[ndm][ld] (ncols valid
+ * columns) at rows d_rows[i] - 32 .. + 31 and columns d_cols[i] - 128 .. + 127, standardised
+ * with the FP64 mean and population std of the cells inside the plane (std 0 -> 1); cells
+ * outside are 0.
+ */
+int snd_snippets(const float* d_plane, int64_t ld, int32_t ndm, int64_t ncols, const int32_t* d_rows,
+                 const int64_t* d_cols, int32_t n, float* d_out, void* stream);
+
+/*
+ * The sifter's tensor-core GEMM, exposed for testing: d_c[m][ldc] (FP32) = A . B^T with
+ * A = d_a[m][lda] and B = d_b[n][ldb] BF16 row-major, k columns used (lda, ldb multiples of
+ * 8, pointers 16-byte aligned). splits > 1 splits K over CTAs and ADDS into d_c (zero it
+ * first). d_err: a device uint32 that receives a nonzero value if a bounded wait gave up.
+ */
+int snd_gemm_bf16(const void* d_a, int64_t lda, const void* d_b, int64_t ldb, int32_t m, int32_t n, int64_t k,
+                  float* d_c, int64_t ldc, int32_t splits, uint32_t* d_err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

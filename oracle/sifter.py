@@ -16,6 +16,9 @@ the GPU implementation:
   Loss: mean binary cross-entropy on the logit, log(1 + e^z) - y z.
 * Parameters live in one flat vector in this order: W1[16][1][3][3], b1, W2[32][16][3][3],
   b2, W3[64][32][3][3], b3, Wf1[128][16384], bf1, Wf2[1][128], bf2.
+* `act` (optional) rounds each post-ReLU convolution output before pooling, so that the
+  pooling decisions (an argmax) can be taken in the precision an implementation stores its
+  activations in; None keeps FP64 throughout.
 """
 from __future__ import annotations
 
@@ -115,7 +118,7 @@ def maxpool2_backward(dy, a, shape):
     return dq.reshape(n, c, h // 2, w // 2, 2, 2).transpose(0, 1, 2, 4, 3, 5).reshape(n, c, h, w)
 
 
-def forward(theta, x):
+def forward(theta, x, act=None):
     """Logits z[n] for snippets x[n][64][256]; also returns the cache for backward."""
     p = unpack(theta)
     a = np.asarray(x, dtype=np.float64)[:, None]
@@ -124,6 +127,8 @@ def forward(theta, x):
         w, b = p[2 * li], p[2 * li + 1]
         y = conv3x3(a, w, b)
         r = np.maximum(y, 0.0)
+        if act is not None:
+            r = act(r)
         pooled, am = maxpool2(r)
         cache.append((a, y, r.shape, am))
         a = pooled
@@ -140,10 +145,11 @@ def loss(z, y) -> float:
     return float(np.mean(np.logaddexp(0.0, z) - y * z))
 
 
-def gradients(theta, x, y):
-    """(loss, flat gradient) of the mean BCE loss by backpropagation."""
+def gradients(theta, x, y, act=None):
+    """(loss, flat gradient) of the mean BCE loss by backpropagation (the rounding `act`,
+    if given, is treated as the identity in the backward pass)."""
     p = unpack(theta)
-    z, (cache, f, hpre, h) = forward(theta, x)
+    z, (cache, f, hpre, h) = forward(theta, x, act)
     y = np.asarray(y, dtype=np.float64)
     n = z.shape[0]
     dz = (1.0 / (1.0 + np.exp(-z)) - y) / n

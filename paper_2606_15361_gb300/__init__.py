@@ -67,7 +67,11 @@ EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", 
            "snd_profile", "snd_profile_read", "snd_encode_static", "snd_destroy", "snd_error_string",
            "snd_multirate_plan", "snd_multirate_info", "snd_multirate_band_plan", "snd_multirate_workspace_size",
            "snd_multirate_bind_workspace", "snd_multirate_execute", "snd_multirate_execute_host",
-           "snd_multirate_candidates", "snd_multirate_destroy")
+           "snd_multirate_candidates", "snd_multirate_destroy",
+           "snd_sifter_create", "snd_sifter_num_params", "snd_sifter_workspace_size", "snd_sifter_bind_workspace",
+           "snd_sifter_set_params", "snd_sifter_get_params", "snd_sifter_forward", "snd_sifter_gradients",
+           "snd_sifter_train_step", "snd_sifter_status", "snd_sifter_launches", "snd_sifter_destroy", "snd_snippets",
+           "snd_gemm_bf16")
 STAGES = ("encode", "tree", "mf", "candidates")
 
 
@@ -109,6 +113,29 @@ def _load():
     lib.snd_multirate_candidates.argtypes = [P, ctypes.POINTER(SndCandidate), I32, ip]
     lib.snd_multirate_destroy.argtypes = [P]
     lib.snd_multirate_destroy.restype = None
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.snd_sifter_create.argtypes = [I32, I32, ctypes.c_uint64, ctypes.POINTER(P)]
+    lib.snd_sifter_num_params.argtypes = []
+    lib.snd_sifter_num_params.restype = I64
+    lib.snd_sifter_workspace_size.argtypes = [P]
+    lib.snd_sifter_workspace_size.restype = SZ
+    lib.snd_sifter_bind_workspace.argtypes = [P, V, SZ, V]
+    lib.snd_sifter_set_params.argtypes = [P, fp, I64, V]
+    lib.snd_sifter_get_params.argtypes = [P, fp, I64]
+    lib.snd_sifter_forward.argtypes = [P, V, I32, V, V]
+    lib.snd_sifter_gradients.argtypes = [P, V, V, I32, V, V, V]
+    lib.snd_sifter_train_step.argtypes = [P, V, V, I32, ctypes.c_float, V, V]
+    lib.snd_sifter_status.argtypes = [P]
+    lib.snd_sifter_launches.argtypes = [P]
+    lib.snd_sifter_launches.restype = I64
+    lib.snd_sifter_destroy.argtypes = [P]
+    lib.snd_sifter_destroy.restype = None
+    lib.snd_snippets.argtypes = [V, I64, I32, I64, V, V, I32, V, V]
+    lib.snd_gemm_bf16.argtypes = [V, I64, V, I64, I32, I32, I64, V, I64, I32, V, V]
+    for name in ("snd_sifter_create", "snd_sifter_bind_workspace", "snd_sifter_set_params", "snd_sifter_get_params",
+                 "snd_sifter_forward", "snd_sifter_gradients", "snd_sifter_train_step", "snd_sifter_status",
+                 "snd_snippets", "snd_gemm_bf16"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_bind_workspace", "snd_execute",
                  "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table", "snd_profile",
                  "snd_profile_read", "snd_encode_static", "snd_multirate_plan", "snd_multirate_info",
@@ -346,3 +373,103 @@ class MultiRatePlan:
             _check(rc, "snd_multirate_candidates")
         arr = np.frombuffer(bytes(buf)[: n.value * CANDIDATE_DTYPE.itemsize], dtype=CANDIDATE_DTYPE).copy()
         return arr, rc
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Sifter:
+    """The learned candidate sifter (snd_sifter_*) with a torch-allocated workspace."""
+
+    NUM_PARAMS = None
+
+    def __init__(self, max_batch: int, training: bool = True, seed: int = 1, device=None, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib.snd_sifter_create(int(max_batch), int(bool(training)), int(seed), ctypes.byref(h)),
+               "snd_sifter_create")
+        self.handle = h
+        self.max_batch = int(max_batch)
+        self.num_params = int(lib.snd_sifter_num_params())
+        import torch
+        n = int(lib.snd_sifter_workspace_size(h))
+        self.workspace = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+        ptr = self.workspace.data_ptr()
+        _check(lib.snd_sifter_bind_workspace(h, ctypes.c_void_p(ptr + (-ptr) % 256), n, _stream_ptr(stream)),
+               "snd_sifter_bind_workspace")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.snd_sifter_destroy(h)
+            self.handle = None
+
+    def set_params(self, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib.snd_sifter_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size,
+                                         _stream_ptr(stream)), "snd_sifter_set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.num_params, dtype=np.float32)
+        _check(lib.snd_sifter_get_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size),
+               "snd_sifter_get_params")
+        return p
+
+    def forward(self, x, logits=None, stream=None):
+        """x: device float32 [n][64][256] -> device float32 logits [n]."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        n = int(x.shape[0])
+        if logits is None:
+            logits = torch.empty(n, dtype=torch.float32, device=x.device)
+        _check(lib.snd_sifter_forward(self.handle, _ptr(x), n, _ptr(logits), _stream_ptr(stream)),
+               "snd_sifter_forward")
+        return logits
+
+    def gradients(self, x, y, stream=None):
+        """(loss, gradient vector) on device tensors x [n][64][256], y [n] (no update)."""
+        import torch
+        n = int(x.shape[0])
+        g = torch.empty(self.num_params, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(lib.snd_sifter_gradients(self.handle, _ptr(x), _ptr(y), n, _ptr(g), _ptr(loss), _stream_ptr(stream)),
+               "snd_sifter_gradients")
+        return loss, g
+
+    def train_step(self, x, y, lr: float, loss=None, stream=None):
+        n = int(x.shape[0])
+        _check(lib.snd_sifter_train_step(self.handle, _ptr(x), _ptr(y), n, float(lr),
+                                         _ptr(loss) if loss is not None else None, _stream_ptr(stream)),
+               "snd_sifter_train_step")
+
+    def status(self):
+        _check(lib.snd_sifter_status(self.handle), "snd_sifter_status")
+
+    @property
+    def launches(self) -> int:
+        return int(lib.snd_sifter_launches(self.handle))
+
+
+def snippets(plane, rows, cols, out=None, stream=None):
+    """Standardised 64 x 256 snippets of a device float32 plane [ndm][ncols] around
+    (rows[i], cols[i]) (device int32 / int64 tensors)."""
+    import torch
+    n = int(rows.shape[0])
+    if out is None:
+        out = torch.empty((n, 64, 256), dtype=torch.float32, device=plane.device)
+    _check(lib.snd_snippets(_ptr(plane), plane.stride(0), plane.shape[0], plane.shape[1], _ptr(rows), _ptr(cols), n,
+                            _ptr(out), _stream_ptr(stream)), "snd_snippets")
+    return out
+
+
+def gemm_bf16(a, b, k=None, splits=1, out=None, stream=None):
+    """FP32 C = A . B^T on the tensor cores (A [m][lda], B [n][ldb] BF16 device tensors)."""
+    import torch
+    m, n = int(a.shape[0]), int(b.shape[0])
+    k = int(a.shape[1] if k is None else k)
+    if out is None:
+        out = torch.zeros((m, n), dtype=torch.float32, device=a.device)
+    err = torch.zeros(1, dtype=torch.int32, device=a.device)
+    _check(lib.snd_gemm_bf16(_ptr(a), a.stride(0), _ptr(b), b.stride(0), m, n, k, _ptr(out), out.stride(0),
+                             int(splits), _ptr(err), _stream_ptr(stream)), "snd_gemm_bf16")
+    return out, err

@@ -1,0 +1,995 @@
+// Learned candidate sifter (the paper's "Discussion" leaves a learned classifier to future
+// work): DM-time snippets around candidates, classified by a small CNN that is trained and
+// run on the GPU with BF16 tensor-core GEMMs.
+//
+// Network (input 1 x 64 x 256): three 3x3 convolutions (16, 32, 64 channels, zero padding
+// 1, bias, ReLU), each followed by 2x2 max pooling; fc1 16384 -> 128 (ReLU); fc2 128 -> 1.
+// Loss: mean binary cross-entropy on the logit. Parameters are one flat FP32 vector:
+// W1[16][1][3][3], b1, W2[32][16][3][3], b2, W3[64][32][3][3], b3, Wf1[128][16384], bf1,
+// Wf2[128], bf2. Adam keeps FP32 moments; the GEMMs read BF16 copies of the weights.
+//
+// Every convolution and fc1, forward and backward, is one GEMM C = A B^T with both operands
+// K-major BF16 (k_gemm): TMA (128-byte swizzle) fills a 4-stage shared-memory ring, one
+// thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a TMEM
+// accumulator, and four warps read it back with tcgen05.ld for the epilogue (bias, ReLU,
+// BF16 or FP32, row-major or transposed store, or FP32 atomic add for split-K).
+// Activations are channel-major ([c][b][h][w]); im2col rows are [m][k] with m = (b, h, w)
+// and k = (cin, ky, kx), zero-padded to a multiple of 64.
+//   forward conv:   Y^T[cout][m] = relu(col[m][:] . W[cout][:] + b)      (transposed store)
+//   weight grad:    dW[cout][k] += dY^T[cout][m] . colT[k][m]            (split-K, atomic)
+//   input grad:     dcol[m][k]   = dY[m][:] . W^T[k][:]                  (then col2im)
+// Every mbarrier wait is bounded (about 2 s of clock); a wait that gives up sets a device
+// error word that the host turns into SND_ERR_TIMEOUT, and the kernel still frees its TMEM.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/snd.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr int kH = 64, kW = 256, kFeat = 64 * 8 * 32, kHid = 128;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+struct ConvL {
+  int cin, cout, h, w, kc, kp;
+};
+constexpr ConvL kConv[3] = {{1, 16, 64, 256, 9, 64}, {16, 32, 32, 128, 144, 192}, {32, 64, 16, 64, 288, 320}};
+
+// flat parameter offsets
+constexpr long long kOffW[3] = {0, 16 * 9 + 16, 16 * 9 + 16 + 32 * 144 + 32};
+constexpr long long kOffB[3] = {16 * 9, 16 * 9 + 16 + 32 * 144, 16 * 9 + 16 + 32 * 144 + 32 + 64 * 288};
+constexpr long long kOffWf1 = 16 * 9 + 16 + 32 * 144 + 32 + 64 * 288 + 64;
+constexpr long long kOffBf1 = kOffWf1 + static_cast<long long>(kHid) * kFeat;
+constexpr long long kOffWf2 = kOffBf1 + kHid;
+constexpr long long kOffBf2 = kOffWf2 + kHid;
+constexpr long long kNumParams = kOffBf2 + 1;
+
+enum : uint32_t { kErrWait = 1u };
+
+// ---------------------------------------------------------------- tcgen05 GEMM
+
+struct Epi {
+  const float* bias;  // [N] or null
+  int relu;
+  void* out;
+  int out_bf16;       // BF16 store (else FP32)
+  int transposed;     // out[n * ldo + m] (else out[m * ldo + n])
+  int atomic;         // FP32 atomic add (split-K)
+  long long ldo;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait on an mbarrier phase
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset: next 8-row group
+  d |= static_cast<uint64_t>(1) << 46;            // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t mma_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, int M, int N, int ktiles,
+           int kt_per_split, Epi epi, uint32_t* err) {
+  constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+  constexpr uint32_t kCols = BN < 32 ? 32 : BN;
+  extern __shared__ uint8_t gsm_raw[];
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sA = smem_u32(gsm), sB = sA + kStages * kABytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int kt0 = blockIdx.z * kt_per_split;
+  const int nkt = min(ktiles, kt0 + kt_per_split) - kt0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads of the A and B tiles of each K step into the stage ring
+    for (int i = 0; i < nkt; ++i) {
+      const int s = i % kStages;
+      if (i >= kStages && !mbar_wait(smem_u32(&bar_empty[s]), ((i / kStages) & 1) ^ 1)) {
+        atomicOr(err, kErrWait);
+        abort_flag = 1;
+        break;
+      }
+      if (*reinterpret_cast<volatile int*>(&abort_flag)) break;
+      const uint32_t fb = smem_u32(&bar_full[s]);
+      mbar_expect_tx(fb, kABytes + kBBytes);
+      tma_load_2d(sA + s * kABytes, &ma, fb, (kt0 + i) * kBK, m0);
+      tma_load_2d(sB + s * kBBytes, &mb, fb, (kt0 + i) * kBK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: four K = 16 steps per stage, then release the stage
+    constexpr uint32_t idesc = mma_idesc(BN);
+    for (int i = 0; i < nkt; ++i) {
+      const int s = i % kStages;
+      if (!mbar_wait(smem_u32(&bar_full[s]), (i / kStages) & 1)) {
+        atomicOr(err, kErrWait);
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint64_t da = sw128_desc(sA + s * kABytes + kk * 32);
+        const uint64_t db = sw128_desc(sB + s * kBBytes + kk * 32);
+        umma_bf16(tmem, da, db, idesc, (i | kk) != 0 ? 1u : 0u);
+      }
+      umma_commit(smem_u32(&bar_empty[s]));
+    }
+    umma_commit(smem_u32(&bar_done));
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w + 31
+  bool ok = mbar_wait(smem_u32(&bar_done), 0);
+  ok = __all_sync(0xFFFFFFFFu, ok);
+  if (!ok && lane == 0) atomicOr(err, kErrWait);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && nkt > 0) {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 8) {
+      float v[8];
+      tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c), v);
+      if (row >= M) continue;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int n = n0 + c + i;
+        if (n >= N) continue;
+        float x = v[i];
+        if (epi.bias) x += epi.bias[n];
+        if (epi.relu) x = fmaxf(x, 0.0f);
+        const long long idx = epi.transposed ? static_cast<long long>(n) * epi.ldo + row
+                                             : static_cast<long long>(row) * epi.ldo + n;
+        if (epi.atomic) {
+          atomicAdd(static_cast<float*>(epi.out) + idx, x);
+        } else if (epi.out_bf16) {
+          static_cast<bf16*>(epi.out)[idx] = __float2bfloat16_rn(x);
+        } else {
+          static_cast<float*>(epi.out)[idx] = x;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- layer kernels
+
+// col[m][kp] = x[ci][b][y + ky - 1][x + kx - 1] (zero outside, zero for k >= kc); x is FP32
+// (the snippets) or BF16 (pooled activations), channel-major with channel stride n*h*w.
+template <typename T>
+__global__ void k_im2col(const T* __restrict__ x, int n, int h, int w, int kc, int kp, bf16* __restrict__ col) {
+  const long long hw = static_cast<long long>(h) * w;
+  const long long total = static_cast<long long>(n) * hw * (kp / 8);
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long m = i / (kp / 8);
+    const int k0 = static_cast<int>(i - m * (kp / 8)) * 8;
+    const int b = static_cast<int>(m / hw);
+    const int yx = static_cast<int>(m - b * hw);
+    const int yy = yx / w, xx = yx - yy * w;
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + j;
+      float val = 0.0f;
+      if (k < kc) {
+        const int ci = k / 9, r = k - ci * 9, ky = r / 3, kx = r - ky * 3;
+        const int sy = yy + ky - 1, sx = xx + kx - 1;
+        if (sy >= 0 && sy < h && sx >= 0 && sx < w)
+          val = static_cast<float>(x[static_cast<long long>(ci) * n * hw + b * hw + sy * w + sx]);
+      }
+      v[j] = __float2bfloat16_rn(val);
+    }
+    *reinterpret_cast<uint4*>(col + m * kp + k0) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// colT[k][m] for k < kc (the weight-gradient GEMM's B operand, K-major along m)
+template <typename T>
+__global__ void k_im2colT(const T* __restrict__ x, int n, int h, int w, int kc, bf16* __restrict__ colT) {
+  const long long hw = static_cast<long long>(h) * w;
+  const long long mtot = static_cast<long long>(n) * hw;
+  const long long total = mtot * kc;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(i / mtot);
+    const long long m = i - k * mtot;
+    const int b = static_cast<int>(m / hw);
+    const int yx = static_cast<int>(m - b * hw);
+    const int yy = yx / w, xx = yx - yy * w;
+    const int ci = k / 9, r = k - ci * 9, ky = r / 3, kx = r - ky * 3;
+    const int sy = yy + ky - 1, sx = xx + kx - 1;
+    float val = 0.0f;
+    if (sy >= 0 && sy < h && sx >= 0 && sx < w)
+      val = static_cast<float>(x[static_cast<long long>(ci) * mtot + b * hw + sy * w + sx]);
+    colT[i] = __float2bfloat16_rn(val);
+  }
+}
+
+// 2x2 max pooling of y[c][b][h][w] (BF16, post-ReLU); ties go to the first of the four in
+// row-major order. Writes p[c][b][h/2][w/2] (chan_major) or p[b][c][h/2][w/2] and its
+// transpose pT[(c, y, x)][b] (row pitch ldt), plus the argmax 0..3.
+__global__ void k_pool(const bf16* __restrict__ y, int c_n, int n, int h, int w, bf16* __restrict__ p,
+                       bf16* __restrict__ pT, long long ldt, int chan_major, uint8_t* __restrict__ am) {
+  const int h2 = h / 2, w2 = w / 2;
+  const long long total = static_cast<long long>(c_n) * n * h2 * w2;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int x2 = static_cast<int>(i % w2);
+    long long r = i / w2;
+    const int y2 = static_cast<int>(r % h2);
+    r /= h2;
+    const int b = static_cast<int>(r % n);
+    const int c = static_cast<int>(r / n);
+    const bf16* src = y + ((static_cast<long long>(c) * n + b) * h + 2 * y2) * w + 2 * x2;
+    const float v0 = __bfloat162float(src[0]), v1 = __bfloat162float(src[1]);
+    const float v2 = __bfloat162float(src[w]), v3 = __bfloat162float(src[w + 1]);
+    int a = 0;
+    float best = v0;
+    if (v1 > best) { best = v1; a = 1; }
+    if (v2 > best) { best = v2; a = 2; }
+    if (v3 > best) { best = v3; a = 3; }
+    am[i] = static_cast<uint8_t>(a);
+    const bf16 bv = __float2bfloat16_rn(best);
+    if (chan_major) {
+      p[i] = bv;
+    } else {
+      const long long f = (static_cast<long long>(c) * h2 + y2) * w2 + x2;
+      p[static_cast<long long>(b) * c_n * h2 * w2 + f] = bv;
+      pT[f * ldt + b] = bv;
+    }
+  }
+}
+
+// Gradient through the pooling and the ReLU: the argmax position of each pooled cell gets
+// dP if its activation is positive. Writes dyT[c][m] (all positions) and, when dy is set,
+// dy[m][ldy] (row-major; columns c < c_n).
+__global__ void k_unpool(const float* __restrict__ dp, int dp_chan_major, const uint8_t* __restrict__ am,
+                         const bf16* __restrict__ y, int c_n, int n, int h, int w, bf16* __restrict__ dyT,
+                         bf16* __restrict__ dy, int ldy) {
+  const int h2 = h / 2, w2 = w / 2;
+  const long long total = static_cast<long long>(c_n) * n * h2 * w2;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    // c fastest, so the row-major dy writes of a warp are contiguous
+    const int c = static_cast<int>(i % c_n);
+    long long r = i / c_n;
+    const int x2 = static_cast<int>(r % w2);
+    r /= w2;
+    const int y2 = static_cast<int>(r % h2);
+    const int b = static_cast<int>(r / h2);
+    const long long pc = ((static_cast<long long>(c) * n + b) * h2 + y2) * w2 + x2;  // channel-major pooled index
+    const float g = dp_chan_major ? dp[pc] : dp[static_cast<long long>(b) * c_n * h2 * w2 +
+                                                 (static_cast<long long>(c) * h2 + y2) * w2 + x2];
+    const int a = am[pc];
+    const long long m00 = (static_cast<long long>(b) * h + 2 * y2) * w + 2 * x2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long m = m00 + (q >> 1) * w + (q & 1);
+      const long long yi = static_cast<long long>(c) * n * h * w + m;
+      const float v = (q == a && __bfloat162float(y[yi]) > 0.0f) ? g : 0.0f;
+      const bf16 bv = __float2bfloat16_rn(v);
+      dyT[yi] = bv;
+      if (dy) dy[m * ldy + c] = bv;
+    }
+  }
+}
+
+// dx[ci][b][y][x] = sum over taps of dcol[m(b, y - ky + 1, x - kx + 1)][ci*9 + ky*3 + kx]
+__global__ void k_col2im(const float* __restrict__ dcol, int ldc, int cin, int n, int h, int w,
+                         float* __restrict__ dx) {
+  const long long hw = static_cast<long long>(h) * w;
+  const long long total = static_cast<long long>(cin) * n * hw;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int xx = static_cast<int>(i % w);
+    long long r = i / w;
+    const int yy = static_cast<int>(r % h);
+    r /= h;
+    const int b = static_cast<int>(r % n);
+    const int ci = static_cast<int>(r / n);
+    float s = 0.0f;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int oy = yy - ky + 1, ox = xx - kx + 1;
+        if (oy < 0 || oy >= h || ox < 0 || ox >= w) continue;
+        const long long m = b * hw + oy * w + ox;
+        s += dcol[m * ldc + ci * 9 + ky * 3 + kx];
+      }
+    }
+    dx[i] = s;
+  }
+}
+
+// fc2, the loss and its gradient, one warp per sample. Forward only when y is null.
+__global__ void k_head(const float* __restrict__ hf, const float* __restrict__ params, int n,
+                       const float* __restrict__ y, float* __restrict__ logits, float* __restrict__ grads,
+                       float* __restrict__ loss, bf16* __restrict__ dh, bf16* __restrict__ dhT, int ldt) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const float* wf2 = params + kOffWf2;
+  const float* hrow = hf + static_cast<long long>(warp) * kHid;
+  float s = 0.0f;
+  for (int j = lane; j < kHid; j += 32) s += hrow[j] * wf2[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  const float z = s + params[kOffBf2];
+  if (lane == 0 && logits) logits[warp] = z;
+  if (!y) return;
+  const float t = y[warp];
+  const float sig = 1.0f / (1.0f + __expf(-z));
+  const float dz = (sig - t) / static_cast<float>(n);
+  if (lane == 0) {
+    // log(1 + e^z) - t z, evaluated stably
+    const float sp = fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)));
+    atomicAdd(loss, (sp - t * z) / static_cast<float>(n));
+    atomicAdd(grads + kOffBf2, dz);
+  }
+  for (int j = lane; j < kHid; j += 32) {
+    const float hv = hrow[j];
+    atomicAdd(grads + kOffWf2 + j, dz * hv);
+    const float g = (hv > 0.0f) ? dz * wf2[j] : 0.0f;
+    atomicAdd(grads + kOffBf1 + j, g);
+    const bf16 bg = __float2bfloat16_rn(g);
+    dh[static_cast<long long>(warp) * kHid + j] = bg;
+    dhT[static_cast<long long>(j) * ldt + warp] = bg;
+  }
+}
+
+// db[c] += sum_m dyT[c][m] (one block per channel)
+__global__ void k_rowsum(const bf16* __restrict__ dyT, long long mtot, float* __restrict__ out) {
+  const int c = blockIdx.x;
+  float s = 0.0f;
+  for (long long m = threadIdx.x; m < mtot; m += blockDim.x) s += __bfloat162float(dyT[c * mtot + m]);
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (threadIdx.x == 0) out[c] += s;
+  }
+}
+
+// dst[r][ldd] (or dst[c][ldd] transposed) = bf16(src[r][cols]), zero-padded to ldd
+__global__ void k_cast_w(const float* __restrict__ src, int rows, int cols, bf16* __restrict__ dst, int ldd,
+                         int transposed, int dst_rows) {
+  const long long total = static_cast<long long>(dst_rows) * ldd;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int a = static_cast<int>(i / ldd), b = static_cast<int>(i - static_cast<long long>(a) * ldd);
+    float v = 0.0f;
+    if (!transposed) {
+      if (a < rows && b < cols) v = src[static_cast<long long>(a) * cols + b];
+    } else {
+      if (b < rows && a < cols) v = src[static_cast<long long>(b) * cols + a];
+    }
+    dst[i] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                       float* __restrict__ m2, long long np, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.0f - b1) * gi;
+    const float v = b2 * m2[i] + (1.0f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    p[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
+  }
+}
+
+// One block per snippet: 64 x 256 plane cells around (row, col), standardised with the FP64
+// mean and population std of the present cells (std 0 -> 1); missing cells are 0.
+__global__ void __launch_bounds__(256) k_snippets(const float* __restrict__ plane, long long ld, int ndm,
+                                                  long long ncols, const int32_t* __restrict__ rows,
+                                                  const int64_t* __restrict__ cols, int n, float* __restrict__ out) {
+  const int s = blockIdx.x;
+  if (s >= n) return;
+  const int r0 = rows[s] - 32;
+  const long long c0 = cols[s] - 128;
+  double s1 = 0.0, s2 = 0.0;
+  long long cnt = 0;
+  for (int i = threadIdx.x; i < kH * kW; i += blockDim.x) {
+    const int r = r0 + i / kW;
+    const long long c = c0 + (i % kW);
+    if (r >= 0 && r < ndm && c >= 0 && c < ncols) {
+      const double v = plane[static_cast<long long>(r) * ld + c];
+      s1 += v;
+      s2 += v * v;
+      ++cnt;
+    }
+  }
+  __shared__ double r1[8], r2[8];
+  __shared__ long long rc[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+    s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+    cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = s1;
+    r2[threadIdx.x >> 5] = s2;
+    rc[threadIdx.x >> 5] = cnt;
+  }
+  __syncthreads();
+  s1 = s2 = 0.0;
+  cnt = 0;
+  for (int k = 0; k < 8; ++k) {
+    s1 += r1[k];
+    s2 += r2[k];
+    cnt += rc[k];
+  }
+  const double mu = cnt ? s1 / cnt : 0.0;
+  const double var = cnt ? s2 / cnt - mu * mu : 0.0;
+  const double sd = var > 0.0 ? sqrt(var) : 1.0;
+  float* o = out + static_cast<long long>(s) * kH * kW;
+  for (int i = threadIdx.x; i < kH * kW; i += blockDim.x) {
+    const int r = r0 + i / kW;
+    const long long c = c0 + (i % kW);
+    float v = 0.0f;
+    if (r >= 0 && r < ndm && c >= 0 && c < ncols)
+      v = static_cast<float>((plane[static_cast<long long>(r) * ld + c] - mu) / sd);
+    o[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 2-D K-major BF16 operand: `rows` rows of `kext` valid elements, `pitch` elements apart;
+// boxes of 64 x box_rows, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* m, const void* base, long long kext, long long rows, long long pitch, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15u) || (pitch * 2) % 16 != 0 || kext < 1 || rows < 1)
+    return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(kext), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch * 2)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_gemm_bn(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int ktiles, int splits,
+                           const Epi& epi, uint32_t* err, cudaStream_t s) {
+  const int per = (ktiles + splits - 1) / splits;
+  const int nz = (ktiles + per - 1) / per;
+  const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, nz);
+  k_gemm<BN><<<grid, 128, smem, s>>>(ma, mb, M, N, ktiles, per, epi, err);
+  return cudaGetLastError();
+}
+
+// C[M][N] = A[M][K] . B[N][K]^T, A and B BF16 K-major with pitches lda / ldb (elements).
+// splits > 1 splits K over CTAs (epi.atomic must be set, output pre-zeroed).
+int gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int N, long long K, const Epi& epi,
+         int splits, uint32_t* err, cudaStream_t s, int64_t* launches) {
+  const int BN = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, K, M, lda, kBM) || !make_map(&mb, B, K, N, ldb, BN)) return SND_ERR_UNSUPPORTED;
+  const int ktiles = static_cast<int>((K + kBK - 1) / kBK);
+  splits = std::max(1, std::min(splits, ktiles));
+  cudaError_t e;
+  if (BN == 32) {
+    e = launch_gemm_bn<32>(ma, mb, M, N, ktiles, splits, epi, err, s);
+  } else if (BN == 64) {
+    e = launch_gemm_bn<64>(ma, mb, M, N, ktiles, splits, epi, err, s);
+  } else {
+    e = launch_gemm_bn<128>(ma, mb, M, N, ktiles, splits, epi, err, s);
+  }
+  if (launches) *launches += 1;
+  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
+int grid_for(long long total) { return static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 32)); }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Sifter {
+  int bm = 0;        // batch capacity (multiple of 64)
+  int training = 0;
+  uint64_t seed = 0;
+  std::vector<float> init;
+  size_t ws_bytes = 0;
+  char* ws = nullptr;
+  bool bound = false;
+  int sticky = 0;
+  int64_t step = 0;
+  int64_t launches = 0;
+  cudaStream_t last = nullptr;
+  struct {
+    size_t params, grads, m1, m2, err, loss, wb[3], wT[3], wf1b, wf1T, col[3], yT[3], p[3], am[3], p3, p3T, hf,
+        logits, dh, dhT, dp3, dy[3], dyT[3], colT[3], dcol[3], dp[3];
+  } o{};
+};
+
+template <typename T>
+T* at(const Sifter& f, size_t off) {
+  return reinterpret_cast<T*>(f.ws + off);
+}
+
+void layout(Sifter& f) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t a = o;
+    o = align256(o + bytes);
+    return a;
+  };
+  const long long B = f.bm;
+  const size_t P = static_cast<size_t>(kNumParams);
+  f.o.params = take(4 * P);
+  f.o.grads = take(4 * P);
+  f.o.m1 = take(f.training ? 4 * P : 0);
+  f.o.m2 = take(f.training ? 4 * P : 0);
+  f.o.err = take(16);
+  f.o.loss = take(16);
+  for (int l = 0; l < 3; ++l) {
+    const ConvL& c = kConv[l];
+    const long long m = B * c.h * c.w;
+    f.o.wb[l] = take(2ull * c.cout * c.kp);
+    f.o.wT[l] = take(2ull * c.kc * 64);
+    f.o.col[l] = take(2ull * m * c.kp);
+    f.o.yT[l] = take(2ull * c.cout * m);
+    f.o.p[l] = take(2ull * c.cout * m / 4);
+    f.o.am[l] = take(1ull * c.cout * m / 4);
+    if (f.training) {
+      f.o.dy[l] = take(l > 0 ? 2ull * m * 64 : 0);
+      f.o.dyT[l] = take(2ull * c.cout * m);
+      f.o.colT[l] = take(2ull * c.kc * m);
+      f.o.dcol[l] = take(l > 0 ? 4ull * m * c.kc : 0);
+      f.o.dp[l] = take(l < 2 ? 4ull * c.cout * m / 4 : 0);
+    }
+  }
+  f.o.wf1b = take(2ull * kHid * kFeat);
+  f.o.wf1T = take(f.training ? 2ull * kFeat * kHid : 0);
+  f.o.p3 = take(2ull * B * kFeat);
+  f.o.p3T = take(2ull * B * kFeat);
+  f.o.hf = take(4ull * B * kHid);
+  f.o.logits = take(4ull * B);
+  if (f.training) {
+    f.o.dh = take(2ull * B * kHid);
+    f.o.dhT = take(2ull * B * kHid);
+    f.o.dp3 = take(4ull * B * kFeat);
+  }
+  f.ws_bytes = o;
+}
+
+// counter-based uniform in [-1, 1): splitmix64 of (seed, index)
+float uniform_pm1(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return static_cast<float>(static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+}
+
+int fail(Sifter& f, int code) {
+  if (!f.sticky) f.sticky = code;
+  return code;
+}
+
+// BF16 copies of the weights (and the transposes the input-gradient GEMMs read)
+cudaError_t prep_weights(Sifter& f, cudaStream_t s) {
+  const float* P = at<float>(f, f.o.params);
+  for (int l = 0; l < 3; ++l) {
+    const ConvL& c = kConv[l];
+    k_cast_w<<<grid_for(1LL * c.cout * c.kp), 256, 0, s>>>(P + kOffW[l], c.cout, c.kc, at<bf16>(f, f.o.wb[l]), c.kp, 0,
+                                                         c.cout);
+    f.launches++;
+    if (f.training && l > 0) {
+      k_cast_w<<<grid_for(1LL * c.kc * 64), 256, 0, s>>>(P + kOffW[l], c.cout, c.kc, at<bf16>(f, f.o.wT[l]), 64, 1,
+                                                       c.kc);
+      f.launches++;
+    }
+  }
+  k_cast_w<<<grid_for(1LL * kHid * kFeat), 256, 0, s>>>(P + kOffWf1, kHid, kFeat, at<bf16>(f, f.o.wf1b), kFeat, 0,
+                                                        kHid);
+  f.launches++;
+  if (f.training) {
+    k_cast_w<<<grid_for(1LL * kHid * kFeat), 256, 0, s>>>(P + kOffWf1, kHid, kFeat, at<bf16>(f, f.o.wf1T), kHid, 1,
+                                                          kFeat);
+    f.launches++;
+  }
+  return cudaGetLastError();
+}
+
+// forward pass of n snippets x[n][64][256] (FP32) into the hidden layer and the logits
+int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
+  uint32_t* err = at<uint32_t>(f, f.o.err);
+  const float* P = at<float>(f, f.o.params);
+  for (int l = 0; l < 3; ++l) {
+    const ConvL& c = kConv[l];
+    const long long m = 1LL * n * c.h * c.w;
+    bf16* col = at<bf16>(f, f.o.col[l]);
+    if (l == 0) {
+      k_im2col<float><<<grid_for(m * c.kp / 8), 256, 0, s>>>(x, n, c.h, c.w, c.kc, c.kp, col);
+    } else {
+      k_im2col<bf16><<<grid_for(m * c.kp / 8), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, c.kp, col);
+    }
+    f.launches++;
+    Epi e{P + kOffB[l], 1, at<bf16>(f, f.o.yT[l]), 1, 1, 0, m};
+    int rc = gemm(col, c.kp, at<bf16>(f, f.o.wb[l]), c.kp, static_cast<int>(m), c.cout, c.kp, e, 1, err, s, &f.launches);
+    if (rc) return rc;
+    const long long pooled = m / 4 * c.cout;
+    k_pool<<<grid_for(pooled), 256, 0, s>>>(at<bf16>(f, f.o.yT[l]), c.cout, n, c.h, c.w,
+                                             l < 2 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3),
+                                             at<bf16>(f, f.o.p3T), f.bm, l < 2 ? 1 : 0, at<uint8_t>(f, f.o.am[l]));
+    f.launches++;
+  }
+  Epi e{P + kOffBf1, 1, at<float>(f, f.o.hf), 0, 0, 0, kHid};
+  return gemm(at<bf16>(f, f.o.p3), kFeat, at<bf16>(f, f.o.wf1b), kFeat, n, kHid, kFeat, e, 1, err, s, &f.launches);
+}
+
+// gradients of the mean loss over n snippets into the grads vector (zeroed here)
+int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
+  uint32_t* err = at<uint32_t>(f, f.o.err);
+  float* G = at<float>(f, f.o.grads);
+  const float* P = at<float>(f, f.o.params);
+  if (cudaMemsetAsync(G, 0, 4ull * kNumParams, s) != cudaSuccess ||
+      cudaMemsetAsync(at<float>(f, f.o.loss), 0, 4, s) != cudaSuccess)
+    return SND_ERR_CUDA;
+  k_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(at<float>(f, f.o.hf), P, n, y, at<float>(f, f.o.logits), G,
+                                               at<float>(f, f.o.loss), at<bf16>(f, f.o.dh), at<bf16>(f, f.o.dhT), f.bm);
+  f.launches++;
+  // fc1: dWf1 = dH^T . F ; dF = dH . Wf1
+  {
+    Epi e{nullptr, 0, G + kOffWf1, 0, 0, 0, kFeat};
+    // K = n valid columns of rows pitched by the batch capacity (the rest reads as zero)
+    int rc = gemm(at<bf16>(f, f.o.dhT), f.bm, at<bf16>(f, f.o.p3T), f.bm, kHid, kFeat, n, e, 1, err, s, &f.launches);
+    if (rc) return rc;
+    Epi e2{nullptr, 0, at<float>(f, f.o.dp3), 0, 0, 0, kFeat};
+    rc = gemm(at<bf16>(f, f.o.dh), kHid, at<bf16>(f, f.o.wf1T), kHid, n, kFeat, kHid, e2, 1, err, s, &f.launches);
+    if (rc) return rc;
+  }
+  for (int l = 2; l >= 0; --l) {
+    const ConvL& c = kConv[l];
+    const long long m = 1LL * n * c.h * c.w;
+    const float* dp = (l == 2) ? at<float>(f, f.o.dp3) : at<float>(f, f.o.dp[l]);
+    bf16* dyT = at<bf16>(f, f.o.dyT[l]);
+    bf16* dy = l > 0 ? at<bf16>(f, f.o.dy[l]) : nullptr;
+    k_unpool<<<grid_for(m / 4 * c.cout), 256, 0, s>>>(dp, l < 2 ? 1 : 0, at<uint8_t>(f, f.o.am[l]),
+                                                       at<bf16>(f, f.o.yT[l]), c.cout, n, c.h, c.w, dyT, dy, 64);
+    f.launches++;
+    // weight and bias gradients
+    bf16* colT = at<bf16>(f, f.o.colT[l]);
+    if (l == 0) {
+      k_im2colT<float><<<grid_for(m * c.kc), 256, 0, s>>>(x, n, c.h, c.w, c.kc, colT);
+    } else {
+      k_im2colT<bf16><<<grid_for(m * c.kc), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, colT);
+    }
+    f.launches++;
+    const int ktiles = static_cast<int>((m + kBK - 1) / kBK);
+    const int ntile = (c.kc + (c.kc <= 32 ? 32 : 64) - 1) / (c.kc <= 32 ? 32 : 64);
+    const int splits = std::max(1, std::min(ktiles, 2 * 152 / std::max(1, ntile)));
+    Epi ew{nullptr, 0, G + kOffW[l], 0, 0, 1, c.kc};
+    int rc = gemm(dyT, m, colT, m, c.cout, c.kc, m, ew, splits, err, s, &f.launches);
+    if (rc) return rc;
+    k_rowsum<<<c.cout, 256, 0, s>>>(dyT, m, G + kOffB[l]);
+    f.launches++;
+    if (l == 0) break;
+    // input gradient through the convolution, then back to the previous pooled map
+    Epi ex{nullptr, 0, at<float>(f, f.o.dcol[l]), 0, 0, 0, c.kc};
+    rc = gemm(dy, 64, at<bf16>(f, f.o.wT[l]), 64, static_cast<int>(m), c.kc, 64, ex, 1, err, s, &f.launches);
+    if (rc) return rc;
+    k_col2im<<<grid_for(m * c.cin), 256, 0, s>>>(at<float>(f, f.o.dcol[l]), c.kc, c.cin, n, c.h, c.w,
+                                                  at<float>(f, f.o.dp[l - 1]));
+    f.launches++;
+  }
+  return cudaGetLastError() == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
+int check_run(Sifter& f, const void* x, int n) {
+  if (f.sticky) return f.sticky;
+  if (!f.bound) return SND_ERR_STATE;
+  if (!x || n < 1 || n > f.bm) return SND_ERR_ARG;
+  return SND_OK;
+}
+
+int read_err(Sifter& f, cudaStream_t s) {
+  uint32_t e = 0;
+  if (cudaMemcpyAsync(&e, at<uint32_t>(f, f.o.err), 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(f, SND_ERR_CUDA);
+  return e ? fail(f, SND_ERR_TIMEOUT) : SND_OK;
+}
+
+}  // namespace
+
+extern "C" int snd_sifter_create(int32_t max_batch, int32_t training, uint64_t seed, snd_sifter_t* out) {
+  if (out) *out = nullptr;
+  if (!out || max_batch < 1 || max_batch > (1 << 16)) return SND_ERR_ARG;
+  Sifter* f = new (std::nothrow) Sifter();
+  if (!f) return SND_ERR_NOMEM;
+  f->bm = (max_batch + 63) / 64 * 64;
+  f->training = training ? 1 : 0;
+  f->seed = seed;
+  try {
+    f->init.assign(static_cast<size_t>(kNumParams), 0.0f);
+    auto fill = [&](long long off, long long count, int fan_in) {
+      const float bound = std::sqrt(6.0f / static_cast<float>(fan_in));
+      for (long long i = 0; i < count; ++i) f->init[off + i] = bound * uniform_pm1(seed, static_cast<uint64_t>(off + i));
+    };
+    for (int l = 0; l < 3; ++l) fill(kOffW[l], 1LL * kConv[l].cout * kConv[l].kc, kConv[l].kc);
+    fill(kOffWf1, 1LL * kHid * kFeat, kFeat);
+    fill(kOffWf2, kHid, kHid);
+  } catch (...) {
+    delete f;
+    return SND_ERR_NOMEM;
+  }
+  layout(*f);
+  *out = reinterpret_cast<snd_sifter_t>(f);
+  return SND_OK;
+}
+
+extern "C" int64_t snd_sifter_num_params(void) { return kNumParams; }
+
+extern "C" size_t snd_sifter_workspace_size(snd_sifter_t h) {
+  return h ? reinterpret_cast<Sifter*>(h)->ws_bytes : 0;
+}
+
+extern "C" int snd_sifter_bind_workspace(snd_sifter_t h, void* d_ws, size_t bytes, void* stream) {
+  if (!h) return SND_ERR_ARG;
+  Sifter& f = *reinterpret_cast<Sifter*>(h);
+  if (!d_ws || bytes < f.ws_bytes || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return SND_ERR_WORKSPACE;
+  if (!encode_fn()) return SND_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  f.ws = static_cast<char*>(d_ws);
+  if (cudaMemsetAsync(d_ws, 0, f.ws_bytes, s) != cudaSuccess ||
+      cudaMemcpyAsync(f.ws + f.o.params, f.init.data(), 4ull * kNumParams, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      prep_weights(f, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return SND_ERR_CUDA;
+  f.bound = true;
+  f.sticky = 0;
+  f.step = 0;
+  f.last = s;
+  return SND_OK;
+}
+
+extern "C" int snd_sifter_set_params(snd_sifter_t h, const float* host_params, int64_t n, void* stream) {
+  if (!h || !host_params || n != kNumParams) return SND_ERR_ARG;
+  Sifter& f = *reinterpret_cast<Sifter*>(h);
+  if (!f.bound) return SND_ERR_STATE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(f.ws + f.o.params, host_params, 4ull * kNumParams, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      prep_weights(f, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(f, SND_ERR_CUDA);
+  if (f.training && (cudaMemsetAsync(f.ws + f.o.m1, 0, 4ull * kNumParams, s) != cudaSuccess ||
+                     cudaMemsetAsync(f.ws + f.o.m2, 0, 4ull * kNumParams, s) != cudaSuccess))
+    return fail(f, SND_ERR_CUDA);
+  f.step = 0;
+  return SND_OK;
+}
+
+extern "C" int snd_sifter_get_params(snd_sifter_t h, float* host_params, int64_t n) {
+  if (!h || !host_params || n != kNumParams) return SND_ERR_ARG;
+  Sifter& f = *reinterpret_cast<Sifter*>(h);
+  if (!f.bound) return SND_ERR_STATE;
+  if (cudaStreamSynchronize(f.last) != cudaSuccess ||
+      cudaMemcpy(host_params, f.ws + f.o.params, 4ull * kNumParams, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(f, SND_ERR_CUDA);
+  return SND_OK;
+}
+
+extern "C" int snd_sifter_forward(snd_sifter_t h, const float* d_x, int32_t n, float* d_logits, void* stream) {
+  if (!h || !d_logits) return SND_ERR_ARG;
+  Sifter& f = *reinterpret_cast<Sifter*>(h);
+  int rc = check_run(f, d_x, n);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = forward(f, d_x, n, s);
+  if (rc) return fail(f, rc);
+  k_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(at<float>(f, f.o.hf), at<float>(f, f.o.params), n, nullptr, d_logits,
+                                               nullptr, nullptr, nullptr, nullptr, f.bm);
+  f.launches++;
+  f.last = s;
+  return cudaGetLastError() == cudaSuccess ? SND_OK : fail(f, SND_ERR_CUDA);
+}
+
+extern "C" int snd_sifter_gradients(snd_sifter_t h, const float* d_x, const float* d_y, int32_t n, float* d_grads,
+                                    float* d_loss, void* stream) {
+  if (!h || !d_y) return SND_ERR_ARG;
+  Sifter& f = *reinterpret_cast<Sifter*>(h);
+  if (!f.training) return SND_ERR_STATE;
+  int rc = check_run(f, d_x, n);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = forward(f, d_x, n, s);
+  if (!rc) rc = backward(f, d_x, d_y, n, s);
+  if (rc) return fail(f, rc);
+  if (d_grads && cudaMemcpyAsync(d_grads, f.ws + f.o.grads, 4ull * kNumParams, cudaMemcpyDeviceToDevice, s) !=
+                     cudaSuccess)
+    return fail(f, SND_ERR_CUDA);
+  if (d_loss && cudaMemcpyAsync(d_loss, f.ws + f.o.loss, 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return fail(f, SND_ERR_CUDA);
+  f.last = s;
+  return read_err(f, s);
+}
+
+extern "C" int snd_sifter_train_step(snd_sifter_t h, const float* d_x, const float* d_y, int32_t n, float lr,
+                                     float* d_loss, void* stream) {
+  if (!h || !d_y || !(lr > 0.0f)) return SND_ERR_ARG;
+  Sifter& f = *reinterpret_cast<Sifter*>(h);
+  if (!f.training) return SND_ERR_STATE;
+  int rc = check_run(f, d_x, n);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = forward(f, d_x, n, s);
+  if (!rc) rc = backward(f, d_x, d_y, n, s);
+  if (rc) return fail(f, rc);
+  ++f.step;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - std::pow(b1, static_cast<float>(f.step));
+  const float c2 = 1.0f - std::pow(b2, static_cast<float>(f.step));
+  k_adam<<<grid_for(kNumParams), 256, 0, s>>>(at<float>(f, f.o.params), at<float>(f, f.o.grads), at<float>(f, f.o.m1),
+                                              at<float>(f, f.o.m2), kNumParams, lr, b1, b2, 1e-8f, c1, c2);
+  f.launches++;
+  if (prep_weights(f, s) != cudaSuccess) return fail(f, SND_ERR_CUDA);
+  if (d_loss && cudaMemcpyAsync(d_loss, f.ws + f.o.loss, 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return fail(f, SND_ERR_CUDA);
+  f.last = s;
+  return cudaGetLastError() == cudaSuccess ? SND_OK : fail(f, SND_ERR_CUDA);
+}
+
+extern "C" int snd_sifter_status(snd_sifter_t h) {
+  if (!h) return SND_ERR_ARG;
+  Sifter& f = *reinterpret_cast<Sifter*>(h);
+  if (!f.bound) return SND_ERR_STATE;
+  if (f.sticky) return f.sticky;
+  return read_err(f, f.last);
+}
+
+extern "C" int64_t snd_sifter_launches(snd_sifter_t h) { return h ? reinterpret_cast<Sifter*>(h)->launches : 0; }
+
+extern "C" void snd_sifter_destroy(snd_sifter_t h) { delete reinterpret_cast<Sifter*>(h); }
+
+extern "C" int snd_snippets(const float* d_plane, int64_t ld, int32_t ndm, int64_t ncols, const int32_t* d_rows,
+                            const int64_t* d_cols, int32_t n, float* d_out, void* stream) {
+  if (!d_plane || !d_rows || !d_cols || !d_out || n < 0 || ndm < 1 || ncols < 1 || ld < ncols) return SND_ERR_ARG;
+  if (n == 0) return SND_OK;
+  k_snippets<<<n, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_plane, ld, ndm, ncols, d_rows, d_cols, n, d_out);
+  return cudaGetLastError() == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
+extern "C" int snd_gemm_bf16(const void* d_a, int64_t lda, const void* d_b, int64_t ldb, int32_t m, int32_t n,
+                             int64_t k, float* d_c, int64_t ldc, int32_t splits, uint32_t* d_err, void* stream) {
+  if (!d_a || !d_b || !d_c || !d_err || m < 1 || n < 1 || k < 1 || lda < k || ldb < k || ldc < n || splits < 1)
+    return SND_ERR_ARG;
+  Epi e{nullptr, 0, d_c, 0, 0, splits > 1 ? 1 : 0, ldc};
+  return gemm(static_cast<const bf16*>(d_a), lda, static_cast<const bf16*>(d_b), ldb, m, n, k, e, splits, d_err,
+              static_cast<cudaStream_t>(stream), nullptr);
+}
