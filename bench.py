@@ -270,6 +270,55 @@ def zfloat_rate(g, args, dev, dchunks, freqs, dms):
     return out
 
 
+SIFTER_FLOPS = 2 * (16384 * 16 * 9 + 4096 * 32 * 144 + 1024 * 64 * 288 + 16384 * 128)  # per snippet, forward
+
+
+def sifter_rate(g, args, dev):
+    """Learned sifter: BF16 tensor-core inference at batch 4096 and training steps at batch
+    256 (CUDA events), and a short train/evaluate run on pipeline-made snippets comparing it
+    with the plain S/N >= 7 sifter at equal false-alarm rate."""
+    import torch
+    from paper_2606_15361_gb300 import sifter_data as sd
+    gen = torch.Generator(device=dev).manual_seed(7)
+    xb = torch.randn((4096, 64, 256), generator=gen, device=dev)
+    inf = g.Sifter(max_batch=4096, training=False, seed=1, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        inf.forward(xb)
+    ev0.record()
+    for _ in range(10):
+        inf.forward(xb)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    inf_ms = ev0.elapsed_time(ev1) / 10
+    tr_sf = g.Sifter(max_batch=256, training=True, seed=1, device=dev)
+    yb = (torch.rand(256, generator=gen, device=dev) < 0.5).float()
+    for _ in range(3):
+        tr_sf.train_step(xb[:256], yb, 1e-4)
+    ev0.record()
+    for _ in range(20):
+        tr_sf.train_step(xb[:256], yb, 1e-4)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    step_ms = ev0.elapsed_time(ev1) / 20
+    del inf, tr_sf
+    tr = sd.concat([sd.make_run(3000 + i, n_burst=96, device=dev) for i in range(30)])
+    te = sd.concat([sd.make_run(93000 + i, n_burst=96, device=dev) for i in range(10)])
+    sf = g.Sifter(max_batch=256, training=True, seed=2, device=dev)
+    sd.train(sf, tr, epochs=5, batch=256, lr=5e-4)
+    cmp = sd.compare(sd.logits(sf, te.x, 256), te)
+    return {"infer_batch": 4096, "infer_ms_per_batch": round(inf_ms, 3),
+            "infer_snippets_per_s": round(4096 / (inf_ms / 1e3), 1),
+            "infer_tflops": round(SIFTER_FLOPS * 4096 / (inf_ms / 1e3) / 1e12, 2),
+            "train_batch": 256, "train_ms_per_step": round(step_ms, 3),
+            "train_snippets_per_s": round(256 / (step_ms / 1e3), 1),
+            "quick_eval": {"train_snippets": int(len(tr.label)), "test_snippets": int(len(te.label)),
+                           "far_plain": round(cmp["far_plain"], 4), "miss_plain": round(cmp["miss_plain"], 4),
+                           "far_learned": round(cmp["far_learned"], 4), "miss_learned": round(cmp["miss_learned"], 4)},
+            "note": "quick_eval: 30 synthetic beam runs, 5 epochs; the full 200k-snippet run is "
+                    "paper_2606_15361_gb300/sifter_train.py"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2606_15361_gb300 as g
@@ -346,6 +395,7 @@ def run_gpu(args, rank, world, local_rank):
 
     mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if rank == 0 else None
     zf = zfloat_rate(g, args, dev, dchunks, freqs, dms) if rank == 0 else None
+    sft = sifter_rate(g, args, dev) if rank == 0 and not args.no_sifter else None
 
     per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
     ms_dev, ms_e2e = reduce_max([ms_dev, ms_e2e], dist, dev)
@@ -400,6 +450,7 @@ def run_gpu(args, rank, world, local_rank):
         "realtime_beams_per_mode": realtime_beams,
         "multirate": mr,
         "zfloat_precision_study": zf,
+        "learned_sifter": sft,
         "candidates_in_timed_steps": ncands,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -429,6 +480,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sifter", action="store_true", help="skip the learned-sifter measurements")
     ap.add_argument("--drive", choices=[m for m, _ in MODES], help="profiling driver: one plan, no timing")
     ap.add_argument("--chunks", type=int, default=3)
     ap.add_argument("--branching", type=int, default=BRANCHING)
