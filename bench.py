@@ -319,6 +319,73 @@ def sifter_rate(g, args, dev):
                     "paper_2606_15361_gb300/sifter_train.py"}
 
 
+def multibeam_rate(g, args, dev, nbeams=48, seed=11):
+    """Ragged beams in one step: 48 beams of 1024 channels, each with its own DM grid
+    (512-4096 trials to a max DM of 500-3000) and chunk length (4096-32768 samples), float
+    mode, branching from the autotuner. Times one step of all beams run plan by plan, as a
+    batch (grouped tree launches), and as a batch replayed through a CUDA graph."""
+    import torch
+    from paper_2606_15361_gb300 import autotune
+    rng = np.random.default_rng(seed)
+    f = synth.channel_freqs(1024)
+    tune = autotune.autotune(f, synth.NC_DT, synth.dm_grid(2048, 2000.0), g.MODE_FLOAT, 16384,
+                             branching=(2, 4, 8, 16), cluster=(4,), steps=2, device=dev)
+    B = tune["branching"]
+    cfgs = [(int(rng.integers(512, 4097)), float(rng.uniform(500.0, 3000.0)), int(rng.integers(4, 33)) * 1024)
+            for _ in range(nbeams)]
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    data = [[torch.randn((ch, 1024), generator=gen, device=dev).mul_(16).add_(128).round_().clamp_(0, 255)
+             .to(torch.uint8) for _ in range(2)] for _, _, ch in cfgs]
+
+    def make():
+        return [g.Plan(f, synth.NC_DT, synth.dm_grid(nd, dmx), B, g.MODE_FLOAT,
+                       g.options(g.MODE_FLOAT, max_chunk=ch), device=dev) for nd, dmx, ch in cfgs]
+
+    fill = max((p_d + ch - 1) // ch for p_d, ch in
+               ((int(2.0 + 4.148808e3 * dmx * (f.min() ** -2 - f.max() ** -2) / synth.NC_DT), ch) for _, dmx, ch in cfgs))
+    steps = max(2, min(args.steps, 5))
+    out = {"beams": nbeams, "autotune": {"branching": B, "trials": [(t["branching"], round(t["ms_per_chunk"], 3))
+                                                                  for t in tune["trials"]]}}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name in ("per_beam", "batch", "batch_graph"):
+        plans = make()
+        batch = g.Batch(plans, graph=(name == "batch_graph")) if name != "per_beam" else None
+
+        def step(k):
+            if batch is None:
+                for i, p in enumerate(plans):
+                    p.execute(data[i][k % 2])
+            else:
+                batch.execute([data[i][k % 2] for i in range(nbeams)])
+
+        for k in range(fill + 2):
+            step(k)
+        for p in plans:
+            p.candidates(check=False)
+        torch.cuda.synchronize(dev)
+        launches0 = sum(p.stats().kernel_launches for p in plans)
+        ev0.record()
+        for k in range(steps):
+            step(k)
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / steps
+        launches = (sum(p.stats().kernel_launches for p in plans) - launches0) // steps
+        out[name] = {"ms_per_step": round(ms, 3), "kernels_per_step": int(launches)}
+        del batch, plans
+        torch.cuda.empty_cache()
+    units = sum(nd * ch for nd, _, ch in cfgs)
+    best = min(out[k]["ms_per_step"] for k in ("batch", "batch_graph"))
+    shortest = min(ch for _, _, ch in cfgs) * synth.NC_DT * 1e3
+    out.update({"dm_samples_per_step": units, "gdm_samples_per_s_batch_graph":
+                round(units / (out["batch_graph"]["ms_per_step"] / 1e3) / 1e9, 2),
+                "shortest_chunk_ms": round(shortest, 1),
+                "realtime_margin": round(shortest / best, 1),
+                "note": "all beams advance one chunk per step; the step must finish within the shortest "
+                        "chunk's duration for every beam to keep up; realtime_margin = that duration / step time"})
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2606_15361_gb300 as g
@@ -396,6 +463,7 @@ def run_gpu(args, rank, world, local_rank):
     mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if rank == 0 else None
     zf = zfloat_rate(g, args, dev, dchunks, freqs, dms) if rank == 0 else None
     sft = sifter_rate(g, args, dev) if rank == 0 and not args.no_sifter else None
+    mb = multibeam_rate(g, args, dev) if rank == 0 and not args.no_multibeam else None
 
     per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
     ms_dev, ms_e2e = reduce_max([ms_dev, ms_e2e], dist, dev)
@@ -451,6 +519,7 @@ def run_gpu(args, rank, world, local_rank):
         "multirate": mr,
         "zfloat_precision_study": zf,
         "learned_sifter": sft,
+        "multibeam": mb,
         "candidates_in_timed_steps": ncands,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -481,6 +550,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sifter", action="store_true", help="skip the learned-sifter measurements")
+    ap.add_argument("--no-multibeam", action="store_true", help="skip the 48-beam batch measurements")
     ap.add_argument("--drive", choices=[m for m, _ in MODES], help="profiling driver: one plan, no timing")
     ap.add_argument("--chunks", type=int, default=3)
     ap.add_argument("--branching", type=int, default=BRANCHING)

@@ -274,6 +274,25 @@ void snd_multirate_destroy(snd_multirate_t mr);
 const char* snd_error_string(int status);
 
 /*
+ * Many beams per step. A batch groups bound plans (one per beam; any mix of DM grids, chunk
+ * lengths and options; the batch does not own them) and advances every beam by one chunk
+ * per call, exactly as one snd_execute per beam would (same planes, same candidates; read
+ * them with snd_candidates on each plan). Trees of beams whose plans share a kernel
+ * instantiation run in one launch. With graphs enabled the step is captured on `stream` and
+ * replayed as one CUDA graph, updated in place from step to step.
+ *   d_chunks[i]  device uint8[nsamp[i]][nchan_i] chunk of beam i (host array of pointers)
+ *   nsamp[i]     1..max_chunk of plan i
+ * Plans with per-stage profiling enabled are rejected (SND_ERR_STATE); errors as snd_execute.
+ */
+typedef struct snd_batch_s* snd_batch_t;
+int snd_batch_create(const snd_plan_t* plans, int32_t nplans, snd_batch_t* out);
+int snd_batch_set_graph(snd_batch_t batch, int32_t enable);
+int snd_batch_execute(snd_batch_t batch, const uint8_t* const* d_chunks, const int32_t* nsamp, void* stream);
+/* Graph instantiations and in-place updates so far. */
+int snd_batch_graph_stats(snd_batch_t batch, int64_t* instantiations, int64_t* updates);
+void snd_batch_destroy(snd_batch_t batch);
+
+/*
  * Learned candidate sifter (the paper leaves a learned classifier to future work,
  * "Discussion"; the plain threshold-and-clustering sifter above stays the default and the
  * reference). A CNN classifies 64-DM x 256-sample snippets of the float plane around

@@ -71,7 +71,8 @@ EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", 
            "snd_sifter_create", "snd_sifter_num_params", "snd_sifter_workspace_size", "snd_sifter_bind_workspace",
            "snd_sifter_set_params", "snd_sifter_get_params", "snd_sifter_forward", "snd_sifter_gradients",
            "snd_sifter_train_step", "snd_sifter_status", "snd_sifter_launches", "snd_sifter_destroy", "snd_snippets",
-           "snd_gemm_bf16")
+           "snd_gemm_bf16", "snd_batch_create", "snd_batch_set_graph", "snd_batch_execute", "snd_batch_graph_stats",
+           "snd_batch_destroy")
 STAGES = ("encode", "tree", "mf", "candidates")
 
 
@@ -132,6 +133,14 @@ def _load():
     lib.snd_sifter_destroy.restype = None
     lib.snd_snippets.argtypes = [V, I64, I32, I64, V, V, I32, V, V]
     lib.snd_gemm_bf16.argtypes = [V, I64, V, I64, I32, I32, I64, V, I64, I32, V, V]
+    lib.snd_batch_create.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(P)]
+    lib.snd_batch_set_graph.argtypes = [P, I32]
+    lib.snd_batch_execute.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(I32), V]
+    lib.snd_batch_graph_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.snd_batch_destroy.argtypes = [P]
+    lib.snd_batch_destroy.restype = None
+    for name in ("snd_batch_create", "snd_batch_set_graph", "snd_batch_execute", "snd_batch_graph_stats"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("snd_sifter_create", "snd_sifter_bind_workspace", "snd_sifter_set_params", "snd_sifter_get_params",
                  "snd_sifter_forward", "snd_sifter_gradients", "snd_sifter_train_step", "snd_sifter_status",
                  "snd_snippets", "snd_gemm_bf16"):
@@ -473,3 +482,36 @@ def gemm_bf16(a, b, k=None, splits=1, out=None, stream=None):
     _check(lib.snd_gemm_bf16(_ptr(a), a.stride(0), _ptr(b), b.stride(0), m, n, k, _ptr(out), out.stride(0),
                              int(splits), _ptr(err), _stream_ptr(stream)), "snd_gemm_bf16")
     return out, err
+
+
+class Batch:
+    """Advance several bound plans (beams) by one chunk each per call (snd_batch_*)."""
+
+    def __init__(self, plans, graph: bool = False):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib.snd_batch_create(arr, len(self.plans), ctypes.byref(h)), "snd_batch_create")
+        self.handle = h
+        self.set_graph(graph)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.snd_batch_destroy(h)
+            self.handle = None
+
+    def set_graph(self, enable: bool):
+        _check(lib.snd_batch_set_graph(self.handle, int(bool(enable))), "snd_batch_set_graph")
+
+    def execute(self, chunks, stream=None):
+        """chunks: one contiguous device uint8 tensor [nsamp_i][nchan_i] per plan."""
+        n = len(self.plans)
+        ptrs = (ctypes.c_void_p * n)(*[c.data_ptr() for c in chunks])
+        ns = (ctypes.c_int32 * n)(*[int(c.shape[0]) for c in chunks])
+        _check(lib.snd_batch_execute(self.handle, ptrs, ns, _stream_ptr(stream)), "snd_batch_execute")
+
+    def graph_stats(self):
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib.snd_batch_graph_stats(self.handle, ctypes.byref(a), ctypes.byref(b)), "snd_batch_graph_stats")
+        return int(a.value), int(b.value)

@@ -17,7 +17,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsnd.so")
 CU_SOURCES = ["encode.cu", "tree.cu", "ztree.cu", "mf.cu", "ccl.cu", "runtime.cu", "noalloc.cu", "multirate.cu",
-              "sifter.cu"]
+              "sifter.cu", "batch.cu"]
 CPP_SOURCES = ["plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,168 @@
+// Many beams per step: every beam is its own plan (its own DM grid, chunk length, options
+// and workspace), and one call advances all of them by one chunk each.
+//
+// The tree, the dominant stage, runs as few launches as possible: beams whose plans share
+// a kernel instantiation and block shape go into one k_tree_multi launch, whose CTAs are
+// spread over the beams by a prefix of their tile counts (the per-beam arguments travel by
+// value in the launch's parameter block). The encoder, matched filter and candidate stages
+// run per beam, in beam order, on the same stream. With graphs enabled the whole step is
+// captured on a private stream and launched as one CUDA graph on the caller's stream; the
+// next step's capture updates the instantiated graph in place (cudaGraphExecUpdate)
+// whenever the topology is unchanged, so a steady stream of chunks re-uses one executable
+// graph.
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "snd_internal.h"
+
+using snd::Plan;
+
+namespace {
+
+struct Batch {
+  std::vector<Plan*> plans;
+  bool graph = false;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;  // private stream the steps are captured on
+  int64_t graph_updates = 0, graph_instantiations = 0;
+  int sticky = 0;
+  ~Batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (capture) cudaStreamDestroy(capture);
+  }
+};
+
+// enqueue one step of every beam on s; the plans record `owner` as the stream their work
+// runs on (the caller's stream, also when s is the capture stream)
+int enqueue_step(Batch& b, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
+                 cudaStream_t owner) {
+  const int n = static_cast<int>(b.plans.size());
+  std::vector<snd::ChunkPos> pos(n);
+  std::vector<const Plan*> tp;
+  std::vector<int64_t> ep, en;
+  for (int i = 0; i < n; ++i) {
+    Plan& p = *b.plans[i];
+    pos[i] = snd::chunk_pos(p, nsamp[i]);
+    if (snd::launch_encode(p, d_chunks[i], nsamp[i], s) != cudaSuccess) return SND_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    Plan& p = *b.plans[i];
+    if (pos[i].e_new <= pos[i].e_prev) continue;
+    if (p.mode == SND_MODE_ZFLOAT) {
+      if (snd::launch_tree_z(p, pos[i].e_prev, pos[i].e_new, nullptr, s) != cudaSuccess) return SND_ERR_CUDA;
+    } else if (p.flags & SND_FLAG_REFERENCE_TREE) {
+      if (snd::launch_tree(p, pos[i].e_prev, pos[i].e_new, s) != cudaSuccess) return SND_ERR_CUDA;
+    } else {
+      tp.push_back(&p);
+      ep.push_back(pos[i].e_prev);
+      en.push_back(pos[i].e_new);
+    }
+  }
+  if (!tp.empty() &&
+      snd::launch_tree_batch(tp.data(), ep.data(), en.data(), static_cast<int>(tp.size()), s) != cudaSuccess)
+    return SND_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    Plan& p = *b.plans[i];
+    if (p.mode == SND_MODE_ZFLOAT) continue;
+    if (snd::chunk_post(p, pos[i], nullptr, s, [](int, auto&& f) { return f(); }) != cudaSuccess)
+      return SND_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) snd::chunk_commit(*b.plans[i], pos[i], nsamp[i], owner);
+  return SND_OK;
+}
+
+int fail(Batch& b, int code) {
+  if (!b.sticky) b.sticky = code;
+  return code;
+}
+
+}  // namespace
+
+extern "C" int snd_batch_create(const snd_plan_t* plans, int32_t nplans, snd_batch_t* out) {
+  if (out) *out = nullptr;
+  if (!out || !plans || nplans < 1 || nplans > 4096) return SND_ERR_ARG;
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return SND_ERR_NOMEM;
+  for (int i = 0; i < nplans; ++i) {
+    if (!plans[i]) {
+      delete b;
+      return SND_ERR_ARG;
+    }
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) {
+        delete b;
+        return SND_ERR_ARG;
+      }
+    b->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
+  }
+  *out = reinterpret_cast<snd_batch_t>(b);
+  return SND_OK;
+}
+
+extern "C" int snd_batch_set_graph(snd_batch_t h, int32_t enable) {
+  if (!h) return SND_ERR_ARG;
+  reinterpret_cast<Batch*>(h)->graph = enable != 0;
+  return SND_OK;
+}
+
+extern "C" int snd_batch_execute(snd_batch_t h, const uint8_t* const* d_chunks, const int32_t* nsamp, void* stream) {
+  if (!h || !d_chunks || !nsamp) return SND_ERR_ARG;
+  Batch& b = *reinterpret_cast<Batch*>(h);
+  if (b.sticky) return b.sticky;
+  for (size_t i = 0; i < b.plans.size(); ++i) {
+    const Plan& p = *b.plans[i];
+    if (p.sticky) return p.sticky;
+    if (!p.bound) return SND_ERR_STATE;
+    if (!d_chunks[i]) return SND_ERR_ARG;
+    if (nsamp[i] < 1 || nsamp[i] > p.max_chunk) return SND_ERR_CHUNK;
+    if (p.profiling) return SND_ERR_STATE;  // per-stage events are not recorded in a batch
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!b.graph) {
+    const int rc = enqueue_step(b, d_chunks, nsamp, s, s);
+    return rc ? fail(b, rc) : SND_OK;
+  }
+  // capture on a private stream (the caller's may be the legacy default stream, which cannot
+  // be captured); the graph is then launched on the caller's stream, in its order
+  if (!b.capture && cudaStreamCreateWithFlags(&b.capture, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(b, SND_ERR_CUDA);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b.capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(b, SND_ERR_CUDA);
+  const int rc = enqueue_step(b, d_chunks, nsamp, b.capture, s);
+  const cudaError_t ec = cudaStreamEndCapture(b.capture, &g);
+  if (rc || ec != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    return fail(b, rc ? rc : SND_ERR_CUDA);
+  }
+  cudaError_t e = cudaSuccess;
+  if (b.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(b.exec, g, &info) != cudaSuccess) {
+      cudaGetLastError();  // an update that does not apply is not an error: instantiate anew
+      cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+    } else {
+      ++b.graph_updates;
+    }
+  }
+  if (!b.exec) {
+    e = cudaGraphInstantiate(&b.exec, g, 0);
+    ++b.graph_instantiations;
+  }
+  cudaGraphDestroy(g);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b.exec, s);
+  return e == cudaSuccess ? SND_OK : fail(b, SND_ERR_CUDA);
+}
+
+extern "C" int snd_batch_graph_stats(snd_batch_t h, int64_t* instantiations, int64_t* updates) {
+  if (!h) return SND_ERR_ARG;
+  const Batch& b = *reinterpret_cast<Batch*>(h);
+  if (instantiations) *instantiations = b.graph_instantiations;
+  if (updates) *updates = b.graph_updates;
+  return SND_OK;
+}
+
+extern "C" void snd_batch_destroy(snd_batch_t h) { delete reinterpret_cast<Batch*>(h); }

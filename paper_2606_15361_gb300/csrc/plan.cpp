@@ -40,6 +40,7 @@ struct VecHash {
 };
 
 int choose_tree_geometry(Plan& p);
+int choose_tree_geometry_w(Plan& p, int warps);
 int choose_ztree_geometry(Plan& p);
 
 }  // namespace
@@ -306,17 +307,30 @@ int build_plan(Plan& p) {
 
 namespace {
 
-// Tree kernel geometry: DMs per CTA, output words per CTA, the per-(tile, leaf) lists of
-// distinct leaf patterns, the staged window sizes, and how many leaves (a multiple of B) are
-// staged per shared-memory round so that a CTA fits the shared-memory budget.
+// Tree kernel geometry: the kernel shape of tree_shape(), or, when a DM tile of that many
+// trial DMs spans delays too wide for shared memory (coarse DM grids), the same kernel with
+// fewer warps (fewer DMs per tile) until it fits.
 int choose_tree_geometry(Plan& p) {
+  const snd::TreeShape sh = snd::tree_shape(p.mode, p.nlev, p.KL > p.KI ? p.KL : p.KI);
+  int rc = SND_ERR_UNSUPPORTED;
+  for (int w = sh.warps; w >= 4; w /= 2) {
+    rc = choose_tree_geometry_w(p, w);
+    if (rc != SND_ERR_UNSUPPORTED) break;
+  }
+  return rc;
+}
+
+// Geometry for `warps` warps: DMs per CTA, output words per CTA, the per-(tile, leaf) lists
+// of distinct leaf patterns, the staged window sizes, and how many leaves (a multiple of B)
+// are staged per shared-memory round so that a CTA fits the shared-memory budget.
+int choose_tree_geometry_w(Plan& p, int warps) {
   snd::TreeGeom& g = p.geom;
   const int ndm = p.ndm, NL = p.nleaves, nchan = p.nchan;
   const snd::TreeShape sh = snd::tree_shape(p.mode, p.nlev, p.KL > p.KI ? p.KL : p.KI);
-  g.warps = sh.warps;
+  g.warps = warps;
   g.dpw = sh.dpw;
   g.kw = sh.kw;
-  g.dms_per_cta = sh.warps * sh.dpw;
+  g.dms_per_cta = warps * sh.dpw;
   g.tile_words = 32 * g.kw;
   g.planes = (p.mode == SND_MODE_BINARY) ? 1 : 3;
   g.ndm_tiles = (ndm + g.dms_per_cta - 1) / g.dms_per_cta;

@@ -12,6 +12,28 @@
 
 using snd::Plan;
 
+namespace snd {
+
+ChunkPos chunk_pos(const Plan& p, int32_t nsamp) {
+  ChunkPos c;
+  c.e_prev = p.E;
+  c.e_new = std::max<int64_t>(0, p.T + nsamp - p.D);
+  c.f_prev = p.F;
+  c.f_new = std::max<int64_t>(0, c.e_new - (p.wmax - 1));
+  c.nb = static_cast<int>(c.f_new - c.f_prev);
+  return c;
+}
+
+void chunk_commit(Plan& p, const ChunkPos& c, int32_t nsamp, cudaStream_t s) {
+  p.T += nsamp;
+  p.E = c.e_new;
+  p.F = (p.mode == SND_MODE_ZFLOAT) ? p.F : c.f_new;
+  p.last_stream = s;
+  p.pending_host = -1;
+}
+
+}  // namespace snd
+
 namespace {
 
 int fail(Plan& p, int code) {
@@ -55,39 +77,20 @@ cudaError_t stage(Plan& p, int id, cudaStream_t s, F&& f) {
 
 int run_chunk(Plan& p, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s, void* d_plane_out,
               int32_t* nemit_out) {
-  const int64_t e_prev = p.E;
-  const int64_t e_new = std::max<int64_t>(0, p.T + nsamp - p.D);
-  const int64_t f_prev = p.F;
-  const int64_t f_new = std::max<int64_t>(0, e_new - (p.wmax - 1));
-  const int nb = static_cast<int>(f_new - f_prev);
+  const snd::ChunkPos c = snd::chunk_pos(p, nsamp);
   cudaError_t e = stage(p, SND_STAGE_ENCODE, s, [&] { return snd::launch_encode(p, d_chunk, nsamp, s); });
   if (p.mode == SND_MODE_ZFLOAT) {
     // labelled-payload plane only: no matched filter or candidates
-    if (e == cudaSuccess && e_new > e_prev)
-      e = stage(p, SND_STAGE_TREE, s, [&] { return snd::launch_tree_z(p, e_prev, e_new, d_plane_out, s); });
-    if (e != cudaSuccess) return fail(p, SND_ERR_CUDA);
-    p.T += nsamp;
-    p.E = e_new;
-    p.last_stream = s;
-    p.pending_host = -1;
-    if (nemit_out) *nemit_out = static_cast<int32_t>(e_new - e_prev);
-    return SND_OK;
+    if (e == cudaSuccess && c.e_new > c.e_prev)
+      e = stage(p, SND_STAGE_TREE, s, [&] { return snd::launch_tree_z(p, c.e_prev, c.e_new, d_plane_out, s); });
+  } else {
+    if (e == cudaSuccess && c.e_new > c.e_prev)
+      e = stage(p, SND_STAGE_TREE, s, [&] { return snd::launch_tree(p, c.e_prev, c.e_new, s); });
+    if (e == cudaSuccess) e = snd::chunk_post(p, c, d_plane_out, s, [&](int id, auto&& f) { return stage(p, id, s, f); });
   }
-  if (e == cudaSuccess && e_new > e_prev)
-    e = stage(p, SND_STAGE_TREE, s, [&] { return snd::launch_tree(p, e_prev, e_new, s); });
-  if (e == cudaSuccess && nb > 0)
-    e = cudaMemsetAsync(p.dp.counters, 0, sizeof(uint32_t) * (snd::kCntBlockCands + 1), s);
-  if (e == cudaSuccess && (nb > 0 || (d_plane_out && e_new > e_prev)))
-    e = stage(p, SND_STAGE_MF, s, [&] { return snd::launch_mf(p, e_prev, e_new, f_prev, f_new, d_plane_out, s); });
-  if (e == cudaSuccess && nb > 0)
-    e = stage(p, SND_STAGE_CANDIDATES, s, [&] { return snd::launch_candidates(p, f_prev, nb, s); });
   if (e != cudaSuccess) return fail(p, SND_ERR_CUDA);
-  p.T += nsamp;
-  p.E = e_new;
-  p.F = f_new;
-  p.last_stream = s;
-  p.pending_host = -1;
-  if (nemit_out) *nemit_out = static_cast<int32_t>(e_new - e_prev);
+  snd::chunk_commit(p, c, nsamp, s);
+  if (nemit_out) *nemit_out = static_cast<int32_t>(c.e_new - c.e_prev);
   return SND_OK;
 }
 

@@ -186,6 +186,20 @@ struct Plan {
 // plan.cpp
 int build_plan(Plan& p);
 
+// runtime.cu: the positions of one chunk (Methods, "Pipeline overview", ring-buffer form):
+// plane samples [e_prev, e_new) are emitted, start times [f_prev, f_new) scored (nb of them)
+struct ChunkPos {
+  int64_t e_prev, e_new, f_prev, f_new;
+  int nb;
+};
+ChunkPos chunk_pos(const Plan& p, int32_t nsamp);
+void chunk_commit(Plan& p, const ChunkPos& c, int32_t nsamp, cudaStream_t s);
+
+// Matched filter and candidate stages of a chunk whose tree has run; `stage(id, f)` runs the
+// launcher f (optionally timed).
+template <typename Stage>
+cudaError_t chunk_post(const Plan& p, const ChunkPos& c, void* d_plane_out, cudaStream_t s, Stage&& stage);
+
 // kernels (launchers), each returns cudaGetLastError() of its launch and adds the number
 // of kernels it enqueued to p.launches
 cudaError_t launch_encode(const Plan& p, const uint8_t* d_chunk, int nsamp, cudaStream_t s);
@@ -194,6 +208,19 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
                       void* d_plane_out, cudaStream_t s);
 cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_t s);
 TreeShape tree_shape(int mode, int nlev, int kmax);  // k_tree launch shape
+cudaError_t launch_tree_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
+                              cudaStream_t s);
 cudaError_t launch_tree_z(const Plan& p, int64_t e_prev, int64_t e_new, void* d_plane_out, cudaStream_t s);
+
+template <typename Stage>
+cudaError_t chunk_post(const Plan& p, const ChunkPos& c, void* d_plane_out, cudaStream_t s, Stage&& stage) {
+  cudaError_t e = cudaSuccess;
+  if (c.nb > 0) e = cudaMemsetAsync(p.dp.counters, 0, sizeof(uint32_t) * (kCntBlockCands + 1), s);
+  if (e == cudaSuccess && (c.nb > 0 || (d_plane_out && c.e_new > c.e_prev)))
+    e = stage(SND_STAGE_MF, [&] { return launch_mf(p, c.e_prev, c.e_new, c.f_prev, c.f_new, d_plane_out, s); });
+  if (e == cudaSuccess && c.nb > 0)
+    e = stage(SND_STAGE_CANDIDATES, [&] { return launch_candidates(p, c.f_prev, c.nb, s); });
+  return e;
+}
 
 }  // namespace snd

@@ -26,6 +26,8 @@
 
 #include <cuda_pipeline.h>
 
+#include <vector>
+
 #include "snd_internal.h"
 
 namespace snd {
@@ -49,6 +51,15 @@ struct TreeArgs {
   int nwords;       // output words of this call
   int32_t* plane;
   int Lp;
+};
+
+constexpr int kMaxBatchBeams = 64;
+
+struct TreeMulti {
+  int nbeams;
+  int first[kMaxBatchBeams];  // first CTA of each beam
+  int ntx[kMaxBatchBeams];    // time tiles of each beam
+  TreeArgs beam[kMaxBatchBeams];
 };
 
 __device__ __forceinline__ uint32_t funnel(uint32_t lo, uint32_t hi, int sh) {
@@ -449,9 +460,9 @@ __device__ __forceinline__ void sum8(const uint32_t (&v)[8][3], uint32_t* out6) 
 //   3. phase 2: every warp gathers, for each of its DMs and each level-1 node of the group,
 //      the node's leaf values at the DM's own leaf shifts (one funnel shift per plane and
 //      word) and pushes the finished node values up the tree.
+// One CTA of the tree: time tile bx (tile_words output words) of DM tile `tile`.
 template <int MODE, int MAXL, int KW, int TH, int DPW, int CT>
-__global__ void __launch_bounds__((MODE != kBinary && DPW == 1 && MAXL == 4) ? 1024 : 512,
-                                  (MODE == kBinary && TH == 2) ? 2 : 1) k_tree(TreeArgs a) {
+__device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
   using T = Tree<MODE, MAXL, KW, TH, DPW>;
   constexpr int PL = T::kLeafPlanes;
   constexpr int NC = CT ? CT : 8;  // channels per leaf iterated at compile time
@@ -460,8 +471,7 @@ __global__ void __launch_bounds__((MODE != kBinary && DPW == 1 && MAXL == 4) ? 1
   const int DT = NW * DPW;
   const int lane = threadIdx.x, wd = threadIdx.y;
   const int tid = wd * 32 + lane, nthr = 32 * NW;
-  const int tile = blockIdx.y;
-  const long long aw0 = a.word0 + static_cast<long long>(blockIdx.x) * a.tile_words;
+  const long long aw0 = a.word0 + static_cast<long long>(bx) * a.tile_words;
   const int awp = static_cast<int>(aw0 % a.R);
   const int NL = a.nleaves, C = a.C, G = a.G, span = a.span, cspan = a.cspan;
   const int span_eff = min(span, a.tile_words + a.span_extra);
@@ -703,6 +713,29 @@ __global__ void __launch_bounds__((MODE != kBinary && DPW == 1 && MAXL == 4) ? 1
   }
 }
 
+#define SND_TREE_BOUNDS                                                                   \
+  __launch_bounds__((MODE != kBinary && DPW == 1 && MAXL == 4) ? 1024 : 512, \
+                    (MODE == kBinary && TH == 2) ? 2 : 1)
+
+template <int MODE, int MAXL, int KW, int TH, int DPW, int CT>
+__global__ void SND_TREE_BOUNDS k_tree(const __grid_constant__ TreeArgs a) {
+  tree_cta<MODE, MAXL, KW, TH, DPW, CT>(a, blockIdx.x, blockIdx.y);
+}
+
+// Several beams (plans with the same kernel instantiation) in one launch: CTA i belongs to
+// the last beam with first[b] <= i; within a beam, CTAs run time tile fastest.
+template <int MODE, int MAXL, int KW, int TH, int DPW, int CT>
+__global__ void SND_TREE_BOUNDS k_tree_multi(const __grid_constant__ TreeMulti m) {
+  const int i = static_cast<int>(blockIdx.x);
+  int lo = 0, hi = m.nbeams - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (m.first[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  const int local = i - m.first[lo];
+  tree_cta<MODE, MAXL, KW, TH, DPW, CT>(m.beam[lo], local % m.ntx[lo], local / m.ntx[lo]);
+}
+
 // Scalar verification kernel: one thread per (DM, output sample), the tree walked leaf by
 // leaf with integer counts straight from the full delay table. Slow; selected by
 // SND_FLAG_REFERENCE_TREE to cross-check k_tree.
@@ -763,6 +796,109 @@ cudaError_t run_tree(const TreeArgs& a, dim3 grid, dim3 block, int smem, cudaStr
   return cudaGetLastError();
 }
 
+template <int MODE, int MAXL, int KW, int TH, int DPW>
+cudaError_t run_tree_multi(const TreeMulti& m, int ct4, int nctas, dim3 block, int smem, cudaStream_t s) {
+  auto kern = ct4 ? k_tree_multi<MODE, MAXL, KW, TH, DPW, 4> : k_tree_multi<MODE, MAXL, KW, TH, DPW, 0>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  kern<<<nctas, block, smem, s>>>(m);
+  return cudaGetLastError();
+}
+
+struct GoSingle {
+  const TreeArgs* a;
+  dim3 grid, block;
+  int smem;
+  cudaStream_t s;
+  template <int MODE, int MAXL, int KW, int TH, int DPW>
+  cudaError_t go() { return run_tree<MODE, MAXL, KW, TH, DPW>(*a, grid, block, smem, s); }
+};
+
+struct GoMulti {
+  const TreeMulti* m;
+  int ct4, ctas;
+  dim3 block;
+  int smem;
+  cudaStream_t s;
+  template <int MODE, int MAXL, int KW, int TH, int DPW>
+  cudaError_t go() { return run_tree_multi<MODE, MAXL, KW, TH, DPW>(*m, ct4, ctas, block, smem, s); }
+};
+
+// The k_tree instantiation a plan uses, following tree_shape(): the accumulators of every
+// open level stay in registers. 0..9 below; +16 when the 4-channel leaf path applies.
+int tree_inst(const Plan& p) {
+  const int kmax = p.KL > p.KI ? p.KL : p.KI;
+  const int maxl = p.nlev <= 4 ? 4 : (p.nlev <= 8 ? 8 : 16);
+  const int ml = maxl == 4 ? 0 : (maxl == 8 ? 1 : 2);
+  int id;
+  if (p.mode == SND_MODE_BINARY) {
+    id = (kmax <= 2 ? 0 : 3) + ml;
+  } else if (p.mode == SND_MODE_GRADED) {
+    id = 6 + ml;
+  } else {
+    id = 9;
+  }
+  return id + ((p.C == 4 && p.nchan % 4 == 0) ? 16 : 0);
+}
+
+template <typename F>
+cudaError_t dispatch_inst(int id, F&& f) {
+  switch (id & 15) {
+    case 0: return f.template go<kBinary, 4, 2, 2, 2>();
+    case 1: return f.template go<kBinary, 8, 1, 2, 2>();
+    case 2: return f.template go<kBinary, 16, 1, 2, 1>();
+    case 3: return f.template go<kBinary, 4, 1, 8, 1>();
+    case 4: return f.template go<kBinary, 8, 1, 8, 1>();
+    case 5: return f.template go<kBinary, 16, 1, 8, 1>();
+    case 6: return f.template go<kGraded, 4, 1, 1, 1>();
+    case 7: return f.template go<kGraded, 8, 1, 1, 1>();
+    case 8: return f.template go<kGraded, 16, 1, 1, 1>();
+    default: return f.template go<kFloat, 4, 1, 1, 1>();
+  }
+}
+
+// Kernel arguments of one plan for output samples [e_prev, e_new); *ntx = time tiles.
+void tree_args(const Plan& p, int64_t e_prev, int64_t e_new, TreeArgs& a, int* ntx) {
+  const DevPtrs& dp = p.dp;
+  a = TreeArgs{};
+  a.ring = dp.ring;
+  a.R = p.R;
+  a.nchan = p.nchan;
+  a.ndm = p.ndm;
+  a.nleaves = p.nleaves;
+  a.C = p.C;
+  a.B = p.B;
+  a.KL = p.KL;
+  a.KI = p.KI;
+  a.N = p.N;
+  a.nlev = p.nlev;
+  for (int l = 0; l < kMaxLevels; ++l) a.level_nodes[l] = l < p.nlev ? p.level_nodes[l] : 1;
+  a.tp_off = dp.tp_off;
+  a.gepk = dp.gepk;
+  a.gleaf = dp.gleaf;
+  a.gmeta = dp.gmeta;
+  a.tile_wb = dp.tile_wb;
+  const TreeGeom& g = p.geom;
+  a.G = g.group_leaves;
+  a.span = g.span;
+  a.cspan = g.cspan;
+  a.maxpat = g.max_pat_group;
+  a.span_extra = g.span - g.tile_words;
+  {
+    const int lmax = p.B * (p.C < p.N ? p.C : p.N);
+    a.plain1 = (lmax <= p.N && lmax <= 63) ? 1 : 0;
+  }
+  a.word0 = e_prev >> 5;
+  a.nwords = static_cast<int>(((e_new - 1) >> 5) - (e_prev >> 5) + 1);
+  // spread the words evenly over the fewest tiles of at most tile_words
+  const int ntiles = (a.nwords + g.tile_words - 1) / g.tile_words;
+  a.tile_words = (a.nwords + ntiles - 1) / ntiles;
+  a.plane = dp.plane;
+  a.Lp = p.Lp;
+  *ntx = ntiles;
+}
+
 }  // namespace
 
 // Kernel shape for a mode and tree depth: {warps per CTA, DMs per warp, words per lane}.
@@ -813,64 +949,49 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
     p.launches += 1;
     return cudaGetLastError();
   }
-  TreeArgs a{};
-  a.ring = dp.ring;
-  a.R = p.R;
-  a.nchan = p.nchan;
-  a.ndm = p.ndm;
-  a.nleaves = p.nleaves;
-  a.C = p.C;
-  a.B = p.B;
-  a.KL = p.KL;
-  a.KI = p.KI;
-  a.N = p.N;
-  a.nlev = p.nlev;
-  for (int l = 0; l < kMaxLevels; ++l) a.level_nodes[l] = l < p.nlev ? p.level_nodes[l] : 1;
-  a.tp_off = dp.tp_off;
-  a.gepk = dp.gepk;
-  a.gleaf = dp.gleaf;
-  a.gmeta = dp.gmeta;
-  a.tile_wb = dp.tile_wb;
+  TreeArgs a;
+  int ntx = 0;
+  tree_args(p, e_prev, e_new, a, &ntx);
   const TreeGeom& g = p.geom;
-  a.G = g.group_leaves;
-  a.span = g.span;
-  a.cspan = g.cspan;
-  a.maxpat = g.max_pat_group;
-  a.span_extra = g.span - g.tile_words;
-  {
-    const int lmax = p.B * (p.C < p.N ? p.C : p.N);
-    a.plain1 = (lmax <= p.N && lmax <= 63) ? 1 : 0;
-  }
-  a.word0 = e_prev >> 5;
-  a.nwords = static_cast<int>(((e_new - 1) >> 5) - (e_prev >> 5) + 1);
-  // spread the words evenly over the fewest tiles of at most tile_words
-  const int ntiles = (a.nwords + g.tile_words - 1) / g.tile_words;
-  a.tile_words = (a.nwords + ntiles - 1) / ntiles;
-  a.plane = dp.plane;
-  a.Lp = p.Lp;
-  dim3 block(32, g.warps);
-  dim3 grid(ntiles, g.ndm_tiles);
+  const dim3 block(32, g.warps), grid(ntx, g.ndm_tiles);
   const int smem = g.smem_bytes;
   p.launches += 1;
-  // instantiations follow tree_shape(): the accumulators of every open level stay in registers
-  const int kmax = p.KL > p.KI ? p.KL : p.KI;
-  const int maxl = p.nlev <= 4 ? 4 : (p.nlev <= 8 ? 8 : 16);
-  if (p.mode == SND_MODE_BINARY) {
-    if (kmax <= 2) {
-      if (maxl == 4) return run_tree<kBinary, 4, 2, 2, 2>(a, grid, block, smem, s);
-      if (maxl == 8) return run_tree<kBinary, 8, 1, 2, 2>(a, grid, block, smem, s);
-      return run_tree<kBinary, 16, 1, 2, 1>(a, grid, block, smem, s);
+  GoSingle go{&a, grid, block, smem, s};
+  return dispatch_inst(tree_inst(p), go);
+}
+
+// Trees of several plans in as few launches as possible: plans that share a kernel
+// instantiation and block shape run in one launch (k_tree_multi, up to 64 beams each).
+cudaError_t launch_tree_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
+                              cudaStream_t s) {
+  std::vector<int> done(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (done[i]) continue;
+    const int key = tree_inst(*plans[i]);
+    const int warps = plans[i]->geom.warps;
+    TreeMulti m{};
+    int smem = 0, ctas = 0;
+    const Plan* owner = nullptr;
+    for (int j = i; j < n && m.nbeams < kMaxBatchBeams; ++j) {
+      if (done[j] || tree_inst(*plans[j]) != key || plans[j]->geom.warps != warps) continue;
+      done[j] = 1;
+      if (e_new[j] <= e_prev[j]) continue;
+      int ntx = 0;
+      tree_args(*plans[j], e_prev[j], e_new[j], m.beam[m.nbeams], &ntx);
+      m.first[m.nbeams] = ctas;
+      m.ntx[m.nbeams] = ntx;
+      ctas += ntx * plans[j]->geom.ndm_tiles;
+      smem = smem > plans[j]->geom.smem_bytes ? smem : plans[j]->geom.smem_bytes;
+      plans[j]->launches += (owner == nullptr) ? 1 : 0;
+      owner = plans[j];
+      ++m.nbeams;
     }
-    if (maxl == 4) return run_tree<kBinary, 4, 1, 8, 1>(a, grid, block, smem, s);
-    if (maxl == 8) return run_tree<kBinary, 8, 1, 8, 1>(a, grid, block, smem, s);
-    return run_tree<kBinary, 16, 1, 8, 1>(a, grid, block, smem, s);
+    if (m.nbeams == 0) continue;
+    GoMulti go{&m, (key & 16) ? 1 : 0, ctas, dim3(32, warps), smem, s};
+    const cudaError_t e = dispatch_inst(key, go);
+    if (e != cudaSuccess) return e;
   }
-  if (p.mode == SND_MODE_GRADED) {
-    if (maxl == 4) return run_tree<kGraded, 4, 1, 1, 1>(a, grid, block, smem, s);
-    if (maxl == 8) return run_tree<kGraded, 8, 1, 1, 1>(a, grid, block, smem, s);
-    return run_tree<kGraded, 16, 1, 1, 1>(a, grid, block, smem, s);
-  }
-  return run_tree<kFloat, 4, 1, 1, 1>(a, grid, block, smem, s);
+  return cudaSuccess;
 }
 
 }  // namespace snd
