@@ -460,10 +460,11 @@ def run_gpu(args, rank, world, local_rank):
     sync()
     ms_e2e = max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
 
-    mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if rank == 0 else None
-    zf = zfloat_rate(g, args, dev, dchunks, freqs, dms) if rank == 0 else None
-    sft = sifter_rate(g, args, dev) if rank == 0 and not args.no_sifter else None
-    mb = multibeam_rate(g, args, dev) if rank == 0 and not args.no_multibeam else None
+    extras = rank == 0 and not args.main_only
+    mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if extras else None
+    zf = zfloat_rate(g, args, dev, dchunks, freqs, dms) if extras else None
+    sft = sifter_rate(g, args, dev) if extras and not args.no_sifter else None
+    mb = multibeam_rate(g, args, dev) if extras and not args.no_multibeam else None
 
     per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
     ms_dev, ms_e2e = reduce_max([ms_dev, ms_e2e], dist, dev)
@@ -528,9 +529,35 @@ def run_gpu(args, rank, world, local_rank):
 
 def drive(mode_name: str, nchunks: int, branching: int):
     """Run one plan of the workload over `nchunks` chunks, untimed (for profiler captures:
-    the tree kernel's second launch is the first steady-state chunk)."""
+    the tree kernel's second launch is the first steady-state chunk). Modes beyond the three
+    tree modes: zfloat / zfloat16 (labelled payload, FP32 / FP16 partial sums), sifter (the
+    learned sifter: forward passes at batch 512, then training steps at batch 256; about 2 GB
+    of device memory, small enough for a full profiler capture)."""
     import torch
     import paper_2606_15361_gb300 as g
+    if mode_name == "sifter":
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        x = torch.randn((512, 64, 256), generator=gen, device="cuda")
+        y = (torch.rand(512, generator=gen, device="cuda") < 0.5).float()
+        inf = g.Sifter(max_batch=512, training=False, seed=1)
+        for _ in range(nchunks):
+            inf.forward(x)
+        tr = g.Sifter(max_batch=256, training=True, seed=1)
+        for _ in range(nchunks):
+            tr.train_step(x[:256], y[:256], 1e-4)
+        tr.status()
+        print(json.dumps({"drive": mode_name, "passes": nchunks}))
+        return
+    if mode_name in ("zfloat", "zfloat16"):
+        chunks = [torch.from_numpy(W.chunk_data(i)).cuda() for i in range(nchunks)]
+        flag = g.FLAG_FP16_PARTIALS if mode_name == "zfloat16" else 0
+        plan = g.Plan(W.freqs(), synth.NC_DT, W.dms(), branching, g.MODE_ZFLOAT,
+                      g.options(g.MODE_ZFLOAT, max_chunk=W.chunk, flags=flag))
+        for c in chunks:
+            plan.execute(c)
+        torch.cuda.synchronize()
+        print(json.dumps({"drive": mode_name, "chunks": nchunks, "branching": branching}))
+        return
     m = dict(MODES)[mode_name]
     chunks = [torch.from_numpy(W.chunk_data(i)).cuda() for i in range(nchunks)]
     plan = g.Plan(W.freqs(), synth.NC_DT, W.dms(), branching, m, g.options(m, max_chunk=W.chunk))
@@ -551,7 +578,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sifter", action="store_true", help="skip the learned-sifter measurements")
     ap.add_argument("--no-multibeam", action="store_true", help="skip the 48-beam batch measurements")
-    ap.add_argument("--drive", choices=[m for m, _ in MODES], help="profiling driver: one plan, no timing")
+    ap.add_argument("--main-only", action="store_true",
+                    help="only the headline workload: no multi-rate, labelled-payload, sifter or multi-beam parts")
+    ap.add_argument("--drive", choices=[m for m, _ in MODES] + ["zfloat", "zfloat16", "sifter"],
+                    help="profiling driver: one plan (or the sifter), no timing")
     ap.add_argument("--chunks", type=int, default=3)
     ap.add_argument("--branching", type=int, default=BRANCHING)
     args = ap.parse_args()

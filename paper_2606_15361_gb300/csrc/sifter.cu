@@ -144,20 +144,31 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent, warp-specialised GEMM. 192 threads: warps 0-3 drain the accumulator (warp w
+// owns TMEM lanes 32w..32w+31, i.e. tile rows), warp 4 issues the TMA loads, warp 5 owns
+// the TMEM allocation and one of its threads issues the MMAs. A CTA walks the output tiles
+// t = blockIdx.x, + gridDim.x, ... (blockIdx.z = K split); the accumulator is double
+// buffered in TMEM (2 x BN columns), so the epilogue of tile j overlaps the MMAs of tile
+// j + 1, and the shared-memory stage ring runs across tiles.
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     k_gemm(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, int M, int N, int ktiles,
            int kt_per_split, Epi epi, uint32_t* err) {
   constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
-  constexpr uint32_t kCols = BN < 32 ? 32 : BN;
+  constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
   extern __shared__ uint8_t gsm_raw[];
-  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_done;
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sA = smem_u32(gsm), sB = sA + kStages * kABytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
+  const int ntiles = mt * nt;
   const int kt0 = blockIdx.z * kt_per_split;
   const int nkt = min(ktiles, kt0 + kt_per_split) - kt0;
 
@@ -166,11 +177,14 @@ __global__ void __launch_bounds__(128, 1)
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_done), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_tfull[b]), 1);
+      mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per epilogue warp
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {
+  if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(kCols)
                  : "memory");
@@ -180,79 +194,112 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  volatile int* abort_v = &abort_flag;
 
-  if (warp == 0 && lane == 0) {
-    // producer: TMA loads of the A and B tiles of each K step into the stage ring
-    for (int i = 0; i < nkt; ++i) {
-      const int s = i % kStages;
-      if (i >= kStages && !mbar_wait(smem_u32(&bar_empty[s]), ((i / kStages) & 1) ^ 1)) {
-        atomicOr(err, kErrWait);
-        abort_flag = 1;
-        break;
-      }
-      if (*reinterpret_cast<volatile int*>(&abort_flag)) break;
-      const uint32_t fb = smem_u32(&bar_full[s]);
-      mbar_expect_tx(fb, kABytes + kBBytes);
-      tma_load_2d(sA + s * kABytes, &ma, fb, (kt0 + i) * kBK, m0);
-      tma_load_2d(sB + s * kBBytes, &mb, fb, (kt0 + i) * kBK, n0);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer: four K = 16 steps per stage, then release the stage
-    constexpr uint32_t idesc = mma_idesc(BN);
-    for (int i = 0; i < nkt; ++i) {
-      const int s = i % kStages;
-      if (!mbar_wait(smem_u32(&bar_full[s]), (i / kStages) & 1)) {
-        atomicOr(err, kErrWait);
-        abort_flag = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint64_t da = sw128_desc(sA + s * kABytes + kk * 32);
-        const uint64_t db = sw128_desc(sB + s * kBBytes + kk * 32);
-        umma_bf16(tmem, da, db, idesc, (i | kk) != 0 ? 1u : 0u);
-      }
-      umma_commit(smem_u32(&bar_empty[s]));
-    }
-    umma_commit(smem_u32(&bar_done));
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w + 31
-  bool ok = mbar_wait(smem_u32(&bar_done), 0);
-  ok = __all_sync(0xFFFFFFFFu, ok);
-  if (!ok && lane == 0) atomicOr(err, kErrWait);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && nkt > 0) {
-    const int row = m0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int c = 0; c < BN; c += 8) {
-      float v[8];
-      tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c), v);
-      if (row >= M) continue;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int n = n0 + c + i;
-        if (n >= N) continue;
-        float x = v[i];
-        if (epi.bias) x += epi.bias[n];
-        if (epi.relu) x = fmaxf(x, 0.0f);
-        const long long idx = epi.transposed ? static_cast<long long>(n) * epi.ldo + row
-                                             : static_cast<long long>(row) * epi.ldo + n;
-        if (epi.atomic) {
-          atomicAdd(static_cast<float*>(epi.out) + idx, x);
-        } else if (epi.out_bf16) {
-          static_cast<bf16*>(epi.out)[idx] = __float2bfloat16_rn(x);
-        } else {
-          static_cast<float*>(epi.out)[idx] = x;
+  if (nkt > 0) {
+    if (warp == 4) {
+      if (lane == 0) {
+        // producer: the K steps of every tile of this CTA through the stage ring
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x) {
+          const int m0 = (t % mt) * kBM, n0 = (t / mt) * BN;
+          for (int i = 0; i < nkt; ++i, ++it) {
+            const int s = it % kStages;
+            if (it >= kStages && !mbar_wait(smem_u32(&bar_empty[s]), ((it / kStages) & 1) ^ 1)) {
+              atomicOr(err, kErrWait);
+              *abort_v = 1;
+              break;
+            }
+            const uint32_t fb = smem_u32(&bar_full[s]);
+            mbar_expect_tx(fb, kABytes + kBBytes);
+            tma_load_2d(sA + s * kABytes, &ma, fb, (kt0 + i) * kBK, m0);
+            tma_load_2d(sB + s * kBBytes, &mb, fb, (kt0 + i) * kBK, n0);
+          }
         }
       }
+    } else if (warp == 5) {
+      if (lane == 0) {
+        // MMA issuer: tile j accumulates into TMEM buffer j & 1 once the epilogue freed it
+        constexpr uint32_t idesc = mma_idesc(BN);
+        int it = 0, j = 0;
+        for (int t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x, ++j) {
+          const int b = j & 1;
+          if (j >= 2 && !mbar_wait(smem_u32(&bar_tempty[b]), ((j >> 1) & 1) ^ 1)) {
+            atomicOr(err, kErrWait);
+            *abort_v = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t acc = tmem + static_cast<uint32_t>(b * BN);
+          for (int i = 0; i < nkt; ++i, ++it) {
+            const int s = it % kStages;
+            if (!mbar_wait(smem_u32(&bar_full[s]), (it / kStages) & 1)) {
+              atomicOr(err, kErrWait);
+              *abort_v = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              const uint64_t da = sw128_desc(sA + s * kABytes + kk * 32);
+              const uint64_t db = sw128_desc(sB + s * kBBytes + kk * 32);
+              umma_bf16(acc, da, db, idesc, (i | kk) != 0 ? 1u : 0u);
+            }
+            umma_commit(smem_u32(&bar_empty[s]));
+          }
+          umma_commit(smem_u32(&bar_tfull[b]));
+        }
+      }
+    } else {
+      // epilogue warps 0-3
+      int j = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+        const int b = j & 1;
+        bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[b]), (j >> 1) & 1);
+        ok = __all_sync(0xFFFFFFFFu, ok);
+        if (!ok) {
+          if (lane == 0) atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int m0 = (t % mt) * kBM, n0 = (t / mt) * BN;
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(b * BN);
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 8) {
+          float v[8];
+          tmem_ld8(tbase + static_cast<uint32_t>(c), v);
+          if (row >= M) continue;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int n = n0 + c + q;
+            if (n >= N) continue;
+            float x = v[q];
+            if (epi.bias) x += epi.bias[n];
+            if (epi.relu) x = fmaxf(x, 0.0f);
+            const long long idx = epi.transposed ? static_cast<long long>(n) * epi.ldo + row
+                                                 : static_cast<long long>(row) * epi.ldo + n;
+            if (epi.atomic) {
+              atomicAdd(static_cast<float*>(epi.out) + idx, x);
+            } else if (epi.out_bf16) {
+              static_cast<bf16*>(epi.out)[idx] = __float2bfloat16_rn(x);
+            } else {
+              static_cast<float*>(epi.out)[idx] = x;
+            }
+          }
+        }
+        // the buffer may take the tile after next
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[b]));
+      }
     }
   }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 2) {
+  if (warp == 5) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
   }
 }
@@ -286,6 +333,40 @@ __global__ void k_im2col(const T* __restrict__ x, int n, int h, int w, int kc, i
       v[j] = __float2bfloat16_rn(val);
     }
     *reinterpret_cast<uint4*>(col + m * kp + k0) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// conv1 (1 input channel, K = 9) on the CUDA cores: a K of 9 would fill one 64-wide tensor
+// core K step to 14%. Same arithmetic as the GEMM path: BF16-rounded snippet values and
+// weights, FP32 sums, bias, ReLU, BF16 store of Y^T[c][m].
+__global__ void __launch_bounds__(256) k_conv1(const float* __restrict__ x, int n, const float* __restrict__ w,
+                                               const float* __restrict__ bias, bf16* __restrict__ yT) {
+  __shared__ float ws[16 * 9], bs[16];
+  for (int i = threadIdx.x; i < 16 * 9; i += blockDim.x) ws[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+  if (threadIdx.x < 16) bs[threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  constexpr int hw = kH * kW;
+  const long long mtot = static_cast<long long>(n) * hw;
+  for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < mtot;
+       m += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long b = m / hw;
+    const int yx = static_cast<int>(m - b * hw);
+    const int yy = yx / kW, xx = yx - yy * kW;
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int sy = yy + k / 3 - 1, sx = xx + k % 3 - 1;
+      v[k] = (sy >= 0 && sy < kH && sx >= 0 && sx < kW)
+                 ? __bfloat162float(__float2bfloat16_rn(x[b * hw + sy * kW + sx]))
+                 : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float a = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a = fmaf(ws[c * 9 + k], v[k], a);
+      yT[c * mtot + m] = __float2bfloat16_rn(fmaxf(a + bs[c], 0.0f));
+    }
   }
 }
 
@@ -408,16 +489,18 @@ __global__ void k_col2im(const float* __restrict__ dcol, int ldc, int cin, int n
   }
 }
 
-// fc2, the loss and its gradient, one warp per sample. Forward only when y is null.
+// fc1's bias and ReLU, fc2, the loss and its gradient, one warp per sample. Forward only
+// when y is null.
 __global__ void k_head(const float* __restrict__ hf, const float* __restrict__ params, int n,
                        const float* __restrict__ y, float* __restrict__ logits, float* __restrict__ grads,
                        float* __restrict__ loss, bf16* __restrict__ dh, bf16* __restrict__ dhT, int ldt) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const float* wf2 = params + kOffWf2;
-  const float* hrow = hf + static_cast<long long>(warp) * kHid;
+  const float* bf1 = params + kOffBf1;
+  const float* hrow = hf + static_cast<long long>(warp) * kHid;  // fc1 pre-activation without bias
   float s = 0.0f;
-  for (int j = lane; j < kHid; j += 32) s += hrow[j] * wf2[j];
+  for (int j = lane; j < kHid; j += 32) s += fmaxf(hrow[j] + bf1[j], 0.0f) * wf2[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
   const float z = s + params[kOffBf2];
@@ -433,7 +516,7 @@ __global__ void k_head(const float* __restrict__ hf, const float* __restrict__ p
     atomicAdd(grads + kOffBf2, dz);
   }
   for (int j = lane; j < kHid; j += 32) {
-    const float hv = hrow[j];
+    const float hv = fmaxf(hrow[j] + bf1[j], 0.0f);
     atomicAdd(grads + kOffWf2 + j, dz * hv);
     const float g = (hv > 0.0f) ? dz * wf2[j] : 0.0f;
     atomicAdd(grads + kOffBf1 + j, g);
@@ -590,8 +673,13 @@ cudaError_t launch_gemm_bn(const CUtensorMap& ma, const CUtensorMap& mb, int M, 
   const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, nz);
-  k_gemm<BN><<<grid, 128, smem, s>>>(ma, mb, M, N, ktiles, per, epi, err);
+  // persistent CTAs: as many as fit on the GPU at once (shared memory bounds it), spread
+  // over the K splits; each walks its share of the output tiles
+  const long long tiles = 1LL * ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
+  const int per_sm = std::max(1, (227 * 1024) / smem);
+  const long long want = std::max<long long>(1, (152LL * per_sm) / nz);
+  dim3 grid(static_cast<unsigned>(std::min(tiles, want)), 1, nz);
+  k_gemm<BN><<<grid, 192, smem, s>>>(ma, mb, M, N, ktiles, per, epi, err);
   return cudaGetLastError();
 }
 
@@ -663,7 +751,7 @@ void layout(Sifter& f) {
     const long long m = B * c.h * c.w;
     f.o.wb[l] = take(2ull * c.cout * c.kp);
     f.o.wT[l] = take(2ull * c.kc * 64);
-    f.o.col[l] = take(2ull * m * c.kp);
+    f.o.col[l] = take(l > 0 ? 2ull * m * c.kp : 0);  // conv1 runs without im2col
     f.o.yT[l] = take(2ull * c.cout * m);
     f.o.p[l] = take(2ull * c.cout * m / 4);
     f.o.am[l] = take(1ull * c.cout * m / 4);
@@ -735,24 +823,32 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
   for (int l = 0; l < 3; ++l) {
     const ConvL& c = kConv[l];
     const long long m = 1LL * n * c.h * c.w;
-    bf16* col = at<bf16>(f, f.o.col[l]);
     if (l == 0) {
-      k_im2col<float><<<grid_for(m * c.kp / 8), 256, 0, s>>>(x, n, c.h, c.w, c.kc, c.kp, col);
+      k_conv1<<<grid_for(m), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]));
+      f.launches++;
     } else {
+      bf16* col = at<bf16>(f, f.o.col[l]);
       k_im2col<bf16><<<grid_for(m * c.kp / 8), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, c.kp, col);
+      f.launches++;
+      Epi e{P + kOffB[l], 1, at<bf16>(f, f.o.yT[l]), 1, 1, 0, m};
+      int rc = gemm(col, c.kp, at<bf16>(f, f.o.wb[l]), c.kp, static_cast<int>(m), c.cout, c.kp, e, 1, err, s,
+                    &f.launches);
+      if (rc) return rc;
     }
-    f.launches++;
-    Epi e{P + kOffB[l], 1, at<bf16>(f, f.o.yT[l]), 1, 1, 0, m};
-    int rc = gemm(col, c.kp, at<bf16>(f, f.o.wb[l]), c.kp, static_cast<int>(m), c.cout, c.kp, e, 1, err, s, &f.launches);
-    if (rc) return rc;
     const long long pooled = m / 4 * c.cout;
     k_pool<<<grid_for(pooled), 256, 0, s>>>(at<bf16>(f, f.o.yT[l]), c.cout, n, c.h, c.w,
                                              l < 2 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3),
                                              at<bf16>(f, f.o.p3T), f.bm, l < 2 ? 1 : 0, at<uint8_t>(f, f.o.am[l]));
     f.launches++;
   }
-  Epi e{P + kOffBf1, 1, at<float>(f, f.o.hf), 0, 0, 0, kHid};
-  return gemm(at<bf16>(f, f.o.p3), kFeat, at<bf16>(f, f.o.wf1b), kFeat, n, kHid, kFeat, e, 1, err, s, &f.launches);
+  // fc1 pre-activation (bias and ReLU are applied where it is read, in k_head), K split
+  // over CTAs: only ceil(n / 128) output tiles exist
+  if (cudaMemsetAsync(at<float>(f, f.o.hf), 0, 4ull * n * kHid, s) != cudaSuccess) return SND_ERR_CUDA;
+  Epi e{nullptr, 0, at<float>(f, f.o.hf), 0, 0, 1, kHid};
+  const int mtiles = (n + kBM - 1) / kBM;
+  const int splits = std::max(1, std::min(kFeat / kBK, 2 * 152 / mtiles));
+  return gemm(at<bf16>(f, f.o.p3), kFeat, at<bf16>(f, f.o.wf1b), kFeat, n, kHid, kFeat, e, splits, err, s,
+              &f.launches);
 }
 
 // gradients of the mean loss over n snippets into the grads vector (zeroed here)

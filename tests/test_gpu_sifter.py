@@ -30,6 +30,8 @@ def _bf16(shape, gen, pitch=None):
     (1000, 9, 640, None, 4),     # split K with atomic accumulation
     (64, 1024, 128, None, 1),
     (128, 200, 4096, None, 7),
+    (89600, 64, 192, None, 1),   # 700 output tiles: persistent CTAs, both TMEM buffers reused
+    (5000, 144, 4096, None, 5),  # many tiles and split K together
 ])
 def test_gemm_tc_matches_fp32_reference(m, n, k, pitch, splits):
     gen = torch.Generator().manual_seed(m * 7 + n * 3 + k)
