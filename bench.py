@@ -213,11 +213,13 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------------------
 
 def multirate_rate(g, args, dev, stream, dchunks, freqs, dms, mode=("graded", 1), s_max=16):
-    """Multi-rate search of the same beam (graded mode, bands up to S = 16 as in Table S1),
-    timed beside the single-rate plan of the same mode: native DM-samples per second."""
+    """Multi-rate search of the same beam (graded mode, bands up to S = 16 as in Table S1;
+    each chunk's scrunching and band stages replayed as one CUDA graph), timed beside the
+    single-rate plan of the same mode: native DM-samples per second."""
     import torch
     m = g.MultiRatePlan(freqs, synth.NC_DT, dms, BRANCHING, mode[1], g.options(mode[1], max_chunk=W.chunk),
                         s_max=s_max, device=dev)
+    m.set_graph(True)
     single = g.Plan(freqs, synth.NC_DT, dms, BRANCHING, mode[1], g.options(mode[1], max_chunk=W.chunk), device=dev)
     steps = max(1, min(args.steps, 5))
     out = {"mode": mode[0], "s_max": s_max, "bands": [[s, n] for s, n in zip(m.scrunch, m.band_ndm)]}

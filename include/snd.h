@@ -261,6 +261,9 @@ int snd_multirate_bind_workspace(snd_multirate_t mr, void* d_workspace, size_t b
 /* Next chunk, device uint8[nsamp][nchan]; nsamp a multiple of the largest S in use, at most
    max_chunk (else SND_ERR_CHUNK). Enqueued on `stream`, no host synchronisation. */
 int snd_multirate_execute(snd_multirate_t mr, const uint8_t* d_chunk, int32_t nsamp, void* stream);
+/* Replay each chunk's work (scrunching and every band's stages) as one CUDA graph, updated
+   in place from chunk to chunk (enable != 0), or launch it directly (0, the default). */
+int snd_multirate_set_graph(snd_multirate_t mr, int32_t enable);
 /* Same for a host chunk, copied into the workspace first (cudaMemcpyAsync on `stream`). */
 int snd_multirate_execute_host(snd_multirate_t mr, const uint8_t* h_chunk, int32_t nsamp, void* stream);
 /* Merge the candidates of all bands found since the previous call (on the GPU), copy at most

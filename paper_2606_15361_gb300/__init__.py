@@ -67,7 +67,7 @@ EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", 
            "snd_profile", "snd_profile_read", "snd_encode_static", "snd_destroy", "snd_error_string",
            "snd_multirate_plan", "snd_multirate_info", "snd_multirate_band_plan", "snd_multirate_workspace_size",
            "snd_multirate_bind_workspace", "snd_multirate_execute", "snd_multirate_execute_host",
-           "snd_multirate_candidates", "snd_multirate_destroy",
+           "snd_multirate_candidates", "snd_multirate_destroy", "snd_multirate_set_graph",
            "snd_sifter_create", "snd_sifter_num_params", "snd_sifter_workspace_size", "snd_sifter_bind_workspace",
            "snd_sifter_set_params", "snd_sifter_get_params", "snd_sifter_forward", "snd_sifter_gradients",
            "snd_sifter_train_step", "snd_sifter_status", "snd_sifter_launches", "snd_sifter_destroy", "snd_snippets",
@@ -112,6 +112,8 @@ def _load():
     lib.snd_multirate_execute.argtypes = [P, V, I32, V]
     lib.snd_multirate_execute_host.argtypes = [P, V, I32, V]
     lib.snd_multirate_candidates.argtypes = [P, ctypes.POINTER(SndCandidate), I32, ip]
+    lib.snd_multirate_set_graph.argtypes = [P, I32]
+    lib.snd_multirate_set_graph.restype = ctypes.c_int
     lib.snd_multirate_destroy.argtypes = [P]
     lib.snd_multirate_destroy.restype = None
     fp = ctypes.POINTER(ctypes.c_float)
@@ -339,6 +341,9 @@ class MultiRatePlan:
     @property
     def workspace_bytes(self) -> int:
         return int(lib.snd_multirate_workspace_size(self.handle))
+
+    def set_graph(self, enable: bool):
+        _check(lib.snd_multirate_set_graph(self.handle, int(bool(enable))), "snd_multirate_set_graph")
 
     def band_plan(self, i: int) -> Plan:
         """Borrowed view of band i's plan (stats, profile, delay table)."""

@@ -12,6 +12,7 @@
 // graph.
 
 #include <algorithm>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -19,59 +20,89 @@
 
 using snd::Plan;
 
-namespace {
+namespace snd {
 
-struct Batch {
-  std::vector<Plan*> plans;
-  bool graph = false;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t capture = nullptr;  // private stream the steps are captured on
-  int64_t graph_updates = 0, graph_instantiations = 0;
-  int sticky = 0;
-  ~Batch() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (capture) cudaStreamDestroy(capture);
-  }
-};
-
-// enqueue one step of every beam on s; the plans record `owner` as the stream their work
-// runs on (the caller's stream, also when s is the capture stream)
-int enqueue_step(Batch& b, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
-                 cudaStream_t owner) {
-  const int n = static_cast<int>(b.plans.size());
-  std::vector<snd::ChunkPos> pos(n);
+int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
+                  cudaStream_t owner) {
+  std::vector<ChunkPos> pos(n);
   std::vector<const Plan*> tp;
   std::vector<int64_t> ep, en;
   for (int i = 0; i < n; ++i) {
-    Plan& p = *b.plans[i];
-    pos[i] = snd::chunk_pos(p, nsamp[i]);
-    if (snd::launch_encode(p, d_chunks[i], nsamp[i], s) != cudaSuccess) return SND_ERR_CUDA;
+    Plan& p = *plans[i];
+    pos[i] = chunk_pos(p, nsamp[i]);
+    if (launch_encode(p, d_chunks[i], nsamp[i], s) != cudaSuccess) return SND_ERR_CUDA;
   }
   for (int i = 0; i < n; ++i) {
-    Plan& p = *b.plans[i];
+    Plan& p = *plans[i];
     if (pos[i].e_new <= pos[i].e_prev) continue;
     if (p.mode == SND_MODE_ZFLOAT) {
-      if (snd::launch_tree_z(p, pos[i].e_prev, pos[i].e_new, nullptr, s) != cudaSuccess) return SND_ERR_CUDA;
+      if (launch_tree_z(p, pos[i].e_prev, pos[i].e_new, nullptr, s) != cudaSuccess) return SND_ERR_CUDA;
     } else if (p.flags & SND_FLAG_REFERENCE_TREE) {
-      if (snd::launch_tree(p, pos[i].e_prev, pos[i].e_new, s) != cudaSuccess) return SND_ERR_CUDA;
+      if (launch_tree(p, pos[i].e_prev, pos[i].e_new, s) != cudaSuccess) return SND_ERR_CUDA;
     } else {
       tp.push_back(&p);
       ep.push_back(pos[i].e_prev);
       en.push_back(pos[i].e_new);
     }
   }
-  if (!tp.empty() &&
-      snd::launch_tree_batch(tp.data(), ep.data(), en.data(), static_cast<int>(tp.size()), s) != cudaSuccess)
+  if (!tp.empty() && launch_tree_batch(tp.data(), ep.data(), en.data(), static_cast<int>(tp.size()), s) != cudaSuccess)
     return SND_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
-    Plan& p = *b.plans[i];
+    Plan& p = *plans[i];
     if (p.mode == SND_MODE_ZFLOAT) continue;
-    if (snd::chunk_post(p, pos[i], nullptr, s, [](int, auto&& f) { return f(); }) != cudaSuccess)
-      return SND_ERR_CUDA;
+    if (chunk_post(p, pos[i], nullptr, s, [](int, auto&& f) { return f(); }) != cudaSuccess) return SND_ERR_CUDA;
   }
-  for (int i = 0; i < n; ++i) snd::chunk_commit(*b.plans[i], pos[i], nsamp[i], owner);
+  for (int i = 0; i < n; ++i) chunk_commit(*plans[i], pos[i], nsamp[i], owner);
   return SND_OK;
 }
+
+int GraphRunner::run(cudaStream_t s, const std::function<int(cudaStream_t)>& enqueue) {
+  // capture on a private stream (the caller's may be the legacy default stream, which cannot
+  // be captured); the graph is then launched on the caller's stream, in its order
+  if (!capture && cudaStreamCreateWithFlags(&capture, cudaStreamNonBlocking) != cudaSuccess) return SND_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SND_ERR_CUDA;
+  const int rc = enqueue(capture);
+  const cudaError_t ec = cudaStreamEndCapture(capture, &g);
+  if (rc || ec != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    return rc ? rc : SND_ERR_CUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  if (exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(exec, g, &info) != cudaSuccess) {
+      cudaGetLastError();  // an update that does not apply is not an error: instantiate anew
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    } else {
+      ++updates;
+    }
+  }
+  if (!exec) {
+    e = cudaGraphInstantiate(&exec, g, 0);
+    ++instantiations;
+  }
+  cudaGraphDestroy(g);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
+GraphRunner::~GraphRunner() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (capture) cudaStreamDestroy(capture);
+}
+
+}  // namespace snd
+
+namespace {
+
+struct Batch {
+  std::vector<Plan*> plans;
+  bool graph = false;
+  snd::GraphRunner runner;
+  int sticky = 0;
+};
 
 int fail(Batch& b, int code) {
   if (!b.sticky) b.sticky = code;
@@ -120,48 +151,20 @@ extern "C" int snd_batch_execute(snd_batch_t h, const uint8_t* const* d_chunks, 
     if (p.profiling) return SND_ERR_STATE;  // per-stage events are not recorded in a batch
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!b.graph) {
-    const int rc = enqueue_step(b, d_chunks, nsamp, s, s);
-    return rc ? fail(b, rc) : SND_OK;
-  }
-  // capture on a private stream (the caller's may be the legacy default stream, which cannot
-  // be captured); the graph is then launched on the caller's stream, in its order
-  if (!b.capture && cudaStreamCreateWithFlags(&b.capture, cudaStreamNonBlocking) != cudaSuccess)
-    return fail(b, SND_ERR_CUDA);
-  cudaGraph_t g = nullptr;
-  if (cudaStreamBeginCapture(b.capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    return fail(b, SND_ERR_CUDA);
-  const int rc = enqueue_step(b, d_chunks, nsamp, b.capture, s);
-  const cudaError_t ec = cudaStreamEndCapture(b.capture, &g);
-  if (rc || ec != cudaSuccess || !g) {
-    if (g) cudaGraphDestroy(g);
-    return fail(b, rc ? rc : SND_ERR_CUDA);
-  }
-  cudaError_t e = cudaSuccess;
-  if (b.exec) {
-    cudaGraphExecUpdateResultInfo info;
-    if (cudaGraphExecUpdate(b.exec, g, &info) != cudaSuccess) {
-      cudaGetLastError();  // an update that does not apply is not an error: instantiate anew
-      cudaGraphExecDestroy(b.exec);
-      b.exec = nullptr;
-    } else {
-      ++b.graph_updates;
-    }
-  }
-  if (!b.exec) {
-    e = cudaGraphInstantiate(&b.exec, g, 0);
-    ++b.graph_instantiations;
-  }
-  cudaGraphDestroy(g);
-  if (e == cudaSuccess) e = cudaGraphLaunch(b.exec, s);
-  return e == cudaSuccess ? SND_OK : fail(b, SND_ERR_CUDA);
+  Plan* const* plans = b.plans.data();
+  const int n = static_cast<int>(b.plans.size());
+  const int rc = b.graph ? b.runner.run(s, [&](cudaStream_t cs) {
+    return snd::enqueue_plans(plans, n, d_chunks, nsamp, cs, s);
+  })
+                         : snd::enqueue_plans(plans, n, d_chunks, nsamp, s, s);
+  return rc ? fail(b, rc) : SND_OK;
 }
 
 extern "C" int snd_batch_graph_stats(snd_batch_t h, int64_t* instantiations, int64_t* updates) {
   if (!h) return SND_ERR_ARG;
   const Batch& b = *reinterpret_cast<Batch*>(h);
-  if (instantiations) *instantiations = b.graph_instantiations;
-  if (updates) *updates = b.graph_updates;
+  if (instantiations) *instantiations = b.runner.instantiations;
+  if (updates) *updates = b.runner.updates;
   return SND_OK;
 }
 

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -42,6 +43,8 @@ struct MultiRate {
   size_t off_all = 0, off_parent = 0, off_best = 0, off_tie = 0, off_out = 0, off_cnt = 0, off_dm = 0, off_native = 0;
   void* ws = nullptr;
   bool bound = false;
+  bool graph = false;
+  snd::GraphRunner runner;
   cudaStream_t last_stream = nullptr;
   int sticky = 0;
 };
@@ -320,22 +323,37 @@ extern "C" int snd_multirate_bind_workspace(snd_multirate_t h, void* d_ws, size_
 
 namespace {
 
-int run_bands(MultiRate& m, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s) {
+// scrunch the chunk for every band with S > 1, then one step of all band plans (their trees
+// grouped into shared launches), enqueued on s
+int enqueue_bands(MultiRate& m, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s, cudaStream_t owner) {
   char* base = static_cast<char*>(m.ws);
+  std::vector<Plan*> plans;
+  std::vector<const uint8_t*> src;
+  std::vector<int32_t> ns;
   for (auto& b : m.bands) {
-    const uint8_t* src = d_chunk;
+    const uint8_t* in = d_chunk;
     if (b.S > 1) {
       uint8_t* st = reinterpret_cast<uint8_t*>(base + b.off_staging);
       const int nout = nsamp / b.S;
       const size_t total = static_cast<size_t>(nout) * m.nchan;
       const int blocks = static_cast<int>(std::min<size_t>((total + 255) / 256, 152 * 16));
       k_scrunch<<<blocks, 256, 0, s>>>(d_chunk, nout, m.nchan, b.S, st);
-      if (cudaGetLastError() != cudaSuccess) return fail(m, SND_ERR_CUDA);
-      src = st;
+      if (cudaGetLastError() != cudaSuccess) return SND_ERR_CUDA;
+      in = st;
     }
-    const int rc = snd_execute(b.plan, src, nsamp / b.S, s, nullptr, nullptr);
-    if (rc) return fail(m, rc);
+    Plan& p = *reinterpret_cast<Plan*>(b.plan);
+    if (p.sticky) return p.sticky;
+    plans.push_back(&p);
+    src.push_back(in);
+    ns.push_back(nsamp / b.S);
   }
+  return snd::enqueue_plans(plans.data(), static_cast<int>(plans.size()), src.data(), ns.data(), s, owner);
+}
+
+int run_bands(MultiRate& m, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s) {
+  const int rc = m.graph ? m.runner.run(s, [&](cudaStream_t cs) { return enqueue_bands(m, d_chunk, nsamp, cs, s); })
+                         : enqueue_bands(m, d_chunk, nsamp, s, s);
+  if (rc) return fail(m, rc);
   m.last_stream = s;
   return SND_OK;
 }
@@ -369,6 +387,12 @@ extern "C" int snd_multirate_execute_host(snd_multirate_t h, const uint8_t* h_ch
       cudaSuccess)
     return fail(m, SND_ERR_CUDA);
   return run_bands(m, native, nsamp, s);
+}
+
+extern "C" int snd_multirate_set_graph(snd_multirate_t h, int32_t enable) {
+  if (!h) return SND_ERR_ARG;
+  reinterpret_cast<MultiRate*>(h)->graph = enable != 0;
+  return SND_OK;
 }
 
 extern "C" int snd_multirate_band_plan(snd_multirate_t h, int32_t band, snd_plan_t* out) {

@@ -526,21 +526,29 @@ __global__ void k_head(const float* __restrict__ hf, const float* __restrict__ p
   }
 }
 
-// db[c] += sum_m dyT[c][m] (one block per channel)
-__global__ void k_rowsum(const bf16* __restrict__ dyT, long long mtot, float* __restrict__ out) {
-  const int c = blockIdx.x;
+// db[c] += sum_m dyT[c][m]: blockIdx.y = channel, blocks along x take contiguous slices
+// (16-byte loads of 8 values) and add their partial sums atomically.
+__global__ void __launch_bounds__(256) k_rowsum(const bf16* __restrict__ dyT, long long mtot, float* __restrict__ out) {
+  const int c = blockIdx.y;
+  const bf16* row = dyT + c * mtot;
+  const long long nvec = mtot / 8;  // mtot is a multiple of 8 (n * h * w)
   float s = 0.0f;
-  for (long long m = threadIdx.x; m < mtot; m += blockDim.x) s += __bfloat162float(dyT[c * mtot + m]);
-  __shared__ float red[32];
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < nvec;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const uint4 q = *reinterpret_cast<const uint4*>(row + 8 * i);
+    const bf16* v = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += __bfloat162float(v[k]);
+  }
+  __shared__ float red[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if (threadIdx.x == 0) out[c] += s;
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(out + c, t);
   }
 }
 
@@ -895,7 +903,10 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     Epi ew{nullptr, 0, G + kOffW[l], 0, 0, 1, c.kc};
     int rc = gemm(dyT, m, colT, m, c.cout, c.kc, m, ew, splits, err, s, &f.launches);
     if (rc) return rc;
-    k_rowsum<<<c.cout, 256, 0, s>>>(dyT, m, G + kOffB[l]);
+    {
+      const long long nb = std::min<long long>(std::max<long long>(1, m / 8 / 256 / 8), 4 * 152 / c.cout + 1);
+      k_rowsum<<<dim3(static_cast<unsigned>(nb), c.cout), 256, 0, s>>>(dyT, m, G + kOffB[l]);
+    }
     f.launches++;
     if (l == 0) break;
     // input gradient through the convolution, then back to the previous pooled map

@@ -5,6 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -210,6 +211,21 @@ cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_
 TreeShape tree_shape(int mode, int nlev, int kmax);  // k_tree launch shape
 cudaError_t launch_tree_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
                               cudaStream_t s);
+// batch.cu: one chunk of each plan (encoders, grouped tree launches, matched filter and
+// candidates), enqueued on s; the plans then record `owner` as their stream
+int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
+                  cudaStream_t owner);
+
+// Replays enqueued work as a CUDA graph: captured on a private stream, updated in place from
+// call to call while the topology is unchanged, launched on the caller's stream.
+struct GraphRunner {
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t instantiations = 0, updates = 0;
+  int run(cudaStream_t s, const std::function<int(cudaStream_t)>& enqueue);
+  ~GraphRunner();
+};
+
 cudaError_t launch_tree_z(const Plan& p, int64_t e_prev, int64_t e_new, void* d_plane_out, cudaStream_t s);
 
 template <typename Stage>

@@ -36,8 +36,9 @@ def _oracle_tuples(lst):
     return [(int(c[0]), int(c[2]), float(c[3]), int(c[4]), int(c[5])) for c in lst]
 
 
-def run_both(freqs, dt, dms, mode, cfg, chunks, s_max=64, host=False, reads=None, **optkw):
+def run_both(freqs, dt, dms, mode, cfg, chunks, s_max=64, host=False, reads=None, graph=False, **optkw):
     plan = g.MultiRatePlan(freqs, dt, dms, cfg.branching, mode, _opts(mode, cfg, **optkw), s_max=s_max)
+    plan.set_graph(graph)
     ref = omr.MultiRateStream(freqs, dt, dms, cfg, s_max=s_max)
     assert plan.scrunch == [s for s, _ in ref.bands]
     assert plan.band_ndm == [len(idx) for _, idx in ref.bands]
@@ -127,10 +128,11 @@ def test_multirate_merges_across_bands_64ch(mode):
 
 @pytest.mark.parametrize("mode", list(MODES))
 def test_multirate_256ch_five_bands(mode):
-    """256 channels, 256 DMs up to 1000 (bands S = 1..16), three chunks, B = 4."""
+    """256 channels, 256 DMs up to 1000 (bands S = 1..16), three chunks, B = 4; float mode
+    replays every chunk through a CUDA graph."""
     f, dms, chunks = _burst_chunks(11, 256, 1000.0, 256, 3, 24, fwhm_range=(2.0, 60.0), snr_range=(9.0, 30.0),
                                    log_fwhm=True)
     cfg = ostream.defaults(MODES[mode], branching=4)
-    got = run_both(f, synth.NC_DT, dms, MODES[mode], cfg, chunks, s_max=16)
+    got = run_both(f, synth.NC_DT, dms, MODES[mode], cfg, chunks, s_max=16, graph=(mode == "float"))
     if mode != "binary":
         assert len(got[0]) >= 10
