@@ -404,45 +404,74 @@ def run_gpu(args, rank, world, local_rank):
     plans = {name: g.Plan(freqs, synth.NC_DT, dms, BRANCHING, m, g.options(m, max_chunk=W.chunk), device=dev)
              for name, m in MODES}
     stream = torch.cuda.current_stream(dev)
+    # the three modes are independent, so by default each plan runs on its own stream and one
+    # mode's small matched-filter and candidate kernels overlap another mode's tree
+    mstreams = {name: torch.cuda.Stream(dev) for name, _ in MODES}
 
-    def step(host: bool):
+    def step(host: bool, concurrent: bool):
+        if concurrent:
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            for name, _ in MODES:
+                mstreams[name].wait_event(ev)
         for name, _ in MODES:
             p = plans[name]
+            st = mstreams[name] if concurrent else stream
             for i in range(W.nchunks):
                 if host:
-                    p.execute_host(pinned[i])
+                    p.execute_host(pinned[i], stream=st)
                 else:
-                    p.execute(dchunks[i])
+                    p.execute(dchunks[i], stream=st)
+        if concurrent:
+            for name, _ in MODES:
+                done = torch.cuda.Event()
+                done.record(mstreams[name])
+                stream.wait_event(done)
 
     def sync():
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
 
+    concurrent = not args.sequential
     # warm-up (also fills the rings: from then on every chunk emits W.chunk samples per row)
     for _ in range(max(args.warmup, 1)):
-        step(False)
+        step(False, concurrent)
     for p in plans.values():
         p.candidates(check=False)
     sync()
-    launches0 = {n: p.stats().kernel_launches for n, p in plans.items()}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # pass 1, modes in sequence on one stream, per-stage CUDA events: every launch's duration
+    # is its own (the roofline and the per-mode stage times)
     for p in plans.values():
         p.profile(True)
         p.profile_read()
+    sync()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(False, False)
+    ev1.record(stream)
+    sync()
+    ms_seq = ev0.elapsed_time(ev1)
+    prof = {n: p.profile_read() for n, p in plans.items()}
+    for p in plans.values():
+        p.profile(False)
+    for p in plans.values():
+        p.candidates(check=False)
+
+    # pass 2, the headline: the three modes on their own streams
+    launches0 = {n: p.stats().kernel_launches for n, p in plans.items()}
     clocks = ClockSampler(local_rank)
     clocks.start()
     sync()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(False)
+        step(False, concurrent)
     ev1.record(stream)
     sync()
     ms_dev = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    prof = {n: p.profile_read() for n, p in plans.items()}
-    for p in plans.values():
-        p.profile(False)
     launches = sum(p.stats().kernel_launches - launches0[n] for n, p in plans.items())
     ncands = sum(len(p.candidates(check=False)[0]) for p in plans.values())
 
@@ -454,7 +483,7 @@ def run_gpu(args, rank, world, local_rank):
     ev0.record(stream)
     d2h = 0
     for _ in range(args.steps):
-        step(True)
+        step(True, concurrent)
         for p in plans.values():
             c, _ = p.candidates(check=False)
             d2h += c.nbytes + 8
@@ -469,7 +498,7 @@ def run_gpu(args, rank, world, local_rank):
     mb = multibeam_rate(g, args, dev) if extras and not args.no_multibeam else None
 
     per_step = len(MODES) * W.nchunks * W.chunk * W.ndm   # DM-samples per step per GPU
-    ms_dev, ms_e2e = reduce_max([ms_dev, ms_e2e], dist, dev)
+    ms_dev, ms_e2e, ms_seq = reduce_max([ms_dev, ms_e2e, ms_seq], dist, dev)
     value = whole_job_rate(per_step, args.steps, world, ms_dev)
     e2e = whole_job_rate(per_step, args.steps, world, ms_e2e)
     if rank != 0:
@@ -508,13 +537,18 @@ def run_gpu(args, rank, world, local_rank):
                                "16 x 16384-sample chunks per step, B=8, modes binary+graded+float (Table S1)",
                    "branching": BRANCHING, "chunk": W.chunk, "chunks_per_step": W.nchunks,
                    "l2": "inputs larger than L2 (16 chunks = 268 MB uint8 per step, 129 MB L2)",
-                   "parallelism": f"beam replicas x{world}"},
+                   "parallelism": f"beam replicas x{world}",
+                   "streams": "one per mode" if concurrent else "one"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": "k_tree (SND tree, all modes, average launch)",
+                     "kernel": "k_tree (SND tree, all modes, average launch, sequential pass)",
                      "peak_source": src, "algorithmic_bytes_per_dm_sample": TREE_BYTES_PER_DM_SAMPLE},
         "per_mode": per_mode,
+        "sequential_pass": {"value": whole_job_rate(per_step, args.steps, world, ms_seq), "unit": "DM-samples/s",
+                            "ms_per_step": ms_seq / args.steps,
+                            "note": "modes in sequence on one stream with per-stage events; the roofline "
+                                    "and per_mode stage times come from this pass"},
         "e2e": {"value": e2e, "unit": "DM-samples/s",
                 "h2d_bytes_per_step": len(MODES) * W.nchunks * W.chunk * W.nchan,
                 "d2h_bytes_per_step": int(d2h / max(args.steps, 1))},
@@ -580,6 +614,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sifter", action="store_true", help="skip the learned-sifter measurements")
     ap.add_argument("--no-multibeam", action="store_true", help="skip the 48-beam batch measurements")
+    ap.add_argument("--sequential", action="store_true",
+                    help="headline pass with the three modes in sequence on one stream (default: own streams)")
     ap.add_argument("--main-only", action="store_true",
                     help="only the headline workload: no multi-rate, labelled-payload, sifter or multi-beam parts")
     ap.add_argument("--drive", choices=[m for m, _ in MODES] + ["zfloat", "zfloat16", "sifter"],
