@@ -4,8 +4,9 @@
 // The tree, the dominant stage, runs as few launches as possible: beams whose plans share
 // a kernel instantiation and block shape go into one k_tree_multi launch, whose CTAs are
 // spread over the beams by a prefix of their tile counts (the per-beam arguments travel by
-// value in the launch's parameter block). The encoder, matched filter and candidate stages
-// run per beam, in beam order, on the same stream. With graphs enabled the whole step is
+// value in the launch's parameter block). The encoders, and then the matched filter and
+// candidate stages, run per beam spread over four side streams forked from and joined back
+// to the caller's stream around the tree launches. With graphs enabled the whole step is
 // captured on a private stream and launched as one CUDA graph on the caller's stream; the
 // next step's capture updates the instantiated graph in place (cudaGraphExecUpdate)
 // whenever the topology is unchanged, so a steady stream of chunks re-uses one executable
@@ -22,16 +23,57 @@ using snd::Plan;
 
 namespace snd {
 
+int ForkJoin::init(int n) {
+  if (!streams.empty()) return SND_OK;
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SND_ERR_CUDA;
+    streams.push_back(st);
+  }
+  for (int i = 0; i < 2 * n; ++i) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SND_ERR_CUDA;
+    events.push_back(e);
+  }
+  return SND_OK;
+}
+
+cudaError_t ForkJoin::fork(cudaStream_t main) {
+  const size_t n = streams.size();
+  cudaError_t e = cudaEventRecord(events[0], main);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(streams[i], events[0], 0);
+  return e;
+}
+
+cudaError_t ForkJoin::join(cudaStream_t main) {
+  const size_t n = streams.size();
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(events[n + i], streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(main, events[n + i], 0);
+  }
+  return e;
+}
+
+ForkJoin::~ForkJoin() {
+  for (cudaEvent_t e : events) cudaEventDestroy(e);
+  for (cudaStream_t st : streams) cudaStreamDestroy(st);
+}
+
 int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
-                  cudaStream_t owner) {
+                  cudaStream_t owner, ForkJoin* fj) {
   std::vector<ChunkPos> pos(n);
   std::vector<const Plan*> tp;
   std::vector<int64_t> ep, en;
+  const int ns = fj ? static_cast<int>(fj->streams.size()) : 0;
+  auto side = [&](int i) { return ns ? fj->streams[i % ns] : s; };
+  if (ns && fj->fork(s) != cudaSuccess) return SND_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     Plan& p = *plans[i];
     pos[i] = chunk_pos(p, nsamp[i]);
-    if (launch_encode(p, d_chunks[i], nsamp[i], s) != cudaSuccess) return SND_ERR_CUDA;
+    if (launch_encode(p, d_chunks[i], nsamp[i], side(i)) != cudaSuccess) return SND_ERR_CUDA;
   }
+  if (ns && fj->join(s) != cudaSuccess) return SND_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     Plan& p = *plans[i];
     if (pos[i].e_new <= pos[i].e_prev) continue;
@@ -47,11 +89,14 @@ int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, con
   }
   if (!tp.empty() && launch_tree_batch(tp.data(), ep.data(), en.data(), static_cast<int>(tp.size()), s) != cudaSuccess)
     return SND_ERR_CUDA;
+  if (ns && fj->fork(s) != cudaSuccess) return SND_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     Plan& p = *plans[i];
     if (p.mode == SND_MODE_ZFLOAT) continue;
-    if (chunk_post(p, pos[i], nullptr, s, [](int, auto&& f) { return f(); }) != cudaSuccess) return SND_ERR_CUDA;
+    if (chunk_post(p, pos[i], nullptr, side(i), [](int, auto&& f) { return f(); }) != cudaSuccess)
+      return SND_ERR_CUDA;
   }
+  if (ns && fj->join(s) != cudaSuccess) return SND_ERR_CUDA;
   for (int i = 0; i < n; ++i) chunk_commit(*plans[i], pos[i], nsamp[i], owner);
   return SND_OK;
 }
@@ -101,6 +146,7 @@ struct Batch {
   std::vector<Plan*> plans;
   bool graph = false;
   snd::GraphRunner runner;
+  snd::ForkJoin fj;  // side streams for the per-beam stages
   int sticky = 0;
 };
 
@@ -153,10 +199,12 @@ extern "C" int snd_batch_execute(snd_batch_t h, const uint8_t* const* d_chunks, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Plan* const* plans = b.plans.data();
   const int n = static_cast<int>(b.plans.size());
+  if (n > 1 && b.fj.init(std::min(n, 4)) != SND_OK) return fail(b, SND_ERR_CUDA);
+  snd::ForkJoin* fj = n > 1 ? &b.fj : nullptr;
   const int rc = b.graph ? b.runner.run(s, [&](cudaStream_t cs) {
-    return snd::enqueue_plans(plans, n, d_chunks, nsamp, cs, s);
+    return snd::enqueue_plans(plans, n, d_chunks, nsamp, cs, s, fj);
   })
-                         : snd::enqueue_plans(plans, n, d_chunks, nsamp, s, s);
+                         : snd::enqueue_plans(plans, n, d_chunks, nsamp, s, s, fj);
   return rc ? fail(b, rc) : SND_OK;
 }
 

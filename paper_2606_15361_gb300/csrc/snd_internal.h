@@ -211,10 +211,22 @@ cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_
 TreeShape tree_shape(int mode, int nlev, int kmax);  // k_tree launch shape
 cudaError_t launch_tree_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
                               cudaStream_t s);
+// Side streams for independent per-plan work: forked from and joined back to a main stream
+// with events (also inside a stream capture, where they become parallel graph branches).
+struct ForkJoin {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;  // one fork event + one join event per side stream
+  int init(int n);
+  cudaError_t fork(cudaStream_t main);
+  cudaError_t join(cudaStream_t main);
+  ~ForkJoin();
+};
+
 // batch.cu: one chunk of each plan (encoders, grouped tree launches, matched filter and
-// candidates), enqueued on s; the plans then record `owner` as their stream
+// candidates), enqueued on s (per-plan stages spread over fj's side streams when given);
+// the plans then record `owner` as their stream
 int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
-                  cudaStream_t owner);
+                  cudaStream_t owner, ForkJoin* fj = nullptr);
 
 // Replays enqueued work as a CUDA graph: captured on a private stream, updated in place from
 // call to call while the topology is unchanged, launched on the caller's stream.
