@@ -182,6 +182,42 @@ def oracle_sample(chunks, rows: int):
                       f"tree + matched filter on {rows} of 2048 DM rows")
 
 
+def oracle_rows_sample(chunks):
+    """The oracle timed on bounded samples of the other rows (single-threaded numpy):
+    multi-rate (the NC64 beam, all bands, graded), the labelled-payload tree (FP16 storage,
+    2 DM rows of the bench beam over one chunk) and the sifter's forward pass (4 snippets).
+    Units are each row's own: native DM-samples/s, DM-samples/s, snippets/s."""
+    from oracle import multirate as omr
+    from oracle import sifter as osf
+    from oracle import stream as ost
+    from oracle import zpayload as oz
+    out = {}
+    w = synth.NC64
+    t0 = time.perf_counter()
+    m = omr.MultiRateStream(w.freqs(), synth.NC_DT, w.dms(), ost.defaults(ost.GRADED, branching=2))
+    m.push(w.chunk_data(0))
+    m.candidates()
+    dt = time.perf_counter() - t0
+    out["multirate"] = {"value": w.ndm * w.chunk / dt, "unit": "native DM-samples/s", "cores": 1,
+                        "sample": "NC64 beam (64 ch, 128 DMs, 16384 samples), graded, bands 1/2/4/8, merge"}
+    t0 = time.perf_counter()
+    z = oz.ZStream(W.freqs(), synth.NC_DT, W.dms(), 4, BRANCHING, 1.5, np.float16, rows=[0, 1024])
+    for c in chunks[:3]:
+        z.push(c)
+    dt = time.perf_counter() - t0
+    emitted = z.E
+    out["zfloat_fp16"] = {"value": 2 * emitted / dt, "unit": "DM-samples/s", "cores": 1,
+                          "sample": "labelled payload, FP16 storage, 2 of 2048 DM rows over 3 chunks of the bench beam"}
+    rng = np.random.default_rng(1)
+    theta = osf.init_params(1)
+    x = rng.normal(size=(4, 64, 256))
+    t0 = time.perf_counter()
+    osf.forward(theta, x)
+    dt = time.perf_counter() - t0
+    out["sifter_forward"] = {"value": 4 / dt, "unit": "snippets/s", "cores": 1, "sample": "FP64 forward of 4 snippets"}
+    return out
+
+
 def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": "DM-trial samples/s", "unit": "DM-samples/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -267,8 +303,15 @@ def zfloat_rate(g, args, dev, dchunks, freqs, dms):
         p.profile(False)
         tms = prof["tree"][0] / max(prof["tree"][1], 1)
         ems = prof["encode"][0] / max(prof["encode"][1], 1)
+        es = 2 if flag else 4
+        bpu = W.nchan / W.ndm * es + 4.0  # payload ring read once per DM tile set + FP32 plane written
+        peaks, src = _peaks()
+        ach = bpu * W.chunk * W.ndm / (tms / 1e3) / 1e9
         out[name] = {"tree_ms_per_chunk": round(tms, 4), "encode_ms_per_chunk": round(ems, 4),
-                     "tree_gdm_samples_per_s": round(W.chunk * W.ndm / (tms / 1e3) / 1e9, 2)}
+                     "tree_gdm_samples_per_s": round(W.chunk * W.ndm / (tms / 1e3) / 1e9, 2),
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": ach / peaks["hbm_gbs"], "peak_source": src,
+                                  "algorithmic_bytes_per_dm_sample": bpu, "kernel": "k_tree_z"}}
     return out
 
 
@@ -309,7 +352,13 @@ def sifter_rate(g, args, dev):
     sf = g.Sifter(max_batch=256, training=True, seed=2, device=dev)
     sd.train(sf, tr, epochs=5, batch=256, lr=5e-4)
     cmp = sd.compare(sd.logits(sf, te.x, 256), te)
-    return {"infer_batch": 4096, "infer_ms_per_batch": round(inf_ms, 3),
+    peaks, src = _peaks()
+    tfl = SIFTER_FLOPS * 4096 / (inf_ms / 1e3) / 1e12
+    return {"roofline": {"bound": "tensor", "achieved": tfl, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": tfl / peaks["bf16_tflops"], "peak_source": src,
+                         "kernel": "sifter forward (k_gemm + layer kernels), batch 4096",
+                         "algorithmic_flops_per_snippet": SIFTER_FLOPS},
+            "infer_batch": 4096, "infer_ms_per_batch": round(inf_ms, 3),
             "infer_snippets_per_s": round(4096 / (inf_ms / 1e3), 1),
             "infer_tflops": round(SIFTER_FLOPS * 4096 / (inf_ms / 1e3) / 1e12, 2),
             "train_batch": 256, "train_ms_per_step": round(step_ms, 3),
@@ -527,6 +576,8 @@ def run_gpu(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         work, secs, desc = oracle_sample(host_chunks[:3], args.ref_rows)
         cpu = {"value": work / secs, "unit": "DM-samples/s", "cores": 1, "kind": "oracle", "sample": desc}
+        if not args.main_only:
+            cpu["rows"] = oracle_rows_sample(host_chunks)
     realtime_beams = e2e / (W.ndm / synth.NC_DT) / len(MODES)
     return {
         "metric": "DM-trial samples/s", "value": value, "unit": "DM-samples/s", "n_gpus": world,
