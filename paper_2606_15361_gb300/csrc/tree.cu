@@ -714,7 +714,7 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
 }
 
 #define SND_TREE_BOUNDS                                                                   \
-  __launch_bounds__((MODE != kBinary && DPW == 1 && MAXL == 4) ? 1024 : 512, \
+  __launch_bounds__((MODE != kBinary && DPW == 1 && MAXL == 4 && KW == 1) ? 1024 : 512, \
                     (MODE == kBinary && TH == 2) ? 2 : 1)
 
 template <int MODE, int MAXL, int KW, int TH, int DPW, int CT>
@@ -851,10 +851,10 @@ cudaError_t dispatch_inst(int id, F&& f) {
     case 3: return f.template go<kBinary, 4, 1, 8, 1>();
     case 4: return f.template go<kBinary, 8, 1, 8, 1>();
     case 5: return f.template go<kBinary, 16, 1, 8, 1>();
-    case 6: return f.template go<kGraded, 4, 1, 1, 1>();
+    case 6: return f.template go<kGraded, 4, 2, 1, 1>();
     case 7: return f.template go<kGraded, 8, 1, 1, 1>();
     case 8: return f.template go<kGraded, 16, 1, 1, 1>();
-    default: return f.template go<kFloat, 4, 1, 1, 1>();
+    default: return f.template go<kFloat, 4, 2, 1, 1>();
   }
 }
 
@@ -914,10 +914,10 @@ TreeShape tree_shape(int mode, int nlev, int kmax) {
   // graded / float: 32 warps x 1 DM (1024 threads, <= 64 registers) keeps 32-DM tiles at
   // twice the warps per SM of 16 warps x 2 DMs
   if (mode == SND_MODE_GRADED) {
-    if (maxl <= 4) return {32, 1, 1};
+    if (maxl <= 4) return {16, 1, 2};
     return {16, 1, 1};
   }
-  return {32, 1, 1};
+  return {16, 1, 2};
 }
 
 cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream_t s) {
