@@ -8,14 +8,15 @@
 // W1[16][1][3][3], b1, W2[32][16][3][3], b2, W3[64][32][3][3], b3, Wf1[128][16384], bf1,
 // Wf2[128], bf2. Adam keeps FP32 moments; the GEMMs read BF16 copies of the weights.
 //
-// Every convolution and fc1, forward and backward, is one GEMM C = A B^T with both operands
-// K-major BF16 (k_gemm): TMA (128-byte swizzle) fills a 4-stage shared-memory ring, one
-// thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a TMEM
-// accumulator, and four warps read it back with tcgen05.ld for the epilogue (bias, ReLU,
-// BF16 or FP32, row-major or transposed store, or FP32 atomic add for split-K).
-// Activations are channel-major ([c][b][h][w]); im2col rows are [m][k] with m = (b, h, w)
+// conv2 and conv3 forward run as implicit GEMMs (k_conv_tc: patches gathered on chip);
+// fc1 and every backward GEMM are C = A B^T with both operands K-major BF16 (k_gemm): TMA
+// (128-byte swizzle) fills a 4-stage shared-memory ring, one thread issues tcgen05.mma
+// (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator, and four warps read it
+// back with tcgen05.ld for the epilogue (bias, ReLU, BF16 or FP32, row-major or transposed
+// store, or FP32 atomic add for split-K). conv1 (K = 9) runs on the CUDA cores (k_conv1).
+// Activations are channel-major ([c][b][h][w]); patch rows are [m][k] with m = (b, h, w)
 // and k = (cin, ky, kx), zero-padded to a multiple of 64.
-//   forward conv:   Y^T[cout][m] = relu(col[m][:] . W[cout][:] + b)      (transposed store)
+//   forward conv:   Y^T[cout][m] = relu(patch[m][:] . W[cout][:] + b)  (k_conv_tc, implicit)
 //   weight grad:    dW[cout][k] += dY^T[cout][m] . colT[k][m]            (split-K, atomic)
 //   input grad:     dcol[m][k]   = dY[m][:] . W^T[k][:]                  (then col2im)
 // Every mbarrier wait is bounded (about 2 s of clock); a wait that gives up sets a device
@@ -304,37 +305,201 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// ---------------------------------------------------------------- layer kernels
+// Implicit-GEMM 3x3 convolution on the tensor cores (conv2 and conv3 forward):
+//   Y^T[cout][m] = relu(sum_k A[m][k] W[cout][k] + b),  A[m][k] = x[ci][b][y+ky-1][x+kx-1]
+// with m = (b, y, x), the patch gathered in tap-major order (k = (ky*3 + kx)*cin + ci, the
+// weights permuted to match), i.e. the im2col GEMM without the im2col buffer. 288 threads: warps 0-3 drain the TMEM accumulator, warps 4-7 build the A
+// tile of every K step in shared memory (one tile row per thread, in the 128-byte swizzled
+// K-major layout the MMA reads, made visible to the tensor core with a proxy fence) while one
+// of them also TMA-loads the weight tile, and warp 8 owns TMEM and issues the MMAs. CTAs are
+// persistent over the M tiles; the accumulator is double buffered as in k_gemm.
+__device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
 
-// col[m][kp] = x[ci][b][y + ky - 1][x + kx - 1] (zero outside, zero for k >= kc); x is FP32
-// (the snippets) or BF16 (pooled activations), channel-major with channel stride n*h*w.
-template <typename T>
-__global__ void k_im2col(const T* __restrict__ x, int n, int h, int w, int kc, int kp, bf16* __restrict__ col) {
-  const long long hw = static_cast<long long>(h) * w;
-  const long long total = static_cast<long long>(n) * hw * (kp / 8);
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long m = i / (kp / 8);
-    const int k0 = static_cast<int>(i - m * (kp / 8)) * 8;
-    const int b = static_cast<int>(m / hw);
-    const int yx = static_cast<int>(m - b * hw);
-    const int yy = yx / w, xx = yx - yy * w;
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k = k0 + j;
-      float val = 0.0f;
-      if (k < kc) {
-        const int ci = k / 9, r = k - ci * 9, ky = r / 3, kx = r - ky * 3;
-        const int sy = yy + ky - 1, sx = xx + kx - 1;
-        if (sy >= 0 && sy < h && sx >= 0 && sx < w)
-          val = static_cast<float>(x[static_cast<long long>(ci) * n * hw + b * hw + sy * w + sx]);
-      }
-      v[j] = __float2bfloat16_rn(val);
+struct ConvArgs {
+  const bf16* x;    // input activations [cin][n][h][w]
+  int n, h, w, cin, kc, ktiles;
+  const float* bias;
+  bf16* yT;         // output [cout][n*h*w]
+  int cout;
+};
+
+template <int BN, int CIN>
+__global__ void __launch_bounds__(288, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap mb, ConvArgs a, uint32_t* err) {
+  constexpr int KT = (9 * CIN + kBK - 1) / kBK;  // K steps
+  constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+  constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
+  extern __shared__ uint8_t gsm_raw[];
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sA = smem_u32(gsm), sB = sA + kStages * kABytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long hw = static_cast<long long>(a.h) * a.w;
+  const long long M = static_cast<long long>(a.n) * hw;
+  const int mt = static_cast<int>((M + kBM - 1) / kBM);
+  const int nkt = KT;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 128);  // one arrival per producer thread
+      mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    *reinterpret_cast<uint4*>(col + m * kp + k0) = *reinterpret_cast<const uint4*>(v);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_tfull[b]), 1);
+      mbar_init(smem_u32(&bar_tempty[b]), 4);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp >= 4 && warp < 8) {
+    // producers: thread pr builds row pr of every A tile. K runs tap-major, k = tap*CIN + ci
+    // (tap = ky*3 + kx; the weights are permuted to match), so with CIN and the K-step count
+    // known at compile time every element is one load at a fixed per-tap offset.
+    const int pr = threadIdx.x - 128;
+    int it = 0;
+    for (int t = blockIdx.x; t < mt && !*abort_v; t += gridDim.x) {
+      const long long m = static_cast<long long>(t) * kBM + pr;
+      const bool mv = m < M;
+      const int b = mv ? static_cast<int>(m / hw) : 0;
+      const int yx = mv ? static_cast<int>(m - b * hw) : 0;
+      const int yy = yx / a.w, xx = yx - yy * a.w;
+      const bf16* xb = a.x + static_cast<long long>(b) * hw;
+      const bf16* tp[9];
+      bool tv[9];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+        tv[tap] = mv && sy >= 0 && sy < a.h && sx >= 0 && sx < a.w;
+        tp[tap] = xb + (tv[tap] ? sy * a.w + sx : 0);
+      }
+      bool quit = false;
+#pragma unroll
+      for (int i = 0; i < KT; ++i, ++it) {
+        const int s = it % kStages;
+        if (it >= kStages && !mbar_wait(smem_u32(&bar_empty[s]), ((it / kStages) & 1) ^ 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          quit = true;
+          break;
+        }
+        const uint32_t fb = smem_u32(&bar_full[s]);
+        if (pr == 0) {
+          mbar_expect_tx_only(fb, kBBytes);
+          tma_load_2d(sB + s * kBBytes, &mb, fb, i * kBK, 0);
+        }
+        const uint32_t rowaddr = sA + s * kABytes + pr * 128;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          __align__(16) bf16 v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            constexpr int kc = 9 * CIN;
+            const int k = i * kBK + q * 8 + e;  // compile-time after unrolling
+            const int tap = k / CIN, ci = k % CIN;
+            v[e] = (k < kc && tv[tap < 9 ? tap : 0]) ? tp[tap < 9 ? tap : 0][static_cast<long long>(ci) * M]
+                                                     : __float2bfloat16_rn(0.0f);
+          }
+          const uint4 pk = *reinterpret_cast<const uint4*>(v);
+          const uint32_t dst = rowaddr + ((q ^ (pr & 7)) << 4);
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk.x), "r"(pk.y), "r"(pk.z),
+                       "r"(pk.w)
+                       : "memory");
+        }
+        // the tensor core reads shared memory through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(fb);
+      }
+      if (quit) break;
+    }
+  } else if (warp == 8) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = mma_idesc(BN);
+      int it = 0, j = 0;
+      for (int t = blockIdx.x; t < mt && !*abort_v; t += gridDim.x, ++j) {
+        const int b = j & 1;
+        if (j >= 2 && !mbar_wait(smem_u32(&bar_tempty[b]), ((j >> 1) & 1) ^ 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + static_cast<uint32_t>(b * BN);
+        for (int i = 0; i < nkt; ++i, ++it) {
+          const int s = it % kStages;
+          if (!mbar_wait(smem_u32(&bar_full[s]), (it / kStages) & 1)) {
+            atomicOr(err, kErrWait);
+            *abort_v = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint64_t da = sw128_desc(sA + s * kABytes + kk * 32);
+            const uint64_t db = sw128_desc(sB + s * kBBytes + kk * 32);
+            umma_bf16(acc, da, db, idesc, (i | kk) != 0 ? 1u : 0u);
+          }
+          umma_commit(smem_u32(&bar_empty[s]));
+        }
+        umma_commit(smem_u32(&bar_tfull[b]));
+      }
+    }
+  } else {
+    // epilogue warps 0-3: bias, ReLU, BF16, channel-major store Y^T[cout][m]
+    int j = 0;
+    for (int t = blockIdx.x; t < mt; t += gridDim.x, ++j) {
+      const int b = j & 1;
+      bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[b]), (j >> 1) & 1);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrWait);
+        *abort_v = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const long long row = static_cast<long long>(t) * kBM + warp * 32 + lane;
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(b * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 8) {
+        float v[8];
+        tmem_ld8(tbase + static_cast<uint32_t>(c), v);
+        if (row >= M) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int n = c + q;
+          if (n >= a.cout) continue;
+          a.yT[static_cast<long long>(n) * M + row] = __float2bfloat16_rn(fmaxf(v[q] + a.bias[n], 0.0f));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[b]));
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 8) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
   }
 }
+
+// ---------------------------------------------------------------- layer kernels
 
 // conv1 (1 input channel, K = 9) on the CUDA cores: a K of 9 would fill one 64-wide tensor
 // core K step to 14%. Same arithmetic as the GEMM path: BF16-rounded snippet values and
@@ -569,6 +734,21 @@ __global__ void k_cast_w(const float* __restrict__ src, int rows, int cols, bf16
   }
 }
 
+// dst[co][tap*cin + ci] = bf16(src[co][ci*9 + tap]) (the tap-major K of k_conv_tc), zero to kp
+__global__ void k_cast_w_tap(const float* __restrict__ src, int cout, int cin, bf16* __restrict__ dst, int kp) {
+  const long long total = static_cast<long long>(cout) * kp;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int co = static_cast<int>(i / kp), k = static_cast<int>(i - static_cast<long long>(co) * kp);
+    float v = 0.0f;
+    if (k < 9 * cin) {
+      const int tap = k / cin, ci = k - tap * cin;
+      v = src[static_cast<long long>(co) * 9 * cin + ci * 9 + tap];
+    }
+    dst[i] = __float2bfloat16_rn(v);
+  }
+}
+
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
                        float* __restrict__ m2, long long np, float lr, float b1, float b2, float eps, float c1,
                        float c2) {
@@ -712,6 +892,35 @@ int gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int 
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
 
+// Forward 3x3 convolution of a [cin][n][h][w] BF16 map on the tensor cores (k_conv_tc):
+// Y^T[cout][m] = relu(conv + bias), weights wb[cout][kp] BF16.
+int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const bf16* wb, int cout,
+            const float* bias, bf16* yT, uint32_t* err, cudaStream_t s, int64_t* launches) {
+  const int BN = cout <= 32 ? 32 : 64;
+  if (cout > 64) return SND_ERR_UNSUPPORTED;
+  CUtensorMap mb;
+  if (!make_map(&mb, wb, kp, cout, kp, BN)) return SND_ERR_UNSUPPORTED;
+  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout};
+  const long long M = 1LL * n * h * w;
+  const long long mt = (M + kBM - 1) / kBM;
+  const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
+  const int per_sm = std::max(1, (227 * 1024) / smem);
+  const unsigned grid = static_cast<unsigned>(std::min<long long>(mt, 152LL * per_sm));
+  cudaError_t e;
+  if (cin == 16 && BN == 32) {
+    e = cudaFuncSetAttribute(k_conv_tc<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) k_conv_tc<32, 16><<<grid, 288, smem, s>>>(mb, a, err);
+  } else if (cin == 32 && BN == 64) {
+    e = cudaFuncSetAttribute(k_conv_tc<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) k_conv_tc<64, 32><<<grid, 288, smem, s>>>(mb, a, err);
+  } else {
+    return SND_ERR_UNSUPPORTED;
+  }
+  if (launches) *launches += 1;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
 int grid_for(long long total) { return static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 32)); }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -729,7 +938,7 @@ struct Sifter {
   int64_t launches = 0;
   cudaStream_t last = nullptr;
   struct {
-    size_t params, grads, m1, m2, err, loss, wb[3], wT[3], wf1b, wf1T, col[3], yT[3], p[3], am[3], p3, p3T, hf,
+    size_t params, grads, m1, m2, err, loss, wb[3], wT[3], wf1b, wf1T, yT[3], p[3], am[3], p3, p3T, hf,
         logits, dh, dhT, dp3, dy[3], dyT[3], colT[3], dcol[3], dp[3];
   } o{};
 };
@@ -759,7 +968,6 @@ void layout(Sifter& f) {
     const long long m = B * c.h * c.w;
     f.o.wb[l] = take(2ull * c.cout * c.kp);
     f.o.wT[l] = take(2ull * c.kc * 64);
-    f.o.col[l] = take(l > 0 ? 2ull * m * c.kp : 0);  // conv1 runs without im2col
     f.o.yT[l] = take(2ull * c.cout * m);
     f.o.p[l] = take(2ull * c.cout * m / 4);
     f.o.am[l] = take(1ull * c.cout * m / 4);
@@ -804,8 +1012,13 @@ cudaError_t prep_weights(Sifter& f, cudaStream_t s) {
   const float* P = at<float>(f, f.o.params);
   for (int l = 0; l < 3; ++l) {
     const ConvL& c = kConv[l];
-    k_cast_w<<<grid_for(1LL * c.cout * c.kp), 256, 0, s>>>(P + kOffW[l], c.cout, c.kc, at<bf16>(f, f.o.wb[l]), c.kp, 0,
-                                                         c.cout);
+    if (l == 0) {
+      k_cast_w<<<grid_for(1LL * c.cout * c.kp), 256, 0, s>>>(P + kOffW[l], c.cout, c.kc, at<bf16>(f, f.o.wb[l]), c.kp,
+                                                           0, c.cout);
+    } else {  // tap-major K for k_conv_tc
+      k_cast_w_tap<<<grid_for(1LL * c.cout * c.kp), 256, 0, s>>>(P + kOffW[l], c.cout, c.cin, at<bf16>(f, f.o.wb[l]),
+                                                               c.kp);
+    }
     f.launches++;
     if (f.training && l > 0) {
       k_cast_w<<<grid_for(1LL * c.kc * 64), 256, 0, s>>>(P + kOffW[l], c.cout, c.kc, at<bf16>(f, f.o.wT[l]), 64, 1,
@@ -835,12 +1048,9 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
       k_conv1<<<grid_for(m), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]));
       f.launches++;
     } else {
-      bf16* col = at<bf16>(f, f.o.col[l]);
-      k_im2col<bf16><<<grid_for(m * c.kp / 8), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, c.kp, col);
-      f.launches++;
-      Epi e{P + kOffB[l], 1, at<bf16>(f, f.o.yT[l]), 1, 1, 0, m};
-      int rc = gemm(col, c.kp, at<bf16>(f, f.o.wb[l]), c.kp, static_cast<int>(m), c.cout, c.kp, e, 1, err, s,
-                    &f.launches);
+      // implicit GEMM: the patches are gathered on chip, no im2col buffer
+      int rc = conv_tc(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, c.kc, c.kp, at<bf16>(f, f.o.wb[l]), c.cout,
+                       P + kOffB[l], at<bf16>(f, f.o.yT[l]), err, s, &f.launches);
       if (rc) return rc;
     }
     const long long pooled = m / 4 * c.cout;
