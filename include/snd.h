@@ -88,6 +88,8 @@ typedef struct {
   int32_t cell_capacity;    /* mask cells with S/N kept per matched-filter block */
   int32_t run_capacity;     /* closed-mask runs per matched-filter block */
   int32_t flags;            /* 0, SND_FLAG_REFERENCE_TREE, or SND_FLAG_FP16_PARTIALS (zfloat) */
+  int32_t plane_dtype;      /* d_plane_out element type: 0 = int32 / float32 (default); 1 = uint8,
+                               binary and graded modes only (their roots are 0..255) */
 } snd_options_t;
 
 /* One detection (Methods, "Candidate detection": one candidate per island, peak pixel). */
@@ -164,7 +166,7 @@ int snd_bind_workspace(snd_plan_t plan, void* d_workspace, size_t bytes, void* s
  *   nsamp        1..max_chunk samples
  *   stream       all work is enqueued on it; no host synchronisation
  *   d_plane_out  optional device output [ndm][*nemit_out] row-major: int32 root values
- *                (binary 0/1, graded 0..N) or float32 (float mode, counts/sqrt(N_f); zfloat,
+ *                (binary 0/1, graded 0..N; uint8 with plane_dtype = 1) or float32 (float mode, counts/sqrt(N_f); zfloat,
  *                the labelled-payload plane) for the newly emitted samples [E_prev, E_new);
  *                NULL to skip
  *   nemit_out    optional host int32: E_new - E_prev, the emitted samples per row, where

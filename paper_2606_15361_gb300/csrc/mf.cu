@@ -38,6 +38,7 @@ struct MfArgs {
   uint32_t* counters;
   void* plane_out;
   int nemit;
+  int out_u8;       // caller's plane in uint8 (binary / graded roots are 0..255)
 };
 
 constexpr int kMfThreads = 256;
@@ -81,6 +82,9 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
     if (a.out_scale != 0.0f) {
       float* o = static_cast<float*>(a.plane_out) + static_cast<size_t>(d) * a.nemit;
       for (int i = tid; i < a.nemit; i += kMfThreads) o[i] = static_cast<float>(y[first + i]) * a.out_scale;
+    } else if (a.out_u8) {
+      uint8_t* o = static_cast<uint8_t*>(a.plane_out) + static_cast<size_t>(d) * a.nemit;
+      for (int i = tid; i < a.nemit; i += kMfThreads) o[i] = static_cast<uint8_t>(y[first + i]);
     } else {
       int32_t* o = static_cast<int32_t*>(a.plane_out) + static_cast<size_t>(d) * a.nemit;
       for (int i = tid; i < a.nemit; i += kMfThreads) o[i] = y[first + i];
@@ -248,6 +252,7 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
   a.counters = p.dp.counters;
   a.plane_out = nemit > 0 ? d_plane_out : nullptr;
   a.nemit = nemit;
+  a.out_u8 = p.plane_u8;
   const int len = static_cast<int>(e_new - f_prev);
   const int smem = (len + 16) * 4;  // front pad (4 + up to 3), prefix total and staging overrun
   cudaError_t e = cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

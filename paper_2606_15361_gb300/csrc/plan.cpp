@@ -547,6 +547,9 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
       o.sigma_min < 0.0 || !std::isfinite(o.mf_alpha) || o.mf_alpha < 0.0)
     return SND_ERR_ARG;
   if (o.closing_size < 1 || o.closing_size > 31 || (o.closing_size & 1) == 0) return SND_ERR_ARG;
+  if (o.plane_dtype < 0 || o.plane_dtype > 1 ||
+      (o.plane_dtype == 1 && mode != SND_MODE_BINARY && mode != SND_MODE_GRADED))
+    return SND_ERR_ARG;
   if (o.n_min_pixels < 1 || o.max_chunk < 1 || o.max_chunk > (1 << 22) || o.cand_capacity < 1 ||
       o.cell_capacity < 1 || o.run_capacity < 1)
     return SND_ERR_ARG;
@@ -584,6 +587,7 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
     p->cell_cap = o.cell_capacity;
     p->run_cap = o.run_capacity;
     p->flags = o.flags;
+    p->plane_u8 = o.plane_dtype;
     p->freqs.assign(freqs_mhz, freqs_mhz + nchan);
     p->dms.assign(dm_grid, dm_grid + ndm);
     int rc = snd::build_plan(*p);

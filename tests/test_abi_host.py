@@ -182,3 +182,14 @@ def test_zfloat_flags_and_stats(snd):
     # FP16 storage halves the per-node history of Eq. hist_mem relative to FP32
     assert s16.hist_mem_bytes < s32.hist_mem_bytes
     assert p16.workspace_bytes < p32.workspace_bytes
+
+
+def test_uint8_plane_option(snd):
+    f = synth.channel_freqs(64)
+    d = synth.dm_grid(128, 100.0)
+    E = snd.ERR
+    for mode in (snd.MODE_BINARY, snd.MODE_GRADED):
+        assert _plan_rc(snd, f, d, mode=mode, opts=snd.options(mode, plane_dtype=1)) == 0
+    assert _plan_rc(snd, f, d, mode=snd.MODE_FLOAT, opts=snd.options(snd.MODE_FLOAT, plane_dtype=1)) == E["SND_ERR_ARG"]
+    assert _plan_rc(snd, f, d, mode=snd.MODE_GRADED, opts=snd.options(snd.MODE_GRADED, plane_dtype=2)) == E["SND_ERR_ARG"]
+    assert ctypes.sizeof(snd.SndOptions) % 8 == 0 and snd.options(snd.MODE_BINARY).plane_dtype == 0

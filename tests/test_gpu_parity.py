@@ -255,3 +255,22 @@ def test_nc1024_full_stream_sampled(mode, B):
         mk, snr, wd, _, _ = omf.row_mf(y, f1 - f0, widths[d], cfg.det_theta, floor)
         assert mk[t - f0]
         assert np.float32(snr[t - f0]) == c["snr"] and wd[t - f0] == c["width"]
+
+
+@pytest.mark.parametrize("mode", ["binary", "graded"])
+def test_uint8_plane_output(mode):
+    """plane_dtype = 1 writes the same root values as uint8."""
+    w = synth.NC64
+    cfg = ostream.defaults(MODES[mode], branching=2)
+    data = w.chunk_data(0)
+    plan = g.Plan(w.freqs(), synth.NC_DT, w.dms(), 2, MODES[mode], _opts(MODES[mode], cfg, plane_dtype=1))
+    ref = ostream.OracleStream(w.freqs(), synth.NC_DT, w.dms(), cfg)
+    for ch in (data[:6000], data[6000:]):
+        ne = plan.nemit_next(ch.shape[0])
+        out = torch.full((len(w.dms()), max(ne, 1)), 77, dtype=torch.uint8, device="cuda")
+        assert plan.execute(torch.from_numpy(np.ascontiguousarray(ch)).cuda(), out) == ne
+        r = ref.push(ch)
+        if ne:
+            assert (out[:, :ne].cpu().numpy().astype(np.int64) == r["plane"]).all()
+    c, rc = plan.candidates()
+    assert rc == 0
