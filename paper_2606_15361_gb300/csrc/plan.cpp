@@ -298,6 +298,7 @@ int build_plan(Plan& p) {
     p.off.zring = take(es * static_cast<size_t>(nchan) * p.zgeom.Rz);
     p.off.ztab = take(es * static_cast<size_t>(nchan) * 256);
     p.off.zwb = take(sizeof(int32_t) * p.zwb.size());
+    p.off.zcarry = take(sizeof(int32_t) * p.zcarry.size());
   }
   p.ws_bytes = o;
   return SND_OK;
@@ -511,6 +512,18 @@ int choose_ztree_geometry(Plan& p) {
   const int gc = z.group_leaves * p.C;
   z.smem_bytes = static_cast<int>(align_up(static_cast<size_t>(gc) * z.win * es, 16) +
                                   static_cast<size_t>(4) * z.dms_per_cta * gc);
+  // carry depth of each leaf: how many consecutive levels, from the leaves' parents up, it
+  // finishes (while the node is the last child of its parent: the B-th or the ragged last)
+  p.zcarry.assign(NL, 0);
+  for (int k = 0; k < NL; ++k) {
+    int i = k, depth = 0;
+    for (int l = 0; l + 1 < p.nlev; ++l) {
+      if (!((i % p.B == p.B - 1) || (i == p.level_nodes[l] - 1))) break;
+      ++depth;
+      i /= p.B;
+    }
+    p.zcarry[k] = depth;
+  }
   // every emitted sample reads [E_prev, T_new): at most D + max_chunk samples back
   z.Rz = static_cast<int>(align_up(static_cast<size_t>(p.D) + p.max_chunk + 64, 8));
   return SND_OK;

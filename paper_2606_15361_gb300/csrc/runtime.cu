@@ -135,6 +135,7 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.zring = z ? at<void>(d_ws, o.zring) : nullptr;
   dp.ztab = z ? at<void>(d_ws, o.ztab) : nullptr;
   dp.zwb = z ? at<int32_t>(d_ws, o.zwb) : nullptr;
+  dp.zcarry = z ? at<int32_t>(d_ws, o.zcarry) : nullptr;
   std::vector<float> dmf(p.dms.begin(), p.dms.end());
   cudaError_t e = cudaMemsetAsync(d_ws, 0, p.ws_bytes, s);
   if (e == cudaSuccess) e = upload(d_ws, o.width_mask, p.width_mask, s);
@@ -146,6 +147,7 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   if (e == cudaSuccess) e = upload(d_ws, o.tile_wb, p.tile_wb, s);
   if (e == cudaSuccess) e = upload(d_ws, o.delays, p.delays, s);
   if (e == cudaSuccess && z) e = upload(d_ws, o.zwb, p.zwb, s);
+  if (e == cudaSuccess && z) e = upload(d_ws, o.zcarry, p.zcarry, s);
   if (e != cudaSuccess) {
     p.bound = false;
     return SND_ERR_CUDA;

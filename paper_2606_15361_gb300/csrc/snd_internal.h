@@ -105,6 +105,7 @@ struct DevPtrs {
   void* zring;             // zfloat: [nchan][Rz] payload ring (half or float), sample a at a mod Rz
   void* ztab;              // zfloat: [nchan][256] payload of each uint8 value (0 below the level)
   int32_t* zwb;            // zfloat: [ndm_tiles][nchan] first staged sample offset per channel
+  int32_t* zcarry;         // zfloat: [nleaves] carry depth of each leaf
 };
 
 // Counter slots.
@@ -150,7 +151,7 @@ struct Plan {
   std::vector<int32_t> gleaf;
   TreeGeom geom{};
   ZGeom zgeom{};
-  std::vector<int32_t> zwb;
+  std::vector<int32_t> zwb, zcarry;
 
   // sizes
   int R = 0;           // ring words per copy
@@ -160,7 +161,7 @@ struct Plan {
   struct Off {
     size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
         run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, width_mask, dm_f32, tp_off,
-        gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb;
+        gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb, zcarry;
   } off{};
 
   // binding and stream state

@@ -27,6 +27,7 @@ struct ZArgs {
   int level_nodes[kMaxLevels];
   const int32_t* delays;  // [ndm][nchan]
   const int32_t* zwb;     // [ndm_tiles][nchan]
+  const int32_t* carry;   // [nleaves] levels a finished leaf completes (its carry depth)
   int win, G;             // staged samples per channel, leaves per group
   long long t0;           // first output sample of this call
   int nout;
@@ -98,30 +99,32 @@ __global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
 #pragma unroll
         for (int j = 0; j < SPT; ++j) v[j] = __fadd_rn(v[j], zload(src + 32 * j));
       }
-      // carry the finished node up: node i of level l goes to its parent's sum; when it is
-      // the parent's last child the parent is finished in turn
-      int i = k;
-      bool carry = true;
+      if (a.nlev == 1) {  // a single leaf is the root: its FP32 sum is not stored
 #pragma unroll
-      for (int l = 0; l < MAXL; ++l) {
-        if (carry && l < a.nlev) {
-          if (l == a.nlev - 1) {
+        for (int j = 0; j < SPT; ++j) root[j] = v[j];
+        continue;
+      }
+      // the stored leaf goes into its parent's sum (acc[l] holds the open node of level l + 1);
+      // when it is the parent's last child the parent is finished, and so on up `depth`
+      // levels. depth depends on the leaf only, so the branch is warp-uniform and taken by one
+      // leaf in B.
 #pragma unroll
-            for (int j = 0; j < SPT; ++j) root[j] = v[j];
-            carry = false;
-          } else {
+      for (int j = 0; j < SPT; ++j) acc[0][j] = __fadd_rn(acc[0][j], zstore_round(v[j], ring));
+      const int depth = __ldg(a.carry + k);
+      if (depth > 0) {
 #pragma unroll
-            for (int j = 0; j < SPT; ++j) acc[l][j] = __fadd_rn(acc[l][j], zstore_round(v[j], ring));
-            const bool last = (i % a.B == a.B - 1) || (i == a.level_nodes[l] - 1);
-            if (last) {
+        for (int l = 0; l + 1 < MAXL; ++l) {
+          if (l < depth) {
+            const bool to_root = (l + 1 == a.nlev - 1);
 #pragma unroll
-              for (int j = 0; j < SPT; ++j) {
-                v[j] = acc[l][j];
-                acc[l][j] = 0.0f;
+            for (int j = 0; j < SPT; ++j) {
+              const float x = acc[l][j];
+              acc[l][j] = 0.0f;
+              if (to_root) {
+                root[j] = x;
+              } else {
+                acc[l + 1][j] = __fadd_rn(acc[l + 1][j], zstore_round(x, ring));
               }
-              i /= a.B;
-            } else {
-              carry = false;
             }
           }
         }
@@ -165,6 +168,7 @@ cudaError_t launch_tree_z(const Plan& p, int64_t e_prev, int64_t e_new, void* d_
   for (int l = 0; l < kMaxLevels; ++l) a.level_nodes[l] = l < p.nlev ? p.level_nodes[l] : 1;
   a.delays = p.dp.delays;
   a.zwb = p.dp.zwb;
+  a.carry = p.dp.zcarry;
   a.win = z.win;
   a.G = z.group_leaves;
   a.t0 = e_prev;
