@@ -42,7 +42,7 @@ __device__ __forceinline__ float zload(const __half* p) { return __half2float(*p
 __device__ __forceinline__ float zstore_round(float v, const float*) { return v; }
 __device__ __forceinline__ float zstore_round(float v, const __half*) { return __half2float(__float2half_rn(v)); }
 
-template <typename ST, int MAXL, int SPT>
+template <typename ST, int MAXL, int SPT, int CT>
 __global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
   extern __shared__ __align__(16) unsigned char zsm[];
   const int DT = blockDim.y;
@@ -75,11 +75,10 @@ __global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
       const int ph = static_cast<int>((tb + wb[c]) % a.Rz);
       const ST* row = ring + static_cast<size_t>(c) * a.Rz;
       ST* dst = win + static_cast<size_t>(cl) * a.win;
-      for (int i = lane; i < a.win; i += 32) {
-        int q = ph + i;
-        if (q >= a.Rz) q -= a.Rz;
-        dst[i] = row[q];
-      }
+      // the window may wrap around the ring end: copy the two runs
+      const int n1 = min(a.win, a.Rz - ph);
+      for (int i = lane; i < n1; i += 32) dst[i] = row[ph + i];
+      for (int i = n1 + lane; i < a.win; i += 32) dst[i] = row[i - n1];
     }
     for (int i = tid; i < DT * nc; i += nthr) {
       const int w = i / nc, cl = i - w * nc;
@@ -94,10 +93,27 @@ __global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
       float v[SPT];
 #pragma unroll
       for (int j = 0; j < SPT; ++j) v[j] = 0.0f;
-      for (int ci = 0; ci < cn; ++ci) {
-        const ST* src = win + static_cast<size_t>(cl0 + ci) * a.win + drel[wd * GC + cl0 + ci] + lane;
+      if (CT) {
+        // C channels known at compile time: all C x SPT loads of the leaf are independent
+        const ST* src[CT > 0 ? CT : 1];
 #pragma unroll
-        for (int j = 0; j < SPT; ++j) v[j] = __fadd_rn(v[j], zload(src + 32 * j));
+        for (int ci = 0; ci < CT; ++ci)
+          src[ci] = win + static_cast<size_t>(cl0 + ci) * a.win + drel[wd * GC + cl0 + ci] + lane;
+        float x[CT > 0 ? CT : 1][SPT];
+#pragma unroll
+        for (int ci = 0; ci < CT; ++ci)
+#pragma unroll
+          for (int j = 0; j < SPT; ++j) x[ci][j] = zload(src[ci] + 32 * j);
+#pragma unroll
+        for (int ci = 0; ci < CT; ++ci)
+#pragma unroll
+          for (int j = 0; j < SPT; ++j) v[j] = __fadd_rn(v[j], x[ci][j]);
+      } else {
+        for (int ci = 0; ci < cn; ++ci) {
+          const ST* src = win + static_cast<size_t>(cl0 + ci) * a.win + drel[wd * GC + cl0 + ci] + lane;
+#pragma unroll
+          for (int j = 0; j < SPT; ++j) v[j] = __fadd_rn(v[j], zload(src + 32 * j));
+        }
       }
       if (a.nlev == 1) {  // a single leaf is the root: its FP32 sum is not stored
 #pragma unroll
@@ -144,7 +160,8 @@ __global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
 
 template <typename ST, int MAXL, int SPT>
 cudaError_t run_z(const ZArgs& a, dim3 grid, dim3 block, int smem, cudaStream_t s) {
-  auto kern = k_tree_z<ST, MAXL, SPT>;
+  // the compile-time 4-channel leaf applies when every leaf has 4 channels
+  auto kern = (a.C == 4 && a.nchan % 4 == 0) ? k_tree_z<ST, MAXL, SPT, 4> : k_tree_z<ST, MAXL, SPT, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(a);
