@@ -2,8 +2,10 @@
 //
 // One CTA per DM row. The row segment [F_prev, E_new) of the plane ring (block start times
 // [F_prev, F_new) plus the Wmax-1 samples their windows reach) is staged in shared memory,
-// its exact integer sums give mu and sigma over the block's start times, and an in-place
-// exclusive scan turns it into prefix sums so every boxcar is P[t+W] - P[t].
+// realigned so that F_prev sits on a 16-byte boundary; its exact integer sums give mu and
+// sigma over the block's start times, and an in-place exclusive scan turns it into prefix
+// sums so every boxcar is P[t+W] - P[t]. Scan and threshold work on groups of four
+// consecutive samples per lane (one 128-bit shared access per group).
 //
 // Decision: a cell is in the mask iff max over the row's widths of
 //   SNR(W) = (S_W - mu*W) / (sigma*sqrt(W))          (FP64, this operation order)
@@ -48,31 +50,47 @@ __device__ __forceinline__ double snr_of(long long s, double mu_w, double den) {
 }
 
 __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
-  // smem: the row segment, placed so that every aligned group of four ring columns lands
-  // on a 16-byte boundary (one 128-bit store per group), with pads on both sides
+  // smem: 4 words of front pad, then y[0..4*G) with y 16-byte aligned, G = len/4 + 2 groups
   extern __shared__ __align__(16) int32_t smem[];
-  __shared__ long long red1[kMfThreads / 32], red2[kMfThreads / 32];
+  constexpr int NWARP = kMfThreads / 32;
+  __shared__ long long red1[NWARP], red2[NWARP];
   __shared__ int tau[kNumWidthSlots];
-  __shared__ double smu, ssig;
+  __shared__ double s_muw[kNumWidthSlots], s_den[kNumWidthSlots];
   __shared__ int s_ok;
-  __shared__ uint32_t wsum[kMfThreads / 32];
+  __shared__ uint32_t wsum[NWARP];
   const int d = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int NWARP = kMfThreads / 32;
   const int len = static_cast<int>(a.e_new - a.f_prev);
   const int c0 = static_cast<int>(a.f_prev % a.Lp);
   const int r0 = c0 & 3;
-  int32_t* y = smem + 4 + r0;  // y[i] = ring column c0 + i
-  // 1. stage ring columns [f_prev, e_new) of row d with 16-byte loads and stores (Lp % 4 == 0,
-  //    so an aligned group of four columns never straddles the ring's wrap point)
+  int32_t* y = smem + 4;  // y[i] = ring column c0 + i, zero from i = len on
+  int4* Y4 = reinterpret_cast<int4*>(y);
+  const int G = (len >> 2) + 2;  // groups staged: y[len] and one group past it
+  // 1. stage: aligned group m of y takes global groups m and m+1 of the row (16-byte loads of
+  //    columns c0 - r0 + 4m ...; Lp % 4 == 0, so a group never straddles the ring's wrap point)
   {
     const int32_t* src = a.plane + static_cast<size_t>(d) * a.Lp;
-    const int ngroups = (len + r0 + 3) >> 2;
-    int4* dst = reinterpret_cast<int4*>(smem + 4);
-    for (int k = tid; k < ngroups; k += kMfThreads) {
-      int c = c0 - r0 + 4 * k;
-      if (c >= a.Lp) c -= a.Lp;
-      dst[k] = __ldg(reinterpret_cast<const int4*>(src + c));
+    for (int m = tid; m < G; m += kMfThreads) {
+      int ca = c0 - r0 + 4 * m;
+      if (ca >= a.Lp) ca -= a.Lp;
+      const int4 g0 = __ldg(reinterpret_cast<const int4*>(src + ca));
+      int4 o = g0;
+      if (r0 != 0) {
+        int cb = ca + 4;
+        if (cb >= a.Lp) cb -= a.Lp;
+        const int4 g1 = __ldg(reinterpret_cast<const int4*>(src + cb));
+        if (r0 == 1) o = make_int4(g0.y, g0.z, g0.w, g1.x);
+        else if (r0 == 2) o = make_int4(g0.z, g0.w, g1.x, g1.y);
+        else o = make_int4(g0.w, g1.x, g1.y, g1.z);
+      }
+      const int i = 4 * m;
+      if (i + 3 >= len) {
+        if (i >= len) o.x = 0;
+        if (i + 1 >= len) o.y = 0;
+        if (i + 2 >= len) o.z = 0;
+        if (i + 3 >= len) o.w = 0;
+      }
+      Y4[m] = o;
     }
   }
   __syncthreads();
@@ -92,39 +110,46 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
   }
   const int nb = a.nb;
   if (nb <= 0) return;
-  __syncthreads();  // the caller's copy has read the raw values before the in-place scan
-  // 2. warp-segmented exclusive scan in place (uint32 wrap-around keeps window sums exact),
-  //    with the exact integer sums over the block's start times taken on the way
-  const int seg = ((len + NWARP * 32 - 1) / (NWARP * 32)) * 32;
-  const int lo = min(len, wid * seg), hi = min(len, lo + seg);
-  uint32_t carry = 0;
-  long long s1 = 0, s2 = 0;
-  for (int base = lo; base < hi; base += 32) {
-    const int i = base + lane;
-    const uint32_t v = (i < hi) ? static_cast<uint32_t>(y[i]) : 0u;
-    if (i < nb) {
-      const long long vv = static_cast<int32_t>(v);
-      s1 += vv;
-      s2 += vv * vv;
+  // 2. per-warp totals of contiguous group segments, and the exact integer sums over the
+  //    block's start times (y[i], i < nb)
+  const int segg = ((G + NWARP * 32 - 1) / (NWARP * 32)) * 32;
+  const int glo = min(G, wid * segg), ghi = min(G, glo + segg);
+  {
+    uint32_t tot = 0;
+    long long s1 = 0, s2 = 0;
+    for (int g = glo + lane; g < ghi; g += 32) {
+      const int4 v = Y4[g];
+      tot += static_cast<uint32_t>(v.x) + static_cast<uint32_t>(v.y) + static_cast<uint32_t>(v.z) +
+             static_cast<uint32_t>(v.w);
+      const int i = 4 * g;
+      const long long vx = v.x, vy = v.y, vz = v.z, vw = v.w;
+      if (i + 3 < nb) {
+        s1 += (vx + vy) + (vz + vw);
+        s2 += (vx * vx + vy * vy) + (vz * vz + vw * vw);
+      } else if (i < nb) {
+        s1 += vx;
+        s2 += vx * vx;
+        if (i + 1 < nb) {
+          s1 += vy;
+          s2 += vy * vy;
+        }
+        if (i + 2 < nb) {
+          s1 += vz;
+          s2 += vz * vz;
+        }
+      }
     }
-    uint32_t incl = v;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += u;
+    for (int o = 16; o > 0; o >>= 1) {
+      tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+      s1 += __shfl_down_sync(0xFFFFFFFFu, s1, o);
+      s2 += __shfl_down_sync(0xFFFFFFFFu, s2, o);
     }
-    if (i < hi) y[i] = static_cast<int32_t>(carry + incl - v);
-    carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
-  }
-  if (lane == 0) wsum[wid] = carry;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_down_sync(0xFFFFFFFFu, s1, o);
-    s2 += __shfl_down_sync(0xFFFFFFFFu, s2, o);
-  }
-  if (lane == 0) {
-    red1[wid] = s1;
-    red2[wid] = s2;
+    if (lane == 0) {
+      wsum[wid] = tot;
+      red1[wid] = s1;
+      red2[wid] = s2;
+    }
   }
   __syncthreads();
   const uint32_t wm = a.width_mask[d];
@@ -140,15 +165,13 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
     const double var = __dsub_rn(__ddiv_rn(static_cast<double>(t2), n), __dmul_rn(mu, mu));
     double sig = var > 0.0 ? __dsqrt_rn(var) : 0.0;
     if (a.binary && sig < a.sigma_min) sig = a.sigma_min;
-    if (lane == 0) {
-      smu = mu;
-      ssig = sig;
-      s_ok = sig > 0.0;
-    }
+    if (lane == 0) s_ok = sig > 0.0;
     if (sig > 0.0 && lane < kNumWidthSlots && ((wm >> lane) & 1)) {
       const double w = static_cast<double>(1 << lane);
       const double mu_w = __dmul_rn(mu, w);
       const double den = __dmul_rn(sig, __dsqrt_rn(w));
+      s_muw[lane] = mu_w;
+      s_den[lane] = den;
       double est = ceil(__dadd_rn(mu_w, __dmul_rn(a.theta, den)));
       if (est < 0.0) est = 0.0;
       if (est > 2147483000.0) est = 2147483000.0;
@@ -166,12 +189,31 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
       tau[lane] = static_cast<int>(sv);
     }
   }
+  // 3. exclusive scan in place (uint32 wrap-around keeps window sums exact): a lane scans its
+  //    group of four, the warp scans the group totals, the running carry starts at the sum of
+  //    the segments before this warp's
   {
-    uint32_t off = 0;
-    for (int w = 0; w < wid; ++w) off += wsum[w];
-    if (off)
-      for (int i = lo + lane; i < hi; i += 32) y[i] = static_cast<int32_t>(static_cast<uint32_t>(y[i]) + off);
-    if (wid == NWARP - 1 && lane == 0) y[len] = static_cast<int32_t>(off + carry);
+    uint32_t carry = 0;
+    for (int w = 0; w < wid; ++w) carry += wsum[w];
+    for (int base = glo; base < ghi; base += 32) {
+      const int g = base + lane;
+      const int4 v = (g < ghi) ? Y4[g] : make_int4(0, 0, 0, 0);
+      const uint32_t a0 = static_cast<uint32_t>(v.x);
+      const uint32_t a1 = a0 + static_cast<uint32_t>(v.y);
+      const uint32_t a2 = a1 + static_cast<uint32_t>(v.z);
+      const uint32_t a3 = a2 + static_cast<uint32_t>(v.w);
+      uint32_t incl = a3;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      const uint32_t ex = carry + incl - a3;
+      if (g < ghi)
+        Y4[g] = make_int4(static_cast<int32_t>(ex), static_cast<int32_t>(ex + a0), static_cast<int32_t>(ex + a1),
+                          static_cast<int32_t>(ex + a2));
+      carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
   }
   __syncthreads();
   const int nbw = (nb + 31) >> 5;
@@ -183,29 +225,62 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
   int tw[kNumWidthSlots];
 #pragma unroll
   for (int j = 0; j < kNumWidthSlots; ++j) tw[j] = ((wm >> j) & 1) ? tau[j] : 0x7FFFFFFF;
-  const double mu = smu, sig = ssig;
   const uint32_t* P = reinterpret_cast<const uint32_t*>(y);
-  for (int q = wid; q < nbw; q += NWARP) {
-    const int t = q * 32 + lane;
-    bool hit = false;
-    if (t < nb) {
-      const uint32_t p0 = P[t];
-#pragma unroll
-      for (int j = 0; j < kNumWidthSlots; ++j) {
-        if ((wm >> j) & 1) hit |= static_cast<int>(P[t + (1 << j)] - p0) >= tw[j];
+  const uint4* P4 = reinterpret_cast<const uint4*>(y);
+  // 4. threshold: lane m of an iteration tests start times 4m..4m+3 against every width of the
+  //    row (window ends P[4m + W ...] are group m + W/4 for W >= 4, groups m and m+1 below);
+  //    eight lanes' nibbles make one mask word
+  const int ngt = (nb + 3) >> 2;
+  for (int base = wid * 32; base < ngt; base += NWARP * 32) {
+    const int m = base + lane;
+    uint32_t nib = 0;
+    if (m < ngt) {
+      const uint4 p = P4[m];
+      const uint4 q = P4[m + 1];
+      if (wm & 1u) {
+        const int tj = tw[0];
+        nib |= (static_cast<int>(p.y - p.x) >= tj ? 1u : 0u) | (static_cast<int>(p.z - p.y) >= tj ? 2u : 0u) |
+               (static_cast<int>(p.w - p.z) >= tj ? 4u : 0u) | (static_cast<int>(q.x - p.w) >= tj ? 8u : 0u);
       }
+      if (wm & 2u) {
+        const int tj = tw[1];
+        nib |= (static_cast<int>(p.z - p.x) >= tj ? 1u : 0u) | (static_cast<int>(p.w - p.y) >= tj ? 2u : 0u) |
+               (static_cast<int>(q.x - p.z) >= tj ? 4u : 0u) | (static_cast<int>(q.y - p.w) >= tj ? 8u : 0u);
+      }
+      if (wm & 4u) {
+        const int tj = tw[2];
+        nib |= (static_cast<int>(q.x - p.x) >= tj ? 1u : 0u) | (static_cast<int>(q.y - p.y) >= tj ? 2u : 0u) |
+               (static_cast<int>(q.z - p.z) >= tj ? 4u : 0u) | (static_cast<int>(q.w - p.w) >= tj ? 8u : 0u);
+      }
+#pragma unroll
+      for (int j = 3; j < kNumWidthSlots; ++j) {
+        if ((wm >> j) & 1u) {
+          const uint4 e = P4[m + (1 << (j - 2))];
+          const int tj = tw[j];
+          nib |= (static_cast<int>(e.x - p.x) >= tj ? 1u : 0u) | (static_cast<int>(e.y - p.y) >= tj ? 2u : 0u) |
+                 (static_cast<int>(e.z - p.z) >= tj ? 4u : 0u) | (static_cast<int>(e.w - p.w) >= tj ? 8u : 0u);
+        }
+      }
+      const int rem = nb - 4 * m;  // start times of this group inside the block
+      if (rem < 4) nib &= (1u << rem) - 1u;
     }
-    const uint32_t word = __ballot_sync(0xFFFFFFFFu, hit);
-    if (lane == 0) mrow[q] = word;
-    if (hit) {
+    uint32_t word = nib << (4 * (lane & 7));
+    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+    const int qw = (base >> 3) + (lane >> 3);
+    if ((lane & 7) == 0 && qw < nbw) mrow[qw] = word;
+    while (nib) {
+      const int e = __ffs(nib) - 1;
+      nib &= nib - 1u;
+      const int t = 4 * m + e;
       const uint32_t p0 = P[t];
       double best = -1.0e300;
       int bw = 0;
       for (int j = 0; j < kNumWidthSlots; ++j) {
         if (!((wm >> j) & 1)) continue;
-        const double w = static_cast<double>(1 << j);
         const long long S = static_cast<int>(P[t + (1 << j)] - p0);
-        const double v = snr_of(S, __dmul_rn(mu, w), __dmul_rn(sig, __dsqrt_rn(w)));
+        const double v = snr_of(S, s_muw[j], s_den[j]);
         if (v > best) {
           best = v;
           bw = 1 << j;
@@ -254,7 +329,7 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
   a.nemit = nemit;
   a.out_u8 = p.plane_u8;
   const int len = static_cast<int>(e_new - f_prev);
-  const int smem = (len + 16) * 4;  // front pad (4 + up to 3), prefix total and staging overrun
+  const int smem = ((len >> 2) + 3) * 16;  // front pad (4 words) and len/4 + 2 aligned groups
   cudaError_t e = cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   k_mf<<<p.ndm, kMfThreads, smem, s>>>(a);
