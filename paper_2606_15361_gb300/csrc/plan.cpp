@@ -407,13 +407,16 @@ int choose_tree_geometry_w(Plan& p, int warps) {
         mp = std::max(mp, s);
       }
     *mp_out = mp;
-    // series as word pairs + two staging buffers (windows, meta, entry offsets and leaves)
+    // series as word pairs + two staging buffers (windows, meta, entry offsets and leaves) +
+    // the tile's window base per channel
     const int64_t buf = (static_cast<int64_t>(G) * p.C * g.cspan + static_cast<int64_t>(g.dms_per_cta) * G +
                          static_cast<int64_t>(mp) * (p.C + 1) + 3) & ~int64_t(3);
-    const int64_t words = 2 * static_cast<int64_t>(mp) * g.planes * g.span + 2 * buf;
+    const int64_t words = 2 * static_cast<int64_t>(mp) * g.planes * g.span + 2 * buf + nchan;
     return words * 4;
   };
-  const int64_t budget = 100 * 1024;
+  // binary trees run two CTAs per SM (about 100 KB each); graded and float trees one, which
+  // may take twice that so a group holds more leaves (fewer rounds of staging and barriers)
+  const int64_t budget = (p.mode == SND_MODE_BINARY ? 100 : 200) * 1024;
   const int unit = (p.nlev == 1) ? 1 : std::min(p.B, NL);
   int G = unit, mp = 0;
   int64_t bytes = smem_for(G, &mp);
