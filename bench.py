@@ -35,6 +35,9 @@ W = synth.NC1024
 MODES = (("binary", 0), ("graded", 1), ("float", 2))
 BRANCHING = 8
 TREE_BYTES_PER_DM_SAMPLE = W.nchan / W.ndm + 4.0  # uint8 input read once + int32 plane written once
+# Integer ALU ceiling of the tree: 152 SMs x 4 schedulers x 32 lanes, one 32-bit integer
+# instruction per lane per cycle, at the 2070 MHz maximum SM clock (Gop/s)
+ALU_PEAK_GOPS = 152 * 4 * 32 * 2070e6 / 1e9
 DATA_NOTE = "synthetic: seeded rint(N(128,16)) uint8 noise + 200 injected dispersed bursts"
 
 
@@ -562,6 +565,9 @@ def run_gpu(args, rank, world, local_rank):
     units = W.chunk * W.ndm
     achieved = TREE_BYTES_PER_DM_SAMPLE * units / (tree_launch_ms / 1e3) / 1e9
     per_mode = {}
+    # the tree's algorithmic integer work: the plan's additions per DM-sample with leaf-pattern
+    # sharing (the same count for the three modes of one plan geometry)
+    adds = {n: float(plans[n].stats().adds_per_dm_sample) for n in prof}
     for n in prof:
         st = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof[n].items()}
         tms = prof[n]["tree"][0] / max(prof[n]["tree"][1], 1)
@@ -569,8 +575,10 @@ def run_gpu(args, rank, world, local_rank):
                        "tree_gdm_samples_per_s": round(units / (tms / 1e3) / 1e9, 2),
                        "tree_hbm_frac": round(TREE_BYTES_PER_DM_SAMPLE * units / (tms / 1e3) / 1e9 /
                                               peaks["hbm_gbs"], 4),
+                       "tree_alu_frac": round(adds[n] * units / (tms / 1e3) / 1e9 / ALU_PEAK_GOPS, 4),
                        "pipeline_gdm_samples_per_s": round(units / (sum(v[0] for v in prof[n].values()) /
                                                                     max(prof[n]["tree"][1], 1) / 1e3) / 1e9, 2)}
+    adds_mean = sum(adds.values()) / max(len(adds), 1)
     traffic = _traffic_from_profile(_tree_source_hash())
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -595,6 +603,12 @@ def run_gpu(args, rank, world, local_rank):
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "k_tree (SND tree, all modes, average launch, sequential pass)",
                      "peak_source": src, "algorithmic_bytes_per_dm_sample": TREE_BYTES_PER_DM_SAMPLE},
+        "roofline_alu": {"bound": "alu", "achieved": adds_mean * units / (tree_launch_ms / 1e3) / 1e9,
+                         "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
+                         "frac": adds_mean * units / (tree_launch_ms / 1e3) / 1e9 / ALU_PEAK_GOPS,
+                         "kernel": "k_tree (SND tree, all modes, average launch, sequential pass)",
+                         "algorithmic_ops_per_dm_sample": adds_mean,
+                         "peak_source": "derived: 152 SMs x 128 int32 lanes x 2070 MHz"},
         "per_mode": per_mode,
         "sequential_pass": {"value": whole_job_rate(per_step, args.steps, world, ms_seq), "unit": "DM-samples/s",
                             "ms_per_step": ms_seq / args.steps,

@@ -475,7 +475,6 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
   const int awp = static_cast<int>(aw0 % a.R);
   const int NL = a.nleaves, C = a.C, G = a.G, span = a.span, cspan = a.cspan;
   const int span_eff = min(span, a.tile_words + a.span_extra);
-  const int nchunk = (span_eff + 31) >> 5;  // 32-word chunks of one leaf series
 
   // leaf series are stored as word pairs (w[j], w[j+1]) so a gather is one 64-bit load
   // shared memory: leaf series (word pairs) + two staging buffers, each holding one group's
@@ -538,54 +537,30 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
     const int* eleaf = reinterpret_cast<const int*>(epk + epk_w);
     (void)ng;
     __syncthreads();
-    // 2. phase 1: distinct (leaf, pattern) series. Binary trees (one plane, two CTAs per SM)
-    //    take one entry per warp; graded and float trees deal (entry, 32-word chunk) pairs
-    //    to the warps in contiguous runs of equal length, so no warp idles on a third entry
-    uint32_t pk[NC];
-    const uint32_t* wch[NC];
-    int cs = 0;
-    uint2* out = ser;
-    auto entry = [&](int e) {  // channel offsets and output of entry e
+    // 2. phase 1: distinct (leaf, pattern) series, one entry per warp, lanes over words
+    for (int e = wd; e < ne; e += NW) {
       const int kl = eleaf[e];
-      cs = CT ? CT : min(C, a.nchan - (g0 + kl) * C);
+      const int cs = CT ? CT : min(C, a.nchan - (g0 + kl) * C);
+      uint32_t pk[NC];
+      const uint32_t* wch[NC];
 #pragma unroll
       for (int ci = 0; ci < NC; ++ci) {
         pk[ci] = (CT || ci < cs) ? epk[e * C + ci] : 0u;
         wch[ci] = win + (kl * C + ci) * cspan + (pk[ci] >> 5);
       }
-      out = ser + e * PL * span;
-    };
-    auto series_word = [&](int j) {  // word j of the current entry's series, as word pairs
-      uint32_t x[NC];
+      uint2* out = ser + e * PL * span;
+      for (int j = lane; j < span_eff; j += 32) {
+        uint32_t x[NC];
 #pragma unroll
-      for (int ci = 0; ci < NC; ++ci)
-        x[ci] = (CT || ci < cs) ? funnel(wch[ci][j], wch[ci][j + 1], pk[ci] & 31) : 0u;
-      uint32_t v[PL];
-      T::template leaf<NC>(a, x, cs, v);
+        for (int ci = 0; ci < NC; ++ci)
+          x[ci] = (CT || ci < cs) ? funnel(wch[ci][j], wch[ci][j + 1], pk[ci] & 31) : 0u;
+        uint32_t v[PL];
+        T::template leaf<NC>(a, x, cs, v);
 #pragma unroll
-      for (int p = 0; p < PL; ++p) {
-        out[p * span + j].x = v[p];
-        if (j > 0) out[p * span + j - 1].y = v[p];
-      }
-    };
-    if constexpr (MODE == kBinary) {
-      for (int e = wd; e < ne; e += NW) {
-        entry(e);
-        for (int j = lane; j < span_eff; j += 32) series_word(j);
-      }
-    } else {
-      const int nit = ne * nchunk;
-      const int per = (nit + NW - 1) / NW;
-      const int it0 = min(nit, wd * per), it1 = min(nit, it0 + per);
-      int e = it0 / nchunk, jc = it0 - e * nchunk;
-      for (int it = it0; it < it1; ++it) {
-        if (it == it0 || jc == 0) entry(e);
-        const int j = jc * 32 + lane;
-        if (++jc == nchunk) {
-          jc = 0;
-          ++e;
+        for (int p = 0; p < PL; ++p) {
+          out[p * span + j].x = v[p];
+          if (j > 0) out[p * span + j - 1].y = v[p];
         }
-        if (j < span_eff) series_word(j);
       }
     }
     __syncthreads();
