@@ -17,6 +17,7 @@
 // Mode A floors sigma at sigma_min; Mode C scores the integer root counts (S/N does not
 // change under the 1/sqrt(N_f) scale).
 
+#include <climits>
 #include <cmath>
 
 #include "snd_internal.h"
@@ -228,8 +229,10 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
   const uint32_t* P = reinterpret_cast<const uint32_t*>(y);
   const uint4* P4 = reinterpret_cast<const uint4*>(y);
   // 4. threshold: lane m of an iteration tests start times 4m..4m+3 against every width of the
-  //    row (window ends P[4m + W ...] are group m + W/4 for W >= 4, groups m and m+1 below);
-  //    eight lanes' nibbles make one mask word
+  //    row (window ends P[4m + W ...] are group m + W/4 for W >= 4, groups m and m+1 below).
+  //    A cell passes iff max over widths of S_W - tau_W >= 0; S_W < 2^31 and tau_W < 2^31, so
+  //    the wrapped difference P[t+W] - P[t] - tau_W read as int32 is exact. Eight lanes'
+  //    nibbles make one mask word.
   const int ngt = (nb + 3) >> 2;
   for (int base = wid * 32; base < ngt; base += NWARP * 32) {
     const int m = base + lane;
@@ -237,30 +240,39 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
     if (m < ngt) {
       const uint4 p = P4[m];
       const uint4 q = P4[m + 1];
+      int h0 = INT_MIN, h1 = INT_MIN, h2 = INT_MIN, h3 = INT_MIN;
+      auto upd = [](int& h, uint32_t end, uint32_t start, int tj) {
+        h = max(h, static_cast<int>(end - start - static_cast<uint32_t>(tj)));
+      };
       if (wm & 1u) {
-        const int tj = tw[0];
-        nib |= (static_cast<int>(p.y - p.x) >= tj ? 1u : 0u) | (static_cast<int>(p.z - p.y) >= tj ? 2u : 0u) |
-               (static_cast<int>(p.w - p.z) >= tj ? 4u : 0u) | (static_cast<int>(q.x - p.w) >= tj ? 8u : 0u);
+        upd(h0, p.y, p.x, tw[0]);
+        upd(h1, p.z, p.y, tw[0]);
+        upd(h2, p.w, p.z, tw[0]);
+        upd(h3, q.x, p.w, tw[0]);
       }
       if (wm & 2u) {
-        const int tj = tw[1];
-        nib |= (static_cast<int>(p.z - p.x) >= tj ? 1u : 0u) | (static_cast<int>(p.w - p.y) >= tj ? 2u : 0u) |
-               (static_cast<int>(q.x - p.z) >= tj ? 4u : 0u) | (static_cast<int>(q.y - p.w) >= tj ? 8u : 0u);
+        upd(h0, p.z, p.x, tw[1]);
+        upd(h1, p.w, p.y, tw[1]);
+        upd(h2, q.x, p.z, tw[1]);
+        upd(h3, q.y, p.w, tw[1]);
       }
       if (wm & 4u) {
-        const int tj = tw[2];
-        nib |= (static_cast<int>(q.x - p.x) >= tj ? 1u : 0u) | (static_cast<int>(q.y - p.y) >= tj ? 2u : 0u) |
-               (static_cast<int>(q.z - p.z) >= tj ? 4u : 0u) | (static_cast<int>(q.w - p.w) >= tj ? 8u : 0u);
+        upd(h0, q.x, p.x, tw[2]);
+        upd(h1, q.y, p.y, tw[2]);
+        upd(h2, q.z, p.z, tw[2]);
+        upd(h3, q.w, p.w, tw[2]);
       }
 #pragma unroll
       for (int j = 3; j < kNumWidthSlots; ++j) {
         if ((wm >> j) & 1u) {
           const uint4 e = P4[m + (1 << (j - 2))];
-          const int tj = tw[j];
-          nib |= (static_cast<int>(e.x - p.x) >= tj ? 1u : 0u) | (static_cast<int>(e.y - p.y) >= tj ? 2u : 0u) |
-                 (static_cast<int>(e.z - p.z) >= tj ? 4u : 0u) | (static_cast<int>(e.w - p.w) >= tj ? 8u : 0u);
+          upd(h0, e.x, p.x, tw[j]);
+          upd(h1, e.y, p.y, tw[j]);
+          upd(h2, e.z, p.z, tw[j]);
+          upd(h3, e.w, p.w, tw[j]);
         }
       }
+      nib = (h0 >= 0 ? 1u : 0u) | (h1 >= 0 ? 2u : 0u) | (h2 >= 0 ? 4u : 0u) | (h3 >= 0 ? 8u : 0u);
       const int rem = nb - 4 * m;  // start times of this group inside the block
       if (rem < 4) nib &= (1u << rem) - 1u;
     }
