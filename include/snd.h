@@ -62,7 +62,8 @@ typedef struct snd_plan_s* snd_plan_t;
 
 /* Option flag: evaluate the tree with the slow scalar verification kernel (one thread per
  * DM-sample, integer counts from the full delay table) instead of the tiled bit-sliced
- * kernel. Results are identical; it exists to cross-check the fast kernel. */
+ * kernel, and the mask closing as four separate separable passes instead of the fused
+ * tiled kernel. Results are identical; it exists to cross-check the fast kernels. */
 #define SND_FLAG_REFERENCE_TREE 1
 /* Option flag (SND_MODE_ZFLOAT only): store the payload and every partial sum below the root
  * in FP16 (round to nearest even) instead of FP32; accumulation stays FP32. */

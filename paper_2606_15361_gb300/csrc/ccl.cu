@@ -64,6 +64,96 @@ __global__ void k_close_v(const uint32_t* __restrict__ in, uint32_t* __restrict_
   out[static_cast<size_t>(d) * mw + q] = acc;
 }
 
+// The four closing passes fused: a CTA owns a tile of kCloseTR rows x kCloseTQ words and
+// stages the rows and words its two dilation + erosion passes reach (2r rows and two words
+// each side) in shared memory. Each pass follows k_close_h / k_close_v exactly: outside
+// the plane the dilation reads 0 and the erosion 1, bits past nb are cleared after every
+// pass (and read as 1 by the horizontal erosion).
+constexpr int kCloseTR = 32, kCloseTQ = 32, kCloseNQ = kCloseTQ + 4, kCloseThreads = 256;
+
+__global__ void __launch_bounds__(kCloseThreads) k_close(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                         int ndm, int mw, int nb, int r) {
+  extern __shared__ uint32_t csm[];
+  const int NR = kCloseTR + 4 * r;
+  uint32_t* A = csm;                 // [NR][kCloseNQ]: input, then the dilated tile
+  uint32_t* Bv = csm + NR * kCloseNQ;  // [NR][kCloseNQ]: horizontal pass results
+  const int d0 = blockIdx.y * kCloseTR, q0 = blockIdx.x * kCloseTQ;
+  const int R0 = d0 - 2 * r, W0 = q0 - 2;
+  const int nbw = (nb + 31) >> 5;
+  const uint32_t tailvalid = (nb & 31) ? ((1u << (nb & 31)) - 1u) : 0xFFFFFFFFu;
+  const int n = NR * kCloseNQ;
+  const int tid = threadIdx.x;
+  // 1. input tile, dilation's outside value 0
+  for (int idx = tid; idx < n; idx += kCloseThreads) {
+    const int i = idx / kCloseNQ, k = idx - i * kCloseNQ;
+    const int d = R0 + i, q = W0 + k;
+    uint32_t w = 0u;
+    if (d >= 0 && d < ndm && q >= 0 && q < nbw) {
+      w = in[static_cast<size_t>(d) * mw + q];
+      if (q == nbw - 1) w &= tailvalid;
+    }
+    A[idx] = w;
+  }
+  __syncthreads();
+  // 2. horizontal dilation, words 1 .. NQ-2
+  for (int idx = tid; idx < n; idx += kCloseThreads) {
+    const int i = idx / kCloseNQ, k = idx - i * kCloseNQ;
+    if (k < 1 || k > kCloseNQ - 2) continue;
+    const uint32_t a = A[idx - 1], b = A[idx], c = A[idx + 1];
+    uint32_t acc = b;
+    for (int kk = 1; kk <= r; ++kk) acc |= __funnelshift_r(b, c, kk) | __funnelshift_l(a, b, kk);
+    if (W0 + k == nbw - 1) acc &= tailvalid;
+    Bv[idx] = acc;
+  }
+  __syncthreads();
+  // 3. vertical dilation into A, rows r .. NR-r-1, words 1 .. NQ-2
+  for (int idx = tid; idx < n; idx += kCloseThreads) {
+    const int i = idx / kCloseNQ, k = idx - i * kCloseNQ;
+    if (i < r || i >= NR - r || k < 1 || k > kCloseNQ - 2) continue;
+    const int d = R0 + i;
+    uint32_t acc = 0u;
+    for (int j = -r; j <= r; ++j) {
+      const int dd = d + j;
+      if (dd >= 0 && dd < ndm) acc |= Bv[idx + j * kCloseNQ];
+    }
+    if (W0 + k == nbw - 1) acc &= tailvalid;
+    A[idx] = acc;
+  }
+  __syncthreads();
+  // 4. horizontal erosion into Bv, rows r .. NR-r-1, words 2 .. NQ-3 (outside reads 1)
+  for (int idx = tid; idx < n; idx += kCloseThreads) {
+    const int i = idx / kCloseNQ, k = idx - i * kCloseNQ;
+    if (i < r || i >= NR - r || k < 2 || k > kCloseNQ - 3) continue;
+    auto word = [&](int kk) -> uint32_t {
+      const int q = W0 + kk;
+      if (q < 0 || q >= nbw) return 0xFFFFFFFFu;
+      uint32_t w = A[i * kCloseNQ + kk];
+      if (q == nbw - 1) w |= ~tailvalid;
+      return w;
+    };
+    const uint32_t a = word(k - 1), b = word(k), c = word(k + 1);
+    uint32_t acc = b;
+    for (int kk = 1; kk <= r; ++kk) acc &= __funnelshift_r(b, c, kk) & __funnelshift_l(a, b, kk);
+    if (W0 + k == nbw - 1) acc &= tailvalid;
+    Bv[idx] = acc;
+  }
+  __syncthreads();
+  // 5. vertical erosion to the output tile, rows 2r .. NR-2r-1, words 2 .. NQ-3
+  for (int idx = tid; idx < n; idx += kCloseThreads) {
+    const int i = idx / kCloseNQ, k = idx - i * kCloseNQ;
+    if (i < 2 * r || i >= NR - 2 * r || k < 2 || k > kCloseNQ - 3) continue;
+    const int d = R0 + i, q = W0 + k;
+    if (d >= ndm || q >= nbw) continue;
+    uint32_t acc = 0xFFFFFFFFu;
+    for (int j = -r; j <= r; ++j) {
+      const int dd = d + j;
+      if (dd >= 0 && dd < ndm) acc &= Bv[idx + j * kCloseNQ];
+    }
+    if (q == nbw - 1) acc &= tailvalid;
+    out[static_cast<size_t>(d) * mw + q] = acc;
+  }
+}
+
 // One warp per row: number of runs (run starts) of the closed mask.
 __global__ void k_run_count(const uint32_t* __restrict__ m, int ndm, int mw, int nb, int32_t* row_runs) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -91,21 +181,33 @@ __global__ void k_scan_rows(int32_t* row_runs, int ndm, uint32_t* counters, int 
   const int lo = min(ndm, tid * per), hi = min(ndm, lo + per);
   int s = 0;
   for (int i = lo; i < hi; ++i) s += row_runs[i];
-  part[tid] = s;
+  // exclusive scan of the 1024 partial sums: within each warp, then over the 32 warp totals
+  const int lane = tid & 31, wid = tid >> 5;
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) part[wid] = incl;
   __syncthreads();
-  if (tid == 0) {
-    int acc = 0;
-    for (int i = 0; i < 1024; ++i) {
-      const int v = part[i];
-      part[i] = acc;
-      acc += v;
+  if (wid == 0) {
+    const int t = part[lane];
+    int wincl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xFFFFFFFFu, wincl, o);
+      if (lane >= o) wincl += u;
     }
-    row_runs[ndm] = acc;
-    counters[kCntRuns] = static_cast<uint32_t>(acc);
-    if (acc > run_cap) atomicOr(&counters[kCntStatus], kStatusRunOverflow);
+    part[32 + lane] = wincl - t;
+    if (lane == 31) {
+      row_runs[ndm] = wincl;
+      counters[kCntRuns] = static_cast<uint32_t>(wincl);
+      if (wincl > run_cap) atomicOr(&counters[kCntStatus], kStatusRunOverflow);
+    }
   }
   __syncthreads();
-  int acc = part[tid];
+  int acc = part[32 + wid] + incl - s;
   for (int i = lo; i < hi; ++i) {
     const int v = row_runs[i];
     row_runs[i] = acc;
@@ -324,12 +426,18 @@ cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_
   const int r = p.closing / 2;
   const int nbw = (nb + 31) / 32;
   dim3 blk(128), grd((nbw + 127) / 128, p.ndm);
-  if (r > 0) {
+  if (r > 0 && (p.flags & kFlagReferenceTree)) {
+    // reference path: the four separable passes as separate launches
     p.launches += 4;
     k_close_h<<<grd, blk, 0, s>>>(dp.mask, dp.mask2, p.mw, nb, r, 0);
     k_close_v<<<grd, blk, 0, s>>>(dp.mask2, dp.mask3, p.ndm, p.mw, nb, r, 0);
     k_close_h<<<grd, blk, 0, s>>>(dp.mask3, dp.mask2, p.mw, nb, r, 1);
     k_close_v<<<grd, blk, 0, s>>>(dp.mask2, dp.mask3, p.ndm, p.mw, nb, r, 1);
+  } else if (r > 0) {
+    p.launches += 1;
+    const int smem = 2 * (kCloseTR + 4 * r) * kCloseNQ * static_cast<int>(sizeof(uint32_t));
+    dim3 cg((nbw + kCloseTQ - 1) / kCloseTQ, (p.ndm + kCloseTR - 1) / kCloseTR);
+    k_close<<<cg, kCloseThreads, smem, s>>>(dp.mask, dp.mask3, p.ndm, p.mw, nb, r);
   } else {
     cudaMemcpyAsync(dp.mask3, dp.mask, sizeof(uint32_t) * static_cast<size_t>(p.ndm) * p.mw,
                     cudaMemcpyDeviceToDevice, s);

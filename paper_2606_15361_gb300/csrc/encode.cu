@@ -32,9 +32,17 @@ __global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk,
   const int r0 = blockIdx.y * kHistRowsPerBlock;
   const int r1 = min(nsamp, r0 + kHistRowsPerBlock);
   if (c < nchan) {
-    for (int r = r0 + wy; r < r1; r += 8) {
-      const uint32_t v = chunk[static_cast<size_t>(r) * nchan + c];
-      atomicAdd(&h[v][lane], 1u);
+    // eight rows per warp in flight before their shared-memory increments
+    for (int r = r0 + wy; r < r1; r += 64) {
+      uint32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int rr = r + 8 * k;
+        v[k] = rr < r1 ? static_cast<uint32_t>(__ldg(chunk + static_cast<size_t>(rr) * nchan + c)) : 256u;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (v[k] < 256u) atomicAdd(&h[v[k]][lane], 1u);
     }
   }
   __syncthreads();
@@ -224,10 +232,11 @@ __global__ void __launch_bounds__(256) k_pack32(const uint8_t* __restrict__ chun
     if (lane == j) mine = word;
   }
   const long long s0 = aw * 32;
-  const uint32_t keep = (s0 < t0) ? ((1u << static_cast<int>(t0 - s0)) - 1u) : 0u;
   const int phys = static_cast<int>(aw % R);
   uint32_t* row = ring + static_cast<size_t>(c0 + lane) * 2 * R;
-  const uint32_t w = (row[phys] & keep) | mine;
+  uint32_t w = mine;
+  // only the chunk's first word keeps bits of samples before the chunk (previous chunk)
+  if (s0 < t0) w |= row[phys] & ((1u << static_cast<int>(t0 - s0)) - 1u);
   row[phys] = w;
   row[phys + R] = w;
 }
