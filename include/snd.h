@@ -178,9 +178,13 @@ int snd_execute(snd_plan_t plan, const uint8_t* d_chunk, int32_t nsamp, void* st
                 void* d_plane_out, int32_t* nemit_out);
 
 /*
- * Same as snd_execute for a HOST chunk: copies h_chunk into the workspace's staging area
- * (cudaMemcpyAsync on `stream`) and then runs the path. h_chunk must stay unchanged until
- * the stream passes the copy; page-locked memory makes the copy asynchronous.
+ * Same as snd_execute for a HOST chunk: copies h_chunk into one of the workspace's two
+ * staging areas and then runs the path on `stream`. The copy runs on a private stream of
+ * the plan that waits only for the chunk before last (the previous user of that staging
+ * area), so it overlaps the previous chunk's kernels; the work on `stream` waits for the
+ * copy. h_chunk must therefore already hold the chunk when the call is made (it may be read
+ * before earlier work on `stream` completes) and stay unchanged until `stream` passes this
+ * chunk; page-locked memory makes the copy asynchronous.
  */
 int snd_execute_host(snd_plan_t plan, const uint8_t* h_chunk, int32_t nsamp, void* stream,
                      void* d_plane_out, int32_t* nemit_out);

@@ -285,6 +285,7 @@ int build_plan(Plan& p) {
   p.off.bcand = take(sizeof(snd_candidate_t) * static_cast<size_t>(p.cand_cap));
   p.off.cand = take(sizeof(snd_candidate_t) * static_cast<size_t>(p.cand_cap));
   p.off.staging = take(static_cast<size_t>(p.max_chunk) * nchan);
+  p.off.staging2 = take(static_cast<size_t>(p.max_chunk) * nchan);
   p.off.width_mask = take(sizeof(uint16_t) * ndm);
   p.off.dm_f32 = take(sizeof(float) * ndm);
   p.off.tp_off = take(sizeof(int32_t) * p.tp_off.size());

@@ -123,6 +123,7 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.bcand = at<snd_candidate_t>(d_ws, o.bcand);
   dp.cand = at<snd_candidate_t>(d_ws, o.cand);
   dp.staging = at<uint8_t>(d_ws, o.staging);
+  dp.staging2 = at<uint8_t>(d_ws, o.staging2);
   dp.width_mask = at<uint16_t>(d_ws, o.width_mask);
   dp.dm_f32 = at<float>(d_ws, o.dm_f32);
   dp.tp_off = at<int32_t>(d_ws, o.tp_off);
@@ -137,6 +138,13 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.zwb = z ? at<int32_t>(d_ws, o.zwb) : nullptr;
   dp.zcarry = z ? at<int32_t>(d_ws, o.zcarry) : nullptr;
   std::vector<float> dmf(p.dms.begin(), p.dms.end());
+  // uploads still in flight target the previous workspace
+  if (p.up_stream && cudaStreamSynchronize(p.up_stream) != cudaSuccess) {
+    p.bound = false;
+    return SND_ERR_CUDA;
+  }
+  p.up_free_set[0] = p.up_free_set[1] = false;
+  p.up_next = 0;
   cudaError_t e = cudaMemsetAsync(d_ws, 0, p.ws_bytes, s);
   if (e == cudaSuccess) e = upload(d_ws, o.width_mask, p.width_mask, s);
   if (e == cudaSuccess) e = upload(d_ws, o.dm_f32, dmf, s);
@@ -198,6 +206,14 @@ extern "C" int snd_profile_read(snd_plan_t plan, double* ms_out, int64_t* count_
 
 snd::Plan::~Plan() {
   for (cudaEvent_t ev : ev_pool) cudaEventDestroy(ev);
+  if (up_stream) {
+    cudaStreamSynchronize(up_stream);
+    cudaStreamDestroy(up_stream);
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (up_done[b]) cudaEventDestroy(up_done[b]);
+    if (up_free[b]) cudaEventDestroy(up_free[b]);
+  }
 }
 
 extern "C" int snd_execute(snd_plan_t plan, const uint8_t* d_chunk, int32_t nsamp, void* stream,
@@ -221,9 +237,31 @@ extern "C" int snd_execute_host(snd_plan_t plan, const uint8_t* h_chunk, int32_t
   if (nsamp < 1 || nsamp > p.max_chunk) return SND_ERR_CHUNK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = static_cast<size_t>(nsamp) * p.nchan;
-  if (cudaMemcpyAsync(p.dp.staging, h_chunk, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (!p.up_stream) {
+    if (cudaStreamCreateWithFlags(&p.up_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      p.up_stream = nullptr;
+      return fail(p, SND_ERR_CUDA);
+    }
+    for (int b = 0; b < 2; ++b)
+      if (cudaEventCreateWithFlags(&p.up_done[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p.up_free[b], cudaEventDisableTiming) != cudaSuccess)
+        return fail(p, SND_ERR_CUDA);
+  }
+  // buffer b was last read by the chunk before the previous one: wait for that chunk only,
+  // not for the rest of `stream`, so this copy overlaps the previous chunk's kernels
+  const int b = p.up_next;
+  uint8_t* buf = b ? p.dp.staging2 : p.dp.staging;
+  if (p.up_free_set[b] && cudaStreamWaitEvent(p.up_stream, p.up_free[b], 0) != cudaSuccess)
     return fail(p, SND_ERR_CUDA);
-  return run_chunk(p, p.dp.staging, nsamp, s, d_plane_out, nemit_out);
+  if (cudaMemcpyAsync(buf, h_chunk, bytes, cudaMemcpyHostToDevice, p.up_stream) != cudaSuccess ||
+      cudaEventRecord(p.up_done[b], p.up_stream) != cudaSuccess || cudaStreamWaitEvent(s, p.up_done[b], 0) != cudaSuccess)
+    return fail(p, SND_ERR_CUDA);
+  const int rc = run_chunk(p, buf, nsamp, s, d_plane_out, nemit_out);
+  if (rc != SND_OK) return rc;
+  if (cudaEventRecord(p.up_free[b], s) != cudaSuccess) return fail(p, SND_ERR_CUDA);
+  p.up_free_set[b] = true;
+  p.up_next = b ^ 1;
+  return SND_OK;
 }
 
 extern "C" int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_t cap, int32_t* n_out) {

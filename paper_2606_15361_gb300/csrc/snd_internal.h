@@ -92,7 +92,8 @@ struct DevPtrs {
   int32_t* pwidth;         // [run_cap] width of the island's peak cell
   snd_candidate_t* bcand;  // [cand_cap] candidates of the current block (unsorted)
   snd_candidate_t* cand;   // [cand_cap] accumulated sorted candidates
-  uint8_t* staging;        // [max_chunk * nchan] host-chunk staging
+  uint8_t* staging;        // [max_chunk * nchan] host-chunk staging (two buffers, used in turn)
+  uint8_t* staging2;       // [max_chunk * nchan]
   // plan tables
   uint16_t* width_mask;    // [ndm]
   float* dm_f32;           // [ndm]
@@ -160,7 +161,7 @@ struct Plan {
   size_t ws_bytes = 0;
   struct Off {
     size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
-        run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, width_mask, dm_f32, tp_off,
+        run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, staging2, width_mask, dm_f32, tp_off,
         gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb, zcarry;
   } off{};
 
@@ -176,6 +177,14 @@ struct Plan {
   int sticky = 0;
   int pending_host = -1;
   mutable int64_t launches = 0;  // kernels enqueued since binding
+
+  // host-chunk uploads (snd_execute_host): the two staging buffers are filled in turn on a
+  // private copy stream, so chunk i+1's copy overlaps chunk i's kernels
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_done[2] = {nullptr, nullptr};  // copy into buffer b finished
+  cudaEvent_t up_free[2] = {nullptr, nullptr};  // the chunk that read buffer b finished
+  bool up_free_set[2] = {false, false};
+  int up_next = 0;
 
   // per-stage timing (snd_profile)
   bool profiling = false;

@@ -100,6 +100,42 @@ def test_nc64_reference_kernel(mode):
     run_both(w.freqs(), synth.NC_DT, w.dms(), MODES[mode], cfg, [w.chunk_data(0)], flags=g.FLAG_REFERENCE_TREE)
 
 
+@pytest.mark.parametrize("mode", ["graded", "float"])
+def test_nc64_host_chunks_overlapped_uploads(mode):
+    """Ragged page-locked host chunks through snd_execute_host on a side stream with no
+    synchronisation between calls: the two staging buffers alternate and each upload waits
+    only for the chunk before last, so uploads overlap the previous chunk's kernels. Every
+    plane and the candidates still match the oracle."""
+    w = synth.NC64
+    data = w.chunk_data(0)
+    cuts = [0, 1300, 1301, 5000, 5037, 9000, 12000, 16384]
+    chunks = [torch.from_numpy(np.ascontiguousarray(data[a:b])).pin_memory() for a, b in zip(cuts[:-1], cuts[1:])]
+    cfg = ostream.defaults(MODES[mode], branching=2)
+    plan = g.Plan(w.freqs(), synth.NC_DT, w.dms(), cfg.branching, MODES[mode], _opts(MODES[mode], cfg, 0))
+    ref = ostream.OracleStream(w.freqs(), synth.NC_DT, w.dms(), cfg)
+    side = torch.cuda.Stream()
+    outs = []
+    for ch in chunks:
+        nemit = plan.nemit_next(ch.shape[0])
+        dtype = torch.float32 if MODES[mode] == ostream.FLOAT else torch.int32
+        out = torch.full((len(w.dms()), max(nemit, 1)), -7, dtype=dtype, device="cuda")
+        side.wait_stream(torch.cuda.current_stream())  # the fill above runs on the default stream
+        assert plan.execute_host(ch, out, stream=side) == nemit
+        outs.append((out, nemit))
+    torch.cuda.synchronize()
+    all_exp = []
+    for ch, (out, nemit) in zip(chunks, outs):
+        r = ref.push(ch.numpy())
+        assert r["e_new"] - r["e_prev"] == nemit
+        if nemit:
+            _compare_plane(MODES[mode], out[:, :nemit].cpu().numpy(), r, w.nchan)
+        all_exp += r["candidates"]
+    cands, rc = plan.candidates()
+    assert rc == 0
+    assert _cand_tuples(cands) == _oracle_cands(all_exp)
+    assert len(cands) >= 1
+
+
 @pytest.mark.parametrize("mode", list(MODES))
 def test_nc64_streaming_ragged_chunks(mode):
     w = synth.NC64
