@@ -474,7 +474,12 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
   const long long aw0 = a.word0 + static_cast<long long>(bx) * a.tile_words;
   const int awp = static_cast<int>(aw0 % a.R);
   const int NL = a.nleaves, C = a.C, G = a.G, span = a.span, cspan = a.cspan;
-  const int span_eff = min(span, a.tile_words + a.span_extra);
+  // words this CTA emits: the chunk's last time tile may hold fewer than tile_words (a chunk
+  // whose emitted range is not word-aligned spans one word more than its length / 32), and
+  // its series, staged windows and phase-2 words shrink with it
+  const int tw_eff = min(a.tile_words, static_cast<int>(a.nwords - static_cast<long long>(bx) * a.tile_words));
+  const int span_eff = min(span, tw_eff + a.span_extra);
+  const int cspan_eff = min(cspan, tw_eff + (cspan - a.tile_words) + 1);
 
   // leaf series are stored as word pairs (w[j], w[j+1]) so a gather is one 64-bit load
   // shared memory: leaf series (word pairs) + two staging buffers, each holding one group's
@@ -506,7 +511,7 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
     for (int cl = wd; cl < c_hi - c_lo; cl += NW) {
       const int c = c_lo + cl;
       const uint32_t* row = a.ring + static_cast<size_t>(c) * 2 * a.R + awp + swb[c];
-      for (int j = lane; j < cspan; j += 32) __pipeline_memcpy_async(win + cl * cspan + j, row + j, 4);
+      for (int j = lane; j < cspan_eff; j += 32) __pipeline_memcpy_async(win + cl * cspan + j, row + j, 4);
     }
     for (int dl = wd; dl < DT; dl += NW) {
       const uint32_t* src = a.gmeta + static_cast<size_t>(min(tile * DT + dl, a.ndm - 1)) * NL + g0;
@@ -598,7 +603,9 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
             for (int jw = 0; jw < KW; ++jw) {
               const int w = lane + 32 * jw;
               uint32_t s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-              if (plain && n == 8) {
+              const bool live = 32 * jw < tw_eff;  // words [32 jw, 32 jw + 32) are emitted here
+              if (!live) {
+              } else if (plain && n == 8) {
                 uint32_t v[8][3];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -637,7 +644,7 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
                 }
               }
               if constexpr (MODE == kFloat) {
-                st.add_node(d, jw, s8);
+                if (live) st.add_node(d, jw, s8);
               } else {
 #pragma unroll
                 for (int p = 0; p < 8; ++p) nd[d].p[jw][p] = s8[p];
@@ -679,6 +686,7 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
               const int sh = m & 31;
 #pragma unroll
               for (int jw = 0; jw < KW; ++jw) {
+                if (32 * jw >= tw_eff) continue;  // no emitted word in this lane slot
                 const int w = lane + 32 * jw;
                 uint32_t v[PL];
 #pragma unroll
@@ -895,9 +903,20 @@ void tree_args(const Plan& p, int64_t e_prev, int64_t e_new, TreeArgs& a, int* n
   }
   a.word0 = e_prev >> 5;
   a.nwords = static_cast<int>(((e_new - 1) >> 5) - (e_prev >> 5) + 1);
-  // spread the words evenly over the fewest tiles of at most tile_words
+  // the fewest tiles of at most tile_words, either spread evenly or (graded and float) full
+  // with one short tail tile, whichever costs less: per tile, 32-word chunks of leaf series
+  // (phase 1, tile + span_extra words), 32-word phase-2 slots and a fixed part, weighted
+  // about 4 : 9 : 2 as measured on the 1024-channel float tree. Binary trees (two CTAs per
+  // SM, cheaper one-plane series) measured faster with even tiles.
   const int ntiles = (a.nwords + g.tile_words - 1) / g.tile_words;
-  a.tile_words = (a.nwords + ntiles - 1) / ntiles;
+  auto tile_cost = [&](int t) { return 4 * ((t + a.span_extra + 31) / 32) + 9 * ((t + 31) / 32) + 2; };
+  auto cost = [&](int tw) {
+    int c = 0;
+    for (int i = 0, left = a.nwords; i < ntiles; ++i, left -= tw) c += tile_cost(left < tw ? left : tw);
+    return c;
+  };
+  const int even = (a.nwords + ntiles - 1) / ntiles;
+  a.tile_words = (p.mode != SND_MODE_BINARY && cost(g.tile_words) < cost(even)) ? g.tile_words : even;
   a.plane = dp.plane;
   a.Lp = p.Lp;
   *ntx = ntiles;
