@@ -32,17 +32,9 @@ __global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk,
   const int r0 = blockIdx.y * kHistRowsPerBlock;
   const int r1 = min(nsamp, r0 + kHistRowsPerBlock);
   if (c < nchan) {
-    // eight rows per warp in flight before their shared-memory increments
-    for (int r = r0 + wy; r < r1; r += 64) {
-      uint32_t v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int rr = r + 8 * k;
-        v[k] = rr < r1 ? static_cast<uint32_t>(__ldg(chunk + static_cast<size_t>(rr) * nchan + c)) : 256u;
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (v[k] < 256u) atomicAdd(&h[v[k]][lane], 1u);
+    for (int r = r0 + wy; r < r1; r += 8) {
+      const uint32_t v = chunk[static_cast<size_t>(r) * nchan + c];
+      atomicAdd(&h[v][lane], 1u);
     }
   }
   __syncthreads();
