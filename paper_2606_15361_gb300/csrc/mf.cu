@@ -113,8 +113,11 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
   if (nb <= 0) return;
   // 2. per-warp totals of contiguous group segments, and the exact integer sums over the
   //    block's start times (y[i], i < nb)
-  const int segg = ((G + NWARP * 32 - 1) / (NWARP * 32)) * 32;
-  const int glo = min(G, wid * segg), ghi = min(G, glo + segg);
+  // warp 0 also finds the row's thresholds in FP64 (a long dependent chain), so the group
+  // segments of both passes go to warps 1..NWARP-1
+  constexpr int NSEG = NWARP - 1;
+  const int segg = ((G + NSEG * 32 - 1) / (NSEG * 32)) * 32;
+  const int glo = wid == 0 ? 0 : min(G, (wid - 1) * segg), ghi = wid == 0 ? 0 : min(G, glo + segg);
   {
     uint32_t tot = 0;
     long long s1 = 0, s2 = 0;
