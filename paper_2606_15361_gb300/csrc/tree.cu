@@ -542,29 +542,49 @@ __device__ __forceinline__ void tree_cta(const TreeArgs& a, int bx, int tile) {
     const int* eleaf = reinterpret_cast<const int*>(epk + epk_w);
     (void)ng;
     __syncthreads();
-    // 2. phase 1: distinct (leaf, pattern) series, one entry per warp, lanes over words
-    for (int e = wd; e < ne; e += NW) {
+    // 2. phase 1: distinct (leaf, pattern) series. Full 32-word chunks: one entry per warp,
+    //    lanes over words. The short remainders (span_eff mod 32 words) of several entries
+    //    share one warp pass, lane l taking word l mod tl of entry l / tl of the pass.
+    const int main_w = span_eff & ~31, tl = span_eff & 31;
+    uint32_t pk[NC];
+    const uint32_t* wch[NC];
+    int cs = 0;
+    uint2* out = ser;
+    auto entry = [&](int e) {  // channel offsets and series of entry e
       const int kl = eleaf[e];
-      const int cs = CT ? CT : min(C, a.nchan - (g0 + kl) * C);
-      uint32_t pk[NC];
-      const uint32_t* wch[NC];
+      cs = CT ? CT : min(C, a.nchan - (g0 + kl) * C);
 #pragma unroll
       for (int ci = 0; ci < NC; ++ci) {
         pk[ci] = (CT || ci < cs) ? epk[e * C + ci] : 0u;
         wch[ci] = win + (kl * C + ci) * cspan + (pk[ci] >> 5);
       }
-      uint2* out = ser + e * PL * span;
-      for (int j = lane; j < span_eff; j += 32) {
-        uint32_t x[NC];
+      out = ser + e * PL * span;
+    };
+    auto series_word = [&](int j) {  // word j of the current entry's series, as word pairs
+      uint32_t x[NC];
 #pragma unroll
-        for (int ci = 0; ci < NC; ++ci)
-          x[ci] = (CT || ci < cs) ? funnel(wch[ci][j], wch[ci][j + 1], pk[ci] & 31) : 0u;
-        uint32_t v[PL];
-        T::template leaf<NC>(a, x, cs, v);
+      for (int ci = 0; ci < NC; ++ci)
+        x[ci] = (CT || ci < cs) ? funnel(wch[ci][j], wch[ci][j + 1], pk[ci] & 31) : 0u;
+      uint32_t v[PL];
+      T::template leaf<NC>(a, x, cs, v);
 #pragma unroll
-        for (int p = 0; p < PL; ++p) {
-          out[p * span + j].x = v[p];
-          if (j > 0) out[p * span + j - 1].y = v[p];
+      for (int p = 0; p < PL; ++p) {
+        out[p * span + j].x = v[p];
+        if (j > 0) out[p * span + j - 1].y = v[p];
+      }
+    };
+    for (int e = wd; e < ne; e += NW) {
+      entry(e);
+      for (int j = lane; j < main_w; j += 32) series_word(j);
+    }
+    if (tl > 0) {
+      const int epi = 32 / tl;  // entries per pass
+      const int el = lane / tl, jl = lane - el * tl;
+      for (int e0 = wd * epi; e0 < ne; e0 += NW * epi) {
+        const int e = e0 + el;
+        if (el < epi && e < ne) {
+          entry(e);
+          series_word(main_w + jl);
         }
       }
     }
