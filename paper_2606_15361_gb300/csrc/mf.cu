@@ -42,6 +42,7 @@ struct MfArgs {
   void* plane_out;
   int nemit;
   int out_u8;       // caller's plane in uint8 (binary / graded roots are 0..255)
+  int pf_rows;      // rows resident at once: row d prefetches row d + pf_rows into L2
 };
 
 constexpr int kMfThreads = 256;
@@ -220,6 +221,16 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
     }
   }
   __syncthreads();
+  // the row a CTA of the next wave will stage: its segment into L2 while this row is scored
+  if (d + a.pf_rows < a.ndm) {
+    const int32_t* nsrc = a.plane + static_cast<size_t>(d + a.pf_rows) * a.Lp;
+    const int nlines = (4 * G + 31) >> 5;  // 128-byte lines of the staged columns
+    for (int k = tid; k < nlines; k += kMfThreads) {
+      int col = c0 - r0 + 32 * k;
+      if (col >= a.Lp) col -= a.Lp;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(nsrc + col));
+    }
+  }
   const int nbw = (nb + 31) >> 5;
   uint32_t* mrow = a.mask + static_cast<size_t>(d) * a.mw;
   if (!s_ok) {
@@ -347,6 +358,14 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
   const int smem = ((len >> 2) + 3) * 16;  // front pad (4 words) and len/4 + 2 aligned groups
   cudaError_t e = cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  {
+    int dev = 0, nsm = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mf, kMfThreads, smem);
+    if (e != cudaSuccess) return e;
+    a.pf_rows = per_sm > 0 ? nsm * per_sm : p.ndm;
+  }
   k_mf<<<p.ndm, kMfThreads, smem, s>>>(a);
   p.launches += 1;
   return cudaGetLastError();

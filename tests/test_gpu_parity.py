@@ -191,6 +191,20 @@ def test_edge_configurations(case):
     run_both(f, synth.NC_DT, dms, mode, cfg, chunks)
 
 
+@pytest.mark.parametrize("size", [1, 3, 15, 31])
+@pytest.mark.parametrize("ref", [False, True], ids=["fused", "separable"])
+def test_closing_sizes(size, ref):
+    """Closing element sides from 1 (no closing) to the largest allowed, through the fused
+    tiled kernel and the four separable passes (reference flag), on a 64-channel beam with a
+    low detection threshold so that many mask cells and islands meet the tile borders."""
+    w = synth.NC64
+    data = w.chunk_data(0)
+    cfg = ostream.defaults(ostream.FLOAT, branching=2, det_theta=4.0, closing=size, n_min=3)
+    flags = g.FLAG_REFERENCE_TREE if ref else 0
+    c = run_both(w.freqs(), synth.NC_DT, w.dms(), ostream.FLOAT, cfg, [data[:9000], data[9000:]], flags=flags)
+    assert len(c) >= 3
+
+
 def test_capacity_overflow_reports_and_keeps_prefix():
     w = synth.NC64
     cfg = ostream.defaults(ostream.GRADED, branching=2)
