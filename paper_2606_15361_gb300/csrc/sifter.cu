@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(192, 1)
 // Implicit-GEMM 3x3 convolution on the tensor cores (conv2 and conv3 forward):
 //   Y^T[cout][m] = relu(sum_k A[m][k] W[cout][k] + b),  A[m][k] = x[ci][b][y+ky-1][x+kx-1]
 // with m = (b, y, x), the patch gathered in tap-major order (k = (ky*3 + kx)*cin + ci, the
-// weights permuted to match), i.e. the im2col GEMM without the im2col buffer. 288 threads: warps 0-3 drain the TMEM accumulator, warps 4-7 build the A
+// weights permuted to match), i.e. the im2col GEMM without the im2col buffer. The input map
+// is channels-last, so eight consecutive K values are one 16-byte load. 288 threads: warps 0-3 drain the TMEM accumulator, warps 4-7 build the A
 // tile of every K step in shared memory (one tile row per thread, in the 128-byte swizzled
 // K-major layout the MMA reads, made visible to the tensor core with a proxy fence) while one
 // of them also TMA-loads the weight tile, and warp 8 owns TMEM and issues the MMAs. CTAs are
@@ -318,7 +319,7 @@ __device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes
 }
 
 struct ConvArgs {
-  const bf16* x;    // input activations [cin][n][h][w]
+  const bf16* x;    // input activations, channels-last [n][h][w][cin]
   int n, h, w, cin, kc, ktiles;
   const float* bias;
   bf16* yT;         // output [cout][n*h*w]
@@ -379,14 +380,14 @@ __global__ void __launch_bounds__(288, 1)
       const int b = mv ? static_cast<int>(m / hw) : 0;
       const int yx = mv ? static_cast<int>(m - b * hw) : 0;
       const int yy = yx / a.w, xx = yx - yy * a.w;
-      const bf16* xb = a.x + static_cast<long long>(b) * hw;
+      const bf16* xb = a.x + static_cast<long long>(b) * hw * CIN;  // channels-last input
       const bf16* tp[9];
       bool tv[9];
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
         tv[tap] = mv && sy >= 0 && sy < a.h && sx >= 0 && sx < a.w;
-        tp[tap] = xb + (tv[tap] ? sy * a.w + sx : 0);
+        tp[tap] = xb + (tv[tap] ? (sy * a.w + sx) * CIN : 0);
       }
       bool quit = false;
 #pragma unroll
@@ -406,16 +407,13 @@ __global__ void __launch_bounds__(288, 1)
         const uint32_t rowaddr = sA + s * kABytes + pr * 128;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          __align__(16) bf16 v[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            constexpr int kc = 9 * CIN;
-            const int k = i * kBK + q * 8 + e;  // compile-time after unrolling
-            const int tap = k / CIN, ci = k % CIN;
-            v[e] = (k < kc && tv[tap < 9 ? tap : 0]) ? tp[tap < 9 ? tap : 0][static_cast<long long>(ci) * M]
-                                                     : __float2bfloat16_rn(0.0f);
-          }
-          const uint4 pk = *reinterpret_cast<const uint4*>(v);
+          // the 8 K values of chunk q are 8 consecutive channels of one tap (CIN % 8 == 0):
+          // one 16-byte load from the channels-last map
+          constexpr int kc = 9 * CIN;
+          const int k0 = i * kBK + q * 8;  // compile-time after unrolling
+          const int tap = k0 / CIN, ci0 = k0 % CIN;
+          uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+          if (k0 < kc && tv[tap < 9 ? tap : 0]) pk = __ldg(reinterpret_cast<const uint4*>(tp[tap < 9 ? tap : 0] + ci0));
           const uint32_t dst = rowaddr + ((q ^ (pr & 7)) << 4);
           asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk.x), "r"(pk.y), "r"(pk.z),
                        "r"(pk.w)
@@ -535,9 +533,11 @@ __global__ void __launch_bounds__(256) k_conv1(const float* __restrict__ x, int 
   }
 }
 
-// colT[k][m] for k < kc (the weight-gradient GEMM's B operand, K-major along m)
+// colT[k][m] for k < kc (the weight-gradient GEMM's B operand, K-major along m) from a
+// channels-last map x[n][h][w][cin], cin = kc / 9 (the snippets themselves for cin = 1)
 template <typename T>
 __global__ void k_im2colT(const T* __restrict__ x, int n, int h, int w, int kc, bf16* __restrict__ colT) {
+  const int cin = kc / 9;
   const long long hw = static_cast<long long>(h) * w;
   const long long mtot = static_cast<long long>(n) * hw;
   const long long total = mtot * kc;
@@ -552,7 +552,7 @@ __global__ void k_im2colT(const T* __restrict__ x, int n, int h, int w, int kc, 
     const int sy = yy + ky - 1, sx = xx + kx - 1;
     float val = 0.0f;
     if (sy >= 0 && sy < h && sx >= 0 && sx < w)
-      val = static_cast<float>(x[static_cast<long long>(ci) * mtot + b * hw + sy * w + sx]);
+      val = static_cast<float>(x[(b * hw + sy * w + sx) * cin + ci]);
     colT[i] = __float2bfloat16_rn(val);
   }
 }
@@ -589,6 +589,45 @@ __global__ void k_pool(const bf16* __restrict__ y, int c_n, int n, int h, int w,
       p[static_cast<long long>(b) * c_n * h2 * w2 + f] = bv;
       pT[f * ldt + b] = bv;
     }
+  }
+}
+
+// The same 2x2 max pooling (same ties, argmax in the chan-major order of k_pool) writing the
+// pooled map channels-last, p[(b, y2, x2)][c], for the implicit-GEMM convolution that reads
+// it. A CTA owns 64 consecutive output pixels of one row: it reads each channel's two input
+// rows coalesced, and stages the results in shared memory so the channels-last writes are
+// contiguous too.
+template <int CN>
+__global__ void __launch_bounds__(256) k_pool_nhwc(const bf16* __restrict__ y, int n, int h, int w,
+                                                   bf16* __restrict__ p, uint8_t* __restrict__ am) {
+  __shared__ bf16 sp[64][CN + 2];
+  const int h2 = h / 2, w2 = w / 2;
+  const long long npix = static_cast<long long>(n) * h2 * w2;
+  const long long pix0 = static_cast<long long>(blockIdx.x) * 64;
+  for (int idx = threadIdx.x; idx < CN * 64; idx += 256) {
+    const int c = idx >> 6, pl = idx & 63;
+    const long long pix = pix0 + pl;
+    if (pix >= npix) continue;
+    const int x2 = static_cast<int>(pix % w2);
+    const long long r = pix / w2;
+    const int y2 = static_cast<int>(r % h2);
+    const int b = static_cast<int>(r / h2);
+    const bf16* src = y + ((static_cast<long long>(c) * n + b) * h + 2 * y2) * w + 2 * x2;
+    const float v0 = __bfloat162float(src[0]), v1 = __bfloat162float(src[1]);
+    const float v2 = __bfloat162float(src[w]), v3 = __bfloat162float(src[w + 1]);
+    int a = 0;
+    float best = v0;
+    if (v1 > best) { best = v1; a = 1; }
+    if (v2 > best) { best = v2; a = 2; }
+    if (v3 > best) { best = v3; a = 3; }
+    am[static_cast<long long>(c) * npix + pix] = static_cast<uint8_t>(a);
+    sp[pl][c] = __float2bfloat16_rn(best);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < CN * 64; idx += 256) {
+    const int pl = idx / CN, c = idx - (idx / CN) * CN;
+    const long long pix = pix0 + pl;
+    if (pix < npix) p[pix * CN + c] = sp[pl][c];
   }
 }
 
@@ -1054,9 +1093,16 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
       if (rc) return rc;
     }
     const long long pooled = m / 4 * c.cout;
-    k_pool<<<grid_for(pooled), 256, 0, s>>>(at<bf16>(f, f.o.yT[l]), c.cout, n, c.h, c.w,
-                                             l < 2 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3),
-                                             at<bf16>(f, f.o.p3T), f.bm, l < 2 ? 1 : 0, at<uint8_t>(f, f.o.am[l]));
+    if (l == 0) {  // 16 channels, channels-last for conv2
+      k_pool_nhwc<16><<<static_cast<unsigned>((m / 4 + 63) / 64), 256, 0, s>>>(
+          at<bf16>(f, f.o.yT[l]), n, c.h, c.w, at<bf16>(f, f.o.p[l]), at<uint8_t>(f, f.o.am[l]));
+    } else if (l == 1) {  // 32 channels, channels-last for conv3
+      k_pool_nhwc<32><<<static_cast<unsigned>((m / 4 + 63) / 64), 256, 0, s>>>(
+          at<bf16>(f, f.o.yT[l]), n, c.h, c.w, at<bf16>(f, f.o.p[l]), at<uint8_t>(f, f.o.am[l]));
+    } else {
+      k_pool<<<grid_for(pooled), 256, 0, s>>>(at<bf16>(f, f.o.yT[l]), c.cout, n, c.h, c.w, at<bf16>(f, f.o.p3),
+                                               at<bf16>(f, f.o.p3T), f.bm, 0, at<uint8_t>(f, f.o.am[l]));
+    }
     f.launches++;
   }
   // fc1 pre-activation (bias and ReLU are applied where it is read, in k_head), K split
