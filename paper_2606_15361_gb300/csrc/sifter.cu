@@ -14,8 +14,10 @@
 // (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator, and four warps read it
 // back with tcgen05.ld for the epilogue (bias, ReLU, BF16 or FP32, row-major or transposed
 // store, or FP32 atomic add for split-K). conv1 (K = 9) runs on the CUDA cores (k_conv1).
-// Activations are channel-major ([c][b][h][w]); patch rows are [m][k] with m = (b, h, w)
-// and k = (cin, ky, kx), zero-padded to a multiple of 64.
+// Activations are channel-major ([c][b][h][w]), except the pooled maps that feed conv2 and
+// conv3, which are channels-last ([b][h][w][c]) so a patch chunk is one 16-byte load; patch
+// rows are [m][k] with m = (b, h, w) and k = (cin, ky, kx) (tap-major in k_conv_tc),
+// zero-padded to a multiple of 64.
 //   forward conv:   Y^T[cout][m] = relu(patch[m][:] . W[cout][:] + b)  (k_conv_tc, implicit)
 //   weight grad:    dW[cout][k] += dY^T[cout][m] . colT[k][m]            (split-K, atomic)
 //   input grad:     dcol[m][k]   = dY[m][:] . W^T[k][:]                  (then col2im)
@@ -530,6 +532,56 @@ __global__ void __launch_bounds__(256) k_conv1(const float* __restrict__ x, int 
       for (int k = 0; k < 9; ++k) a = fmaf(ws[c * 9 + k], v[k], a);
       yT[c * mtot + m] = __float2bfloat16_rn(fmaxf(a + bs[c], 0.0f));
     }
+  }
+}
+
+// conv1 and its 2x2 max pooling fused, for a sifter without training state (no gradient
+// will need the unpooled map or the argmax): a thread computes the four conv1 outputs of one
+// pooled pixel for all 16 channels from the 4x4 input patch, with k_conv1's roundings and
+// summation order (BF16 inputs and weights, FP32 sums in tap order, bias, ReLU, BF16), takes
+// their maximum as k_pool does, and writes the pooled pixel channels-last (32 bytes).
+__global__ void __launch_bounds__(256, 3) k_conv1_pool(const float* __restrict__ x, int n, const float* __restrict__ w,
+                                                    const float* __restrict__ bias, bf16* __restrict__ p) {
+  __shared__ float ws[16 * 9], bs[16];
+  for (int i = threadIdx.x; i < 16 * 9; i += blockDim.x) ws[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+  if (threadIdx.x < 16) bs[threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  constexpr int hw = kH * kW, h2 = kH / 2, w2 = kW / 2;
+  const long long npix = static_cast<long long>(n) * h2 * w2;
+  for (long long q = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; q < npix;
+       q += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long b = q / (h2 * w2);
+    const int r = static_cast<int>(q - b * (h2 * w2));
+    const int y2 = r / w2, x2 = r - y2 * w2;
+    float v[4][4];
+#pragma unroll
+    for (int dy = 0; dy < 4; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 4; ++dx) {
+        const int sy = 2 * y2 - 1 + dy, sx = 2 * x2 - 1 + dx;
+        v[dy][dx] = (sy >= 0 && sy < kH && sx >= 0 && sx < kW)
+                        ? __bfloat162float(__float2bfloat16_rn(x[b * hw + sy * kW + sx]))
+                        : 0.0f;
+      }
+    uint32_t packed[8];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float best = 0.0f;
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int oy = o >> 1, ox = o & 1;
+        float a = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a = fmaf(ws[c * 9 + k], v[oy + k / 3][ox + k % 3], a);
+        const float y = __bfloat162float(__float2bfloat16_rn(fmaxf(a + bs[c], 0.0f)));
+        best = (o == 0 || y > best) ? y : best;
+      }
+      const uint32_t bits = __bfloat16_as_ushort(__float2bfloat16_rn(best));
+      packed[c >> 1] = (c & 1) ? (packed[c >> 1] | (bits << 16)) : bits;
+    }
+    uint4* dst = reinterpret_cast<uint4*>(p + q * 16);
+    dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
   }
 }
 
@@ -1083,6 +1135,12 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
   for (int l = 0; l < 3; ++l) {
     const ConvL& c = kConv[l];
     const long long m = 1LL * n * c.h * c.w;
+    if (l == 0 && !f.training) {
+      // inference: conv1 and pool1 in one pass, straight to the channels-last conv2 input
+      k_conv1_pool<<<grid_for(m / 4), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.p[0]));
+      f.launches++;
+      continue;
+    }
     if (l == 0) {
       k_conv1<<<grid_for(m), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]));
       f.launches++;

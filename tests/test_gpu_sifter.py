@@ -110,6 +110,26 @@ def test_logits_and_gradients_match_oracle():
         assert cos >= 0.9999 and rel <= 1e-2, (t, s, cos, rel)
 
 
+def test_inference_sifter_matches_training_path():
+    """A sifter built without training state runs conv1 and its pooling as one fused kernel
+    (no unpooled map, no argmax). With the same parameters its logits equal those of a
+    training-capable sifter (separate conv1 and pooling kernels): both take the same roundings
+    in the same order, and only the split-K FP32 atomics of fc1 may reorder the last bits."""
+    rng = np.random.default_rng(21)
+    theta = osf.init_params(9).astype(np.float32)
+    x = rng.normal(size=(70, 64, 256)).astype(np.float32)  # not a multiple of 64
+    x[:20, 20:40, 60:200] += 2.5
+    xd = torch.from_numpy(x).cuda()
+    za = g.Sifter(max_batch=128, training=True, seed=1)
+    zb = g.Sifter(max_batch=128, training=False, seed=1)
+    za.set_params(theta)
+    zb.set_params(theta)
+    a = za.forward(xd).cpu().numpy()
+    b = zb.forward(xd).cpu().numpy()
+    assert np.abs(a).max() > 0.1
+    assert np.allclose(a, b, rtol=1e-5, atol=1e-5), float(np.abs(a - b).max())
+
+
 def test_training_learns_a_separable_task():
     """Bright sloped tracks (burst-like) against pure noise: Adam on the GPU drives the loss
     down and classifies held-out snippets."""
