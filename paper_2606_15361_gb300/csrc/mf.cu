@@ -46,6 +46,12 @@ struct MfArgs {
 };
 
 constexpr int kMfThreads = 256;
+constexpr uint32_t kAllWidths = (1u << kNumWidthSlots) - 1u;
+
+template <bool A>
+struct WidthSet {  // tag: every width slot of the row is in use (A) or not known to be
+  static constexpr bool kAll = A;
+};
 
 __device__ __forceinline__ double snr_of(long long s, double mu_w, double den) {
   return __ddiv_rn(__dsub_rn(static_cast<double>(s), mu_w), den);
@@ -247,46 +253,53 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
   //    A cell passes iff max over widths of S_W - tau_W >= 0; S_W < 2^31 and tau_W < 2^31, so
   //    the wrapped difference P[t+W] - P[t] - tau_W read as int32 is exact. Eight lanes'
   //    nibbles make one mask word.
+  // hit nibble of start times 4m..4m+3 (bit e: start time 4m + e passes)
+  auto group_hits = [&](int m, auto all) -> uint32_t {
+    constexpr bool ALL = decltype(all)::kAll;
+    const uint4 p = P4[m];
+    const uint4 q = P4[m + 1];
+    int h0 = INT_MIN, h1 = INT_MIN, h2 = INT_MIN, h3 = INT_MIN;
+    auto upd = [](int& h, uint32_t end, uint32_t start, int tj) {
+      h = max(h, static_cast<int>(end - start - static_cast<uint32_t>(tj)));
+    };
+    if (ALL || (wm & 1u)) {
+      upd(h0, p.y, p.x, tw[0]);
+      upd(h1, p.z, p.y, tw[0]);
+      upd(h2, p.w, p.z, tw[0]);
+      upd(h3, q.x, p.w, tw[0]);
+    }
+    if (ALL || (wm & 2u)) {
+      upd(h0, p.z, p.x, tw[1]);
+      upd(h1, p.w, p.y, tw[1]);
+      upd(h2, q.x, p.z, tw[1]);
+      upd(h3, q.y, p.w, tw[1]);
+    }
+    if (ALL || (wm & 4u)) {
+      upd(h0, q.x, p.x, tw[2]);
+      upd(h1, q.y, p.y, tw[2]);
+      upd(h2, q.z, p.z, tw[2]);
+      upd(h3, q.w, p.w, tw[2]);
+    }
+#pragma unroll
+    for (int j = 3; j < kNumWidthSlots; ++j) {
+      if (ALL || ((wm >> j) & 1u)) {
+        const uint4 e = P4[m + (1 << (j - 2))];
+        upd(h0, e.x, p.x, tw[j]);
+        upd(h1, e.y, p.y, tw[j]);
+        upd(h2, e.z, p.z, tw[j]);
+        upd(h3, e.w, p.w, tw[j]);
+      }
+    }
+    return (h0 >= 0 ? 1u : 0u) | (h1 >= 0 ? 2u : 0u) | (h2 >= 0 ? 4u : 0u) | (h3 >= 0 ? 8u : 0u);
+  };
   const int ngt = (nb + 3) >> 2;
   for (int base = wid * 32; base < ngt; base += NWARP * 32) {
     const int m = base + lane;
     uint32_t nib = 0;
     if (m < ngt) {
-      const uint4 p = P4[m];
-      const uint4 q = P4[m + 1];
-      int h0 = INT_MIN, h1 = INT_MIN, h2 = INT_MIN, h3 = INT_MIN;
-      auto upd = [](int& h, uint32_t end, uint32_t start, int tj) {
-        h = max(h, static_cast<int>(end - start - static_cast<uint32_t>(tj)));
-      };
-      if (wm & 1u) {
-        upd(h0, p.y, p.x, tw[0]);
-        upd(h1, p.z, p.y, tw[0]);
-        upd(h2, p.w, p.z, tw[0]);
-        upd(h3, q.x, p.w, tw[0]);
-      }
-      if (wm & 2u) {
-        upd(h0, p.z, p.x, tw[1]);
-        upd(h1, p.w, p.y, tw[1]);
-        upd(h2, q.x, p.z, tw[1]);
-        upd(h3, q.y, p.w, tw[1]);
-      }
-      if (wm & 4u) {
-        upd(h0, q.x, p.x, tw[2]);
-        upd(h1, q.y, p.y, tw[2]);
-        upd(h2, q.z, p.z, tw[2]);
-        upd(h3, q.w, p.w, tw[2]);
-      }
-#pragma unroll
-      for (int j = 3; j < kNumWidthSlots; ++j) {
-        if ((wm >> j) & 1u) {
-          const uint4 e = P4[m + (1 << (j - 2))];
-          upd(h0, e.x, p.x, tw[j]);
-          upd(h1, e.y, p.y, tw[j]);
-          upd(h2, e.z, p.z, tw[j]);
-          upd(h3, e.w, p.w, tw[j]);
-        }
-      }
-      nib = (h0 >= 0 ? 1u : 0u) | (h1 >= 0 ? 2u : 0u) | (h2 >= 0 ? 4u : 0u) | (h3 >= 0 ? 8u : 0u);
+      // rows with every width (most rows above a small DM) take a copy of the loop with no
+      // width tests, so all window loads of the group can be in flight together
+      nib = (wm == kAllWidths) ? group_hits(m, WidthSet<true>{}) : group_hits(m, WidthSet<false>{});
       const int rem = nb - 4 * m;  // start times of this group inside the block
       if (rem < 4) nib &= (1u << rem) - 1u;
     }
