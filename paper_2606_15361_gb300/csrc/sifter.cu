@@ -609,6 +609,39 @@ __global__ void k_im2colT(const T* __restrict__ x, int n, int h, int w, int kc, 
   }
 }
 
+// colT[k][m] (k = ci*9 + tap, as k_im2colT) from a channels-last BF16 map x[n][h][w][CIN]:
+// a thread takes one (tap, m), reads the CIN channels of the tap's source pixel with 16-byte
+// loads and writes them to CIN rows of colT, so both the reads and the writes of neighbouring
+// threads (neighbouring m) are contiguous.
+template <int CIN>
+__global__ void __launch_bounds__(256) k_im2colT_nhwc(const bf16* __restrict__ x, int n, int h, int w,
+                                                      bf16* __restrict__ colT) {
+  const long long hw = static_cast<long long>(h) * w;
+  const long long mtot = static_cast<long long>(n) * hw;
+  const long long total = mtot * 9;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int tap = static_cast<int>(i / mtot);
+    const long long m = i - tap * mtot;
+    const int b = static_cast<int>(m / hw);
+    const int yx = static_cast<int>(m - b * hw);
+    const int yy = yx / w, xx = yx - yy * w;
+    const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+    uint4 v[CIN / 8];
+    if (sy >= 0 && sy < h && sx >= 0 && sx < w) {
+      const uint4* src = reinterpret_cast<const uint4*>(x + (b * hw + sy * w + sx) * CIN);
+#pragma unroll
+      for (int q = 0; q < CIN / 8; ++q) v[q] = __ldg(src + q);
+    } else {
+#pragma unroll
+      for (int q = 0; q < CIN / 8; ++q) v[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const bf16* vb = reinterpret_cast<const bf16*>(v);
+#pragma unroll
+    for (int ci = 0; ci < CIN; ++ci) colT[static_cast<long long>(ci * 9 + tap) * mtot + m] = vb[ci];
+  }
+}
+
 // 2x2 max pooling of y[c][b][h][w] (BF16, post-ReLU); ties go to the first of the four in
 // row-major order. Writes p[c][b][h/2][w/2] (chan_major) or p[b][c][h/2][w/2] and its
 // transpose pT[(c, y, x)][b] (row pitch ldt), plus the argmax 0..3.
@@ -685,41 +718,61 @@ __global__ void __launch_bounds__(256) k_pool_nhwc(const bf16* __restrict__ y, i
 
 // Gradient through the pooling and the ReLU: the argmax position of each pooled cell gets
 // dP if its activation is positive. Writes dyT[c][m] (all positions) and, when dy is set,
-// dy[m][ldy] (row-major; columns c < c_n).
-__global__ void k_unpool(const float* __restrict__ dp, int dp_chan_major, const uint8_t* __restrict__ am,
-                         const bf16* __restrict__ y, int c_n, int n, int h, int w, bf16* __restrict__ dyT,
-                         bf16* __restrict__ dy, int ldy) {
+// dy[m][ldy] (row-major; columns c < CN). A CTA owns 64 consecutive pooled pixels for all
+// CN channels: pass 1 runs along the pixels of one channel (coalesced dP, argmax, y and dyT),
+// and stages the four gradients of each pixel in shared memory; pass 2 writes the dy rows
+// of the tile channel-fastest (coalesced).
+template <int CN>
+__global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, int dp_chan_major,
+                                                const uint8_t* __restrict__ am, const bf16* __restrict__ y, int n,
+                                                int h, int w, bf16* __restrict__ dyT, bf16* __restrict__ dy,
+                                                int ldy) {
+  __shared__ bf16 sdy[64 * 4][CN + 2];
   const int h2 = h / 2, w2 = w / 2;
-  const long long total = static_cast<long long>(c_n) * n * h2 * w2;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    // c fastest, so the row-major dy writes of a warp are contiguous
-    const int c = static_cast<int>(i % c_n);
-    long long r = i / c_n;
-    const int x2 = static_cast<int>(r % w2);
-    r /= w2;
+  const long long npix = static_cast<long long>(n) * h2 * w2;
+  const long long mtot = static_cast<long long>(n) * h * w;
+  const long long pix0 = static_cast<long long>(blockIdx.x) * 64;
+  for (int idx = threadIdx.x; idx < CN * 64; idx += 256) {
+    const int c = idx >> 6, pl = idx & 63;
+    const long long pix = pix0 + pl;
+    if (pix >= npix) continue;
+    const int x2 = static_cast<int>(pix % w2);
+    const long long r = pix / w2;
     const int y2 = static_cast<int>(r % h2);
     const int b = static_cast<int>(r / h2);
-    const long long pc = ((static_cast<long long>(c) * n + b) * h2 + y2) * w2 + x2;  // channel-major pooled index
-    const float g = dp_chan_major ? dp[pc] : dp[static_cast<long long>(b) * c_n * h2 * w2 +
+    const long long pc = static_cast<long long>(c) * npix + pix;  // channel-major pooled index
+    const float g = dp_chan_major ? dp[pc] : dp[static_cast<long long>(b) * CN * h2 * w2 +
                                                  (static_cast<long long>(c) * h2 + y2) * w2 + x2];
     const int a = am[pc];
     const long long m00 = (static_cast<long long>(b) * h + 2 * y2) * w + 2 * x2;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const long long m = m00 + (q >> 1) * w + (q & 1);
-      const long long yi = static_cast<long long>(c) * n * h * w + m;
+      const long long yi = static_cast<long long>(c) * mtot + m;
       const float v = (q == a && __bfloat162float(y[yi]) > 0.0f) ? g : 0.0f;
       const bf16 bv = __float2bfloat16_rn(v);
       dyT[yi] = bv;
-      if (dy) dy[m * ldy + c] = bv;
+      sdy[pl * 4 + q][c] = bv;
     }
+  }
+  if (!dy) return;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 64 * 4 * CN; idx += 256) {
+    const int c = idx % CN, pq = idx / CN;
+    const int pl = pq >> 2, q = pq & 3;
+    const long long pix = pix0 + pl;
+    if (pix >= npix) continue;
+    const int x2 = static_cast<int>(pix % w2);
+    const long long r = pix / w2;
+    const int y2 = static_cast<int>(r % h2);
+    const int b = static_cast<int>(r / h2);
+    const long long m = (static_cast<long long>(b) * h + 2 * y2 + (q >> 1)) * w + 2 * x2 + (q & 1);
+    dy[m * ldy + c] = sdy[pq][c];
   }
 }
 
-// dx[ci][b][y][x] = sum over taps of dcol[m(b, y - ky + 1, x - kx + 1)][ci*9 + ky*3 + kx]
-__global__ void k_col2im(const float* __restrict__ dcol, int ldc, int cin, int n, int h, int w,
-                         float* __restrict__ dx) {
+// neighbouring m)
+__global__ void k_col2im(const float* __restrict__ dcolT, int cin, int n, int h, int w, float* __restrict__ dx) {
   const long long hw = static_cast<long long>(h) * w;
   const long long total = static_cast<long long>(cin) * n * hw;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
@@ -738,7 +791,7 @@ __global__ void k_col2im(const float* __restrict__ dcol, int ldc, int cin, int n
         const int oy = yy - ky + 1, ox = xx - kx + 1;
         if (oy < 0 || oy >= h || ox < 0 || ox >= w) continue;
         const long long m = b * hw + oy * w + ox;
-        s += dcol[m * ldc + ci * 9 + ky * 3 + kx];
+        s += dcolT[static_cast<long long>(ci * 9 + ky * 3 + kx) * (n * hw) + m];
       }
     }
     dx[i] = s;
@@ -1200,13 +1253,27 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     const float* dp = (l == 2) ? at<float>(f, f.o.dp3) : at<float>(f, f.o.dp[l]);
     bf16* dyT = at<bf16>(f, f.o.dyT[l]);
     bf16* dy = l > 0 ? at<bf16>(f, f.o.dy[l]) : nullptr;
-    k_unpool<<<grid_for(m / 4 * c.cout), 256, 0, s>>>(dp, l < 2 ? 1 : 0, at<uint8_t>(f, f.o.am[l]),
-                                                       at<bf16>(f, f.o.yT[l]), c.cout, n, c.h, c.w, dyT, dy, 64);
+    {
+      const unsigned ub = static_cast<unsigned>((m / 4 + 63) / 64);
+      const uint8_t* am = at<uint8_t>(f, f.o.am[l]);
+      const bf16* yl = at<bf16>(f, f.o.yT[l]);
+      if (c.cout == 16) {
+        k_unpool<16><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, 64);
+      } else if (c.cout == 32) {
+        k_unpool<32><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, 64);
+      } else {
+        k_unpool<64><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, 64);
+      }
+    }
     f.launches++;
     // weight and bias gradients
     bf16* colT = at<bf16>(f, f.o.colT[l]);
     if (l == 0) {
       k_im2colT<float><<<grid_for(m * c.kc), 256, 0, s>>>(x, n, c.h, c.w, c.kc, colT);
+    } else if (c.cin == 16) {
+      k_im2colT_nhwc<16><<<grid_for(m * 9), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
+    } else if (c.cin == 32) {
+      k_im2colT_nhwc<32><<<grid_for(m * 9), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
     } else {
       k_im2colT<bf16><<<grid_for(m * c.kc), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, colT);
     }
@@ -1224,10 +1291,11 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     f.launches++;
     if (l == 0) break;
     // input gradient through the convolution, then back to the previous pooled map
-    Epi ex{nullptr, 0, at<float>(f, f.o.dcol[l]), 0, 0, 0, c.kc};
+    // stored transposed, dcolT[k][m], so the col2im gather reads along m
+    Epi ex{nullptr, 0, at<float>(f, f.o.dcol[l]), 0, 1, 0, m};
     rc = gemm(dy, 64, at<bf16>(f, f.o.wT[l]), 64, static_cast<int>(m), c.kc, 64, ex, 1, err, s, &f.launches);
     if (rc) return rc;
-    k_col2im<<<grid_for(m * c.cin), 256, 0, s>>>(at<float>(f, f.o.dcol[l]), c.kc, c.cin, n, c.h, c.w,
+    k_col2im<<<grid_for(m * c.cin), 256, 0, s>>>(at<float>(f, f.o.dcol[l]), c.cin, n, c.h, c.w,
                                                   at<float>(f, f.o.dp[l - 1]));
     f.launches++;
   }
