@@ -20,7 +20,7 @@
 // zero-padded to a multiple of 64.
 //   forward conv:   Y^T[cout][m] = relu(patch[m][:] . W[cout][:] + b)  (k_conv_tc, implicit)
 //   weight grad:    dW[cout][k] += dY^T[cout][m] . colT[k][m]            (split-K, atomic)
-//   input grad:     dcol[m][k]   = dY[m][:] . W^T[k][:]                  (then col2im)
+//   input grad:     dX^T[cin][m] = dY (x) flipped W                        (k_conv_tc, DX mode)
 // Every mbarrier wait is bounded (about 2 s of clock); a wait that gives up sets a device
 // error word that the host turns into SND_ERR_TIMEOUT, and the kernel still frees its TMEM.
 
@@ -321,14 +321,18 @@ __device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes
 }
 
 struct ConvArgs {
-  const bf16* x;    // input activations, channels-last [n][h][w][cin]
+  const bf16* x;    // input activations, channels-last [n][h][w][ldx] (channels 0..cin-1 used)
   int n, h, w, cin, kc, ktiles;
   const float* bias;
-  bf16* yT;         // output [cout][n*h*w]
+  bf16* yT;         // output [cout][n*h*w] (forward: bias, ReLU, BF16)
   int cout;
+  int ldx;          // elements per input pixel
+  float* yTf;       // DX: output [cout][n*h*w] in FP32, no bias or ReLU
 };
 
-template <int BN, int CIN>
+// DX: the input gradient of a convolution written as the forward convolution of the output
+// gradient (row-major dY, ldx = 64) with the flipped, channel-transposed kernel (k_cast_w_flip)
+template <int BN, int CIN, bool DX = false>
 __global__ void __launch_bounds__(288, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mb, ConvArgs a, uint32_t* err) {
   constexpr int KT = (9 * CIN + kBK - 1) / kBK;  // K steps
@@ -382,14 +386,14 @@ __global__ void __launch_bounds__(288, 1)
       const int b = mv ? static_cast<int>(m / hw) : 0;
       const int yx = mv ? static_cast<int>(m - b * hw) : 0;
       const int yy = yx / a.w, xx = yx - yy * a.w;
-      const bf16* xb = a.x + static_cast<long long>(b) * hw * CIN;  // channels-last input
+      const bf16* xb = a.x + static_cast<long long>(b) * hw * a.ldx;  // channels-last input
       const bf16* tp[9];
       bool tv[9];
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
         tv[tap] = mv && sy >= 0 && sy < a.h && sx >= 0 && sx < a.w;
-        tp[tap] = xb + (tv[tap] ? (sy * a.w + sx) * CIN : 0);
+        tp[tap] = xb + (tv[tap] ? (sy * a.w + sx) * a.ldx : 0);
       }
       bool quit = false;
 #pragma unroll
@@ -483,7 +487,11 @@ __global__ void __launch_bounds__(288, 1)
         for (int q = 0; q < 8; ++q) {
           const int n = c + q;
           if (n >= a.cout) continue;
-          a.yT[static_cast<long long>(n) * M + row] = __float2bfloat16_rn(fmaxf(v[q] + a.bias[n], 0.0f));
+          if constexpr (DX) {
+            a.yTf[static_cast<long long>(n) * M + row] = v[q];
+          } else {
+            a.yT[static_cast<long long>(n) * M + row] = __float2bfloat16_rn(fmaxf(v[q] + a.bias[n], 0.0f));
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -771,33 +779,6 @@ __global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, in
   }
 }
 
-// neighbouring m)
-__global__ void k_col2im(const float* __restrict__ dcolT, int cin, int n, int h, int w, float* __restrict__ dx) {
-  const long long hw = static_cast<long long>(h) * w;
-  const long long total = static_cast<long long>(cin) * n * hw;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int xx = static_cast<int>(i % w);
-    long long r = i / w;
-    const int yy = static_cast<int>(r % h);
-    r /= h;
-    const int b = static_cast<int>(r % n);
-    const int ci = static_cast<int>(r / n);
-    float s = 0.0f;
-#pragma unroll
-    for (int ky = 0; ky < 3; ++ky) {
-#pragma unroll
-      for (int kx = 0; kx < 3; ++kx) {
-        const int oy = yy - ky + 1, ox = xx - kx + 1;
-        if (oy < 0 || oy >= h || ox < 0 || ox >= w) continue;
-        const long long m = b * hw + oy * w + ox;
-        s += dcolT[static_cast<long long>(ci * 9 + ky * 3 + kx) * (n * hw) + m];
-      }
-    }
-    dx[i] = s;
-  }
-}
-
 // fc1's bias and ReLU, fc2, the loss and its gradient, one warp per sample. Forward only
 // when y is null.
 __global__ void k_head(const float* __restrict__ hf, const float* __restrict__ params, int n,
@@ -879,6 +860,22 @@ __global__ void k_cast_w(const float* __restrict__ src, int rows, int cols, bf16
 }
 
 // dst[co][tap*cin + ci] = bf16(src[co][ci*9 + tap]) (the tap-major K of k_conv_tc), zero to kp
+// dst[ci][tap*cout + co] = bf16(src[co][ci*9 + (8 - tap)]), zero to kp: the kernel of the input
+// gradient as a forward convolution of dY (rotated by 180 degrees, in and out channels swapped)
+__global__ void k_cast_w_flip(const float* __restrict__ src, int cout, int cin, bf16* __restrict__ dst, int kp) {
+  const long long total = static_cast<long long>(cin) * kp;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int ci = static_cast<int>(i / kp), k = static_cast<int>(i - static_cast<long long>(ci) * kp);
+    float v = 0.0f;
+    if (k < 9 * cout) {
+      const int tap = k / cout, co = k - tap * cout;
+      v = src[static_cast<long long>(co) * 9 * cin + ci * 9 + (8 - tap)];
+    }
+    dst[i] = __float2bfloat16_rn(v);
+  }
+}
+
 __global__ void k_cast_w_tap(const float* __restrict__ src, int cout, int cin, bf16* __restrict__ dst, int kp) {
   const long long total = static_cast<long long>(cout) * kp;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
@@ -1044,7 +1041,7 @@ int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const b
   if (cout > 64) return SND_ERR_UNSUPPORTED;
   CUtensorMap mb;
   if (!make_map(&mb, wb, kp, cout, kp, BN)) return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout};
+  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout, cin, nullptr};
   const long long M = 1LL * n * h * w;
   const long long mt = (M + kBM - 1) / kBM;
   const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
@@ -1057,6 +1054,36 @@ int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const b
   } else if (cin == 32 && BN == 64) {
     e = cudaFuncSetAttribute(k_conv_tc<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) k_conv_tc<64, 32><<<grid, 288, smem, s>>>(mb, a, err);
+  } else {
+    return SND_ERR_UNSUPPORTED;
+  }
+  if (launches) *launches += 1;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
+// Input gradient of a 3x3 convolution on the tensor cores (k_conv_tc in DX mode):
+// dX^T[cin][m] = sum over taps and output channels of dY[m + tap offset][co] * W'[ci][tap*cdy + co],
+// with dY row-major [m][64] (cdy channels used) and W' = k_cast_w_flip of the layer's kernel.
+int conv_tc_dx(const bf16* dy, int n, int h, int w, int cdy, const bf16* wflip, int kp, int cin, float* dxT,
+               uint32_t* err, cudaStream_t s, int64_t* launches) {
+  constexpr int BN = 32;
+  if (cin > BN) return SND_ERR_UNSUPPORTED;
+  CUtensorMap mb;
+  if (!make_map(&mb, wflip, kp, cin, kp, BN)) return SND_ERR_UNSUPPORTED;
+  ConvArgs a{dy, n, h, w, cdy, 9 * cdy, kp / kBK, nullptr, nullptr, cin, 64, dxT};
+  const long long M = 1LL * n * h * w;
+  const long long mt = (M + kBM - 1) / kBM;
+  const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
+  const int per_sm = std::max(1, (227 * 1024) / smem);
+  const unsigned grid = static_cast<unsigned>(std::min<long long>(mt, 152LL * per_sm));
+  cudaError_t e;
+  if (cdy == 32) {
+    e = cudaFuncSetAttribute(k_conv_tc<32, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) k_conv_tc<32, 32, true><<<grid, 288, smem, s>>>(mb, a, err);
+  } else if (cdy == 64) {
+    e = cudaFuncSetAttribute(k_conv_tc<32, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) k_conv_tc<32, 64, true><<<grid, 288, smem, s>>>(mb, a, err);
   } else {
     return SND_ERR_UNSUPPORTED;
   }
@@ -1083,7 +1110,7 @@ struct Sifter {
   cudaStream_t last = nullptr;
   struct {
     size_t params, grads, m1, m2, err, loss, wb[3], wT[3], wf1b, wf1T, yT[3], p[3], am[3], p3, p3T, hf,
-        logits, dh, dhT, dp3, dy[3], dyT[3], colT[3], dcol[3], dp[3];
+        logits, dh, dhT, dp3, dy[3], dyT[3], colT[3], dp[3];
   } o{};
 };
 
@@ -1111,7 +1138,7 @@ void layout(Sifter& f) {
     const ConvL& c = kConv[l];
     const long long m = B * c.h * c.w;
     f.o.wb[l] = take(2ull * c.cout * c.kp);
-    f.o.wT[l] = take(2ull * c.kc * 64);
+    f.o.wT[l] = take(2ull * c.cin * ((9 * c.cout + kBK - 1) / kBK * kBK));
     f.o.yT[l] = take(2ull * c.cout * m);
     f.o.p[l] = take(2ull * c.cout * m / 4);
     f.o.am[l] = take(1ull * c.cout * m / 4);
@@ -1119,7 +1146,6 @@ void layout(Sifter& f) {
       f.o.dy[l] = take(l > 0 ? 2ull * m * 64 : 0);
       f.o.dyT[l] = take(2ull * c.cout * m);
       f.o.colT[l] = take(2ull * c.kc * m);
-      f.o.dcol[l] = take(l > 0 ? 4ull * m * c.kc : 0);
       f.o.dp[l] = take(l < 2 ? 4ull * c.cout * m / 4 : 0);
     }
   }
@@ -1164,9 +1190,10 @@ cudaError_t prep_weights(Sifter& f, cudaStream_t s) {
                                                                c.kp);
     }
     f.launches++;
-    if (f.training && l > 0) {
-      k_cast_w<<<grid_for(1LL * c.kc * 64), 256, 0, s>>>(P + kOffW[l], c.cout, c.kc, at<bf16>(f, f.o.wT[l]), 64, 1,
-                                                       c.kc);
+    if (f.training && l > 0) {  // the input gradient's flipped kernel, [cin][kpd]
+      const int kpd = (9 * c.cout + kBK - 1) / kBK * kBK;
+      k_cast_w_flip<<<grid_for(1LL * c.cin * kpd), 256, 0, s>>>(P + kOffW[l], c.cout, c.cin, at<bf16>(f, f.o.wT[l]),
+                                                               kpd);
       f.launches++;
     }
   }
@@ -1290,14 +1317,11 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     }
     f.launches++;
     if (l == 0) break;
-    // input gradient through the convolution, then back to the previous pooled map
-    // stored transposed, dcolT[k][m], so the col2im gather reads along m
-    Epi ex{nullptr, 0, at<float>(f, f.o.dcol[l]), 0, 1, 0, m};
-    rc = gemm(dy, 64, at<bf16>(f, f.o.wT[l]), 64, static_cast<int>(m), c.kc, 64, ex, 1, err, s, &f.launches);
+    // input gradient, straight into the previous pooled map's gradient dP[cin][m]: the
+    // forward convolution of dY with the flipped kernel, an implicit GEMM like conv2/conv3
+    rc = conv_tc_dx(dy, n, c.h, c.w, c.cout, at<bf16>(f, f.o.wT[l]), (9 * c.cout + kBK - 1) / kBK * kBK, c.cin,
+                    at<float>(f, f.o.dp[l - 1]), err, s, &f.launches);
     if (rc) return rc;
-    k_col2im<<<grid_for(m * c.cin), 256, 0, s>>>(at<float>(f, f.o.dcol[l]), c.cin, n, c.h, c.w,
-                                                  at<float>(f, f.o.dp[l - 1]));
-    f.launches++;
   }
   return cudaGetLastError() == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
