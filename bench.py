@@ -11,8 +11,8 @@ DM row. Metric: DM-trial samples per second (DM rows x emitted plane samples / t
 Multi-GPU: beams are independent, so N ranks run N beam replicas with no collective
 (weak scaling); value = all ranks' DM-samples / the slowest rank's time.
 
---impl reference runs the FP64 CPU oracle (the only other implementation of this method
-here) on a bounded sample of the same workload on the host cores.
+--impl reference runs the C++/OpenMP CPU oracle (the only other implementation of this method
+here) on bounded samples of the same workload on all host cores.
 """
 from __future__ import annotations
 
@@ -155,34 +155,82 @@ def whole_job_rate(units_per_rank_step: float, steps: int, world: int, ms: float
 # CPU oracle (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------------------
 
-def oracle_sample(chunks, rows: int):
-    """Time the FP64 oracle on a bounded sample of the workload: the steady-state chunk
-    (index 2) of every mode, encoder over all channels, SND tree + matched filter on the
-    first `rows` DM rows. Returns (DM-samples, seconds, description)."""
-    from oracle import delays as od
-    from oracle import encoder as oe
-    from oracle import mf as om
+def _cxx_streams(chunks, fill: int = 2):
+    """One C++-oracle stream per mode, filled with the first `fill` chunks (from then on
+    every chunk emits W.chunk plane samples per DM row)."""
+    from oracle import cxx
     from oracle import stream as ost
-    from oracle import tree as ot
-    freqs, dms = W.freqs(), W.dms()
-    tab = od.delay_table(freqs, synth.NC_DT, dms)
-    D = int(tab.max())
-    widths = [om.row_widths(freqs, synth.NC_DT, d, 0.1) for d in dms[:rows]]
+    out = {}
+    for name, m in MODES:
+        s = cxx.Stream(W.freqs(), synth.NC_DT, W.dms(), ost.defaults(m, branching=BRANCHING))
+        for i in range(fill):
+            s.push(chunks[i], want_plane=False)
+        out[name] = s
+    return out
+
+
+def oracle_sample(chunks):
+    """The C++/OpenMP oracle (oracle/cpp, as it stands) timed on the host cores on bounded
+    samples of the workload. Returns the cpu_baseline object:
+    * value: the whole path (encoder, SND tree per DM with no sharing, matched filter,
+      closing + labelling) on one steady-state chunk of the bench beam in each of the three
+      modes, all cores, in DM-samples/s;
+    * brute_force: direct dedispersion of one chunk (all 2048 rows), all cores;
+    * single_thread: the same whole-path chunk in float mode on one core, over a bounded
+      sample of rows (the tree and matched filter of 128 rows; the encoder of all channels);
+    * c1_full: the 64-channel / 128-DM beam (one 16384-sample chunk, binary, B = 2) in full,
+      all cores and one core."""
+    from oracle import cxx
+    from oracle import stream as ost
+    ncpu = cxx.max_threads()
+    streams = _cxx_streams(chunks)
     t0 = time.perf_counter()
     work = 0
-    for name, m in MODES:
-        cfg = ost.defaults(m, branching=BRANCHING)
-        x = np.concatenate([oe.encode_chunk(chunks[i], cfg.enc_theta)[0] for i in range(3)], axis=1)
-        e_prev = 2 * W.chunk - D
-        y = ot.snd_rows(x, 0, tab, range(rows), e_prev, W.chunk, m, cfg.cluster, cfg.branching,
-                        cfg.k_leaf, cfg.k_internal, cfg.cap)
-        floor = cfg.sigma_min if m == 0 else None
+    for name, _ in MODES:
+        r = streams[name].push(chunks[2], want_plane=False)
+        work += W.ndm * (r["e_new"] - r["e_prev"])
+    secs = time.perf_counter() - t0
+    out = {"value": work / secs, "unit": "DM-samples/s", "cores": ncpu, "kind": "oracle",
+           "sample": "C++/OpenMP oracle, whole path (encoder, SND tree per DM without sharing, matched filter, "
+                     "closing + labelling) on one steady-state 16384-sample chunk of the bench beam in each of "
+                     "the three modes (B = 8), all host cores"}
+    x = np.concatenate([cxx.encode_chunk(chunks[i], 1.5)[0] for i in range(3)], axis=1)
+    tab = cxx.delay_table(W.freqs(), synth.NC_DT, W.dms())
+    D = int(tab.max())
+    t0 = time.perf_counter()
+    cxx.brute_rows(x, 0, tab, range(W.ndm), 2 * W.chunk - D, W.chunk)
+    secs = time.perf_counter() - t0
+    out["brute_force"] = {"value": W.ndm * W.chunk / secs, "unit": "DM-samples/s", "cores": ncpu,
+                          "sample": "direct dedispersion y_d(t) = sum_c x_c(t + delta_c(d)) of one chunk, 2048 rows"}
+    rows = 128
+    cfg = ost.defaults(2, branching=BRANCHING)
+    widths = [cxx.row_widths(W.freqs(), synth.NC_DT, d, cfg.mf_alpha) for d in W.dms()[:rows]]
+    cxx.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        xe = np.concatenate([cxx.encode_chunk(chunks[i], cfg.enc_theta)[0] for i in range(3)], axis=1)
+        y = cxx.snd_rows(xe, 0, tab, range(rows), 2 * W.chunk - D, W.chunk, 2, cfg.cluster, cfg.branching)
         for r in range(rows):
-            om.row_mf(y[r], W.chunk - 1023, widths[r], cfg.det_theta, floor)
-        work += rows * W.chunk
-    dt = time.perf_counter() - t0
-    return work, dt, (f"FP64 numpy oracle, 1 chunk x 3 modes: encoder on all 1024 channels, "
-                      f"tree + matched filter on {rows} of 2048 DM rows")
+            cxx.row_mf(y[r], W.chunk - 1023, widths[r], cfg.det_theta)
+        secs = time.perf_counter() - t0
+        out["single_thread"] = {"value": rows * W.chunk / secs, "unit": "DM-samples/s", "cores": 1,
+                                "sample": "float mode, one chunk: encoder (3 chunks, all channels), tree + matched "
+                                          f"filter of {rows} of 2048 rows"}
+        c1 = {}
+        w = synth.NC64
+        d64 = w.chunk_data(0)
+        for label, th in (("one_core", 1), ("all_cores", ncpu)):
+            cxx.set_threads(th)
+            t0 = time.perf_counter()
+            s = cxx.Stream(w.freqs(), synth.NC_DT, w.dms(), ost.defaults(0, branching=2))
+            r = s.push(d64, want_plane=False)
+            secs = time.perf_counter() - t0
+            c1[label] = w.ndm * (r["e_new"] - r["e_prev"]) / secs
+        out["c1_full"] = {"value": c1["all_cores"], "single_thread_value": c1["one_core"], "unit": "DM-samples/s",
+                          "cores": ncpu, "sample": "64 ch, 128 DMs 0-100, one 16384-sample chunk, binary, B = 2"}
+    finally:
+        cxx.set_threads(ncpu)
+    return out
 
 
 def oracle_rows_sample(chunks):
@@ -222,27 +270,41 @@ def oracle_rows_sample(chunks):
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands (C++/OpenMP, all host cores) on the bench's workload: one
+    step = the next steady-state 16384-sample chunk of one mode's stream, the modes in turn
+    (binary, graded, float), so a step is a bounded sample of the GPU arm's step."""
     out = {"impl": "reference", "metric": "DM-trial samples/s", "unit": "DM-samples/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA_NOTE}
+           "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": DATA_NOTE}
     if rank != 0:
         return None
-    chunks = [W.chunk_data(i) for i in range(3)]
-    for _ in range(args.warmup):
-        oracle_sample(chunks, 1)
+    from oracle import cxx
+    total = args.warmup + args.steps
+    per_mode = (total + len(MODES) - 1) // len(MODES)
+    chunks = [W.chunk_data(i) for i in range(min(W.nchunks, 2 + per_mode))]
+    streams = _cxx_streams(chunks)
+    nxt = {name: 2 for name, _ in MODES}
     work = 0
     secs = 0.0
-    desc = ""
-    for _ in range(args.steps):
-        w_, s_, desc = oracle_sample(chunks, args.ref_rows)
-        work += w_
-        secs += s_
+    for k in range(total):
+        name = MODES[k % len(MODES)][0]
+        i = nxt[name]
+        nxt[name] = 2 + (i - 1) % (len(chunks) - 2)
+        t0 = time.perf_counter()
+        r = streams[name].push(chunks[i], want_plane=False)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            work += W.ndm * (r["e_new"] - r["e_prev"])
+            secs += dt
     v = work / secs
+    ncpu = cxx.max_threads()
+    desc = ("C++/OpenMP oracle, whole path (encoder, SND tree per DM without sharing, matched filter, closing + "
+            "labelling); a step = one steady-state 16384-sample chunk of one mode, modes in turn; all host cores")
     out.update({"value": v, "ms_per_step": 1e3 * secs / max(args.steps, 1),
                 "config": {"workload": "nc1024_2048dm: 1024 ch 400-416 MHz, dt 0.138 ms, 2048 DMs 0-2000, "
                                        "16384-sample chunks, B=8, binary+graded+float",
                            "sample": desc},
-                "cpu_baseline": {"value": v, "unit": "DM-samples/s", "cores": 1, "kind": "oracle", "sample": desc},
+                "cpu_baseline": {"value": v, "unit": "DM-samples/s", "cores": ncpu, "kind": "oracle", "sample": desc},
                 "e2e": {"value": v, "unit": "DM-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
     return out
 
@@ -582,8 +644,7 @@ def run_gpu(args, rank, world, local_rank):
     traffic = _traffic_from_profile(_tree_source_hash())
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        work, secs, desc = oracle_sample(host_chunks[:3], args.ref_rows)
-        cpu = {"value": work / secs, "unit": "DM-samples/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = oracle_sample(host_chunks[:3])
         if not args.main_only:
             cpu["rows"] = oracle_rows_sample(host_chunks)
     realtime_beams = e2e / (W.ndm / synth.NC_DT) / len(MODES)
@@ -675,7 +736,6 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sifter", action="store_true", help="skip the learned-sifter measurements")
     ap.add_argument("--no-multibeam", action="store_true", help="skip the 48-beam batch measurements")

@@ -23,10 +23,13 @@ Modules and the passages they follow:
                    "Pipeline overview").
 * ``analytic``   - closed forms used as pins: fire probability, the cascade
                    recursion (Eq. cascade) and SNR_A (Eq. snr_A).
+* ``cxx``        - the same definitions once more in plain C++17 with OpenMP over
+                   trial-DM rows (``cpp/snd_oracle.cpp``), fast enough to check the
+                   full 1024-channel / 2048-DM stream cell by cell; pinned to the
+                   modules above and to the paper's invariants.
 
 Where the paper is silent or ambiguous, each function states the reading it
-takes; the same readings are listed in DESIGN.md. Nothing here is "parity
-unpinned" except the candidate identity beyond the closing/labelling pins
+takes. Nothing here is "parity unpinned" except the candidate identity beyond the closing/labelling pins
 (no printed values exist for it), which the candidates module header says.
 """
 from . import analytic, candidates, delays, encoder, mf, stream, tree  # noqa: F401

@@ -155,6 +155,14 @@ class Workload:
             return draw_bursts(self.seed, self.nbursts, dm_range=(10.0, 90.0),
                                fwhm_range=(1e-3 / NC_DT, 1e-3 / NC_DT), snr_range=(8.0, 20.0),
                                t_range=(sw + 200.0, self.nsamp - 200.0), min_sep=400.0)
+        if self.name.startswith("nc4096"):
+            # a short stream: bursts arrive (at the top of the band) within the plane range
+            # the stream emits, [0, nsamp - sweep), away from its ends
+            t_end = self.nsamp - sw
+            return draw_bursts(self.seed, self.nbursts, dm_range=(20.0, self.dm_max - 20.0),
+                               fwhm_range=(1.0, 10e-3 / NC_DT), snr_range=(6.0, 50.0),
+                               t_range=(1500.0, t_end - 1500.0), log_fwhm=True, log_snr=True,
+                               min_sep=0.05 / NC_DT)
         return draw_bursts(self.seed, self.nbursts, dm_range=(20.0, min(1980.0, self.dm_max)),
                            fwhm_range=(1.0, 10e-3 / NC_DT), snr_range=(6.0, 50.0),
                            t_range=(sw + 200.0, self.nsamp - 200.0), log_fwhm=True, log_snr=True,
@@ -171,3 +179,7 @@ NC64 = Workload("nc64_128dm", seed=1, nchan=64, ndm=128, dm_max=100.0, chunk=163
 # Full Northern Cross beam: 1024 channels, 2048 DMs over 0-2000, 2^18 samples in 16 chunks.
 NC1024 = Workload("nc1024_2048dm", seed=2, nchan=1024, ndm=2048, dm_max=2000.0, chunk=16384,
                   nchunks=16, branching=8, nbursts=200)
+# Stress-scale beam: 4096 channels 400-416 MHz, 8192 DMs over 0-3000, 1 s chunks of 7246
+# samples (eight of them: the stream emits plane samples from the sixth chunk on), B = 4.
+NC4096 = Workload("nc4096_8192dm", seed=500, nchan=4096, ndm=8192, dm_max=3000.0, chunk=7246,
+                  nchunks=8, branching=4, nbursts=12)

@@ -225,88 +225,6 @@ def test_chunk_too_long_rejected():
     assert plan.execute(torch.zeros((1000, 64), dtype=torch.uint8, device="cuda")) == 0
 
 
-# --------------------------------------------------------------------------------------
-# Full Northern Cross beam (1024 channels, 2048 DMs over 0-2000, 16384-sample chunks), in
-# the launch configuration the bench times: sampled plane rows against the oracle row by
-# row, and every candidate re-derived by the oracle from its own row.
-# --------------------------------------------------------------------------------------
-
-_NC = {}
-
-
-def _nc_chunks():
-    if "data" not in _NC:
-        w = synth.NC1024
-        b = w.bursts()
-        _NC["data"] = [w.chunk_data(i, b) for i in range(w.nchunks)]
-    return _NC["data"]
-
-
-def _oracle_rows(x_list, x_t0, delays, rows, t0, n, cfg):
-    x = np.concatenate(x_list, axis=1)
-    return otree.snd_rows(x, x_t0, delays, rows, t0, n, cfg.mode, cfg.cluster, cfg.branching,
-                          cfg.k_leaf, cfg.k_internal, cfg.cap)
-
-
-@pytest.mark.parametrize("mode,B", [("float", 8), ("graded", 8), ("binary", 8), ("binary", 2)])
-def test_nc1024_full_stream_sampled(mode, B):
-    w = synth.NC1024
-    m = MODES[mode]
-    cfg = ostream.defaults(m, branching=B)
-    freqs, dms = w.freqs(), w.dms()
-    plan = g.Plan(freqs, synth.NC_DT, dms, B, m, _opts(m, cfg))
-    tab = odelays.delay_table(freqs, synth.NC_DT, dms)
-    D = int(tab.max())
-    widths = [omf.row_widths(freqs, synth.NC_DT, d, cfg.mf_alpha) for d in dms]
-    wmax = max(max(x) for x in widths)
-    rng = np.random.default_rng(B + 10 * m)
-    rows = sorted(set([0, 1, 7, 8, 1023, 2040, 2047] + list(rng.integers(0, 2048, 5))))
-    chunks = _nc_chunks()
-    xs, check_at = [], {1, 2, 7, 15}
-    T = E = 0
-    planes = {}
-    for i, ch in enumerate(chunks):
-        nemit = plan.nemit_next(ch.shape[0])
-        dtype = torch.float32 if m == ostream.FLOAT else torch.int32
-        out = torch.empty((2048, max(nemit, 1)), dtype=dtype, device="cuda") if i in check_at else None
-        plan.execute(torch.from_numpy(ch).cuda(), out)
-        xs.append(oenc.encode_chunk(ch, cfg.enc_theta)[0])
-        if out is not None and nemit:
-            got = out[rows, :nemit].cpu().numpy()
-            exp = _oracle_rows(xs[-3:], T + ch.shape[0] - sum(x.shape[1] for x in xs[-3:]), tab, rows, E, nemit, cfg)
-            r = {"plane": exp, "plane_float": otree.float_scale(exp, 1024)}
-            _compare_plane(m, got, r, 1024)
-        T += ch.shape[0]
-        E = max(0, T - D)
-    cands, rc = plan.candidates()
-    assert rc == 0
-    # sorted by (t, dm); every peak re-derived by the oracle from its own row and block
-    keys = [(int(c["t"]), int(c["dm_index"])) for c in cands]
-    assert keys == sorted(keys) and len(set(keys)) == len(keys)
-    assert all(c["npix"] >= cfg.n_min for c in cands)
-    full_x = np.concatenate(xs, axis=1)
-    F_edges = []
-    T = 0
-    E = F = 0
-    for ch in chunks:
-        T += ch.shape[0]
-        E = max(0, T - D)
-        Fn = max(0, E - (wmax - 1))
-        if Fn > F:
-            F_edges.append((F, Fn, E))
-        F = Fn
-    sample = cands if len(cands) <= 40 else [cands[i] for i in np.linspace(0, len(cands) - 1, 40).astype(int)]
-    for c in sample:
-        d, t = int(c["dm_index"]), int(c["t"])
-        f0, f1, e1 = next(b for b in F_edges if b[0] <= t < b[1])
-        y = otree.snd_rows(full_x, 0, tab, [d], f0, e1 - f0, cfg.mode, cfg.cluster, cfg.branching,
-                           cfg.k_leaf, cfg.k_internal, cfg.cap)[0]
-        floor = cfg.sigma_min if m == ostream.BINARY else None
-        mk, snr, wd, _, _ = omf.row_mf(y, f1 - f0, widths[d], cfg.det_theta, floor)
-        assert mk[t - f0]
-        assert np.float32(snr[t - f0]) == c["snr"] and wd[t - f0] == c["width"]
-
-
 @pytest.mark.parametrize("mode", ["binary", "graded"])
 def test_uint8_plane_output(mode):
     """plane_dtype = 1 writes the same root values as uint8."""
