@@ -68,6 +68,10 @@ typedef struct snd_plan_s* snd_plan_t;
 /* Option flag (SND_MODE_ZFLOAT only): store the payload and every partial sum below the root
  * in FP16 (round to nearest even) instead of FP32; accumulation stays FP32. */
 #define SND_FLAG_FP16_PARTIALS 2
+/* Option flag: evaluate the tree with the leaf-sharing kernel (distinct leaf patterns of a DM
+ * tile evaluated once, then gathered per DM) even where the direct kernel applies. Results
+ * are identical; it keeps the paper's shared-leaf evaluation available for comparison. */
+#define SND_FLAG_LEAF_SHARING 4
 
 /*
  * Options. Fill with snd_options_init(mode, &o) (Supplementary Table S1 operating point
@@ -88,7 +92,8 @@ typedef struct {
   int32_t cand_capacity;    /* candidates held on the device between snd_candidates calls */
   int32_t cell_capacity;    /* mask cells with S/N kept per matched-filter block */
   int32_t run_capacity;     /* closed-mask runs per matched-filter block */
-  int32_t flags;            /* 0, SND_FLAG_REFERENCE_TREE, or SND_FLAG_FP16_PARTIALS (zfloat) */
+  int32_t flags;            /* 0 or SND_FLAG_REFERENCE_TREE / SND_FLAG_LEAF_SHARING, or
+                               SND_FLAG_FP16_PARTIALS (zfloat) */
   int32_t plane_dtype;      /* d_plane_out element type: 0 = int32 / float32 (default); 1 = uint8,
                                binary and graded modes only (their roots are 0..255) */
 } snd_options_t;
@@ -125,6 +130,8 @@ typedef struct {
   int32_t tree_smem_bytes;         /* dynamic shared memory of the tree kernel */
   int32_t max_patterns_per_group;
   int64_t kernel_launches;         /* CUDA kernels enqueued by this plan since binding */
+  int32_t tree_kernel;             /* 0 leaf-sharing k_tree, 1 direct k_snd, 2 reference, 3 labelled payload */
+  int32_t reserved_stats;
 } snd_plan_stats_t;
 
 /* Pipeline stages timed by snd_profile / snd_profile_read. */

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libsnd.so")
 MODE_BINARY, MODE_GRADED, MODE_FLOAT, MODE_ZFLOAT = 0, 1, 2, 3
 FLAG_REFERENCE_TREE = 1
 FLAG_FP16_PARTIALS = 2
+FLAG_LEAF_SHARING = 4
+TREE_KERNELS = {0: "leaf-sharing k_tree", 1: "direct k_snd", 2: "reference k_tree_ref", 3: "labelled-payload k_tree_z"}
 
 STATUS = {
     0: "SND_OK", -1: "SND_ERR_ARG", -2: "SND_ERR_FREQ_ORDER", -3: "SND_ERR_DM",
@@ -55,7 +57,7 @@ class SndPlanStats(ctypes.Structure):
         ("scored", ctypes.c_int64), ("candidates_pending", ctypes.c_int32), ("tree_tile_dms", ctypes.c_int32),
         ("tree_tile_words", ctypes.c_int32), ("tree_group_leaves", ctypes.c_int32),
         ("tree_smem_bytes", ctypes.c_int32), ("max_patterns_per_group", ctypes.c_int32),
-        ("kernel_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64), ("tree_kernel", ctypes.c_int32), ("reserved_stats", ctypes.c_int32),
     ]
 
 

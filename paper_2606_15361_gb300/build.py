@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsnd.so")
-CU_SOURCES = ["encode.cu", "tree.cu", "ztree.cu", "mf.cu", "ccl.cu", "runtime.cu", "noalloc.cu", "multirate.cu",
+CU_SOURCES = ["encode.cu", "tree.cu", "tree_direct.cu", "ztree.cu", "mf.cu", "ccl.cu", "runtime.cu", "noalloc.cu", "multirate.cu",
               "sifter.cu", "batch.cu"]
 CPP_SOURCES = ["plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -42,6 +42,7 @@ struct VecHash {
 int choose_tree_geometry(Plan& p);
 int choose_tree_geometry_w(Plan& p, int warps);
 int choose_ztree_geometry(Plan& p);
+void choose_direct_geometry(Plan& p);
 
 }  // namespace
 
@@ -250,13 +251,18 @@ int build_plan(Plan& p) {
   // --- DM tiles: distinct leaf patterns per (tile, leaf), per-DM index and shift, for the
   // bit-sliced tree; the labelled-payload tree has tiles of its own (and no bit ring use) ---
   int rc = (p.mode == SND_MODE_ZFLOAT) ? choose_ztree_geometry(p) : choose_tree_geometry(p);
+  if (p.mode != SND_MODE_ZFLOAT) {
+    choose_direct_geometry(p);
+    if (p.direct) rc = SND_OK;  // the leaf-sharing kernel may not fit; the direct one does
+  }
   if (rc) return rc;
 
   // --- ring, plane ring and workspace layout ---
   const TreeGeom& g = p.geom;
   const int maxw_chunk = (p.max_chunk + 31) / 32;
   // words reachable from one emitted block: delay + chunk + tile padding + funnel partner
-  p.R = (p.D >> 5) + maxw_chunk + g.cspan + 8;
+  p.R = (p.D >> 5) + maxw_chunk + std::max(g.cspan, p.dgeom.cspan) + 8;
+  p.R = static_cast<int>(align_up(static_cast<size_t>(p.R), 4));  // 16-byte aligned bulk copies of ring rows
   p.Lp = static_cast<int>(align_up(static_cast<size_t>(p.wmax) - 1 + p.max_chunk + 96, 32));
   p.mw = (p.Lp + 31) / 32;
   size_t o = 0;
@@ -294,6 +300,8 @@ int build_plan(Plan& p) {
   p.off.gmeta = take(sizeof(uint32_t) * p.gmeta.size());
   p.off.tile_wb = take(sizeof(int32_t) * p.tile_wb.size());
   p.off.delays = take(sizeof(int32_t) * p.delays.size());
+  p.off.dmeta = take(sizeof(uint16_t) * std::max<size_t>(8, p.dmeta.size()));
+  p.off.dbase = take(sizeof(int32_t) * std::max<size_t>(4, p.dbase.size()));
   if (p.mode == SND_MODE_ZFLOAT) {
     const size_t es = p.zgeom.fp16 ? 2 : 4;
     p.off.zring = take(es * static_cast<size_t>(nchan) * p.zgeom.Rz);
@@ -473,6 +481,106 @@ int choose_tree_geometry_w(Plan& p, int warps) {
   return SND_OK;
 }
 
+// Direct tree kernel (tree_direct.cu): whether it applies to the plan, its instantiation and
+// tile shape, and its tables. A CTA covers 32 consecutive trial DMs (lanes) and warps x kw
+// output words; channels are staged 64 at a time. Per (DM tile, channel) the first staged ring
+// word is base4 = (min over the tile of delta >> 5) rounded down to a multiple of 4 (16-byte
+// aligned bulk copies), and per (tile, channel, DM) the 16-bit entry (delta >> 5) - base4 << 5 |
+// delta & 31 gives the DM's window word and funnel shift.
+void choose_direct_geometry(Plan& p) {
+  snd::DirectGeom& g = p.dgeom;
+  g = snd::DirectGeom{};
+  p.direct = false;
+  p.dmeta.clear();
+  p.dbase.clear();
+  if (p.mode == SND_MODE_ZFLOAT || (p.flags & (SND_FLAG_REFERENCE_TREE | SND_FLAG_LEAF_SHARING))) return;
+  const int nchan = p.nchan, ndm = p.ndm;
+  if (nchan % 64 != 0 || nchan >= 8192) return;
+  int inst = snd::kDirNone, kw = 4;
+  if (p.mode == SND_MODE_FLOAT) {
+    inst = nchan < 2048 ? snd::kDirFloat11 : snd::kDirFloat13;
+  } else if (p.mode == SND_MODE_GRADED) {
+    // the exact level: the first level whose (full) nodes hold more than N channels; below it
+    // every node value is its plain channel sum
+    int sub = p.nlev - 1;
+    int64_t width = p.C;
+    for (int l = 0; l < p.nlev; ++l, width *= p.B) {
+      if (std::min<int64_t>(width, nchan) > p.N) {
+        sub = l;
+        break;
+      }
+    }
+    int64_t sub_ch = p.C;
+    for (int l = 0; l < sub; ++l) sub_ch *= p.B;
+    if (sub == p.nlev - 1) sub_ch = nchan;
+    if (sub_ch % 64 != 0 || nchan % sub_ch != 0) return;
+    int planes = 0;
+    while ((int64_t(1) << planes) <= sub_ch) ++planes;
+    const int up = p.nlev - 1 - sub;
+    if (up == 0) {
+      inst = planes <= 11 ? snd::kDirGraded11U0 : snd::kDirGraded13U0;
+    } else if (planes <= 9 && up == 1) {
+      inst = snd::kDirGraded9U1;
+    } else if (planes <= 9 && up == 2) {
+      inst = snd::kDirGraded9U2;
+      kw = 2;
+    } else {
+      return;
+    }
+    g.sub_lev = sub;
+    g.sub_groups = static_cast<int>(sub_ch / 64);
+  } else {
+    if (p.C != 4 || p.KL < 1 || p.KL > 4 || p.KI < 1 || p.KI > 2 || p.nlev < 2) return;
+    const int up = p.nlev - 1;
+    if (up <= 4) {
+      inst = snd::kDirBinary4;
+    } else if (up <= 8) {
+      inst = snd::kDirBinary8;
+    } else if (up <= 12) {
+      inst = snd::kDirBinary12;
+      kw = 2;
+    } else {
+      return;
+    }
+  }
+  g.kw = kw;
+  g.warps = 8;
+  g.tile_words = g.warps * kw;
+  g.ndm_tiles = (ndm + 31) / 32;
+  p.dbase.assign(static_cast<size_t>(g.ndm_tiles) * nchan, 0);
+  int64_t omax = 0;
+  for (int t = 0; t < g.ndm_tiles; ++t)
+    for (int c = 0; c < nchan; ++c) {
+      int32_t lo = INT32_MAX, hi = 0;
+      for (int d = t * 32; d < std::min(ndm, t * 32 + 32); ++d) {
+        const int32_t v = p.delays[static_cast<size_t>(d) * nchan + c];
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+      }
+      const int32_t b4 = (lo >> 5) & ~3;
+      p.dbase[static_cast<size_t>(t) * nchan + c] = b4;
+      omax = std::max<int64_t>(omax, (hi >> 5) - b4);
+    }
+  if (omax > 2047) return;
+  g.cspan = static_cast<int>(align_up(static_cast<size_t>(4 + omax + g.tile_words), 4));
+  const int64_t smem = (2 * 64 * static_cast<int64_t>(g.cspan) + 64 * 32 + nchan) * 4;
+  if (smem > 200 * 1024) return;
+  g.smem_bytes = static_cast<int>(smem);
+  p.dmeta.assign(static_cast<size_t>(g.ndm_tiles) * nchan * 32, 0);
+  for (int t = 0; t < g.ndm_tiles; ++t)
+    for (int c = 0; c < nchan; ++c) {
+      const int32_t b4 = p.dbase[static_cast<size_t>(t) * nchan + c];
+      for (int l = 0; l < 32; ++l) {
+        const int d = std::min(ndm - 1, t * 32 + l);
+        const int32_t v = p.delays[static_cast<size_t>(d) * nchan + c];
+        p.dmeta[(static_cast<size_t>(t) * nchan + c) * 32 + l] =
+            static_cast<uint16_t>((((v >> 5) - b4) << 5) | (v & 31));
+      }
+    }
+  g.inst = inst;
+  p.direct = true;
+}
+
 // Labelled-payload tree geometry: DMs per CTA, samples per CTA (32 lanes x samples per
 // lane, fewer samples for deeper trees so the per-level partial sums stay in registers), the
 // first staged sample of each channel per DM tile (its smallest delay over the tile) and the
@@ -553,7 +661,7 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
   } else {
     snd_options_init(mode, &o);
   }
-  if (o.flags & ~(SND_FLAG_REFERENCE_TREE | SND_FLAG_FP16_PARTIALS)) return SND_ERR_ARG;
+  if (o.flags & ~(SND_FLAG_REFERENCE_TREE | SND_FLAG_FP16_PARTIALS | SND_FLAG_LEAF_SHARING)) return SND_ERR_ARG;
   if ((o.flags & SND_FLAG_FP16_PARTIALS) && mode != SND_MODE_ZFLOAT) return SND_ERR_ARG;
   if ((o.flags & SND_FLAG_REFERENCE_TREE) && mode == SND_MODE_ZFLOAT) return SND_ERR_UNSUPPORTED;
   if (o.cluster_size < 1 || o.cluster_size > 7) return SND_ERR_UNSUPPORTED;
@@ -676,6 +784,13 @@ extern "C" int snd_plan_stats(snd_plan_t plan, snd_plan_stats_t* s) {
   }
   s->max_patterns_per_group = p.geom.max_pat_group;
   s->kernel_launches = p.launches;
+  s->tree_kernel = (p.mode == SND_MODE_ZFLOAT) ? 3 : (p.flags & SND_FLAG_REFERENCE_TREE) ? 2 : p.direct ? 1 : 0;
+  if (p.direct) {
+    s->tree_tile_dms = 32;
+    s->tree_tile_words = p.dgeom.tile_words;
+    s->tree_group_leaves = 64 / p.C;
+    s->tree_smem_bytes = p.dgeom.smem_bytes;
+  }
   return SND_OK;
 }
 

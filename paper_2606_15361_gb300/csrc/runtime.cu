@@ -132,6 +132,8 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.gmeta = at<uint32_t>(d_ws, o.gmeta);
   dp.tile_wb = at<int32_t>(d_ws, o.tile_wb);
   dp.delays = at<int32_t>(d_ws, o.delays);
+  dp.dmeta = at<uint16_t>(d_ws, o.dmeta);
+  dp.dbase = at<int32_t>(d_ws, o.dbase);
   const bool z = p.mode == SND_MODE_ZFLOAT;
   dp.zring = z ? at<void>(d_ws, o.zring) : nullptr;
   dp.ztab = z ? at<void>(d_ws, o.ztab) : nullptr;
@@ -154,6 +156,8 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   if (e == cudaSuccess) e = upload(d_ws, o.gmeta, p.gmeta, s);
   if (e == cudaSuccess) e = upload(d_ws, o.tile_wb, p.tile_wb, s);
   if (e == cudaSuccess) e = upload(d_ws, o.delays, p.delays, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.dmeta, p.dmeta, s);
+  if (e == cudaSuccess) e = upload(d_ws, o.dbase, p.dbase, s);
   if (e == cudaSuccess && z) e = upload(d_ws, o.zwb, p.zwb, s);
   if (e == cudaSuccess && z) e = upload(d_ws, o.zcarry, p.zcarry, s);
   if (e != cudaSuccess) {
@@ -285,7 +289,7 @@ extern "C" int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_
   *n_out = take;
   p.pending_host = 0;
   const uint32_t st = cnt[snd::kCntStatus];
-  if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout)) return SND_ERR_TIMEOUT;
+  if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout | snd::kStatusTreeTimeout)) return SND_ERR_TIMEOUT;
   if (st & (snd::kStatusCellOverflow | snd::kStatusRunOverflow | snd::kStatusCandOverflow |
             snd::kStatusBlockCandOverflow | snd::kStatusBounds))
     return SND_ERR_OVERFLOW;

@@ -27,6 +27,7 @@ enum : uint32_t {
   kStatusTauTimeout = 1u << 4,
   kStatusUnionTimeout = 1u << 5,
   kStatusBounds = 1u << 6,
+  kStatusTreeTimeout = 1u << 7,
 };
 
 // One matched-filter cell kept for peak selection.
@@ -55,6 +56,33 @@ struct TreeGeom {
   int planes;          // planes of a leaf value (1 binary, 3 graded/float)
   int smem_bytes;      // dynamic shared memory per CTA
   int ndm_tiles;
+};
+
+// Direct tree kernel (tree_direct.cu) instantiations.
+enum {
+  kDirNone = -1,
+  kDirFloat11 = 0,   // float, counts < 2048, 4 words per lane
+  kDirFloat13,       // float, counts < 8192
+  kDirGraded9U1,     // graded, exact-level nodes of <= 511 channels, one capped level above
+  kDirGraded9U2,     // graded, as above with two capped levels above (2 words per lane)
+  kDirGraded11U0,    // graded, the exact level is the root (<= 2047 channels)
+  kDirGraded13U0,    // graded, the exact level is the root (<= 8191 channels)
+  kDirBinary4,       // binary, C = 4, <= 4 levels above the leaves
+  kDirBinary8,       // binary, <= 8 levels above the leaves
+  kDirBinary12,      // binary, <= 12 levels above the leaves (2 words per lane)
+};
+
+// Direct tree kernel geometry: CTA = 32 consecutive trial DMs (lane = DM) x warps * kw words.
+struct DirectGeom {
+  int inst = kDirNone;
+  int warps = 8;
+  int kw = 4;
+  int tile_words = 32;   // warps * kw
+  int ndm_tiles = 0;     // ceil(ndm / 32)
+  int cspan = 0;         // staged ring words per channel (multiple of 4)
+  int smem_bytes = 0;
+  int sub_lev = 0;       // graded: the exact level (first level whose nodes may exceed N)
+  int sub_groups = 1;    // graded: 64-channel groups per exact-level node
 };
 
 // Labelled-payload (zfloat) tree geometry (chosen on the host).
@@ -107,6 +135,8 @@ struct DevPtrs {
   void* ztab;              // zfloat: [nchan][256] payload of each uint8 value (0 below the level)
   int32_t* zwb;            // zfloat: [ndm_tiles][nchan] first staged sample offset per channel
   int32_t* zcarry;         // zfloat: [nleaves] carry depth of each leaf
+  uint16_t* dmeta;         // direct tree: [ndm_tiles][nchan][32] staged word offset << 5 | shift
+  int32_t* dbase;          // direct tree: [ndm_tiles][nchan] first staged ring word (multiple of 4)
 };
 
 // Counter slots.
@@ -151,6 +181,10 @@ struct Plan {
   std::vector<uint32_t> gepk, gmeta;  // precomputed staging offsets (see choose_tree_geometry)
   std::vector<int32_t> gleaf;
   TreeGeom geom{};
+  DirectGeom dgeom{};
+  bool direct = false;                  // the tree runs on the direct kernel (tree_direct.cu)
+  std::vector<uint16_t> dmeta;
+  std::vector<int32_t> dbase;
   ZGeom zgeom{};
   std::vector<int32_t> zwb, zcarry;
 
@@ -162,7 +196,7 @@ struct Plan {
   struct Off {
     size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
         run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, staging2, width_mask, dm_f32, tp_off,
-        gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb, zcarry;
+        gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb, zcarry, dmeta, dbase;
   } off{};
 
   // binding and stream state
@@ -249,6 +283,10 @@ struct GraphRunner {
 };
 
 cudaError_t launch_tree_z(const Plan& p, int64_t e_prev, int64_t e_new, void* d_plane_out, cudaStream_t s);
+// tree_direct.cu: the direct tree kernel of plans with p.direct
+cudaError_t launch_tree_direct(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream_t s);
+cudaError_t launch_tree_direct_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
+                                     cudaStream_t s);
 
 template <typename Stage>
 cudaError_t chunk_post(const Plan& p, const ChunkPos& c, void* d_plane_out, cudaStream_t s, Stage&& stage) {

@@ -992,6 +992,7 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
     p.launches += 1;
     return cudaGetLastError();
   }
+  if (p.direct) return launch_tree_direct(p, e_prev, e_new, s);
   TreeArgs a;
   int ntx = 0;
   tree_args(p, e_prev, e_new, a, &ntx);
@@ -1007,7 +1008,23 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
 // instantiation and block shape run in one launch (k_tree_multi, up to 64 beams each).
 cudaError_t launch_tree_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
                               cudaStream_t s) {
+  {
+    // plans on the direct kernel go through its own grouped launches
+    std::vector<const Plan*> dp;
+    std::vector<int64_t> dep, den;
+    for (int i = 0; i < n; ++i)
+      if (plans[i]->direct) {
+        dp.push_back(plans[i]);
+        dep.push_back(e_prev[i]);
+        den.push_back(e_new[i]);
+      }
+    if (!dp.empty()) {
+      const cudaError_t e = launch_tree_direct_batch(dp.data(), dep.data(), den.data(), static_cast<int>(dp.size()), s);
+      if (e != cudaSuccess) return e;
+    }
+  }
   std::vector<int> done(n, 0);
+  for (int i = 0; i < n; ++i) done[i] = plans[i]->direct ? 1 : 0;
   for (int i = 0; i < n; ++i) {
     if (done[i]) continue;
     const int key = tree_inst(*plans[i]);

@@ -1,0 +1,636 @@
+// SND tree, direct form (Methods, "The Spiking Neural Dedispersion algorithm", "Tree
+// activation modes"), for one GB300 CTA per (32 trial DMs x tile of output words).
+//
+// What is computed is the tree of the paper, node rule by node rule; only the order of the
+// exact integer additions differs from a level-by-level walk:
+//  * Mode C (float): no node rule, so the root is the sum of all channel bits. Every channel's
+//    bit is added straight into a bit-sliced counter (carry-save full adders, 2 logic ops per
+//    channel and word), which is the same integer.
+//  * Mode B (graded): min(s, N) can only bind at a node whose channel count exceeds N. Below
+//    the first such level ("exact level") every node value is its plain channel sum, so each
+//    exact-level node is counted directly over its channels, clipped to N, and the few levels
+//    above it are evaluated node by node with saturating 8-plane adders (the cap at every node,
+//    the root included).
+//  * Mode A (binary): every node thresholds, so the tree is walked leaf by leaf: a leaf is the
+//    quorum of its C = 4 channel bits (>= K_L), and every node above keeps a two-plane
+//    thermometer of its child count for the quorum K_I <= 2.
+// Every channel is read at t + delta_c(d) (the shifts telescope), as in the leaf-sharing
+// kernel (tree.cu), so both give the oracle's planes bit for bit.
+//
+// GPU mapping:
+//  * lanes are 32 consecutive trial DMs; a warp owns KW consecutive 32-sample words of the
+//    CTA's time tile (warp w: words w*KW ..), so per channel a lane reads one 16-bit offset
+//    and then KW+1 consecutive window words (a sliding funnel-shift window). The 32 DMs of a
+//    tile read one channel at offsets that differ by less than 32 words, so the reads hit
+//    distinct banks (or broadcast) without conflicts.
+//  * channels are staged 64 at a time: the producer (warp 0) issues one TMA bulk copy
+//    (cp.async.bulk) per channel window of the L2-resident bit ring, plus one for the group's
+//    offset table, onto a double-buffered mbarrier pipeline, so the next group lands while
+//    the current one is added. Waits are bounded; a wait that runs out sets a status bit and
+//    ends the CTA.
+//  * the counter planes stay in registers across groups; the root is turned into int32
+//    samples by a 32x32 bit transpose and written with 128-bit stores.
+
+#include <vector>
+
+#include "snd_internal.h"
+
+namespace snd {
+namespace {
+
+constexpr int kDG = 64;                          // channels per staged group
+constexpr long long kDirWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+struct DirArgs {
+  const uint32_t* ring;
+  int R, nchan, ndm;
+  int B, KL, KI, N, nlev;
+  int level_nodes[kMaxLevels];
+  int sub_groups;          // graded: staged groups per exact-level node
+  int sub_lev;             // graded: the exact level
+  const uint16_t* meta;    // [ndm_tiles][nchan][32]: (word offset << 5) | bit shift
+  const int32_t* base4;    // [ndm_tiles][nchan]: first staged ring word (relative, multiple of 4)
+  int cspan;               // staged words per channel (multiple of 4)
+  int tile_words;          // NW * KW output words per CTA
+  long long word0;         // absolute index of the first output word
+  int nwords;              // output words of this call
+  int32_t* plane;
+  int Lp;
+  uint32_t* status;
+};
+
+constexpr int kMaxDirBeams = 64;
+
+struct DirMulti {
+  int nbeams;
+  int first[kMaxDirBeams];
+  int ntx[kMaxDirBeams];
+  DirArgs beam[kMaxDirBeams];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  if (bar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!bar_try(bar, parity))
+    if (clock64() - t0 > kDirWaitCycles) return false;
+  return true;
+}
+
+// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// s += a + b in carry-save form: s keeps the sum bit, the carry (weight x2) is returned
+__device__ __forceinline__ uint32_t fa(uint32_t& s, uint32_t a, uint32_t b) {
+  const uint32_t x = s;
+  s = x ^ a ^ b;
+  return (x & a) | (b & (x ^ a));
+}
+
+// Counter planes P[0..NPL) += 2^L bits fetched for channels c0 .. c0 + 2^L: a balanced tree
+// of full adders; the single carry out (weight 2^L) is returned in cout.
+template <int L, int KW, int NPL, typename F>
+__device__ __forceinline__ void hs_block(uint32_t (&P)[NPL][KW], uint32_t (&cout)[KW], int c0, F& fetch) {
+  if constexpr (L == 1) {
+    uint32_t a[KW], b[KW];
+    fetch(c0, a);
+    fetch(c0 + 1, b);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) cout[j] = fa(P[0][j], a[j], b[j]);
+  } else {
+    uint32_t ca[KW], cb[KW];
+    hs_block<L - 1, KW, NPL>(P, ca, c0, fetch);
+    hs_block<L - 1, KW, NPL>(P, cb, c0 + (1 << (L - 1)), fetch);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) cout[j] = fa(P[L - 1][j], ca[j], cb[j]);
+  }
+}
+
+// Add one group of 64 channels into P (planes 0..5 by the adder tree, the weight-64 carry
+// rippled up from plane 6).
+template <int KW, int NPL, typename F>
+__device__ __forceinline__ void add_group(uint32_t (&P)[NPL][KW], F& fetch) {
+  uint32_t c[KW];
+  hs_block<6, KW, NPL>(P, c, 0, fetch);
+#pragma unroll
+  for (int p = 6; p < NPL; ++p)
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+      const uint32_t t = P[p][j] & c[j];
+      P[p][j] ^= c[j];
+      c[j] = t;
+    }
+}
+
+// min(s, N) of an NP-plane count as 8 planes (N <= 255)
+template <int NP>
+__device__ __forceinline__ void cap8(const uint32_t* s, int N, uint32_t* out) {
+  uint32_t gt = 0, eq = 0xFFFFFFFFu;
+#pragma unroll
+  for (int p = NP - 1; p >= 0; --p) {
+    if ((N >> p) & 1) {
+      eq &= s[p];
+    } else {
+      gt |= eq & s[p];
+      eq &= ~s[p];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const uint32_t sp = p < NP ? s[p < NP ? p : 0] : 0u;
+    out[p] = ((N >> p) & 1) ? (sp | gt) : (sp & ~gt);
+  }
+}
+
+// acc = min(acc + v, N) on 8 planes (acc, v <= N <= 255)
+__device__ __forceinline__ void add_sat8(uint32_t* acc, const uint32_t* v, int N) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const uint32_t x = acc[p], y = v[p];
+    acc[p] = x ^ y ^ c;
+    c = (x & y) | (c & (x ^ y));
+  }
+  uint32_t s9[9];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) s9[p] = acc[p];
+  s9[8] = c;
+  cap8<9>(s9, N, acc);
+}
+
+// 32x32 bit transpose: bit c of m[r] <-> bit r of m[c]
+__device__ __forceinline__ void transpose32(uint32_t* m) {
+  uint32_t mask = 0x0000FFFFu;
+#pragma unroll
+  for (int j = 16; j != 0; j >>= 1, mask ^= (mask << j)) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k & j) continue;
+      const uint32_t t = ((m[k] >> j) ^ m[k + j]) & mask;
+      m[k + j] ^= t;
+      m[k] ^= t << j;
+    }
+  }
+}
+
+template <int NP>
+__device__ __forceinline__ void store_planes(int32_t* dst, const uint32_t* planes) {
+  uint32_t m[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) m[i] = (i < NP) ? planes[i < NP ? i : 0] : 0u;
+  transpose32(m);
+  int4* d4 = reinterpret_cast<int4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    d4[i] = make_int4(static_cast<int>(m[4 * i]), static_cast<int>(m[4 * i + 1]), static_cast<int>(m[4 * i + 2]),
+                      static_cast<int>(m[4 * i + 3]));
+}
+
+__device__ __forceinline__ void store_bits(int32_t* dst, uint32_t v) {
+  int4* d4 = reinterpret_cast<int4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    d4[i] = make_int4((v >> (4 * i)) & 1, (v >> (4 * i + 1)) & 1, (v >> (4 * i + 2)) & 1, (v >> (4 * i + 3)) & 1);
+}
+
+constexpr int kBinary = SND_MODE_BINARY, kGraded = SND_MODE_GRADED, kFloat = SND_MODE_FLOAT;
+
+// Per-lane tree state of each mode. NPL: counter planes; MAXU: levels kept above the counted
+// level (graded: above the exact level; binary: above the leaves).
+template <int MODE, int KW, int NPL, int MAXU>
+struct DState;
+
+template <int KW, int NPL, int MAXU>
+struct DState<kFloat, KW, NPL, MAXU> {
+  uint32_t P[NPL][KW];
+  __device__ __forceinline__ void init(const DirArgs&) {
+#pragma unroll
+    for (int p = 0; p < NPL; ++p)
+#pragma unroll
+      for (int j = 0; j < KW; ++j) P[p][j] = 0;
+  }
+  template <typename F>
+  __device__ __forceinline__ void group(const DirArgs&, int, F& fetch) {
+    add_group<KW, NPL>(P, fetch);
+  }
+  __device__ __forceinline__ void store(int32_t* row, int j) const {
+    uint32_t pl[NPL];
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) pl[p] = P[p][j];
+    store_planes<NPL>(row, pl);
+  }
+};
+
+template <int KW, int NPL, int MAXU>
+struct DState<kGraded, KW, NPL, MAXU> {
+  static_assert(NPL >= 8, "the root is kept in the counter planes");
+  uint32_t P[NPL][KW];  // count of the open exact-level node; at the end, the root's 8 planes
+  uint32_t acc[MAXU > 0 ? MAXU : 1][KW][8];
+  int cnt[MAXU > 0 ? MAXU : 1], node[MAXU > 0 ? MAXU : 1], fan[MAXU > 0 ? MAXU : 1];
+  __device__ __forceinline__ void clearP() {
+#pragma unroll
+    for (int p = 0; p < NPL; ++p)
+#pragma unroll
+      for (int j = 0; j < KW; ++j) P[p][j] = 0;
+  }
+  __device__ __forceinline__ void set_root(const uint32_t (&v)[KW][8]) {
+#pragma unroll
+    for (int j = 0; j < KW; ++j)
+#pragma unroll
+      for (int p = 0; p < 8; ++p) P[p][j] = v[j][p];
+  }
+  __device__ __forceinline__ void init(const DirArgs& a) {
+    clearP();
+#pragma unroll
+    for (int u = 0; u < (MAXU > 0 ? MAXU : 1); ++u) {
+#pragma unroll
+      for (int j = 0; j < KW; ++j)
+#pragma unroll
+        for (int p = 0; p < 8; ++p) acc[u][j][p] = 0;
+      const int l = a.sub_lev + 1 + u;  // level of the node accumulated in acc[u]
+      cnt[u] = 0;
+      node[u] = 0;
+      fan[u] = (l < a.nlev) ? min(a.B, a.level_nodes[l - 1]) : 1;
+    }
+  }
+  template <typename F>
+  __device__ __forceinline__ void group(const DirArgs& a, int g, F& fetch) {
+    add_group<KW, NPL>(P, fetch);
+    if ((g + 1) % a.sub_groups != 0) return;
+    // an exact-level node is complete: its value min(count, N) goes up the capped levels
+    uint32_t cur[KW][8];
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+      uint32_t s[NPL];
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) s[p] = P[p][j];
+      cap8<NPL>(s, a.N, cur[j]);
+    }
+    clearP();
+    if (MAXU == 0 || a.sub_lev == a.nlev - 1) {
+      set_root(cur);
+      return;
+    }
+#pragma unroll
+    for (int u = 0; u < (MAXU > 0 ? MAXU : 1); ++u) {
+      const int l = a.sub_lev + 1 + u;
+      if (l >= a.nlev) break;
+#pragma unroll
+      for (int j = 0; j < KW; ++j) add_sat8(acc[u][j], cur[j], a.N);
+      if (++cnt[u] < fan[u]) break;
+#pragma unroll
+      for (int j = 0; j < KW; ++j)
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          cur[j][p] = acc[u][j][p];
+          acc[u][j][p] = 0;
+        }
+      cnt[u] = 0;
+      ++node[u];
+      fan[u] = min(a.B, a.level_nodes[l - 1] - a.B * node[u]);
+      if (l == a.nlev - 1) set_root(cur);
+    }
+  }
+  __device__ __forceinline__ void store(int32_t* row, int j) const {
+    uint32_t pl[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) pl[p] = P[p][j];
+    store_planes<8>(row, pl);
+  }
+};
+
+template <int KW, int NPL, int MAXU>
+struct DState<kBinary, KW, NPL, MAXU> {
+  uint32_t t0[MAXU][KW], t1[MAXU][KW];  // thermometer of the open node of every level >= 1
+  uint32_t root[KW];
+  int cnt[MAXU], node[MAXU], fan[MAXU];
+  uint32_t ki2;  // all-ones when K_I = 2 (else K_I = 1)
+  __device__ __forceinline__ void init(const DirArgs& a) {
+    ki2 = a.KI >= 2 ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+    for (int u = 0; u < MAXU; ++u) {
+#pragma unroll
+      for (int j = 0; j < KW; ++j) t0[u][j] = t1[u][j] = 0;
+      const int l = 1 + u;
+      cnt[u] = 0;
+      node[u] = 0;
+      fan[u] = (l < a.nlev) ? min(a.B, a.level_nodes[l - 1]) : 1;
+    }
+#pragma unroll
+    for (int j = 0; j < KW; ++j) root[j] = 0;
+  }
+  // push a finished leaf's bits up the tree
+  __device__ __forceinline__ void push(const DirArgs& a, uint32_t (&v)[KW]) {
+#pragma unroll
+    for (int u = 0; u < MAXU; ++u) {
+      const int l = 1 + u;
+      if (l >= a.nlev) break;
+#pragma unroll
+      for (int j = 0; j < KW; ++j) {
+        t1[u][j] |= t0[u][j] & v[j];
+        t0[u][j] |= v[j];
+      }
+      if (++cnt[u] < fan[u]) return;
+#pragma unroll
+      for (int j = 0; j < KW; ++j) {
+        v[j] = (t1[u][j] & ki2) | (t0[u][j] & ~ki2);
+        t0[u][j] = t1[u][j] = 0;
+      }
+      cnt[u] = 0;
+      ++node[u];
+      fan[u] = min(a.B, a.level_nodes[l - 1] - a.B * node[u]);
+      if (l == a.nlev - 1) {
+#pragma unroll
+        for (int j = 0; j < KW; ++j) root[j] = v[j];
+      }
+    }
+  }
+  template <typename F>
+  __device__ __forceinline__ void group(const DirArgs& a, int, F& fetch) {
+#pragma unroll 1
+    for (int k = 0; k < kDG / 4; ++k) {
+      uint32_t x0[KW], x1[KW], x2[KW], x3[KW], v[KW];
+      fetch(4 * k, x0);
+      fetch(4 * k + 1, x1);
+      fetch(4 * k + 2, x2);
+      fetch(4 * k + 3, x3);
+#pragma unroll
+      for (int j = 0; j < KW; ++j) {
+        const uint32_t a0 = x0[j], a1 = x1[j], a2 = x2[j], a3 = x3[j];
+        const uint32_t o01 = a0 | a1, o23 = a2 | a3, n01 = a0 & a1, n23 = a2 & a3;
+        uint32_t r;
+        switch (a.KL) {
+          case 1: r = o01 | o23; break;
+          case 2: r = n01 | n23 | (o01 & o23); break;
+          case 3: r = (n01 & o23) | (n23 & o01); break;
+          default: r = n01 & n23; break;
+        }
+        v[j] = r;
+      }
+      push(a, v);
+    }
+  }
+  __device__ __forceinline__ void store(int32_t* row, int j) const { store_bits(row, root[j]); }
+};
+
+// One CTA: DM tile `tile` (32 DMs, lane = DM) x time tile bx (NW warps x KW words).
+template <int MODE, int KW, int NPL, int MAXU>
+__device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
+  extern __shared__ __align__(128) uint32_t sm[];
+  const int lane = threadIdx.x, wd = threadIdx.y, NW = blockDim.y;
+  const int tid = wd * 32 + lane, nthr = 32 * NW;
+  const int cspan = a.cspan;
+  const int wbuf = kDG * cspan;                    // window words per buffer
+  uint32_t* win = sm;                              // [2][kDG][cspan]
+  uint16_t* met = reinterpret_cast<uint16_t*>(sm + 2 * wbuf);  // [2][kDG][32]
+  int32_t* sbase = reinterpret_cast<int32_t*>(sm + 2 * wbuf + kDG * 32);  // [nchan]
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ int s_abort;
+  const long long aw0 = a.word0 + static_cast<long long>(bx) * a.tile_words;
+  const int lead = static_cast<int>(aw0 & 3);
+  const long long aw4 = aw0 - lead;
+  const int ngroups = a.nchan / kDG;
+
+  for (int c = tid; c < a.nchan; c += nthr) sbase[c] = a.base4[static_cast<size_t>(tile) * a.nchan + c];
+  if (tid == 0) {
+    bar_init(smem_u32(&bars[0]), 1);
+    bar_init(smem_u32(&bars[1]), 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // warp 0 stages group g into buffer b: one bulk copy per channel window, one for the offsets
+  auto issue = [&](int g, int b) {
+    if (wd != 0) return;
+    const uint32_t bar = smem_u32(&bars[b]);
+    // the buffer's previous contents were read by every warp before the last barrier
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (lane == 0) bar_expect(bar, static_cast<uint32_t>(kDG * cspan * 4 + kDG * 64));
+    __syncwarp();
+    for (int i = lane; i < kDG; i += 32) {
+      const int c = g * kDG + i;
+      const int start = static_cast<int>((aw4 + sbase[c]) % a.R);
+      bulk_g2s(smem_u32(win + b * wbuf + i * cspan), a.ring + static_cast<size_t>(c) * 2 * a.R + start,
+               static_cast<uint32_t>(cspan * 4), bar);
+    }
+    if (lane == 0)
+      bulk_g2s(smem_u32(met + b * kDG * 32), a.meta + (static_cast<size_t>(tile) * a.nchan + g * kDG) * 32,
+               kDG * 64, bar);
+  };
+
+  DState<MODE, KW, NPL, MAXU> st;
+  st.init(a);
+  issue(0, 0);
+  int g = 0;
+  for (; g < ngroups; ++g) {
+    const int b = g & 1;
+    if (g + 1 < ngroups) issue(g + 1, b ^ 1);
+    if (!bar_wait(smem_u32(&bars[b]), (g >> 1) & 1)) s_abort = 1;
+    __syncthreads();
+    if (s_abort) break;
+    const uint16_t* M = met + b * kDG * 32 + lane;
+    const uint32_t* Wb = win + b * wbuf + lead + wd * KW;
+    auto fetch = [&](int ci, uint32_t (&v)[KW]) {
+      const uint32_t m = M[ci * 32];
+      const uint32_t* p = Wb + ci * cspan + (m >> 5);
+      uint32_t x[KW + 1];
+#pragma unroll
+      for (int j = 0; j <= KW; ++j) x[j] = p[j];
+#pragma unroll
+      for (int j = 0; j < KW; ++j) v[j] = __funnelshift_r(x[j], x[j + 1], m);
+    };
+    st.group(a, g, fetch);
+    __syncthreads();
+  }
+  if (s_abort) {
+    // a staging wait ran out: report it, and give the copies still in flight (groups g and
+    // g + 1) another bounded wait before the CTA's shared memory is released
+    if (tid == 0) {
+      atomicOr(a.status, kStatusTreeTimeout);
+      for (int gi = g; gi < g + 2 && gi < ngroups; ++gi) bar_wait(smem_u32(&bars[gi & 1]), (gi >> 1) & 1);
+    }
+    return;
+  }
+  const int drow = tile * 32 + lane;
+  if (drow >= a.ndm) return;
+  const int lw = a.Lp >> 5;
+#pragma unroll
+  for (int j = 0; j < KW; ++j) {
+    const int w = wd * KW + j;
+    const long long aw = aw0 + w;
+    if (w >= a.tile_words || aw - a.word0 >= a.nwords) continue;
+    const int col = static_cast<int>(aw % lw) * 32;
+    st.store(a.plane + static_cast<size_t>(drow) * a.Lp + col, j);
+  }
+}
+
+template <int MODE, int KW, int NPL, int MAXU>
+__global__ void __launch_bounds__(256, 2) k_snd(const __grid_constant__ DirArgs a) {
+  direct_cta<MODE, KW, NPL, MAXU>(a, blockIdx.x, blockIdx.y);
+}
+
+template <int MODE, int KW, int NPL, int MAXU>
+__global__ void __launch_bounds__(256, 2) k_snd_multi(const __grid_constant__ DirMulti m) {
+  const int i = static_cast<int>(blockIdx.x);
+  int lo = 0, hi = m.nbeams - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (m.first[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  const int local = i - m.first[lo];
+  direct_cta<MODE, KW, NPL, MAXU>(m.beam[lo], local % m.ntx[lo], local / m.ntx[lo]);
+}
+
+template <int MODE, int KW, int NPL, int MAXU>
+cudaError_t run_direct(const DirArgs& a, dim3 grid, dim3 block, int smem, cudaStream_t s) {
+  auto kern = k_snd<MODE, KW, NPL, MAXU>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int KW, int NPL, int MAXU>
+cudaError_t run_direct_multi(const DirMulti& m, int ctas, dim3 block, int smem, cudaStream_t s) {
+  auto kern = k_snd_multi<MODE, KW, NPL, MAXU>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ctas, block, smem, s>>>(m);
+  return cudaGetLastError();
+}
+
+struct DGoSingle {
+  const DirArgs* a;
+  dim3 grid, block;
+  int smem;
+  cudaStream_t s;
+  template <int MODE, int KW, int NPL, int MAXU>
+  cudaError_t go() { return run_direct<MODE, KW, NPL, MAXU>(*a, grid, block, smem, s); }
+};
+
+struct DGoMulti {
+  const DirMulti* m;
+  int ctas;
+  dim3 block;
+  int smem;
+  cudaStream_t s;
+  template <int MODE, int KW, int NPL, int MAXU>
+  cudaError_t go() { return run_direct_multi<MODE, KW, NPL, MAXU>(*m, ctas, block, smem, s); }
+};
+
+template <typename F>
+cudaError_t dispatch_direct(int id, F&& f) {
+  switch (id) {
+    case kDirFloat11: return f.template go<kFloat, 4, 11, 0>();
+    case kDirFloat13: return f.template go<kFloat, 4, 13, 0>();
+    case kDirGraded9U1: return f.template go<kGraded, 4, 9, 1>();
+    case kDirGraded9U2: return f.template go<kGraded, 2, 9, 2>();
+    case kDirGraded11U0: return f.template go<kGraded, 4, 11, 0>();
+    case kDirGraded13U0: return f.template go<kGraded, 4, 13, 0>();
+    case kDirBinary4: return f.template go<kBinary, 4, 1, 4>();
+    case kDirBinary8: return f.template go<kBinary, 4, 1, 8>();
+    case kDirBinary12: return f.template go<kBinary, 2, 1, 12>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+void direct_args(const Plan& p, int64_t e_prev, int64_t e_new, DirArgs& a, int* ntx) {
+  const DevPtrs& dp = p.dp;
+  const DirectGeom& g = p.dgeom;
+  a = DirArgs{};
+  a.ring = dp.ring;
+  a.R = p.R;
+  a.nchan = p.nchan;
+  a.ndm = p.ndm;
+  a.B = p.B;
+  a.KL = p.KL;
+  a.KI = p.KI;
+  a.N = p.N;
+  a.nlev = p.nlev;
+  for (int l = 0; l < kMaxLevels; ++l) a.level_nodes[l] = l < p.nlev ? p.level_nodes[l] : 1;
+  a.sub_groups = g.sub_groups;
+  a.sub_lev = g.sub_lev;
+  a.meta = dp.dmeta;
+  a.base4 = dp.dbase;
+  a.cspan = g.cspan;
+  a.tile_words = g.tile_words;
+  a.word0 = e_prev >> 5;
+  a.nwords = static_cast<int>(((e_new - 1) >> 5) - (e_prev >> 5) + 1);
+  a.plane = dp.plane;
+  a.Lp = p.Lp;
+  a.status = dp.counters + kCntStatus;
+  *ntx = (a.nwords + g.tile_words - 1) / g.tile_words;
+}
+
+}  // namespace
+
+cudaError_t launch_tree_direct(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream_t s) {
+  if (e_new <= e_prev) return cudaSuccess;
+  DirArgs a;
+  int ntx = 0;
+  direct_args(p, e_prev, e_new, a, &ntx);
+  const DirectGeom& g = p.dgeom;
+  p.launches += 1;
+  DGoSingle go{&a, dim3(ntx, g.ndm_tiles), dim3(32, g.warps), g.smem_bytes, s};
+  return dispatch_direct(g.inst, go);
+}
+
+cudaError_t launch_tree_direct_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
+                                     cudaStream_t s) {
+  std::vector<int> done(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (done[i]) continue;
+    const int key = plans[i]->dgeom.inst;
+    const int warps = plans[i]->dgeom.warps;
+    DirMulti m{};
+    int smem = 0, ctas = 0;
+    bool counted = false;
+    for (int j = i; j < n && m.nbeams < kMaxDirBeams; ++j) {
+      if (done[j] || plans[j]->dgeom.inst != key || plans[j]->dgeom.warps != warps) continue;
+      done[j] = 1;
+      if (e_new[j] <= e_prev[j]) continue;
+      int ntx = 0;
+      direct_args(*plans[j], e_prev[j], e_new[j], m.beam[m.nbeams], &ntx);
+      m.first[m.nbeams] = ctas;
+      m.ntx[m.nbeams] = ntx;
+      ctas += ntx * plans[j]->dgeom.ndm_tiles;
+      smem = smem > plans[j]->dgeom.smem_bytes ? smem : plans[j]->dgeom.smem_bytes;
+      if (!counted) plans[j]->launches += 1;
+      counted = true;
+      ++m.nbeams;
+    }
+    if (m.nbeams == 0) continue;
+    DGoMulti go{&m, ctas, dim3(32, warps), smem, s};
+    const cudaError_t e = dispatch_direct(key, go);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace snd

@@ -71,7 +71,7 @@ def test_plan_argument_errors(snd):
     assert _plan_rc(snd, f, np.array([1.0, np.inf])) == E["SND_ERR_DM"]
     for k, v, err in [("cluster_size", 8, "SND_ERR_UNSUPPORTED"), ("k_leaf", 0, "SND_ERR_UNSUPPORTED"),
                       ("det_theta", 0.0, "SND_ERR_ARG"), ("closing_size", 4, "SND_ERR_ARG"),
-                      ("max_chunk", 0, "SND_ERR_ARG"), ("flags", 4, "SND_ERR_ARG")]:
+                      ("max_chunk", 0, "SND_ERR_ARG"), ("flags", 8, "SND_ERR_ARG")]:
         assert _plan_rc(snd, f, d, opts=snd.options(0, **{k: v})) == E[err], k
     assert _plan_rc(snd, f, d, mode=1, opts=snd.options(1, graded_cap=256)) == E["SND_ERR_UNSUPPORTED"]
     # unsorted grids, duplicate DMs and a single DM are accepted
