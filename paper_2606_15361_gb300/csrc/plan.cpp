@@ -563,7 +563,10 @@ void choose_direct_geometry(Plan& p) {
     }
   if (omax > 2047) return;
   g.cspan = static_cast<int>(align_up(static_cast<size_t>(4 + omax + g.tile_words), 4));
-  const int64_t smem = (2 * 64 * static_cast<int64_t>(g.cspan) + 64 * 32 + nchan) * 4;
+  // stage 128 channels per round (half the barriers) when they fit two CTAs per SM
+  auto smem_for = [&](int sg) { return (2 * 64 * sg * static_cast<int64_t>(g.cspan) + 64 * sg * 32 + nchan) * 4; };
+  g.sgroups = (nchan % 128 == 0 && smem_for(2) <= 100 * 1024) ? 2 : 1;
+  const int64_t smem = smem_for(g.sgroups);
   if (smem > 200 * 1024) return;
   g.smem_bytes = static_cast<int>(smem);
   p.dmeta.assign(static_cast<size_t>(g.ndm_tiles) * nchan * 32, 0);

@@ -80,6 +80,7 @@ struct DirectGeom {
   int tile_words = 32;   // warps * kw
   int ndm_tiles = 0;     // ceil(ndm / 32)
   int cspan = 0;         // staged ring words per channel (multiple of 4)
+  int sgroups = 1;       // 64-channel adder groups staged per round (1 or 2)
   int smem_bytes = 0;
   int sub_lev = 0;       // graded: the exact level (first level whose nodes may exceed N)
   int sub_groups = 1;    // graded: 64-channel groups per exact-level node

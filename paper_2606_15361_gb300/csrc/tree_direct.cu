@@ -23,11 +23,11 @@
 //    and then KW+1 consecutive window words (a sliding funnel-shift window). The 32 DMs of a
 //    tile read one channel at offsets that differ by less than 32 words, so the reads hit
 //    distinct banks (or broadcast) without conflicts.
-//  * channels are staged 64 at a time: the producer (warp 0) issues one TMA bulk copy
-//    (cp.async.bulk) per channel window of the L2-resident bit ring, plus one for the group's
-//    offset table, onto a double-buffered mbarrier pipeline, so the next group lands while
-//    the current one is added. Waits are bounded; a wait that runs out sets a status bit and
-//    ends the CTA.
+//  * channels are staged 64 or 128 at a time (a round): every warp issues TMA bulk copies
+//    (cp.async.bulk) of its share of the round's channel windows from the L2-resident bit
+//    ring, and warp 0 the round's offset table, onto a double-buffered mbarrier pipeline, so
+//    the next round lands while the current one is added. Waits are bounded; a wait that runs
+//    out sets a status bit and ends the CTA.
 //  * the counter planes stay in registers across groups; the root is turned into int32
 //    samples by a 32x32 bit transpose and written with 128-bit stores.
 
@@ -38,7 +38,7 @@
 namespace snd {
 namespace {
 
-constexpr int kDG = 64;                          // channels per staged group
+constexpr int kDG = 64;                          // channels per adder group (one carry out)
 constexpr long long kDirWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
 struct DirArgs {
@@ -51,6 +51,7 @@ struct DirArgs {
   const uint16_t* meta;    // [ndm_tiles][nchan][32]: (word offset << 5) | bit shift
   const int32_t* base4;    // [ndm_tiles][nchan]: first staged ring word (relative, multiple of 4)
   int cspan;               // staged words per channel (multiple of 4)
+  int sgroups;             // adder groups of kDG channels staged per round (1 or 2)
   int tile_words;          // NW * KW output words per CTA
   long long word0;         // absolute index of the first output word
   int nwords;              // output words of this call
@@ -370,8 +371,9 @@ struct DState<kBinary, KW, NPL, MAXU> {
       }
     }
   }
-  template <typename F>
-  __device__ __forceinline__ void group(const DirArgs& a, int, F& fetch) {
+  // the 16 leaves of a staged group, each the quorum >= KL of its four channel bits
+  template <int KL, typename F>
+  __device__ __forceinline__ void leaves(const DirArgs& a, F& fetch) {
 #pragma unroll 1
     for (int k = 0; k < kDG / 4; ++k) {
       uint32_t x0[KW], x1[KW], x2[KW], x3[KW], v[KW];
@@ -382,17 +384,28 @@ struct DState<kBinary, KW, NPL, MAXU> {
 #pragma unroll
       for (int j = 0; j < KW; ++j) {
         const uint32_t a0 = x0[j], a1 = x1[j], a2 = x2[j], a3 = x3[j];
-        const uint32_t o01 = a0 | a1, o23 = a2 | a3, n01 = a0 & a1, n23 = a2 & a3;
-        uint32_t r;
-        switch (a.KL) {
-          case 1: r = o01 | o23; break;
-          case 2: r = n01 | n23 | (o01 & o23); break;
-          case 3: r = (n01 & o23) | (n23 & o01); break;
-          default: r = n01 & n23; break;
+        if constexpr (KL == 1) {
+          v[j] = a0 | a1 | a2 | a3;
+        } else if constexpr (KL == 2) {
+          const uint32_t m3 = (a0 & a1) | (a2 & (a0 | a1));  // >= 2 of a0..a2
+          v[j] = m3 | ((a0 | a1 | a2) & a3);
+        } else if constexpr (KL == 3) {
+          const uint32_t m3 = (a0 & a1) | (a2 & (a0 | a1));
+          v[j] = (a0 & a1 & a2) | (m3 & a3);
+        } else {
+          v[j] = a0 & a1 & a2 & a3;
         }
-        v[j] = r;
       }
       push(a, v);
+    }
+  }
+  template <typename F>
+  __device__ __forceinline__ void group(const DirArgs& a, int, F& fetch) {
+    switch (a.KL) {
+      case 1: leaves<1>(a, fetch); break;
+      case 2: leaves<2>(a, fetch); break;
+      case 3: leaves<3>(a, fetch); break;
+      default: leaves<4>(a, fetch); break;
     }
   }
   __device__ __forceinline__ void store(int32_t* row, int j) const { store_bits(row, root[j]); }
@@ -405,70 +418,90 @@ __device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
   const int lane = threadIdx.x, wd = threadIdx.y, NW = blockDim.y;
   const int tid = wd * 32 + lane, nthr = 32 * NW;
   const int cspan = a.cspan;
-  const int wbuf = kDG * cspan;                    // window words per buffer
-  uint32_t* win = sm;                              // [2][kDG][cspan]
-  uint16_t* met = reinterpret_cast<uint16_t*>(sm + 2 * wbuf);  // [2][kDG][32]
-  int32_t* sbase = reinterpret_cast<int32_t*>(sm + 2 * wbuf + kDG * 32);  // [nchan]
+  const int SG = kDG * a.sgroups;                  // channels per staging round
+  const int wbuf = SG * cspan;                     // window words per buffer
+  uint32_t* win = sm;                              // [2][SG][cspan]
+  uint16_t* met = reinterpret_cast<uint16_t*>(sm + 2 * wbuf);  // [2][SG][32]
+  int32_t* sbase = reinterpret_cast<int32_t*>(sm + 2 * wbuf + SG * 32);  // [nchan]
   __shared__ __align__(8) unsigned long long bars[2];
-  __shared__ int s_abort;
   const long long aw0 = a.word0 + static_cast<long long>(bx) * a.tile_words;
   const int lead = static_cast<int>(aw0 & 3);
   const long long aw4 = aw0 - lead;
-  const int ngroups = a.nchan / kDG;
+  const int ngroups = a.nchan / SG;
 
-  for (int c = tid; c < a.nchan; c += nthr) sbase[c] = a.base4[static_cast<size_t>(tile) * a.nchan + c];
+  // ring index of every channel's first staged word for this CTA (R is a multiple of 4 and
+  // base4 < R, so one conditional subtract after a single 64-bit modulo per CTA)
+  {
+    const int r0 = static_cast<int>(aw4 % a.R);
+    for (int c = tid; c < a.nchan; c += nthr) {
+      int st0 = r0 + a.base4[static_cast<size_t>(tile) * a.nchan + c];
+      if (st0 >= a.R) st0 -= a.R;
+      sbase[c] = st0;
+    }
+  }
   if (tid == 0) {
-    bar_init(smem_u32(&bars[0]), 1);
-    bar_init(smem_u32(&bars[1]), 1);
-    s_abort = 0;
+    // one arrival per warp: every warp stages its share of a round
+    bar_init(smem_u32(&bars[0]), NW);
+    bar_init(smem_u32(&bars[1]), NW);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  // warp 0 stages group g into buffer b: one bulk copy per channel window, one for the offsets
+  // Stage round g into buffer b. Every warp issues the bulk copies of its share of the SG
+  // channel windows (and warp 0 the round's offset table) after announcing its bytes on the
+  // buffer's mbarrier, so the transaction count never runs ahead of the copies and no warp
+  // carries the whole round's issue cost.
+  const int share = (SG + NW - 1) / NW;
   auto issue = [&](int g, int b) {
-    if (wd != 0) return;
     const uint32_t bar = smem_u32(&bars[b]);
+    const int i0 = wd * share, i1 = min(SG, i0 + share);
     // the buffer's previous contents were read by every warp before the last barrier
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (lane == 0) bar_expect(bar, static_cast<uint32_t>(kDG * cspan * 4 + kDG * 64));
+    if (lane == 0)
+      bar_expect(bar, static_cast<uint32_t>((i1 > i0 ? i1 - i0 : 0) * cspan * 4 + (wd == 0 ? SG * 64 : 0)));
     __syncwarp();
-    for (int i = lane; i < kDG; i += 32) {
-      const int c = g * kDG + i;
-      const int start = static_cast<int>((aw4 + sbase[c]) % a.R);
-      bulk_g2s(smem_u32(win + b * wbuf + i * cspan), a.ring + static_cast<size_t>(c) * 2 * a.R + start,
+    for (int i = i0 + lane; i < i1; i += 32) {
+      const int c = g * SG + i;
+      bulk_g2s(smem_u32(win + b * wbuf + i * cspan), a.ring + static_cast<size_t>(c) * 2 * a.R + sbase[c],
                static_cast<uint32_t>(cspan * 4), bar);
     }
-    if (lane == 0)
-      bulk_g2s(smem_u32(met + b * kDG * 32), a.meta + (static_cast<size_t>(tile) * a.nchan + g * kDG) * 32,
-               kDG * 64, bar);
+    if (wd == 0 && lane == 0)
+      bulk_g2s(smem_u32(met + b * SG * 32), a.meta + (static_cast<size_t>(tile) * a.nchan + g * SG) * 32,
+               static_cast<uint32_t>(SG * 64), bar);
   };
 
   DState<MODE, KW, NPL, MAXU> st;
   st.init(a);
+  // a warp none of whose words is emitted here (the short last tile of a call) only keeps the
+  // CTA's barriers
+  const bool busy = wd * KW < min(a.tile_words, a.nwords - bx * a.tile_words);
   issue(0, 0);
-  int g = 0;
+  int g = 0, abort = 0;
   for (; g < ngroups; ++g) {
     const int b = g & 1;
-    if (g + 1 < ngroups) issue(g + 1, b ^ 1);
-    if (!bar_wait(smem_u32(&bars[b]), (g >> 1) & 1)) s_abort = 1;
-    __syncthreads();
-    if (s_abort) break;
-    const uint16_t* M = met + b * kDG * 32 + lane;
-    const uint32_t* Wb = win + b * wbuf + lead + wd * KW;
-    auto fetch = [&](int ci, uint32_t (&v)[KW]) {
-      const uint32_t m = M[ci * 32];
-      const uint32_t* p = Wb + ci * cspan + (m >> 5);
-      uint32_t x[KW + 1];
+    if (g + 1 < ngroups) issue(g + 1, b ^ 1);  // buffer b ^ 1 was released by the last barrier
+    const bool ok = bar_wait(smem_u32(&bars[b]), (g >> 1) & 1);
+    if (ok && busy) {
+#pragma unroll 1
+      for (int h = 0; h < a.sgroups; ++h) {
+        const uint16_t* M = met + b * SG * 32 + h * kDG * 32 + lane;
+        const uint32_t* Wb = win + b * wbuf + h * kDG * cspan + lead + wd * KW;
+        auto fetch = [&](int ci, uint32_t (&v)[KW]) {
+          const uint32_t m = M[ci * 32];
+          const uint32_t* p = Wb + ci * cspan + (m >> 5);
+          uint32_t x[KW + 1];
 #pragma unroll
-      for (int j = 0; j <= KW; ++j) x[j] = p[j];
+          for (int j = 0; j <= KW; ++j) x[j] = p[j];
 #pragma unroll
-      for (int j = 0; j < KW; ++j) v[j] = __funnelshift_r(x[j], x[j + 1], m);
-    };
-    st.group(a, g, fetch);
-    __syncthreads();
+          for (int j = 0; j < KW; ++j) v[j] = __funnelshift_r(x[j], x[j + 1], m);
+        };
+        st.group(a, g * a.sgroups + h, fetch);
+      }
+    }
+    abort = __syncthreads_or(!ok);
+    if (abort) break;
   }
-  if (s_abort) {
+  if (abort) {
     // a staging wait ran out: report it, and give the copies still in flight (groups g and
     // g + 1) another bounded wait before the CTA's shared memory is released
     if (tid == 0) {
@@ -579,6 +612,7 @@ void direct_args(const Plan& p, int64_t e_prev, int64_t e_new, DirArgs& a, int* 
   a.meta = dp.dmeta;
   a.base4 = dp.dbase;
   a.cspan = g.cspan;
+  a.sgroups = g.sgroups;
   a.tile_words = g.tile_words;
   a.word0 = e_prev >> 5;
   a.nwords = static_cast<int>(((e_new - 1) >> 5) - (e_prev >> 5) + 1);
