@@ -374,7 +374,7 @@ struct DState<kBinary, KW, NPL, MAXU> {
   // the 16 leaves of a staged group, each the quorum >= KL of its four channel bits
   template <int KL, typename F>
   __device__ __forceinline__ void leaves(const DirArgs& a, F& fetch) {
-#pragma unroll 1
+#pragma unroll 4
     for (int k = 0; k < kDG / 4; ++k) {
       uint32_t x0[KW], x1[KW], x2[KW], x3[KW], v[KW];
       fetch(4 * k, x0);
