@@ -435,30 +435,39 @@ def sifter_rate(g, args, dev):
                     "paper_2606_15361_gb300/sifter_train.py"}
 
 
+def multibeam_setup(g, dev, nbeams=48, seed=11, branching=None, steps_tune=2):
+    """The 48 ragged beams of the many-beam row: configs, data (two chunks per beam) and B."""
+    import torch
+    from paper_2606_15361_gb300 import autotune
+    rng = np.random.default_rng(seed)
+    f = synth.channel_freqs(1024)
+    tune = None
+    if branching is None:
+        tune = autotune.autotune(f, synth.NC_DT, synth.dm_grid(2048, 2000.0), g.MODE_FLOAT, 16384,
+                                 branching=(2, 4, 8, 16), cluster=(4,), steps=steps_tune, device=dev)
+        branching = tune["branching"]
+    cfgs = [(int(rng.integers(512, 4097)), float(rng.uniform(500.0, 3000.0)), int(rng.integers(4, 33)) * 1024)
+            for _ in range(nbeams)]
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    data = [[torch.randn((ch, 1024), generator=gen, device=dev).mul_(16).add_(128).round_().clamp_(0, 255)
+             .to(torch.uint8) for _ in range(2)] for _, _, ch in cfgs]
+    fill = max((p_d + ch - 1) // ch for p_d, ch in
+               ((int(2.0 + 4.148808e3 * dmx * (f.min() ** -2 - f.max() ** -2) / synth.NC_DT), ch) for _, dmx, ch in cfgs))
+    return f, cfgs, data, branching, tune, fill
+
+
 def multibeam_rate(g, args, dev, nbeams=48, seed=11):
     """Ragged beams in one step: 48 beams of 1024 channels, each with its own DM grid
     (512-4096 trials to a max DM of 500-3000) and chunk length (4096-32768 samples), float
     mode, branching from the autotuner. Times one step of all beams run plan by plan, as a
     batch (grouped tree launches), and as a batch replayed through a CUDA graph."""
     import torch
-    from paper_2606_15361_gb300 import autotune
-    rng = np.random.default_rng(seed)
-    f = synth.channel_freqs(1024)
-    tune = autotune.autotune(f, synth.NC_DT, synth.dm_grid(2048, 2000.0), g.MODE_FLOAT, 16384,
-                             branching=(2, 4, 8, 16), cluster=(4,), steps=2, device=dev)
-    B = tune["branching"]
-    cfgs = [(int(rng.integers(512, 4097)), float(rng.uniform(500.0, 3000.0)), int(rng.integers(4, 33)) * 1024)
-            for _ in range(nbeams)]
-    gen = torch.Generator(device=dev).manual_seed(seed)
-    data = [[torch.randn((ch, 1024), generator=gen, device=dev).mul_(16).add_(128).round_().clamp_(0, 255)
-             .to(torch.uint8) for _ in range(2)] for _, _, ch in cfgs]
+    f, cfgs, data, B, tune, fill = multibeam_setup(g, dev, nbeams, seed)
 
     def make():
         return [g.Plan(f, synth.NC_DT, synth.dm_grid(nd, dmx), B, g.MODE_FLOAT,
                        g.options(g.MODE_FLOAT, max_chunk=ch), device=dev) for nd, dmx, ch in cfgs]
 
-    fill = max((p_d + ch - 1) // ch for p_d, ch in
-               ((int(2.0 + 4.148808e3 * dmx * (f.min() ** -2 - f.max() ** -2) / synth.NC_DT), ch) for _, dmx, ch in cfgs))
     steps = max(2, min(args.steps, 5))
     out = {"beams": nbeams, "autotune": {"branching": B, "trials": [(t["branching"], round(t["ms_per_chunk"], 3))
                                                                   for t in tune["trials"]]}}
@@ -697,6 +706,17 @@ def drive(mode_name: str, nchunks: int, branching: int):
     of device memory, small enough for a full profiler capture)."""
     import torch
     import paper_2606_15361_gb300 as g
+    if mode_name == "batch48":
+        dev = torch.device("cuda", 0)
+        f, cfgs, data, B, _, fill = multibeam_setup(g, dev, branching=branching)
+        plans = [g.Plan(f, synth.NC_DT, synth.dm_grid(nd, dmx), B, g.MODE_FLOAT,
+                        g.options(g.MODE_FLOAT, max_chunk=ch), device=dev) for nd, dmx, ch in cfgs]
+        batch = g.Batch(plans)
+        for k in range(fill + nchunks):
+            batch.execute([data[i][k % 2] for i in range(len(plans))])
+        torch.cuda.synchronize()
+        print(json.dumps({"drive": mode_name, "steps": fill + nchunks, "branching": B}))
+        return
     if mode_name == "sifter":
         gen = torch.Generator(device="cuda").manual_seed(7)
         x = torch.randn((512, 64, 256), generator=gen, device="cuda")
@@ -743,7 +763,7 @@ def main():
                     help="headline pass with the three modes in sequence on one stream (default: own streams)")
     ap.add_argument("--main-only", action="store_true",
                     help="only the headline workload: no multi-rate, labelled-payload, sifter or multi-beam parts")
-    ap.add_argument("--drive", choices=[m for m, _ in MODES] + ["zfloat", "zfloat16", "sifter"],
+    ap.add_argument("--drive", choices=[m for m, _ in MODES] + ["zfloat", "zfloat16", "sifter", "batch48"],
                     help="profiling driver: one plan (or the sifter), no timing")
     ap.add_argument("--chunks", type=int, default=3)
     ap.add_argument("--branching", type=int, default=BRANCHING)

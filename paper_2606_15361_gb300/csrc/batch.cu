@@ -1,12 +1,16 @@
 // Many beams per step: every beam is its own plan (its own DM grid, chunk length, options
 // and workspace), and one call advances all of them by one chunk each.
 //
-// The tree, the dominant stage, runs as few launches as possible: beams whose plans share
-// a kernel instantiation and block shape go into one k_tree_multi launch, whose CTAs are
-// spread over the beams by a prefix of their tile counts (the per-beam arguments travel by
-// value in the launch's parameter block). The encoders, and then the matched filter and
-// candidate stages, run per beam spread over four side streams forked from and joined back
-// to the caller's stream around the tree launches. With graphs enabled the whole step is
+// Every stage of a step runs for all beams at once, in a fixed handful of launches:
+//  * the encoders: three launches (histogram, levels, pack) whose CTAs are spread over the
+//    beams by a prefix of their CTA counts;
+//  * the trees: one persistent launch per kernel instantiation, whose resident CTAs take
+//    (beam, DM tile, time tile) work items from a device counter until none is left;
+//  * the matched filters: one launch, one CTA per (beam, DM row);
+//  * the candidate stages: one cooperative launch whose stages are separated by bounded
+//    grid-wide barriers.
+// The per-beam arguments travel by value in each launch's parameter block. With graphs
+// enabled the whole step is
 // captured on a private stream and launched as one CUDA graph on the caller's stream; the
 // next step's capture updates the instantiated graph in place (cudaGraphExecUpdate)
 // whenever the topology is unchanged, so a steady stream of chunks re-uses one executable
@@ -23,57 +27,17 @@ using snd::Plan;
 
 namespace snd {
 
-int ForkJoin::init(int n) {
-  if (!streams.empty()) return SND_OK;
-  for (int i = 0; i < n; ++i) {
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SND_ERR_CUDA;
-    streams.push_back(st);
-  }
-  for (int i = 0; i < 2 * n; ++i) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SND_ERR_CUDA;
-    events.push_back(e);
-  }
-  return SND_OK;
-}
-
-cudaError_t ForkJoin::fork(cudaStream_t main) {
-  const size_t n = streams.size();
-  cudaError_t e = cudaEventRecord(events[0], main);
-  for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(streams[i], events[0], 0);
-  return e;
-}
-
-cudaError_t ForkJoin::join(cudaStream_t main) {
-  const size_t n = streams.size();
-  cudaError_t e = cudaSuccess;
-  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
-    e = cudaEventRecord(events[n + i], streams[i]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(main, events[n + i], 0);
-  }
-  return e;
-}
-
-ForkJoin::~ForkJoin() {
-  for (cudaEvent_t e : events) cudaEventDestroy(e);
-  for (cudaStream_t st : streams) cudaStreamDestroy(st);
-}
-
 int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
-                  cudaStream_t owner, ForkJoin* fj) {
+                  cudaStream_t owner) {
   std::vector<ChunkPos> pos(n);
-  std::vector<const Plan*> tp;
+  std::vector<const Plan*> cp(plans, plans + n);
+  std::vector<const Plan*> tp, post;
+  std::vector<ChunkPos> ppos;
   std::vector<int64_t> ep, en;
-  const int ns = fj ? static_cast<int>(fj->streams.size()) : 0;
-  auto side = [&](int i) { return ns ? fj->streams[i % ns] : s; };
-  if (ns && fj->fork(s) != cudaSuccess) return SND_ERR_CUDA;
-  for (int i = 0; i < n; ++i) {
-    Plan& p = *plans[i];
-    pos[i] = chunk_pos(p, nsamp[i]);
-    if (launch_encode(p, d_chunks[i], nsamp[i], side(i)) != cudaSuccess) return SND_ERR_CUDA;
-  }
-  if (ns && fj->join(s) != cudaSuccess) return SND_ERR_CUDA;
+  for (int i = 0; i < n; ++i) pos[i] = chunk_pos(*plans[i], nsamp[i]);
+  // 1. every encoder (three launches for all bit-ring plans; each clears its block counters)
+  if (launch_encode_batch(cp.data(), d_chunks, nsamp, n, s) != cudaSuccess) return SND_ERR_CUDA;
+  // 2. the trees: one persistent launch per kernel instantiation
   for (int i = 0; i < n; ++i) {
     Plan& p = *plans[i];
     if (pos[i].e_new <= pos[i].e_prev) continue;
@@ -89,14 +53,17 @@ int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, con
   }
   if (!tp.empty() && launch_tree_batch(tp.data(), ep.data(), en.data(), static_cast<int>(tp.size()), s) != cudaSuccess)
     return SND_ERR_CUDA;
-  if (ns && fj->fork(s) != cudaSuccess) return SND_ERR_CUDA;
+  // 3. every matched filter in one launch, 4. every candidate stage in one cooperative launch
   for (int i = 0; i < n; ++i) {
-    Plan& p = *plans[i];
-    if (p.mode == SND_MODE_ZFLOAT) continue;
-    if (chunk_post(p, pos[i], nullptr, side(i), [](int, auto&& f) { return f(); }) != cudaSuccess)
-      return SND_ERR_CUDA;
+    if (plans[i]->mode == SND_MODE_ZFLOAT) continue;
+    post.push_back(plans[i]);
+    ppos.push_back(pos[i]);
   }
-  if (ns && fj->join(s) != cudaSuccess) return SND_ERR_CUDA;
+  if (!post.empty()) {
+    const int np = static_cast<int>(post.size());
+    if (launch_mf_batch(post.data(), ppos.data(), np, s) != cudaSuccess) return SND_ERR_CUDA;
+    if (launch_candidates_batch(post.data(), ppos.data(), np, s) != cudaSuccess) return SND_ERR_CUDA;
+  }
   for (int i = 0; i < n; ++i) chunk_commit(*plans[i], pos[i], nsamp[i], owner);
   return SND_OK;
 }
@@ -146,7 +113,6 @@ struct Batch {
   std::vector<Plan*> plans;
   bool graph = false;
   snd::GraphRunner runner;
-  snd::ForkJoin fj;  // side streams for the per-beam stages
   int sticky = 0;
 };
 
@@ -199,12 +165,10 @@ extern "C" int snd_batch_execute(snd_batch_t h, const uint8_t* const* d_chunks, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Plan* const* plans = b.plans.data();
   const int n = static_cast<int>(b.plans.size());
-  if (n > 1 && b.fj.init(std::min(n, 4)) != SND_OK) return fail(b, SND_ERR_CUDA);
-  snd::ForkJoin* fj = n > 1 ? &b.fj : nullptr;
   const int rc = b.graph ? b.runner.run(s, [&](cudaStream_t cs) {
-    return snd::enqueue_plans(plans, n, d_chunks, nsamp, cs, s, fj);
+    return snd::enqueue_plans(plans, n, d_chunks, nsamp, cs, s);
   })
-                         : snd::enqueue_plans(plans, n, d_chunks, nsamp, s, s, fj);
+                         : snd::enqueue_plans(plans, n, d_chunks, nsamp, s, s);
   return rc ? fail(b, rc) : SND_OK;
 }
 

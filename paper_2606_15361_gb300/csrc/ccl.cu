@@ -15,6 +15,8 @@
 // Every data-dependent loop is bounded; a bound that is hit sets a status bit instead of
 // spinning.
 
+#include <vector>
+
 #include "snd_internal.h"
 
 namespace snd {
@@ -71,13 +73,12 @@ __global__ void k_close_v(const uint32_t* __restrict__ in, uint32_t* __restrict_
 // pass (and read as 1 by the horizontal erosion).
 constexpr int kCloseTR = 32, kCloseTQ = 32, kCloseNQ = kCloseTQ + 4, kCloseThreads = 256;
 
-__global__ void __launch_bounds__(kCloseThreads) k_close(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                                         int ndm, int mw, int nb, int r) {
-  extern __shared__ uint32_t csm[];
+__device__ __forceinline__ void close_tile(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int ndm, int mw,
+                                           int nb, int r, int bx, int by, uint32_t* csm) {
   const int NR = kCloseTR + 4 * r;
   uint32_t* A = csm;                 // [NR][kCloseNQ]: input, then the dilated tile
   uint32_t* Bv = csm + NR * kCloseNQ;  // [NR][kCloseNQ]: horizontal pass results
-  const int d0 = blockIdx.y * kCloseTR, q0 = blockIdx.x * kCloseTQ;
+  const int d0 = by * kCloseTR, q0 = bx * kCloseTQ;
   const int R0 = d0 - 2 * r, W0 = q0 - 2;
   const int nbw = (nb + 31) >> 5;
   const uint32_t tailvalid = (nb & 31) ? ((1u << (nb & 31)) - 1u) : 0xFFFFFFFFu;
@@ -154,10 +155,15 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const uint32_t* __restr
   }
 }
 
+__global__ void __launch_bounds__(kCloseThreads) k_close(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                         int ndm, int mw, int nb, int r) {
+  extern __shared__ uint32_t csm[];
+  close_tile(in, out, ndm, mw, nb, r, blockIdx.x, blockIdx.y, csm);
+}
+
 // One warp per row: number of runs (run starts) of the closed mask.
-__global__ void k_run_count(const uint32_t* __restrict__ m, int ndm, int mw, int nb, int32_t* row_runs) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void run_count_row(const uint32_t* __restrict__ m, int ndm, int mw, int nb,
+                                              int32_t* row_runs, const int warp, const int lane) {
   if (warp >= ndm) return;
   const int nbw = (nb + 31) >> 5;
   const uint32_t* row = m + static_cast<size_t>(warp) * mw;
@@ -173,11 +179,16 @@ __global__ void k_run_count(const uint32_t* __restrict__ m, int ndm, int mw, int
   if (lane == 0) row_runs[warp] = cnt;
 }
 
-// Single CTA: exclusive scan of the per-row run counts; total -> counters[kCntRuns].
-__global__ void k_scan_rows(int32_t* row_runs, int ndm, uint32_t* counters, int run_cap) {
-  __shared__ int part[1024];
+__global__ void k_run_count(const uint32_t* __restrict__ m, int ndm, int mw, int nb, int32_t* row_runs) {
+  run_count_row(m, ndm, mw, nb, row_runs, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
+}
+
+// One CTA of NT threads: exclusive scan of the per-row run counts; total -> counters[kCntRuns].
+template <int NT>
+__device__ __forceinline__ void scan_rows_cta(int32_t* row_runs, int ndm, uint32_t* counters, int run_cap) {
+  __shared__ int part[64];
   const int tid = threadIdx.x;
-  const int per = (ndm + 1023) / 1024;
+  const int per = (ndm + NT - 1) / NT;
   const int lo = min(ndm, tid * per), hi = min(ndm, lo + per);
   int s = 0;
   for (int i = lo; i < hi; ++i) s += row_runs[i];
@@ -192,7 +203,7 @@ __global__ void k_scan_rows(int32_t* row_runs, int ndm, uint32_t* counters, int 
   if (lane == 31) part[wid] = incl;
   __syncthreads();
   if (wid == 0) {
-    const int t = part[lane];
+    const int t = lane < NT / 32 ? part[lane] : 0;
     int wincl = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -215,12 +226,16 @@ __global__ void k_scan_rows(int32_t* row_runs, int ndm, uint32_t* counters, int 
   }
 }
 
+__global__ void k_scan_rows(int32_t* row_runs, int ndm, uint32_t* counters, int run_cap) {
+  scan_rows_cta<1024>(row_runs, ndm, counters, run_cap);
+}
+
 // One warp per row: write runs [start, end) in order, initialise union-find state.
-__global__ void k_run_write(const uint32_t* __restrict__ m, int ndm, int mw, int nb, const int32_t* row_runs,
-                            int32_t* run_start, int32_t* run_end, int32_t* run_row, int32_t* parent,
-                            int32_t* npix, unsigned long long* peak, int32_t* pwidth, int run_cap) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void run_write_row(const uint32_t* __restrict__ m, int ndm, int mw, int nb,
+                                              const int32_t* row_runs, int32_t* run_start, int32_t* run_end,
+                                              int32_t* run_row, int32_t* parent, int32_t* npix,
+                                              unsigned long long* peak, int32_t* pwidth, int run_cap, const int warp,
+                                              const int lane) {
   if (warp >= ndm) return;
   if (row_runs[ndm] > run_cap) return;
   const int nbw = (nb + 31) >> 5;
@@ -266,6 +281,13 @@ __global__ void k_run_write(const uint32_t* __restrict__ m, int ndm, int mw, int
   }
 }
 
+__global__ void k_run_write(const uint32_t* __restrict__ m, int ndm, int mw, int nb, const int32_t* row_runs,
+                            int32_t* run_start, int32_t* run_end, int32_t* run_row, int32_t* parent,
+                            int32_t* npix, unsigned long long* peak, int32_t* pwidth, int run_cap) {
+  run_write_row(m, ndm, mw, nb, row_runs, run_start, run_end, run_row, parent, npix, peak, pwidth, run_cap,
+                (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
+}
+
 __device__ __forceinline__ int find_root(const int32_t* parent, int x, uint32_t* status) {
   const volatile int32_t* vp = parent;
   for (int it = 0; it < (1 << 20); ++it) {
@@ -297,10 +319,13 @@ __device__ __forceinline__ int runs_total(const int32_t* row_runs, int ndm, int 
   return n > run_cap ? -1 : n;
 }
 
-__global__ void k_union(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
-                        const int32_t* run_end, const int32_t* run_row, int32_t* parent, uint32_t* counters) {
+// The remaining stages loop over their items i = i0, i0 + stride, ... (a grid-stride loop in
+// the single-plan kernels, a loop over the whole cooperative grid in the many-beam kernel).
+__device__ __forceinline__ void union_items(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
+                                            const int32_t* run_end, const int32_t* run_row, int32_t* parent,
+                                            uint32_t* counters, int i0, int stride) {
   const int n = runs_total(row_runs, ndm, run_cap);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = i0; i < n; i += stride) {
     const int d = run_row[i];
     if (d == 0) continue;
     const int s = run_start[i], e = run_end[i];
@@ -315,14 +340,27 @@ __global__ void k_union(const int32_t* row_runs, int ndm, int run_cap, const int
   }
 }
 
-__global__ void k_flatten(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
-                          const int32_t* run_end, int32_t* parent, int32_t* npix, uint32_t* counters) {
+__global__ void k_union(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
+                        const int32_t* run_end, const int32_t* run_row, int32_t* parent, uint32_t* counters) {
+  union_items(row_runs, ndm, run_cap, run_start, run_end, run_row, parent, counters,
+              blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__device__ __forceinline__ void flatten_items(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
+                                              const int32_t* run_end, int32_t* parent, int32_t* npix,
+                                              uint32_t* counters, int i0, int stride) {
   const int n = runs_total(row_runs, ndm, run_cap);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = i0; i < n; i += stride) {
     const int r = find_root(parent, i, &counters[kCntStatus]);
     parent[i] = r;
     atomicAdd(&npix[r], run_end[i] - run_start[i]);
   }
+}
+
+__global__ void k_flatten(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
+                          const int32_t* run_end, int32_t* parent, int32_t* npix, uint32_t* counters) {
+  flatten_items(row_runs, ndm, run_cap, run_start, run_end, parent, npix, counters,
+                blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Run of row d that contains column t, or -1.
@@ -338,12 +376,13 @@ __device__ __forceinline__ int run_of(const int32_t* row_runs, const int32_t* ru
   return a;
 }
 
-__global__ void k_peak(const MfCell* cells, uint32_t* counters, int cell_cap, int nb, const int32_t* row_runs,
-                       int ndm, int run_cap, const int32_t* run_start, const int32_t* run_end,
-                       const int32_t* parent, unsigned long long* peak, int32_t* pwidth, int pass) {
+__device__ __forceinline__ void peak_items(const MfCell* cells, uint32_t* counters, int cell_cap, int nb,
+                                           const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
+                                           const int32_t* run_end, const int32_t* parent, unsigned long long* peak,
+                                           int32_t* pwidth, int pass, int i0, int stride) {
   if (runs_total(row_runs, ndm, run_cap) < 0) return;
   const int nc = min(static_cast<int>(counters[kCntCells]), cell_cap);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+  for (int i = i0; i < nc; i += stride) {
     const MfCell c = cells[i];
     const int d = static_cast<int>(c.cell / static_cast<uint32_t>(nb));
     const int t = static_cast<int>(c.cell - static_cast<uint32_t>(d) * static_cast<uint32_t>(nb));
@@ -363,12 +402,20 @@ __global__ void k_peak(const MfCell* cells, uint32_t* counters, int cell_cap, in
   }
 }
 
-__global__ void k_emit(const int32_t* row_runs, int ndm, int run_cap, const int32_t* parent, const int32_t* npix,
-                       const unsigned long long* peak, const int32_t* pwidth, int nb, int n_min,
-                       long long f_prev, const float* dm_f32, snd_candidate_t* bcand, int cand_cap,
-                       uint32_t* counters) {
+__global__ void k_peak(const MfCell* cells, uint32_t* counters, int cell_cap, int nb, const int32_t* row_runs,
+                       int ndm, int run_cap, const int32_t* run_start, const int32_t* run_end,
+                       const int32_t* parent, unsigned long long* peak, int32_t* pwidth, int pass) {
+  peak_items(cells, counters, cell_cap, nb, row_runs, ndm, run_cap, run_start, run_end, parent, peak, pwidth, pass,
+             blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__device__ __forceinline__ void emit_items(const int32_t* row_runs, int ndm, int run_cap, const int32_t* parent,
+                                           const int32_t* npix, const unsigned long long* peak, const int32_t* pwidth,
+                                           int nb, int n_min, long long f_prev, const float* dm_f32,
+                                           snd_candidate_t* bcand, int cand_cap, uint32_t* counters, int i0,
+                                           int stride) {
   const int n = runs_total(row_runs, ndm, run_cap);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = i0; i < n; i += stride) {
     if (parent[i] != i || npix[i] < n_min || peak[i] == 0ull) continue;
     const uint32_t cell = 0xFFFFFFFFu - static_cast<uint32_t>(peak[i] & 0xFFFFFFFFull);
     const int d = static_cast<int>(cell / static_cast<uint32_t>(nb));
@@ -390,13 +437,21 @@ __global__ void k_emit(const int32_t* row_runs, int ndm, int run_cap, const int3
   }
 }
 
+__global__ void k_emit(const int32_t* row_runs, int ndm, int run_cap, const int32_t* parent, const int32_t* npix,
+                       const unsigned long long* peak, const int32_t* pwidth, int nb, int n_min,
+                       long long f_prev, const float* dm_f32, snd_candidate_t* bcand, int cand_cap,
+                       uint32_t* counters) {
+  emit_items(row_runs, ndm, run_cap, parent, npix, peak, pwidth, nb, n_min, f_prev, dm_f32, bcand, cand_cap, counters,
+             blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 // Rank every block candidate by (t, dm_index) (keys are distinct: one peak pixel per island)
 // and place it after the candidates already held.
-__global__ void k_rank_append(const snd_candidate_t* bcand, snd_candidate_t* cand, uint32_t* counters,
-                              int cand_cap) {
+__device__ __forceinline__ void rank_items(const snd_candidate_t* bcand, snd_candidate_t* cand, uint32_t* counters,
+                                           int cand_cap, int i0, int stride) {
   const int n = min(static_cast<int>(counters[kCntBlockCands]), cand_cap);
   const int base = static_cast<int>(counters[kCntCands]);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = i0; i < n; i += stride) {
     const snd_candidate_t ci = bcand[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
@@ -412,10 +467,164 @@ __global__ void k_rank_append(const snd_candidate_t* bcand, snd_candidate_t* can
   }
 }
 
-__global__ void k_bump(uint32_t* counters, int cand_cap) {
+__global__ void k_rank_append(const snd_candidate_t* bcand, snd_candidate_t* cand, uint32_t* counters,
+                              int cand_cap) {
+  rank_items(bcand, cand, counters, cand_cap, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__device__ __forceinline__ void bump(uint32_t* counters, int cand_cap) {
   const int n = min(static_cast<int>(counters[kCntBlockCands]), cand_cap);
   const int tot = static_cast<int>(counters[kCntCands]) + n;
   counters[kCntCands] = static_cast<uint32_t>(min(tot, cand_cap));
+}
+
+__global__ void k_bump(uint32_t* counters, int cand_cap) { bump(counters, cand_cap); }
+
+// ---------------------------------------------------------------------------------------
+// Candidate stage of many plans in ONE cooperative launch: the stages above run one after
+// another over all beams' blocks, separated by grid-wide barriers (every CTA is resident, as a
+// cooperative launch guarantees). Each barrier is a counter + generation pair in device
+// memory; its wait is bounded, and a wait that runs out marks every beam's status word and
+// ends the kernel.
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxCandBeams = 64;
+constexpr long long kGridWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+struct CandBeam {
+  const uint32_t* mask;
+  uint32_t* mask3;
+  int ndm, mw, nb, r, run_cap, cell_cap, cand_cap, n_min;
+  int32_t *row_runs, *run_start, *run_end, *run_row, *parent, *npix, *pwidth;
+  unsigned long long* peak;
+  const MfCell* cells;
+  long long f_prev;
+  const float* dm_f32;
+  snd_candidate_t *bcand, *cand;
+  uint32_t* counters;
+};
+
+struct CandMulti {
+  int nbeams;
+  int first_close[kMaxCandBeams];  // closing tiles of the beams before
+  int first_rows[kMaxCandBeams];   // 8-row groups of the beams before
+  int total_close, total_rows;
+  unsigned int* gbar;              // [2]: arrivals, generation
+  CandBeam beam[kMaxCandBeams];
+};
+
+__device__ __forceinline__ int cbeam_of(const int* first, int n, int i) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ bool grid_barrier(const CandMulti& m) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = m.gbar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(m.gbar, 1u) == gridDim.x - 1) {
+      m.gbar[0] = 0;
+      __threadfence();
+      atomicAdd(m.gbar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > kGridWaitCycles) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (!ok)
+      for (int b = 0; b < m.nbeams; ++b) atomicOr(&m.beam[b].counters[kCntStatus], kStatusGridTimeout);
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(256) k_cand_multi(const __grid_constant__ CandMulti m) {
+  extern __shared__ uint32_t csm[];
+  const int nblk = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int gtid = bid * 256 + tid, gthreads = nblk * 256;
+  // 1. closing (a plain copy for a 1 x 1 element)
+  for (int v = bid; v < m.total_close; v += nblk) {
+    const int b = cbeam_of(m.first_close, m.nbeams, v);
+    const CandBeam& e = m.beam[b];
+    const int local = v - m.first_close[b];
+    const int nbw = (e.nb + 31) >> 5;
+    const int tx = (nbw + kCloseTQ - 1) / kCloseTQ;
+    const int bx = local % tx, by = local / tx;
+    if (e.r > 0) {
+      close_tile(e.mask, e.mask3, e.ndm, e.mw, e.nb, e.r, bx, by, csm);
+    } else {
+      for (int k = tid; k < kCloseTR * kCloseTQ; k += 256) {
+        const int d = by * kCloseTR + k / kCloseTQ, q = bx * kCloseTQ + k % kCloseTQ;
+        if (d < e.ndm && q < nbw) e.mask3[static_cast<size_t>(d) * e.mw + q] = e.mask[static_cast<size_t>(d) * e.mw + q];
+      }
+    }
+    __syncthreads();
+  }
+  if (!grid_barrier(m)) return;
+  // 2. runs per row
+  for (int v = bid; v < m.total_rows; v += nblk) {
+    const int b = cbeam_of(m.first_rows, m.nbeams, v);
+    const CandBeam& e = m.beam[b];
+    run_count_row(e.mask3, e.ndm, e.mw, e.nb, e.row_runs, (v - m.first_rows[b]) * 8 + warp, lane);
+  }
+  if (!grid_barrier(m)) return;
+  // 3. scan of the run counts, one CTA per beam
+  for (int b = bid; b < m.nbeams; b += nblk) {
+    const CandBeam& e = m.beam[b];
+    scan_rows_cta<256>(e.row_runs, e.ndm, e.counters, e.run_cap);
+    __syncthreads();
+  }
+  if (!grid_barrier(m)) return;
+  // 4. runs and union-find state
+  for (int v = bid; v < m.total_rows; v += nblk) {
+    const int b = cbeam_of(m.first_rows, m.nbeams, v);
+    const CandBeam& e = m.beam[b];
+    run_write_row(e.mask3, e.ndm, e.mw, e.nb, e.row_runs, e.run_start, e.run_end, e.run_row, e.parent, e.npix,
+                  e.peak, e.pwidth, e.run_cap, (v - m.first_rows[b]) * 8 + warp, lane);
+  }
+  if (!grid_barrier(m)) return;
+  // 5. - 10. over each beam's runs, cells and block candidates
+  for (int b = 0; b < m.nbeams; ++b) {
+    const CandBeam& e = m.beam[b];
+    union_items(e.row_runs, e.ndm, e.run_cap, e.run_start, e.run_end, e.run_row, e.parent, e.counters, gtid, gthreads);
+  }
+  if (!grid_barrier(m)) return;
+  for (int b = 0; b < m.nbeams; ++b) {
+    const CandBeam& e = m.beam[b];
+    flatten_items(e.row_runs, e.ndm, e.run_cap, e.run_start, e.run_end, e.parent, e.npix, e.counters, gtid, gthreads);
+  }
+  if (!grid_barrier(m)) return;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int b = 0; b < m.nbeams; ++b) {
+      const CandBeam& e = m.beam[b];
+      peak_items(e.cells, e.counters, e.cell_cap, e.nb, e.row_runs, e.ndm, e.run_cap, e.run_start, e.run_end,
+                 e.parent, e.peak, e.pwidth, pass, gtid, gthreads);
+    }
+    if (!grid_barrier(m)) return;
+  }
+  for (int b = 0; b < m.nbeams; ++b) {
+    const CandBeam& e = m.beam[b];
+    emit_items(e.row_runs, e.ndm, e.run_cap, e.parent, e.npix, e.peak, e.pwidth, e.nb, e.n_min, e.f_prev, e.dm_f32,
+               e.bcand, e.cand_cap, e.counters, gtid, gthreads);
+  }
+  if (!grid_barrier(m)) return;
+  for (int b = 0; b < m.nbeams; ++b) {
+    const CandBeam& e = m.beam[b];
+    rank_items(e.bcand, e.cand, e.counters, e.cand_cap, gtid, gthreads);
+  }
+  if (!grid_barrier(m)) return;
+  for (int b = gtid; b < m.nbeams; b += gthreads) bump(m.beam[b].counters, m.beam[b].cand_cap);
 }
 
 }  // namespace
@@ -461,6 +670,82 @@ cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_
   k_bump<<<1, 1, 0, s>>>(dp.counters, p.cand_cap);
   p.launches += 11;
   return cudaGetLastError();
+}
+
+// The candidate stages of several plans' blocks in one cooperative launch (plans on the
+// reference closing path keep their own launches). The grid barrier's two words are slots
+// kCntGridBar.. of the first plan's counters; the arrival count is cleared before the launch.
+cudaError_t launch_candidates_batch(const Plan* const* plans, const ChunkPos* pos, int n, cudaStream_t s) {
+  std::vector<int> batch;
+  for (int i = 0; i < n; ++i) {
+    if (pos[i].nb <= 0) continue;
+    if (plans[i]->flags & kFlagReferenceTree) {
+      const cudaError_t e = launch_candidates(*plans[i], pos[i].f_prev, pos[i].nb, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      batch.push_back(i);
+    }
+  }
+  for (size_t i0 = 0; i0 < batch.size(); i0 += kMaxCandBeams) {
+    CandMulti m{};
+    int rmax = 0;
+    for (size_t k = i0; k < batch.size() && m.nbeams < kMaxCandBeams; ++k) {
+      const Plan& p = *plans[batch[k]];
+      const ChunkPos& c = pos[batch[k]];
+      const DevPtrs& dp = p.dp;
+      CandBeam& e = m.beam[m.nbeams];
+      e.mask = dp.mask;
+      e.mask3 = dp.mask3;
+      e.ndm = p.ndm;
+      e.mw = p.mw;
+      e.nb = c.nb;
+      e.r = p.closing / 2;
+      e.run_cap = p.run_cap;
+      e.cell_cap = p.cell_cap;
+      e.cand_cap = p.cand_cap;
+      e.n_min = p.n_min;
+      e.row_runs = dp.row_runs;
+      e.run_start = dp.run_start;
+      e.run_end = dp.run_end;
+      e.run_row = dp.run_row;
+      e.parent = dp.parent;
+      e.npix = dp.npix;
+      e.pwidth = dp.pwidth;
+      e.peak = dp.peak;
+      e.cells = dp.cells;
+      e.f_prev = c.f_prev;
+      e.dm_f32 = dp.dm_f32;
+      e.bcand = dp.bcand;
+      e.cand = dp.cand;
+      e.counters = dp.counters;
+      const int nbw = (c.nb + 31) / 32;
+      m.first_close[m.nbeams] = m.total_close;
+      m.first_rows[m.nbeams] = m.total_rows;
+      m.total_close += ((nbw + kCloseTQ - 1) / kCloseTQ) * ((p.ndm + kCloseTR - 1) / kCloseTR);
+      m.total_rows += (p.ndm + 7) / 8;
+      rmax = rmax > e.r ? rmax : e.r;
+      ++m.nbeams;
+    }
+    const Plan& owner = *plans[batch[i0]];
+    m.gbar = owner.dp.counters + kCntGridBar;
+    const int smem = 2 * (kCloseTR + 4 * rmax) * kCloseNQ * static_cast<int>(sizeof(uint32_t));
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cand_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_multi, 256, smem);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.gbar, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM at most 2: the stages are latency bound, and fewer CTAs make cheaper barriers
+    const int grid = nsm * (per_sm < 2 ? per_sm : 2);
+    void* args[] = {&m};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_cand_multi), dim3(grid), dim3(256), args,
+                                    static_cast<size_t>(smem), s);
+    owner.launches += 1;
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace snd

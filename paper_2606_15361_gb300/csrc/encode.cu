@@ -21,15 +21,16 @@ namespace {
 
 constexpr int kHistRowsPerBlock = 2048;
 
-__global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
-                                              uint32_t* __restrict__ hist) {
+// CTA (bx, by) of the histogram: 32 channels x kHistRowsPerBlock samples
+__device__ __forceinline__ void hist_cta(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
+                                         uint32_t* __restrict__ hist, int bx, int by) {
   __shared__ uint32_t h[256][32];
   const int lane = threadIdx.x, wy = threadIdx.y;
   const int tid = wy * 32 + lane;
   for (int i = tid; i < 256 * 32; i += 256) (&h[0][0])[i] = 0;
   __syncthreads();
-  const int c = blockIdx.x * 32 + lane;
-  const int r0 = blockIdx.y * kHistRowsPerBlock;
+  const int c = bx * 32 + lane;
+  const int r0 = by * kHistRowsPerBlock;
   const int r1 = min(nsamp, r0 + kHistRowsPerBlock);
   if (c < nchan) {
     for (int r = r0 + wy; r < r1; r += 8) {
@@ -40,10 +41,15 @@ __global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk,
   __syncthreads();
   for (int i = tid; i < 256 * 32; i += 256) {
     const int v = i >> 5, l = i & 31;
-    const int cc = blockIdx.x * 32 + l;
+    const int cc = bx * 32 + l;
     const uint32_t n = h[v][l];
     if (cc < nchan && n) atomicAdd(&hist[static_cast<size_t>(cc) * 256 + v], n);
   }
+}
+
+__global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
+                                              uint32_t* __restrict__ hist) {
+  hist_cta(chunk, nsamp, nchan, hist, blockIdx.x, blockIdx.y);
 }
 
 // One warp per channel; lane l holds bins l, l+32, ..., l+224. Integer sums are exact; the
@@ -52,10 +58,9 @@ __global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk,
 // clip bounds and the level are exact integer decisions.
 // With ztab set (labelled payload), every lane also writes the payload of its 8 values,
 // z = (v - mu)/sigma in FP64 for v >= u (0 below), rounded once to FP16 (zfp16) or FP32.
-__global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
-                                                int32_t* __restrict__ levels, void* __restrict__ ztab, int zfp16) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void levels_warp(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
+                                            int32_t* __restrict__ levels, void* __restrict__ ztab, int zfp16,
+                                            const int c, const int lane) {
   if (c >= nchan) return;
   uint32_t* h = hist + static_cast<size_t>(c) * 256;
   long long n[8];
@@ -134,6 +139,12 @@ __global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int
   }
 }
 
+__global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
+                                                int32_t* __restrict__ levels, void* __restrict__ ztab, int zfp16) {
+  levels_warp(hist, nchan, nsamp, theta, levels, ztab, zfp16, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+              threadIdx.x & 31);
+}
+
 // Labelled payload into the ring: zring[c][(t0 + r) mod Rz] = ztab[c][P_c(r)]. A CTA
 // transposes 32 channels x 256 samples through shared memory, so both the chunk reads and
 // the ring writes are contiguous runs; the 32 payload tables it uses stay in L1.
@@ -195,11 +206,10 @@ __global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ chunk,
 // Warp per (ring word, 32 channels): lane l holds sample 32*aw + l and loads its 32 channel
 // bytes with two 16-byte loads; one ballot per channel turns the 32 comparisons into that
 // channel's spike word. Requires nchan % 32 == 0 and a 16-byte aligned chunk.
-__global__ void __launch_bounds__(256) k_pack32(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
-                                                const int32_t* __restrict__ levels, long long t0, long long word0,
-                                                int nwords, uint32_t* __restrict__ ring, int R) {
-  const int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void pack32_warp(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
+                                            const int32_t* __restrict__ levels, long long t0, long long word0,
+                                            int nwords, uint32_t* __restrict__ ring, int R, const int task,
+                                            const int lane) {
   const int ncb = nchan >> 5;
   if (task >= nwords * ncb) return;
   const int q = task / ncb, cb = task - q * ncb;
@@ -231,6 +241,77 @@ __global__ void __launch_bounds__(256) k_pack32(const uint8_t* __restrict__ chun
   if (s0 < t0) w |= row[phys] & ((1u << static_cast<int>(t0 - s0)) - 1u);
   row[phys] = w;
   row[phys + R] = w;
+}
+
+__global__ void __launch_bounds__(256) k_pack32(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
+                                                const int32_t* __restrict__ levels, long long t0, long long word0,
+                                                int nwords, uint32_t* __restrict__ ring, int R) {
+  pack32_warp(chunk, nsamp, nchan, levels, t0, word0, nwords, ring, R, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+              threadIdx.x & 31);
+}
+
+// Many plans' encoders, three launches in all: every kernel's CTAs are spread over the beams
+// by a prefix of their CTA counts (a CTA finds its beam by binary search).
+constexpr int kMaxEncBeams = 64;
+
+struct EncBeam {
+  const uint8_t* chunk;
+  int nsamp, nchan;
+  uint32_t* hist;
+  int32_t* levels;
+  double theta;
+  long long t0, w0;
+  int nwords;
+  uint32_t* ring;
+  int R;
+  uint32_t* counters;  // the beam's matched-filter / candidate block counters, cleared here
+  int hx;              // histogram CTAs along channels
+};
+
+struct EncMulti {
+  int nbeams;
+  int first_h[kMaxEncBeams], first_l[kMaxEncBeams], first_p[kMaxEncBeams];
+  EncBeam beam[kMaxEncBeams];
+};
+
+__device__ __forceinline__ int beam_of(const int* first, int n, int i) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_hist_multi(const __grid_constant__ EncMulti m) {
+  const int i = static_cast<int>(blockIdx.x);
+  const int b = beam_of(m.first_h, m.nbeams, i);
+  const EncBeam& e = m.beam[b];
+  const int local = i - m.first_h[b];
+  hist_cta(e.chunk, e.nsamp, e.nchan, e.hist, local % e.hx, local / e.hx);
+}
+
+__global__ void __launch_bounds__(256) k_levels_multi(const __grid_constant__ EncMulti m) {
+  const int i = static_cast<int>(blockIdx.x);
+  const int b = beam_of(m.first_l, m.nbeams, i);
+  const EncBeam& e = m.beam[b];
+  const int local = i - m.first_l[b];
+  if (local == 0 && threadIdx.x == 0) {
+    e.counters[kCntCells] = 0;
+    e.counters[kCntRuns] = 0;
+    e.counters[kCntBlockCands] = 0;
+  }
+  levels_warp(e.hist, e.nchan, e.nsamp, e.theta, e.levels, nullptr, 0, local * 8 + (threadIdx.x >> 5),
+              threadIdx.x & 31);
+}
+
+__global__ void __launch_bounds__(256) k_pack32_multi(const __grid_constant__ EncMulti m) {
+  const int i = static_cast<int>(blockIdx.x);
+  const int b = beam_of(m.first_p, m.nbeams, i);
+  const EncBeam& e = m.beam[b];
+  const int local = i - m.first_p[b];
+  pack32_warp(e.chunk, e.nsamp, e.nchan, e.levels, e.t0, e.w0, e.nwords, e.ring, e.R,
+              local * 8 + (threadIdx.x >> 5), threadIdx.x & 31);
 }
 
 }  // namespace
@@ -268,6 +349,65 @@ cudaError_t launch_encode(const Plan& p, const uint8_t* d_chunk, int nsamp, cuda
   }
   p.launches += 3;
   return cudaGetLastError();
+}
+
+// Encoders of several plans (bit-ring modes, 32-channel multiples, 16-byte aligned chunks) in
+// three launches; each beam's matched-filter and candidate block counters are cleared by its
+// first levels CTA. Plans outside those conditions take their own launch_encode (and the
+// counters are cleared by a memset).
+cudaError_t launch_encode_batch(const Plan* const* plans, const uint8_t* const* chunks, const int32_t* nsamp, int n,
+                                cudaStream_t s) {
+  EncMulti m{};
+  int nh = 0, nl = 0, np = 0;
+  const Plan* owner = nullptr;
+  auto flush = [&]() -> cudaError_t {
+    if (m.nbeams == 0) return cudaSuccess;
+    k_hist_multi<<<nh, dim3(32, 8), 0, s>>>(m);
+    k_levels_multi<<<nl, 256, 0, s>>>(m);
+    k_pack32_multi<<<np, 256, 0, s>>>(m);
+    owner->launches += 3;
+    m.nbeams = 0;
+    nh = nl = np = 0;
+    owner = nullptr;
+    return cudaGetLastError();
+  };
+  for (int i = 0; i < n; ++i) {
+    const Plan& p = *plans[i];
+    const bool fits = p.mode != SND_MODE_ZFLOAT && p.nchan % 32 == 0 &&
+                      (reinterpret_cast<uintptr_t>(chunks[i]) & 15u) == 0;
+    if (!fits) {
+      cudaError_t e = launch_encode(p, chunks[i], nsamp[i], s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(p.dp.counters, 0, sizeof(uint32_t) * (kCntBlockCands + 1), s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    EncBeam& e = m.beam[m.nbeams];
+    e.chunk = chunks[i];
+    e.nsamp = nsamp[i];
+    e.nchan = p.nchan;
+    e.hist = p.dp.hist;
+    e.levels = p.dp.levels;
+    e.theta = p.enc_theta;
+    e.t0 = p.T;
+    e.w0 = p.T >> 5;
+    e.nwords = static_cast<int>(((p.T + nsamp[i] - 1) >> 5) - e.w0 + 1);
+    e.ring = p.dp.ring;
+    e.R = p.R;
+    e.counters = p.dp.counters;
+    e.hx = (p.nchan + 31) / 32;
+    m.first_h[m.nbeams] = nh;
+    m.first_l[m.nbeams] = nl;
+    m.first_p[m.nbeams] = np;
+    nh += e.hx * ((nsamp[i] + kHistRowsPerBlock - 1) / kHistRowsPerBlock);
+    nl += (p.nchan * 32 + 255) / 256;
+    np += static_cast<int>((static_cast<long long>(e.nwords) * (p.nchan / 32) * 32 + 255) / 256);
+    if (!owner) owner = &p;
+    if (++m.nbeams == kMaxEncBeams) {
+      const cudaError_t err = flush();
+      if (err != cudaSuccess) return err;
+    }
+  }
+  return flush();
 }
 
 }  // namespace snd

@@ -19,6 +19,7 @@
 
 #include <climits>
 #include <cmath>
+#include <vector>
 
 #include "snd_internal.h"
 
@@ -57,7 +58,8 @@ __device__ __forceinline__ double snr_of(long long s, double mu_w, double den) {
   return __ddiv_rn(__dsub_rn(static_cast<double>(s), mu_w), den);
 }
 
-__global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
+// One DM row d of one plan's block (the body of k_mf and of the many-beam k_mf_multi).
+__device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
   // smem: 4 words of front pad, then y[0..4*G) with y 16-byte aligned, G = len/4 + 2 groups
   extern __shared__ __align__(16) int32_t smem[];
   constexpr int NWARP = kMfThreads / 32;
@@ -66,7 +68,6 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
   __shared__ double s_muw[kNumWidthSlots], s_den[kNumWidthSlots];
   __shared__ int s_ok;
   __shared__ uint32_t wsum[NWARP];
-  const int d = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int len = static_cast<int>(a.e_new - a.f_prev);
   const int c0 = static_cast<int>(a.f_prev % a.Lp);
@@ -339,14 +340,36 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf(MfArgs a) {
   }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(kMfThreads, 3) k_mf(const __grid_constant__ MfArgs a) { mf_row(a, blockIdx.x); }
 
-cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64_t f_new,
-                      void* d_plane_out, cudaStream_t s) {
+constexpr int kMaxMfBeams = 64;
+
+// Many plans' blocks in one launch: CTA i scores row i - first[b] of the last beam b with
+// first[b] <= i.
+struct MfMulti {
+  int nbeams;
+  int first[kMaxMfBeams];
+  MfArgs beam[kMaxMfBeams];
+};
+
+__global__ void __launch_bounds__(kMfThreads, 3) k_mf_multi(const __grid_constant__ MfMulti m) {
+  const int i = static_cast<int>(blockIdx.x);
+  int lo = 0, hi = m.nbeams - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (m.first[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  mf_row(m.beam[lo], i - m.first[lo]);
+}
+
+// Arguments of one plan's block; *smem = the dynamic shared memory of its row staging.
+// Returns false when the block has nothing to do.
+bool mf_args(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64_t f_new, void* d_plane_out,
+             MfArgs& a, int* smem) {
   const int nb = static_cast<int>(f_new - f_prev);
   const int nemit = static_cast<int>(e_new - e_prev);
-  if (nb <= 0 && (d_plane_out == nullptr || nemit <= 0)) return cudaSuccess;
-  MfArgs a{};
+  if (nb <= 0 && (d_plane_out == nullptr || nemit <= 0)) return false;
+  a = MfArgs{};
   a.plane = p.dp.plane;
   a.Lp = p.Lp;
   a.ndm = p.ndm;
@@ -368,20 +391,74 @@ cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_pr
   a.nemit = nemit;
   a.out_u8 = p.plane_u8;
   const int len = static_cast<int>(e_new - f_prev);
-  const int smem = ((len >> 2) + 3) * 16;  // front pad (4 words) and len/4 + 2 aligned groups
+  *smem = ((len >> 2) + 3) * 16;  // front pad (4 words) and len/4 + 2 aligned groups
+  return true;
+}
+
+// rows resident at once on the GPU for a kernel with `smem` bytes per CTA
+template <typename K>
+cudaError_t resident_rows(K kern, int smem, int fallback, int* out) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMfThreads, smem);
+  *out = per_sm > 0 ? nsm * per_sm : fallback;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64_t f_new,
+                      void* d_plane_out, cudaStream_t s) {
+  MfArgs a;
+  int smem = 0;
+  if (!mf_args(p, e_prev, e_new, f_prev, f_new, d_plane_out, a, &smem)) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = resident_rows(k_mf, smem, p.ndm, &a.pf_rows);
   if (e != cudaSuccess) return e;
-  {
-    int dev = 0, nsm = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mf, kMfThreads, smem);
-    if (e != cudaSuccess) return e;
-    a.pf_rows = per_sm > 0 ? nsm * per_sm : p.ndm;
-  }
   k_mf<<<p.ndm, kMfThreads, smem, s>>>(a);
   p.launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_mf_batch(const Plan* const* plans, const ChunkPos* pos, int n, cudaStream_t s) {
+  // Blocks are grouped by the CTAs per SM their row staging allows (shared memory up to about
+  // 72 KB: three, 110 KB: two, more: one), so a long-chunk beam does not lower the occupancy of
+  // every other beam's rows: at most three launches (more only past 64 beams per group).
+  auto cls = [](int smem) { return smem <= 72 * 1024 ? 0 : (smem <= 110 * 1024 ? 1 : 2); };
+  std::vector<MfArgs> args(n);
+  std::vector<int> sm(n, 0), live(n, 0);
+  for (int i = 0; i < n; ++i)
+    live[i] = mf_args(*plans[i], pos[i].e_prev, pos[i].e_new, pos[i].f_prev, pos[i].f_new, nullptr, args[i], &sm[i]);
+  for (int c = 0; c < 3; ++c) {
+    for (int i0 = 0; i0 < n;) {
+      MfMulti m{};
+      int smem = 0, ctas = 0;
+      const Plan* owner = nullptr;
+      int i = i0;
+      for (; i < n && m.nbeams < kMaxMfBeams; ++i) {
+        if (!live[i] || cls(sm[i]) != c) continue;
+        m.beam[m.nbeams] = args[i];
+        m.first[m.nbeams] = ctas;
+        ctas += plans[i]->ndm;
+        smem = smem > sm[i] ? smem : sm[i];
+        if (!owner) owner = plans[i];
+        ++m.nbeams;
+      }
+      i0 = i;
+      if (m.nbeams == 0) continue;
+      cudaError_t e = cudaFuncSetAttribute(k_mf_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      int pf = 0;
+      if (e == cudaSuccess) e = resident_rows(k_mf_multi, smem, ctas, &pf);
+      if (e != cudaSuccess) return e;
+      for (int b = 0; b < m.nbeams; ++b) m.beam[b].pf_rows = pf;
+      k_mf_multi<<<ctas, kMfThreads, smem, s>>>(m);
+      owner->launches += 1;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace snd

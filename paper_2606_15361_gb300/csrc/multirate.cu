@@ -45,7 +45,6 @@ struct MultiRate {
   bool bound = false;
   bool graph = false;
   snd::GraphRunner runner;
-  snd::ForkJoin fj;
   cudaStream_t last_stream = nullptr;
   int sticky = 0;
 };
@@ -348,9 +347,7 @@ int enqueue_bands(MultiRate& m, const uint8_t* d_chunk, int32_t nsamp, cudaStrea
     src.push_back(in);
     ns.push_back(nsamp / b.S);
   }
-  if (plans.size() > 1 && m.fj.init(static_cast<int>(std::min<size_t>(plans.size(), 4))) != SND_OK) return SND_ERR_CUDA;
-  return snd::enqueue_plans(plans.data(), static_cast<int>(plans.size()), src.data(), ns.data(), s, owner,
-                            plans.size() > 1 ? &m.fj : nullptr);
+  return snd::enqueue_plans(plans.data(), static_cast<int>(plans.size()), src.data(), ns.data(), s, owner);
 }
 
 int run_bands(MultiRate& m, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s) {

@@ -289,7 +289,8 @@ extern "C" int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_
   *n_out = take;
   p.pending_host = 0;
   const uint32_t st = cnt[snd::kCntStatus];
-  if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout | snd::kStatusTreeTimeout)) return SND_ERR_TIMEOUT;
+  if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout | snd::kStatusTreeTimeout | snd::kStatusGridTimeout))
+    return SND_ERR_TIMEOUT;
   if (st & (snd::kStatusCellOverflow | snd::kStatusRunOverflow | snd::kStatusCandOverflow |
             snd::kStatusBlockCandOverflow | snd::kStatusBounds))
     return SND_ERR_OVERFLOW;

@@ -28,6 +28,7 @@ enum : uint32_t {
   kStatusUnionTimeout = 1u << 5,
   kStatusBounds = 1u << 6,
   kStatusTreeTimeout = 1u << 7,
+  kStatusGridTimeout = 1u << 8,
 };
 
 // One matched-filter cell kept for peak selection.
@@ -147,6 +148,8 @@ enum {
   kCntBlockCands = 2,
   kCntCands = 3,
   kCntStatus = 4,
+  kCntTreeQueue = 8,   // many-beam tree: next work item (the first plan of a batch launch)
+  kCntGridBar = 12,    // many-beam candidates: grid barrier arrivals, generation (two slots)
   kCntSlots = 16
 };
 
@@ -253,25 +256,19 @@ cudaError_t launch_tree(const Plan& p, int64_t e_prev, int64_t e_new, cudaStream
 cudaError_t launch_mf(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64_t f_new,
                       void* d_plane_out, cudaStream_t s);
 cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_t s);
+// many-beam launchers (encode.cu, mf.cu, ccl.cu): several plans' chunk stages in few launches
+cudaError_t launch_encode_batch(const Plan* const* plans, const uint8_t* const* chunks, const int32_t* nsamp, int n,
+                                cudaStream_t s);
+cudaError_t launch_mf_batch(const Plan* const* plans, const ChunkPos* pos, int n, cudaStream_t s);
+cudaError_t launch_candidates_batch(const Plan* const* plans, const ChunkPos* pos, int n, cudaStream_t s);
 TreeShape tree_shape(int mode, int nlev, int kmax);  // k_tree launch shape
 cudaError_t launch_tree_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,
                               cudaStream_t s);
-// Side streams for independent per-plan work: forked from and joined back to a main stream
-// with events (also inside a stream capture, where they become parallel graph branches).
-struct ForkJoin {
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> events;  // one fork event + one join event per side stream
-  int init(int n);
-  cudaError_t fork(cudaStream_t main);
-  cudaError_t join(cudaStream_t main);
-  ~ForkJoin();
-};
-
-// batch.cu: one chunk of each plan (encoders, grouped tree launches, matched filter and
-// candidates), enqueued on s (per-plan stages spread over fj's side streams when given);
-// the plans then record `owner` as their stream
+// batch.cu: one chunk of each plan (all encoders, the trees, all matched filters and all
+// candidate stages, each in a few launches), enqueued on s; the plans then record `owner` as
+// their stream
 int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, const int32_t* nsamp, cudaStream_t s,
-                  cudaStream_t owner, ForkJoin* fj = nullptr);
+                  cudaStream_t owner);
 
 // Replays enqueued work as a CUDA graph: captured on a private stream, updated in place from
 // call to call while the topology is unchanged, launched on the caller's stream.

@@ -64,6 +64,8 @@ constexpr int kMaxDirBeams = 64;
 
 struct DirMulti {
   int nbeams;
+  int total;               // work items of all beams
+  unsigned int* queue;     // next work item (zero at launch)
   int first[kMaxDirBeams];
   int ntx[kMaxDirBeams];
   DirArgs beam[kMaxDirBeams];
@@ -412,8 +414,11 @@ struct DState<kBinary, KW, NPL, MAXU> {
 };
 
 // One CTA: DM tile `tile` (32 DMs, lane = DM) x time tile bx (NW warps x KW words).
+// bars: the CTA's two staging mbarriers (initialised once per CTA with one arrival per warp);
+// k0: staging rounds this CTA ran before (round k uses buffer k & 1, phase parity (k >> 1) & 1).
+// Returns false when a staging wait ran out (the CTA must stop).
 template <int MODE, int KW, int NPL, int MAXU>
-__device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
+__device__ __forceinline__ bool direct_cta(const DirArgs& a, int bx, int tile, unsigned long long* bars, int k0) {
   extern __shared__ __align__(128) uint32_t sm[];
   const int lane = threadIdx.x, wd = threadIdx.y, NW = blockDim.y;
   const int tid = wd * 32 + lane, nthr = 32 * NW;
@@ -423,7 +428,6 @@ __device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
   uint32_t* win = sm;                              // [2][SG][cspan]
   uint16_t* met = reinterpret_cast<uint16_t*>(sm + 2 * wbuf);  // [2][SG][32]
   int32_t* sbase = reinterpret_cast<int32_t*>(sm + 2 * wbuf + SG * 32);  // [nchan]
-  __shared__ __align__(8) unsigned long long bars[2];
   const long long aw0 = a.word0 + static_cast<long long>(bx) * a.tile_words;
   const int lead = static_cast<int>(aw0 & 3);
   const long long aw4 = aw0 - lead;
@@ -439,12 +443,6 @@ __device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
       sbase[c] = st0;
     }
   }
-  if (tid == 0) {
-    // one arrival per warp: every warp stages its share of a round
-    bar_init(smem_u32(&bars[0]), NW);
-    bar_init(smem_u32(&bars[1]), NW);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
   __syncthreads();
 
   // Stage round g into buffer b. Every warp issues the bulk copies of its share of the SG
@@ -452,7 +450,8 @@ __device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
   // buffer's mbarrier, so the transaction count never runs ahead of the copies and no warp
   // carries the whole round's issue cost.
   const int share = (SG + NW - 1) / NW;
-  auto issue = [&](int g, int b) {
+  auto issue = [&](int g) {
+    const int b = (k0 + g) & 1;
     const uint32_t bar = smem_u32(&bars[b]);
     const int i0 = wd * share, i1 = min(SG, i0 + share);
     // the buffer's previous contents were read by every warp before the last barrier
@@ -475,12 +474,12 @@ __device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
   // a warp none of whose words is emitted here (the short last tile of a call) only keeps the
   // CTA's barriers
   const bool busy = wd * KW < min(a.tile_words, a.nwords - bx * a.tile_words);
-  issue(0, 0);
+  issue(0);
   int g = 0, abort = 0;
   for (; g < ngroups; ++g) {
-    const int b = g & 1;
-    if (g + 1 < ngroups) issue(g + 1, b ^ 1);  // buffer b ^ 1 was released by the last barrier
-    const bool ok = bar_wait(smem_u32(&bars[b]), (g >> 1) & 1);
+    const int b = (k0 + g) & 1;
+    if (g + 1 < ngroups) issue(g + 1);  // buffer b ^ 1 was released by the last barrier
+    const bool ok = bar_wait(smem_u32(&bars[b]), ((k0 + g) >> 1) & 1);
     if (ok && busy) {
 #pragma unroll 1
       for (int h = 0; h < a.sgroups; ++h) {
@@ -506,12 +505,13 @@ __device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
     // g + 1) another bounded wait before the CTA's shared memory is released
     if (tid == 0) {
       atomicOr(a.status, kStatusTreeTimeout);
-      for (int gi = g; gi < g + 2 && gi < ngroups; ++gi) bar_wait(smem_u32(&bars[gi & 1]), (gi >> 1) & 1);
+      for (int gi = g; gi < g + 2 && gi < ngroups; ++gi)
+        bar_wait(smem_u32(&bars[(k0 + gi) & 1]), ((k0 + gi) >> 1) & 1);
     }
-    return;
+    return false;
   }
   const int drow = tile * 32 + lane;
-  if (drow >= a.ndm) return;
+  if (drow >= a.ndm) return true;
   const int lw = a.Lp >> 5;
 #pragma unroll
   for (int j = 0; j < KW; ++j) {
@@ -521,23 +521,50 @@ __device__ __forceinline__ void direct_cta(const DirArgs& a, int bx, int tile) {
     const int col = static_cast<int>(aw % lw) * 32;
     st.store(a.plane + static_cast<size_t>(drow) * a.Lp + col, j);
   }
+  return true;
+}
+
+__device__ __forceinline__ void init_bars(unsigned long long* bars) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    // one arrival per warp: every warp stages its share of a round
+    bar_init(smem_u32(&bars[0]), blockDim.y);
+    bar_init(smem_u32(&bars[1]), blockDim.y);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
 }
 
 template <int MODE, int KW, int NPL, int MAXU>
 __global__ void __launch_bounds__(256, 2) k_snd(const __grid_constant__ DirArgs a) {
-  direct_cta<MODE, KW, NPL, MAXU>(a, blockIdx.x, blockIdx.y);
+  __shared__ __align__(8) unsigned long long bars[2];
+  init_bars(bars);
+  direct_cta<MODE, KW, NPL, MAXU>(a, blockIdx.x, blockIdx.y, bars, 0);
 }
 
+// Many beams, persistent: each CTA takes (beam, DM tile, time tile) work items from a device
+// counter (m.queue, zero at launch) until none is left; item i belongs to the last beam b with
+// first[b] <= i, its time tile fastest.
 template <int MODE, int KW, int NPL, int MAXU>
 __global__ void __launch_bounds__(256, 2) k_snd_multi(const __grid_constant__ DirMulti m) {
-  const int i = static_cast<int>(blockIdx.x);
-  int lo = 0, hi = m.nbeams - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (m.first[mid] <= i) lo = mid; else hi = mid - 1;
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ int s_item;
+  init_bars(bars);
+  int k0 = 0;
+  for (;;) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_item = static_cast<int>(atomicAdd(m.queue, 1u));
+    __syncthreads();
+    const int i = s_item;
+    __syncthreads();
+    if (i >= m.total) return;
+    int lo = 0, hi = m.nbeams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (m.first[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const DirArgs& a = m.beam[lo];
+    const int local = i - m.first[lo];
+    if (!direct_cta<MODE, KW, NPL, MAXU>(a, local % m.ntx[lo], local / m.ntx[lo], bars, k0)) return;
+    k0 += a.nchan / (kDG * a.sgroups);
   }
-  const int local = i - m.first[lo];
-  direct_cta<MODE, KW, NPL, MAXU>(m.beam[lo], local % m.ntx[lo], local / m.ntx[lo]);
 }
 
 template <int MODE, int KW, int NPL, int MAXU>
@@ -553,8 +580,16 @@ template <int MODE, int KW, int NPL, int MAXU>
 cudaError_t run_direct_multi(const DirMulti& m, int ctas, dim3 block, int smem, cudaStream_t s) {
   auto kern = k_snd_multi<MODE, KW, NPL, MAXU>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // persistent: as many CTAs as fit on the GPU at once (fewer if there are fewer items)
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, static_cast<int>(block.x * block.y), smem);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, block, smem, s>>>(m);
+  const int grid = per_sm > 0 && nsm * per_sm < ctas ? nsm * per_sm : ctas;
+  kern<<<grid, block, smem, s>>>(m);
   return cudaGetLastError();
 }
 
@@ -660,6 +695,8 @@ cudaError_t launch_tree_direct_batch(const Plan* const* plans, const int64_t* e_
       ++m.nbeams;
     }
     if (m.nbeams == 0) continue;
+    m.total = ctas;
+    m.queue = reinterpret_cast<unsigned int*>(plans[i]->dp.counters + kCntTreeQueue);
     DGoMulti go{&m, ctas, dim3(32, warps), smem, s};
     const cudaError_t e = dispatch_direct(key, go);
     if (e != cudaSuccess) return e;

@@ -1,12 +1,14 @@
 """Many beams per step (snd_batch_*): a batch of ragged beams (own DM grids, chunk lengths,
 modes and branching) gives every beam exactly the candidates of its own plan run alone,
-eagerly and through a CUDA graph; the single-beam plans are themselves checked against the
-oracle in test_gpu_parity.py, and one batched beam is checked against the oracle here. The
+eagerly and through a CUDA graph, and every batched beam's candidates equal the oracle's.
+A step of all beams takes a fixed handful of launches (multi-beam encoder, persistent tree,
+multi-beam matched filter, cooperative candidate stage), whatever the number of beams. The
 autotuner's pick leaves a float beam's plane unchanged."""
 import numpy as np
 import pytest
 
 import synth
+from oracle import cxx
 from oracle import stream as ostream
 
 pytestmark = pytest.mark.gpu
@@ -78,21 +80,49 @@ def test_batch_equals_each_plan_alone(graph):
         assert inst >= 1 and inst + upd == nsteps
 
 
-def test_batched_beam_matches_oracle():
-    """Beam 1 of a batch (128 channels, B = 8, float) against the FP64 oracle stream."""
+@pytest.mark.parametrize("graph", [False, True])
+def test_every_batched_beam_matches_oracle(graph):
+    """Every beam of the batch against the C++ oracle stream of its own configuration."""
     nsteps = 4
     data = [_beam_data(i, nc, chunk, nsteps, dmx) for i, (nc, nd, dmx, chunk, mode, B) in enumerate(BEAMS)]
     plans = _plans()
-    batch = g.Batch(plans, graph=True)
-    nc, nd, dmx, chunk, mode, B = BEAMS[1]
-    cfg = ostream.defaults(ostream.FLOAT, branching=B, det_theta=5.5)
-    ref = ostream.OracleStream(synth.channel_freqs(nc), synth.NC_DT, synth.dm_grid(nd, dmx), cfg)
-    exp = []
+    batch = g.Batch(plans, graph=graph)
+    refs = [cxx.Stream(synth.channel_freqs(nc), synth.NC_DT, synth.dm_grid(nd, dmx),
+                       ostream.defaults(mode, branching=B, det_theta=5.5))
+            for nc, nd, dmx, chunk, mode, B in BEAMS]
+    exp = [[] for _ in BEAMS]
     for s in range(nsteps):
         batch.execute([torch.from_numpy(data[i][s]).cuda() for i in range(len(BEAMS))])
-        exp += ref.push(data[1][s])["candidates"]
-    got = _tuples(plans[1].candidates()[0])
-    assert got == [(c[0], c[2], float(c[3]), c[4], c[5]) for c in exp]
+        for i in range(len(BEAMS)):
+            exp[i] += refs[i].push(data[i][s], want_plane=False)["candidates"]
+    total = 0
+    for i in range(len(BEAMS)):
+        got = _tuples(plans[i].candidates()[0])
+        assert got == [(c[0], c[2], float(c[3]), c[4], c[5]) for c in exp[i]], f"beam {i}"
+        total += len(got)
+    assert total >= 10
+
+
+def test_step_launch_count_is_fixed():
+    """A steady step of 7 ragged beams in 3 modes: encoder (3), one tree launch per kernel
+    instantiation, one matched-filter and one candidate launch, i.e. at most 3 + 4 + 2
+    launches, and the same count with twice the beams."""
+    nsteps = 5
+    data = [_beam_data(i, nc, chunk, nsteps, dmx) for i, (nc, nd, dmx, chunk, mode, B) in enumerate(BEAMS)]
+    dev = [[torch.from_numpy(c).cuda() for c in d] for d in data]
+    counts = []
+    for copies in (1, 2):
+        plans = _plans() + (_plans() if copies == 2 else [])
+        batch = g.Batch(plans)
+        for s in range(nsteps - 1):
+            batch.execute([dev[i % len(BEAMS)][s] for i in range(len(plans))])
+        torch.cuda.synchronize()
+        l0 = sum(p.stats().kernel_launches for p in plans)
+        batch.execute([dev[i % len(BEAMS)][nsteps - 1] for i in range(len(plans))])
+        torch.cuda.synchronize()
+        counts.append(sum(p.stats().kernel_launches for p in plans) - l0)
+    insts = len({(p.stats().tree_kernel, p.stats().mode, p.stats().tree_smem_bytes > 0) for p in _plans()})
+    assert counts[0] == counts[1] and counts[0] <= 3 + 4 + 2, (counts, insts)
 
 
 def test_autotune_pick_keeps_the_float_plane():
