@@ -348,6 +348,34 @@ def multirate_rate(g, args, dev, stream, dchunks, freqs, dms, mode=("graded", 1)
     return out
 
 
+def branching_sweep(g, args, dev, dchunks, freqs, dms, branchings=(2, 4, 8)):
+    """Tree time per steady 16384-sample chunk of the bench beam for each branching factor and
+    mode (the factor is free in Methods, "Tree levels"; float and uncapped graded planes do
+    not depend on it), from the stage events, with the HBM fraction on 4.5 B per DM-sample."""
+    peaks, src = _peaks()
+    out = {}
+    for B in branchings:
+        row = {}
+        for name, m in MODES:
+            p = g.Plan(freqs, synth.NC_DT, dms, B, m, g.options(m, max_chunk=W.chunk), device=dev)
+            for c in dchunks[:3]:
+                p.execute(c)
+            p.profile(True)
+            p.profile_read()
+            for c in dchunks[3:8]:
+                p.execute(c)
+            prof = p.profile_read()
+            tms = prof["tree"][0] / max(prof["tree"][1], 1)
+            ach = TREE_BYTES_PER_DM_SAMPLE * W.chunk * W.ndm / (tms / 1e3) / 1e9
+            row[name] = {"tree_ms_per_chunk": round(tms, 4), "hbm_frac": round(ach / peaks["hbm_gbs"], 4),
+                         "kernel": g.TREE_KERNELS[p.stats().tree_kernel], "levels": int(p.stats().nlevels)}
+            del p
+        out[str(B)] = row
+    out["note"] = ("tree stage per chunk (CUDA events), 5 steady chunks after 3 warm-up; hbm_frac of the measured "
+                   f"copy bandwidth ({src})")
+    return out
+
+
 def zfloat_rate(g, args, dev, dchunks, freqs, dms):
     """Labelled-payload Mode C (precision study) on the same beam: the tree with FP16 and with
     FP32 partial-sum storage, timed per chunk by the stage events (plane only)."""
@@ -616,6 +644,7 @@ def run_gpu(args, rank, world, local_rank):
 
     extras = rank == 0 and not args.main_only
     mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if extras else None
+    bsw = branching_sweep(g, args, dev, dchunks, freqs, dms) if extras else None
     zf = zfloat_rate(g, args, dev, dchunks, freqs, dms) if extras else None
     sft = sifter_rate(g, args, dev) if extras and not args.no_sifter else None
     mb = multibeam_rate(g, args, dev) if extras and not args.no_multibeam else None
@@ -689,6 +718,7 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(d2h / max(args.steps, 1))},
         "realtime_beams_per_mode": realtime_beams,
         "multirate": mr,
+        "branching_sweep": bsw,
         "zfloat_precision_study": zf,
         "learned_sifter": sft,
         "multibeam": mb,

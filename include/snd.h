@@ -131,7 +131,10 @@ typedef struct {
   int32_t max_patterns_per_group;
   int64_t kernel_launches;         /* CUDA kernels enqueued by this plan since binding */
   int32_t tree_kernel;             /* 0 leaf-sharing k_tree, 1 direct k_snd, 2 reference, 3 labelled payload */
-  int32_t reserved_stats;
+  int32_t device_status;           /* device status bits read by the last snd_candidates (0 = clean):
+                                      1 matched-filter cells, 2 runs, 4 candidates, 8 block candidates
+                                      overflowed; 16 threshold search, 32 union-find, 128 tree staging
+                                      wait, 256 grid barrier wait gave up; 64 a cell outside its run */
 } snd_plan_stats_t;
 
 /* Pipeline stages timed by snd_profile / snd_profile_read. */
@@ -223,6 +226,27 @@ int snd_profile(snd_plan_t plan, int enable);
 int snd_profile_read(snd_plan_t plan, double* ms_out, int64_t* count_out);
 
 /*
+ * Test hook (the paper has no counterpart): make a later host allocation of object
+ * construction fail. after >= 0 arms a countdown over the library's host allocation points
+ * (plan, multi-rate plan and batch construction): the point that finds it at zero fails as an
+ * out-of-memory allocation would, so that call returns SND_ERR_NOMEM and creates nothing; the
+ * hook then disarms itself. after < 0 disarms it. Process-wide; returns SND_OK.
+ */
+int snd_debug_fail_host_alloc(int32_t after);
+
+/*
+ * Test hook (the paper has no counterpart): bound every bounded device loop of this plan's
+ * kernels by `limit` (iterations for the union-find walks and the matched filter's threshold
+ * search, clock cycles for the tree's staging waits and the many-beam candidate stage's grid
+ * barrier; a batch uses its first plan's limit for the barrier). A loop that reaches its bound
+ * sets a device status bit and the kernel returns (a staging wait that gives up still waits,
+ * with the normal bound, for its copies in flight); snd_candidates then returns
+ * SND_ERR_TIMEOUT and snd_plan_stats shows the bits. limit = 0 restores the defaults.
+ * Rebinding the workspace clears the status word.
+ */
+int snd_debug_loop_limit(snd_plan_t plan, int64_t limit);
+
+/*
  * Encoder without device allocation (the paper has no counterpart: this is a convenience for
  * callers that cannot allocate device memory, e.g. code running where cudaMalloc is not
  * allowed or plugins that are handed only pre-allocated buffers). Encodes one chunk on its
@@ -232,9 +256,12 @@ int snd_profile_read(snd_plan_t plan, double* ms_out, int64_t* count_out);
  *   theta       encoder threshold in sigma (snd_options_t.enc_theta)
  *   d_bits_out  device uint32[nchan][ceil(nsamp/32)]: bit i of word w is x_c(32 w + i)
  * Needs no workspace: its histogram scratch is a static device array sized for at most 4096
- * channels (nchan > 4096 returns SND_ERR_UNSUPPORTED). The first call on a device looks the
- * array up and must come before any stream capture. Calls on one device share the array, so
- * calls that overlap on the GPU race; serialise them. No allocation is made.
+ * channels; nchan > 4096 or nsamp > 16,776,960 (= 65535 x 256) returns SND_ERR_UNSUPPORTED
+ * before any work is enqueued. The first call on a device looks the array up and must come
+ * before any stream capture. Calls on one device share the array, so calls that overlap on
+ * the GPU race; serialise them. No allocation is made. Launch errors are checked after every
+ * launch (SND_ERR_CUDA); a launch error left pending by earlier work on the calling thread is
+ * reported, and cleared, the same way.
  */
 int snd_encode_static(const uint8_t* d_chunk, int32_t nsamp, int32_t nchan, double theta, uint32_t* d_bits_out,
                       void* stream);

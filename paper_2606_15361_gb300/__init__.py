@@ -57,7 +57,7 @@ class SndPlanStats(ctypes.Structure):
         ("scored", ctypes.c_int64), ("candidates_pending", ctypes.c_int32), ("tree_tile_dms", ctypes.c_int32),
         ("tree_tile_words", ctypes.c_int32), ("tree_group_leaves", ctypes.c_int32),
         ("tree_smem_bytes", ctypes.c_int32), ("max_patterns_per_group", ctypes.c_int32),
-        ("kernel_launches", ctypes.c_int64), ("tree_kernel", ctypes.c_int32), ("reserved_stats", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int64), ("tree_kernel", ctypes.c_int32), ("device_status", ctypes.c_int32),
     ]
 
 
@@ -67,7 +67,8 @@ assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(SndCandidate) == 32
 
 EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", "snd_bind_workspace",
            "snd_execute", "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table",
-           "snd_profile", "snd_profile_read", "snd_encode_static", "snd_destroy", "snd_error_string",
+           "snd_profile", "snd_profile_read", "snd_encode_static", "snd_debug_fail_host_alloc", "snd_debug_loop_limit", "snd_destroy",
+           "snd_error_string",
            "snd_multirate_plan", "snd_multirate_info", "snd_multirate_band_plan", "snd_multirate_workspace_size",
            "snd_multirate_bind_workspace", "snd_multirate_execute", "snd_multirate_execute_host",
            "snd_multirate_candidates", "snd_multirate_destroy", "snd_multirate_set_graph",
@@ -100,6 +101,10 @@ def _load():
     lib.snd_profile.argtypes = [P, ctypes.c_int]
     lib.snd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.snd_encode_static.argtypes = [V, I32, I32, D, V, V]
+    lib.snd_debug_fail_host_alloc.argtypes = [I32]
+    lib.snd_debug_loop_limit.argtypes = [P, I64]
+    lib.snd_debug_loop_limit.restype = ctypes.c_int
+    lib.snd_debug_fail_host_alloc.restype = ctypes.c_int
     lib.snd_destroy.argtypes = [P]
     lib.snd_destroy.restype = None
     lib.snd_error_string.argtypes = [ctypes.c_int]

@@ -16,6 +16,8 @@
 // whenever the topology is unchanged, so a steady stream of chunks re-uses one executable
 // graph.
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <functional>
 #include <new>
@@ -126,19 +128,20 @@ int fail(Batch& b, int code) {
 extern "C" int snd_batch_create(const snd_plan_t* plans, int32_t nplans, snd_batch_t* out) {
   if (out) *out = nullptr;
   if (!out || !plans || nplans < 1 || nplans > 4096) return SND_ERR_ARG;
-  Batch* b = new (std::nothrow) Batch();
-  if (!b) return SND_ERR_NOMEM;
   for (int i = 0; i < nplans; ++i) {
-    if (!plans[i]) {
-      delete b;
-      return SND_ERR_ARG;
-    }
+    if (!plans[i]) return SND_ERR_ARG;
     for (int j = 0; j < i; ++j)
-      if (plans[j] == plans[i]) {
-        delete b;
-        return SND_ERR_ARG;
-      }
-    b->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
+      if (plans[j] == plans[i]) return SND_ERR_ARG;
+  }
+  Batch* b = nullptr;
+  try {
+    snd::alloc_point();
+    b = new Batch();
+    snd::alloc_point();  // the plan list
+    for (int i = 0; i < nplans; ++i) b->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
+  } catch (const std::bad_alloc&) {
+    delete b;
+    return SND_ERR_NOMEM;
   }
   *out = reinterpret_cast<snd_batch_t>(b);
   return SND_OK;
@@ -165,10 +168,12 @@ extern "C" int snd_batch_execute(snd_batch_t h, const uint8_t* const* d_chunks, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Plan* const* plans = b.plans.data();
   const int n = static_cast<int>(b.plans.size());
+  nvtxRangePushA("snd.batch_step");
   const int rc = b.graph ? b.runner.run(s, [&](cudaStream_t cs) {
     return snd::enqueue_plans(plans, n, d_chunks, nsamp, cs, s);
   })
                          : snd::enqueue_plans(plans, n, d_chunks, nsamp, s, s);
+  nvtxRangePop();
   return rc ? fail(b, rc) : SND_OK;
 }
 

@@ -288,9 +288,9 @@ __global__ void k_run_write(const uint32_t* __restrict__ m, int ndm, int mw, int
                 (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
 }
 
-__device__ __forceinline__ int find_root(const int32_t* parent, int x, uint32_t* status) {
+__device__ __forceinline__ int find_root(const int32_t* parent, int x, uint32_t* status, int lim) {
   const volatile int32_t* vp = parent;
-  for (int it = 0; it < (1 << 20); ++it) {
+  for (int it = 0; it < lim; ++it) {
     const int p = vp[x];
     if (p == x) return x;
     x = p;
@@ -299,10 +299,10 @@ __device__ __forceinline__ int find_root(const int32_t* parent, int x, uint32_t*
   return x;
 }
 
-__device__ __forceinline__ void unite(int32_t* parent, int a, int b, uint32_t* status) {
-  for (int it = 0; it < 4096; ++it) {
-    a = find_root(parent, a, status);
-    b = find_root(parent, b, status);
+__device__ __forceinline__ void unite(int32_t* parent, int a, int b, uint32_t* status, int lim) {
+  for (int it = 0; it < (lim < 4096 ? lim : 4096); ++it) {
+    a = find_root(parent, a, status, lim);
+    b = find_root(parent, b, status, lim);
     if (a == b) return;
     if (a < b) {
       const int t = a;
@@ -323,7 +323,7 @@ __device__ __forceinline__ int runs_total(const int32_t* row_runs, int ndm, int 
 // the single-plan kernels, a loop over the whole cooperative grid in the many-beam kernel).
 __device__ __forceinline__ void union_items(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
                                             const int32_t* run_end, const int32_t* run_row, int32_t* parent,
-                                            uint32_t* counters, int i0, int stride) {
+                                            uint32_t* counters, int lim, int i0, int stride) {
   const int n = runs_total(row_runs, ndm, run_cap);
   for (int i = i0; i < n; i += stride) {
     const int d = run_row[i];
@@ -336,30 +336,30 @@ __device__ __forceinline__ void union_items(const int32_t* row_runs, int ndm, in
       const int mid = (a + b) >> 1;
       if (run_end[mid] >= s) b = mid; else a = mid + 1;
     }
-    for (int j = a; j < hi && run_start[j] <= e; ++j) unite(parent, i, j, &counters[kCntStatus]);
+    for (int j = a; j < hi && run_start[j] <= e; ++j) unite(parent, i, j, &counters[kCntStatus], lim);
   }
 }
 
 __global__ void k_union(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
-                        const int32_t* run_end, const int32_t* run_row, int32_t* parent, uint32_t* counters) {
-  union_items(row_runs, ndm, run_cap, run_start, run_end, run_row, parent, counters,
+                        const int32_t* run_end, const int32_t* run_row, int32_t* parent, uint32_t* counters, int lim) {
+  union_items(row_runs, ndm, run_cap, run_start, run_end, run_row, parent, counters, lim,
               blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 __device__ __forceinline__ void flatten_items(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
                                               const int32_t* run_end, int32_t* parent, int32_t* npix,
-                                              uint32_t* counters, int i0, int stride) {
+                                              uint32_t* counters, int lim, int i0, int stride) {
   const int n = runs_total(row_runs, ndm, run_cap);
   for (int i = i0; i < n; i += stride) {
-    const int r = find_root(parent, i, &counters[kCntStatus]);
+    const int r = find_root(parent, i, &counters[kCntStatus], lim);
     parent[i] = r;
     atomicAdd(&npix[r], run_end[i] - run_start[i]);
   }
 }
 
 __global__ void k_flatten(const int32_t* row_runs, int ndm, int run_cap, const int32_t* run_start,
-                          const int32_t* run_end, int32_t* parent, int32_t* npix, uint32_t* counters) {
-  flatten_items(row_runs, ndm, run_cap, run_start, run_end, parent, npix, counters,
+                          const int32_t* run_end, int32_t* parent, int32_t* npix, uint32_t* counters, int lim) {
+  flatten_items(row_runs, ndm, run_cap, run_start, run_end, parent, npix, counters, lim,
                 blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
@@ -493,7 +493,7 @@ constexpr long long kGridWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 struct CandBeam {
   const uint32_t* mask;
   uint32_t* mask3;
-  int ndm, mw, nb, r, run_cap, cell_cap, cand_cap, n_min;
+  int ndm, mw, nb, r, run_cap, cell_cap, cand_cap, n_min, lim;
   int32_t *row_runs, *run_start, *run_end, *run_row, *parent, *npix, *pwidth;
   unsigned long long* peak;
   const MfCell* cells;
@@ -509,6 +509,7 @@ struct CandMulti {
   int first_rows[kMaxCandBeams];   // 8-row groups of the beams before
   int total_close, total_rows;
   unsigned int* gbar;              // [2]: arrivals, generation
+  long long wait_cycles;           // bound of a barrier wait (clock cycles)
   CandBeam beam[kMaxCandBeams];
 };
 
@@ -535,7 +536,7 @@ __device__ bool grid_barrier(const CandMulti& m) {
     } else {
       const long long t0 = clock64();
       while (*gen == g) {
-        if (clock64() - t0 > kGridWaitCycles) {
+        if (clock64() - t0 > m.wait_cycles) {
           ok = 0;
           break;
         }
@@ -597,12 +598,14 @@ __global__ void __launch_bounds__(256) k_cand_multi(const __grid_constant__ Cand
   // 5. - 10. over each beam's runs, cells and block candidates
   for (int b = 0; b < m.nbeams; ++b) {
     const CandBeam& e = m.beam[b];
-    union_items(e.row_runs, e.ndm, e.run_cap, e.run_start, e.run_end, e.run_row, e.parent, e.counters, gtid, gthreads);
+    union_items(e.row_runs, e.ndm, e.run_cap, e.run_start, e.run_end, e.run_row, e.parent, e.counters, e.lim, gtid,
+                gthreads);
   }
   if (!grid_barrier(m)) return;
   for (int b = 0; b < m.nbeams; ++b) {
     const CandBeam& e = m.beam[b];
-    flatten_items(e.row_runs, e.ndm, e.run_cap, e.run_start, e.run_end, e.parent, e.npix, e.counters, gtid, gthreads);
+    flatten_items(e.row_runs, e.ndm, e.run_cap, e.run_start, e.run_end, e.parent, e.npix, e.counters, e.lim, gtid,
+                  gthreads);
   }
   if (!grid_barrier(m)) return;
   for (int pass = 0; pass < 2; ++pass) {
@@ -625,6 +628,11 @@ __global__ void __launch_bounds__(256) k_cand_multi(const __grid_constant__ Cand
   }
   if (!grid_barrier(m)) return;
   for (int b = gtid; b < m.nbeams; b += gthreads) bump(m.beam[b].counters, m.beam[b].cand_cap);
+}
+
+// iteration bound of a union-find root walk (the plan's test limit, if set)
+int union_limit(const Plan& p) {
+  return p.loop_limit > 0 ? static_cast<int>(p.loop_limit < (1 << 20) ? p.loop_limit : (1 << 20)) : (1 << 20);
 }
 
 }  // namespace
@@ -656,10 +664,11 @@ cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_
   k_scan_rows<<<1, 1024, 0, s>>>(dp.row_runs, p.ndm, dp.counters, p.run_cap);
   k_run_write<<<wblocks, 256, 0, s>>>(dp.mask3, p.ndm, p.mw, nb, dp.row_runs, dp.run_start, dp.run_end,
                                       dp.run_row, dp.parent, dp.npix, dp.peak, dp.pwidth, p.run_cap);
+  const int lim = union_limit(p);
   k_union<<<kGridStride, 256, 0, s>>>(dp.row_runs, p.ndm, p.run_cap, dp.run_start, dp.run_end, dp.run_row,
-                                      dp.parent, dp.counters);
+                                      dp.parent, dp.counters, lim);
   k_flatten<<<kGridStride, 256, 0, s>>>(dp.row_runs, p.ndm, p.run_cap, dp.run_start, dp.run_end, dp.parent,
-                                        dp.npix, dp.counters);
+                                        dp.npix, dp.counters, lim);
   k_peak<<<kGridStride, 256, 0, s>>>(dp.cells, dp.counters, p.cell_cap, nb, dp.row_runs, p.ndm, p.run_cap,
                                      dp.run_start, dp.run_end, dp.parent, dp.peak, dp.pwidth, 0);
   k_peak<<<kGridStride, 256, 0, s>>>(dp.cells, dp.counters, p.cell_cap, nb, dp.row_runs, p.ndm, p.run_cap,
@@ -704,6 +713,7 @@ cudaError_t launch_candidates_batch(const Plan* const* plans, const ChunkPos* po
       e.cell_cap = p.cell_cap;
       e.cand_cap = p.cand_cap;
       e.n_min = p.n_min;
+      e.lim = union_limit(p);
       e.row_runs = dp.row_runs;
       e.run_start = dp.run_start;
       e.run_end = dp.run_end;
@@ -728,6 +738,7 @@ cudaError_t launch_candidates_batch(const Plan* const* plans, const ChunkPos* po
     }
     const Plan& owner = *plans[batch[i0]];
     m.gbar = owner.dp.counters + kCntGridBar;
+    m.wait_cycles = owner.loop_limit > 0 ? owner.loop_limit : kGridWaitCycles;
     const int smem = 2 * (kCloseTR + 4 * rmax) * kCloseNQ * static_cast<int>(sizeof(uint32_t));
     int dev = 0, nsm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);

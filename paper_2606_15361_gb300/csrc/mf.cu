@@ -44,6 +44,7 @@ struct MfArgs {
   int nemit;
   int out_u8;       // caller's plane in uint8 (binary / graded roots are 0..255)
   int pf_rows;      // rows resident at once: row d prefetches row d + pf_rows into L2
+  int tau_steps;    // bound of the threshold search, steps each way
 };
 
 constexpr int kMfThreads = 256;
@@ -189,15 +190,15 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
       if (est > 2147483000.0) est = 2147483000.0;
       long long sv = static_cast<long long>(est);
       int down = 0, up = 0;
-      while (sv > 0 && down < 64 && snr_of(sv - 1, mu_w, den) >= a.theta) {
+      while (sv > 0 && down < a.tau_steps && snr_of(sv - 1, mu_w, den) >= a.theta) {
         --sv;
         ++down;
       }
-      while (up < 64 && snr_of(sv, mu_w, den) < a.theta) {
+      while (up < a.tau_steps && snr_of(sv, mu_w, den) < a.theta) {
         ++sv;
         ++up;
       }
-      if (down == 64 || up == 64) atomicOr(&a.counters[kCntStatus], kStatusTauTimeout);
+      if (down == a.tau_steps || up == a.tau_steps) atomicOr(&a.counters[kCntStatus], kStatusTauTimeout);
       tau[lane] = static_cast<int>(sv);
     }
   }
@@ -390,6 +391,7 @@ bool mf_args(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64
   a.plane_out = nemit > 0 ? d_plane_out : nullptr;
   a.nemit = nemit;
   a.out_u8 = p.plane_u8;
+  a.tau_steps = p.loop_limit > 0 ? static_cast<int>(p.loop_limit < 64 ? p.loop_limit : 64) : 64;
   const int len = static_cast<int>(e_new - f_prev);
   *smem = ((len >> 2) + 3) * 16;  // front pad (4 words) and len/4 + 2 aligned groups
   return true;

@@ -200,8 +200,14 @@ extern "C" int snd_multirate_plan(const double* freqs_mhz, int32_t nchan, double
     int rc = snd_options_init(mode, &o);
     if (rc) return rc;
   }
-  MultiRate* m = new (std::nothrow) MultiRate();
-  if (!m) return SND_ERR_NOMEM;
+  MultiRate* m = nullptr;
+  try {
+    snd::alloc_point();
+    m = new MultiRate();
+  } catch (const std::bad_alloc&) {
+    return SND_ERR_NOMEM;
+  }
+  try {
   m->nchan = nchan;
   m->ndm = ndm;
   m->dt = dt_s;
@@ -277,6 +283,12 @@ extern "C" int snd_multirate_plan(const double* freqs_mhz, int32_t nchan, double
   m->off_dm = take(sizeof(double) * ndm);
   m->off_native = take(static_cast<size_t>(o.max_chunk) * nchan);
   m->ws_bytes = off;
+  snd::alloc_point();  // the band tables are complete
+  } catch (const std::bad_alloc&) {
+    for (auto& x : m->bands) snd_destroy(x.plan);
+    delete m;
+    return SND_ERR_NOMEM;
+  }
   *out = reinterpret_cast<snd_multirate_t>(m);
   return SND_OK;
 }

@@ -16,6 +16,12 @@
 // stream capture. All calls on one device share the array: the histogram is cleared at the
 // start of every call, and calls whose work overlaps on the GPU (different streams without
 // ordering) race on it and must be serialised by the caller.
+//
+// Limits: nchan <= kStaticMaxChan (the scratch size) and nsamp <= kStaticMaxSamp (the
+// pack kernel's grid height of 65535 rows of 8 words); both are checked before any work is
+// enqueued. A launch error is checked after every launch, and the call stops enqueuing at the
+// first one; like any CUDA runtime error check this also reports (and clears) a launch error
+// that earlier work on the calling thread left pending.
 
 #include <cmath>
 #include <mutex>
@@ -26,6 +32,7 @@ namespace snd {
 namespace {
 
 constexpr int kStaticMaxChan = 4096;  // largest nchan accepted
+constexpr int kStaticMaxSamp = 65535 * 8 * 32;  // largest nsamp accepted (pack grid height)
 constexpr int kStaticScratchWords = kStaticMaxChan * 256 + kStaticMaxChan;
 constexpr int kMaxDevices = 64;
 constexpr int kRowsPerBlock = 2048;
@@ -140,7 +147,7 @@ extern "C" int snd_encode_static(const uint8_t* d_chunk, int32_t nsamp, int32_t 
                                  uint32_t* d_bits_out, void* stream) {
   using namespace snd;
   if (!d_chunk || !d_bits_out || nsamp < 1 || nchan < 1 || !std::isfinite(theta)) return SND_ERR_ARG;
-  if (nchan > kStaticMaxChan) return SND_ERR_UNSUPPORTED;
+  if (nchan > kStaticMaxChan || nsamp > kStaticMaxSamp) return SND_ERR_UNSUPPORTED;
   uint32_t* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc) return rc;
@@ -151,7 +158,9 @@ extern "C" int snd_encode_static(const uint8_t* d_chunk, int32_t nsamp, int32_t 
     return SND_ERR_CUDA;
   dim3 hb(32, 8), hg((nchan + 31) / 32, (nsamp + kRowsPerBlock - 1) / kRowsPerBlock);
   k_hist_static<<<hg, hb, 0, s>>>(d_chunk, nsamp, nchan, hist);
+  if (cudaGetLastError() != cudaSuccess) return SND_ERR_CUDA;
   k_levels_static<<<(nchan + 127) / 128, 128, 0, s>>>(hist, nchan, nsamp, theta, levels);
+  if (cudaGetLastError() != cudaSuccess) return SND_ERR_CUDA;
   const int nwords = (nsamp + 31) / 32;
   dim3 pb(32, 8), pg((nchan + 31) / 32, (nwords + 7) / 8);
   k_pack_static<<<pg, pb, 0, s>>>(d_chunk, nsamp, nchan, levels, nwords, d_bits_out);

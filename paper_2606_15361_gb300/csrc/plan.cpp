@@ -11,6 +11,7 @@
 // the delay rounding and the width rule are FP64 decisions with a fixed operation order.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -46,6 +47,30 @@ void choose_direct_geometry(Plan& p);
 
 }  // namespace
 
+namespace snd {
+
+// Host allocation failure injection (snd_debug_fail_host_alloc): the allocation point that
+// finds the countdown at zero throws std::bad_alloc, as a failed allocation would, and
+// disarms it; -1 = disarmed.
+std::atomic<int> g_fail_alloc{-1};
+
+void alloc_point() {
+  int v = g_fail_alloc.load();
+  while (v >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(v, v == 0 ? -1 : v - 1)) {
+      if (v == 0) throw std::bad_alloc();
+      return;
+    }
+  }
+}
+
+}  // namespace snd
+
+extern "C" int snd_debug_fail_host_alloc(int32_t after) {
+  snd::g_fail_alloc.store(after < 0 ? -1 : after);
+  return SND_OK;
+}
+
 extern "C" int snd_options_init(snd_mode_t mode, snd_options_t* o) {
   if (!o) return SND_ERR_ARG;
   if (mode != SND_MODE_BINARY && mode != SND_MODE_GRADED && mode != SND_MODE_FLOAT && mode != SND_MODE_ZFLOAT)
@@ -74,6 +99,7 @@ namespace snd {
 
 int build_plan(Plan& p) {
   const int nchan = p.nchan, ndm = p.ndm, C = p.C, B = p.B;
+  alloc_point();  // the delay table
   // --- delays (Methods, "Incoherent dedispersion") ---
   std::vector<double> inv2(nchan);
   for (int c = 0; c < nchan; ++c) inv2[c] = 1.0 / (p.freqs[c] * p.freqs[c]);
@@ -146,6 +172,7 @@ int build_plan(Plan& p) {
   }
 
   // --- leaf patterns: distinct relative delays delta_c(d) - delta_ref(d) per leaf ---
+  alloc_point();
   p.leaf_pid.assign(static_cast<size_t>(ndm) * NL, 0);
   std::vector<int32_t> leaf_loc(static_cast<size_t>(ndm) * NL, 0);  // id local to the leaf
   p.pat_rel.clear();
@@ -182,6 +209,7 @@ int build_plan(Plan& p) {
   }
 
   // --- statistics: distinct patterns at every level, additions, Eq. hist_mem ---
+  alloc_point();
   {
     p.level_unique.assign(p.nlev, 0);
     double adds = 0.0;
@@ -250,6 +278,7 @@ int build_plan(Plan& p) {
 
   // --- DM tiles: distinct leaf patterns per (tile, leaf), per-DM index and shift, for the
   // bit-sliced tree; the labelled-payload tree has tiles of its own (and no bit ring use) ---
+  alloc_point();  // the kernel tables
   int rc = (p.mode == SND_MODE_ZFLOAT) ? choose_ztree_geometry(p) : choose_tree_geometry(p);
   if (p.mode != SND_MODE_ZFLOAT) {
     choose_direct_geometry(p);
@@ -692,8 +721,13 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
   for (int d = 0; d < ndm; ++d)
     if (!std::isfinite(dm_grid[d]) || dm_grid[d] < 0.0) return SND_ERR_DM;
 
-  Plan* p = new (std::nothrow) Plan();
-  if (!p) return SND_ERR_NOMEM;
+  Plan* p = nullptr;
+  try {
+    snd::alloc_point();
+    p = new Plan();
+  } catch (const std::bad_alloc&) {
+    return SND_ERR_NOMEM;
+  }
   try {
     p->nchan = nchan;
     p->ndm = ndm;
@@ -787,6 +821,7 @@ extern "C" int snd_plan_stats(snd_plan_t plan, snd_plan_stats_t* s) {
   }
   s->max_patterns_per_group = p.geom.max_pat_group;
   s->kernel_launches = p.launches;
+  s->device_status = static_cast<int32_t>(p.last_status);
   s->tree_kernel = (p.mode == SND_MODE_ZFLOAT) ? 3 : (p.flags & SND_FLAG_REFERENCE_TREE) ? 2 : p.direct ? 1 : 0;
   if (p.direct) {
     s->tree_tile_dms = 32;

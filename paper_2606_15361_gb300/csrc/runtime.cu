@@ -4,6 +4,8 @@
 // E = max(0, samples consumed - D) are emitted (each has its full delay history), and the
 // matched filter scores start times [F_prev, F_new) with F = max(0, E - (Wmax - 1)).
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -63,9 +65,21 @@ cudaError_t mark(Plan& p, cudaStream_t s, size_t* slot) {
   return cudaEventRecord(p.ev_pool[*slot], s);
 }
 
-// Run one stage, bracketed by an event pair when profiling.
+// Run one stage inside an NVTX range named for it (host-side enqueue time in a timeline
+// profiler), bracketed by an event pair when profiling.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+const char* stage_name(int id) {
+  static const char* const names[SND_NUM_STAGES] = {"snd.encode", "snd.tree", "snd.matched_filter", "snd.candidates"};
+  return (id >= 0 && id < SND_NUM_STAGES) ? names[id] : "snd.stage";
+}
+
 template <typename F>
 cudaError_t stage(Plan& p, int id, cudaStream_t s, F&& f) {
+  NvtxRange range(stage_name(id));
   if (!p.profiling) return f();
   size_t a = 0, b = 0;
   cudaError_t e = mark(p, s, &a);
@@ -77,6 +91,7 @@ cudaError_t stage(Plan& p, int id, cudaStream_t s, F&& f) {
 
 int run_chunk(Plan& p, const uint8_t* d_chunk, int32_t nsamp, cudaStream_t s, void* d_plane_out,
               int32_t* nemit_out) {
+  NvtxRange range("snd.execute");
   const snd::ChunkPos c = snd::chunk_pos(p, nsamp);
   cudaError_t e = stage(p, SND_STAGE_ENCODE, s, [&] { return snd::launch_encode(p, d_chunk, nsamp, s); });
   if (p.mode == SND_MODE_ZFLOAT) {
@@ -174,6 +189,12 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   p.launches = 0;
   p.ev_used = 0;
   p.ev_marks.clear();
+  return SND_OK;
+}
+
+extern "C" int snd_debug_loop_limit(snd_plan_t plan, int64_t limit) {
+  if (!plan || limit < 0) return SND_ERR_ARG;
+  reinterpret_cast<Plan*>(plan)->loop_limit = limit;
   return SND_OK;
 }
 
@@ -289,6 +310,7 @@ extern "C" int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_
   *n_out = take;
   p.pending_host = 0;
   const uint32_t st = cnt[snd::kCntStatus];
+  p.last_status = st;
   if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout | snd::kStatusTreeTimeout | snd::kStatusGridTimeout))
     return SND_ERR_TIMEOUT;
   if (st & (snd::kStatusCellOverflow | snd::kStatusRunOverflow | snd::kStatusCandOverflow |

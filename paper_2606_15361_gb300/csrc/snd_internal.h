@@ -214,6 +214,8 @@ struct Plan {
   int64_t F = 0;   // scored start times
   int sticky = 0;
   int pending_host = -1;
+  int64_t loop_limit = 0;        // test hook: bound of every bounded device loop (0 = defaults)
+  uint32_t last_status = 0;      // device status word read by the last snd_candidates
   mutable int64_t launches = 0;  // kernels enqueued since binding
 
   // host-chunk uploads (snd_execute_host): the two staging buffers are filled in turn on a
@@ -234,6 +236,9 @@ struct Plan {
 
 // plan.cpp
 int build_plan(Plan& p);
+// A host allocation point of object construction: throws std::bad_alloc when the failure
+// injection of snd_debug_fail_host_alloc reaches it (callers map that to SND_ERR_NOMEM).
+void alloc_point();
 
 // runtime.cu: the positions of one chunk (Methods, "Pipeline overview", ring-buffer form):
 // plane samples [e_prev, e_new) are emitted, start times [f_prev, f_new) scored (nb of them)

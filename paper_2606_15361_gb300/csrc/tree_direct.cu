@@ -58,6 +58,7 @@ struct DirArgs {
   int32_t* plane;
   int Lp;
   uint32_t* status;
+  long long wait_cycles;   // bound of a staging wait (clock cycles)
 };
 
 constexpr int kMaxDirBeams = 64;
@@ -93,11 +94,11 @@ __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, long long limit) {
   if (bar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!bar_try(bar, parity))
-    if (clock64() - t0 > kDirWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -479,7 +480,7 @@ __device__ __forceinline__ bool direct_cta(const DirArgs& a, int bx, int tile, u
   for (; g < ngroups; ++g) {
     const int b = (k0 + g) & 1;
     if (g + 1 < ngroups) issue(g + 1);  // buffer b ^ 1 was released by the last barrier
-    const bool ok = bar_wait(smem_u32(&bars[b]), ((k0 + g) >> 1) & 1);
+    const bool ok = bar_wait(smem_u32(&bars[b]), ((k0 + g) >> 1) & 1, a.wait_cycles);
     if (ok && busy) {
 #pragma unroll 1
       for (int h = 0; h < a.sgroups; ++h) {
@@ -506,7 +507,7 @@ __device__ __forceinline__ bool direct_cta(const DirArgs& a, int bx, int tile, u
     if (tid == 0) {
       atomicOr(a.status, kStatusTreeTimeout);
       for (int gi = g; gi < g + 2 && gi < ngroups; ++gi)
-        bar_wait(smem_u32(&bars[(k0 + gi) & 1]), ((k0 + gi) >> 1) & 1);
+        bar_wait(smem_u32(&bars[(k0 + gi) & 1]), ((k0 + gi) >> 1) & 1, kDirWaitCycles);
     }
     return false;
   }
@@ -654,6 +655,7 @@ void direct_args(const Plan& p, int64_t e_prev, int64_t e_new, DirArgs& a, int* 
   a.plane = dp.plane;
   a.Lp = p.Lp;
   a.status = dp.counters + kCntStatus;
+  a.wait_cycles = p.loop_limit > 0 ? p.loop_limit : kDirWaitCycles;
   *ntx = (a.nwords + g.tile_words - 1) / g.tile_words;
 }
 

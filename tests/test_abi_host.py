@@ -193,3 +193,54 @@ def test_uint8_plane_option(snd):
     assert _plan_rc(snd, f, d, mode=snd.MODE_FLOAT, opts=snd.options(snd.MODE_FLOAT, plane_dtype=1)) == E["SND_ERR_ARG"]
     assert _plan_rc(snd, f, d, mode=snd.MODE_GRADED, opts=snd.options(snd.MODE_GRADED, plane_dtype=2)) == E["SND_ERR_ARG"]
     assert ctypes.sizeof(snd.SndOptions) % 8 == 0 and snd.options(snd.MODE_BINARY).plane_dtype == 0
+
+
+def test_injected_host_allocation_failures_return_nomem(snd):
+    """Every host allocation point of plan, multi-rate plan and batch construction, made to
+    fail in turn by the injection hook, gives SND_ERR_NOMEM and no object; once the countdown
+    passes the last point the call succeeds (the hook disarms itself after firing)."""
+    E = snd.ERR
+    f = synth.channel_freqs(64)
+    d = np.linspace(0, 80, 40)
+    try:
+        k = 0
+        while True:
+            snd.lib.snd_debug_fail_host_alloc(k)
+            rc = _plan_rc(snd, f, d, mode=snd.MODE_FLOAT)
+            if rc == 0:
+                break
+            assert rc == E["SND_ERR_NOMEM"], (k, rc)
+            k += 1
+        assert k >= 5  # the plan object, delays, leaf patterns, statistics, kernel tables
+        snd.lib.snd_debug_fail_host_alloc(-1)  # the countdown outlived the last point: disarm
+        # multi-rate plan (its band plans included)
+        fp = np.ascontiguousarray(f)
+        dp = ctypes.POINTER(ctypes.c_double)
+        dm = np.ascontiguousarray(np.linspace(0, 600, 64))
+        k = 0
+        while True:
+            snd.lib.snd_debug_fail_host_alloc(k)
+            h = ctypes.c_void_p()
+            o = snd.options(snd.MODE_GRADED, max_chunk=4096)
+            rc = snd.lib.snd_multirate_plan(fp.ctypes.data_as(dp), 64, 1.38e-4, dm.ctypes.data_as(dp), dm.size, 2,
+                                            snd.MODE_GRADED, ctypes.byref(o), 16, ctypes.byref(h))
+            if rc == 0:
+                snd.lib.snd_multirate_destroy(h)
+                break
+            assert rc == E["SND_ERR_NOMEM"] and not h.value, (k, rc)
+            k += 1
+        assert k >= 3
+        snd.lib.snd_debug_fail_host_alloc(-1)
+        # batch of two plans
+        plans = [snd.Plan(f, 1.38e-4, d, 2, snd.MODE_FLOAT, bind=False) for _ in range(2)]
+        arr = (ctypes.c_void_p * 2)(plans[0].handle.value, plans[1].handle.value)
+        for k in range(2):
+            snd.lib.snd_debug_fail_host_alloc(k)
+            b = ctypes.c_void_p()
+            assert snd.lib.snd_batch_create(arr, 2, ctypes.byref(b)) == E["SND_ERR_NOMEM"] and not b.value
+        snd.lib.snd_debug_fail_host_alloc(-1)
+        b = ctypes.c_void_p()
+        assert snd.lib.snd_batch_create(arr, 2, ctypes.byref(b)) == 0
+        snd.lib.snd_batch_destroy(b)
+    finally:
+        snd.lib.snd_debug_fail_host_alloc(-1)

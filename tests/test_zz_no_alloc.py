@@ -3,14 +3,18 @@ that cannot call cudaMalloc). Its spike raster must equal the one the regular st
 entry point (snd_execute) produces. With one channel, one trial DM of 0 and float mode the
 plane snd_execute writes is exactly the channel's spike train (the tree is a single leaf,
 the delay is 0 and 1/sqrt(N_f) = 1), so every channel is checked against its own
-single-channel plan. Two calls in a row, on different chunks, check that the shared scratch
-starts clean each time. This file is collected last on purpose."""
+single-channel plan, and against the oracle's encoder (oracle.encoder.encode_chunk). Two calls
+in a row, on different chunks, check that the shared scratch starts clean each time. The
+largest accepted channel count (4096, whose histogram fills the scratch up to the levels) and
+a multiple of 32 over several channel blocks are covered too. This file is collected last on
+purpose."""
 import ctypes
 
 import numpy as np
 import pytest
 
 import synth
+from oracle import encoder as oenc
 
 pytestmark = pytest.mark.gpu
 
@@ -57,11 +61,32 @@ def test_encode_static_matches_execute(theta):
         assert not got[3].any()
         for c in range(nchan):
             assert (got[c] == _execute_single_channel(data[:, c], theta)).all(), (call, c)
+        assert (got == oenc.encode_chunk(data, theta)[0]).all()
 
 
-def test_encode_static_rejects_too_many_channels():
+@pytest.mark.parametrize("nchan,nsamp", [(96, 2500), (4096, 300)])
+def test_encode_static_channel_blocks_and_largest_size(nchan, nsamp):
+    """96 channels: three full 32-channel blocks; 4096: the largest accepted, its histogram
+    ends where the levels begin. Two calls in a row; every channel against the oracle, a
+    spread of channels (the last ones included) against single-channel snd_execute plans."""
+    freqs = synth.channel_freqs(nchan)
+    for call in range(2):
+        data = synth.filterbank_chunk(70 + call, 0, 0, nsamp, freqs, synth.NC_DT, [])
+        data[::5, -1] = 250
+        got = _encode_static(torch.from_numpy(data).cuda(), 1.5)
+        assert (got == oenc.encode_chunk(data, 1.5)[0]).all()
+        for c in sorted({0, 31, 32, nchan // 2, nchan - 2, nchan - 1}):
+            assert (got[c] == _execute_single_channel(data[:, c], 1.5)).all(), (call, c)
+
+
+def test_encode_static_rejects_sizes_beyond_its_limits():
     chunk = torch.zeros((64, 4097), dtype=torch.uint8, device="cuda")
     bits = torch.zeros((4097, 2), dtype=torch.int32, device="cuda")
     rc = g.lib.snd_encode_static(ctypes.c_void_p(chunk.data_ptr()), 64, 4097, 1.5, ctypes.c_void_p(bits.data_ptr()),
                                  None)
+    assert rc == g.ERR["SND_ERR_UNSUPPORTED"]
+    # too many samples: rejected before any work is enqueued, so the (small) buffers are
+    # never read or written
+    rc = g.lib.snd_encode_static(ctypes.c_void_p(chunk.data_ptr()), 65535 * 256 + 1, 1, 1.5,
+                                 ctypes.c_void_p(bits.data_ptr()), None)
     assert rc == g.ERR["SND_ERR_UNSUPPORTED"]
