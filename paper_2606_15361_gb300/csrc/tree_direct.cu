@@ -94,10 +94,24 @@ __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// non-blocking probe of a phase (try_wait above may suspend the thread for a while first)
+__device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a phase. With a bound below the default (the loop-limit test hook) the wait
+// only polls, so the bound is all the time it may take.
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, long long limit) {
-  if (bar_try(bar, parity)) return true;
+  const bool poll = limit < kDirWaitCycles;
+  if (poll ? bar_test(bar, parity) : bar_try(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!bar_try(bar, parity))
+  while (!(poll ? bar_test(bar, parity) : bar_try(bar, parity)))
     if (clock64() - t0 > limit) return false;
   return true;
 }
