@@ -35,9 +35,16 @@ W = synth.NC1024
 MODES = (("binary", 0), ("graded", 1), ("float", 2))
 BRANCHING = 8
 TREE_BYTES_PER_DM_SAMPLE = W.nchan / W.ndm + 4.0  # uint8 input read once + int32 plane written once
-# Integer ALU ceiling of the tree: 152 SMs x 4 schedulers x 32 lanes, one 32-bit integer
-# instruction per lane per cycle, at the 2070 MHz maximum SM clock (Gop/s)
-ALU_PEAK_GOPS = 152 * 4 * 32 * 2070e6 / 1e9
+# ALU-pipe ceiling of the bit-sliced tree. The logic and shift instructions that make up the
+# tree's arithmetic (LOP3, SHF) issue on each SM sub-partition's ALU pipe at 16 lanes per cycle
+# (ncu's pipe_alu peak of 0.5 warp-instructions per cycle), so a GPU retires
+# SMs x 4 x 16 x clock of them per second. The work the direct kernel cannot avoid, in those
+# operations per DM-sample (a 32-sample word per operation):
+#   float / graded: per channel one funnel shift (align the channel's word to the DM's delay)
+#     and one carry-save full adder (two LOP3) -> 3 N_f / 32;
+#   binary (C = 4): per leaf four funnel shifts, the quorum (three LOP3) and the parent's
+#     thermometer (two LOP3) -> 9 N_f / (4 * 32).
+ALU_LANES_PER_SM_CYCLE = 4 * 16
 DATA_NOTE = "synthetic: seeded rint(N(128,16)) uint8 noise + 200 injected dispersed bursts"
 
 
@@ -108,7 +115,7 @@ class ClockSampler:
 def _traffic_from_profile(src_hash: str):
     """DRAM bytes per tree launch from the committed ncu summary, if it was taken on this
     exact tree kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_tree_nc1024_2048dm.md")
+    path = os.path.join(ROOT, "profiles", "k_snd_nc1024_2048dm.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -129,7 +136,7 @@ def _traffic_from_profile(src_hash: str):
 def _tree_source_hash() -> str:
     import hashlib
     h = hashlib.sha1()
-    for f in ("tree.cu", "snd_internal.h"):
+    for f in ("tree_direct.cu", "snd_internal.h"):
         with open(os.path.join(ROOT, "paper_2606_15361_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -373,6 +380,83 @@ def branching_sweep(g, args, dev, dchunks, freqs, dms, branchings=(2, 4, 8)):
         out[str(B)] = row
     out["note"] = ("tree stage per chunk (CUDA events), 5 steady chunks after 3 warm-up; hbm_frac of the measured "
                    f"copy bandwidth ({src})")
+    return out
+
+
+def stress_rate(g, args, dev, nbeams=16):
+    """Stress scale (4096 channels 400-416 MHz, dt 0.138 ms, 8192 DMs over 0-3000, 1 s chunks
+    of 7246 samples, B = 4; graded and float): per mode, one beam's tree time per chunk and its
+    HBM fraction on 4.5 B per DM-sample, and the L2-residency sweep: steps of k = 1..16 beams
+    advanced together through the batch API (the bit rings of k beams, 26 MB each, are the
+    working set the 129 MB L2 holds or not), in whole-step DM-samples per second."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    w = synth.NC4096
+    freqs, dms = w.freqs(), w.dms()
+    peaks, src = _peaks()
+    gen = torch.Generator(device=dev).manual_seed(500)
+    data = [[torch.randn((w.chunk, w.nchan), generator=gen, device=dev).mul_(16).add_(128).round_().clamp_(0, 255)
+             .to(torch.uint8) for _ in range(2)] for _ in range(nbeams)]
+    fill = int(np.ceil(4.148808e3 * w.dm_max * (freqs.min() ** -2 - freqs.max() ** -2) / synth.NC_DT / w.chunk)) + 1
+    bpu = w.nchan / w.ndm + 4.0
+    out = {"beams": nbeams, "nchan": w.nchan, "ndm": w.ndm, "chunk": w.chunk, "branching": w.branching}
+    for name, m in (("graded", 1), ("float", 2)):
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=min(nbeams, os.cpu_count() or 1)) as ex:
+            plans = list(ex.map(lambda _: g.Plan(freqs, synth.NC_DT, dms, w.branching, m,
+                                                 g.options(m, max_chunk=w.chunk), bind=False), range(nbeams)))
+        build_s = time.perf_counter() - t0
+        for p in plans:
+            p.bind(device=dev)
+        # one beam alone: tree time per steady chunk
+        p0 = plans[0]
+        for k in range(fill):
+            p0.execute(data[0][k % 2])
+        p0.profile(True)
+        p0.profile_read()
+        for k in range(4):
+            p0.execute(data[0][k % 2])
+        prof = p0.profile_read()
+        p0.profile(False)
+        tms = prof["tree"][0] / max(prof["tree"][1], 1)
+        ach = bpu * w.chunk * w.ndm / (tms / 1e3) / 1e9
+        row = {"plan_build_s": round(build_s, 2), "tree_ms_per_chunk": round(tms, 4),
+               "tree_gdm_samples_per_s": round(w.chunk * w.ndm / (tms / 1e3) / 1e9, 2),
+               "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": ach / peaks["hbm_gbs"], "peak_source": src,
+                            "algorithmic_bytes_per_dm_sample": bpu},
+               "stage_ms_per_chunk": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items()}}
+        sweep = {}
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in (1, 2, 4, 8, 16):
+            if k > nbeams:
+                break
+            for p in plans[:k]:
+                p.bind(device=dev)
+            batch = g.Batch(plans[:k])
+            for s in range(fill):
+                batch.execute([data[i][s % 2] for i in range(k)])
+            torch.cuda.synchronize(dev)
+            ev0.record()
+            steps = 4
+            for s in range(steps):
+                batch.execute([data[i][s % 2] for i in range(k)])
+            ev1.record()
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1) / steps
+            sweep[str(k)] = {"ms_per_step": round(ms, 3),
+                             "gdm_samples_per_s": round(k * w.chunk * w.ndm / (ms / 1e3) / 1e9, 2),
+                             "ring_mb_resident": round(k * w.nchan * p0.stats().ring_words * 4 / 1e6, 1)}
+            for p in plans[:k]:
+                p.candidates(check=False)
+            del batch
+        row["l2_residency_sweep"] = sweep
+        out[name] = row
+        del plans
+        torch.cuda.empty_cache()
+    out["note"] = ("random-noise beams (throughput only; parity of this shape is tests/test_gpu_fullsize.py); "
+                   "graded saturates at N = 255 at 4096 channels; ring_mb_resident = one copy of every beam's "
+                   "bit ring")
     return out
 
 
@@ -645,6 +729,7 @@ def run_gpu(args, rank, world, local_rank):
     extras = rank == 0 and not args.main_only
     mr = multirate_rate(g, args, dev, stream, dchunks, freqs, dms) if extras else None
     bsw = branching_sweep(g, args, dev, dchunks, freqs, dms) if extras else None
+    c5 = stress_rate(g, args, dev) if extras and not args.no_stress else None
     zf = zfloat_rate(g, args, dev, dchunks, freqs, dms) if extras else None
     sft = sifter_rate(g, args, dev) if extras and not args.no_sifter else None
     mb = multibeam_rate(g, args, dev) if extras and not args.no_multibeam else None
@@ -665,9 +750,12 @@ def run_gpu(args, rank, world, local_rank):
     units = W.chunk * W.ndm
     achieved = TREE_BYTES_PER_DM_SAMPLE * units / (tree_launch_ms / 1e3) / 1e9
     per_mode = {}
-    # the tree's algorithmic integer work: the plan's additions per DM-sample with leaf-pattern
-    # sharing (the same count for the three modes of one plan geometry)
-    adds = {n: float(plans[n].stats().adds_per_dm_sample) for n in prof}
+    # the tree's algorithmic ALU work per DM-sample (see ALU_LANES_PER_SM_CYCLE) against the
+    # ALU-pipe ceiling of this GPU at the maximum SM clock
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    alu_peak = props.multi_processor_count * ALU_LANES_PER_SM_CYCLE * sm_max * 1e6 / 1e9  # Gop/s
+    adds = {n: (9.0 * W.nchan / 128.0 if n == "binary" else 3.0 * W.nchan / 32.0) for n in prof}
     for n in prof:
         st = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof[n].items()}
         tms = prof[n]["tree"][0] / max(prof[n]["tree"][1], 1)
@@ -675,7 +763,7 @@ def run_gpu(args, rank, world, local_rank):
                        "tree_gdm_samples_per_s": round(units / (tms / 1e3) / 1e9, 2),
                        "tree_hbm_frac": round(TREE_BYTES_PER_DM_SAMPLE * units / (tms / 1e3) / 1e9 /
                                               peaks["hbm_gbs"], 4),
-                       "tree_alu_frac": round(adds[n] * units / (tms / 1e3) / 1e9 / ALU_PEAK_GOPS, 4),
+                       "tree_alu_frac": round(adds[n] * units / (tms / 1e3) / 1e9 / alu_peak, 4),
                        "pipeline_gdm_samples_per_s": round(units / (sum(v[0] for v in prof[n].values()) /
                                                                     max(prof[n]["tree"][1], 1) / 1e3) / 1e9, 2)}
     adds_mean = sum(adds.values()) / max(len(adds), 1)
@@ -700,14 +788,16 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": "k_tree (SND tree, all modes, average launch, sequential pass)",
+                     "kernel": "k_snd (SND tree, all modes, average launch, sequential pass)",
                      "peak_source": src, "algorithmic_bytes_per_dm_sample": TREE_BYTES_PER_DM_SAMPLE},
         "roofline_alu": {"bound": "alu", "achieved": adds_mean * units / (tree_launch_ms / 1e3) / 1e9,
-                         "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
-                         "frac": adds_mean * units / (tree_launch_ms / 1e3) / 1e9 / ALU_PEAK_GOPS,
-                         "kernel": "k_tree (SND tree, all modes, average launch, sequential pass)",
+                         "peak": alu_peak, "unit": "Gop/s",
+                         "frac": adds_mean * units / (tree_launch_ms / 1e3) / 1e9 / alu_peak,
+                         "kernel": "k_snd (SND tree, all modes, average launch, sequential pass)",
                          "algorithmic_ops_per_dm_sample": adds_mean,
-                         "peak_source": "derived: 152 SMs x 128 int32 lanes x 2070 MHz"},
+                         "peak_source": (f"derived: {props.multi_processor_count} SMs x 4 sub-partitions x 16 ALU lanes "
+                                         f"(LOP3/SHF) x {sm_max:.0f} MHz; ops = funnel shifts + carry-save adders "
+                                         "(float/graded 3 N_f/32, binary 9 N_f/128 per DM-sample)")},
         "per_mode": per_mode,
         "sequential_pass": {"value": whole_job_rate(per_step, args.steps, world, ms_seq), "unit": "DM-samples/s",
                             "ms_per_step": ms_seq / args.steps,
@@ -719,6 +809,7 @@ def run_gpu(args, rank, world, local_rank):
         "realtime_beams_per_mode": realtime_beams,
         "multirate": mr,
         "branching_sweep": bsw,
+        "stress_nc4096": c5,
         "zfloat_precision_study": zf,
         "learned_sifter": sft,
         "multibeam": mb,
@@ -789,6 +880,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sifter", action="store_true", help="skip the learned-sifter measurements")
     ap.add_argument("--no-multibeam", action="store_true", help="skip the 48-beam batch measurements")
+    ap.add_argument("--no-stress", action="store_true", help="skip the 16-beam 4096-channel stress measurements")
     ap.add_argument("--sequential", action="store_true",
                     help="headline pass with the three modes in sequence on one stream (default: own streams)")
     ap.add_argument("--main-only", action="store_true",

@@ -72,6 +72,10 @@ typedef struct snd_plan_s* snd_plan_t;
  * tile evaluated once, then gathered per DM) even where the direct kernel applies. Results
  * are identical; it keeps the paper's shared-leaf evaluation available for comparison. */
 #define SND_FLAG_LEAF_SHARING 4
+/* Option flag (SND_MODE_ZFLOAT only): the payload of a spike is 1 (the paper's own 0/1 raster)
+ * instead of z, so every node holds a spike count and the storage type alone decides the
+ * plane's error (FP16 holds every count up to 2048 exactly). */
+#define SND_FLAG_UNIT_PAYLOAD 16
 
 /*
  * Options. Fill with snd_options_init(mode, &o) (Supplementary Table S1 operating point
@@ -93,7 +97,7 @@ typedef struct {
   int32_t cell_capacity;    /* mask cells with S/N kept per matched-filter block */
   int32_t run_capacity;     /* closed-mask runs per matched-filter block */
   int32_t flags;            /* 0 or SND_FLAG_REFERENCE_TREE / SND_FLAG_LEAF_SHARING, or
-                               SND_FLAG_FP16_PARTIALS (zfloat) */
+                               SND_FLAG_FP16_PARTIALS / SND_FLAG_UNIT_PAYLOAD (zfloat) */
   int32_t plane_dtype;      /* d_plane_out element type: 0 = int32 / float32 (default); 1 = uint8,
                                binary and graded modes only (their roots are 0..255) */
 } snd_options_t;

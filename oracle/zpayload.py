@@ -30,9 +30,10 @@ from . import encoder as enc_mod
 from . import tree as tree_mod
 
 
-def payload_table(chunk, theta: float):
+def payload_table(chunk, theta: float, unit: bool = False):
     """(z64 float64[nchan][256], u int64[nchan]): the FP64 payload of every uint8 value
-    per channel (0 below the level u_c), from the chunk's clipped statistics."""
+    per channel (0 below the level u_c), from the chunk's clipped statistics. With
+    ``unit`` the payload of a spike is 1: the paper's own 0/1 raster."""
     chunk = np.asarray(chunk, dtype=np.uint8)
     nchan = chunk.shape[1]
     z = np.zeros((nchan, 256), dtype=np.float64)
@@ -42,7 +43,7 @@ def payload_table(chunk, theta: float):
         mu, sigma, _, _ = enc_mod.channel_stats(chunk[:, c])
         u[c] = enc_mod.level_from_stats(mu, sigma, theta)
         if u[c] < 256:
-            z[c, u[c]:] = (v[u[c]:] - mu) / sigma
+            z[c, u[c]:] = 1.0 if unit else (v[u[c]:] - mu) / sigma
     return z, u
 
 
@@ -88,7 +89,9 @@ class ZStream:
     plane (`store` = np.float16 or np.float32) and the FP64 reference, for the same rows
     and emission rule as the main path (E = max(0, samples consumed - D))."""
 
-    def __init__(self, freqs, dt: float, dms, cluster: int, branching: int, theta: float, store, rows=None):
+    def __init__(self, freqs, dt: float, dms, cluster: int, branching: int, theta: float, store, rows=None,
+                 unit: bool = False):
+        self.unit = bool(unit)
         self.freqs = np.asarray(freqs, dtype=np.float64)
         self.delays = delays_mod.delay_table(self.freqs, float(dt), np.asarray(dms, dtype=np.float64))
         self.D = int(self.delays.max()) if self.delays.size else 0
@@ -104,7 +107,7 @@ class ZStream:
 
     def push(self, chunk) -> dict:
         chunk = np.asarray(chunk, dtype=np.uint8)
-        z64, u = payload_table(chunk, self.theta)
+        z64, u = payload_table(chunk, self.theta, self.unit)
         self.xs = np.concatenate([self.xs, payload(chunk, z64.astype(self.store))], axis=1)
         self.x64 = np.concatenate([self.x64, payload(chunk, z64)], axis=1)
         e_new = max(0, self.T + chunk.shape[0] - self.D)

@@ -19,6 +19,7 @@ MODE_BINARY, MODE_GRADED, MODE_FLOAT, MODE_ZFLOAT = 0, 1, 2, 3
 FLAG_REFERENCE_TREE = 1
 FLAG_FP16_PARTIALS = 2
 FLAG_LEAF_SHARING = 4
+FLAG_UNIT_PAYLOAD = 16
 TREE_KERNELS = {0: "leaf-sharing k_tree", 1: "direct k_snd", 2: "reference k_tree_ref", 3: "labelled-payload k_tree_z"}
 
 STATUS = {

@@ -57,9 +57,10 @@ __global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk,
 // and v > hi <=> v > floor(hi), and the smallest integer above thr is floor(thr) + 1, so the
 // clip bounds and the level are exact integer decisions.
 // With ztab set (labelled payload), every lane also writes the payload of its 8 values,
-// z = (v - mu)/sigma in FP64 for v >= u (0 below), rounded once to FP16 (zfp16) or FP32.
+// z = (v - mu)/sigma in FP64 for v >= u (0 below), rounded once to FP16 (zmode bit 0) or FP32;
+// with zmode bit 1 (the paper's own 0/1 spike payload) z = 1 for v >= u instead.
 __device__ __forceinline__ void levels_warp(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
-                                            int32_t* __restrict__ levels, void* __restrict__ ztab, int zfp16,
+                                            int32_t* __restrict__ levels, void* __restrict__ ztab, int zmode,
                                             const int c, const int lane) {
   if (c >= nchan) return;
   uint32_t* h = hist + static_cast<size_t>(c) * 256;
@@ -129,8 +130,8 @@ __device__ __forceinline__ void levels_warp(uint32_t* __restrict__ hist, int nch
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int v = lane + 32 * k;
-      const double z = (v >= u) ? __ddiv_rn(__dsub_rn(static_cast<double>(v), mu), sig) : 0.0;
-      if (zfp16) {
+      const double z = (v >= u) ? ((zmode & 2) ? 1.0 : __ddiv_rn(__dsub_rn(static_cast<double>(v), mu), sig)) : 0.0;
+      if (zmode & 1) {
         static_cast<__half*>(ztab)[static_cast<size_t>(c) * 256 + v] = __double2half(z);
       } else {
         static_cast<float*>(ztab)[static_cast<size_t>(c) * 256 + v] = __double2float_rn(z);
@@ -140,8 +141,8 @@ __device__ __forceinline__ void levels_warp(uint32_t* __restrict__ hist, int nch
 }
 
 __global__ void __launch_bounds__(256) k_levels(uint32_t* __restrict__ hist, int nchan, int nsamp, double theta,
-                                                int32_t* __restrict__ levels, void* __restrict__ ztab, int zfp16) {
-  levels_warp(hist, nchan, nsamp, theta, levels, ztab, zfp16, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                                                int32_t* __restrict__ levels, void* __restrict__ ztab, int zmode) {
+  levels_warp(hist, nchan, nsamp, theta, levels, ztab, zmode, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
               threadIdx.x & 31);
 }
 
@@ -322,7 +323,7 @@ cudaError_t launch_encode(const Plan& p, const uint8_t* d_chunk, int nsamp, cuda
   k_hist<<<hg, hb, 0, s>>>(d_chunk, nsamp, p.nchan, dp.hist);
   const bool z = p.mode == SND_MODE_ZFLOAT;
   k_levels<<<(p.nchan * 32 + 255) / 256, 256, 0, s>>>(dp.hist, p.nchan, nsamp, p.enc_theta, dp.levels,
-                                                      z ? dp.ztab : nullptr, p.zgeom.fp16);
+                                                      z ? dp.ztab : nullptr, p.zgeom.fp16 | (p.zgeom.unit << 1));
   const long long t0 = p.T;
   if (z) {
     dim3 zb(32, 8), zg((p.nchan + 31) / 32, (nsamp + 255) / 256);

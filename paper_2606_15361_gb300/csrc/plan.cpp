@@ -622,6 +622,7 @@ int choose_ztree_geometry(Plan& p) {
   const int ndm = p.ndm, nchan = p.nchan, NL = p.nleaves;
   if (p.nlev > 16) return SND_ERR_UNSUPPORTED;
   z.fp16 = (p.flags & SND_FLAG_FP16_PARTIALS) ? 1 : 0;
+  z.unit = (p.flags & SND_FLAG_UNIT_PAYLOAD) ? 1 : 0;
   z.maxl = p.nlev <= 4 ? 4 : (p.nlev <= 8 ? 8 : 16);
   z.spt = z.maxl == 4 ? 8 : (z.maxl == 8 ? 4 : 2);
   z.dms_per_cta = 16;
@@ -693,8 +694,9 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
   } else {
     snd_options_init(mode, &o);
   }
-  if (o.flags & ~(SND_FLAG_REFERENCE_TREE | SND_FLAG_FP16_PARTIALS | SND_FLAG_LEAF_SHARING)) return SND_ERR_ARG;
-  if ((o.flags & SND_FLAG_FP16_PARTIALS) && mode != SND_MODE_ZFLOAT) return SND_ERR_ARG;
+  if (o.flags & ~(SND_FLAG_REFERENCE_TREE | SND_FLAG_FP16_PARTIALS | SND_FLAG_LEAF_SHARING | SND_FLAG_UNIT_PAYLOAD))
+    return SND_ERR_ARG;
+  if ((o.flags & (SND_FLAG_FP16_PARTIALS | SND_FLAG_UNIT_PAYLOAD)) && mode != SND_MODE_ZFLOAT) return SND_ERR_ARG;
   if ((o.flags & SND_FLAG_REFERENCE_TREE) && mode == SND_MODE_ZFLOAT) return SND_ERR_UNSUPPORTED;
   if (o.cluster_size < 1 || o.cluster_size > 7) return SND_ERR_UNSUPPORTED;
   if (mode == SND_MODE_BINARY && (o.k_leaf < 1 || o.k_leaf > 8 || o.k_internal < 1 || o.k_internal > 8))

@@ -90,6 +90,7 @@ struct DirectGeom {
 // Labelled-payload (zfloat) tree geometry (chosen on the host).
 struct ZGeom {
   int fp16;           // payload and partial sums stored in FP16 (else FP32)
+  int unit;           // payload 1 for every spike (the paper's 0/1 raster) instead of z
   int maxl;           // level capacity of the kernel instantiation (4, 8, 16)
   int spt;            // output samples per lane
   int dms_per_cta;    // DM rows per CTA (one warp each)

@@ -87,3 +87,33 @@ def test_nc1024_full_size_sampled_rows(store):
           f"median {np.median(e['max_abs']):.3e} max {e['max_abs'].max():.3e}; max_rel_to_peak "
           f"median {np.median(e['max_rel_to_peak']):.3e} max {e['max_rel_to_peak'].max():.3e}")
     assert e["max_rel_to_peak"].max() < (2e-3 if store == "fp16" else 1e-6)
+
+
+@pytest.mark.parametrize("store", list(STORES))
+def test_unit_payload_4100_channels_rounds_above_2048(store):
+    """The paper's own 0/1 payload (SND_FLAG_UNIT_PAYLOAD) on 4100 channels with B = 2: the
+    root's first child holds 4096 channels and is stored. At theta = -2 almost every channel
+    fires, so its count passes 2048 and FP16 storage rounds it (ties to even) exactly as the
+    oracle's stored-sum tree does; FP32 storage keeps the count. Bit-identical planes."""
+    nchan = 4100
+    freqs = synth.channel_freqs(nchan)
+    dms = np.linspace(0.0, 6.0, 5)
+    rng = np.random.default_rng(41)
+    data = np.clip(np.rint(rng.normal(128, 16, (1500, nchan))), 0, 255).astype(np.uint8)
+    st, flag = STORES[store]
+    o = g.options(g.MODE_ZFLOAT, cluster_size=4, enc_theta=-2.0, flags=flag | g.FLAG_UNIT_PAYLOAD, max_chunk=1000)
+    plan = g.Plan(freqs, synth.NC_DT, dms, 2, g.MODE_ZFLOAT, o)
+    ref = oz.ZStream(freqs, synth.NC_DT, dms, 4, 2, -2.0, st, unit=True)
+    rounded = 0
+    for ch in (data[:700], data[700:]):
+        ne = plan.nemit_next(ch.shape[0])
+        out = torch.full((len(dms), max(ne, 1)), float("nan"), dtype=torch.float32, device="cuda")
+        assert plan.execute(torch.from_numpy(np.ascontiguousarray(ch)).cuda(), out) == ne
+        r = ref.push(ch)
+        if ne:
+            got = out[:, :ne].cpu().numpy()
+            assert (got.view(np.uint32) == r["plane"].view(np.uint32)).all()
+            exact = (np.rint(r["plane64"] * np.sqrt(float(nchan))).astype(np.float32) *
+                     oz.plane_scale(nchan)).astype(np.float32)
+            rounded += int((got != exact).sum())
+    assert (rounded > 0) == (store == "fp16")

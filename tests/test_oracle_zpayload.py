@@ -153,3 +153,45 @@ def test_zstream_emits_like_main_path_and_reports_error():
                        axis=1)
     t0, t1 = r2["e_prev"], r2["e_new"]
     assert np.allclose(r2["plane64"][0], x[:, t0:t1].sum(axis=0) / math.sqrt(64), rtol=1e-12, atol=0)
+
+
+def test_unit_payload_is_the_paper_raster():
+    """With the unit payload (the paper's 0/1 spikes) the stored-sum tree is the spike count:
+    FP32 storage gives fp32(count) * fp32(1/sqrt(N_f)) for any tree, FP16 storage too while no
+    stored node holds more than 2048 channels."""
+    w = synth.NC64
+    data = w.chunk_data(0)[:3000]
+    freqs, dms = w.freqs(), w.dms()[:12]
+    tab = odelays.delay_table(freqs, synth.NC_DT, dms)
+    x = oenc.encode_chunk(data, 1.5)[0]
+    D = int(tab.max())
+    counts = otree.snd_rows(x, 0, tab, range(12), 0, 3000 - D, otree.FLOAT, 4, 2)
+    for st in (np.float16, np.float32):
+        r = oz.ZStream(freqs, synth.NC_DT, dms, 4, 2, 1.5, st, unit=True).push(data)
+        exp = (counts.astype(np.float32) * oz.plane_scale(64)).astype(np.float32)
+        assert r["e_new"] == 3000 - D and (r["plane"] == exp).all()
+
+
+def test_unit_payload_fp16_rounds_nodes_above_2048():
+    """4100 channels, B = 2: the root's first child holds 4096 channels and is stored. At
+    theta = -2 almost every channel fires, so that child's count exceeds 2048 and FP16 storage
+    rounds it to an even number (ties to even); FP32 storage keeps the exact count."""
+    nchan = 4100
+    freqs = synth.channel_freqs(nchan)
+    dms = np.array([0.0, 3.0])
+    rng = np.random.default_rng(4)
+    data = np.clip(np.rint(rng.normal(128, 16, (300, nchan))), 0, 255).astype(np.uint8)
+    r16 = oz.ZStream(freqs, synth.NC_DT, dms, 4, 2, -2.0, np.float16, unit=True).push(data)
+    r32 = oz.ZStream(freqs, synth.NC_DT, dms, 4, 2, -2.0, np.float32, unit=True).push(data)
+    sc = oz.plane_scale(nchan)
+    count32 = np.rint(r32["plane"].astype(np.float64) / float(sc))
+    exact = np.rint(r32["plane64"] * np.sqrt(float(nchan)))
+    assert (count32 == exact).all() and exact.min() > 2048 + 4
+    x = oenc.encode_chunk(data, -2.0)[0]
+    tab = odelays.delay_table(freqs, synth.NC_DT, dms)
+    n = r16["e_new"]
+    a_first = otree.snd_rows(x[:4096], 0, tab[:, :4096], [0, 1], 0, n, otree.FLOAT, 4, 2)
+    a_rest = otree.snd_rows(x[4096:], 0, tab[:, 4096:], [0, 1], 0, n, otree.FLOAT, 4, 2)
+    want16 = (a_first.astype(np.float16).astype(np.float32) + a_rest.astype(np.float32)) * sc
+    assert (r16["plane"] == want16.astype(np.float32)).all()
+    assert (r16["plane"] != r32["plane"]).any()
