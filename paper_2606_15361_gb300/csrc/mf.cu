@@ -45,14 +45,16 @@ struct MfArgs {
   int out_u8;       // caller's plane in uint8 (binary / graded roots are 0..255)
   int pf_rows;      // rows resident at once: row d prefetches row d + pf_rows into L2
   int tau_steps;    // bound of the threshold search, steps each way
+  int nowrap;       // every prefix sum of the staged segment is below 2^31 (no wrap-around)
 };
 
 constexpr int kMfThreads = 256;
 constexpr uint32_t kAllWidths = (1u << kNumWidthSlots) - 1u;
 
-template <bool A>
-struct WidthSet {  // tag: every width slot of the row is in use (A) or not known to be
-  static constexpr bool kAll = A;
+template <bool A, bool NW = false>
+struct WidthSet {  // tag: every width slot of the row is in use (A) or not known to be; prefix
+  static constexpr bool kAll = A;     // sums that never wrap (NW)
+  static constexpr bool kNoWrap = NW;
 };
 
 __device__ __forceinline__ double snr_of(long long s, double mu_w, double den) {
@@ -256,13 +258,21 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
   //    the wrapped difference P[t+W] - P[t] - tau_W read as int32 is exact. Eight lanes'
   //    nibbles make one mask word.
   // hit nibble of start times 4m..4m+3 (bit e: start time 4m + e passes)
+  // Without wrap-around (prefix sums below 2^31, the usual case) the test is rearranged as
+  // max over W of (P[t+W] - tau_W) >= P[t]: one add-and-max per (start time, width), which
+  // the compiler can issue as a single three-input integer instruction.
   auto group_hits = [&](int m, auto all) -> uint32_t {
     constexpr bool ALL = decltype(all)::kAll;
+    constexpr bool NOWRAP = decltype(all)::kNoWrap;
     const uint4 p = P4[m];
     const uint4 q = P4[m + 1];
     int h0 = INT_MIN, h1 = INT_MIN, h2 = INT_MIN, h3 = INT_MIN;
     auto upd = [](int& h, uint32_t end, uint32_t start, int tj) {
-      h = max(h, static_cast<int>(end - start - static_cast<uint32_t>(tj)));
+      if constexpr (NOWRAP) {
+        h = max(static_cast<int>(end) + (-tj), h);
+      } else {
+        h = max(h, static_cast<int>(end - start - static_cast<uint32_t>(tj)));
+      }
     };
     if (ALL || (wm & 1u)) {
       upd(h0, p.y, p.x, tw[0]);
@@ -292,6 +302,9 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
         upd(h3, e.w, p.w, tw[j]);
       }
     }
+    if constexpr (NOWRAP)
+      return (h0 >= static_cast<int>(p.x) ? 1u : 0u) | (h1 >= static_cast<int>(p.y) ? 2u : 0u) |
+             (h2 >= static_cast<int>(p.z) ? 4u : 0u) | (h3 >= static_cast<int>(p.w) ? 8u : 0u);
     return (h0 >= 0 ? 1u : 0u) | (h1 >= 0 ? 2u : 0u) | (h2 >= 0 ? 4u : 0u) | (h3 >= 0 ? 8u : 0u);
   };
   const int ngt = (nb + 3) >> 2;
@@ -301,7 +314,10 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
     if (m < ngt) {
       // rows with every width (most rows above a small DM) take a copy of the loop with no
       // width tests, so all window loads of the group can be in flight together
-      nib = (wm == kAllWidths) ? group_hits(m, WidthSet<true>{}) : group_hits(m, WidthSet<false>{});
+      if (a.nowrap)
+        nib = (wm == kAllWidths) ? group_hits(m, WidthSet<true, true>{}) : group_hits(m, WidthSet<false, true>{});
+      else
+        nib = (wm == kAllWidths) ? group_hits(m, WidthSet<true>{}) : group_hits(m, WidthSet<false>{});
       const int rem = nb - 4 * m;  // start times of this group inside the block
       if (rem < 4) nib &= (1u << rem) - 1u;
     }
@@ -394,6 +410,11 @@ bool mf_args(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64
   a.tau_steps = p.loop_limit > 0 ? static_cast<int>(p.loop_limit < 64 ? p.loop_limit : 64) : 64;
   const int len = static_cast<int>(e_new - f_prev);
   *smem = ((len >> 2) + 3) * 16;  // front pad (4 words) and len/4 + 2 aligned groups
+  {
+    // largest root value of the mode times the staged samples bounds every prefix sum
+    const double vmax = p.mode == SND_MODE_BINARY ? 1.0 : (p.mode == SND_MODE_GRADED ? p.N : p.nchan);
+    a.nowrap = vmax * (len + 8.0) < 2147483647.0 ? 1 : 0;
+  }
   return true;
 }
 
