@@ -554,10 +554,12 @@ def multibeam_setup(g, dev, nbeams=48, seed=11, branching=None, steps_tune=2):
     rng = np.random.default_rng(seed)
     f = synth.channel_freqs(1024)
     tune = None
+    shape = {"tree_warps": 0, "tree_round": 0}
     if branching is None:
         tune = autotune.autotune(f, synth.NC_DT, synth.dm_grid(2048, 2000.0), g.MODE_FLOAT, 16384,
-                                 branching=(2, 4, 8, 16), cluster=(4,), steps=steps_tune, device=dev)
+                                 branching=(8, 2, 4, 16), cluster=(4,), steps=steps_tune, device=dev)
         branching = tune["branching"]
+        shape = {"tree_warps": tune["tree_warps"], "tree_round": tune["tree_round"]}
     cfgs = [(int(rng.integers(512, 4097)), float(rng.uniform(500.0, 3000.0)), int(rng.integers(4, 33)) * 1024)
             for _ in range(nbeams)]
     gen = torch.Generator(device=dev).manual_seed(seed)
@@ -565,7 +567,7 @@ def multibeam_setup(g, dev, nbeams=48, seed=11, branching=None, steps_tune=2):
              .to(torch.uint8) for _ in range(2)] for _, _, ch in cfgs]
     fill = max((p_d + ch - 1) // ch for p_d, ch in
                ((int(2.0 + 4.148808e3 * dmx * (f.min() ** -2 - f.max() ** -2) / synth.NC_DT), ch) for _, dmx, ch in cfgs))
-    return f, cfgs, data, branching, tune, fill
+    return f, cfgs, data, branching, tune, fill, shape
 
 
 def multibeam_rate(g, args, dev, nbeams=48, seed=11):
@@ -574,15 +576,21 @@ def multibeam_rate(g, args, dev, nbeams=48, seed=11):
     mode, branching from the autotuner. Times one step of all beams run plan by plan, as a
     batch (grouped tree launches), and as a batch replayed through a CUDA graph."""
     import torch
-    f, cfgs, data, B, tune, fill = multibeam_setup(g, dev, nbeams, seed)
+    f, cfgs, data, B, tune, fill, shape = multibeam_setup(g, dev, nbeams, seed)
 
     def make():
         return [g.Plan(f, synth.NC_DT, synth.dm_grid(nd, dmx), B, g.MODE_FLOAT,
-                       g.options(g.MODE_FLOAT, max_chunk=ch), device=dev) for nd, dmx, ch in cfgs]
+                       g.options(g.MODE_FLOAT, max_chunk=ch, **shape), device=dev) for nd, dmx, ch in cfgs]
 
     steps = max(2, min(args.steps, 5))
-    out = {"beams": nbeams, "autotune": {"branching": B, "trials": [(t["branching"], round(t["ms_per_chunk"], 3))
-                                                                  for t in tune["trials"]]}}
+    out = {"beams": nbeams,
+           "autotune": {"branching": B, "tree_warps": tune["tree_warps"], "tree_round": tune["tree_round"],
+                        "significant": tune["significant"],
+                        "trials": [(t["branching"], t["tree_warps"], t["tree_round"], round(t["ms_per_chunk"], 4),
+                                    round(t["spread_ms"], 4)) for t in tune["trials"]],
+                        "note": "trial = (B, warps per tree CTA, channels per staging round, median pipeline ms per "
+                                "chunk, spread over 3 repeats); a pick replaces the default (B = 8, 8 warps, 128) "
+                                "only when it beats it by more than both spreads"}}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name in ("per_beam", "batch", "batch_graph"):
         plans = make()
@@ -829,9 +837,9 @@ def drive(mode_name: str, nchunks: int, branching: int):
     import paper_2606_15361_gb300 as g
     if mode_name == "batch48":
         dev = torch.device("cuda", 0)
-        f, cfgs, data, B, _, fill = multibeam_setup(g, dev, branching=branching)
+        f, cfgs, data, B, _, fill, shape = multibeam_setup(g, dev, branching=branching)
         plans = [g.Plan(f, synth.NC_DT, synth.dm_grid(nd, dmx), B, g.MODE_FLOAT,
-                        g.options(g.MODE_FLOAT, max_chunk=ch), device=dev) for nd, dmx, ch in cfgs]
+                        g.options(g.MODE_FLOAT, max_chunk=ch, **shape), device=dev) for nd, dmx, ch in cfgs]
         batch = g.Batch(plans)
         for k in range(fill + nchunks):
             batch.execute([data[i][k % 2] for i in range(len(plans))])

@@ -100,6 +100,10 @@ typedef struct {
                                SND_FLAG_FP16_PARTIALS / SND_FLAG_UNIT_PAYLOAD (zfloat) */
   int32_t plane_dtype;      /* d_plane_out element type: 0 = int32 / float32 (default); 1 = uint8,
                                binary and graded modes only (their roots are 0..255) */
+  int32_t tree_warps;       /* direct tree kernel: warps per CTA, 2, 4 or 8 (0 = 8); a CTA covers
+                               32 trial DMs x warps x (2 or 4) output words. Results never depend on it */
+  int32_t tree_round;       /* direct tree kernel: channels staged per round, 64 or 128 (0 = 128 where
+                               it fits two CTAs per SM, else 64). Results never depend on it */
 } snd_options_t;
 
 /* One detection (Methods, "Candidate detection": one candidate per island, peak pixel). */

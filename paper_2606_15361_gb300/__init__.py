@@ -37,7 +37,7 @@ class SndOptions(ctypes.Structure):
         ("sigma_min", ctypes.c_double), ("mf_alpha", ctypes.c_double), ("closing_size", ctypes.c_int32),
         ("n_min_pixels", ctypes.c_int32), ("max_chunk", ctypes.c_int32), ("cand_capacity", ctypes.c_int32),
         ("cell_capacity", ctypes.c_int32), ("run_capacity", ctypes.c_int32), ("flags", ctypes.c_int32),
-        ("plane_dtype", ctypes.c_int32),
+        ("plane_dtype", ctypes.c_int32), ("tree_warps", ctypes.c_int32), ("tree_round", ctypes.c_int32),
     ]
 
 

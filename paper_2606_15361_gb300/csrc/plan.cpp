@@ -573,7 +573,7 @@ void choose_direct_geometry(Plan& p) {
     }
   }
   g.kw = kw;
-  g.warps = 8;
+  g.warps = p.tree_warps ? p.tree_warps : 8;
   g.tile_words = g.warps * kw;
   g.ndm_tiles = (ndm + 31) / 32;
   p.dbase.assign(static_cast<size_t>(g.ndm_tiles) * nchan, 0);
@@ -594,7 +594,12 @@ void choose_direct_geometry(Plan& p) {
   g.cspan = static_cast<int>(align_up(static_cast<size_t>(4 + omax + g.tile_words), 4));
   // stage 128 channels per round (half the barriers) when they fit two CTAs per SM
   auto smem_for = [&](int sg) { return (2 * 64 * sg * static_cast<int64_t>(g.cspan) + 64 * sg * 32 + nchan) * 4; };
-  g.sgroups = (nchan % 128 == 0 && smem_for(2) <= 100 * 1024) ? 2 : 1;
+  if (p.tree_round == 64)
+    g.sgroups = 1;
+  else if (p.tree_round == 128)
+    g.sgroups = nchan % 128 == 0 ? 2 : 1;
+  else
+    g.sgroups = (nchan % 128 == 0 && smem_for(2) <= 100 * 1024) ? 2 : 1;
   const int64_t smem = smem_for(g.sgroups);
   if (smem > 200 * 1024) return;
   g.smem_bytes = static_cast<int>(smem);
@@ -709,6 +714,9 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
   if (o.plane_dtype < 0 || o.plane_dtype > 1 ||
       (o.plane_dtype == 1 && mode != SND_MODE_BINARY && mode != SND_MODE_GRADED))
     return SND_ERR_ARG;
+  if ((o.tree_warps != 0 && o.tree_warps != 2 && o.tree_warps != 4 && o.tree_warps != 8) ||
+      (o.tree_round != 0 && o.tree_round != 64 && o.tree_round != 128))
+    return SND_ERR_ARG;
   if (o.n_min_pixels < 1 || o.max_chunk < 1 || o.max_chunk > (1 << 22) || o.cand_capacity < 1 ||
       o.cell_capacity < 1 || o.run_capacity < 1)
     return SND_ERR_ARG;
@@ -752,6 +760,8 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
     p->run_cap = o.run_capacity;
     p->flags = o.flags;
     p->plane_u8 = o.plane_dtype;
+    p->tree_warps = o.tree_warps;
+    p->tree_round = o.tree_round;
     p->freqs.assign(freqs_mhz, freqs_mhz + nchan);
     p->dms.assign(dm_grid, dm_grid + ndm);
     int rc = snd::build_plan(*p);

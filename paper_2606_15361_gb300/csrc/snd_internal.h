@@ -159,7 +159,7 @@ struct Plan {
   int nchan = 0, ndm = 0, mode = 0, B = 2, C = 4, KL = 2, KI = 2, N = 255;
   double dt = 0, enc_theta = 1.5, det_theta = 7.0, sigma_min = 0.2, mf_alpha = 0.1;
   int closing = 9, n_min = 10, max_chunk = 32768, cand_cap = 65536, cell_cap = 1 << 20,
-      run_cap = 1 << 21, flags = 0, plane_u8 = 0;
+      run_cap = 1 << 21, flags = 0, plane_u8 = 0, tree_warps = 0, tree_round = 0;
   std::vector<double> freqs, dms;
 
   // derived

@@ -128,13 +128,21 @@ def test_step_launch_count_is_fixed():
 def test_autotune_pick_keeps_the_float_plane():
     f = synth.channel_freqs(256)
     dms = synth.dm_grid(256, 300.0)
-    res = autotune.autotune(f, synth.NC_DT, dms, g.MODE_FLOAT, 4096, branching=(2, 8), cluster=(3, 4), steps=2)
-    assert len(res["trials"]) == 4 and res["branching"] in (2, 8) and res["cluster"] in (3, 4)
+    res = autotune.autotune(f, synth.NC_DT, dms, g.MODE_FLOAT, 4096, branching=(2, 8), cluster=(3, 4), steps=2,
+                            warps=(8, 4), rounds=(128, 64))
+    assert len(res["trials"]) == 16 and res["branching"] in (2, 8) and res["cluster"] in (3, 4)
+    assert res["tree_warps"] in (8, 4) and res["tree_round"] in (128, 64)
+    t0 = res["trials"][0]
+    assert (t0["branching"], t0["cluster"], t0["tree_warps"], t0["tree_round"]) == (2, 4, 8, 128)
+    if not res["significant"]:
+        assert (res["branching"], res["cluster"], res["tree_warps"]) == (2, 4, 8)
+    assert all(t["spread_ms"] >= 0 for t in res["trials"])
     assert not autotune.tunable(g.MODE_BINARY, 256) and not autotune.tunable(g.MODE_GRADED, 1024)
     chunks = [synth.filterbank_chunk(9, i, 0, 4096, f, synth.NC_DT, []) for i in range(3)]
     planes = []
-    for B, C in ((8, 4), (res["branching"], res["cluster"])):
-        p = g.Plan(f, synth.NC_DT, dms, B, g.MODE_FLOAT, g.options(g.MODE_FLOAT, cluster_size=C, max_chunk=4096))
+    for B, C, w, r in ((8, 4, 0, 0), (res["branching"], res["cluster"], res["tree_warps"], res["tree_round"])):
+        p = g.Plan(f, synth.NC_DT, dms, B, g.MODE_FLOAT,
+                   g.options(g.MODE_FLOAT, cluster_size=C, max_chunk=4096, tree_warps=w, tree_round=r))
         rows = []
         for ch in chunks:
             ne = p.nemit_next(ch.shape[0])
@@ -143,3 +151,13 @@ def test_autotune_pick_keeps_the_float_plane():
             rows.append(out[:, :ne].cpu().numpy())
         planes.append(np.concatenate(rows, axis=1))
     assert planes[0].shape[1] > 0 and np.array_equal(planes[0], planes[1])
+
+
+def test_autotune_untunable_binary_searches_tile_shape_only():
+    f = synth.channel_freqs(128)
+    dms = synth.dm_grid(64, 200.0)
+    res = autotune.autotune(f, synth.NC_DT, dms, g.MODE_BINARY, 2048, branching=(4, 8), cluster=(3,), steps=1,
+                            repeats=2, warps=(8, 2), rounds=(64,))
+    assert res["branching"] is None and res["cluster"] == 4
+    assert {(t["branching"], t["cluster"]) for t in res["trials"]} == {(4, 4)}
+    assert len(res["trials"]) == 2
