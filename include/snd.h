@@ -76,6 +76,12 @@ typedef struct snd_plan_s* snd_plan_t;
  * instead of z, so every node holds a spike count and the storage type alone decides the
  * plane's error (FP16 holds every count up to 2048 exactly). */
 #define SND_FLAG_UNIT_PAYLOAD 16
+/* Option flag (binary, graded, float): count, per tree level, the node-samples whose output is
+ * nonzero over the emitted samples (the per-level fire rates of Supplementary Table S2 that the
+ * paper's dynamic-power model uses); read them with snd_level_rates. Needs the direct tree
+ * kernel with C = 4 (nchan a multiple of 64, at most 13 levels); otherwise the plan returns
+ * SND_ERR_UNSUPPORTED. Float and graded plans pay one extra counting pass per chunk. */
+#define SND_FLAG_LEVEL_RATES 32
 
 /*
  * Options. Fill with snd_options_init(mode, &o) (Supplementary Table S1 operating point
@@ -96,8 +102,8 @@ typedef struct {
   int32_t cand_capacity;    /* candidates held on the device between snd_candidates calls */
   int32_t cell_capacity;    /* mask cells with S/N kept per matched-filter block */
   int32_t run_capacity;     /* closed-mask runs per matched-filter block */
-  int32_t flags;            /* 0 or SND_FLAG_REFERENCE_TREE / SND_FLAG_LEAF_SHARING, or
-                               SND_FLAG_FP16_PARTIALS / SND_FLAG_UNIT_PAYLOAD (zfloat) */
+  int32_t flags;            /* 0 or SND_FLAG_REFERENCE_TREE / SND_FLAG_LEAF_SHARING / SND_FLAG_LEVEL_RATES,
+                               or SND_FLAG_FP16_PARTIALS / SND_FLAG_UNIT_PAYLOAD (zfloat) */
   int32_t plane_dtype;      /* d_plane_out element type: 0 = int32 / float32 (default); 1 = uint8,
                                binary and graded modes only (their roots are 0..255) */
   int32_t tree_warps;       /* direct tree kernel: warps per CTA, 2, 4 or 8 (0 = 8); a CTA covers
@@ -218,6 +224,15 @@ int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_t cap, int3
 
 /* Plan statistics (host only; stream counters are those of the last enqueued call). */
 int snd_plan_stats(snd_plan_t plan, snd_plan_stats_t* out);
+
+/*
+ * Per-level fire counts of a plan made with SND_FLAG_LEVEL_RATES (Supplementary Table S2):
+ * fires_out[l] (nullable) = node-samples of tree level l (0 = leaves) with a nonzero output,
+ * rates_out[l] (nullable) = fires / (nodes of level l x ndm x samples emitted per row), both
+ * accumulated since the workspace was bound; for l < min(cap, nlevels). *nlevels_out = levels.
+ * Synchronises the plan's last stream. SND_ERR_STATE without the flag or before binding.
+ */
+int snd_level_rates(snd_plan_t plan, uint64_t* fires_out, double* rates_out, int32_t cap, int32_t* nlevels_out);
 
 /* Copy the plan's integer delay table int32[ndm][nchan] to host memory (n >= ndm*nchan). */
 int snd_delay_table(snd_plan_t plan, int32_t* host_out, int64_t n);

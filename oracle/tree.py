@@ -86,3 +86,20 @@ def brute_rows(x, x_t0: int, delays, rows, t_start: int, nout: int) -> np.ndarra
 def float_scale(counts, nchan: int) -> np.ndarray:
     """Mode C root normalisation: y = s / sqrt(N_f), in FP64."""
     return np.asarray(counts, dtype=np.float64) / np.sqrt(float(nchan))
+
+
+def level_fire_counts(x, x_t0: int, delays, rows, t_start: int, nout: int, mode: int, cluster: int,
+                      branching: int, k_leaf: int = 0, k_internal: int = 0, cap: int = 255) -> list:
+    """Per tree level (0 = leaves), the number of (node, DM row, output time) with a nonzero
+    node value over the selected rows and times: the per-level fire counts behind the
+    per-level mean fire rates of the paper's dynamic-power model (Supplementary Table S2)."""
+    levels = tree_levels(x.shape[0], cluster, branching)
+    counts = [0] * len(levels)
+    for d in rows:
+        a = gather(x, x_t0, delays[d], t_start, nout)
+        vals = [_rule(a[lo:hi].sum(axis=0), mode, k_leaf, cap) for lo, hi in levels[0]]
+        counts[0] += int(sum(int((v != 0).sum()) for v in vals))
+        for li, lev in enumerate(levels[1:], start=1):
+            vals = [_rule(np.sum(vals[lo:hi], axis=0), mode, k_internal, cap) for lo, hi in lev]
+            counts[li] += int(sum(int((v != 0).sum()) for v in vals))
+    return counts

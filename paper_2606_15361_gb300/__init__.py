@@ -20,6 +20,7 @@ FLAG_REFERENCE_TREE = 1
 FLAG_FP16_PARTIALS = 2
 FLAG_LEAF_SHARING = 4
 FLAG_UNIT_PAYLOAD = 16
+FLAG_LEVEL_RATES = 32
 TREE_KERNELS = {0: "leaf-sharing k_tree", 1: "direct k_snd", 2: "reference k_tree_ref", 3: "labelled-payload k_tree_z"}
 
 STATUS = {
@@ -68,7 +69,8 @@ assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(SndCandidate) == 32
 
 EXPORTS = ("snd_options_init", "snd_plan", "snd_plan_ex", "snd_workspace_size", "snd_bind_workspace",
            "snd_execute", "snd_execute_host", "snd_candidates", "snd_plan_stats", "snd_delay_table",
-           "snd_profile", "snd_profile_read", "snd_encode_static", "snd_debug_fail_host_alloc", "snd_debug_loop_limit", "snd_destroy",
+           "snd_profile", "snd_profile_read", "snd_encode_static", "snd_debug_fail_host_alloc", "snd_debug_loop_limit", "snd_level_rates",
+           "snd_destroy",
            "snd_error_string",
            "snd_multirate_plan", "snd_multirate_info", "snd_multirate_band_plan", "snd_multirate_workspace_size",
            "snd_multirate_bind_workspace", "snd_multirate_execute", "snd_multirate_execute_host",
@@ -104,6 +106,9 @@ def _load():
     lib.snd_encode_static.argtypes = [V, I32, I32, D, V, V]
     lib.snd_debug_fail_host_alloc.argtypes = [I32]
     lib.snd_debug_loop_limit.argtypes = [P, I64]
+    lib.snd_level_rates.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), I32,
+                                    ctypes.POINTER(I32)]
+    lib.snd_level_rates.restype = ctypes.c_int
     lib.snd_debug_loop_limit.restype = ctypes.c_int
     lib.snd_debug_fail_host_alloc.restype = ctypes.c_int
     lib.snd_destroy.argtypes = [P]
@@ -294,6 +299,16 @@ class Plan:
         cnt = (ctypes.c_int64 * 4)()
         _check(lib.snd_profile_read(self.handle, ms, cnt), "snd_profile_read")
         return {STAGES[i]: (ms[i], cnt[i]) for i in range(4)}
+
+    def level_rates(self):
+        """(fires uint64[nlev], rates float64[nlev]) of a plan made with FLAG_LEVEL_RATES."""
+        fires = np.zeros(24, dtype=np.uint64)
+        rates = np.zeros(24, dtype=np.float64)
+        n = ctypes.c_int32(0)
+        _check(lib.snd_level_rates(self.handle, fires.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 24, ctypes.byref(n)),
+               "snd_level_rates")
+        return fires[:n.value], rates[:n.value]
 
     def delay_table(self) -> np.ndarray:
         out = np.zeros((self.ndm, self.nchan), dtype=np.int32)

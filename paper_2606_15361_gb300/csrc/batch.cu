@@ -45,7 +45,7 @@ int enqueue_plans(Plan* const* plans, int n, const uint8_t* const* d_chunks, con
     if (pos[i].e_new <= pos[i].e_prev) continue;
     if (p.mode == SND_MODE_ZFLOAT) {
       if (launch_tree_z(p, pos[i].e_prev, pos[i].e_new, nullptr, s) != cudaSuccess) return SND_ERR_CUDA;
-    } else if (p.flags & SND_FLAG_REFERENCE_TREE) {
+    } else if ((p.flags & SND_FLAG_REFERENCE_TREE) || ((p.flags & SND_FLAG_LEVEL_RATES) && p.mode != SND_MODE_BINARY)) {
       if (launch_tree(p, pos[i].e_prev, pos[i].e_new, s) != cudaSuccess) return SND_ERR_CUDA;
     } else {
       tp.push_back(&p);

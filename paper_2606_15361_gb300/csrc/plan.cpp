@@ -331,6 +331,7 @@ int build_plan(Plan& p) {
   p.off.delays = take(sizeof(int32_t) * p.delays.size());
   p.off.dmeta = take(sizeof(uint16_t) * std::max<size_t>(8, p.dmeta.size()));
   p.off.dbase = take(sizeof(int32_t) * std::max<size_t>(4, p.dbase.size()));
+  p.off.level_fires = take(sizeof(unsigned long long) * snd::kMaxLevels);
   if (p.mode == SND_MODE_ZFLOAT) {
     const size_t es = p.zgeom.fp16 ? 2 : 4;
     p.off.zring = take(es * static_cast<size_t>(nchan) * p.zgeom.Rz);
@@ -575,6 +576,15 @@ void choose_direct_geometry(Plan& p) {
   g.kw = kw;
   g.warps = p.tree_warps ? p.tree_warps : 8;
   g.tile_words = g.warps * kw;
+  int span_kw = kw;  // words per warp the staged windows must cover
+  if ((p.flags & SND_FLAG_LEVEL_RATES) && p.mode != SND_MODE_BINARY) {
+    // the binary counting pass (K_L = K_I = 1) on the same tables
+    const int up = p.nlev - 1;
+    if (p.C != 4 || up < 1 || up > 12) return;
+    g.rates_inst = up <= 4 ? snd::kDirBinary4 : (up <= 8 ? snd::kDirBinary8 : snd::kDirBinary12);
+    g.rates_kw = up <= 8 ? 4 : 2;
+    span_kw = std::max(kw, g.rates_kw);
+  }
   g.ndm_tiles = (ndm + 31) / 32;
   p.dbase.assign(static_cast<size_t>(g.ndm_tiles) * nchan, 0);
   int64_t omax = 0;
@@ -591,7 +601,7 @@ void choose_direct_geometry(Plan& p) {
       omax = std::max<int64_t>(omax, (hi >> 5) - b4);
     }
   if (omax > 2047) return;
-  g.cspan = static_cast<int>(align_up(static_cast<size_t>(4 + omax + g.tile_words), 4));
+  g.cspan = static_cast<int>(align_up(static_cast<size_t>(4 + omax + g.warps * span_kw), 4));
   // stage 128 channels per round (half the barriers) when they fit two CTAs per SM
   auto smem_for = [&](int sg) { return (2 * 64 * sg * static_cast<int64_t>(g.cspan) + 64 * sg * 32 + nchan) * 4; };
   if (p.tree_round == 64)
@@ -699,8 +709,11 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
   } else {
     snd_options_init(mode, &o);
   }
-  if (o.flags & ~(SND_FLAG_REFERENCE_TREE | SND_FLAG_FP16_PARTIALS | SND_FLAG_LEAF_SHARING | SND_FLAG_UNIT_PAYLOAD))
+  if (o.flags & ~(SND_FLAG_REFERENCE_TREE | SND_FLAG_FP16_PARTIALS | SND_FLAG_LEAF_SHARING | SND_FLAG_UNIT_PAYLOAD |
+                  SND_FLAG_LEVEL_RATES))
     return SND_ERR_ARG;
+  if ((o.flags & SND_FLAG_LEVEL_RATES) && (mode == SND_MODE_ZFLOAT || (o.flags & SND_FLAG_REFERENCE_TREE)))
+    return SND_ERR_UNSUPPORTED;
   if ((o.flags & (SND_FLAG_FP16_PARTIALS | SND_FLAG_UNIT_PAYLOAD)) && mode != SND_MODE_ZFLOAT) return SND_ERR_ARG;
   if ((o.flags & SND_FLAG_REFERENCE_TREE) && mode == SND_MODE_ZFLOAT) return SND_ERR_UNSUPPORTED;
   if (o.cluster_size < 1 || o.cluster_size > 7) return SND_ERR_UNSUPPORTED;
@@ -765,6 +778,9 @@ extern "C" int snd_plan_ex(const double* freqs_mhz, int32_t nchan, double dt_s,
     p->freqs.assign(freqs_mhz, freqs_mhz + nchan);
     p->dms.assign(dm_grid, dm_grid + ndm);
     int rc = snd::build_plan(*p);
+    if (!rc && (p->flags & SND_FLAG_LEVEL_RATES) &&
+        (!p->direct || p->C != 4 || (p->mode != SND_MODE_BINARY && p->dgeom.rates_inst == snd::kDirNone)))
+      rc = SND_ERR_UNSUPPORTED;  // the fire counts come from the direct kernel's binary tree
     if (rc) {
       delete p;
       return rc;

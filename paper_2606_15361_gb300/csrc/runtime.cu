@@ -149,6 +149,7 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   dp.delays = at<int32_t>(d_ws, o.delays);
   dp.dmeta = at<uint16_t>(d_ws, o.dmeta);
   dp.dbase = at<int32_t>(d_ws, o.dbase);
+  dp.level_fires = at<unsigned long long>(d_ws, o.level_fires);
   const bool z = p.mode == SND_MODE_ZFLOAT;
   dp.zring = z ? at<void>(d_ws, o.zring) : nullptr;
   dp.ztab = z ? at<void>(d_ws, o.ztab) : nullptr;
@@ -189,6 +190,24 @@ extern "C" int snd_bind_workspace(snd_plan_t plan, void* d_ws, size_t bytes, voi
   p.launches = 0;
   p.ev_used = 0;
   p.ev_marks.clear();
+  return SND_OK;
+}
+
+extern "C" int snd_level_rates(snd_plan_t plan, uint64_t* fires_out, double* rates_out, int32_t cap,
+                               int32_t* nlevels_out) {
+  if (!plan || cap < 0) return SND_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (!p.bound || !(p.flags & SND_FLAG_LEVEL_RATES)) return SND_ERR_STATE;
+  if (p.sticky) return p.sticky;
+  if (cudaStreamSynchronize(p.last_stream) != cudaSuccess) return fail(p, SND_ERR_CUDA);
+  unsigned long long f[snd::kMaxLevels];
+  if (cudaMemcpy(f, p.dp.level_fires, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(p, SND_ERR_CUDA);
+  if (nlevels_out) *nlevels_out = p.nlev;
+  for (int l = 0; l < p.nlev && l < cap; ++l) {
+    if (fires_out) fires_out[l] = f[l];
+    const double den = static_cast<double>(p.level_nodes[l]) * p.ndm * static_cast<double>(p.E);
+    if (rates_out) rates_out[l] = den > 0 ? static_cast<double>(f[l]) / den : 0.0;
+  }
   return SND_OK;
 }
 

@@ -85,6 +85,8 @@ struct DirectGeom {
   int smem_bytes = 0;
   int sub_lev = 0;       // graded: the exact level (first level whose nodes may exceed N)
   int sub_groups = 1;    // graded: 64-channel groups per exact-level node
+  int rates_inst = kDirNone;  // float / graded with per-level fire counts: the binary counting pass
+  int rates_kw = 4;
 };
 
 // Labelled-payload (zfloat) tree geometry (chosen on the host).
@@ -140,6 +142,7 @@ struct DevPtrs {
   int32_t* zcarry;         // zfloat: [nleaves] carry depth of each leaf
   uint16_t* dmeta;         // direct tree: [ndm_tiles][nchan][32] staged word offset << 5 | shift
   int32_t* dbase;          // direct tree: [ndm_tiles][nchan] first staged ring word (multiple of 4)
+  unsigned long long* level_fires;  // [kMaxLevels] firing node-samples per tree level (SND_FLAG_LEVEL_RATES)
 };
 
 // Counter slots.
@@ -201,7 +204,7 @@ struct Plan {
   struct Off {
     size_t ring, hist, levels, plane, mask, mask2, mask3, cells, counters, row_runs, run_start,
         run_end, run_row, parent, npix, peak, pwidth, bcand, cand, staging, staging2, width_mask, dm_f32, tp_off,
-        gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb, zcarry, dmeta, dbase;
+        gepk, gleaf, gmeta, tile_wb, delays, zring, ztab, zwb, zcarry, dmeta, dbase, level_fires;
   } off{};
 
   // binding and stream state

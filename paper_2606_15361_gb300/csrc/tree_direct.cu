@@ -59,6 +59,9 @@ struct DirArgs {
   int Lp;
   uint32_t* status;
   long long wait_cycles;   // bound of a staging wait (clock cycles)
+  long long e_prev, e_new; // emitted samples of this call
+  int store;               // write the root plane (0: a fire-count pass only)
+  unsigned long long* level_fires;  // binary: per-level counts of firing node-samples (null: off)
 };
 
 constexpr int kMaxDirBeams = 64;
@@ -246,6 +249,8 @@ struct DState;
 template <int KW, int NPL, int MAXU>
 struct DState<kFloat, KW, NPL, MAXU> {
   uint32_t P[NPL][KW];
+  __device__ __forceinline__ void set_counting(const DirArgs&, long long, bool) {}
+  __device__ __forceinline__ void flush(const DirArgs&, int) {}
   __device__ __forceinline__ void init(const DirArgs&) {
 #pragma unroll
     for (int p = 0; p < NPL; ++p)
@@ -268,6 +273,8 @@ template <int KW, int NPL, int MAXU>
 struct DState<kGraded, KW, NPL, MAXU> {
   static_assert(NPL >= 8, "the root is kept in the counter planes");
   uint32_t P[NPL][KW];  // count of the open exact-level node; at the end, the root's 8 planes
+  __device__ __forceinline__ void set_counting(const DirArgs&, long long, bool) {}
+  __device__ __forceinline__ void flush(const DirArgs&, int) {}
   uint32_t acc[MAXU > 0 ? MAXU : 1][KW][8];
   int cnt[MAXU > 0 ? MAXU : 1], node[MAXU > 0 ? MAXU : 1], fan[MAXU > 0 ? MAXU : 1];
   __device__ __forceinline__ void clearP() {
@@ -348,6 +355,28 @@ struct DState<kBinary, KW, NPL, MAXU> {
   uint32_t root[KW];
   int cnt[MAXU], node[MAXU], fan[MAXU];
   uint32_t ki2;  // all-ones when K_I = 2 (else K_I = 1)
+  // per-level fire counts (level 0 = leaves) over this lane's emitted samples, when counting
+  bool counting;
+  uint32_t vmask[KW];
+  unsigned fires[MAXU + 1];
+  __device__ __forceinline__ void set_counting(const DirArgs& a, long long aw_first, bool row_ok) {
+    counting = a.level_fires != nullptr;
+#pragma unroll
+    for (int u = 0; u <= MAXU; ++u) fires[u] = 0;
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+      // bits of word aw_first + j whose samples lie in [e_prev, e_new)
+      const long long s0 = (aw_first + j) * 32;
+      const long long lo = a.e_prev > s0 ? a.e_prev - s0 : 0, hi = a.e_new - s0 < 32 ? a.e_new - s0 : 32;
+      uint32_t m = 0;
+      if (row_ok && hi > lo) m = (hi - lo >= 32 ? 0xFFFFFFFFu : ((1u << (hi - lo)) - 1u)) << lo;
+      vmask[j] = m;
+    }
+  }
+  __device__ __forceinline__ void count(int level, const uint32_t (&v)[KW]) {
+#pragma unroll
+    for (int j = 0; j < KW; ++j) fires[level] += __popc(v[j] & vmask[j]);
+  }
   __device__ __forceinline__ void init(const DirArgs& a) {
     ki2 = a.KI >= 2 ? 0xFFFFFFFFu : 0u;
 #pragma unroll
@@ -382,10 +411,23 @@ struct DState<kBinary, KW, NPL, MAXU> {
       cnt[u] = 0;
       ++node[u];
       fan[u] = min(a.B, a.level_nodes[l - 1] - a.B * node[u]);
+      if (counting) count(l, v);
       if (l == a.nlev - 1) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) root[j] = v[j];
       }
+    }
+  }
+  // the lanes' counts summed per warp, added to the plan's per-level totals
+  __device__ __forceinline__ void flush(const DirArgs& a, int lane) {
+    if (!counting) return;
+#pragma unroll
+    for (int u = 0; u <= MAXU; ++u) {
+      if (u >= a.nlev) break;
+      unsigned c = fires[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+      if (lane == 0 && c) atomicAdd(a.level_fires + u, static_cast<unsigned long long>(c));
     }
   }
   // the 16 leaves of a staged group, each the quorum >= KL of its four channel bits
@@ -413,6 +455,7 @@ struct DState<kBinary, KW, NPL, MAXU> {
           v[j] = a0 & a1 & a2 & a3;
         }
       }
+      if (counting) count(0, v);
       push(a, v);
     }
   }
@@ -486,6 +529,7 @@ __device__ __forceinline__ bool direct_cta(const DirArgs& a, int bx, int tile, u
 
   DState<MODE, KW, NPL, MAXU> st;
   st.init(a);
+  st.set_counting(a, aw0 + wd * KW, tile * 32 + lane < a.ndm);
   // a warp none of whose words is emitted here (the short last tile of a call) only keeps the
   // CTA's barriers
   const bool busy = wd * KW < min(a.tile_words, a.nwords - bx * a.tile_words);
@@ -525,8 +569,9 @@ __device__ __forceinline__ bool direct_cta(const DirArgs& a, int bx, int tile, u
     }
     return false;
   }
+  st.flush(a, lane);
   const int drow = tile * 32 + lane;
-  if (drow >= a.ndm) return true;
+  if (drow >= a.ndm || !a.store) return true;
   const int lw = a.Lp >> 5;
 #pragma unroll
   for (int j = 0; j < KW; ++j) {
@@ -670,6 +715,10 @@ void direct_args(const Plan& p, int64_t e_prev, int64_t e_new, DirArgs& a, int* 
   a.Lp = p.Lp;
   a.status = dp.counters + kCntStatus;
   a.wait_cycles = p.loop_limit > 0 ? p.loop_limit : kDirWaitCycles;
+  a.e_prev = e_prev;
+  a.e_new = e_new;
+  a.store = 1;
+  a.level_fires = (p.flags & SND_FLAG_LEVEL_RATES) && p.mode == SND_MODE_BINARY ? dp.level_fires : nullptr;
   *ntx = (a.nwords + g.tile_words - 1) / g.tile_words;
 }
 
@@ -681,9 +730,23 @@ cudaError_t launch_tree_direct(const Plan& p, int64_t e_prev, int64_t e_new, cud
   int ntx = 0;
   direct_args(p, e_prev, e_new, a, &ntx);
   const DirectGeom& g = p.dgeom;
+  const DevPtrs& dp = p.dp;
   p.launches += 1;
   DGoSingle go{&a, dim3(ntx, g.ndm_tiles), dim3(32, g.warps), g.smem_bytes, s};
-  return dispatch_direct(g.inst, go);
+  cudaError_t e = dispatch_direct(g.inst, go);
+  if (e != cudaSuccess || !(p.flags & SND_FLAG_LEVEL_RATES) || p.mode == SND_MODE_BINARY) return e;
+  // float / graded: a node is nonzero iff some channel of its subtree fired, i.e. iff the
+  // same node of the binary tree with K_L = K_I = 1 fires; that tree's fire counts are the
+  // per-level rates (a counting pass that writes no plane)
+  DirArgs r = a;
+  r.KL = r.KI = 1;
+  r.store = 0;
+  r.level_fires = dp.level_fires;
+  r.tile_words = g.warps * g.rates_kw;
+  p.launches += 1;
+  DGoSingle gr{&r, dim3((r.nwords + r.tile_words - 1) / r.tile_words, g.ndm_tiles), dim3(32, g.warps), g.smem_bytes,
+               s};
+  return dispatch_direct(g.rates_inst, gr);
 }
 
 cudaError_t launch_tree_direct_batch(const Plan* const* plans, const int64_t* e_prev, const int64_t* e_new, int n,

@@ -144,3 +144,24 @@ def test_table1_printed_noise_rates():
             assert abs(s - float(s_txt)) <= 0.05 + 0.002 * float(s_txt)
         if s_txt == ">1e7":
             assert analytic.snr_binary(1, 1.0, p) > 1e7
+
+
+@pytest.mark.parametrize("mode,kl,ki", [(BINARY, 2, 2), (BINARY, 1, 2), (FLOAT, 0, 0), (GRADED, 0, 0)])
+def test_level_fire_rates_match_eq_cascade(mode, kl, ki):
+    """Per-level fire rates on a Bernoulli(p) raster with zero delays: binary levels follow Eq.
+    cascade level by level; a float or graded node is nonzero iff any of its n channels fired,
+    so its rate is 1 - (1 - p)^n (the OR cascade)."""
+    nchan, C, B, p0, n = 64, 4, 2, 0.1, 30000
+    x = synth.bernoulli_raster(900 + kl + 10 * mode, nchan, n, p0)
+    tab = np.zeros((1, nchan), np.int64)
+    counts = tree.level_fire_counts(x, 0, tab, [0], 0, n, mode, C, B, kl, ki)
+    lv = tree.tree_levels(nchan, C, B)
+    fan = [l[0][1] - l[0][0] for l in lv[1:]]
+    if mode == BINARY:
+        want = analytic.cascade(p0, C, fan, kl, ki)
+    else:
+        want = [1 - (1 - p0) ** (C * B ** l) for l in range(len(lv))]
+    for l, (c, w) in enumerate(zip(counts, want)):
+        nodes = len(lv[l])
+        rate = c / (nodes * n)
+        assert abs(rate - w) < 5 * math.sqrt(max(w * (1 - w), 1e-12) / (nodes * n)) + 1e-9, (l, rate, w)
