@@ -84,6 +84,7 @@ __device__ __forceinline__ void close_tile(const uint32_t* __restrict__ in, uint
   const uint32_t tailvalid = (nb & 31) ? ((1u << (nb & 31)) - 1u) : 0xFFFFFFFFu;
   const int n = NR * kCloseNQ;
   const int tid = threadIdx.x;
+  uint32_t any = 0u;
   // 1. input tile, dilation's outside value 0
   for (int idx = tid; idx < n; idx += kCloseThreads) {
     const int i = idx / kCloseNQ, k = idx - i * kCloseNQ;
@@ -94,8 +95,17 @@ __device__ __forceinline__ void close_tile(const uint32_t* __restrict__ in, uint
       if (q == nbw - 1) w &= tailvalid;
     }
     A[idx] = w;
+    any |= w;
   }
-  __syncthreads();
+  // a tile whose staged input (halo included) is empty closes to an empty tile: most tiles of
+  // a block far from any detection
+  if (!__syncthreads_or(any != 0u)) {
+    for (int idx = tid; idx < kCloseTR * kCloseTQ; idx += kCloseThreads) {
+      const int d = d0 + idx / kCloseTQ, q = q0 + idx % kCloseTQ;
+      if (d < ndm && q < nbw) out[static_cast<size_t>(d) * mw + q] = 0u;
+    }
+    return;
+  }
   // 2. horizontal dilation, words 1 .. NQ-2
   for (int idx = tid; idx < n; idx += kCloseThreads) {
     const int i = idx / kCloseNQ, k = idx - i * kCloseNQ;
@@ -238,6 +248,7 @@ __device__ __forceinline__ void run_write_row(const uint32_t* __restrict__ m, in
                                               const int lane) {
   if (warp >= ndm) return;
   if (row_runs[ndm] > run_cap) return;
+  if (row_runs[warp + 1] == row_runs[warp]) return;  // a row without runs (most rows)
   const int nbw = (nb + 31) >> 5;
   const uint32_t* row = m + static_cast<size_t>(warp) * mw;
   int base_s = row_runs[warp], base_e = row_runs[warp];
