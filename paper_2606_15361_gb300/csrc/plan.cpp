@@ -562,7 +562,15 @@ void choose_direct_geometry(Plan& p) {
   } else {
     if (p.C != 4 || p.KL < 1 || p.KL > 4 || p.KI < 1 || p.KI > 2 || p.nlev < 2) return;
     const int up = p.nlev - 1;
-    if (up <= 4) {
+    // regular trees (B = 4 or 8): the levels inside a 16-leaf group as fixed logic; per-level
+    // fire counts take the general state
+    const int uin = p.B == 4 ? 2 : 1;
+    const bool reg = (p.B == 4 || p.B == 8) && !(p.flags & SND_FLAG_LEVEL_RATES) && up >= uin &&
+                     up - uin <= (p.B == 4 ? 4 : 3);
+    if (reg) {
+      inst = p.B == 4 ? (p.KI == 1 ? snd::kDirBinReg4K1 : snd::kDirBinReg4K2)
+                      : (p.KI == 1 ? snd::kDirBinReg8K1 : snd::kDirBinReg8K2);
+    } else if (up <= 4) {
       inst = snd::kDirBinary4;
     } else if (up <= 8) {
       inst = snd::kDirBinary8;
@@ -629,7 +637,7 @@ void choose_direct_geometry(Plan& p) {
 }
 
 // Labelled-payload tree geometry: DMs per CTA, samples per CTA (32 lanes x samples per
-// lane, fewer samples for deeper trees so the per-level partial sums stay in registers), the
+// lane, in pairs; fewer samples for deeper trees so the per-level partial sums stay in registers), the
 // first staged sample of each channel per DM tile (its smallest delay over the tile) and the
 // widest staged window, leaves staged per shared-memory round, and the payload ring length.
 int choose_ztree_geometry(Plan& p) {
@@ -660,8 +668,10 @@ int choose_ztree_geometry(Plan& p) {
   if (spread > (1 << 20)) return SND_ERR_UNSUPPORTED;
   const int es = z.fp16 ? 2 : 4;
   z.win = static_cast<int>(align_up(static_cast<size_t>(z.tile_samples + spread), 8));
-  // per staged channel: its window and the tile's DM offsets into it
-  const int64_t per_chan = static_cast<int64_t>(z.win) * es + 4 * z.dms_per_cta;
+  // per staged channel: its window twice (as stored and shifted by one value, each with a
+  // 16-byte alignment slack and one spare chunk) and the tile's DM offsets into it
+  const int64_t wz = z.win + 2 * (16 / es);
+  const int64_t per_chan = 2 * wz * es + 4 * z.dms_per_cta;
   const int64_t budget = 72 * 1024;
   int G = static_cast<int>(budget / (per_chan * p.C));
   if (G < 1) {
@@ -670,8 +680,7 @@ int choose_ztree_geometry(Plan& p) {
   }
   z.group_leaves = std::min(G, NL);
   const int gc = z.group_leaves * p.C;
-  z.smem_bytes = static_cast<int>(align_up(static_cast<size_t>(gc) * z.win * es, 16) +
-                                  static_cast<size_t>(4) * z.dms_per_cta * gc);
+  z.smem_bytes = static_cast<int>(static_cast<size_t>(gc) * 2 * wz * es + static_cast<size_t>(4) * z.dms_per_cta * gc);
   // carry depth of each leaf: how many consecutive levels, from the leaves' parents up, it
   // finishes (while the node is the last child of its parent: the B-th or the ragged last)
   p.zcarry.assign(NL, 0);

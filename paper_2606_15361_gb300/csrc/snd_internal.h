@@ -29,6 +29,7 @@ enum : uint32_t {
   kStatusBounds = 1u << 6,
   kStatusTreeTimeout = 1u << 7,
   kStatusGridTimeout = 1u << 8,
+  kStatusMfTimeout = 1u << 9,
 };
 
 // One matched-filter cell kept for peak selection.
@@ -71,6 +72,10 @@ enum {
   kDirBinary4,       // binary, C = 4, <= 4 levels above the leaves
   kDirBinary8,       // binary, <= 8 levels above the leaves
   kDirBinary12,      // binary, <= 12 levels above the leaves (2 words per lane)
+  kDirBinReg4K1,     // binary, regular tree B = 4, K_I = 1, <= 4 levels above level 2
+  kDirBinReg4K2,     // binary, regular tree B = 4, K_I = 2
+  kDirBinReg8K1,     // binary, regular tree B = 8, K_I = 1, <= 3 levels above level 1
+  kDirBinReg8K2,     // binary, regular tree B = 8, K_I = 2
 };
 
 // Direct tree kernel geometry: CTA = 32 consecutive trial DMs (lane = DM) x warps * kw words.
@@ -218,7 +223,8 @@ struct Plan {
   int64_t F = 0;   // scored start times
   int sticky = 0;
   int pending_host = -1;
-  int64_t loop_limit = 0;        // test hook: bound of every bounded device loop (0 = defaults)
+  int64_t loop_limit = 0;        // test hook: bound of the iteration loops (0 = defaults)
+  int64_t wait_limit = 0;        // test hook: bound of the waits, clock cycles (0 = defaults)
   uint32_t last_status = 0;      // device status word read by the last snd_candidates
   mutable int64_t launches = 0;  // kernels enqueued since binding
 

@@ -33,13 +33,14 @@
 
 #include <vector>
 
+#include "bulk.h"
 #include "snd_internal.h"
 
 namespace snd {
 namespace {
 
 constexpr int kDG = 64;                          // channels per adder group (one carry out)
-constexpr long long kDirWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+constexpr long long kDirWaitCycles = kStageWaitCycles;
 
 struct DirArgs {
   const uint32_t* ring;
@@ -74,57 +75,6 @@ struct DirMulti {
   int ntx[kMaxDirBeams];
   DirArgs beam[kMaxDirBeams];
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// non-blocking probe of a phase (try_wait above may suspend the thread for a while first)
-__device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on a phase. With a bound below the default (the loop-limit test hook) the wait
-// only polls, so the bound is all the time it may take.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, long long limit) {
-  const bool poll = limit < kDirWaitCycles;
-  if (poll ? bar_test(bar, parity) : bar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!(poll ? bar_test(bar, parity) : bar_try(bar, parity)))
-    if (clock64() - t0 > limit) return false;
-  return true;
-}
-
-// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
 
 // s += a + b in carry-save form: s keeps the sum bit, the carry (weight x2) is returned
 __device__ __forceinline__ uint32_t fa(uint32_t& s, uint32_t a, uint32_t b) {
@@ -471,6 +421,147 @@ struct DState<kBinary, KW, NPL, MAXU> {
   __device__ __forceinline__ void store(int32_t* row, int j) const { store_bits(row, root[j]); }
 };
 
+// Mode A on a regular tree: B = 4 or 8 (MODE = kBinReg + 10 B + K_I), C = 4, and each level
+// groups B consecutive nodes of the one below (the last node of a level may have fewer). The
+// levels whose nodes lie inside one staged group of 64 channels (16 leaves: up to level 2 for
+// B = 4, level 1 for B = 8) are evaluated per group as a fixed tree of logic operations, with
+// no per-leaf bookkeeping; only the levels above them keep an open node (its two-plane
+// thermometer) from group to group. The same node rules, so the same planes, as the general
+// binary state above.
+constexpr int kBinReg = 100;
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <int MODE, int KW, int NPL, int MAXU>
+struct DState {
+  static constexpr int BB = (MODE - kBinReg) / 10, KI = (MODE - kBinReg) % 10;
+  static_assert(BB == 4 || BB == 8, "regular binary tree: B = 4 or 8");
+  static_assert(KI == 1 || KI == 2, "K_I = 1 or 2");
+  static constexpr int UIN = BB == 4 ? 2 : 1;      // highest level inside a group of 16 leaves
+  static constexpr int SPAN = ipow(BB, UIN);       // leaves under one such node
+  static constexpr int NTOP = 16 / SPAN;           // such nodes per group
+  uint32_t t0[MAXU][KW], t1[MAXU][KW];  // thermometer of the open node of every level > UIN
+  uint32_t root[KW];
+  int cnt[MAXU], node_i[MAXU], fan[MAXU];
+  __device__ __forceinline__ void set_counting(const DirArgs&, long long, bool) {}
+  __device__ __forceinline__ void flush(const DirArgs&, int) {}
+  __device__ __forceinline__ void init(const DirArgs& a) {
+#pragma unroll
+    for (int u = 0; u < MAXU; ++u) {
+#pragma unroll
+      for (int j = 0; j < KW; ++j) t0[u][j] = t1[u][j] = 0;
+      const int l = UIN + 1 + u;
+      cnt[u] = 0;
+      node_i[u] = 0;
+      fan[u] = (l < a.nlev) ? min(a.B, a.level_nodes[l - 1]) : 1;
+    }
+#pragma unroll
+    for (int j = 0; j < KW; ++j) root[j] = 0;
+  }
+  // leaf L0: the quorum >= KL of its four channel bits
+  template <int KL, int L0, typename F>
+  __device__ __forceinline__ void leaf(F& fetch, uint32_t (&v)[KW]) {
+    uint32_t x0[KW], x1[KW], x2[KW], x3[KW];
+    fetch(4 * L0, x0);
+    fetch(4 * L0 + 1, x1);
+    fetch(4 * L0 + 2, x2);
+    fetch(4 * L0 + 3, x3);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+      const uint32_t a0 = x0[j], a1 = x1[j], a2 = x2[j], a3 = x3[j];
+      if constexpr (KL == 1) {
+        v[j] = a0 | a1 | a2 | a3;
+      } else if constexpr (KL == 2) {
+        const uint32_t m3 = (a0 & a1) | (a2 & (a0 | a1));  // >= 2 of a0..a2
+        v[j] = m3 | ((a0 | a1 | a2) & a3);
+      } else if constexpr (KL == 3) {
+        const uint32_t m3 = (a0 & a1) | (a2 & (a0 | a1));
+        v[j] = (a0 & a1 & a2) | (m3 & a3);
+      } else {
+        v[j] = a0 & a1 & a2 & a3;
+      }
+    }
+  }
+  // children I.. of the level-U node over leaves L0.., folded into its thermometer (t0: >= 1
+  // child fired, t1: >= 2)
+  template <int KL, int U, int L0, int I, typename F>
+  __device__ __forceinline__ void children(F& fetch, uint32_t (&s0)[KW], uint32_t (&s1)[KW]) {
+    uint32_t c[KW];
+    node<KL, U - 1, L0 + I * ipow(BB, U - 1)>(fetch, c);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+      if constexpr (I == 0) {
+        s0[j] = c[j];
+        s1[j] = 0u;
+      } else {
+        s1[j] |= s0[j] & c[j];
+        s0[j] |= c[j];
+      }
+    }
+    if constexpr (I + 1 < BB) children<KL, U, L0, I + 1>(fetch, s0, s1);
+  }
+  // the fire bits of the level-U node whose first leaf is L0
+  template <int KL, int U, int L0, typename F>
+  __device__ __forceinline__ void node(F& fetch, uint32_t (&v)[KW]) {
+    if constexpr (U == 0) {
+      leaf<KL, L0>(fetch, v);
+    } else {
+      uint32_t s0[KW], s1[KW];
+      children<KL, U, L0, 0>(fetch, s0, s1);
+#pragma unroll
+      for (int j = 0; j < KW; ++j) v[j] = KI == 2 ? s1[j] : s0[j];
+    }
+  }
+  // a finished level-UIN node goes up the levels kept across groups
+  __device__ __forceinline__ void push(const DirArgs& a, uint32_t (&v)[KW]) {
+    if (UIN == a.nlev - 1) {
+#pragma unroll
+      for (int j = 0; j < KW; ++j) root[j] = v[j];
+      return;
+    }
+#pragma unroll
+    for (int u = 0; u < MAXU; ++u) {
+      const int l = UIN + 1 + u;
+      if (l >= a.nlev) break;
+#pragma unroll
+      for (int j = 0; j < KW; ++j) {
+        t1[u][j] |= t0[u][j] & v[j];
+        t0[u][j] |= v[j];
+      }
+      if (++cnt[u] < fan[u]) return;
+#pragma unroll
+      for (int j = 0; j < KW; ++j) {
+        v[j] = KI == 2 ? t1[u][j] : t0[u][j];
+        t0[u][j] = t1[u][j] = 0;
+      }
+      cnt[u] = 0;
+      ++node_i[u];
+      fan[u] = min(a.B, a.level_nodes[l - 1] - a.B * node_i[u]);
+      if (l == a.nlev - 1) {
+#pragma unroll
+        for (int j = 0; j < KW; ++j) root[j] = v[j];
+      }
+    }
+  }
+  template <int KL, int K, typename F>
+  __device__ __forceinline__ void tops(const DirArgs& a, F& fetch) {
+    uint32_t v[KW];
+    node<KL, UIN, K * SPAN>(fetch, v);
+    push(a, v);
+    if constexpr (K + 1 < NTOP) tops<KL, K + 1>(a, fetch);
+  }
+  template <typename F>
+  __device__ __forceinline__ void group(const DirArgs& a, int, F& fetch) {
+    switch (a.KL) {
+      case 1: tops<1, 0>(a, fetch); break;
+      case 2: tops<2, 0>(a, fetch); break;
+      case 3: tops<3, 0>(a, fetch); break;
+      default: tops<4, 0>(a, fetch); break;
+    }
+  }
+  __device__ __forceinline__ void store(int32_t* row, int j) const { store_bits(row, root[j]); }
+};
+
 // One CTA: DM tile `tile` (32 DMs, lane = DM) x time tile bx (NW warps x KW words).
 // bars: the CTA's two staging mbarriers (initialised once per CTA with one arrival per warp);
 // k0: staging rounds this CTA ran before (round k uses buffer k & 1, phase parity (k >> 1) & 1).
@@ -589,7 +680,7 @@ __device__ __forceinline__ void init_bars(unsigned long long* bars) {
     // one arrival per warp: every warp stages its share of a round
     bar_init(smem_u32(&bars[0]), blockDim.y);
     bar_init(smem_u32(&bars[1]), blockDim.y);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bar_init_fence();
   }
 }
 
@@ -684,6 +775,10 @@ cudaError_t dispatch_direct(int id, F&& f) {
     case kDirBinary4: return f.template go<kBinary, 4, 1, 4>();
     case kDirBinary8: return f.template go<kBinary, 4, 1, 8>();
     case kDirBinary12: return f.template go<kBinary, 2, 1, 12>();
+    case kDirBinReg4K1: return f.template go<kBinReg + 41, 4, 1, 4>();
+    case kDirBinReg4K2: return f.template go<kBinReg + 42, 4, 1, 4>();
+    case kDirBinReg8K1: return f.template go<kBinReg + 81, 4, 1, 3>();
+    case kDirBinReg8K2: return f.template go<kBinReg + 82, 4, 1, 3>();
     default: return cudaErrorInvalidValue;
   }
 }
@@ -714,7 +809,7 @@ void direct_args(const Plan& p, int64_t e_prev, int64_t e_new, DirArgs& a, int* 
   a.plane = dp.plane;
   a.Lp = p.Lp;
   a.status = dp.counters + kCntStatus;
-  a.wait_cycles = p.loop_limit > 0 ? p.loop_limit : kDirWaitCycles;
+  a.wait_cycles = p.wait_limit > 0 ? p.wait_limit : kDirWaitCycles;
   a.e_prev = e_prev;
   a.e_new = e_new;
   a.store = 1;

@@ -1,7 +1,7 @@
 """The direct tree kernel (csrc/tree_direct.cu) against the oracle, over the configurations it
 takes: float at 64 to 4096 channels; graded with the exact level at the root, one or two capped
 levels above it, and caps that bind below the root; binary with every leaf quorum K_L = 1..4,
-K_I = 1..2 and regular and ragged upper levels. Each case streams ragged chunks with injected
+K_I = 1..2, regular and ragged upper levels, and the fixed-logic state of B = 4 and 8. Each case streams ragged chunks with injected
 bursts; every plane cell and the candidate list must equal the C++ oracle's, and the plan must
 report the kernel that the case is meant to exercise. A last case checks that the leaf-sharing
 kernel (SND_FLAG_LEAF_SHARING) and the direct kernel give the same planes on the 1024-channel
@@ -43,6 +43,13 @@ CASES = [
     ("binary-1024-b2-k4", 1024, 2, 33, 400.0, B_, 4, 2, 255, True),
     ("binary-1024-b8-k2", 1024, 8, 64, 900.0, B_, 2, 2, 255, True),
     ("binary-4096-b2-k2", 4096, 2, 32, 200.0, B_, 2, 2, 255, True),
+    # regular trees (B = 4, 8): the in-group levels as fixed logic; the root inside one group
+    # (64 channels at B = 4), just above it (64 at B = 8), and ragged top levels
+    ("binary-64-b4-root-in-group", 64, 4, 40, 80.0, B_, 2, 2, 255, True),
+    ("binary-64-b8-k1", 64, 8, 40, 80.0, B_, 2, 1, 255, True),
+    ("binary-192-b4-k1", 192, 4, 35, 150.0, B_, 1, 1, 255, True),
+    ("binary-1024-b4-k3", 1024, 4, 40, 600.0, B_, 3, 2, 255, True),
+    ("binary-3072-b8-k2", 3072, 8, 33, 300.0, B_, 2, 2, 255, True),
     ("binary-k3-internal-fallback", 256, 2, 20, 100.0, B_, 2, 3, 255, False),
 ]
 
