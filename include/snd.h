@@ -148,7 +148,8 @@ typedef struct {
   int32_t device_status;           /* device status bits read by the last snd_candidates (0 = clean):
                                       1 matched-filter cells, 2 runs, 4 candidates, 8 block candidates
                                       overflowed; 16 threshold search, 32 union-find, 128 tree staging
-                                      wait, 256 grid barrier wait gave up; 64 a cell outside its run */
+                                      wait, 256 grid barrier wait, 512 matched-filter staging wait
+                                      gave up; 64 a cell outside its run */
 } snd_plan_stats_t;
 
 /* Pipeline stages timed by snd_profile / snd_profile_read. */
@@ -258,16 +259,17 @@ int snd_profile_read(snd_plan_t plan, double* ms_out, int64_t* count_out);
 int snd_debug_fail_host_alloc(int32_t after);
 
 /*
- * Test hook (the paper has no counterpart): bound every bounded device loop of this plan's
- * kernels by `limit` (iterations for the union-find walks and the matched filter's threshold
- * search, clock cycles for the tree's staging waits and the many-beam candidate stage's grid
- * barrier; a batch uses its first plan's limit for the barrier). A loop that reaches its bound
- * sets a device status bit and the kernel returns (a staging wait that gives up still waits,
- * with the normal bound, for its copies in flight); snd_candidates then returns
- * SND_ERR_TIMEOUT and snd_plan_stats shows the bits. limit = 0 restores the defaults.
- * Rebinding the workspace clears the status word.
+ * Test hook (the paper has no counterpart): shrink the bounds of this plan's bounded device
+ * loops. `limit` bounds the iteration loops (the union-find walks and the matched filter's
+ * threshold search, in steps); `wait_cycles` bounds the waits (the tree's and the matched
+ * filter's staging waits and the many-beam candidate stage's grid barrier, in clock cycles; a
+ * batch uses its first plan's bound for the barrier). A loop that reaches its bound sets a
+ * device status bit and the kernel returns (a staging wait that gives up still waits, with the
+ * normal bound, for its copies in flight); snd_candidates then returns SND_ERR_TIMEOUT and
+ * snd_plan_stats shows the bits. 0 restores the default of either bound; negative values are
+ * SND_ERR_ARG. Rebinding the workspace clears the status word.
  */
-int snd_debug_loop_limit(snd_plan_t plan, int64_t limit);
+int snd_debug_loop_limit(snd_plan_t plan, int64_t limit, int64_t wait_cycles);
 
 /*
  * Encoder without device allocation (the paper has no counterpart: this is a convenience for

@@ -105,7 +105,7 @@ def _load():
     lib.snd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.snd_encode_static.argtypes = [V, I32, I32, D, V, V]
     lib.snd_debug_fail_host_alloc.argtypes = [I32]
-    lib.snd_debug_loop_limit.argtypes = [P, I64]
+    lib.snd_debug_loop_limit.argtypes = [P, I64, I64]
     lib.snd_level_rates.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), I32,
                                     ctypes.POINTER(I32)]
     lib.snd_level_rates.restype = ctypes.c_int

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <vector>
 
+#include "bulk.h"
 #include "snd_internal.h"
 
 namespace snd {
@@ -46,6 +47,8 @@ struct MfArgs {
   int pf_rows;      // rows resident at once: row d prefetches row d + pf_rows into L2
   int tau_steps;    // bound of the threshold search, steps each way
   int nowrap;       // every prefix sum of the staged segment is below 2^31 (no wrap-around)
+  int stat32;       // a lane's sums of y and y^2 over its groups fit in 32 bits
+  long long wait_cycles;  // bound of the staging wait (clock cycles)
 };
 
 constexpr int kMfThreads = 256;
@@ -63,7 +66,8 @@ __device__ __forceinline__ double snr_of(long long s, double mu_w, double den) {
 
 // One DM row d of one plan's block (the body of k_mf and of the many-beam k_mf_multi).
 __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
-  // smem: 4 words of front pad, then y[0..4*G) with y 16-byte aligned, G = len/4 + 2 groups
+  // smem: 4 words of front pad, then y[0..4*G) with y 16-byte aligned, G = len/4 + 2 groups, and
+  // one spare group
   extern __shared__ __align__(16) int32_t smem[];
   constexpr int NWARP = kMfThreads / 32;
   __shared__ long long red1[NWARP], red2[NWARP];
@@ -78,82 +82,159 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
   int32_t* y = smem + 4;  // y[i] = ring column c0 + i, zero from i = len on
   int4* Y4 = reinterpret_cast<int4*>(y);
   const int G = (len >> 2) + 2;  // groups staged: y[len] and one group past it
-  // 1. stage: aligned group m of y takes global groups m and m+1 of the row (16-byte loads of
-  //    columns c0 - r0 + 4m ...; Lp % 4 == 0, so a group never straddles the ring's wrap point)
-  {
-    const int32_t* src = a.plane + static_cast<size_t>(d) * a.Lp;
-    for (int m = tid; m < G; m += kMfThreads) {
-      int ca = c0 - r0 + 4 * m;
-      if (ca >= a.Lp) ca -= a.Lp;
-      const int4 g0 = __ldg(reinterpret_cast<const int4*>(src + ca));
-      int4 o = g0;
-      if (r0 != 0) {
-        int cb = ca + 4;
-        if (cb >= a.Lp) cb -= a.Lp;
-        const int4 g1 = __ldg(reinterpret_cast<const int4*>(src + cb));
-        if (r0 == 1) o = make_int4(g0.y, g0.z, g0.w, g1.x);
-        else if (r0 == 2) o = make_int4(g0.z, g0.w, g1.x, g1.y);
-        else o = make_int4(g0.w, g1.x, g1.y, g1.z);
-      }
-      const int i = 4 * m;
-      if (i + 3 >= len) {
-        if (i >= len) o.x = 0;
-        if (i + 1 >= len) o.y = 0;
-        if (i + 2 >= len) o.z = 0;
-        if (i + 3 >= len) o.w = 0;
-      }
-      Y4[m] = o;
-    }
-  }
-  __syncthreads();
-  // caller's plane: the newly emitted samples [E_prev, E_new)
-  if (a.plane_out) {
-    const int first = static_cast<int>(a.e_prev - a.f_prev);
-    if (a.out_scale != 0.0f) {
-      float* o = static_cast<float*>(a.plane_out) + static_cast<size_t>(d) * a.nemit;
-      for (int i = tid; i < a.nemit; i += kMfThreads) o[i] = static_cast<float>(y[first + i]) * a.out_scale;
-    } else if (a.out_u8) {
-      uint8_t* o = static_cast<uint8_t*>(a.plane_out) + static_cast<size_t>(d) * a.nemit;
-      for (int i = tid; i < a.nemit; i += kMfThreads) o[i] = static_cast<uint8_t>(y[first + i]);
-    } else {
-      int32_t* o = static_cast<int32_t*>(a.plane_out) + static_cast<size_t>(d) * a.nemit;
-      for (int i = tid; i < a.nemit; i += kMfThreads) o[i] = y[first + i];
-    }
-  }
   const int nb = a.nb;
-  if (nb <= 0) return;
-  // 2. per-warp totals of contiguous group segments, and the exact integer sums over the
-  //    block's start times (y[i], i < nb)
-  // warp 0 also finds the row's thresholds in FP64 (a long dependent chain), so the group
-  // segments of both passes go to warps 1..NWARP-1
+  // groups of the statistics passes: warp 0 also finds the row's thresholds in FP64 (a long
+  // dependent chain), so the contiguous group segments go to warps 1..NWARP-1
   constexpr int NSEG = NWARP - 1;
   const int segg = ((G + NSEG * 32 - 1) / (NSEG * 32)) * 32;
   const int glo = wid == 0 ? 0 : min(G, (wid - 1) * segg), ghi = wid == 0 ? 0 : min(G, glo + segg);
+  // 1. stage the row segment. Bulk path: the TMA engine copies ring columns c0 - r0 ... (16-byte
+  //    aligned) as they are, and the statistics pass below shifts them by sh = r0 in place, so
+  //    that y[i] = column c0 + i. Otherwise each thread loads and realigns its groups (sh = 0).
+  __shared__ int4 bnd[NWARP];  // first staged group of each warp's segment, before the shift
+  int sh = 0;
+  const int32_t* src = a.plane + static_cast<size_t>(d) * a.Lp;
+  const int ng = G + (r0 != 0 ? 1 : 0);  // groups copied by the bulk path
+  if (4 * ng <= a.Lp) {
+    // one thread issues the bulk copies (one, or two across the ring's wrap point) onto an
+    // mbarrier; every thread waits for them (bounded)
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_u32(&bar);
+    if (tid == 0) {
+      bar_init(b, 1);
+      bar_init_fence();
+    }
+    __syncthreads();
+    const int ca0 = c0 - r0;
+    const int n1 = min(ng, (a.Lp - ca0) >> 2);  // groups before the wrap point
+    if (tid == 0) {
+      bar_expect(b, static_cast<uint32_t>(ng) * 16u);
+      bulk_g2s(smem_u32(y), src + ca0, static_cast<uint32_t>(n1) * 16u, b);
+      if (n1 < ng) bulk_g2s(smem_u32(y + 4 * n1), src, static_cast<uint32_t>(ng - n1) * 16u, b);
+    }
+    const bool ok = bar_wait(b, 0, a.wait_cycles);
+    if (!__syncthreads_and(ok)) {
+      // the wait gave up: report it, let the copies land (normal bound) before the CTA leaves
+      if (tid == 0) {
+        atomicOr(&a.counters[kCntStatus], kStatusMfTimeout);
+        bar_wait(b, 0, kStageWaitCycles);
+      }
+      return;
+    }
+    sh = r0;
+    if (lane == 0 && glo < ghi) bnd[wid] = Y4[glo];
+  } else {
+    // aligned group m of y takes global groups m and m+1 of the row (16-byte loads of columns
+    // c0 - r0 + 4m ...; Lp % 4 == 0, so a group never straddles the ring's wrap point); four
+    // groups per thread are loaded before any is stored, so their loads are in flight together
+    constexpr int KB = 4;
+    for (int m0 = tid; m0 < G; m0 += KB * kMfThreads) {
+      int4 g0[KB], g1[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const int m = m0 + k * kMfThreads;
+        if (m >= G) break;
+        int ca = c0 - r0 + 4 * m;
+        if (ca >= a.Lp) ca -= a.Lp;
+        int cb = ca + 4;
+        if (cb >= a.Lp) cb -= a.Lp;
+        g0[k] = __ldg(reinterpret_cast<const int4*>(src + ca));
+        g1[k] = r0 != 0 ? __ldg(reinterpret_cast<const int4*>(src + cb)) : g0[k];
+      }
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const int m = m0 + k * kMfThreads;
+        if (m >= G) break;
+        int4 o = g0[k];
+        if (r0 == 1) o = make_int4(g0[k].y, g0[k].z, g0[k].w, g1[k].x);
+        else if (r0 == 2) o = make_int4(g0[k].z, g0[k].w, g1[k].x, g1[k].y);
+        else if (r0 == 3) o = make_int4(g0[k].w, g1[k].x, g1[k].y, g1[k].z);
+        const int i = 4 * m;
+        if (i + 3 >= len) {
+          if (i >= len) o.x = 0;
+          if (i + 1 >= len) o.y = 0;
+          if (i + 2 >= len) o.z = 0;
+          if (i + 3 >= len) o.w = 0;
+        }
+        Y4[m] = o;
+      }
+    }
+  }
+  __syncthreads();
+  // 2. one pass over each warp's segment: the shift by sh (bulk path) and the zero tail from
+  //    y[len] on, the caller's plane (the newly emitted samples [E_prev, E_new)), the segment's
+  //    total (for the scan) and the exact integer sums over the block's start times (y[i], i < nb)
+  const int first = static_cast<int>(a.e_prev - a.f_prev);
   {
     uint32_t tot = 0;
     long long s1 = 0, s2 = 0;
-    for (int g = glo + lane; g < ghi; g += 32) {
-      const int4 v = Y4[g];
-      tot += static_cast<uint32_t>(v.x) + static_cast<uint32_t>(v.y) + static_cast<uint32_t>(v.z) +
-             static_cast<uint32_t>(v.w);
-      const int i = 4 * g;
-      const long long vx = v.x, vy = v.y, vz = v.z, vw = v.w;
-      if (i + 3 < nb) {
-        s1 += (vx + vy) + (vz + vw);
-        s2 += (vx * vx + vy * vy) + (vz * vz + vw * vw);
-      } else if (i < nb) {
-        s1 += vx;
-        s2 += vx * vx;
-        if (i + 1 < nb) {
-          s1 += vy;
-          s2 += vy * vy;
+    // a lane sums y and y^2 in 32 bits where its groups cannot overflow them (a.stat32), else
+    // in 64 bits; the warp reduction is in 64 bits either way
+    auto pass = [&](auto zero) {
+      using Acc = decltype(zero);
+      Acc a1 = 0, a2 = 0;
+      for (int base = glo; base < ghi; base += 32) {
+        const int g = base + lane;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (g < ghi) {
+          v = Y4[g];
+          if (sh != 0) {
+            // y group g = the last 4 - sh values of staged group g and the first sh of group g + 1
+            // (the next warp's first group as it was before that warp shifted it)
+            const int4 nx = (g + 1 == ghi && g + 1 < G) ? bnd[wid + 1] : Y4[g + 1];
+            if (sh == 1) v = make_int4(v.y, v.z, v.w, nx.x);
+            else if (sh == 2) v = make_int4(v.z, v.w, nx.x, nx.y);
+            else v = make_int4(v.w, nx.x, nx.y, nx.z);
+          }
+          const int i = 4 * g;
+          if (i + 3 >= len) {
+            if (i >= len) v.x = 0;
+            if (i + 1 >= len) v.y = 0;
+            if (i + 2 >= len) v.z = 0;
+            if (i + 3 >= len) v.w = 0;
+          }
         }
-        if (i + 2 < nb) {
-          s1 += vz;
-          s2 += vz * vz;
+        if (sh != 0) __syncwarp();  // every lane has read its next group before any is rewritten
+        if (g < ghi && (sh != 0 || 4 * g + 3 >= len)) Y4[g] = v;
+        if (g >= ghi) continue;
+        const int i = 4 * g;
+        if (a.plane_out && i + 3 >= first && i < first + a.nemit) {
+          const int vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = i + e - first;
+            if (k < 0 || k >= a.nemit) continue;
+            const size_t o = static_cast<size_t>(d) * a.nemit + k;
+            if (a.out_scale != 0.0f) static_cast<float*>(a.plane_out)[o] = static_cast<float>(vv[e]) * a.out_scale;
+            else if (a.out_u8) static_cast<uint8_t*>(a.plane_out)[o] = static_cast<uint8_t>(vv[e]);
+            else static_cast<int32_t*>(a.plane_out)[o] = vv[e];
+          }
+        }
+        const uint32_t gs = static_cast<uint32_t>(v.x) + static_cast<uint32_t>(v.y) + static_cast<uint32_t>(v.z) +
+                            static_cast<uint32_t>(v.w);
+        tot += gs;
+        const Acc vx = static_cast<Acc>(v.x), vy = static_cast<Acc>(v.y), vz = static_cast<Acc>(v.z),
+                  vw = static_cast<Acc>(v.w);
+        if (i + 3 < nb) {
+          a1 += static_cast<Acc>(gs);
+          a2 += (vx * vx + vy * vy) + (vz * vz + vw * vw);
+        } else if (i < nb) {
+          a1 += vx;
+          a2 += vx * vx;
+          if (i + 1 < nb) {
+            a1 += vy;
+            a2 += vy * vy;
+          }
+          if (i + 2 < nb) {
+            a1 += vz;
+            a2 += vz * vz;
+          }
         }
       }
-    }
+      s1 = static_cast<long long>(a1);
+      s2 = static_cast<long long>(a2);
+    };
+    if (a.stat32) pass(0u); else pass(0ll);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
@@ -167,6 +248,7 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
     }
   }
   __syncthreads();
+  if (nb <= 0) return;
   const uint32_t wm = a.width_mask[d];
   if (wid == 0) {
     // row statistics (FP64, fixed order) and, lane j, the integer threshold of width 2^j
@@ -231,15 +313,14 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
     }
   }
   __syncthreads();
-  // the row a CTA of the next wave will stage: its segment into L2 while this row is scored
-  if (d + a.pf_rows < a.ndm) {
+  // the row a CTA of the next wave will stage: its segment into L2 (bulk prefetches, one or two
+  // across the wrap point) while this row is scored
+  if (tid == 0 && d + a.pf_rows < a.ndm) {
     const int32_t* nsrc = a.plane + static_cast<size_t>(d + a.pf_rows) * a.Lp;
-    const int nlines = (4 * G + 31) >> 5;  // 128-byte lines of the staged columns
-    for (int k = tid; k < nlines; k += kMfThreads) {
-      int col = c0 - r0 + 32 * k;
-      if (col >= a.Lp) col -= a.Lp;
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(nsrc + col));
-    }
+    const int gq = min(G + 1, a.Lp >> 2);  // 16-byte groups of the next row's staged columns
+    const int n1 = min(gq, (a.Lp - (c0 - r0)) >> 2);
+    bulk_prefetch_l2(nsrc + (c0 - r0), static_cast<uint32_t>(n1) * 16u);
+    if (n1 < gq) bulk_prefetch_l2(nsrc, static_cast<uint32_t>(gq - n1) * 16u);
   }
   const int nbw = (nb + 31) >> 5;
   uint32_t* mrow = a.mask + static_cast<size_t>(d) * a.mw;
@@ -292,16 +373,16 @@ __device__ __forceinline__ void mf_row(const MfArgs& a, const int d) {
       upd(h2, q.z, p.z, tw[2]);
       upd(h3, q.w, p.w, tw[2]);
     }
+    auto wide = [&](int j) {
+      const uint4 e = P4[m + (1 << (j - 2))];
+      upd(h0, e.x, p.x, tw[j]);
+      upd(h1, e.y, p.y, tw[j]);
+      upd(h2, e.z, p.z, tw[j]);
+      upd(h3, e.w, p.w, tw[j]);
+    };
 #pragma unroll
-    for (int j = 3; j < kNumWidthSlots; ++j) {
-      if (ALL || ((wm >> j) & 1u)) {
-        const uint4 e = P4[m + (1 << (j - 2))];
-        upd(h0, e.x, p.x, tw[j]);
-        upd(h1, e.y, p.y, tw[j]);
-        upd(h2, e.z, p.z, tw[j]);
-        upd(h3, e.w, p.w, tw[j]);
-      }
-    }
+    for (int j = 3; j < kNumWidthSlots; ++j)
+      if (ALL || ((wm >> j) & 1u)) wide(j);
     if constexpr (NOWRAP)
       return (h0 >= static_cast<int>(p.x) ? 1u : 0u) | (h1 >= static_cast<int>(p.y) ? 2u : 0u) |
              (h2 >= static_cast<int>(p.z) ? 4u : 0u) | (h3 >= static_cast<int>(p.w) ? 8u : 0u);
@@ -409,12 +490,18 @@ bool mf_args(const Plan& p, int64_t e_prev, int64_t e_new, int64_t f_prev, int64
   a.out_u8 = p.plane_u8;
   a.tau_steps = p.loop_limit > 0 ? static_cast<int>(p.loop_limit < 64 ? p.loop_limit : 64) : 64;
   const int len = static_cast<int>(e_new - f_prev);
-  *smem = ((len >> 2) + 3) * 16;  // front pad (4 words) and len/4 + 2 aligned groups
+  *smem = ((len >> 2) + 4) * 16;  // front pad (4 words), len/4 + 2 aligned groups and one more for the
+                                  // bulk copy of a segment that starts off a 16-byte boundary
   {
     // largest root value of the mode times the staged samples bounds every prefix sum
     const double vmax = p.mode == SND_MODE_BINARY ? 1.0 : (p.mode == SND_MODE_GRADED ? p.N : p.nchan);
     a.nowrap = vmax * (len + 8.0) < 2147483647.0 ? 1 : 0;
+    // samples a lane of the statistics pass sums (its groups of the seven-warp segments)
+    const int groups = (len >> 2) + 2;
+    const double per_lane = 4.0 * ((groups + 7 * 32 - 1) / (7 * 32));
+    a.stat32 = per_lane * vmax * vmax < 4294967295.0 ? 1 : 0;
   }
+  a.wait_cycles = p.wait_limit > 0 ? p.wait_limit : kStageWaitCycles;
   return true;
 }
 

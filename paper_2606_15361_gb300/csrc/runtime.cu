@@ -211,9 +211,10 @@ extern "C" int snd_level_rates(snd_plan_t plan, uint64_t* fires_out, double* rat
   return SND_OK;
 }
 
-extern "C" int snd_debug_loop_limit(snd_plan_t plan, int64_t limit) {
-  if (!plan || limit < 0) return SND_ERR_ARG;
+extern "C" int snd_debug_loop_limit(snd_plan_t plan, int64_t limit, int64_t wait_cycles) {
+  if (!plan || limit < 0 || wait_cycles < 0) return SND_ERR_ARG;
   reinterpret_cast<Plan*>(plan)->loop_limit = limit;
+  reinterpret_cast<Plan*>(plan)->wait_limit = wait_cycles;
   return SND_OK;
 }
 
@@ -330,7 +331,8 @@ extern "C" int snd_candidates(snd_plan_t plan, snd_candidate_t* host_out, int32_
   p.pending_host = 0;
   const uint32_t st = cnt[snd::kCntStatus];
   p.last_status = st;
-  if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout | snd::kStatusTreeTimeout | snd::kStatusGridTimeout))
+  if (st & (snd::kStatusTauTimeout | snd::kStatusUnionTimeout | snd::kStatusTreeTimeout | snd::kStatusGridTimeout |
+            snd::kStatusMfTimeout))
     return SND_ERR_TIMEOUT;
   if (st & (snd::kStatusCellOverflow | snd::kStatusRunOverflow | snd::kStatusCandOverflow |
             snd::kStatusBlockCandOverflow | snd::kStatusBounds))

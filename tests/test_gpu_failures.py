@@ -1,11 +1,12 @@
 """Failure detection on the GPU without a GPU fault: the plan's loop-limit test hook
-(snd_debug_loop_limit) shrinks the bound of every bounded device loop, each loop that reaches
-its bound sets a device status bit and its kernel returns, snd_candidates reports
+(snd_debug_loop_limit) shrinks the bounds of the bounded device loops (iterations) and waits
+(clock cycles), each loop that reaches its bound sets a device status bit and its kernel
+returns, snd_candidates reports
 SND_ERR_TIMEOUT, and the context stays usable: after the limit is lifted and the workspace
 rebound (which clears the status word) the same plan gives the oracle's results again.
 
 Bits (include/snd.h, snd_plan_stats_t.device_status): 16 threshold search, 32 union-find,
-128 tree staging wait, 256 grid barrier wait."""
+128 tree staging wait, 256 grid barrier wait, 512 matched-filter staging wait."""
 import pytest
 
 import synth
@@ -20,7 +21,7 @@ if not torch.cuda.is_available():
 
 import paper_2606_15361_gb300 as g  # noqa: E402
 
-TAU, UNION, TREE_WAIT, GRID_WAIT = 16, 32, 128, 256
+TAU, UNION, TREE_WAIT, GRID_WAIT, MF_WAIT = 16, 32, 128, 256, 512
 
 
 def _tuples(arr):
@@ -38,14 +39,15 @@ def test_single_plan_loops_time_out_and_recover():
     chunk = torch.from_numpy(w.chunk_data(0)).cuda()
     plan = g.Plan(w.freqs(), synth.NC_DT, w.dms(), 2, g.MODE_GRADED)
     assert plan.stats().tree_kernel == 1  # the direct kernel with its mbarrier staging waits
-    assert g.lib.snd_debug_loop_limit(plan.handle, 1) == 0
+    assert g.lib.snd_debug_loop_limit(plan.handle, 1, 1) == 0
     plan.execute(chunk)
     _, rc = plan.candidates(check=False)
     st = plan.stats().device_status
-    # the tree's first staging wait gives up (its CTAs stop, so no plane and no islands follow)
-    assert rc == g.ERR["SND_ERR_TIMEOUT"] and st & TREE_WAIT, (rc, st)
+    # the tree's first staging wait gives up (its CTAs stop, so no plane and no islands follow),
+    # and so does the matched filter's row staging wait (a bulk copy cannot land in one cycle)
+    assert rc == g.ERR["SND_ERR_TIMEOUT"] and st & TREE_WAIT and st & MF_WAIT, (rc, st)
     # lift the limit, rebind (clears the status word): the oracle's candidates again
-    assert g.lib.snd_debug_loop_limit(plan.handle, 0) == 0
+    assert g.lib.snd_debug_loop_limit(plan.handle, 0, 0) == 0
     plan.bind()
     plan.execute(chunk)
     got, rc = plan.candidates()
@@ -60,13 +62,13 @@ def test_batch_grid_barrier_times_out_and_recovers():
     chunk = torch.from_numpy(w.chunk_data(0)).cuda()
     plans = [g.Plan(w.freqs(), synth.NC_DT, w.dms(), 2, m) for m in (g.MODE_FLOAT, g.MODE_GRADED)]
     batch = g.Batch(plans)
-    assert g.lib.snd_debug_loop_limit(plans[0].handle, 1) == 0
+    assert g.lib.snd_debug_loop_limit(plans[0].handle, 0, 1) == 0
     batch.execute([chunk, chunk])
     _, rc = plans[1].candidates(check=False)
     assert rc == g.ERR["SND_ERR_TIMEOUT"] and plans[1].stats().device_status & GRID_WAIT
     _, rc = plans[0].candidates(check=False)
     assert rc == g.ERR["SND_ERR_TIMEOUT"] and plans[0].stats().device_status & GRID_WAIT
-    assert g.lib.snd_debug_loop_limit(plans[0].handle, 0) == 0
+    assert g.lib.snd_debug_loop_limit(plans[0].handle, 0, 0) == 0
     for p in plans:
         p.bind()
     batch = g.Batch(plans)
@@ -78,10 +80,11 @@ def test_batch_grid_barrier_times_out_and_recovers():
 
 def test_leaf_sharing_plan_bounds():
     """The leaf-sharing tree has no waits; the union-find walks of a plan with candidates (its
-    islands span several DM rows, so several runs) reach a bound of one step."""
+    islands span several DM rows, so several runs) reach a bound of one step (the waits keep
+    their default bound, so the matched filter's mask is complete)."""
     w = synth.NC64
     plan = g.Plan(w.freqs(), synth.NC_DT, w.dms(), 2, g.MODE_FLOAT, g.options(g.MODE_FLOAT, flags=g.FLAG_LEAF_SHARING))
-    assert g.lib.snd_debug_loop_limit(plan.handle, 1) == 0
+    assert g.lib.snd_debug_loop_limit(plan.handle, 1, 0) == 0
     plan.execute(torch.from_numpy(w.chunk_data(0)).cuda())
     _, rc = plan.candidates(check=False)
     st = plan.stats().device_status
