@@ -328,11 +328,73 @@ struct ConvArgs {
   int cout;
   int ldx;          // elements per input pixel
   float* yTf;       // DX: output [cout][n*h*w] in FP32, no bias or ReLU
+  // POOL (forward): the 2x2 max pooling of the activations instead of yT. pool_cl: pooled map
+  // channels-last p[(b, y2, x2)][cout]; else p[b][(c, y2, x2)] (fc1's input rows)
+  bf16* p;
+  int pool_cl;
 };
 
 // DX: the input gradient of a convolution written as the forward convolution of the output
 // gradient (row-major dY, ldx = 64) with the flipped, channel-transposed kernel (k_cast_w_flip)
-template <int BN, int CIN, bool DX = false>
+// Epilogue of a pooled forward tile (warps 0-3; warp w holds tile rows 32w.., i.e. image row
+// y0 + (w >> 1), columns x0 + 32 (w & 1) + lane). Per 8 channels: bias, ReLU and the BF16
+// rounding of each activation, the horizontal pair by a lane shuffle, and the lower row's
+// pair handed to the upper row's warp through shared memory. The comparison order is
+// k_pool's: v0 (upper left), v1 (upper right), v2, v3, each replacing the best if greater.
+template <int BN>
+__device__ __forceinline__ void pool_epilogue(const ConvArgs& a, int t, int warp, int lane, uint32_t tbase) {
+  __shared__ float xv[2][16][8];
+  const int tpr = a.w >> 6, rp = t / tpr;
+  const int b = rp / (a.h >> 1), y2 = rp - b * (a.h >> 1);
+  const int x2 = (t - rp * tpr) * 32 + (warp & 1) * 16 + (lane >> 1);
+  const int h2 = a.h >> 1, w2 = a.w >> 1;
+  const bool live = b < a.n;
+#pragma unroll 1
+  for (int c = 0; c < BN; c += 8) {
+    float v[8];
+    tmem_ld8(tbase + static_cast<uint32_t>(c), v);
+    float best[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float y = __bfloat162float(__float2bfloat16_rn(fmaxf(v[q] + a.bias[c + q], 0.0f)));
+      const float o = __shfl_xor_sync(0xFFFFFFFFu, y, 1);  // the odd column's value on even lanes
+      // upper row: v0 = y, v1 = o; lower row: v2 = y, v3 = o (v3 wins only if greater)
+      best[q] = o > y ? o : y;
+    }
+    if (warp >= 2 && !(lane & 1)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xv[warp - 2][lane >> 1][q] = best[q];
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (warp < 2 && !(lane & 1) && live) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) {
+        const float l0 = xv[warp][lane >> 1][q], l1 = xv[warp][lane >> 1][q + 1];
+        const float r0 = l0 > best[q] ? l0 : best[q], r1 = l1 > best[q + 1] ? l1 : best[q + 1];
+        const __nv_bfloat162 pr = __floats2bfloat162_rn(r0, r1);
+        pk[q >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+      }
+      if (a.pool_cl) {
+        bf16* dst = a.p + ((static_cast<long long>(b) * h2 + y2) * w2 + x2) * a.cout + c;
+        *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      } else {
+        bf16* dst = a.p + static_cast<long long>(b) * a.cout * h2 * w2 + static_cast<long long>(y2) * w2 + x2;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t word = pk[q >> 1];
+          dst[static_cast<long long>(c + q) * h2 * w2] = __ushort_as_bfloat16(static_cast<unsigned short>((q & 1) ? (word >> 16) : (word & 0xFFFFu)));
+        }
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // xv is rewritten by the next 8 channels
+  }
+}
+
+// POOL: M tiles of two image rows x 64 columns (w % 64 == 0, h even), rows 0-63 the upper
+// row, and the epilogue writes the 2x2 max pooling of the activations (ties to the first of
+// the four in row-major order, as k_pool) instead of the activations.
+template <int BN, int CIN, bool DX = false, bool POOL = false>
 __global__ void __launch_bounds__(288, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mb, ConvArgs a, uint32_t* err) {
   constexpr int KT = (9 * CIN + kBK - 1) / kBK;  // K steps
@@ -341,7 +403,7 @@ __global__ void __launch_bounds__(288, 1)
   extern __shared__ uint8_t gsm_raw[];
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag, epi_fail;
   uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sA = smem_u32(gsm), sB = sA + kStages * kABytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -360,6 +422,7 @@ __global__ void __launch_bounds__(288, 1)
       mbar_init(smem_u32(&bar_tempty[b]), 4);
     }
     abort_flag = 0;
+    epi_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 8) {
@@ -377,15 +440,37 @@ __global__ void __launch_bounds__(288, 1)
   if (warp >= 4 && warp < 8) {
     // producers: thread pr builds row pr of every A tile. K runs tap-major, k = tap*CIN + ci
     // (tap = ky*3 + kx; the weights are permuted to match), so with CIN and the K-step count
-    // known at compile time every element is one load at a fixed per-tap offset.
+    // known at compile time every 8-value chunk is one 16-byte asynchronous copy (cp.async,
+    // zero-filled outside the map) at a fixed per-tap offset. Each K step's copies are one
+    // commit group; a step is handed to the MMA (proxy fence, then the stage's arrival) two
+    // steps later, so three steps of copies are in flight per thread.
+    constexpr int kLag = 2;
     const int pr = threadIdx.x - 128;
     int it = 0;
-    for (int t = blockIdx.x; t < mt && !*abort_v; t += gridDim.x) {
-      const long long m = static_cast<long long>(t) * kBM + pr;
-      const bool mv = m < M;
-      const int b = mv ? static_cast<int>(m / hw) : 0;
-      const int yx = mv ? static_cast<int>(m - b * hw) : 0;
-      const int yy = yx / a.w, xx = yx - yy * a.w;
+    bool quit = false;
+    auto complete = [&](int step) {
+      const uint32_t fb = smem_u32(&bar_full[step % kStages]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(fb);
+    };
+    for (int t = blockIdx.x; t < mt && !quit && !*abort_v; t += gridDim.x) {
+      int b, yy, xx;
+      bool mv;
+      if constexpr (POOL) {
+        const int tpr = a.w >> 6, rp = t / tpr;
+        b = rp / (a.h >> 1);
+        yy = 2 * (rp - b * (a.h >> 1)) + (pr >> 6);
+        xx = (t - rp * tpr) * 64 + (pr & 63);
+        mv = b < a.n;
+        if (!mv) b = yy = xx = 0;
+      } else {
+        const long long m = static_cast<long long>(t) * kBM + pr;
+        mv = m < M;
+        b = mv ? static_cast<int>(m / hw) : 0;
+        const int yx = mv ? static_cast<int>(m - b * hw) : 0;
+        yy = yx / a.w;
+        xx = yx - yy * a.w;
+      }
       const bf16* xb = a.x + static_cast<long long>(b) * hw * a.ldx;  // channels-last input
       const bf16* tp[9];
       bool tv[9];
@@ -395,7 +480,6 @@ __global__ void __launch_bounds__(288, 1)
         tv[tap] = mv && sy >= 0 && sy < a.h && sx >= 0 && sx < a.w;
         tp[tap] = xb + (tv[tap] ? (sy * a.w + sx) * a.ldx : 0);
       }
-      bool quit = false;
 #pragma unroll
       for (int i = 0; i < KT; ++i, ++it) {
         const int s = it % kStages;
@@ -405,32 +489,35 @@ __global__ void __launch_bounds__(288, 1)
           quit = true;
           break;
         }
-        const uint32_t fb = smem_u32(&bar_full[s]);
         if (pr == 0) {
+          const uint32_t fb = smem_u32(&bar_full[s]);
           mbar_expect_tx_only(fb, kBBytes);
           tma_load_2d(sB + s * kBBytes, &mb, fb, i * kBK, 0);
         }
         const uint32_t rowaddr = sA + s * kABytes + pr * 128;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          // the 8 K values of chunk q are 8 consecutive channels of one tap (CIN % 8 == 0):
-          // one 16-byte load from the channels-last map
+          // the 8 K values of chunk q are 8 consecutive channels of one tap (CIN % 8 == 0)
           constexpr int kc = 9 * CIN;
           const int k0 = i * kBK + q * 8;  // compile-time after unrolling
           const int tap = k0 / CIN, ci0 = k0 % CIN;
-          uint4 pk = make_uint4(0u, 0u, 0u, 0u);
-          if (k0 < kc && tv[tap < 9 ? tap : 0]) pk = __ldg(reinterpret_cast<const uint4*>(tp[tap < 9 ? tap : 0] + ci0));
+          const bool valid = k0 < kc && tv[tap < 9 ? tap : 0];
+          const bf16* src = tp[tap < 9 ? tap : 0] + (k0 < kc ? ci0 : 0);
           const uint32_t dst = rowaddr + ((q ^ (pr & 7)) << 4);
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk.x), "r"(pk.y), "r"(pk.z),
-                       "r"(pk.w)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
                        : "memory");
         }
-        // the tensor core reads shared memory through the async proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(fb);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (it >= kLag) {
+          asm volatile("cp.async.wait_group %0;" ::"n"(kLag) : "memory");
+          complete(it - kLag);
+        }
       }
-      if (quit) break;
     }
+    // the last steps' copies (also before leaving after an abort: no copy may still be in flight)
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (!quit)
+      for (int st = it - kLag < 0 ? 0 : it - kLag; st < it; ++st) complete(st);
   } else if (warp == 8) {
     if (lane == 0) {
       constexpr uint32_t idesc = mma_idesc(BN);
@@ -470,6 +557,13 @@ __global__ void __launch_bounds__(288, 1)
       const int b = j & 1;
       bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[b]), (j >> 1) & 1);
       ok = __all_sync(0xFFFFFFFFu, ok);
+      if constexpr (POOL) {
+        // the pooled epilogue's warps meet at named barriers: they stop together (the flag is
+        // only set before this barrier and read after it)
+        if (!ok && lane == 0) epi_fail = 1;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        ok = !*reinterpret_cast<volatile int*>(&epi_fail);
+      }
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrWait);
         *abort_v = 1;
@@ -478,6 +572,9 @@ __global__ void __launch_bounds__(288, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long row = static_cast<long long>(t) * kBM + warp * 32 + lane;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(b * BN);
+      if constexpr (POOL) {
+        pool_epilogue<BN>(a, t, warp, lane, tbase);
+      } else {
 #pragma unroll 1
       for (int c = 0; c < BN; c += 8) {
         float v[8];
@@ -493,6 +590,7 @@ __global__ void __launch_bounds__(288, 1)
             a.yT[static_cast<long long>(n) * M + row] = __float2bfloat16_rn(fmaxf(v[q] + a.bias[n], 0.0f));
           }
         }
+      }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -1035,25 +1133,32 @@ int gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int 
 
 // Forward 3x3 convolution of a [cin][n][h][w] BF16 map on the tensor cores (k_conv_tc):
 // Y^T[cout][m] = relu(conv + bias), weights wb[cout][kp] BF16.
+// With pool set, the 2x2 max pooling of Y is written instead (pool_cl: channels-last
+// [(b, y2, x2)][cout], else [b][(c, y2, x2)]).
 int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const bf16* wb, int cout,
-            const float* bias, bf16* yT, uint32_t* err, cudaStream_t s, int64_t* launches) {
+            const float* bias, bf16* yT, uint32_t* err, cudaStream_t s, int64_t* launches, bf16* pool = nullptr,
+            int pool_cl = 0) {
   const int BN = cout <= 32 ? 32 : 64;
   if (cout > 64) return SND_ERR_UNSUPPORTED;
+  if (pool && (w % 64 != 0 || h % 2 != 0 || cout % 8 != 0)) return SND_ERR_UNSUPPORTED;
   CUtensorMap mb;
   if (!make_map(&mb, wb, kp, cout, kp, BN)) return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout, cin, nullptr};
+  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout, cin, nullptr, pool, pool_cl};
   const long long M = 1LL * n * h * w;
   const long long mt = (M + kBM - 1) / kBM;
   const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
   const int per_sm = std::max(1, (227 * 1024) / smem);
   const unsigned grid = static_cast<unsigned>(std::min<long long>(mt, 152LL * per_sm));
   cudaError_t e;
+  auto go = [&](auto kern) {
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r == cudaSuccess) kern<<<grid, 288, smem, s>>>(mb, a, err);
+    return r;
+  };
   if (cin == 16 && BN == 32) {
-    e = cudaFuncSetAttribute(k_conv_tc<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) k_conv_tc<32, 16><<<grid, 288, smem, s>>>(mb, a, err);
+    e = pool ? go(k_conv_tc<32, 16, false, true>) : go(k_conv_tc<32, 16>);
   } else if (cin == 32 && BN == 64) {
-    e = cudaFuncSetAttribute(k_conv_tc<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) k_conv_tc<64, 32><<<grid, 288, smem, s>>>(mb, a, err);
+    e = pool ? go(k_conv_tc<64, 32, false, true>) : go(k_conv_tc<64, 32>);
   } else {
     return SND_ERR_UNSUPPORTED;
   }
@@ -1224,6 +1329,14 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
     if (l == 0) {
       k_conv1<<<grid_for(m), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]));
       f.launches++;
+    } else if (!f.training) {
+      // inference: implicit GEMM with the pooling in its epilogue (channels-last for conv3,
+      // fc1's feature rows after conv3)
+      int rc = conv_tc(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, c.kc, c.kp, at<bf16>(f, f.o.wb[l]), c.cout,
+                       P + kOffB[l], nullptr, err, s, &f.launches, l == 1 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3),
+                       l == 1 ? 1 : 0);
+      if (rc) return rc;
+      continue;
     } else {
       // implicit GEMM: the patches are gathered on chip, no im2col buffer
       int rc = conv_tc(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, c.kc, c.kp, at<bf16>(f, f.o.wb[l]), c.cout,
