@@ -668,19 +668,19 @@ int choose_ztree_geometry(Plan& p) {
   if (spread > (1 << 20)) return SND_ERR_UNSUPPORTED;
   const int es = z.fp16 ? 2 : 4;
   z.win = static_cast<int>(align_up(static_cast<size_t>(z.tile_samples + spread), 8));
-  // per staged channel: its window twice (as stored and shifted by one value, each with a
-  // 16-byte alignment slack and one spare chunk) and the tile's DM offsets into it
+  // per staged channel and buffer (two buffers: one filled while the other is read): its
+  // window with a 16-byte alignment slack and one spare chunk, and the tile's DM offsets
   const int64_t wz = z.win + 2 * (16 / es);
-  const int64_t per_chan = 2 * wz * es + 4 * z.dms_per_cta;
-  const int64_t budget = 72 * 1024;
+  const int64_t per_chan = wz * es + 4 * z.dms_per_cta;
+  const int64_t budget = 52 * 1024;
   int G = static_cast<int>(budget / (per_chan * p.C));
   if (G < 1) {
     G = 1;
-    if (per_chan * p.C > 200 * 1024) return SND_ERR_UNSUPPORTED;
+    if (2 * per_chan * p.C > 200 * 1024) return SND_ERR_UNSUPPORTED;
   }
   z.group_leaves = std::min(G, NL);
   const int gc = z.group_leaves * p.C;
-  z.smem_bytes = static_cast<int>(static_cast<size_t>(gc) * 2 * wz * es + static_cast<size_t>(4) * z.dms_per_cta * gc);
+  z.smem_bytes = static_cast<int>(2 * (static_cast<size_t>(gc) * wz * es + static_cast<size_t>(4) * z.dms_per_cta * gc));
   // carry depth of each leaf: how many consecutive levels, from the leaves' parents up, it
   // finishes (while the node is the last child of its parent: the B-th or the ragged last)
   p.zcarry.assign(NL, 0);

@@ -10,13 +10,14 @@
 //
 // CTA = 16 trial DMs (one warp each) x 64*NP consecutive output samples; lane L holds the
 // sample pairs t0 + 64 j + 2 L, + 1 (slot j). Leaves are processed in groups whose channel
-// windows (the tile's smallest delay per channel onwards, tile width + the tile's delay
-// spread) are staged from the payload ring in shared memory, twice (as stored and shifted by
-// one value) so that every pair is one aligned load. The open nodes of every level are
-// per-thread FP32 registers (MAXL levels x 2 NP samples).
+// windows (from a 16-byte aligned ring position at or before the tile's smallest delay per
+// channel: tile width + the tile's delay spread) are copied by the TMA engine into one of two
+// shared-memory buffers while the previous group is summed from the other. The open nodes of
+// every level are per-thread FP32 registers (MAXL levels x 2 NP samples).
 
 #include <cuda_fp16.h>
 
+#include "bulk.h"
 #include "snd_internal.h"
 
 namespace snd {
@@ -36,6 +37,8 @@ struct ZArgs {
   long long ostride;
   int omode, Lp;
   float scale;
+  uint32_t* status;        // plan status word (a staging wait that gives up sets kStatusTreeTimeout)
+  long long wait_cycles;   // bound of a staging wait (clock cycles)
 };
 
 // Two consecutive stored values x = (lo, hi) added to two FP32 sums: lo_sum += lo, hi_sum += hi,
@@ -60,27 +63,32 @@ __device__ __forceinline__ float add_stored(float parent, float v, const __half*
 }
 __device__ __forceinline__ float add_stored(float parent, float v, const float*) { return __fadd_rn(parent, v); }
 
+// the pair (window[i], window[i + 1]) of a staged channel window, i = 2 k + odd: one aligned
+// load, or for an odd start two aligned words and a byte permute
+__device__ __forceinline__ uint32_t load_pair(const __half* w, int k, bool odd) {
+  const uint32_t* W = reinterpret_cast<const uint32_t*>(w);
+  if (!odd) return W[k];
+  return __byte_perm(W[k], W[k + 1], 0x5432);
+}
+__device__ __forceinline__ uint2 load_pair(const float* w, int k, bool odd) {
+  if (!odd) return reinterpret_cast<const uint2*>(w)[k];
+  return make_uint2(__float_as_uint(w[2 * k + 1]), __float_as_uint(w[2 * k + 2]));
+}
 template <typename ST> struct PairT;           // two stored values
 template <> struct PairT<__half> { using T = uint32_t; };
 template <> struct PairT<float> { using T = uint2; };
 
-// one 16-byte chunk of stored values shifted by one value: (a1 .. a_last, b0)
-__device__ __forceinline__ uint4 shift_one(uint4 a, uint4 b, const __half*) {
-  return make_uint4(__byte_perm(a.x, a.y, 0x5432), __byte_perm(a.y, a.z, 0x5432), __byte_perm(a.z, a.w, 0x5432),
-                    __byte_perm(a.w, b.x, 0x5432));
-}
-__device__ __forceinline__ uint4 shift_one(uint4 a, uint4 b, const float*) { return make_uint4(a.y, a.z, a.w, b.x); }
-
 // CTA = DT trial DMs (one warp each) x 64 NP consecutive output samples: lane L holds samples
-// t0 + 64 j + 2 L and + 1 (pair slot j < NP). Per staged channel, shared memory holds its window
-// twice: as stored (copy 0) and shifted by one value (copy 1), both from a 16-byte aligned ring
-// position; a DM whose offset into the window is even reads its pairs from copy 0, odd from
-// copy 1, so every pair is one aligned 4- (FP16) or 8-byte (FP32) load.
+// t0 + 64 j + 2 L and + 1 (pair slot j < NP). Leaves are processed in groups of G; a group's
+// channel windows (each from a 16-byte aligned ring position: the tile's smallest delay, the
+// tile width and its delay spread) are copied by the TMA engine into one of two shared-memory
+// buffers while the previous group is summed from the other, so staging overlaps the adds.
 template <typename ST, int MAXL, int NP, int CT>
-__global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
+__global__ void __launch_bounds__(512, 2) k_tree_z(const __grid_constant__ ZArgs a) {
   using P2 = typename PairT<ST>::T;
-  constexpr int EPC = 16 / sizeof(ST);  // stored values per 16-byte chunk
+  constexpr int EPC = 16 / sizeof(ST);  // stored values per 16 bytes
   extern __shared__ __align__(16) unsigned char zsm[];
+  __shared__ __align__(8) unsigned long long bars[2];
   const int DT = blockDim.y;
   const int lane = threadIdx.x, wd = threadIdx.y, tid = wd * 32 + lane, nthr = 32 * DT;
   const int tile = blockIdx.y;
@@ -88,12 +96,49 @@ __global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
   const int d = tile * DT + wd;
   const bool active = d < a.ndm;
   const int GC = a.G * a.C;
-  const int WZ = a.win + 2 * EPC;  // staged values per copy: the window, its alignment slack and one chunk
-  const int nck = WZ / EPC;        // chunks per copy
-  ST* win = reinterpret_cast<ST*>(zsm);  // [GC][2][WZ]
-  int* drel = reinterpret_cast<int*>(zsm + static_cast<size_t>(GC) * 2 * WZ * sizeof(ST));
+  const int WZ = a.win + 2 * EPC;  // staged values per channel: the window, its slack and one chunk
+  const size_t bufb = static_cast<size_t>(GC) * WZ * sizeof(ST) + static_cast<size_t>(4) * DT * GC;
   const ST* ring = static_cast<const ST*>(a.zring);
   const int* wb = a.zwb + static_cast<size_t>(tile) * a.nchan;
+  const int ngroups = (a.nleaves + a.G - 1) / a.G;
+  if (tid == 0) {
+    bar_init(smem_u32(&bars[0]), 1);
+    bar_init(smem_u32(&bars[1]), 1);
+    bar_init_fence();
+  }
+  __syncthreads();
+
+  // stage group gi into buffer gi & 1: warp 0 issues one bulk copy per channel window (two
+  // across the ring's end) after announcing the bytes; every thread fills the DM offsets
+  auto issue = [&](int gi) {
+    unsigned char* buf = zsm + (gi & 1) * bufb;
+    ST* win = reinterpret_cast<ST*>(buf);
+    int* drel = reinterpret_cast<int*>(buf + static_cast<size_t>(GC) * WZ * sizeof(ST));
+    const int c0 = gi * a.G * a.C, nc = min(a.nchan, (gi + 1) * a.G * a.C) - c0;
+    if (wd == 0) {
+      const uint32_t bar = smem_u32(&bars[gi & 1]);
+      // the buffer was last read by generic loads, before the barrier that ended that group
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (lane == 0) bar_expect(bar, static_cast<uint32_t>(nc) * WZ * sizeof(ST));
+      __syncwarp();
+      for (int cl = lane; cl < nc; cl += 32) {
+        const int c = c0 + cl;
+        const ST* row = ring + static_cast<size_t>(c) * a.Rz;
+        const int r0 = static_cast<int>(((tb + wb[c]) & ~static_cast<long long>(EPC - 1)) % a.Rz);
+        const int n1 = min(WZ, a.Rz - r0);
+        ST* dst = win + static_cast<size_t>(cl) * WZ;
+        bulk_g2s(smem_u32(dst), row + r0, static_cast<uint32_t>(n1 * sizeof(ST)), bar);
+        if (n1 < WZ) bulk_g2s(smem_u32(dst + n1), row, static_cast<uint32_t>((WZ - n1) * sizeof(ST)), bar);
+      }
+    }
+    for (int i = tid; i < DT * nc; i += nthr) {
+      const int w = i / nc, cl = i - w * nc;
+      const int dd = min(tile * DT + w, a.ndm - 1);
+      const int c = c0 + cl;
+      const int slack = static_cast<int>((tb + wb[c]) & (EPC - 1));
+      drel[w * GC + cl] = a.delays[static_cast<size_t>(dd) * a.nchan + c] - wb[c] + slack;
+    }
+  };
 
   float acc[MAXL][2 * NP];
   float root[2 * NP];
@@ -104,99 +149,82 @@ __global__ void __launch_bounds__(512, 2) k_tree_z(ZArgs a) {
 #pragma unroll
   for (int j = 0; j < 2 * NP; ++j) root[j] = 0.0f;
 
-  for (int k0 = 0; k0 < a.nleaves; k0 += a.G) {
-    const int k1 = min(a.nleaves, k0 + a.G);
-    const int c0 = k0 * a.C, nc = min(a.nchan, k1 * a.C) - c0;
-    __syncthreads();  // the previous group's readers are done
-    // stage: a warp per channel, chunk q of it from ring samples (start & ~(EPC-1)) + EPC q
-    // (Rz is a multiple of EPC, so a chunk never straddles the ring's end)
-    for (int cl = wd; cl < nc; cl += DT) {
-      const int c = c0 + cl;
-      const ST* row = ring + static_cast<size_t>(c) * a.Rz;
-      const int r0 = static_cast<int>(((tb + wb[c]) & ~static_cast<long long>(EPC - 1)) % a.Rz);
-      ST* dst = win + static_cast<size_t>(cl) * 2 * WZ;
-      for (int q = lane; q < nck; q += 32) {
-        int r = r0 + q * EPC;
-        if (r >= a.Rz) r -= a.Rz;
-        const uint4 x = *reinterpret_cast<const uint4*>(row + r);
-        r += EPC;
-        if (r >= a.Rz) r -= a.Rz;
-        const uint4 y = *reinterpret_cast<const uint4*>(row + r);
-        *reinterpret_cast<uint4*>(dst + q * EPC) = x;
-        *reinterpret_cast<uint4*>(dst + WZ + q * EPC) = shift_one(x, y, ring);
+  issue(0);
+  __syncthreads();  // group 0's DM offsets
+  for (int gi = 0; gi < ngroups; ++gi) {
+    if (gi + 1 < ngroups) issue(gi + 1);  // its buffer was released by the last barrier
+    const bool ok = bar_wait(smem_u32(&bars[gi & 1]), (gi >> 1) & 1, a.wait_cycles);
+    if (__syncthreads_or(!ok)) {
+      // a staging wait ran out: report it, and let the copies in flight land (normal bound)
+      // before the CTA's shared memory is released
+      if (tid == 0) {
+        atomicOr(a.status, kStatusTreeTimeout);
+        for (int g2 = gi; g2 < gi + 2 && g2 < ngroups; ++g2)
+          bar_wait(smem_u32(&bars[g2 & 1]), (g2 >> 1) & 1, kStageWaitCycles);
       }
+      return;
     }
-    for (int i = tid; i < DT * nc; i += nthr) {
-      const int w = i / nc, cl = i - w * nc;
-      const int dd = min(tile * DT + w, a.ndm - 1);
-      const int c = c0 + cl;
-      const int slack = static_cast<int>((tb + wb[c]) & (EPC - 1));
-      drel[w * GC + cl] = a.delays[static_cast<size_t>(dd) * a.nchan + c] - wb[c] + slack;
-    }
-    __syncthreads();
-    if (!active) continue;
-    // pairs of channel cl: copy (rel & 1), pair index rel / 2 + 32 j + lane
-    auto pairs = [&](int cl) -> const P2* {
-      const int rel = drel[wd * GC + cl];
-      return reinterpret_cast<const P2*>(win + static_cast<size_t>(cl) * 2 * WZ + (rel & 1) * WZ + (rel & ~1)) + lane;
-    };
-    for (int k = k0; k < k1; ++k) {
-      const int cl0 = (k - k0) * a.C;
-      const int cn = min(a.C, a.nchan - k * a.C);
-      float v[2 * NP];
+    const unsigned char* buf = zsm + (gi & 1) * bufb;
+    const ST* win = reinterpret_cast<const ST*>(buf);
+    const int* drel = reinterpret_cast<const int*>(buf + static_cast<size_t>(GC) * WZ * sizeof(ST));
+    const int k0 = gi * a.G, k1 = min(a.nleaves, k0 + a.G);
+    if (active) {
+      for (int k = k0; k < k1; ++k) {
+        const int cl0 = (k - k0) * a.C;
+        const int cn = min(a.C, a.nchan - k * a.C);
+        float v[2 * NP];
 #pragma unroll
-      for (int j = 0; j < 2 * NP; ++j) v[j] = 0.0f;
-      if (CT) {
-        // C channels known at compile time: all C x NP loads of the leaf are independent
-        P2 x[CT > 0 ? CT : 1][NP];
+        for (int j = 0; j < 2 * NP; ++j) v[j] = 0.0f;
+        auto add_channel = [&](int cl) {
+          const int rel = drel[wd * GC + cl];
+          const ST* w = win + static_cast<size_t>(cl) * WZ;
+          const int kb = (rel >> 1) + lane;
+          const bool odd = rel & 1;
+          P2 x[NP];
 #pragma unroll
-        for (int ci = 0; ci < CT; ++ci) {
-          const P2* src = pairs(cl0 + ci);
+          for (int j = 0; j < NP; ++j) x[j] = load_pair(w, kb + 32 * j, odd);
 #pragma unroll
-          for (int j = 0; j < NP; ++j) x[ci][j] = src[32 * j];
+          for (int j = 0; j < NP; ++j) add_pair(v[2 * j], v[2 * j + 1], x[j], ring);
+        };
+        if (CT) {
+#pragma unroll
+          for (int ci = 0; ci < (CT > 0 ? CT : 1); ++ci) add_channel(cl0 + ci);
+        } else {
+          for (int ci = 0; ci < cn; ++ci) add_channel(cl0 + ci);
         }
+        if (a.nlev == 1) {  // a single leaf is the root: its FP32 sum is not stored
 #pragma unroll
-        for (int ci = 0; ci < CT; ++ci)
-#pragma unroll
-          for (int j = 0; j < NP; ++j) add_pair(v[2 * j], v[2 * j + 1], x[ci][j], ring);
-      } else {
-        for (int ci = 0; ci < cn; ++ci) {
-          const P2* src = pairs(cl0 + ci);
-#pragma unroll
-          for (int j = 0; j < NP; ++j) add_pair(v[2 * j], v[2 * j + 1], src[32 * j], ring);
+          for (int j = 0; j < 2 * NP; ++j) root[j] = v[j];
+          continue;
         }
-      }
-      if (a.nlev == 1) {  // a single leaf is the root: its FP32 sum is not stored
+        // the stored leaf goes into its parent's sum (acc[l] holds the open node of level
+        // l + 1); when it is the parent's last child the parent is finished, and so on up
+        // `depth` levels. depth depends on the leaf only, so the branch is warp-uniform and
+        // taken by one leaf in B.
 #pragma unroll
-        for (int j = 0; j < 2 * NP; ++j) root[j] = v[j];
-        continue;
-      }
-      // the stored leaf goes into its parent's sum (acc[l] holds the open node of level l + 1);
-      // when it is the parent's last child the parent is finished, and so on up `depth`
-      // levels. depth depends on the leaf only, so the branch is warp-uniform and taken by one
-      // leaf in B.
+        for (int j = 0; j < 2 * NP; ++j) acc[0][j] = add_stored(acc[0][j], v[j], ring);
+        const int depth = __ldg(a.carry + k);
+        if (depth > 0) {
 #pragma unroll
-      for (int j = 0; j < 2 * NP; ++j) acc[0][j] = add_stored(acc[0][j], v[j], ring);
-      const int depth = __ldg(a.carry + k);
-      if (depth > 0) {
+          for (int l = 0; l + 1 < MAXL; ++l) {
+            if (l < depth) {
+              const bool to_root = (l + 1 == a.nlev - 1);
 #pragma unroll
-        for (int l = 0; l + 1 < MAXL; ++l) {
-          if (l < depth) {
-            const bool to_root = (l + 1 == a.nlev - 1);
-#pragma unroll
-            for (int j = 0; j < 2 * NP; ++j) {
-              const float x = acc[l][j];
-              acc[l][j] = 0.0f;
-              if (to_root) {
-                root[j] = x;
-              } else {
-                acc[l + 1][j] = add_stored(acc[l + 1][j], x, ring);
+              for (int j = 0; j < 2 * NP; ++j) {
+                const float x = acc[l][j];
+                acc[l][j] = 0.0f;
+                if (to_root) {
+                  root[j] = x;
+                } else {
+                  acc[l + 1][j] = add_stored(acc[l + 1][j], x, ring);
+                }
               }
             }
           }
         }
       }
     }
+    __syncthreads();  // every reader of this buffer is done: the group after next may refill it
   }
   if (!active) return;
   float* orow = a.out + static_cast<size_t>(d) * a.ostride;
@@ -252,6 +280,8 @@ cudaError_t launch_tree_z(const Plan& p, int64_t e_prev, int64_t e_new, void* d_
   }
   a.Lp = p.Lp;
   a.scale = static_cast<float>(1.0 / std::sqrt(static_cast<double>(p.nchan)));
+  a.status = p.dp.counters + kCntStatus;
+  a.wait_cycles = p.wait_limit > 0 ? p.wait_limit : kStageWaitCycles;
   dim3 block(32, z.dms_per_cta);
   dim3 grid(static_cast<unsigned>((a.nout + z.tile_samples - 1) / z.tile_samples), z.ndm_tiles);
   p.launches += 1;
