@@ -605,6 +605,211 @@ __global__ void __launch_bounds__(288, 1)
   }
 }
 
+// ---------------------------------------------------------------- halo convolution
+
+// shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x 16 bytes
+// (rows 16 bytes apart), lbo bytes between core matrices along K, sbo along M / N
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version; layout type 0: no swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// Forward 3x3 convolution with its 2x2 max pooling (inference), without any gather. A work
+// item is one pair of image rows (y0, y0 + 1) of one snippet. The TMA engine loads the four
+// input rows y0 - 1 .. y0 + 2 of the channels-last map three times, shifted by -1, 0 and +1
+// pixel, as 8-channel planes (16 bytes a pixel; pixels outside the map read as zero), so the
+// A operand of tap (ky, kx) is a plain K-major view into the kx copy starting ky rows down:
+// 128 consecutive pixels, 8 channels per core matrix, the next 8 channels one plane further.
+// W = 128: an M tile is one image row (two tiles per item, their accumulators side by side);
+// W = 64: one tile of both rows. The weights sit in shared memory as [tap][plane][cout][8].
+// 192 threads: warps 0-3 pool and store from TMEM, warp 4 issues the TMA loads, warp 5 owns
+// TMEM and issues the MMAs; items are double buffered in TMEM and shared memory.
+template <int CIN, int COUT, int W>
+__global__ void __launch_bounds__(192, 1)
+    k_conv_halo(const __grid_constant__ CUtensorMap mx, ConvArgs a, const bf16* __restrict__ wb, int kp,
+                uint32_t* err) {
+  constexpr int NPL = CIN / 8;                 // 8-channel planes
+  constexpr int PB = 4 * W * 16;               // bytes of one plane copy (4 rows)
+  constexpr int SB = 3 * NPL * PB;             // bytes of one stage (three shifted copies)
+  constexpr int T = W == 128 ? 2 : 1;          // M tiles per item
+  constexpr int KS = NPL / 2;                  // K steps of 16 per tap
+  constexpr int S = 2;                         // stages
+  constexpr uint32_t kCols = 2 * T * COUT < 32 ? 32 : 2 * T * COUT;
+  static_assert(W == 128 || W == 64, "tile geometry");
+  extern __shared__ uint8_t hsm_raw[];
+  __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S], bar_tfull[2], bar_tempty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag, epi_fail;
+  uint8_t* hsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(hsm_raw) + 127) & ~uintptr_t(127));
+  const uint32_t sX = smem_u32(hsm), sW = sX + S * SB;
+  bf16* wsm = reinterpret_cast<bf16*>(hsm + S * SB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = a.n * (a.h >> 1);
+
+  // weights: wb[co][tap * CIN + ci] (tap-major K) -> wsm[((tap * NPL + ci / 8) * COUT + co) * 8 + ci % 8]
+  for (int i = threadIdx.x; i < COUT * 9 * CIN; i += blockDim.x) {
+    const int co = i / (9 * CIN), k = i - co * (9 * CIN);
+    const int tap = k / CIN, ci = k - tap * CIN;
+    wsm[((tap * NPL + ci / 8) * COUT + co) * 8 + (ci & 7)] = wb[static_cast<long long>(co) * kp + k];
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tensor core reads them
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_tfull[b]), 1);
+      mbar_init(smem_u32(&bar_tempty[b]), 4);
+    }
+    abort_flag = 0;
+    epi_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      int j = 0;
+      for (int it = blockIdx.x; it < items && !*abort_v; it += gridDim.x, ++j) {
+        const int s = j % S;
+        if (j >= S && !mbar_wait(smem_u32(&bar_empty[s]), ((j / S) & 1) ^ 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        const int b = it / (a.h >> 1), y0 = 2 * (it - b * (a.h >> 1));
+        const uint32_t fb = smem_u32(&bar_full[s]);
+        mbar_expect_tx(fb, SB);
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+          for (int pc = 0; pc < NPL; ++pc)
+            tma_load_4d(sX + s * SB + (kx * NPL + pc) * PB, &mx, fb, 8 * pc, kx - 1, y0 - 1, b);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = mma_idesc(COUT);
+      int j = 0;
+      for (int it = blockIdx.x; it < items && !*abort_v; it += gridDim.x, ++j) {
+        const int s = j % S, bb = j & 1;
+        if (j >= 2 && !mbar_wait(smem_u32(&bar_tempty[bb]), ((j >> 1) & 1) ^ 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        if (!mbar_wait(smem_u32(&bar_full[s]), (j / S) & 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int tau = 0; tau < T; ++tau) {
+          const uint32_t acc = tmem + static_cast<uint32_t>((bb * T + tau) * COUT);
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+              const uint32_t aaddr = sX + s * SB + (kx * NPL + 2 * ks) * PB + ((tau + ky) * W) * 16;
+              const uint32_t baddr = sW + ((tap * NPL + 2 * ks) * COUT) * 16;
+              umma_bf16(acc, kmajor_desc(aaddr, PB, 128), kmajor_desc(baddr, COUT * 16, 128), idesc,
+                        (tap | ks) != 0 ? 1u : 0u);
+            }
+          }
+        }
+        umma_commit(smem_u32(&bar_empty[s]));
+        umma_commit(smem_u32(&bar_tfull[bb]));
+      }
+    }
+  } else {
+    // epilogue warps 0-3 (TMEM lanes 32 warp ..)
+    int j = 0;
+    const int h2 = a.h >> 1, w2 = W >> 1;
+    for (int it = blockIdx.x; it < items; it += gridDim.x, ++j) {
+      const int bb = j & 1;
+      bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[bb]), (j >> 1) & 1);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      // the epilogue warps meet at named barriers (W = 64): they stop together
+      if (!ok && lane == 0) epi_fail = 1;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      ok = !*reinterpret_cast<volatile int*>(&epi_fail);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrWait);
+        *abort_v = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t lanes = static_cast<uint32_t>(warp * 32) << 16;
+      if constexpr (T == 2) {
+        // pixel x = 32 warp + lane of rows y0 (tile 0) and y0 + 1 (tile 1)
+        const int b = it / h2, yp = it - b * h2;
+        const int x2 = (32 * warp + lane) >> 1;
+#pragma unroll 1
+        for (int c = 0; c < COUT; c += 8) {
+          float v0[8], v1[8];
+          tmem_ld8(tmem + lanes + static_cast<uint32_t>((bb * T) * COUT + c), v0);
+          tmem_ld8(tmem + lanes + static_cast<uint32_t>((bb * T + 1) * COUT + c), v1);
+          uint32_t pk[4];
+#pragma unroll
+          for (int q = 0; q < 8; q += 2) {
+            float r[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float bq = a.bias[c + q + e];
+              const float u = __bfloat162float(__float2bfloat16_rn(fmaxf(v0[q + e] + bq, 0.0f)));
+              const float l = __bfloat162float(__float2bfloat16_rn(fmaxf(v1[q + e] + bq, 0.0f)));
+              const float m = u > l ? u : l;
+              const float o = __shfl_xor_sync(0xFFFFFFFFu, m, 1);
+              r[e] = m > o ? m : o;
+            }
+            const __nv_bfloat162 pr = __floats2bfloat162_rn(r[0], r[1]);
+            pk[q >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+          }
+          if (!(lane & 1)) {
+            bf16* dst = a.p + ((static_cast<long long>(b) * h2 + yp) * w2 + x2) * COUT + c;
+            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          }
+        }
+      } else {
+        pool_epilogue<COUT>(a, it, warp, lane, tmem + lanes + static_cast<uint32_t>(bb * T * COUT));
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[bb]));
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 5) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- layer kernels
 
 // conv1 (1 input channel, K = 9) on the CUDA cores: a K of 9 would fill one 64-wide tensor
@@ -1167,6 +1372,50 @@ int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const b
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
 
+// Forward 3x3 convolution and 2x2 max pooling of a channels-last [n][h][w][cin] BF16 map
+// with k_conv_halo (inference): pooled output channels-last [(b, y2, x2)][cout] (pool_cl) or
+// [b][(c, y2, x2)]. Weights wb[cout][kp] BF16, tap-major K.
+int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int kp, int cout, const float* bias,
+              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
+  const cuuint64_t dims[4] = {static_cast<cuuint64_t>(cin), static_cast<cuuint64_t>(w), static_cast<cuuint64_t>(h),
+                              static_cast<cuuint64_t>(n)};
+  const cuuint64_t strides[3] = {static_cast<cuuint64_t>(cin) * 2, static_cast<cuuint64_t>(w) * cin * 2,
+                                 static_cast<cuuint64_t>(h) * w * cin * 2};
+  const cuuint32_t box[4] = {8, static_cast<cuuint32_t>(w), 4, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUtensorMap mx;
+  if (fn(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), dims, strides, box, estr,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return SND_ERR_UNSUPPORTED;
+  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl};
+  const int items = n * (h / 2);
+  auto go = [&](auto kern, int npl, int cw) {
+    const int smem = 128 + 2 * (3 * npl * 4 * w * 16) + 9 * npl * cw * 16;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(items, nsm * std::max(per_sm, 1)));
+    kern<<<grid, 192, smem, s>>>(mx, a, wb, kp, err);
+    return cudaGetLastError();
+  };
+  cudaError_t e;
+  if (cin == 16 && cout == 32 && w == 128 && h % 2 == 0) {
+    e = go(k_conv_halo<16, 32, 128>, 2, 32);
+  } else if (cin == 32 && cout == 64 && w == 64 && h % 2 == 0) {
+    e = go(k_conv_halo<32, 64, 64>, 4, 64);
+  } else {
+    return SND_ERR_UNSUPPORTED;
+  }
+  if (launches) *launches += 1;
+  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
 // Input gradient of a 3x3 convolution on the tensor cores (k_conv_tc in DX mode):
 // dX^T[cin][m] = sum over taps and output channels of dY[m + tap offset][co] * W'[ci][tap*cdy + co],
 // with dY row-major [m][64] (cdy channels used) and W' = k_cast_w_flip of the layer's kernel.
@@ -1330,11 +1579,11 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
       k_conv1<<<grid_for(m), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]));
       f.launches++;
     } else if (!f.training) {
-      // inference: implicit GEMM with the pooling in its epilogue (channels-last for conv3,
+      // inference: halo convolution with the pooling in its epilogue (channels-last for conv3,
       // fc1's feature rows after conv3)
-      int rc = conv_tc(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, c.kc, c.kp, at<bf16>(f, f.o.wb[l]), c.cout,
-                       P + kOffB[l], nullptr, err, s, &f.launches, l == 1 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3),
-                       l == 1 ? 1 : 0);
+      int rc = conv_halo(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, at<bf16>(f, f.o.wb[l]), c.kp, c.cout,
+                         P + kOffB[l], l == 1 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3), l == 1 ? 1 : 0, err, s,
+                         &f.launches);
       if (rc) return rc;
       continue;
     } else {
