@@ -147,6 +147,25 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive TMEM columns of this warp's 32 lanes (one wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// BF16 of relu(v + bias), two values packed
+__device__ __forceinline__ uint32_t act_pack2(float v0, float b0, float v1, float b1) {
+  const __nv_bfloat162 pr = __floats2bfloat162_rn(fmaxf(v0 + b0, 0.0f), fmaxf(v1 + b1, 0.0f));
+  return *reinterpret_cast<const uint32_t*>(&pr);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -328,8 +347,8 @@ struct ConvArgs {
   int cout;
   int ldx;          // elements per input pixel
   float* yTf;       // DX: output [cout][n*h*w] in FP32, no bias or ReLU
-  // POOL (forward): the 2x2 max pooling of the activations instead of yT. pool_cl: pooled map
-  // channels-last p[(b, y2, x2)][cout]; else p[b][(c, y2, x2)] (fc1's input rows)
+  // k_conv_halo: the 2x2 max pooling of the activations. pool_cl: pooled map channels-last
+  // p[(b, y2, x2)][cout]; else p[b][(c, y2, x2)] (fc1's input rows)
   bf16* p;
   int pool_cl;
 };
@@ -337,64 +356,59 @@ struct ConvArgs {
 // DX: the input gradient of a convolution written as the forward convolution of the output
 // gradient (row-major dY, ldx = 64) with the flipped, channel-transposed kernel (k_cast_w_flip)
 // Epilogue of a pooled forward tile (warps 0-3; warp w holds tile rows 32w.., i.e. image row
-// y0 + (w >> 1), columns x0 + 32 (w & 1) + lane). Per 8 channels: bias, ReLU and the BF16
-// rounding of each activation, the horizontal pair by a lane shuffle, and the lower row's
-// pair handed to the upper row's warp through shared memory. The comparison order is
-// k_pool's: v0 (upper left), v1 (upper right), v2, v3, each replacing the best if greater.
+// y0 + (w >> 1), columns x0 + 32 (w & 1) + lane). Per 16 channels: the larger FP32 sum of each
+// horizontal pair by a lane shuffle, the lower row's handed to the upper row's warp through
+// shared memory, then bias, ReLU and the BF16 rounding of the largest of the four.
 template <int BN>
-__device__ __forceinline__ void pool_epilogue(const ConvArgs& a, int t, int warp, int lane, uint32_t tbase) {
-  __shared__ float xv[2][16][8];
+__device__ __forceinline__ void pool_epilogue(const ConvArgs& a, int t, int warp, int lane, uint32_t tbase, int grp) {
+  // the maximum of the four rounded activations is the rounded activation of the largest of
+  // the four FP32 sums (bias, ReLU and BF16 rounding are monotone non-decreasing), so the
+  // pooling runs on the accumulators and one value per pooled cell is rounded. warp: 0-3
+  // within the epilogue warpgroup grp, which meets at named barrier 1 + grp.
+  __shared__ float xv[2][2][16][16];
   const int tpr = a.w >> 6, rp = t / tpr;
   const int b = rp / (a.h >> 1), y2 = rp - b * (a.h >> 1);
   const int x2 = (t - rp * tpr) * 32 + (warp & 1) * 16 + (lane >> 1);
   const int h2 = a.h >> 1, w2 = a.w >> 1;
   const bool live = b < a.n;
+  float (*xg)[16][16] = xv[grp];
 #pragma unroll 1
-  for (int c = 0; c < BN; c += 8) {
-    float v[8];
-    tmem_ld8(tbase + static_cast<uint32_t>(c), v);
-    float best[8];
+  for (int c = 0; c < BN; c += 16) {
+    float v[16];
+    tmem_ld16(tbase + static_cast<uint32_t>(c), v);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float y = __bfloat162float(__float2bfloat16_rn(fmaxf(v[q] + a.bias[c + q], 0.0f)));
-      const float o = __shfl_xor_sync(0xFFFFFFFFu, y, 1);  // the odd column's value on even lanes
-      // upper row: v0 = y, v1 = o; lower row: v2 = y, v3 = o (v3 wins only if greater)
-      best[q] = o > y ? o : y;
-    }
+    for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], __shfl_xor_sync(0xFFFFFFFFu, v[q], 1));
     if (warp >= 2 && !(lane & 1)) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) xv[warp - 2][lane >> 1][q] = best[q];
+      for (int q = 0; q < 16; ++q) xg[warp - 2][lane >> 1][q] = v[q];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
     if (warp < 2 && !(lane & 1) && live) {
-      uint32_t pk[4];
+      uint32_t pk[8];
 #pragma unroll
-      for (int q = 0; q < 8; q += 2) {
-        const float l0 = xv[warp][lane >> 1][q], l1 = xv[warp][lane >> 1][q + 1];
-        const float r0 = l0 > best[q] ? l0 : best[q], r1 = l1 > best[q + 1] ? l1 : best[q + 1];
-        const __nv_bfloat162 pr = __floats2bfloat162_rn(r0, r1);
-        pk[q >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+      for (int q = 0; q < 16; q += 2) {
+        const float m0 = fmaxf(v[q], xg[warp][lane >> 1][q]), m1 = fmaxf(v[q + 1], xg[warp][lane >> 1][q + 1]);
+        pk[q >> 1] = act_pack2(m0, a.bias[c + q], m1, a.bias[c + q + 1]);
       }
       if (a.pool_cl) {
-        bf16* dst = a.p + ((static_cast<long long>(b) * h2 + y2) * w2 + x2) * a.cout + c;
-        *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        uint4* dst = reinterpret_cast<uint4*>(a.p + ((static_cast<long long>(b) * h2 + y2) * w2 + x2) * a.cout + c);
+        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
       } else {
         bf16* dst = a.p + static_cast<long long>(b) * a.cout * h2 * w2 + static_cast<long long>(y2) * w2 + x2;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 16; ++q) {
           const uint32_t word = pk[q >> 1];
-          dst[static_cast<long long>(c + q) * h2 * w2] = __ushort_as_bfloat16(static_cast<unsigned short>((q & 1) ? (word >> 16) : (word & 0xFFFFu)));
+          dst[static_cast<long long>(c + q) * h2 * w2] =
+              __ushort_as_bfloat16(static_cast<unsigned short>((q & 1) ? (word >> 16) : (word & 0xFFFFu)));
         }
       }
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // xv is rewritten by the next 8 channels
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");  // xv is rewritten by the next 16 channels
   }
 }
 
-// POOL: M tiles of two image rows x 64 columns (w % 64 == 0, h even), rows 0-63 the upper
-// row, and the epilogue writes the 2x2 max pooling of the activations (ties to the first of
-// the four in row-major order, as k_pool) instead of the activations.
-template <int BN, int CIN, bool DX = false, bool POOL = false>
+template <int BN, int CIN, bool DX = false>
 __global__ void __launch_bounds__(288, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mb, ConvArgs a, uint32_t* err) {
   constexpr int KT = (9 * CIN + kBK - 1) / kBK;  // K steps
@@ -403,7 +417,7 @@ __global__ void __launch_bounds__(288, 1)
   extern __shared__ uint8_t gsm_raw[];
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag, epi_fail;
+  __shared__ int abort_flag;
   uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sA = smem_u32(gsm), sB = sA + kStages * kABytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -422,7 +436,6 @@ __global__ void __launch_bounds__(288, 1)
       mbar_init(smem_u32(&bar_tempty[b]), 4);
     }
     abort_flag = 0;
-    epi_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 8) {
@@ -454,23 +467,11 @@ __global__ void __launch_bounds__(288, 1)
       mbar_arrive(fb);
     };
     for (int t = blockIdx.x; t < mt && !quit && !*abort_v; t += gridDim.x) {
-      int b, yy, xx;
-      bool mv;
-      if constexpr (POOL) {
-        const int tpr = a.w >> 6, rp = t / tpr;
-        b = rp / (a.h >> 1);
-        yy = 2 * (rp - b * (a.h >> 1)) + (pr >> 6);
-        xx = (t - rp * tpr) * 64 + (pr & 63);
-        mv = b < a.n;
-        if (!mv) b = yy = xx = 0;
-      } else {
-        const long long m = static_cast<long long>(t) * kBM + pr;
-        mv = m < M;
-        b = mv ? static_cast<int>(m / hw) : 0;
-        const int yx = mv ? static_cast<int>(m - b * hw) : 0;
-        yy = yx / a.w;
-        xx = yx - yy * a.w;
-      }
+      const long long m = static_cast<long long>(t) * kBM + pr;
+      const bool mv = m < M;
+      const int b = mv ? static_cast<int>(m / hw) : 0;
+      const int yx = mv ? static_cast<int>(m - b * hw) : 0;
+      const int yy = yx / a.w, xx = yx - yy * a.w;
       const bf16* xb = a.x + static_cast<long long>(b) * hw * a.ldx;  // channels-last input
       const bf16* tp[9];
       bool tv[9];
@@ -557,13 +558,6 @@ __global__ void __launch_bounds__(288, 1)
       const int b = j & 1;
       bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[b]), (j >> 1) & 1);
       ok = __all_sync(0xFFFFFFFFu, ok);
-      if constexpr (POOL) {
-        // the pooled epilogue's warps meet at named barriers: they stop together (the flag is
-        // only set before this barrier and read after it)
-        if (!ok && lane == 0) epi_fail = 1;
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        ok = !*reinterpret_cast<volatile int*>(&epi_fail);
-      }
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrWait);
         *abort_v = 1;
@@ -572,9 +566,7 @@ __global__ void __launch_bounds__(288, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long row = static_cast<long long>(t) * kBM + warp * 32 + lane;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(b * BN);
-      if constexpr (POOL) {
-        pool_epilogue<BN>(a, t, warp, lane, tbase);
-      } else {
+      {
 #pragma unroll 1
       for (int c = 0; c < BN; c += 8) {
         float v[8];
@@ -626,31 +618,39 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 }
 
 // Forward 3x3 convolution with its 2x2 max pooling (inference), without any gather. A work
-// item is one pair of image rows (y0, y0 + 1) of one snippet. The TMA engine loads the four
-// input rows y0 - 1 .. y0 + 2 of the channels-last map three times, shifted by -1, 0 and +1
-// pixel, as 8-channel planes (16 bytes a pixel; pixels outside the map read as zero), so the
-// A operand of tap (ky, kx) is a plain K-major view into the kx copy starting ky rows down:
-// 128 consecutive pixels, 8 channels per core matrix, the next 8 channels one plane further.
-// W = 128: an M tile is one image row (two tiles per item, their accumulators side by side);
-// W = 64: one tile of both rows. The weights sit in shared memory as [tap][plane][cout][8].
-// 192 threads: warps 0-3 pool and store from TMEM, warp 4 issues the TMA loads, warp 5 owns
-// TMEM and issues the MMAs; items are double buffered in TMEM and shared memory.
+// item is one pair of image rows (y0, y0 + 1) of one snippet; the TMA engine loads the four
+// input rows y0 - 1 .. y0 + 2 of the channels-last map as 8-channel planes (16 bytes a pixel;
+// pixels outside the map read as zero), and the A operand of tap (ky, kx) is a plain K-major
+// view into them, 128 consecutive pixels, 8 channels per core matrix, the next 8 channels
+// one plane further:
+//  * W = 128: an M tile is one image row (two tiles per item, accumulated side by side in
+//    TMEM). The rows are loaded once, 130 pixels wide (-1 .. 128), and tap (ky, kx) starts
+//    ky rows down and kx pixels in.
+//  * W = 64: one tile holds both rows, so a view runs from one row into the next; the rows
+//    are loaded three times, shifted by -1, 0 and +1 pixel (64 wide each), and tap (ky, kx)
+//    reads the kx copy ky rows down.
+// The weights sit in shared memory as [tap][plane][cout][8]. 320 threads: two epilogue
+// warpgroups (warps 0-3 and 4-7), each draining one of the two TMEM accumulator buffers (items
+// alternate between them), warp 8 issues the TMA loads and warp 9 owns TMEM and issues the
+// MMAs; S shared-memory stages.
 template <int CIN, int COUT, int W>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     k_conv_halo(const __grid_constant__ CUtensorMap mx, ConvArgs a, const bf16* __restrict__ wb, int kp,
                 uint32_t* err) {
   constexpr int NPL = CIN / 8;                 // 8-channel planes
-  constexpr int PB = 4 * W * 16;               // bytes of one plane copy (4 rows)
-  constexpr int SB = 3 * NPL * PB;             // bytes of one stage (three shifted copies)
   constexpr int T = W == 128 ? 2 : 1;          // M tiles per item
+  constexpr int NCOPY = T == 2 ? 1 : 3;        // loaded copies of the rows
+  constexpr int PITCH = T == 2 ? W + 2 : W;    // pixels per loaded row
+  constexpr int PB = 4 * PITCH * 16;           // bytes of one plane copy (4 rows)
+  constexpr int SB = NCOPY * NPL * PB;         // bytes of one stage
   constexpr int KS = NPL / 2;                  // K steps of 16 per tap
-  constexpr int S = 2;                         // stages
+  constexpr int S = T == 2 ? 3 : 2;            // stages
   constexpr uint32_t kCols = 2 * T * COUT < 32 ? 32 : 2 * T * COUT;
   static_assert(W == 128 || W == 64, "tile geometry");
   extern __shared__ uint8_t hsm_raw[];
   __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S], bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag, epi_fail;
+  __shared__ int abort_flag, epi_fail[2];
   uint8_t* hsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(hsm_raw) + 127) & ~uintptr_t(127));
   const uint32_t sX = smem_u32(hsm), sW = sX + S * SB;
   bf16* wsm = reinterpret_cast<bf16*>(hsm + S * SB);
@@ -671,13 +671,13 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_tfull[b]), 1);
-      mbar_init(smem_u32(&bar_tempty[b]), 4);
+      mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per warp of the buffer's warpgroup
     }
     abort_flag = 0;
-    epi_fail = 0;
+    epi_fail[0] = epi_fail[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(kCols)
                  : "memory");
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = tmem_slot;
   volatile int* abort_v = &abort_flag;
 
-  if (warp == 4) {
+  if (warp == 8) {
     if (lane == 0) {
       int j = 0;
       for (int it = blockIdx.x; it < items && !*abort_v; it += gridDim.x, ++j) {
@@ -703,13 +703,13 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t fb = smem_u32(&bar_full[s]);
         mbar_expect_tx(fb, SB);
 #pragma unroll
-        for (int kx = 0; kx < 3; ++kx)
+        for (int cp = 0; cp < NCOPY; ++cp)
 #pragma unroll
           for (int pc = 0; pc < NPL; ++pc)
-            tma_load_4d(sX + s * SB + (kx * NPL + pc) * PB, &mx, fb, 8 * pc, kx - 1, y0 - 1, b);
+            tma_load_4d(sX + s * SB + (cp * NPL + pc) * PB, &mx, fb, 8 * pc, NCOPY == 1 ? -1 : cp - 1, y0 - 1, b);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     if (lane == 0) {
       constexpr uint32_t idesc = mma_idesc(COUT);
       int j = 0;
@@ -734,7 +734,8 @@ __global__ void __launch_bounds__(192, 1)
             const int ky = tap / 3, kx = tap % 3;
 #pragma unroll
             for (int ks = 0; ks < KS; ++ks) {
-              const uint32_t aaddr = sX + s * SB + (kx * NPL + 2 * ks) * PB + ((tau + ky) * W) * 16;
+              const uint32_t aaddr = NCOPY == 1 ? sX + s * SB + (2 * ks) * PB + ((tau + ky) * PITCH + kx) * 16
+                                                : sX + s * SB + (kx * NPL + 2 * ks) * PB + (ky * PITCH) * 16;
               const uint32_t baddr = sW + ((tap * NPL + 2 * ks) * COUT) * 16;
               umma_bf16(acc, kmajor_desc(aaddr, PB, 128), kmajor_desc(baddr, COUT * 16, 128), idesc,
                         (tap | ks) != 0 ? 1u : 0u);
@@ -746,56 +747,55 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // epilogue warps 0-3 (TMEM lanes 32 warp ..)
-    int j = 0;
+    // epilogue warpgroup grp (warps 4 grp ..): the items j with j & 1 == grp, from TMEM buffer
+    // grp; warp wq of the group reads TMEM lanes 32 wq ..
+    const int grp = warp >> 2, wq = warp & 3;
+    int j = grp;
     const int h2 = a.h >> 1, w2 = W >> 1;
-    for (int it = blockIdx.x; it < items; it += gridDim.x, ++j) {
-      const int bb = j & 1;
+    for (int it = blockIdx.x + grp * gridDim.x; it < items; it += 2 * gridDim.x, j += 2) {
+      const int bb = grp;
       bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[bb]), (j >> 1) & 1);
       ok = __all_sync(0xFFFFFFFFu, ok);
-      // the epilogue warps meet at named barriers (W = 64): they stop together
-      if (!ok && lane == 0) epi_fail = 1;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      ok = !*reinterpret_cast<volatile int*>(&epi_fail);
+      // the group's warps meet at named barriers: they stop together (the flag is set only
+      // before this barrier and read after it)
+      if (!ok && lane == 0) epi_fail[grp] = 1;
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
+      ok = !*reinterpret_cast<volatile int*>(&epi_fail[grp]);
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrWait);
         *abort_v = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t lanes = static_cast<uint32_t>(warp * 32) << 16;
+      const uint32_t lanes = static_cast<uint32_t>(wq * 32) << 16;
       if constexpr (T == 2) {
-        // pixel x = 32 warp + lane of rows y0 (tile 0) and y0 + 1 (tile 1)
+        // pixel x = 32 wq + lane of rows y0 (tile 0) and y0 + 1 (tile 1). Bias, ReLU and the
+        // BF16 rounding are monotone non-decreasing, so the maximum of the four rounded
+        // activations is the rounded activation of the largest of the four sums: the pooling
+        // runs on the FP32 accumulators and one value per pooled cell is rounded.
         const int b = it / h2, yp = it - b * h2;
-        const int x2 = (32 * warp + lane) >> 1;
+        const int x2 = (32 * wq + lane) >> 1;
 #pragma unroll 1
-        for (int c = 0; c < COUT; c += 8) {
-          float v0[8], v1[8];
-          tmem_ld8(tmem + lanes + static_cast<uint32_t>((bb * T) * COUT + c), v0);
-          tmem_ld8(tmem + lanes + static_cast<uint32_t>((bb * T + 1) * COUT + c), v1);
-          uint32_t pk[4];
+        for (int c = 0; c < COUT; c += 16) {
+          float v0[16], v1[16];
+          tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T) * COUT + c), v0);
+          tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T + 1) * COUT + c), v1);
 #pragma unroll
-          for (int q = 0; q < 8; q += 2) {
-            float r[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const float bq = a.bias[c + q + e];
-              const float u = __bfloat162float(__float2bfloat16_rn(fmaxf(v0[q + e] + bq, 0.0f)));
-              const float l = __bfloat162float(__float2bfloat16_rn(fmaxf(v1[q + e] + bq, 0.0f)));
-              const float m = u > l ? u : l;
-              const float o = __shfl_xor_sync(0xFFFFFFFFu, m, 1);
-              r[e] = m > o ? m : o;
-            }
-            const __nv_bfloat162 pr = __floats2bfloat162_rn(r[0], r[1]);
-            pk[q >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+          for (int q = 0; q < 16; ++q) {
+            const float m = fmaxf(v0[q], v1[q]);
+            v0[q] = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
           }
           if (!(lane & 1)) {
-            bf16* dst = a.p + ((static_cast<long long>(b) * h2 + yp) * w2 + x2) * COUT + c;
-            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            uint32_t pk[8];
+#pragma unroll
+            for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], a.bias[c + q], v0[q + 1], a.bias[c + q + 1]);
+            uint4* dst = reinterpret_cast<uint4*>(a.p + ((static_cast<long long>(b) * h2 + yp) * w2 + x2) * COUT + c);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
           }
         }
       } else {
-        pool_epilogue<COUT>(a, it, warp, lane, tmem + lanes + static_cast<uint32_t>(bb * T * COUT));
+        pool_epilogue<COUT>(a, it, wq, lane, tmem + lanes + static_cast<uint32_t>(bb * T * COUT), grp);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -805,7 +805,7 @@ __global__ void __launch_bounds__(192, 1)
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
   }
 }
@@ -847,10 +847,11 @@ __global__ void __launch_bounds__(256) k_conv1(const float* __restrict__ x, int 
 }
 
 // conv1 and its 2x2 max pooling fused, for a sifter without training state (no gradient
-// will need the unpooled map or the argmax): a thread computes the four conv1 outputs of one
+// will need the unpooled map or the argmax): a thread computes the four conv1 sums of one
 // pooled pixel for all 16 channels from the 4x4 input patch, with k_conv1's roundings and
-// summation order (BF16 inputs and weights, FP32 sums in tap order, bias, ReLU, BF16), takes
-// their maximum as k_pool does, and writes the pooled pixel channels-last (32 bytes).
+// summation order (BF16 inputs and weights, FP32 sums in tap order), and applies bias, ReLU
+// and the BF16 rounding to their maximum (the same value as pooling the four activations),
+// writing the pooled pixel channels-last (32 bytes).
 __global__ void __launch_bounds__(256, 3) k_conv1_pool(const float* __restrict__ x, int n, const float* __restrict__ w,
                                                     const float* __restrict__ bias, bf16* __restrict__ p) {
   __shared__ float ws[16 * 9], bs[16];
@@ -874,6 +875,8 @@ __global__ void __launch_bounds__(256, 3) k_conv1_pool(const float* __restrict__
                         ? __bfloat162float(__float2bfloat16_rn(x[b * hw + sy * kW + sx]))
                         : 0.0f;
       }
+    // the maximum of the four rounded activations is the rounded activation of the largest of
+    // the four sums (bias, ReLU and BF16 rounding are monotone non-decreasing)
     uint32_t packed[8];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -884,10 +887,9 @@ __global__ void __launch_bounds__(256, 3) k_conv1_pool(const float* __restrict__
         float a = 0.0f;
 #pragma unroll
         for (int k = 0; k < 9; ++k) a = fmaf(ws[c * 9 + k], v[oy + k / 3][ox + k % 3], a);
-        const float y = __bfloat162float(__float2bfloat16_rn(fmaxf(a + bs[c], 0.0f)));
-        best = (o == 0 || y > best) ? y : best;
+        best = o == 0 ? a : fmaxf(best, a);
       }
-      const uint32_t bits = __bfloat16_as_ushort(__float2bfloat16_rn(best));
+      const uint32_t bits = __bfloat16_as_ushort(__float2bfloat16_rn(fmaxf(best + bs[c], 0.0f)));
       packed[c >> 1] = (c & 1) ? (packed[c >> 1] | (bits << 16)) : bits;
     }
     uint4* dst = reinterpret_cast<uint4*>(p + q * 16);
@@ -900,23 +902,26 @@ __global__ void __launch_bounds__(256, 3) k_conv1_pool(const float* __restrict__
 // channels-last map x[n][h][w][cin], cin = kc / 9 (the snippets themselves for cin = 1)
 template <typename T>
 __global__ void k_im2colT(const T* __restrict__ x, int n, int h, int w, int kc, bf16* __restrict__ colT) {
+  // a thread takes one output pixel m and writes its kc patch values (coalesced along m for
+  // every k); m, its image and its row come from 32-bit index arithmetic once per pixel
   const int cin = kc / 9;
-  const long long hw = static_cast<long long>(h) * w;
+  const int hw = h * w;
   const long long mtot = static_cast<long long>(n) * hw;
-  const long long total = mtot * kc;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int k = static_cast<int>(i / mtot);
-    const long long m = i - k * mtot;
+  for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < mtot;
+       m += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int b = static_cast<int>(m / hw);
-    const int yx = static_cast<int>(m - b * hw);
+    const int yx = static_cast<int>(m - static_cast<long long>(b) * hw);
     const int yy = yx / w, xx = yx - yy * w;
-    const int ci = k / 9, r = k - ci * 9, ky = r / 3, kx = r - ky * 3;
-    const int sy = yy + ky - 1, sx = xx + kx - 1;
-    float val = 0.0f;
-    if (sy >= 0 && sy < h && sx >= 0 && sx < w)
-      val = static_cast<float>(x[(b * hw + sy * w + sx) * cin + ci]);
-    colT[i] = __float2bfloat16_rn(val);
+    const T* xb = x + static_cast<long long>(b) * hw * cin;
+    for (int ci = 0; ci < cin; ++ci) {
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        const int sy = yy + r / 3 - 1, sx = xx + r % 3 - 1;
+        float val = 0.0f;
+        if (sy >= 0 && sy < h && sx >= 0 && sx < w) val = static_cast<float>(xb[(sy * w + sx) * cin + ci]);
+        colT[static_cast<long long>(ci * 9 + r) * mtot + m] = __float2bfloat16_rn(val);
+      }
+    }
   }
 }
 
@@ -1338,17 +1343,13 @@ int gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int 
 
 // Forward 3x3 convolution of a [cin][n][h][w] BF16 map on the tensor cores (k_conv_tc):
 // Y^T[cout][m] = relu(conv + bias), weights wb[cout][kp] BF16.
-// With pool set, the 2x2 max pooling of Y is written instead (pool_cl: channels-last
-// [(b, y2, x2)][cout], else [b][(c, y2, x2)]).
 int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const bf16* wb, int cout,
-            const float* bias, bf16* yT, uint32_t* err, cudaStream_t s, int64_t* launches, bf16* pool = nullptr,
-            int pool_cl = 0) {
+            const float* bias, bf16* yT, uint32_t* err, cudaStream_t s, int64_t* launches) {
   const int BN = cout <= 32 ? 32 : 64;
   if (cout > 64) return SND_ERR_UNSUPPORTED;
-  if (pool && (w % 64 != 0 || h % 2 != 0 || cout % 8 != 0)) return SND_ERR_UNSUPPORTED;
   CUtensorMap mb;
   if (!make_map(&mb, wb, kp, cout, kp, BN)) return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout, cin, nullptr, pool, pool_cl};
+  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout, cin, nullptr, nullptr, 0};
   const long long M = 1LL * n * h * w;
   const long long mt = (M + kBM - 1) / kBM;
   const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
@@ -1361,9 +1362,9 @@ int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const b
     return r;
   };
   if (cin == 16 && BN == 32) {
-    e = pool ? go(k_conv_tc<32, 16, false, true>) : go(k_conv_tc<32, 16>);
+    e = go(k_conv_tc<32, 16>);
   } else if (cin == 32 && BN == 64) {
-    e = pool ? go(k_conv_tc<64, 32, false, true>) : go(k_conv_tc<64, 32>);
+    e = go(k_conv_tc<64, 32>);
   } else {
     return SND_ERR_UNSUPPORTED;
   }
@@ -1383,7 +1384,8 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
                               static_cast<cuuint64_t>(n)};
   const cuuint64_t strides[3] = {static_cast<cuuint64_t>(cin) * 2, static_cast<cuuint64_t>(w) * cin * 2,
                                  static_cast<cuuint64_t>(h) * w * cin * 2};
-  const cuuint32_t box[4] = {8, static_cast<cuuint32_t>(w), 4, 1};
+  // rows 128 wide are loaded once with a pixel of zero padding each side; 64-wide rows as they are
+  const cuuint32_t box[4] = {8, static_cast<cuuint32_t>(w == 128 ? w + 2 : w), 4, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUtensorMap mx;
   if (fn(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), dims, strides, box, estr,
@@ -1393,15 +1395,17 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
   ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl};
   const int items = n * (h / 2);
   auto go = [&](auto kern, int npl, int cw) {
-    const int smem = 128 + 2 * (3 * npl * 4 * w * 16) + 9 * npl * cw * 16;
+    // stages x copies x planes x 4 rows x pitch x 16 bytes, then the weights
+    const int stage = w == 128 ? npl * 4 * (w + 2) * 16 : 3 * npl * 4 * w * 16;
+    const int smem = 128 + (w == 128 ? 3 : 2) * stage + 9 * npl * cw * 16;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, nsm = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 320, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(items, nsm * std::max(per_sm, 1)));
-    kern<<<grid, 192, smem, s>>>(mx, a, wb, kp, err);
+    kern<<<grid, 320, smem, s>>>(mx, a, wb, kp, err);
     return cudaGetLastError();
   };
   cudaError_t e;
@@ -1658,13 +1662,13 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     // weight and bias gradients
     bf16* colT = at<bf16>(f, f.o.colT[l]);
     if (l == 0) {
-      k_im2colT<float><<<grid_for(m * c.kc), 256, 0, s>>>(x, n, c.h, c.w, c.kc, colT);
+      k_im2colT<float><<<grid_for(m), 256, 0, s>>>(x, n, c.h, c.w, c.kc, colT);
     } else if (c.cin == 16) {
       k_im2colT_nhwc<16><<<grid_for(m * 9), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
     } else if (c.cin == 32) {
       k_im2colT_nhwc<32><<<grid_for(m * 9), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
     } else {
-      k_im2colT<bf16><<<grid_for(m * c.kc), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, colT);
+      k_im2colT<bf16><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, colT);
     }
     f.launches++;
     const int ktiles = static_cast<int>((m + kBK - 1) / kBK);
