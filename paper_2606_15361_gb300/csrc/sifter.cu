@@ -8,12 +8,14 @@
 // W1[16][1][3][3], b1, W2[32][16][3][3], b2, W3[64][32][3][3], b3, Wf1[128][16384], bf1,
 // Wf2[128], bf2. Adam keeps FP32 moments; the GEMMs read BF16 copies of the weights.
 //
-// conv2 and conv3 forward run as implicit GEMMs (k_conv_tc: patches gathered on chip);
+// Inference runs conv2 and conv3 with their pooling as k_conv_halo (TMA-loaded input rows,
+// each tap a descriptor view into them); in training they run as implicit GEMMs (k_conv_tc:
+// patches copied on chip) so the unpooled activations and the argmax can be kept;
 // fc1 and every backward GEMM are C = A B^T with both operands K-major BF16 (k_gemm): TMA
 // (128-byte swizzle) fills a 4-stage shared-memory ring, one thread issues tcgen05.mma
 // (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator, and four warps read it
 // back with tcgen05.ld for the epilogue (bias, ReLU, BF16 or FP32, row-major or transposed
-// store, or FP32 atomic add for split-K). conv1 (K = 9) runs on the CUDA cores (k_conv1).
+// store, or FP32 atomic add for split-K). conv1 (one input channel) runs as k_conv1_tc.
 // Activations are channel-major ([c][b][h][w]), except the pooled maps that feed conv2 and
 // conv3, which are channels-last ([b][h][w][c]) so a patch chunk is one 16-byte load; patch
 // rows are [m][k] with m = (b, h, w) and k = (cin, ky, kx) (tap-major in k_conv_tc),
@@ -107,6 +109,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_rows(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                                 int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
 
@@ -355,59 +365,6 @@ struct ConvArgs {
 
 // DX: the input gradient of a convolution written as the forward convolution of the output
 // gradient (row-major dY, ldx = 64) with the flipped, channel-transposed kernel (k_cast_w_flip)
-// Epilogue of a pooled forward tile (warps 0-3; warp w holds tile rows 32w.., i.e. image row
-// y0 + (w >> 1), columns x0 + 32 (w & 1) + lane). Per 16 channels: the larger FP32 sum of each
-// horizontal pair by a lane shuffle, the lower row's handed to the upper row's warp through
-// shared memory, then bias, ReLU and the BF16 rounding of the largest of the four.
-template <int BN>
-__device__ __forceinline__ void pool_epilogue(const ConvArgs& a, int t, int warp, int lane, uint32_t tbase, int grp) {
-  // the maximum of the four rounded activations is the rounded activation of the largest of
-  // the four FP32 sums (bias, ReLU and BF16 rounding are monotone non-decreasing), so the
-  // pooling runs on the accumulators and one value per pooled cell is rounded. warp: 0-3
-  // within the epilogue warpgroup grp, which meets at named barrier 1 + grp.
-  __shared__ float xv[2][2][16][16];
-  const int tpr = a.w >> 6, rp = t / tpr;
-  const int b = rp / (a.h >> 1), y2 = rp - b * (a.h >> 1);
-  const int x2 = (t - rp * tpr) * 32 + (warp & 1) * 16 + (lane >> 1);
-  const int h2 = a.h >> 1, w2 = a.w >> 1;
-  const bool live = b < a.n;
-  float (*xg)[16][16] = xv[grp];
-#pragma unroll 1
-  for (int c = 0; c < BN; c += 16) {
-    float v[16];
-    tmem_ld16(tbase + static_cast<uint32_t>(c), v);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], __shfl_xor_sync(0xFFFFFFFFu, v[q], 1));
-    if (warp >= 2 && !(lane & 1)) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) xg[warp - 2][lane >> 1][q] = v[q];
-    }
-    asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
-    if (warp < 2 && !(lane & 1) && live) {
-      uint32_t pk[8];
-#pragma unroll
-      for (int q = 0; q < 16; q += 2) {
-        const float m0 = fmaxf(v[q], xg[warp][lane >> 1][q]), m1 = fmaxf(v[q + 1], xg[warp][lane >> 1][q + 1]);
-        pk[q >> 1] = act_pack2(m0, a.bias[c + q], m1, a.bias[c + q + 1]);
-      }
-      if (a.pool_cl) {
-        uint4* dst = reinterpret_cast<uint4*>(a.p + ((static_cast<long long>(b) * h2 + y2) * w2 + x2) * a.cout + c);
-        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-      } else {
-        bf16* dst = a.p + static_cast<long long>(b) * a.cout * h2 * w2 + static_cast<long long>(y2) * w2 + x2;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const uint32_t word = pk[q >> 1];
-          dst[static_cast<long long>(c + q) * h2 * w2] =
-              __ushort_as_bfloat16(static_cast<unsigned short>((q & 1) ? (word >> 16) : (word & 0xFFFFu)));
-        }
-      }
-    }
-    asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");  // xv is rewritten by the next 16 channels
-  }
-}
-
 template <int BN, int CIN, bool DX = false>
 __global__ void __launch_bounds__(288, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mb, ConvArgs a, uint32_t* err) {
@@ -619,38 +576,33 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 
 // Forward 3x3 convolution with its 2x2 max pooling (inference), without any gather. A work
 // item is one pair of image rows (y0, y0 + 1) of one snippet; the TMA engine loads the four
-// input rows y0 - 1 .. y0 + 2 of the channels-last map as 8-channel planes (16 bytes a pixel;
-// pixels outside the map read as zero), and the A operand of tap (ky, kx) is a plain K-major
-// view into them, 128 consecutive pixels, 8 channels per core matrix, the next 8 channels
-// one plane further:
-//  * W = 128: an M tile is one image row (two tiles per item, accumulated side by side in
-//    TMEM). The rows are loaded once, 130 pixels wide (-1 .. 128), and tap (ky, kx) starts
-//    ky rows down and kx pixels in.
-//  * W = 64: one tile holds both rows, so a view runs from one row into the next; the rows
-//    are loaded three times, shifted by -1, 0 and +1 pixel (64 wide each), and tap (ky, kx)
-//    reads the kx copy ky rows down.
-// The weights sit in shared memory as [tap][plane][cout][8]. 320 threads: two epilogue
-// warpgroups (warps 0-3 and 4-7), each draining one of the two TMEM accumulator buffers (items
-// alternate between them), warp 8 issues the TMA loads and warp 9 owns TMEM and issues the
-// MMAs; S shared-memory stages.
+// input rows y0 - 1 .. y0 + 2 of the channels-last map once, W + 2 pixels wide (-1 .. W, zero
+// outside the map), as 8-channel planes (16 bytes a pixel). An M tile is one image row (two
+// tiles per item, accumulated side by side in TMEM), and the A operand of tap (ky, kx) is a
+// plain K-major view 128 pixels long starting ky rows down and kx pixels in: 8 channels per
+// core matrix, the next 8 one plane further. For W = 64 the tile's last 64 rows run into the
+// next row (and for the last tap past the stage) and are not used. The weights sit in shared
+// memory as [tap][plane][cout][8]. 320 threads: two epilogue warpgroups (warps 0-3 and 4-7),
+// each draining one of the two TMEM accumulator buffers (items alternate between them), warp 8
+// issues the TMA loads and warp 9 owns TMEM and issues the MMAs; three shared-memory stages.
 template <int CIN, int COUT, int W>
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(320, 2)
     k_conv_halo(const __grid_constant__ CUtensorMap mx, ConvArgs a, const bf16* __restrict__ wb, int kp,
                 uint32_t* err) {
   constexpr int NPL = CIN / 8;                 // 8-channel planes
-  constexpr int T = W == 128 ? 2 : 1;          // M tiles per item
-  constexpr int NCOPY = T == 2 ? 1 : 3;        // loaded copies of the rows
-  constexpr int PITCH = T == 2 ? W + 2 : W;    // pixels per loaded row
-  constexpr int PB = 4 * PITCH * 16;           // bytes of one plane copy (4 rows)
-  constexpr int SB = NCOPY * NPL * PB;         // bytes of one stage
+  constexpr int T = 2;                         // M tiles (image rows) per item
+  constexpr int PITCH = W + 2;                 // pixels per loaded row
+  constexpr int PB = 4 * PITCH * 16;           // bytes of one plane (4 rows)
+  constexpr int SB = NPL * PB;                 // bytes of one stage
   constexpr int KS = NPL / 2;                  // K steps of 16 per tap
-  constexpr int S = T == 2 ? 3 : 2;            // stages
+  constexpr int S = 3;                         // stages
   constexpr uint32_t kCols = 2 * T * COUT < 32 ? 32 : 2 * T * COUT;
   static_assert(W == 128 || W == 64, "tile geometry");
   extern __shared__ uint8_t hsm_raw[];
   __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S], bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag, epi_fail[2];
+  __shared__ int abort_flag;
+  __shared__ float bsm[COUT];
   uint8_t* hsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(hsm_raw) + 127) & ~uintptr_t(127));
   const uint32_t sX = smem_u32(hsm), sW = sX + S * SB;
   bf16* wsm = reinterpret_cast<bf16*>(hsm + S * SB);
@@ -663,6 +615,7 @@ __global__ void __launch_bounds__(320, 1)
     const int tap = k / CIN, ci = k - tap * CIN;
     wsm[((tap * NPL + ci / 8) * COUT + co) * 8 + (ci & 7)] = wb[static_cast<long long>(co) * kp + k];
   }
+  if (threadIdx.x < COUT) bsm[threadIdx.x] = a.bias[threadIdx.x];
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tensor core reads them
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -674,7 +627,6 @@ __global__ void __launch_bounds__(320, 1)
       mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per warp of the buffer's warpgroup
     }
     abort_flag = 0;
-    epi_fail[0] = epi_fail[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 9) {
@@ -703,10 +655,7 @@ __global__ void __launch_bounds__(320, 1)
         const uint32_t fb = smem_u32(&bar_full[s]);
         mbar_expect_tx(fb, SB);
 #pragma unroll
-        for (int cp = 0; cp < NCOPY; ++cp)
-#pragma unroll
-          for (int pc = 0; pc < NPL; ++pc)
-            tma_load_4d(sX + s * SB + (cp * NPL + pc) * PB, &mx, fb, 8 * pc, NCOPY == 1 ? -1 : cp - 1, y0 - 1, b);
+        for (int pc = 0; pc < NPL; ++pc) tma_load_4d(sX + s * SB + pc * PB, &mx, fb, 8 * pc, -1, y0 - 1, b);
       }
     }
   } else if (warp == 9) {
@@ -734,8 +683,7 @@ __global__ void __launch_bounds__(320, 1)
             const int ky = tap / 3, kx = tap % 3;
 #pragma unroll
             for (int ks = 0; ks < KS; ++ks) {
-              const uint32_t aaddr = NCOPY == 1 ? sX + s * SB + (2 * ks) * PB + ((tau + ky) * PITCH + kx) * 16
-                                                : sX + s * SB + (kx * NPL + 2 * ks) * PB + (ky * PITCH) * 16;
+              const uint32_t aaddr = sX + s * SB + (2 * ks) * PB + ((tau + ky) * PITCH + kx) * 16;
               const uint32_t baddr = sW + ((tap * NPL + 2 * ks) * COUT) * 16;
               umma_bf16(acc, kmajor_desc(aaddr, PB, 128), kmajor_desc(baddr, COUT * 16, 128), idesc,
                         (tap | ks) != 0 ? 1u : 0u);
@@ -756,11 +704,6 @@ __global__ void __launch_bounds__(320, 1)
       const int bb = grp;
       bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[bb]), (j >> 1) & 1);
       ok = __all_sync(0xFFFFFFFFu, ok);
-      // the group's warps meet at named barriers: they stop together (the flag is set only
-      // before this barrier and read after it)
-      if (!ok && lane == 0) epi_fail[grp] = 1;
-      asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
-      ok = !*reinterpret_cast<volatile int*>(&epi_fail[grp]);
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrWait);
         *abort_v = 1;
@@ -768,7 +711,7 @@ __global__ void __launch_bounds__(320, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t lanes = static_cast<uint32_t>(wq * 32) << 16;
-      if constexpr (T == 2) {
+      if (32 * wq < W) {
         // pixel x = 32 wq + lane of rows y0 (tile 0) and y0 + 1 (tile 1). Bias, ReLU and the
         // BF16 rounding are monotone non-decreasing, so the maximum of the four rounded
         // activations is the rounded activation of the largest of the four sums: the pooling
@@ -788,14 +731,20 @@ __global__ void __launch_bounds__(320, 1)
           if (!(lane & 1)) {
             uint32_t pk[8];
 #pragma unroll
-            for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], a.bias[c + q], v0[q + 1], a.bias[c + q + 1]);
-            uint4* dst = reinterpret_cast<uint4*>(a.p + ((static_cast<long long>(b) * h2 + yp) * w2 + x2) * COUT + c);
-            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], bsm[c + q], v0[q + 1], bsm[c + q + 1]);
+            if (a.pool_cl) {  // channels-last [(b, y2, x2)][COUT]
+              uint4* dst = reinterpret_cast<uint4*>(a.p + ((static_cast<long long>(b) * h2 + yp) * w2 + x2) * COUT + c);
+              dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            } else {  // fc1's rows [b][(c, y2, x2)]
+              bf16* dst = a.p + static_cast<long long>(b) * COUT * h2 * w2 + static_cast<long long>(yp) * w2 + x2;
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                dst[static_cast<long long>(c + q) * h2 * w2] = __ushort_as_bfloat16(
+                    static_cast<unsigned short>((q & 1) ? (pk[q >> 1] >> 16) : (pk[q >> 1] & 0xFFFFu)));
+            }
           }
         }
-      } else {
-        pool_epilogue<COUT>(a, it, wq, lane, tmem + lanes + static_cast<uint32_t>(bb * T * COUT), grp);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -810,93 +759,217 @@ __global__ void __launch_bounds__(320, 1)
   }
 }
 
+// conv1 (one input channel) on the tensor cores. A work item is one pair of image rows
+// (y0, y0 + 1) of one half (128 pixels) of one snippet row; its two M tiles are the two rows.
+// The TMA engine loads the four input rows y0 - 1 .. y0 + 2 (FP32, 136 values from x0 - 4,
+// zero outside the snippet) into a deep ring of small raw stages; four builder warps turn
+// them into U: for every pixel its three horizontal taps (x - 1, x, x + 1) as BF16 and five
+// zeros, 16 bytes. The A operand of a row tile is then a K-major view into U whose K core
+// matrices are the U rows of the vertical taps, one U row apart (a fourth, of zero weight,
+// reads the next row or a zero row): two MMAs of K = 16 per tile, weights [ky][cout][8] with
+// zeros past kx = 2 and ky = 2.
+// POOL: the 2x2 max pooling of the activations, channels-last [(b, y2, x2)][16] (inference);
+// else the activations channel-major yT[c][m] (training). 320 threads: warps 0-3 epilogue,
+// warps 4-7 build U, warp 8 owns TMEM and issues the MMAs, warp 9 issues the TMA loads.
+// Rounding: BF16 snippet values and weights, FP32 sums (the tensor core adds the nine
+// products in its own order), bias, ReLU, BF16 store.
+template <bool POOL>
+__global__ void __launch_bounds__(320, 1)
+    k_conv1_tc(const __grid_constant__ CUtensorMap mx, int n, const float* __restrict__ w, const float* __restrict__ bias,
+               bf16* __restrict__ out, uint32_t* err) {
+  constexpr int RS = 12, US = 4;               // raw and U stages
+  constexpr int RAWW = 136;                    // FP32 values per loaded row (x0 - 4 .. x0 + 131)
+  constexpr int RB = 4 * RAWW * 4;             // raw bytes per stage
+  constexpr int UB = 5 * 128 * 16;             // U bytes per stage (row 4 stays zero)
+  constexpr uint32_t kCols = 64;               // 2 buffers x 2 tiles x 16 channels
+  extern __shared__ uint8_t csm_raw[];
+  __shared__ __align__(8) uint64_t bar_raw[RS], bar_rawfree[RS], bar_u[US], bar_uempty[US], bar_tfull[2],
+      bar_tempty[2];
+  __shared__ __align__(16) bf16 wsm[4 * 16 * 8];
+  __shared__ float bsm[16];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  uint8_t* csm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(csm_raw) + 127) & ~uintptr_t(127));
+  const uint32_t sU = smem_u32(csm), sR = sU + US * UB;
+  const float* raw = reinterpret_cast<const float*>(csm + US * UB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = n * 32 * 2;
+
+  // weights [ky][c][j]: bf16(w[c][3 ky + j]) for j, ky < 3, else 0; U's zero row 4 of every stage
+  for (int i = threadIdx.x; i < 4 * 16 * 8; i += blockDim.x) {
+    const int ky = i / 128, c = (i / 8) % 16, jx = i % 8;
+    wsm[i] = __float2bfloat16_rn((ky < 3 && jx < 3) ? w[c * 9 + ky * 3 + jx] : 0.0f);
+  }
+  if (threadIdx.x < 16) bsm[threadIdx.x] = bias[threadIdx.x];
+  for (int i = threadIdx.x; i < US * 128; i += blockDim.x)
+    *reinterpret_cast<uint4*>(csm + (i / 128) * UB + (4 * 128 + i % 128) * 16) = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RS; ++s) {
+      mbar_init(smem_u32(&bar_raw[s]), 1);
+      mbar_init(smem_u32(&bar_rawfree[s]), 4);  // one arrival per builder warp
+    }
+    for (int s = 0; s < US; ++s) {
+      mbar_init(smem_u32(&bar_u[s]), 4);
+      mbar_init(smem_u32(&bar_uempty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_tfull[b]), 1);
+      mbar_init(smem_u32(&bar_tempty[b]), 4);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 9) {
+    if (lane == 0) {
+      int j = 0;
+      for (int it = blockIdx.x; it < items && !*abort_v; it += gridDim.x, ++j) {
+        const int r = j % RS;
+        if (j >= RS && !mbar_wait(smem_u32(&bar_rawfree[r]), ((j / RS) & 1) ^ 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        const int b = it >> 6, yp = (it >> 1) & 31, hx = it & 1;
+        const uint32_t rb = smem_u32(&bar_raw[r]);
+        mbar_expect_tx(rb, RB);
+        tma_load_2d_rows(sR + r * RB, &mx, rb, hx * 128 - 4, 2 * yp - 1, b);
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    const int pr = threadIdx.x - 128;  // pixel of the half row
+    int j = 0;
+    for (int it = blockIdx.x; it < items && !*abort_v; it += gridDim.x, ++j) {
+      const int r = j % RS, u = j % US;
+      bool ok = mbar_wait(smem_u32(&bar_raw[r]), (j / RS) & 1);
+      if (ok && j >= US) ok = mbar_wait(smem_u32(&bar_uempty[u]), ((j / US) & 1) ^ 1);
+      if (!ok) {
+        atomicOr(err, kErrWait);
+        *abort_v = 1;
+        break;
+      }
+      const float* rs = raw + r * (RB / 4);
+      uint8_t* us = csm + u * UB;
+#pragma unroll
+      for (int row = 0; row < 4; ++row) {
+        // raw value of pixel pr + d is rs[row * RAWW + 4 + pr + d]
+        const float* rr = rs + row * RAWW + 4 + pr;
+        const __nv_bfloat162 p01 = __floats2bfloat162_rn(rr[-1], rr[0]);
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(rr[1], 0.0f);
+        *reinterpret_cast<uint4*>(us + (row * 128 + pr) * 16) =
+            make_uint4(*reinterpret_cast<const uint32_t*>(&p01), *reinterpret_cast<const uint32_t*>(&p2), 0u, 0u);
+      }
+      // the raw stage is read (and may be refilled by the TMA engine) and U is written (for
+      // the tensor core): proxy fence, then one arrival per warp on each
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&bar_rawfree[r]));
+        mbar_arrive(smem_u32(&bar_u[u]));
+      }
+    }
+  } else if (warp == 8) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = mma_idesc(16);
+      int j = 0;
+      for (int it = blockIdx.x; it < items && !*abort_v; it += gridDim.x, ++j) {
+        const int u = j % US, bb = j & 1;
+        if (j >= 2 && !mbar_wait(smem_u32(&bar_tempty[bb]), ((j >> 1) & 1) ^ 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        if (!mbar_wait(smem_u32(&bar_u[u]), (j / US) & 1)) {
+          atomicOr(err, kErrWait);
+          *abort_v = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int tau = 0; tau < 2; ++tau) {
+          const uint32_t acc = tmem + static_cast<uint32_t>((bb * 2 + tau) * 16);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            // K core matrices: U rows tau + 2h, tau + 2h + 1 (vertical taps 2h, 2h + 1)
+            const uint32_t aaddr = sU + u * UB + ((tau + 2 * h) * 128) * 16;
+            const uint32_t baddr = smem_u32(wsm) + (2 * h) * 16 * 16;
+            umma_bf16(acc, kmajor_desc(aaddr, 128 * 16, 128), kmajor_desc(baddr, 16 * 16, 128), idesc, h ? 1u : 0u);
+          }
+        }
+        umma_commit(smem_u32(&bar_uempty[u]));
+        umma_commit(smem_u32(&bar_tfull[bb]));
+      }
+    }
+  } else {
+    // epilogue warps 0-3 (TMEM lanes 32 warp ..: pixel 32 warp + lane of the half row)
+    int j = 0;
+    for (int it = blockIdx.x; it < items; it += gridDim.x, ++j) {
+      const int bb = j & 1;
+      bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[bb]), (j >> 1) & 1);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrWait);
+        *abort_v = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t lanes = static_cast<uint32_t>(warp * 32) << 16;
+      const int b = it >> 6, yp = (it >> 1) & 31, hx = it & 1;
+      const int xg = hx * 128 + warp * 32 + lane;
+      float v0[16], v1[16];
+      tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * 2) * 16), v0);
+      tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * 2 + 1) * 16), v1);
+      if constexpr (POOL) {
+        // the maximum of the four rounded activations is the rounded activation of the
+        // largest of the four sums (bias, ReLU and BF16 rounding are monotone non-decreasing)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float m = fmaxf(v0[q], v1[q]);
+          v0[q] = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
+        }
+        if (!(lane & 1)) {
+          uint32_t pk[8];
+#pragma unroll
+          for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], bsm[q], v0[q + 1], bsm[q + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(out + ((static_cast<long long>(b) * 32 + yp) * 128 + (xg >> 1)) * 16);
+          dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      } else {
+        const long long mtot = static_cast<long long>(n) * kH * kW;
+        const long long m0 = (static_cast<long long>(b) * kH + 2 * yp) * kW + xg;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          out[q * mtot + m0] = __float2bfloat16_rn(fmaxf(v0[q] + bsm[q], 0.0f));
+          out[q * mtot + m0 + kW] = __float2bfloat16_rn(fmaxf(v1[q] + bsm[q], 0.0f));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[bb]));
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 8) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- layer kernels
-
-// conv1 (1 input channel, K = 9) on the CUDA cores: a K of 9 would fill one 64-wide tensor
-// core K step to 14%. Same arithmetic as the GEMM path: BF16-rounded snippet values and
-// weights, FP32 sums, bias, ReLU, BF16 store of Y^T[c][m].
-__global__ void __launch_bounds__(256) k_conv1(const float* __restrict__ x, int n, const float* __restrict__ w,
-                                               const float* __restrict__ bias, bf16* __restrict__ yT) {
-  __shared__ float ws[16 * 9], bs[16];
-  for (int i = threadIdx.x; i < 16 * 9; i += blockDim.x) ws[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
-  if (threadIdx.x < 16) bs[threadIdx.x] = bias[threadIdx.x];
-  __syncthreads();
-  constexpr int hw = kH * kW;
-  const long long mtot = static_cast<long long>(n) * hw;
-  for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < mtot;
-       m += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long b = m / hw;
-    const int yx = static_cast<int>(m - b * hw);
-    const int yy = yx / kW, xx = yx - yy * kW;
-    float v[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const int sy = yy + k / 3 - 1, sx = xx + k % 3 - 1;
-      v[k] = (sy >= 0 && sy < kH && sx >= 0 && sx < kW)
-                 ? __bfloat162float(__float2bfloat16_rn(x[b * hw + sy * kW + sx]))
-                 : 0.0f;
-    }
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      float a = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) a = fmaf(ws[c * 9 + k], v[k], a);
-      yT[c * mtot + m] = __float2bfloat16_rn(fmaxf(a + bs[c], 0.0f));
-    }
-  }
-}
-
-// conv1 and its 2x2 max pooling fused, for a sifter without training state (no gradient
-// will need the unpooled map or the argmax): a thread computes the four conv1 sums of one
-// pooled pixel for all 16 channels from the 4x4 input patch, with k_conv1's roundings and
-// summation order (BF16 inputs and weights, FP32 sums in tap order), and applies bias, ReLU
-// and the BF16 rounding to their maximum (the same value as pooling the four activations),
-// writing the pooled pixel channels-last (32 bytes).
-__global__ void __launch_bounds__(256, 3) k_conv1_pool(const float* __restrict__ x, int n, const float* __restrict__ w,
-                                                    const float* __restrict__ bias, bf16* __restrict__ p) {
-  __shared__ float ws[16 * 9], bs[16];
-  for (int i = threadIdx.x; i < 16 * 9; i += blockDim.x) ws[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
-  if (threadIdx.x < 16) bs[threadIdx.x] = bias[threadIdx.x];
-  __syncthreads();
-  constexpr int hw = kH * kW, h2 = kH / 2, w2 = kW / 2;
-  const long long npix = static_cast<long long>(n) * h2 * w2;
-  for (long long q = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; q < npix;
-       q += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long b = q / (h2 * w2);
-    const int r = static_cast<int>(q - b * (h2 * w2));
-    const int y2 = r / w2, x2 = r - y2 * w2;
-    float v[4][4];
-#pragma unroll
-    for (int dy = 0; dy < 4; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 4; ++dx) {
-        const int sy = 2 * y2 - 1 + dy, sx = 2 * x2 - 1 + dx;
-        v[dy][dx] = (sy >= 0 && sy < kH && sx >= 0 && sx < kW)
-                        ? __bfloat162float(__float2bfloat16_rn(x[b * hw + sy * kW + sx]))
-                        : 0.0f;
-      }
-    // the maximum of the four rounded activations is the rounded activation of the largest of
-    // the four sums (bias, ReLU and BF16 rounding are monotone non-decreasing)
-    uint32_t packed[8];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      float best = 0.0f;
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const int oy = o >> 1, ox = o & 1;
-        float a = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) a = fmaf(ws[c * 9 + k], v[oy + k / 3][ox + k % 3], a);
-        best = o == 0 ? a : fmaxf(best, a);
-      }
-      const uint32_t bits = __bfloat16_as_ushort(__float2bfloat16_rn(fmaxf(best + bs[c], 0.0f)));
-      packed[c >> 1] = (c & 1) ? (packed[c >> 1] | (bits << 16)) : bits;
-    }
-    uint4* dst = reinterpret_cast<uint4*>(p + q * 16);
-    dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-  }
-}
 
 // colT[k][m] for k < kc (the weight-gradient GEMM's B operand, K-major along m) from a
 // channels-last map x[n][h][w][cin], cin = kc / 9 (the snippets themselves for cin = 1)
@@ -1373,6 +1446,29 @@ int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const b
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
 
+// Persistent grid of a kernel with `smem` bytes of dynamic shared memory, `threads` per CTA
+// and `tmem_cols` TMEM columns: as many CTAs as fit on an SM at once by shared memory (the
+// carveout set to its maximum), threads, registers and TMEM (512 columns, so that no CTA's
+// allocation ever waits for another's), times the SMs, at most `items`.
+template <typename K>
+cudaError_t persistent_grid(K kern, int smem, int threads, int tmem_cols, int items, int* grid) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaFuncAttributes fa{};
+  int dev = 0, nsm = 0;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int regs = ((std::max(fa.numRegs, 1) + 7) / 8) * 8;
+  int per_sm = (227 * 1024) / (smem + static_cast<int>(fa.sharedSizeBytes) + 1024);
+  per_sm = std::min(per_sm, 2048 / threads);
+  per_sm = std::min(per_sm, 65536 / (regs * ((threads + 31) / 32) * 32));
+  per_sm = std::min(per_sm, 512 / tmem_cols);
+  *grid = std::max(1, std::min(items, nsm * std::max(per_sm, 1)));
+  return cudaSuccess;
+}
+
 // Forward 3x3 convolution and 2x2 max pooling of a channels-last [n][h][w][cin] BF16 map
 // with k_conv_halo (inference): pooled output channels-last [(b, y2, x2)][cout] (pool_cl) or
 // [b][(c, y2, x2)]. Weights wb[cout][kp] BF16, tap-major K.
@@ -1384,8 +1480,8 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
                               static_cast<cuuint64_t>(n)};
   const cuuint64_t strides[3] = {static_cast<cuuint64_t>(cin) * 2, static_cast<cuuint64_t>(w) * cin * 2,
                                  static_cast<cuuint64_t>(h) * w * cin * 2};
-  // rows 128 wide are loaded once with a pixel of zero padding each side; 64-wide rows as they are
-  const cuuint32_t box[4] = {8, static_cast<cuuint32_t>(w == 128 ? w + 2 : w), 4, 1};
+  // four rows with a pixel of zero padding each side
+  const cuuint32_t box[4] = {8, static_cast<cuuint32_t>(w + 2), 4, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUtensorMap mx;
   if (fn(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), dims, strides, box, estr,
@@ -1395,16 +1491,12 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
   ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl};
   const int items = n * (h / 2);
   auto go = [&](auto kern, int npl, int cw) {
-    // stages x copies x planes x 4 rows x pitch x 16 bytes, then the weights
-    const int stage = w == 128 ? npl * 4 * (w + 2) * 16 : 3 * npl * 4 * w * 16;
-    const int smem = 128 + (w == 128 ? 3 : 2) * stage + 9 * npl * cw * 16;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int dev = 0, nsm = 0, per_sm = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 320, smem);
+    // 3 stages x planes x 4 rows x (w + 2) pixels x 16 bytes, then the weights
+    const int stage = npl * 4 * (w + 2) * 16;
+    const int smem = 128 + 3 * stage + 9 * npl * cw * 16;
+    int grid = 0;
+    const cudaError_t e = persistent_grid(kern, smem, 320, 4 * cw, items, &grid);
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(items, nsm * std::max(per_sm, 1)));
     kern<<<grid, 320, smem, s>>>(mx, a, wb, kp, err);
     return cudaGetLastError();
   };
@@ -1416,6 +1508,35 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
   } else {
     return SND_ERR_UNSUPPORTED;
   }
+  if (launches) *launches += 1;
+  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
+// conv1 of FP32 snippets x[n][64][256] on the tensor cores (k_conv1_tc): pooled and
+// channels-last [(b, y2, x2)][16] (pool), or the activations yT[16][m].
+int conv1_tc(const float* x, int n, const float* w, const float* bias, bf16* out, bool pool, uint32_t* err,
+             cudaStream_t s, int64_t* launches) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(kW), static_cast<cuuint64_t>(kH), static_cast<cuuint64_t>(n)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(kW) * 4, static_cast<cuuint64_t>(kH) * kW * 4};
+  const cuuint32_t box[3] = {136, 4, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUtensorMap mx;
+  if (fn(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(x), dims, strides, box, estr,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return SND_ERR_UNSUPPORTED;
+  const int smem = 128 + 4 * (5 * 128 * 16) + 12 * (4 * 136 * 4);
+  const int items = n * 64;
+  auto go = [&](auto kern) {
+    int grid = 0;
+    const cudaError_t e = persistent_grid(kern, smem, 320, 64, items, &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 320, smem, s>>>(mx, n, w, bias, out, err);
+    return cudaGetLastError();
+  };
+  const cudaError_t e = pool ? go(k_conv1_tc<true>) : go(k_conv1_tc<false>);
   if (launches) *launches += 1;
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
@@ -1575,13 +1696,13 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
     const long long m = 1LL * n * c.h * c.w;
     if (l == 0 && !f.training) {
       // inference: conv1 and pool1 in one pass, straight to the channels-last conv2 input
-      k_conv1_pool<<<grid_for(m / 4), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.p[0]));
-      f.launches++;
+      const int rc = conv1_tc(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.p[0]), true, err, s, &f.launches);
+      if (rc) return rc;
       continue;
     }
     if (l == 0) {
-      k_conv1<<<grid_for(m), 256, 0, s>>>(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]));
-      f.launches++;
+      const int rc = conv1_tc(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]), false, err, s, &f.launches);
+      if (rc) return rc;
     } else if (!f.training) {
       // inference: halo convolution with the pooling in its epilogue (channels-last for conv3,
       // fc1's feature rows after conv3)
