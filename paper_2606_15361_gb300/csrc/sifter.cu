@@ -999,35 +999,36 @@ __global__ void k_im2colT(const T* __restrict__ x, int n, int h, int w, int kc, 
 }
 
 // colT[k][m] (k = ci*9 + tap, as k_im2colT) from a channels-last BF16 map x[n][h][w][CIN]:
-// a thread takes one (tap, m), reads the CIN channels of the tap's source pixel with 16-byte
+// a thread takes one pixel m, reads the CIN channels of each tap's source pixel with 16-byte
 // loads and writes them to CIN rows of colT, so both the reads and the writes of neighbouring
 // threads (neighbouring m) are contiguous.
 template <int CIN>
 __global__ void __launch_bounds__(256) k_im2colT_nhwc(const bf16* __restrict__ x, int n, int h, int w,
                                                       bf16* __restrict__ colT) {
-  const long long hw = static_cast<long long>(h) * w;
-  const long long mtot = static_cast<long long>(n) * hw;
-  const long long total = mtot * 9;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int tap = static_cast<int>(i / mtot);
-    const long long m = i - tap * mtot;
-    const int b = static_cast<int>(m / hw);
-    const int yx = static_cast<int>(m - b * hw);
+  // a thread takes one pixel m (decoded once, in 32 bits: map sizes stay below 2^31) and all
+  // nine taps; the writes run along m for every (ci, tap)
+  const int hw = h * w;
+  const int mtot = n * hw;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < mtot; m += gridDim.x * blockDim.x) {
+    const int b = m / hw;
+    const int yx = m - b * hw;
     const int yy = yx / w, xx = yx - yy * w;
-    const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
-    uint4 v[CIN / 8];
-    if (sy >= 0 && sy < h && sx >= 0 && sx < w) {
-      const uint4* src = reinterpret_cast<const uint4*>(x + (b * hw + sy * w + sx) * CIN);
 #pragma unroll
-      for (int q = 0; q < CIN / 8; ++q) v[q] = __ldg(src + q);
-    } else {
+    for (int tap = 0; tap < 9; ++tap) {
+      const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+      uint4 v[CIN / 8];
+      if (sy >= 0 && sy < h && sx >= 0 && sx < w) {
+        const uint4* src = reinterpret_cast<const uint4*>(x + (static_cast<long long>(b) * hw + sy * w + sx) * CIN);
 #pragma unroll
-      for (int q = 0; q < CIN / 8; ++q) v[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (int q = 0; q < CIN / 8; ++q) v[q] = __ldg(src + q);
+      } else {
+#pragma unroll
+        for (int q = 0; q < CIN / 8; ++q) v[q] = make_uint4(0u, 0u, 0u, 0u);
+      }
+      const bf16* vb = reinterpret_cast<const bf16*>(v);
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) colT[static_cast<long long>(ci * 9 + tap) * mtot + m] = vb[ci];
     }
-    const bf16* vb = reinterpret_cast<const bf16*>(v);
-#pragma unroll
-    for (int ci = 0; ci < CIN; ++ci) colT[static_cast<long long>(ci * 9 + tap) * mtot + m] = vb[ci];
   }
 }
 
@@ -1038,14 +1039,13 @@ __global__ void k_pool(const bf16* __restrict__ y, int c_n, int n, int h, int w,
                        bf16* __restrict__ pT, long long ldt, int chan_major, uint8_t* __restrict__ am) {
   const int h2 = h / 2, w2 = w / 2;
   const long long total = static_cast<long long>(c_n) * n * h2 * w2;
+  const int plane = n * h2 * w2;  // pooled pixels per channel (below 2^31)
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int x2 = static_cast<int>(i % w2);
-    long long r = i / w2;
-    const int y2 = static_cast<int>(r % h2);
-    r /= h2;
-    const int b = static_cast<int>(r % n);
-    const int c = static_cast<int>(r / n);
+    const int c = static_cast<int>(i / plane);
+    const int pix = static_cast<int>(i - static_cast<long long>(c) * plane);
+    const int x2 = pix % w2, r = pix / w2;
+    const int y2 = r % h2, b = r / h2;
     const bf16* src = y + ((static_cast<long long>(c) * n + b) * h + 2 * y2) * w + 2 * x2;
     const float v0 = __bfloat162float(src[0]), v1 = __bfloat162float(src[1]);
     const float v2 = __bfloat162float(src[w]), v3 = __bfloat162float(src[w + 1]);
@@ -1075,17 +1075,16 @@ template <int CN>
 __global__ void __launch_bounds__(256) k_pool_nhwc(const bf16* __restrict__ y, int n, int h, int w,
                                                    bf16* __restrict__ p, uint8_t* __restrict__ am) {
   __shared__ bf16 sp[64][CN + 2];
+  // the pixel of a thread is decoded once, in 32 bits (pooled pixel counts stay below 2^31)
   const int h2 = h / 2, w2 = w / 2;
-  const long long npix = static_cast<long long>(n) * h2 * w2;
-  const long long pix0 = static_cast<long long>(blockIdx.x) * 64;
-  for (int idx = threadIdx.x; idx < CN * 64; idx += 256) {
-    const int c = idx >> 6, pl = idx & 63;
-    const long long pix = pix0 + pl;
-    if (pix >= npix) continue;
-    const int x2 = static_cast<int>(pix % w2);
-    const long long r = pix / w2;
-    const int y2 = static_cast<int>(r % h2);
-    const int b = static_cast<int>(r / h2);
+  const int npix = n * h2 * w2;
+  const int pix0 = blockIdx.x * 64;
+  const int pl0 = threadIdx.x & 63, pixt = pix0 + pl0;
+  const int x2 = pixt % w2, r = pixt / w2;
+  const int y2 = r % h2, b = r / h2;
+  for (int idx = threadIdx.x; idx < CN * 64 && pixt < npix; idx += 256) {
+    const int c = idx >> 6, pl = pl0;
+    const long long pix = pixt;
     const bf16* src = y + ((static_cast<long long>(c) * n + b) * h + 2 * y2) * w + 2 * x2;
     const float v0 = __bfloat162float(src[0]), v1 = __bfloat162float(src[1]);
     const float v2 = __bfloat162float(src[w]), v3 = __bfloat162float(src[w + 1]);
@@ -1117,23 +1116,23 @@ __global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, in
                                                 int h, int w, bf16* __restrict__ dyT, bf16* __restrict__ dy,
                                                 int ldy) {
   __shared__ bf16 sdy[64 * 4][CN + 2];
+  // pooled pixel counts and map sizes stay below 2^31 (the workspace is sized for them), so
+  // the pixel of a thread is decoded once, in 32 bits (256 threads = 4 channel rows of the
+  // same 64 pixels)
   const int h2 = h / 2, w2 = w / 2;
-  const long long npix = static_cast<long long>(n) * h2 * w2;
+  const int npix = n * h2 * w2;
   const long long mtot = static_cast<long long>(n) * h * w;
-  const long long pix0 = static_cast<long long>(blockIdx.x) * 64;
-  for (int idx = threadIdx.x; idx < CN * 64; idx += 256) {
-    const int c = idx >> 6, pl = idx & 63;
-    const long long pix = pix0 + pl;
-    if (pix >= npix) continue;
-    const int x2 = static_cast<int>(pix % w2);
-    const long long r = pix / w2;
-    const int y2 = static_cast<int>(r % h2);
-    const int b = static_cast<int>(r / h2);
+  const int pl = threadIdx.x & 63;
+  const int pix = blockIdx.x * 64 + pl;
+  const int x2 = pix % w2, r = pix / w2;
+  const int y2 = r % h2, b = r / h2;
+  const long long m00 = (static_cast<long long>(b) * h + 2 * y2) * w + 2 * x2;
+  for (int idx = threadIdx.x; idx < CN * 64 && pix < npix; idx += 256) {
+    const int c = idx >> 6;
     const long long pc = static_cast<long long>(c) * npix + pix;  // channel-major pooled index
     const float g = dp_chan_major ? dp[pc] : dp[static_cast<long long>(b) * CN * h2 * w2 +
                                                  (static_cast<long long>(c) * h2 + y2) * w2 + x2];
     const int a = am[pc];
-    const long long m00 = (static_cast<long long>(b) * h + 2 * y2) * w + 2 * x2;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const long long m = m00 + (q >> 1) * w + (q & 1);
@@ -1148,14 +1147,12 @@ __global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, in
   __syncthreads();
   for (int idx = threadIdx.x; idx < 64 * 4 * CN; idx += 256) {
     const int c = idx % CN, pq = idx / CN;
-    const int pl = pq >> 2, q = pq & 3;
-    const long long pix = pix0 + pl;
-    if (pix >= npix) continue;
-    const int x2 = static_cast<int>(pix % w2);
-    const long long r = pix / w2;
-    const int y2 = static_cast<int>(r % h2);
-    const int b = static_cast<int>(r / h2);
-    const long long m = (static_cast<long long>(b) * h + 2 * y2 + (q >> 1)) * w + 2 * x2 + (q & 1);
+    const int pq_l = pq >> 2, q = pq & 3;
+    const int pix2 = blockIdx.x * 64 + pq_l;
+    if (pix2 >= npix) continue;
+    const int xx2 = pix2 % w2, rr = pix2 / w2;
+    const int yy2 = rr % h2, bb = rr / h2;
+    const long long m = (static_cast<long long>(bb) * h + 2 * yy2 + (q >> 1)) * w + 2 * xx2 + (q & 1);
     dy[m * ldy + c] = sdy[pq][c];
   }
 }
@@ -1785,9 +1782,9 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     if (l == 0) {
       k_im2colT<float><<<grid_for(m), 256, 0, s>>>(x, n, c.h, c.w, c.kc, colT);
     } else if (c.cin == 16) {
-      k_im2colT_nhwc<16><<<grid_for(m * 9), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
+      k_im2colT_nhwc<16><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
     } else if (c.cin == 32) {
-      k_im2colT_nhwc<32><<<grid_for(m * 9), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
+      k_im2colT_nhwc<32><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
     } else {
       k_im2colT<bf16><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, colT);
     }
