@@ -650,6 +650,15 @@ int union_limit(const Plan& p) {
 
 cudaError_t launch_candidates(const Plan& p, int64_t f_prev, int nb, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
+  if (!(p.flags & kFlagReferenceTree)) {
+    // one cooperative launch instead of the eleven stage launches below
+    ChunkPos c{};
+    c.f_prev = f_prev;
+    c.nb = nb;
+    const Plan* pp = &p;
+    return launch_candidates_batch(&pp, &c, 1, s);
+  }
+  // the reference tree's plans: the closing as separate passes and one launch per stage
   const DevPtrs& dp = p.dp;
   const int r = p.closing / 2;
   const int nbw = (nb + 31) / 32;
@@ -749,7 +758,7 @@ cudaError_t launch_candidates_batch(const Plan* const* plans, const ChunkPos* po
     }
     const Plan& owner = *plans[batch[i0]];
     m.gbar = owner.dp.counters + kCntGridBar;
-    m.wait_cycles = owner.loop_limit > 0 ? owner.loop_limit : kGridWaitCycles;
+    m.wait_cycles = owner.wait_limit > 0 ? owner.wait_limit : kGridWaitCycles;
     const int smem = 2 * (kCloseTR + 4 * rmax) * kCloseNQ * static_cast<int>(sizeof(uint32_t));
     int dev = 0, nsm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
