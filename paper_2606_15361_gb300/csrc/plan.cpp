@@ -562,14 +562,18 @@ void choose_direct_geometry(Plan& p) {
   } else {
     if (p.C != 4 || p.KL < 1 || p.KL > 4 || p.KI < 1 || p.KI > 2 || p.nlev < 2) return;
     const int up = p.nlev - 1;
-    // regular trees (B = 4 or 8): the levels inside a 16-leaf group as fixed logic; per-level
+    // regular trees (B = 2, 4 or 8): the levels inside a 16-leaf group as fixed logic; per-level
     // fire counts take the general state
-    const int uin = p.B == 4 ? 2 : 1;
-    const bool reg = (p.B == 4 || p.B == 8) && !(p.flags & SND_FLAG_LEVEL_RATES) && up >= uin &&
-                     up - uin <= (p.B == 4 ? 4 : 3);
+    const int uin = p.B == 2 ? 4 : (p.B == 4 ? 2 : 1);
+    const bool reg = (p.B == 2 || p.B == 4 || p.B == 8) && !(p.flags & SND_FLAG_LEVEL_RATES) && up >= uin &&
+                     up - uin <= (p.B == 8 ? 3 : 4);
     if (reg) {
-      inst = p.B == 4 ? (p.KI == 1 ? snd::kDirBinReg4K1 : snd::kDirBinReg4K2)
-                      : (p.KI == 1 ? snd::kDirBinReg8K1 : snd::kDirBinReg8K2);
+      if (p.B == 2)
+        inst = p.KI == 1 ? snd::kDirBinReg2K1 : snd::kDirBinReg2K2;
+      else if (p.B == 4)
+        inst = p.KI == 1 ? snd::kDirBinReg4K1 : snd::kDirBinReg4K2;
+      else
+        inst = p.KI == 1 ? snd::kDirBinReg8K1 : snd::kDirBinReg8K2;
     } else if (up <= 4) {
       inst = snd::kDirBinary4;
     } else if (up <= 8) {

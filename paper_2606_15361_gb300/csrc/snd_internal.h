@@ -76,6 +76,8 @@ enum {
   kDirBinReg4K2,     // binary, regular tree B = 4, K_I = 2
   kDirBinReg8K1,     // binary, regular tree B = 8, K_I = 1, <= 3 levels above level 1
   kDirBinReg8K2,     // binary, regular tree B = 8, K_I = 2
+  kDirBinReg2K1,     // binary, regular tree B = 2, K_I = 1, <= 4 levels above level 4
+  kDirBinReg2K2,     // binary, regular tree B = 2, K_I = 2
 };
 
 // Direct tree kernel geometry: CTA = 32 consecutive trial DMs (lane = DM) x warps * kw words.

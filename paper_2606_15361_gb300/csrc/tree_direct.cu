@@ -421,10 +421,10 @@ struct DState<kBinary, KW, NPL, MAXU> {
   __device__ __forceinline__ void store(int32_t* row, int j) const { store_bits(row, root[j]); }
 };
 
-// Mode A on a regular tree: B = 4 or 8 (MODE = kBinReg + 10 B + K_I), C = 4, and each level
+// Mode A on a regular tree: B = 2, 4 or 8 (MODE = kBinReg + 10 B + K_I), C = 4, and each level
 // groups B consecutive nodes of the one below (the last node of a level may have fewer). The
-// levels whose nodes lie inside one staged group of 64 channels (16 leaves: up to level 2 for
-// B = 4, level 1 for B = 8) are evaluated per group as a fixed tree of logic operations, with
+// levels whose nodes lie inside one staged group of 64 channels (16 leaves: up to level 4 for
+// B = 2, level 2 for B = 4, level 1 for B = 8) are evaluated per group as a fixed tree of logic operations, with
 // no per-leaf bookkeeping; only the levels above them keep an open node (its two-plane
 // thermometer) from group to group. The same node rules, so the same planes, as the general
 // binary state above.
@@ -435,9 +435,9 @@ __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * i
 template <int MODE, int KW, int NPL, int MAXU>
 struct DState {
   static constexpr int BB = (MODE - kBinReg) / 10, KI = (MODE - kBinReg) % 10;
-  static_assert(BB == 4 || BB == 8, "regular binary tree: B = 4 or 8");
+  static_assert(BB == 2 || BB == 4 || BB == 8, "regular binary tree: B = 2, 4 or 8");
   static_assert(KI == 1 || KI == 2, "K_I = 1 or 2");
-  static constexpr int UIN = BB == 4 ? 2 : 1;      // highest level inside a group of 16 leaves
+  static constexpr int UIN = BB == 2 ? 4 : (BB == 4 ? 2 : 1);  // highest level inside a group of 16 leaves
   static constexpr int SPAN = ipow(BB, UIN);       // leaves under one such node
   static constexpr int NTOP = 16 / SPAN;           // such nodes per group
   uint32_t t0[MAXU][KW], t1[MAXU][KW];  // thermometer of the open node of every level > UIN
@@ -775,6 +775,8 @@ cudaError_t dispatch_direct(int id, F&& f) {
     case kDirBinary4: return f.template go<kBinary, 4, 1, 4>();
     case kDirBinary8: return f.template go<kBinary, 4, 1, 8>();
     case kDirBinary12: return f.template go<kBinary, 2, 1, 12>();
+    case kDirBinReg2K1: return f.template go<kBinReg + 21, 4, 1, 4>();
+    case kDirBinReg2K2: return f.template go<kBinReg + 22, 4, 1, 4>();
     case kDirBinReg4K1: return f.template go<kBinReg + 41, 4, 1, 4>();
     case kDirBinReg4K2: return f.template go<kBinReg + 42, 4, 1, 4>();
     case kDirBinReg8K1: return f.template go<kBinReg + 81, 4, 1, 3>();
