@@ -33,10 +33,16 @@ __device__ __forceinline__ void hist_cta(const uint8_t* __restrict__ chunk, int 
   const int r0 = by * kHistRowsPerBlock;
   const int r1 = min(nsamp, r0 + kHistRowsPerBlock);
   if (c < nchan) {
-    for (int r = r0 + wy; r < r1; r += 8) {
-      const uint32_t v = chunk[static_cast<size_t>(r) * nchan + c];
-      atomicAdd(&h[v][lane], 1u);
+    // eight rows' loads in flight per lane before their counts are added
+    int r = r0 + wy;
+    for (; r + 56 < r1; r += 64) {
+      uint32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldg(chunk + static_cast<size_t>(r + 8 * k) * nchan + c);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) atomicAdd(&h[v[k]][lane], 1u);
     }
+    for (; r < r1; r += 8) atomicAdd(&h[__ldg(chunk + static_cast<size_t>(r) * nchan + c)][lane], 1u);
   }
   __syncthreads();
   for (int i = tid; i < 256 * 32; i += 256) {
