@@ -463,6 +463,7 @@ def stress_rate(g, args, dev, nbeams=16):
 def zfloat_rate(g, args, dev, dchunks, freqs, dms):
     """Labelled-payload Mode C (precision study) on the same beam: the tree with FP16 and with
     FP32 partial-sum storage, timed per chunk by the stage events (plane only)."""
+    import torch
     out = {}
     steps = max(1, min(args.steps, 3))
     for name, flag in (("fp16", g.FLAG_FP16_PARTIALS), ("fp32", 0)):
@@ -484,11 +485,21 @@ def zfloat_rate(g, args, dev, dchunks, freqs, dms):
         bpu = W.nchan / W.ndm * es + 4.0  # payload ring read once per DM tile set + FP32 plane written
         peaks, src = _peaks()
         ach = bpu * W.chunk * W.ndm / (tms / 1e3) / 1e9
+        # its real bound: one shared-memory read of es bytes per (DM, sample, channel) against
+        # SMs x 128 bytes per clock at the maximum SM clock
+        props = torch.cuda.get_device_properties(dev)
+        smem_peak = props.multi_processor_count * 128 * float(peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e9
+        smem_ach = W.nchan * es * W.chunk * W.ndm / (tms / 1e3) / 1e9
         out[name] = {"tree_ms_per_chunk": round(tms, 4), "encode_ms_per_chunk": round(ems, 4),
                      "tree_gdm_samples_per_s": round(W.chunk * W.ndm / (tms / 1e3) / 1e9, 2),
                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                   "frac": ach / peaks["hbm_gbs"], "peak_source": src,
-                                  "algorithmic_bytes_per_dm_sample": bpu, "kernel": "k_tree_z"}}
+                                  "algorithmic_bytes_per_dm_sample": bpu, "kernel": "k_tree_z"},
+                     "roofline_smem": {"bound": "smem", "achieved": smem_ach, "peak": smem_peak, "unit": "GB/s",
+                                       "frac": smem_ach / smem_peak, "kernel": "k_tree_z",
+                                       "peak_source": f"derived: {props.multi_processor_count} SMs x 128 B/clock x "
+                                                      "max SM clock",
+                                       "algorithmic_bytes_per_dm_sample": W.nchan * es}}
     return out
 
 
@@ -772,6 +783,9 @@ def run_gpu(args, rank, world, local_rank):
                        "tree_hbm_frac": round(TREE_BYTES_PER_DM_SAMPLE * units / (tms / 1e3) / 1e9 /
                                               peaks["hbm_gbs"], 4),
                        "tree_alu_frac": round(adds[n] * units / (tms / 1e3) / 1e9 / alu_peak, 4),
+                       # the matched filter reads the int32 plane once: 4 B per DM-sample
+                       "mf_hbm_frac": round(4.0 * units / (prof[n]["mf"][0] / max(prof[n]["mf"][1], 1) / 1e3) / 1e9 /
+                                            peaks["hbm_gbs"], 4),
                        "pipeline_gdm_samples_per_s": round(units / (sum(v[0] for v in prof[n].values()) /
                                                                     max(prof[n]["tree"][1], 1) / 1e3) / 1e9, 2)}
     adds_mean = sum(adds.values()) / max(len(adds), 1)
