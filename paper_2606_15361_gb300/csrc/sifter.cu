@@ -8,9 +8,9 @@
 // W1[16][1][3][3], b1, W2[32][16][3][3], b2, W3[64][32][3][3], b3, Wf1[128][16384], bf1,
 // Wf2[128], bf2. Adam keeps FP32 moments; the GEMMs read BF16 copies of the weights.
 //
-// Inference runs conv2 and conv3 with their pooling as k_conv_halo (TMA-loaded input rows,
-// each tap a descriptor view into them); in training they run as implicit GEMMs (k_conv_tc:
-// patches copied on chip) so the unpooled activations and the argmax can be kept;
+// conv2 and conv3 run with their pooling as k_conv_halo (TMA-loaded input rows, each tap a
+// descriptor view into them; in training the epilogue also keeps the argmax of every pooled
+// cell); the input gradients run as implicit GEMMs (k_conv_tc in DX mode: patches copied on chip);
 // fc1 and every backward GEMM are C = A B^T with both operands K-major BF16 (k_gemm): TMA
 // (128-byte swizzle) fills a 4-stage shared-memory ring, one thread issues tcgen05.mma
 // (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator, and four warps read it
@@ -361,6 +361,12 @@ struct ConvArgs {
   // p[(b, y2, x2)][cout]; else p[b][(c, y2, x2)] (fc1's input rows)
   bf16* p;
   int pool_cl;
+  // training: the argmax 0..3 of every pooled cell, am[c * npix + pooled pixel] (first maximum
+  // of the four BF16 activations in row-major order), and for fc1's input rows also their
+  // transpose pT[(c, y2, x2) * ldt + b]; null in inference
+  uint8_t* am;
+  bf16* pT;
+  long long ldt;
 };
 
 // DX: the input gradient of a convolution written as the forward convolution of the output
@@ -554,6 +560,35 @@ __global__ void __launch_bounds__(288, 1)
   }
 }
 
+// The 2x2 max pooling of 16 channels with its argmax, for training (the backward pass routes
+// the gradient to the argmax). Lane pairs (x even, x odd) hold one pooled cell; v0 / v1 are the
+// FP32 sums of the lane's pixel in the upper / lower row. Each activation is bias, ReLU and
+// BF16 rounding of its sum; the cell takes the first maximum in row-major order (upper left,
+// upper right, lower left, lower right), as the oracle's pooling does. Even lanes get the packed pooled
+// values in pk and write the argmax bytes am[(c0 + q) * npix + pix].
+__device__ __forceinline__ void pool_argmax16(const float* v0, const float* v1, const float* bias, int lane,
+                                              uint32_t* pk, uint8_t* am, int c0, long long npix, long long pix) {
+#pragma unroll
+  for (int q = 0; q < 16; q += 2) {
+    float best[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float u = __bfloat162float(__float2bfloat16_rn(fmaxf(v0[q + e] + bias[q + e], 0.0f)));
+      const float l = __bfloat162float(__float2bfloat16_rn(fmaxf(v1[q + e] + bias[q + e], 0.0f)));
+      const float ur = __shfl_xor_sync(0xFFFFFFFFu, u, 1), lr = __shfl_xor_sync(0xFFFFFFFFu, l, 1);
+      int a = 0;
+      float bv = u;
+      if (ur > bv) { bv = ur; a = 1; }
+      if (l > bv) { bv = l; a = 2; }
+      if (lr > bv) { bv = lr; a = 3; }
+      best[e] = bv;
+      if (!(lane & 1)) am[static_cast<long long>(c0 + q + e) * npix + pix] = static_cast<uint8_t>(a);
+    }
+    const __nv_bfloat162 pr = __floats2bfloat162_rn(best[0], best[1]);
+    pk[q >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+  }
+}
+
 // ---------------------------------------------------------------- halo convolution
 
 // shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x 16 bytes
@@ -585,7 +620,7 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 // memory as [tap][plane][cout][8]. 320 threads: two epilogue warpgroups (warps 0-3 and 4-7),
 // each draining one of the two TMEM accumulator buffers (items alternate between them), warp 8
 // issues the TMA loads and warp 9 owns TMEM and issues the MMAs; three shared-memory stages.
-template <int CIN, int COUT, int W>
+template <int CIN, int COUT, int W, bool TRAIN>
 __global__ void __launch_bounds__(320, 2)
     k_conv_halo(const __grid_constant__ CUtensorMap mx, ConvArgs a, const bf16* __restrict__ wb, int kp,
                 uint32_t* err) {
@@ -723,25 +758,39 @@ __global__ void __launch_bounds__(320, 2)
           float v0[16], v1[16];
           tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T) * COUT + c), v0);
           tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T + 1) * COUT + c), v1);
+          uint32_t pk[8];
+          if constexpr (TRAIN) {
+            // training: the four rounded activations and their argmax (first maximum)
+            pool_argmax16(v0, v1, bsm + c, lane, pk, a.am, c, static_cast<long long>(a.n) * h2 * w2,
+                          (static_cast<long long>(b) * h2 + yp) * w2 + x2);
+          } else {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const float m = fmaxf(v0[q], v1[q]);
-            v0[q] = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
+            for (int q = 0; q < 16; ++q) {
+              const float m = fmaxf(v0[q], v1[q]);
+              v0[q] = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
+            }
           }
           if (!(lane & 1)) {
-            uint32_t pk[8];
+            if constexpr (!TRAIN) {
 #pragma unroll
-            for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], bsm[c + q], v0[q + 1], bsm[c + q + 1]);
+              for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], bsm[c + q], v0[q + 1], bsm[c + q + 1]);
+            }
             if (a.pool_cl) {  // channels-last [(b, y2, x2)][COUT]
               uint4* dst = reinterpret_cast<uint4*>(a.p + ((static_cast<long long>(b) * h2 + yp) * w2 + x2) * COUT + c);
               dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
               dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            } else {  // fc1's rows [b][(c, y2, x2)]
+            } else {  // fc1's rows [b][(c, y2, x2)] (and in training their transpose)
               bf16* dst = a.p + static_cast<long long>(b) * COUT * h2 * w2 + static_cast<long long>(yp) * w2 + x2;
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                dst[static_cast<long long>(c + q) * h2 * w2] = __ushort_as_bfloat16(
+              for (int q = 0; q < 16; ++q) {
+                const bf16 v = __ushort_as_bfloat16(
                     static_cast<unsigned short>((q & 1) ? (pk[q >> 1] >> 16) : (pk[q >> 1] & 0xFFFFu)));
+                const long long f = static_cast<long long>(c + q) * h2 * w2 + static_cast<long long>(yp) * w2 + x2;
+                dst[static_cast<long long>(c + q) * h2 * w2] = v;
+                if constexpr (TRAIN) {
+                  if (a.pT) a.pT[f * a.ldt + b] = v;
+                }
+              }
             }
           }
         }
@@ -768,15 +817,15 @@ __global__ void __launch_bounds__(320, 2)
 // matrices are the U rows of the vertical taps, one U row apart (a fourth, of zero weight,
 // reads the next row or a zero row): two MMAs of K = 16 per tile, weights [ky][cout][8] with
 // zeros past kx = 2 and ky = 2.
-// POOL: the 2x2 max pooling of the activations, channels-last [(b, y2, x2)][16] (inference);
-// else the activations channel-major yT[c][m] (training). 320 threads: warps 0-3 epilogue,
+// The epilogue writes the 2x2 max pooling of the activations, channels-last [(b, y2, x2)][16];
+// TRAIN: also the argmax of every pooled cell (am). 320 threads: warps 0-3 epilogue,
 // warps 4-7 build U, warp 8 owns TMEM and issues the MMAs, warp 9 issues the TMA loads.
 // Rounding: BF16 snippet values and weights, FP32 sums (the tensor core adds the nine
 // products in its own order), bias, ReLU, BF16 store.
-template <bool POOL>
+template <bool TRAIN>
 __global__ void __launch_bounds__(320, 1)
     k_conv1_tc(const __grid_constant__ CUtensorMap mx, int n, const float* __restrict__ w, const float* __restrict__ bias,
-               bf16* __restrict__ out, uint32_t* err) {
+               bf16* __restrict__ out, uint8_t* __restrict__ am, uint32_t* err) {
   constexpr int RS = 12, US = 4;               // raw and U stages
   constexpr int RAWW = 136;                    // FP32 values per loaded row (x0 - 4 .. x0 + 131)
   constexpr int RB = 4 * RAWW * 4;             // raw bytes per stage
@@ -931,29 +980,29 @@ __global__ void __launch_bounds__(320, 1)
       float v0[16], v1[16];
       tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * 2) * 16), v0);
       tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * 2 + 1) * 16), v1);
-      if constexpr (POOL) {
-        // the maximum of the four rounded activations is the rounded activation of the
-        // largest of the four sums (bias, ReLU and BF16 rounding are monotone non-decreasing)
+      {
+        uint32_t pk[8];
+        if constexpr (TRAIN) {
+          // training: the four rounded activations and their argmax (first maximum)
+          pool_argmax16(v0, v1, bsm, lane, pk, am, 0, static_cast<long long>(n) * 32 * 128,
+                        (static_cast<long long>(b) * 32 + yp) * 128 + (xg >> 1));
+        } else {
+          // the maximum of the four rounded activations is the rounded activation of the
+          // largest of the four sums (bias, ReLU and BF16 rounding are monotone non-decreasing)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float m = fmaxf(v0[q], v1[q]);
-          v0[q] = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
+          for (int q = 0; q < 16; ++q) {
+            const float m = fmaxf(v0[q], v1[q]);
+            v0[q] = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
+          }
         }
         if (!(lane & 1)) {
-          uint32_t pk[8];
+          if constexpr (!TRAIN) {
 #pragma unroll
-          for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], bsm[q], v0[q + 1], bsm[q + 1]);
+            for (int q = 0; q < 16; q += 2) pk[q >> 1] = act_pack2(v0[q], bsm[q], v0[q + 1], bsm[q + 1]);
+          }
           uint4* dst = reinterpret_cast<uint4*>(out + ((static_cast<long long>(b) * 32 + yp) * 128 + (xg >> 1)) * 16);
           dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
           dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-        }
-      } else {
-        const long long mtot = static_cast<long long>(n) * kH * kW;
-        const long long m0 = (static_cast<long long>(b) * kH + 2 * yp) * kW + xg;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          out[q * mtot + m0] = __float2bfloat16_rn(fmaxf(v0[q] + bsm[q], 0.0f));
-          out[q * mtot + m0 + kW] = __float2bfloat16_rn(fmaxf(v1[q] + bsm[q], 0.0f));
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1032,78 +1081,6 @@ __global__ void __launch_bounds__(256) k_im2colT_nhwc(const bf16* __restrict__ x
   }
 }
 
-// 2x2 max pooling of y[c][b][h][w] (BF16, post-ReLU); ties go to the first of the four in
-// row-major order. Writes p[c][b][h/2][w/2] (chan_major) or p[b][c][h/2][w/2] and its
-// transpose pT[(c, y, x)][b] (row pitch ldt), plus the argmax 0..3.
-__global__ void k_pool(const bf16* __restrict__ y, int c_n, int n, int h, int w, bf16* __restrict__ p,
-                       bf16* __restrict__ pT, long long ldt, int chan_major, uint8_t* __restrict__ am) {
-  const int h2 = h / 2, w2 = w / 2;
-  const long long total = static_cast<long long>(c_n) * n * h2 * w2;
-  const int plane = n * h2 * w2;  // pooled pixels per channel (below 2^31)
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int c = static_cast<int>(i / plane);
-    const int pix = static_cast<int>(i - static_cast<long long>(c) * plane);
-    const int x2 = pix % w2, r = pix / w2;
-    const int y2 = r % h2, b = r / h2;
-    const bf16* src = y + ((static_cast<long long>(c) * n + b) * h + 2 * y2) * w + 2 * x2;
-    const float v0 = __bfloat162float(src[0]), v1 = __bfloat162float(src[1]);
-    const float v2 = __bfloat162float(src[w]), v3 = __bfloat162float(src[w + 1]);
-    int a = 0;
-    float best = v0;
-    if (v1 > best) { best = v1; a = 1; }
-    if (v2 > best) { best = v2; a = 2; }
-    if (v3 > best) { best = v3; a = 3; }
-    am[i] = static_cast<uint8_t>(a);
-    const bf16 bv = __float2bfloat16_rn(best);
-    if (chan_major) {
-      p[i] = bv;
-    } else {
-      const long long f = (static_cast<long long>(c) * h2 + y2) * w2 + x2;
-      p[static_cast<long long>(b) * c_n * h2 * w2 + f] = bv;
-      pT[f * ldt + b] = bv;
-    }
-  }
-}
-
-// The same 2x2 max pooling (same ties, argmax in the chan-major order of k_pool) writing the
-// pooled map channels-last, p[(b, y2, x2)][c], for the implicit-GEMM convolution that reads
-// it. A CTA owns 64 consecutive output pixels of one row: it reads each channel's two input
-// rows coalesced, and stages the results in shared memory so the channels-last writes are
-// contiguous too.
-template <int CN>
-__global__ void __launch_bounds__(256) k_pool_nhwc(const bf16* __restrict__ y, int n, int h, int w,
-                                                   bf16* __restrict__ p, uint8_t* __restrict__ am) {
-  __shared__ bf16 sp[64][CN + 2];
-  // the pixel of a thread is decoded once, in 32 bits (pooled pixel counts stay below 2^31)
-  const int h2 = h / 2, w2 = w / 2;
-  const int npix = n * h2 * w2;
-  const int pix0 = blockIdx.x * 64;
-  const int pl0 = threadIdx.x & 63, pixt = pix0 + pl0;
-  const int x2 = pixt % w2, r = pixt / w2;
-  const int y2 = r % h2, b = r / h2;
-  for (int idx = threadIdx.x; idx < CN * 64 && pixt < npix; idx += 256) {
-    const int c = idx >> 6, pl = pl0;
-    const long long pix = pixt;
-    const bf16* src = y + ((static_cast<long long>(c) * n + b) * h + 2 * y2) * w + 2 * x2;
-    const float v0 = __bfloat162float(src[0]), v1 = __bfloat162float(src[1]);
-    const float v2 = __bfloat162float(src[w]), v3 = __bfloat162float(src[w + 1]);
-    int a = 0;
-    float best = v0;
-    if (v1 > best) { best = v1; a = 1; }
-    if (v2 > best) { best = v2; a = 2; }
-    if (v3 > best) { best = v3; a = 3; }
-    am[static_cast<long long>(c) * npix + pix] = static_cast<uint8_t>(a);
-    sp[pl][c] = __float2bfloat16_rn(best);
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < CN * 64; idx += 256) {
-    const int pl = idx / CN, c = idx - (idx / CN) * CN;
-    const long long pix = pix0 + pl;
-    if (pix < npix) p[pix * CN + c] = sp[pl][c];
-  }
-}
-
 // Gradient through the pooling and the ReLU: the argmax position of each pooled cell gets
 // dP if its activation is positive. Writes dyT[c][m] (all positions) and, when dy is set,
 // dy[m][ldy] (row-major; columns c < CN). A CTA owns 64 consecutive pooled pixels for all
@@ -1112,7 +1089,7 @@ __global__ void __launch_bounds__(256) k_pool_nhwc(const bf16* __restrict__ y, i
 // of the tile channel-fastest (coalesced).
 template <int CN>
 __global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, int dp_chan_major,
-                                                const uint8_t* __restrict__ am, const bf16* __restrict__ y, int n,
+                                                const uint8_t* __restrict__ am, const bf16* __restrict__ pooled, int n,
                                                 int h, int w, bf16* __restrict__ dyT, bf16* __restrict__ dy,
                                                 int ldy) {
   __shared__ bf16 sdy[64 * 4][CN + 2];
@@ -1133,11 +1110,16 @@ __global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, in
     const float g = dp_chan_major ? dp[pc] : dp[static_cast<long long>(b) * CN * h2 * w2 +
                                                  (static_cast<long long>(c) * h2 + y2) * w2 + x2];
     const int a = am[pc];
+    // the activation at the argmax is the pooled value (channels-last when the gradient is
+    // channel-major, fc1's rows [b][(c, y2, x2)] otherwise)
+    const long long pi = dp_chan_major ? static_cast<long long>(pix) * CN + c
+                                       : static_cast<long long>(b) * CN * h2 * w2 + (static_cast<long long>(c) * h2 + y2) * w2 + x2;
+    const bool live = __bfloat162float(pooled[pi]) > 0.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const long long m = m00 + (q >> 1) * w + (q & 1);
       const long long yi = static_cast<long long>(c) * mtot + m;
-      const float v = (q == a && __bfloat162float(y[yi]) > 0.0f) ? g : 0.0f;
+      const float v = (q == a && live) ? g : 0.0f;
       const bf16 bv = __float2bfloat16_rn(v);
       dyT[yi] = bv;
       sdy[pl * 4 + q][c] = bv;
@@ -1411,38 +1393,6 @@ int gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int 
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
 
-// Forward 3x3 convolution of a [cin][n][h][w] BF16 map on the tensor cores (k_conv_tc):
-// Y^T[cout][m] = relu(conv + bias), weights wb[cout][kp] BF16.
-int conv_tc(const bf16* x, int n, int h, int w, int cin, int kc, int kp, const bf16* wb, int cout,
-            const float* bias, bf16* yT, uint32_t* err, cudaStream_t s, int64_t* launches) {
-  const int BN = cout <= 32 ? 32 : 64;
-  if (cout > 64) return SND_ERR_UNSUPPORTED;
-  CUtensorMap mb;
-  if (!make_map(&mb, wb, kp, cout, kp, BN)) return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, kc, kp / kBK, bias, yT, cout, cin, nullptr, nullptr, 0};
-  const long long M = 1LL * n * h * w;
-  const long long mt = (M + kBM - 1) / kBM;
-  const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
-  const int per_sm = std::max(1, (227 * 1024) / smem);
-  const unsigned grid = static_cast<unsigned>(std::min<long long>(mt, 152LL * per_sm));
-  cudaError_t e;
-  auto go = [&](auto kern) {
-    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (r == cudaSuccess) kern<<<grid, 288, smem, s>>>(mb, a, err);
-    return r;
-  };
-  if (cin == 16 && BN == 32) {
-    e = go(k_conv_tc<32, 16>);
-  } else if (cin == 32 && BN == 64) {
-    e = go(k_conv_tc<64, 32>);
-  } else {
-    return SND_ERR_UNSUPPORTED;
-  }
-  if (launches) *launches += 1;
-  if (e == cudaSuccess) e = cudaGetLastError();
-  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
-}
-
 // Persistent grid of a kernel with `smem` bytes of dynamic shared memory, `threads` per CTA
 // and `tmem_cols` TMEM columns: as many CTAs as fit on an SM at once by shared memory (the
 // carveout set to its maximum), threads, registers and TMEM (512 columns, so that no CTA's
@@ -1470,7 +1420,8 @@ cudaError_t persistent_grid(K kern, int smem, int threads, int tmem_cols, int it
 // with k_conv_halo (inference): pooled output channels-last [(b, y2, x2)][cout] (pool_cl) or
 // [b][(c, y2, x2)]. Weights wb[cout][kp] BF16, tap-major K.
 int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int kp, int cout, const float* bias,
-              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches) {
+              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches, uint8_t* am = nullptr,
+              bf16* pT = nullptr, long long ldt = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
   const cuuint64_t dims[4] = {static_cast<cuuint64_t>(cin), static_cast<cuuint64_t>(w), static_cast<cuuint64_t>(h),
@@ -1485,7 +1436,7 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl};
+  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl, am, pT, ldt};
   const int items = n * (h / 2);
   auto go = [&](auto kern, int npl, int cw) {
     // 3 stages x planes x 4 rows x (w + 2) pixels x 16 bytes, then the weights
@@ -1499,9 +1450,9 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
   };
   cudaError_t e;
   if (cin == 16 && cout == 32 && w == 128 && h % 2 == 0) {
-    e = go(k_conv_halo<16, 32, 128>, 2, 32);
+    e = am ? go(k_conv_halo<16, 32, 128, true>, 2, 32) : go(k_conv_halo<16, 32, 128, false>, 2, 32);
   } else if (cin == 32 && cout == 64 && w == 64 && h % 2 == 0) {
-    e = go(k_conv_halo<32, 64, 64>, 4, 64);
+    e = am ? go(k_conv_halo<32, 64, 64, true>, 4, 64) : go(k_conv_halo<32, 64, 64, false>, 4, 64);
   } else {
     return SND_ERR_UNSUPPORTED;
   }
@@ -1509,9 +1460,9 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
 
-// conv1 of FP32 snippets x[n][64][256] on the tensor cores (k_conv1_tc): pooled and
-// channels-last [(b, y2, x2)][16] (pool), or the activations yT[16][m].
-int conv1_tc(const float* x, int n, const float* w, const float* bias, bf16* out, bool pool, uint32_t* err,
+// conv1 of FP32 snippets x[n][64][256] on the tensor cores (k_conv1_tc) with its pooling,
+// channels-last [(b, y2, x2)][16]; with am set (training) also the argmax of every pooled cell.
+int conv1_tc(const float* x, int n, const float* w, const float* bias, bf16* out, uint8_t* am, uint32_t* err,
              cudaStream_t s, int64_t* launches) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
@@ -1530,10 +1481,10 @@ int conv1_tc(const float* x, int n, const float* w, const float* bias, bf16* out
     int grid = 0;
     const cudaError_t e = persistent_grid(kern, smem, 320, 64, items, &grid);
     if (e != cudaSuccess) return e;
-    kern<<<grid, 320, smem, s>>>(mx, n, w, bias, out, err);
+    kern<<<grid, 320, smem, s>>>(mx, n, w, bias, out, am, err);
     return cudaGetLastError();
   };
-  const cudaError_t e = pool ? go(k_conv1_tc<true>) : go(k_conv1_tc<false>);
+  const cudaError_t e = am ? go(k_conv1_tc<true>) : go(k_conv1_tc<false>);
   if (launches) *launches += 1;
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
@@ -1585,7 +1536,7 @@ struct Sifter {
   int64_t launches = 0;
   cudaStream_t last = nullptr;
   struct {
-    size_t params, grads, m1, m2, err, loss, wb[3], wT[3], wf1b, wf1T, yT[3], p[3], am[3], p3, p3T, hf,
+    size_t params, grads, m1, m2, err, loss, wb[3], wT[3], wf1b, wf1T, p[3], am[3], p3, p3T, hf,
         logits, dh, dhT, dp3, dy[3], dyT[3], colT[3], dp[3];
   } o{};
 };
@@ -1615,7 +1566,6 @@ void layout(Sifter& f) {
     const long long m = B * c.h * c.w;
     f.o.wb[l] = take(2ull * c.cout * c.kp);
     f.o.wT[l] = take(2ull * c.cin * ((9 * c.cout + kBK - 1) / kBK * kBK));
-    f.o.yT[l] = take(2ull * c.cout * m);
     f.o.p[l] = take(2ull * c.cout * m / 4);
     f.o.am[l] = take(1ull * c.cout * m / 4);
     if (f.training) {
@@ -1688,44 +1638,23 @@ cudaError_t prep_weights(Sifter& f, cudaStream_t s) {
 int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
   uint32_t* err = at<uint32_t>(f, f.o.err);
   const float* P = at<float>(f, f.o.params);
-  for (int l = 0; l < 3; ++l) {
+  // every convolution runs with its 2x2 max pooling in the epilogue; a sifter with training
+  // state also keeps the argmax of every pooled cell (and fc1's input rows transposed), which
+  // is all the backward pass needs of the forward activations
+  uint8_t* am[3] = {nullptr, nullptr, nullptr};
+  if (f.training)
+    for (int l = 0; l < 3; ++l) am[l] = at<uint8_t>(f, f.o.am[l]);
+  {
+    const int rc = conv1_tc(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.p[0]), am[0], err, s, &f.launches);
+    if (rc) return rc;
+  }
+  for (int l = 1; l < 3; ++l) {
     const ConvL& c = kConv[l];
-    const long long m = 1LL * n * c.h * c.w;
-    if (l == 0 && !f.training) {
-      // inference: conv1 and pool1 in one pass, straight to the channels-last conv2 input
-      const int rc = conv1_tc(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.p[0]), true, err, s, &f.launches);
-      if (rc) return rc;
-      continue;
-    }
-    if (l == 0) {
-      const int rc = conv1_tc(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.yT[0]), false, err, s, &f.launches);
-      if (rc) return rc;
-    } else if (!f.training) {
-      // inference: halo convolution with the pooling in its epilogue (channels-last for conv3,
-      // fc1's feature rows after conv3)
-      int rc = conv_halo(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, at<bf16>(f, f.o.wb[l]), c.kp, c.cout,
-                         P + kOffB[l], l == 1 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3), l == 1 ? 1 : 0, err, s,
-                         &f.launches);
-      if (rc) return rc;
-      continue;
-    } else {
-      // implicit GEMM: the patches are gathered on chip, no im2col buffer
-      int rc = conv_tc(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, c.kc, c.kp, at<bf16>(f, f.o.wb[l]), c.cout,
-                       P + kOffB[l], at<bf16>(f, f.o.yT[l]), err, s, &f.launches);
-      if (rc) return rc;
-    }
-    const long long pooled = m / 4 * c.cout;
-    if (l == 0) {  // 16 channels, channels-last for conv2
-      k_pool_nhwc<16><<<static_cast<unsigned>((m / 4 + 63) / 64), 256, 0, s>>>(
-          at<bf16>(f, f.o.yT[l]), n, c.h, c.w, at<bf16>(f, f.o.p[l]), at<uint8_t>(f, f.o.am[l]));
-    } else if (l == 1) {  // 32 channels, channels-last for conv3
-      k_pool_nhwc<32><<<static_cast<unsigned>((m / 4 + 63) / 64), 256, 0, s>>>(
-          at<bf16>(f, f.o.yT[l]), n, c.h, c.w, at<bf16>(f, f.o.p[l]), at<uint8_t>(f, f.o.am[l]));
-    } else {
-      k_pool<<<grid_for(pooled), 256, 0, s>>>(at<bf16>(f, f.o.yT[l]), c.cout, n, c.h, c.w, at<bf16>(f, f.o.p3),
-                                               at<bf16>(f, f.o.p3T), f.bm, 0, at<uint8_t>(f, f.o.am[l]));
-    }
-    f.launches++;
+    // channels-last for conv3, fc1's feature rows after conv3
+    const int rc = conv_halo(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, at<bf16>(f, f.o.wb[l]), c.kp, c.cout,
+                             P + kOffB[l], l == 1 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3), l == 1 ? 1 : 0, err, s,
+                             &f.launches, am[l], (l == 2 && f.training) ? at<bf16>(f, f.o.p3T) : nullptr, f.bm);
+    if (rc) return rc;
   }
   // fc1 pre-activation (bias and ReLU are applied where it is read, in k_head), K split
   // over CTAs: only ceil(n / 128) output tiles exist
@@ -1767,7 +1696,7 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     {
       const unsigned ub = static_cast<unsigned>((m / 4 + 63) / 64);
       const uint8_t* am = at<uint8_t>(f, f.o.am[l]);
-      const bf16* yl = at<bf16>(f, f.o.yT[l]);
+      const bf16* yl = l == 2 ? at<bf16>(f, f.o.p3) : at<bf16>(f, f.o.p[l]);  // the pooled map
       if (c.cout == 16) {
         k_unpool<16><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, 64);
       } else if (c.cout == 32) {
