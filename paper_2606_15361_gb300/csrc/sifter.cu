@@ -362,11 +362,8 @@ struct ConvArgs {
   bf16* p;
   int pool_cl;
   // training: the argmax 0..3 of every pooled cell, am[c * npix + pooled pixel] (first maximum
-  // of the four BF16 activations in row-major order), and for fc1's input rows also their
-  // transpose pT[(c, y2, x2) * ldt + b]; null in inference
+  // of the four BF16 activations in row-major order); null in inference
   uint8_t* am;
-  bf16* pT;
-  long long ldt;
 };
 
 // DX: the input gradient of a convolution written as the forward convolution of the output
@@ -779,17 +776,14 @@ __global__ void __launch_bounds__(320, 2)
               uint4* dst = reinterpret_cast<uint4*>(a.p + ((static_cast<long long>(b) * h2 + yp) * w2 + x2) * COUT + c);
               dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
               dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            } else {  // fc1's rows [b][(c, y2, x2)] (and in training their transpose)
+            } else {  // fc1's rows [b][(c, y2, x2)]
               bf16* dst = a.p + static_cast<long long>(b) * COUT * h2 * w2 + static_cast<long long>(yp) * w2 + x2;
 #pragma unroll
               for (int q = 0; q < 16; ++q) {
                 const bf16 v = __ushort_as_bfloat16(
                     static_cast<unsigned short>((q & 1) ? (pk[q >> 1] >> 16) : (pk[q >> 1] & 0xFFFFu)));
-                const long long f = static_cast<long long>(c + q) * h2 * w2 + static_cast<long long>(yp) * w2 + x2;
                 dst[static_cast<long long>(c + q) * h2 * w2] = v;
-                if constexpr (TRAIN) {
-                  if (a.pT) a.pT[f * a.ldt + b] = v;
-                }
+
               }
             }
           }
@@ -1081,6 +1075,23 @@ __global__ void __launch_bounds__(256) k_im2colT_nhwc(const bf16* __restrict__ x
   }
 }
 
+// out[c * ldo + r] = in[r * cols + c] for r < rows (BF16): 32 x 32 tiles through shared memory,
+// both sides coalesced. fc1's input rows transposed for its weight gradient.
+__global__ void __launch_bounds__(256) k_transpose(const bf16* __restrict__ in, int rows, int cols,
+                                                   bf16* __restrict__ out, long long ldo) {
+  __shared__ bf16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = in[static_cast<long long>(r) * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[static_cast<long long>(c) * ldo + r] = tile[threadIdx.x][i];
+  }
+}
+
 // Gradient through the pooling and the ReLU: the argmax position of each pooled cell gets
 // dP if its activation is positive. Writes dyT[c][m] (all positions) and, when dy is set,
 // dy[m][ldy] (row-major; columns c < CN). A CTA owns 64 consecutive pooled pixels for all
@@ -1357,17 +1368,21 @@ bool make_map(CUtensorMap* m, const void* base, long long kext, long long rows, 
 template <int BN>
 cudaError_t launch_gemm_bn(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int ktiles, int splits,
                            const Epi& epi, uint32_t* err, cudaStream_t s) {
-  const int per = (ktiles + splits - 1) / splits;
-  const int nz = (ktiles + per - 1) / per;
   const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  // persistent CTAs: as many as fit on the GPU at once (shared memory bounds it), spread
-  // over the K splits; each walks its share of the output tiles
+  // CTAs: every output tile gets its own, and K is split (at most `splits` ways, at least 8 K
+  // steps a split) so that tiles x splits fill the GPU once (shared memory bounds the CTAs per
+  // SM); with more tiles than that, each CTA walks several tiles
   const long long tiles = 1LL * ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
   const int per_sm = std::max(1, (227 * 1024) / smem);
-  const long long want = std::max<long long>(1, (152LL * per_sm) / nz);
-  dim3 grid(static_cast<unsigned>(std::min(tiles, want)), 1, nz);
+  const long long slots = 152LL * per_sm;
+  long long want_splits = std::max<long long>(1, slots / std::max<long long>(1, tiles));
+  want_splits = std::min<long long>(want_splits, std::max(1, ktiles / 8));
+  const int nsplit = static_cast<int>(std::max<long long>(1, std::min<long long>(splits, want_splits)));
+  const int per = (ktiles + nsplit - 1) / nsplit;
+  const int nz = (ktiles + per - 1) / per;
+  dim3 grid(static_cast<unsigned>(std::min(tiles, std::max<long long>(1, slots / nz))), 1, nz);
   k_gemm<BN><<<grid, 192, smem, s>>>(ma, mb, M, N, ktiles, per, epi, err);
   return cudaGetLastError();
 }
@@ -1420,8 +1435,7 @@ cudaError_t persistent_grid(K kern, int smem, int threads, int tmem_cols, int it
 // with k_conv_halo (inference): pooled output channels-last [(b, y2, x2)][cout] (pool_cl) or
 // [b][(c, y2, x2)]. Weights wb[cout][kp] BF16, tap-major K.
 int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int kp, int cout, const float* bias,
-              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches, uint8_t* am = nullptr,
-              bf16* pT = nullptr, long long ldt = 0) {
+              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches, uint8_t* am = nullptr) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
   const cuuint64_t dims[4] = {static_cast<cuuint64_t>(cin), static_cast<cuuint64_t>(w), static_cast<cuuint64_t>(h),
@@ -1436,7 +1450,7 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl, am, pT, ldt};
+  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl, am};
   const int items = n * (h / 2);
   auto go = [&](auto kern, int npl, int cw) {
     // 3 stages x planes x 4 rows x (w + 2) pixels x 16 bytes, then the weights
@@ -1653,8 +1667,13 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
     // channels-last for conv3, fc1's feature rows after conv3
     const int rc = conv_halo(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.cin, at<bf16>(f, f.o.wb[l]), c.kp, c.cout,
                              P + kOffB[l], l == 1 ? at<bf16>(f, f.o.p[l]) : at<bf16>(f, f.o.p3), l == 1 ? 1 : 0, err, s,
-                             &f.launches, am[l], (l == 2 && f.training) ? at<bf16>(f, f.o.p3T) : nullptr, f.bm);
+                             &f.launches, am[l]);
     if (rc) return rc;
+  }
+  if (f.training) {  // fc1's input rows transposed, for its weight gradient
+    k_transpose<<<dim3((kFeat + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, s>>>(at<bf16>(f, f.o.p3), n, kFeat,
+                                                                             at<bf16>(f, f.o.p3T), f.bm);
+    f.launches++;
   }
   // fc1 pre-activation (bias and ReLU are applied where it is read, in k_head), K split
   // over CTAs: only ceil(n / 128) output tiles exist
