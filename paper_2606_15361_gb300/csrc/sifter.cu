@@ -10,19 +10,20 @@
 //
 // conv2 and conv3 run with their pooling as k_conv_halo (TMA-loaded input rows, each tap a
 // descriptor view into them; in training the epilogue also keeps the argmax of every pooled
-// cell); the input gradients run as implicit GEMMs (k_conv_tc in DX mode: patches copied on chip);
+// cell); their input gradients run on the same kernel (the convolution of dY with the flipped
+// kernel, FP32 output);
 // fc1 and every backward GEMM are C = A B^T with both operands K-major BF16 (k_gemm): TMA
 // (128-byte swizzle) fills a 4-stage shared-memory ring, one thread issues tcgen05.mma
 // (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator, and four warps read it
 // back with tcgen05.ld for the epilogue (bias, ReLU, BF16 or FP32, row-major or transposed
 // store, or FP32 atomic add for split-K). conv1 (one input channel) runs as k_conv1_tc.
-// Activations are channel-major ([c][b][h][w]), except the pooled maps that feed conv2 and
-// conv3, which are channels-last ([b][h][w][c]) so a patch chunk is one 16-byte load; patch
-// rows are [m][k] with m = (b, h, w) and k = (cin, ky, kx) (tap-major in k_conv_tc),
-// zero-padded to a multiple of 64.
-//   forward conv:   Y^T[cout][m] = relu(patch[m][:] . W[cout][:] + b)  (k_conv_tc, implicit)
-//   weight grad:    dW[cout][k] += dY^T[cout][m] . colT[k][m]            (split-K, atomic)
-//   input grad:     dX^T[cin][m] = dY (x) flipped W                        (k_conv_tc, DX mode)
+// The pooled maps that feed conv2 and conv3 and the output gradients dY that feed the input
+// gradients are channels-last ([b][h][w][c]); gradients routed through the pooling are also
+// kept channel-major (dY^T[c][m], m = (b, h, w)) for the weight gradients, whose patch rows
+// colT[k][m] have k tap-major ((ky*3 + kx)*cin + ci), zero-padded to a multiple of 64.
+//   forward conv:   pool(relu(x (x) W + b))                               (k_conv_halo)
+//   weight grad:    dW[cout][k] += dY^T[cout][m] . colT[k][m]            (k_gemm, split-K, atomic)
+//   input grad:     dX^T[cin][m] = dY (x) flipped W                        (k_conv_halo, DX)
 // Every mbarrier wait is bounded (about 2 s of clock); a wait that gives up sets a device
 // error word that the host turns into SND_ERR_TIMEOUT, and the kernel still frees its TMEM.
 
@@ -336,27 +337,14 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// Implicit-GEMM 3x3 convolution on the tensor cores (conv2 and conv3 forward):
-//   Y^T[cout][m] = relu(sum_k A[m][k] W[cout][k] + b),  A[m][k] = x[ci][b][y+ky-1][x+kx-1]
-// with m = (b, y, x), the patch gathered in tap-major order (k = (ky*3 + kx)*cin + ci, the
-// weights permuted to match), i.e. the im2col GEMM without the im2col buffer. The input map
-// is channels-last, so eight consecutive K values are one 16-byte load. 288 threads: warps 0-3 drain the TMEM accumulator, warps 4-7 build the A
-// tile of every K step in shared memory (one tile row per thread, in the 128-byte swizzled
-// K-major layout the MMA reads, made visible to the tensor core with a proxy fence) while one
-// of them also TMA-loads the weight tile, and warp 8 owns TMEM and issues the MMAs. CTAs are
-// persistent over the M tiles; the accumulator is double buffered as in k_gemm.
-__device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
 struct ConvArgs {
   const bf16* x;    // input activations, channels-last [n][h][w][ldx] (channels 0..cin-1 used)
   int n, h, w, cin, kc, ktiles;
   const float* bias;
-  bf16* yT;         // output [cout][n*h*w] (forward: bias, ReLU, BF16)
+  bf16* yT;         // unused
   int cout;
   int ldx;          // elements per input pixel
-  float* yTf;       // DX: output [cout][n*h*w] in FP32, no bias or ReLU
+  float* yTf;       // DX: the convolution itself, [cout][n*h*w] FP32 (no bias, ReLU or pooling)
   // k_conv_halo: the 2x2 max pooling of the activations. pool_cl: pooled map channels-last
   // p[(b, y2, x2)][cout]; else p[b][(c, y2, x2)] (fc1's input rows)
   bf16* p;
@@ -365,197 +353,6 @@ struct ConvArgs {
   // of the four BF16 activations in row-major order); null in inference
   uint8_t* am;
 };
-
-// DX: the input gradient of a convolution written as the forward convolution of the output
-// gradient (row-major dY, ldx = 64) with the flipped, channel-transposed kernel (k_cast_w_flip)
-template <int BN, int CIN, bool DX = false>
-__global__ void __launch_bounds__(288, 1)
-    k_conv_tc(const __grid_constant__ CUtensorMap mb, ConvArgs a, uint32_t* err) {
-  constexpr int KT = (9 * CIN + kBK - 1) / kBK;  // K steps
-  constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
-  constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
-  extern __shared__ uint8_t gsm_raw[];
-  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2];
-  __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
-  uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t sA = smem_u32(gsm), sB = sA + kStages * kABytes;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long hw = static_cast<long long>(a.h) * a.w;
-  const long long M = static_cast<long long>(a.n) * hw;
-  const int mt = static_cast<int>((M + kBM - 1) / kBM);
-  const int nkt = KT;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(smem_u32(&bar_full[s]), 128);  // one arrival per producer thread
-      mbar_init(smem_u32(&bar_empty[s]), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&bar_tfull[b]), 1);
-      mbar_init(smem_u32(&bar_tempty[b]), 4);
-    }
-    abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 8) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(kCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_slot;
-  volatile int* abort_v = &abort_flag;
-
-  if (warp >= 4 && warp < 8) {
-    // producers: thread pr builds row pr of every A tile. K runs tap-major, k = tap*CIN + ci
-    // (tap = ky*3 + kx; the weights are permuted to match), so with CIN and the K-step count
-    // known at compile time every 8-value chunk is one 16-byte asynchronous copy (cp.async,
-    // zero-filled outside the map) at a fixed per-tap offset. Each K step's copies are one
-    // commit group; a step is handed to the MMA (proxy fence, then the stage's arrival) two
-    // steps later, so three steps of copies are in flight per thread.
-    constexpr int kLag = 2;
-    const int pr = threadIdx.x - 128;
-    int it = 0;
-    bool quit = false;
-    auto complete = [&](int step) {
-      const uint32_t fb = smem_u32(&bar_full[step % kStages]);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(fb);
-    };
-    for (int t = blockIdx.x; t < mt && !quit && !*abort_v; t += gridDim.x) {
-      const long long m = static_cast<long long>(t) * kBM + pr;
-      const bool mv = m < M;
-      const int b = mv ? static_cast<int>(m / hw) : 0;
-      const int yx = mv ? static_cast<int>(m - b * hw) : 0;
-      const int yy = yx / a.w, xx = yx - yy * a.w;
-      const bf16* xb = a.x + static_cast<long long>(b) * hw * a.ldx;  // channels-last input
-      const bf16* tp[9];
-      bool tv[9];
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
-        tv[tap] = mv && sy >= 0 && sy < a.h && sx >= 0 && sx < a.w;
-        tp[tap] = xb + (tv[tap] ? (sy * a.w + sx) * a.ldx : 0);
-      }
-#pragma unroll
-      for (int i = 0; i < KT; ++i, ++it) {
-        const int s = it % kStages;
-        if (it >= kStages && !mbar_wait(smem_u32(&bar_empty[s]), ((it / kStages) & 1) ^ 1)) {
-          atomicOr(err, kErrWait);
-          *abort_v = 1;
-          quit = true;
-          break;
-        }
-        if (pr == 0) {
-          const uint32_t fb = smem_u32(&bar_full[s]);
-          mbar_expect_tx_only(fb, kBBytes);
-          tma_load_2d(sB + s * kBBytes, &mb, fb, i * kBK, 0);
-        }
-        const uint32_t rowaddr = sA + s * kABytes + pr * 128;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          // the 8 K values of chunk q are 8 consecutive channels of one tap (CIN % 8 == 0)
-          constexpr int kc = 9 * CIN;
-          const int k0 = i * kBK + q * 8;  // compile-time after unrolling
-          const int tap = k0 / CIN, ci0 = k0 % CIN;
-          const bool valid = k0 < kc && tv[tap < 9 ? tap : 0];
-          const bf16* src = tp[tap < 9 ? tap : 0] + (k0 < kc ? ci0 : 0);
-          const uint32_t dst = rowaddr + ((q ^ (pr & 7)) << 4);
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-                       : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        if (it >= kLag) {
-          asm volatile("cp.async.wait_group %0;" ::"n"(kLag) : "memory");
-          complete(it - kLag);
-        }
-      }
-    }
-    // the last steps' copies (also before leaving after an abort: no copy may still be in flight)
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (!quit)
-      for (int st = it - kLag < 0 ? 0 : it - kLag; st < it; ++st) complete(st);
-  } else if (warp == 8) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = mma_idesc(BN);
-      int it = 0, j = 0;
-      for (int t = blockIdx.x; t < mt && !*abort_v; t += gridDim.x, ++j) {
-        const int b = j & 1;
-        if (j >= 2 && !mbar_wait(smem_u32(&bar_tempty[b]), ((j >> 1) & 1) ^ 1)) {
-          atomicOr(err, kErrWait);
-          *abort_v = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc = tmem + static_cast<uint32_t>(b * BN);
-        for (int i = 0; i < nkt; ++i, ++it) {
-          const int s = it % kStages;
-          if (!mbar_wait(smem_u32(&bar_full[s]), (it / kStages) & 1)) {
-            atomicOr(err, kErrWait);
-            *abort_v = 1;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t da = sw128_desc(sA + s * kABytes + kk * 32);
-            const uint64_t db = sw128_desc(sB + s * kBBytes + kk * 32);
-            umma_bf16(acc, da, db, idesc, (i | kk) != 0 ? 1u : 0u);
-          }
-          umma_commit(smem_u32(&bar_empty[s]));
-        }
-        umma_commit(smem_u32(&bar_tfull[b]));
-      }
-    }
-  } else {
-    // epilogue warps 0-3: bias, ReLU, BF16, channel-major store Y^T[cout][m]
-    int j = 0;
-    for (int t = blockIdx.x; t < mt; t += gridDim.x, ++j) {
-      const int b = j & 1;
-      bool ok = !*abort_v && mbar_wait(smem_u32(&bar_tfull[b]), (j >> 1) & 1);
-      ok = __all_sync(0xFFFFFFFFu, ok);
-      if (!ok) {
-        if (lane == 0) atomicOr(err, kErrWait);
-        *abort_v = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const long long row = static_cast<long long>(t) * kBM + warp * 32 + lane;
-      const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(b * BN);
-      {
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 8) {
-        float v[8];
-        tmem_ld8(tbase + static_cast<uint32_t>(c), v);
-        if (row >= M) continue;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int n = c + q;
-          if (n >= a.cout) continue;
-          if constexpr (DX) {
-            a.yTf[static_cast<long long>(n) * M + row] = v[q];
-          } else {
-            a.yT[static_cast<long long>(n) * M + row] = __float2bfloat16_rn(fmaxf(v[q] + a.bias[n], 0.0f));
-          }
-        }
-      }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[b]));
-    }
-  }
-  __syncwarp();
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 8) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
-  }
-}
 
 // The 2x2 max pooling of 16 channels with its argmax, for training (the backward pass routes
 // the gradient to the argmax). Lane pairs (x even, x odd) hold one pooled cell; v0 / v1 are the
@@ -606,6 +403,12 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Shared-memory stages of k_conv_halo: three when they and the weights fit in half an SM's
+// shared memory (two CTAs a SM), else two.
+__host__ __device__ constexpr int halo_stages(int cin, int cout, int w) {
+  return 3 * (cin / 8) * 4 * (w + 2) * 16 + 9 * (cin / 8) * cout * 16 + 128 <= 113 * 1024 ? 3 : 2;
+}
+
 // Forward 3x3 convolution with its 2x2 max pooling (inference), without any gather. A work
 // item is one pair of image rows (y0, y0 + 1) of one snippet; the TMA engine loads the four
 // input rows y0 - 1 .. y0 + 2 of the channels-last map once, W + 2 pixels wide (-1 .. W, zero
@@ -616,8 +419,11 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 // next row (and for the last tap past the stage) and are not used. The weights sit in shared
 // memory as [tap][plane][cout][8]. 320 threads: two epilogue warpgroups (warps 0-3 and 4-7),
 // each draining one of the two TMEM accumulator buffers (items alternate between them), warp 8
-// issues the TMA loads and warp 9 owns TMEM and issues the MMAs; three shared-memory stages.
-template <int CIN, int COUT, int W, bool TRAIN>
+// issues the TMA loads and warp 9 owns TMEM and issues the MMAs; two or three shared-memory
+// stages. DX: the input gradient of a convolution, i.e. the same convolution of the output
+// gradient dY (channels-last) with the flipped, channel-transposed kernel; the epilogue writes
+// the sums as they are, FP32 channel-major [c][(b, y, x)].
+template <int CIN, int COUT, int W, bool TRAIN, bool DX = false>
 __global__ void __launch_bounds__(320, 2)
     k_conv_halo(const __grid_constant__ CUtensorMap mx, ConvArgs a, const bf16* __restrict__ wb, int kp,
                 uint32_t* err) {
@@ -627,7 +433,7 @@ __global__ void __launch_bounds__(320, 2)
   constexpr int PB = 4 * PITCH * 16;           // bytes of one plane (4 rows)
   constexpr int SB = NPL * PB;                 // bytes of one stage
   constexpr int KS = NPL / 2;                  // K steps of 16 per tap
-  constexpr int S = 3;                         // stages
+  constexpr int S = halo_stages(CIN, COUT, W);  // stages
   constexpr uint32_t kCols = 2 * T * COUT < 32 ? 32 : 2 * T * COUT;
   static_assert(W == 128 || W == 64, "tile geometry");
   extern __shared__ uint8_t hsm_raw[];
@@ -647,7 +453,7 @@ __global__ void __launch_bounds__(320, 2)
     const int tap = k / CIN, ci = k - tap * CIN;
     wsm[((tap * NPL + ci / 8) * COUT + co) * 8 + (ci & 7)] = wb[static_cast<long long>(co) * kp + k];
   }
-  if (threadIdx.x < COUT) bsm[threadIdx.x] = a.bias[threadIdx.x];
+  if (threadIdx.x < COUT) bsm[threadIdx.x] = DX ? 0.0f : a.bias[threadIdx.x];
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tensor core reads them
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -743,7 +549,23 @@ __global__ void __launch_bounds__(320, 2)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t lanes = static_cast<uint32_t>(wq * 32) << 16;
-      if (32 * wq < W) {
+      if (DX && 32 * wq < W) {
+        // the two rows' sums as they are, channel-major FP32 (coalesced along x)
+        const int b = it / h2, y0 = 2 * (it - b * h2);
+        const long long mtot = static_cast<long long>(a.n) * a.h * W;
+        const long long m0 = (static_cast<long long>(b) * a.h + y0) * W + 32 * wq + lane;
+#pragma unroll 1
+        for (int c = 0; c < COUT; c += 16) {
+          float v0[16], v1[16];
+          tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T) * COUT + c), v0);
+          tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T + 1) * COUT + c), v1);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            a.yTf[static_cast<long long>(c + q) * mtot + m0] = v0[q];
+            a.yTf[static_cast<long long>(c + q) * mtot + m0 + W] = v1[q];
+          }
+        }
+      } else if (!DX && 32 * wq < W) {
         // pixel x = 32 wq + lane of rows y0 (tile 0) and y0 + 1 (tile 1). Bias, ReLU and the
         // BF16 rounding are monotone non-decreasing, so the maximum of the four rounded
         // activations is the rounded activation of the largest of the four sums: the pooling
@@ -1093,60 +915,86 @@ __global__ void __launch_bounds__(256) k_transpose(const bf16* __restrict__ in, 
 }
 
 // Gradient through the pooling and the ReLU: the argmax position of each pooled cell gets
-// dP if its activation is positive. Writes dyT[c][m] (all positions) and, when dy is set,
-// dy[m][ldy] (row-major; columns c < CN). A CTA owns 64 consecutive pooled pixels for all
-// CN channels: pass 1 runs along the pixels of one channel (coalesced dP, argmax, y and dyT),
-// and stages the four gradients of each pixel in shared memory; pass 2 writes the dy rows
-// of the tile channel-fastest (coalesced).
+// dP if its activation is positive, the other three positions zero. A thread owns one pooled
+// pixel and 8 channels c0 .. c0 + 7 (blockIdx.y), the lanes of a warp consecutive pixels of
+// one image row (w / 2 is a multiple of 32): it writes dyT[c][m] as two 4-byte pairs per
+// channel (upper and lower row), coalesced along the row, and, when dy is set, the
+// channels-last dy[m][CN] of its four pixels as 16-byte stores. The bias gradient
+// db[c] = sum over m of dY[c][m] (the BF16 values) is reduced over the CTA and added
+// atomically.
 template <int CN>
 __global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, int dp_chan_major,
                                                 const uint8_t* __restrict__ am, const bf16* __restrict__ pooled, int n,
                                                 int h, int w, bf16* __restrict__ dyT, bf16* __restrict__ dy,
-                                                int ldy) {
-  __shared__ bf16 sdy[64 * 4][CN + 2];
-  // pooled pixel counts and map sizes stay below 2^31 (the workspace is sized for them), so
-  // the pixel of a thread is decoded once, in 32 bits (256 threads = 4 channel rows of the
-  // same 64 pixels)
+                                                float* __restrict__ db) {
+  __shared__ float red[8][8];
+  // pooled pixel counts and map sizes stay below 2^31 (the workspace is sized for them)
   const int h2 = h / 2, w2 = w / 2;
   const int npix = n * h2 * w2;
   const long long mtot = static_cast<long long>(n) * h * w;
-  const int pl = threadIdx.x & 63;
-  const int pix = blockIdx.x * 64 + pl;
+  const int pix = blockIdx.x * 256 + threadIdx.x, c0 = blockIdx.y * 8;
+  const bool valid = pix < npix;
   const int x2 = pix % w2, r = pix / w2;
   const int y2 = r % h2, b = r / h2;
   const long long m00 = (static_cast<long long>(b) * h + 2 * y2) * w + 2 * x2;
-  for (int idx = threadIdx.x; idx < CN * 64 && pix < npix; idx += 256) {
-    const int c = idx >> 6;
-    const long long pc = static_cast<long long>(c) * npix + pix;  // channel-major pooled index
-    const float g = dp_chan_major ? dp[pc] : dp[static_cast<long long>(b) * CN * h2 * w2 +
-                                                 (static_cast<long long>(c) * h2 + y2) * w2 + x2];
-    const int a = am[pc];
-    // the activation at the argmax is the pooled value (channels-last when the gradient is
-    // channel-major, fc1's rows [b][(c, y2, x2)] otherwise)
-    const long long pi = dp_chan_major ? static_cast<long long>(pix) * CN + c
-                                       : static_cast<long long>(b) * CN * h2 * w2 + (static_cast<long long>(c) * h2 + y2) * w2 + x2;
-    const bool live = __bfloat162float(pooled[pi]) > 0.0f;
+  float bsum[8];
+  uint32_t d0[4], d1[4], d2[4], d3[4];  // dy of the four pixels q (channel pairs)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long m = m00 + (q >> 1) * w + (q & 1);
-      const long long yi = static_cast<long long>(c) * mtot + m;
-      const float v = (q == a && live) ? g : 0.0f;
-      const bf16 bv = __float2bfloat16_rn(v);
-      dyT[yi] = bv;
-      sdy[pl * 4 + q][c] = bv;
+  for (int j = 0; j < 8; ++j) {
+    const int c = c0 + j;
+    float g = 0.0f;
+    int a = 0;
+    bool live = false;
+    if (valid) {
+      const long long pc = static_cast<long long>(c) * npix + pix;  // channel-major pooled index
+      // the activation at the argmax is the pooled value (channels-last when the gradient is
+      // channel-major, fc1's rows [b][(c, y2, x2)] otherwise)
+      const long long fi = static_cast<long long>(b) * CN * h2 * w2 + (static_cast<long long>(c) * h2 + y2) * w2 + x2;
+      g = dp_chan_major ? dp[pc] : dp[fi];
+      a = am[pc];
+      const long long pi = dp_chan_major ? static_cast<long long>(pix) * CN + c : fi;
+      live = __bfloat162float(pooled[pi]) > 0.0f;
+    }
+    const bf16 bv = __float2bfloat16_rn(live ? g : 0.0f);
+    const uint32_t u = __bfloat16_as_ushort(bv);
+    bsum[j] = __bfloat162float(bv);
+    const uint32_t top = a == 0 ? u : (a == 1 ? (u << 16) : 0u);
+    const uint32_t bot = a == 2 ? u : (a == 3 ? (u << 16) : 0u);
+    if (valid) {
+      *reinterpret_cast<uint32_t*>(dyT + static_cast<long long>(c) * mtot + m00) = top;
+      *reinterpret_cast<uint32_t*>(dyT + static_cast<long long>(c) * mtot + m00 + w) = bot;
+    }
+    // channel j of pixel q: half j & 1 of word j / 2
+    const int sh = (j & 1) * 16;
+    const uint32_t e0 = (a == 0 ? u : 0u) << sh, e1 = (a == 1 ? u : 0u) << sh;
+    const uint32_t e2 = (a == 2 ? u : 0u) << sh, e3 = (a == 3 ? u : 0u) << sh;
+    if (j & 1) {
+      d0[j >> 1] |= e0; d1[j >> 1] |= e1; d2[j >> 1] |= e2; d3[j >> 1] |= e3;
+    } else {
+      d0[j >> 1] = e0; d1[j >> 1] = e1; d2[j >> 1] = e2; d3[j >> 1] = e3;
     }
   }
-  if (!dy) return;
+  if (dy && valid) {
+    bf16* base = dy + m00 * CN + c0;
+    *reinterpret_cast<uint4*>(base) = make_uint4(d0[0], d0[1], d0[2], d0[3]);
+    *reinterpret_cast<uint4*>(base + CN) = make_uint4(d1[0], d1[1], d1[2], d1[3]);
+    *reinterpret_cast<uint4*>(base + static_cast<long long>(w) * CN) = make_uint4(d2[0], d2[1], d2[2], d2[3]);
+    *reinterpret_cast<uint4*>(base + static_cast<long long>(w + 1) * CN) = make_uint4(d3[0], d3[1], d3[2], d3[3]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float v = bsum[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0) red[warp][j] = v;
+  }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 64 * 4 * CN; idx += 256) {
-    const int c = idx % CN, pq = idx / CN;
-    const int pq_l = pq >> 2, q = pq & 3;
-    const int pix2 = blockIdx.x * 64 + pq_l;
-    if (pix2 >= npix) continue;
-    const int xx2 = pix2 % w2, rr = pix2 / w2;
-    const int yy2 = rr % h2, bb = rr / h2;
-    const long long m = (static_cast<long long>(bb) * h + 2 * yy2 + (q >> 1)) * w + 2 * xx2 + (q & 1);
-    dy[m * ldy + c] = sdy[pq][c];
+  if (threadIdx.x < 8) {
+    float v = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v += red[k][threadIdx.x];
+    atomicAdd(db + c0 + threadIdx.x, v);
   }
 }
 
@@ -1187,32 +1035,6 @@ __global__ void k_head(const float* __restrict__ hf, const float* __restrict__ p
   }
 }
 
-// db[c] += sum_m dyT[c][m]: blockIdx.y = channel, blocks along x take contiguous slices
-// (16-byte loads of 8 values) and add their partial sums atomically.
-__global__ void __launch_bounds__(256) k_rowsum(const bf16* __restrict__ dyT, long long mtot, float* __restrict__ out) {
-  const int c = blockIdx.y;
-  const bf16* row = dyT + c * mtot;
-  const long long nvec = mtot / 8;  // mtot is a multiple of 8 (n * h * w)
-  float s = 0.0f;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < nvec;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const uint4 q = *reinterpret_cast<const uint4*>(row + 8 * i);
-    const bf16* v = reinterpret_cast<const bf16*>(&q);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) s += __bfloat162float(v[k]);
-  }
-  __shared__ float red[8];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.0f;
-    for (int w = 0; w < 8; ++w) t += red[w];
-    atomicAdd(out + c, t);
-  }
-}
-
 // dst[r][ldd] (or dst[c][ldd] transposed) = bf16(src[r][cols]), zero-padded to ldd
 __global__ void k_cast_w(const float* __restrict__ src, int rows, int cols, bf16* __restrict__ dst, int ldd,
                          int transposed, int dst_rows) {
@@ -1230,7 +1052,6 @@ __global__ void k_cast_w(const float* __restrict__ src, int rows, int cols, bf16
   }
 }
 
-// dst[co][tap*cin + ci] = bf16(src[co][ci*9 + tap]) (the tap-major K of k_conv_tc), zero to kp
 // dst[ci][tap*cout + co] = bf16(src[co][ci*9 + (8 - tap)]), zero to kp: the kernel of the input
 // gradient as a forward convolution of dY (rotated by 180 degrees, in and out channels swapped)
 __global__ void k_cast_w_flip(const float* __restrict__ src, int cout, int cin, bf16* __restrict__ dst, int kp) {
@@ -1247,6 +1068,7 @@ __global__ void k_cast_w_flip(const float* __restrict__ src, int cout, int cin, 
   }
 }
 
+// dst[co][tap*cin + ci] = bf16(src[co][ci*9 + tap]) (the tap-major K of k_conv_halo), zero to kp
 __global__ void k_cast_w_tap(const float* __restrict__ src, int cout, int cin, bf16* __restrict__ dst, int kp) {
   const long long total = static_cast<long long>(cout) * kp;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
@@ -1432,10 +1254,14 @@ cudaError_t persistent_grid(K kern, int smem, int threads, int tmem_cols, int it
 }
 
 // Forward 3x3 convolution and 2x2 max pooling of a channels-last [n][h][w][cin] BF16 map
-// with k_conv_halo (inference): pooled output channels-last [(b, y2, x2)][cout] (pool_cl) or
-// [b][(c, y2, x2)]. Weights wb[cout][kp] BF16, tap-major K.
+// with k_conv_halo: pooled output channels-last [(b, y2, x2)][cout] (pool_cl) or
+// [b][(c, y2, x2)], with am set (training) also the argmax of every pooled cell. With dxT set
+// instead: the plain convolution (no bias, ReLU or pooling) into dxT[cout][(b, y, x)] FP32,
+// which with dY as x and the flipped kernel is a layer's input gradient. Weights wb[cout][kp]
+// BF16, tap-major K.
 int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int kp, int cout, const float* bias,
-              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches, uint8_t* am = nullptr) {
+              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches, uint8_t* am = nullptr,
+              float* dxT = nullptr) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
   const cuuint64_t dims[4] = {static_cast<cuuint64_t>(cin), static_cast<cuuint64_t>(w), static_cast<cuuint64_t>(h),
@@ -1450,12 +1276,12 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl, am};
+  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, dxT, pool, pool_cl, am};
   const int items = n * (h / 2);
   auto go = [&](auto kern, int npl, int cw) {
-    // 3 stages x planes x 4 rows x (w + 2) pixels x 16 bytes, then the weights
+    // stages x planes x 4 rows x (w + 2) pixels x 16 bytes, then the weights
     const int stage = npl * 4 * (w + 2) * 16;
-    const int smem = 128 + 3 * stage + 9 * npl * cw * 16;
+    const int smem = 128 + halo_stages(8 * npl, cw, w) * stage + 9 * npl * cw * 16;
     int grid = 0;
     const cudaError_t e = persistent_grid(kern, smem, 320, 4 * cw, items, &grid);
     if (e != cudaSuccess) return e;
@@ -1463,9 +1289,18 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
     return cudaGetLastError();
   };
   cudaError_t e;
-  if (cin == 16 && cout == 32 && w == 128 && h % 2 == 0) {
+  if (h % 2 != 0) return SND_ERR_UNSUPPORTED;
+  if (dxT) {
+    if (cin == 32 && cout == 16 && w == 128) {
+      e = go(k_conv_halo<32, 16, 128, false, true>, 4, 16);
+    } else if (cin == 64 && cout == 32 && w == 64) {
+      e = go(k_conv_halo<64, 32, 64, false, true>, 8, 32);
+    } else {
+      return SND_ERR_UNSUPPORTED;
+    }
+  } else if (cin == 16 && cout == 32 && w == 128) {
     e = am ? go(k_conv_halo<16, 32, 128, true>, 2, 32) : go(k_conv_halo<16, 32, 128, false>, 2, 32);
-  } else if (cin == 32 && cout == 64 && w == 64 && h % 2 == 0) {
+  } else if (cin == 32 && cout == 64 && w == 64) {
     e = am ? go(k_conv_halo<32, 64, 64, true>, 4, 64) : go(k_conv_halo<32, 64, 64, false>, 4, 64);
   } else {
     return SND_ERR_UNSUPPORTED;
@@ -1500,36 +1335,6 @@ int conv1_tc(const float* x, int n, const float* w, const float* bias, bf16* out
   };
   const cudaError_t e = am ? go(k_conv1_tc<true>) : go(k_conv1_tc<false>);
   if (launches) *launches += 1;
-  return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
-}
-
-// Input gradient of a 3x3 convolution on the tensor cores (k_conv_tc in DX mode):
-// dX^T[cin][m] = sum over taps and output channels of dY[m + tap offset][co] * W'[ci][tap*cdy + co],
-// with dY row-major [m][64] (cdy channels used) and W' = k_cast_w_flip of the layer's kernel.
-int conv_tc_dx(const bf16* dy, int n, int h, int w, int cdy, const bf16* wflip, int kp, int cin, float* dxT,
-               uint32_t* err, cudaStream_t s, int64_t* launches) {
-  constexpr int BN = 32;
-  if (cin > BN) return SND_ERR_UNSUPPORTED;
-  CUtensorMap mb;
-  if (!make_map(&mb, wflip, kp, cin, kp, BN)) return SND_ERR_UNSUPPORTED;
-  ConvArgs a{dy, n, h, w, cdy, 9 * cdy, kp / kBK, nullptr, nullptr, cin, 64, dxT};
-  const long long M = 1LL * n * h * w;
-  const long long mt = (M + kBM - 1) / kBM;
-  const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
-  const int per_sm = std::max(1, (227 * 1024) / smem);
-  const unsigned grid = static_cast<unsigned>(std::min<long long>(mt, 152LL * per_sm));
-  cudaError_t e;
-  if (cdy == 32) {
-    e = cudaFuncSetAttribute(k_conv_tc<32, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) k_conv_tc<32, 32, true><<<grid, 288, smem, s>>>(mb, a, err);
-  } else if (cdy == 64) {
-    e = cudaFuncSetAttribute(k_conv_tc<32, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) k_conv_tc<32, 64, true><<<grid, 288, smem, s>>>(mb, a, err);
-  } else {
-    return SND_ERR_UNSUPPORTED;
-  }
-  if (launches) *launches += 1;
-  if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
 
@@ -1583,7 +1388,7 @@ void layout(Sifter& f) {
     f.o.p[l] = take(2ull * c.cout * m / 4);
     f.o.am[l] = take(1ull * c.cout * m / 4);
     if (f.training) {
-      f.o.dy[l] = take(l > 0 ? 2ull * m * 64 : 0);
+      f.o.dy[l] = take(l > 0 ? 2ull * m * c.cout : 0);
       f.o.dyT[l] = take(2ull * c.cout * m);
       f.o.colT[l] = take(2ull * c.kc * m);
       f.o.dp[l] = take(l < 2 ? 4ull * c.cout * m / 4 : 0);
@@ -1625,7 +1430,7 @@ cudaError_t prep_weights(Sifter& f, cudaStream_t s) {
     if (l == 0) {
       k_cast_w<<<grid_for(1LL * c.cout * c.kp), 256, 0, s>>>(P + kOffW[l], c.cout, c.kc, at<bf16>(f, f.o.wb[l]), c.kp,
                                                            0, c.cout);
-    } else {  // tap-major K for k_conv_tc
+    } else {  // tap-major K for k_conv_halo
       k_cast_w_tap<<<grid_for(1LL * c.cout * c.kp), 256, 0, s>>>(P + kOffW[l], c.cout, c.cin, at<bf16>(f, f.o.wb[l]),
                                                                c.kp);
     }
@@ -1713,19 +1518,21 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     bf16* dyT = at<bf16>(f, f.o.dyT[l]);
     bf16* dy = l > 0 ? at<bf16>(f, f.o.dy[l]) : nullptr;
     {
-      const unsigned ub = static_cast<unsigned>((m / 4 + 63) / 64);
+      // the routed gradient and, fused, the bias gradient
+      const dim3 ub(static_cast<unsigned>((m / 4 + 255) / 256), static_cast<unsigned>(c.cout / 8));
       const uint8_t* am = at<uint8_t>(f, f.o.am[l]);
       const bf16* yl = l == 2 ? at<bf16>(f, f.o.p3) : at<bf16>(f, f.o.p[l]);  // the pooled map
+      float* db = G + kOffB[l];
       if (c.cout == 16) {
-        k_unpool<16><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, 64);
+        k_unpool<16><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, db);
       } else if (c.cout == 32) {
-        k_unpool<32><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, 64);
+        k_unpool<32><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, db);
       } else {
-        k_unpool<64><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, 64);
+        k_unpool<64><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, db);
       }
     }
     f.launches++;
-    // weight and bias gradients
+    // weight gradient
     bf16* colT = at<bf16>(f, f.o.colT[l]);
     if (l == 0) {
       k_im2colT<float><<<grid_for(m), 256, 0, s>>>(x, n, c.h, c.w, c.kc, colT);
@@ -1743,16 +1550,11 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     Epi ew{nullptr, 0, G + kOffW[l], 0, 0, 1, c.kc};
     int rc = gemm(dyT, m, colT, m, c.cout, c.kc, m, ew, splits, err, s, &f.launches);
     if (rc) return rc;
-    {
-      const long long nb = std::min<long long>(std::max<long long>(1, m / 8 / 256 / 8), 4 * 152 / c.cout + 1);
-      k_rowsum<<<dim3(static_cast<unsigned>(nb), c.cout), 256, 0, s>>>(dyT, m, G + kOffB[l]);
-    }
-    f.launches++;
     if (l == 0) break;
     // input gradient, straight into the previous pooled map's gradient dP[cin][m]: the
-    // forward convolution of dY with the flipped kernel, an implicit GEMM like conv2/conv3
-    rc = conv_tc_dx(dy, n, c.h, c.w, c.cout, at<bf16>(f, f.o.wT[l]), (9 * c.cout + kBK - 1) / kBK * kBK, c.cin,
-                    at<float>(f, f.o.dp[l - 1]), err, s, &f.launches);
+    // convolution of dY with the flipped kernel, on the halo kernel
+    rc = conv_halo(dy, n, c.h, c.w, c.cout, at<bf16>(f, f.o.wT[l]), (9 * c.cout + kBK - 1) / kBK * kBK, c.cin, nullptr,
+                   nullptr, 0, err, s, &f.launches, nullptr, at<float>(f, f.o.dp[l - 1]));
     if (rc) return rc;
   }
   return cudaGetLastError() == cudaSuccess ? SND_OK : SND_ERR_CUDA;
