@@ -344,14 +344,17 @@ struct ConvArgs {
   bf16* yT;         // unused
   int cout;
   int ldx;          // elements per input pixel
-  float* yTf;       // DX: the convolution itself, [cout][n*h*w] FP32 (no bias, ReLU or pooling)
+  float* yTf;       // unused
   // k_conv_halo: the 2x2 max pooling of the activations. pool_cl: pooled map channels-last
   // p[(b, y2, x2)][cout]; else p[b][(c, y2, x2)] (fc1's input rows)
   bf16* p;
   int pool_cl;
-  // training: the argmax 0..3 of every pooled cell, am[c * npix + pooled pixel] (first maximum
-  // of the four BF16 activations in row-major order); null in inference
-  uint8_t* am;
+  // training: the argmax 0..3 of every pooled cell (first maximum of the four BF16 activations
+  // in row-major order), 2 bits a channel: am[(c / 16) * npix + pooled pixel] bits 2 (c % 16);
+  // null in inference
+  uint32_t* am;
+  // DX: the convolution itself, channels-last BF16 [(b, y, x)][cout] (no bias, ReLU or pooling)
+  bf16* dx;
 };
 
 // The 2x2 max pooling of 16 channels with its argmax, for training (the backward pass routes
@@ -359,9 +362,11 @@ struct ConvArgs {
 // FP32 sums of the lane's pixel in the upper / lower row. Each activation is bias, ReLU and
 // BF16 rounding of its sum; the cell takes the first maximum in row-major order (upper left,
 // upper right, lower left, lower right), as the oracle's pooling does. Even lanes get the packed pooled
-// values in pk and write the argmax bytes am[(c0 + q) * npix + pix].
+// values in pk and write the 16 argmaxes, 2 bits each (channel c0 + q at bits 2q, 2q + 1), as one
+// word am[(c0 / 16) * npix + pix].
 __device__ __forceinline__ void pool_argmax16(const float* v0, const float* v1, const float* bias, int lane,
-                                              uint32_t* pk, uint8_t* am, int c0, long long npix, long long pix) {
+                                              uint32_t* pk, uint32_t* am, int c0, long long npix, long long pix) {
+  uint32_t code = 0;
 #pragma unroll
   for (int q = 0; q < 16; q += 2) {
     float best[2];
@@ -376,11 +381,12 @@ __device__ __forceinline__ void pool_argmax16(const float* v0, const float* v1, 
       if (l > bv) { bv = l; a = 2; }
       if (lr > bv) { bv = lr; a = 3; }
       best[e] = bv;
-      if (!(lane & 1)) am[static_cast<long long>(c0 + q + e) * npix + pix] = static_cast<uint8_t>(a);
+      code |= static_cast<uint32_t>(a) << (2 * (q + e));
     }
     const __nv_bfloat162 pr = __floats2bfloat162_rn(best[0], best[1]);
     pk[q >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
   }
+  if (!(lane & 1)) am[static_cast<long long>(c0 >> 4) * npix + pix] = code;
 }
 
 // ---------------------------------------------------------------- halo convolution
@@ -422,7 +428,7 @@ __host__ __device__ constexpr int halo_stages(int cin, int cout, int w) {
 // issues the TMA loads and warp 9 owns TMEM and issues the MMAs; two or three shared-memory
 // stages. DX: the input gradient of a convolution, i.e. the same convolution of the output
 // gradient dY (channels-last) with the flipped, channel-transposed kernel; the epilogue writes
-// the sums as they are, FP32 channel-major [c][(b, y, x)].
+// the sums rounded to BF16, channels-last [(b, y, x)][c].
 template <int CIN, int COUT, int W, bool TRAIN, bool DX = false>
 __global__ void __launch_bounds__(320, 2)
     k_conv_halo(const __grid_constant__ CUtensorMap mx, ConvArgs a, const bf16* __restrict__ wb, int kp,
@@ -550,19 +556,25 @@ __global__ void __launch_bounds__(320, 2)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t lanes = static_cast<uint32_t>(wq * 32) << 16;
       if (DX && 32 * wq < W) {
-        // the two rows' sums as they are, channel-major FP32 (coalesced along x)
+        // the two rows' sums rounded to BF16, channels-last (a lane's 16 channels are 32
+        // contiguous bytes, the lanes consecutive pixels)
         const int b = it / h2, y0 = 2 * (it - b * h2);
-        const long long mtot = static_cast<long long>(a.n) * a.h * W;
         const long long m0 = (static_cast<long long>(b) * a.h + y0) * W + 32 * wq + lane;
 #pragma unroll 1
         for (int c = 0; c < COUT; c += 16) {
-          float v0[16], v1[16];
-          tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T) * COUT + c), v0);
-          tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T + 1) * COUT + c), v1);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            a.yTf[static_cast<long long>(c + q) * mtot + m0] = v0[q];
-            a.yTf[static_cast<long long>(c + q) * mtot + m0 + W] = v1[q];
+          for (int r = 0; r < 2; ++r) {
+            float v[16];
+            tmem_ld16(tmem + lanes + static_cast<uint32_t>((bb * T + r) * COUT + c), v);
+            uint32_t pk[8];
+#pragma unroll
+            for (int q = 0; q < 16; q += 2) {
+              const __nv_bfloat162 pr = __floats2bfloat162_rn(v[q], v[q + 1]);
+              pk[q >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(a.dx + (m0 + r * W) * COUT + c);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
           }
         }
       } else if (!DX && 32 * wq < W) {
@@ -641,7 +653,7 @@ __global__ void __launch_bounds__(320, 2)
 template <bool TRAIN>
 __global__ void __launch_bounds__(320, 1)
     k_conv1_tc(const __grid_constant__ CUtensorMap mx, int n, const float* __restrict__ w, const float* __restrict__ bias,
-               bf16* __restrict__ out, uint8_t* __restrict__ am, uint32_t* err) {
+               bf16* __restrict__ out, uint32_t* __restrict__ am, uint32_t* err) {
   constexpr int RS = 12, US = 4;               // raw and U stages
   constexpr int RAWW = 136;                    // FP32 values per loaded row (x0 - 4 .. x0 + 131)
   constexpr int RB = 4 * RAWW * 4;             // raw bytes per stage
@@ -836,34 +848,85 @@ __global__ void __launch_bounds__(320, 1)
 
 // ---------------------------------------------------------------- layer kernels
 
-// colT[k][m] for k < kc (the weight-gradient GEMM's B operand, K-major along m) from a
-// channels-last map x[n][h][w][cin], cin = kc / 9 (the snippets themselves for cin = 1)
-template <typename T>
-__global__ void k_im2colT(const T* __restrict__ x, int n, int h, int w, int kc, bf16* __restrict__ colT) {
-  // a thread takes one output pixel m and writes its kc patch values (coalesced along m for
-  // every k); m, its image and its row come from 32-bit index arithmetic once per pixel
-  const int cin = kc / 9;
-  const int hw = h * w;
-  const long long mtot = static_cast<long long>(n) * hw;
-  for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < mtot;
-       m += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int b = static_cast<int>(m / hw);
-    const int yx = static_cast<int>(m - static_cast<long long>(b) * hw);
-    const int yy = yx / w, xx = yx - yy * w;
-    const T* xb = x + static_cast<long long>(b) * hw * cin;
-    for (int ci = 0; ci < cin; ++ci) {
+// conv1's weight gradient dW[co][tap] += sum over pixels m of dY^T[co][m] * x[m + tap offset]
+// (the snippet values rounded to BF16, as the forward convolution reads them; zero outside the
+// snippet). 16 x 9 outputs, so the CUDA cores reduce it directly: a CTA takes one snippet and 4
+// output channels (blockIdx.y) and stages the snippet in shared memory; a warp takes one image
+// row at a time (rows warp, warp + 8, ...), a lane 8 consecutive pixels, whose gradients come
+// as one 16-byte load per channel. A thread keeps its 36 partial sums in registers; the CTA's
+// sums are added atomically.
+__global__ void __launch_bounds__(256) k_dw1(const float* __restrict__ x, int n, const bf16* __restrict__ dyT,
+                                             float* __restrict__ dw) {
+  constexpr int XP = kW + 16;  // staged row (BF16): pixel xx at xx + 8, zero at 7 and kW + 8
+  __shared__ __align__(16) bf16 xs[kH + 2][XP];
+  __shared__ float red[8][36];
+  const int b = blockIdx.x, c0 = blockIdx.y * 4;
+  const float* xb = x + static_cast<long long>(b) * kH * kW;
+  const int tx = threadIdx.x;
+  for (int r = 0; r < kH + 2; ++r) {
+    const int yy = r - 1;
+    xs[r][tx + 8] = __float2bfloat16_rn((yy >= 0 && yy < kH) ? xb[yy * kW + tx] : 0.0f);
+  }
+  if (tx < kH + 2) {
+    xs[tx][7] = __float2bfloat16_rn(0.0f);
+    xs[tx][kW + 8] = __float2bfloat16_rn(0.0f);
+  }
+  __syncthreads();
+  const long long mtot = static_cast<long long>(n) * kH * kW;
+  const int warp = tx >> 5, lane = tx & 31;
+  float acc[4][9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        const int sy = yy + r / 3 - 1, sx = xx + r % 3 - 1;
-        float val = 0.0f;
-        if (sy >= 0 && sy < h && sx >= 0 && sx < w) val = static_cast<float>(xb[(sy * w + sx) * cin + ci]);
-        colT[static_cast<long long>(ci * 9 + r) * mtot + m] = __float2bfloat16_rn(val);
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[j][k] = 0.0f;
+  const bf16* dyb = dyT + static_cast<long long>(c0) * mtot + static_cast<long long>(b) * kH * kW + 8 * lane;
+#pragma unroll 1
+  for (int y = warp; y < kH; y += 8) {
+    uint4 gq[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gq[j] = *reinterpret_cast<const uint4*>(dyb + j * mtot + y * kW);
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      // pixels 8 lane - 1 .. 8 lane + 8 of input row y + ky - 1 (staged row y + ky)
+      const bf16* row = &xs[y + ky][8 * lane + 8];
+      const uint4 mid = *reinterpret_cast<const uint4*>(row);
+      const bf16* mv = reinterpret_cast<const bf16*>(&mid);
+      float win[10];
+      win[0] = __bfloat162float(row[-1]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) win[k + 1] = __bfloat162float(mv[k]);
+      win[9] = __bfloat162float(row[8]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bf16* g = reinterpret_cast<const bf16*>(&gq[j]);
+#pragma unroll
+        for (int px = 0; px < 8; ++px) {
+          const float gv = __bfloat162float(g[px]);
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) acc[j][ky * 3 + kx] = fmaf(gv, win[px + kx], acc[j][ky * 3 + kx]);
+        }
       }
     }
   }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float v = acc[j][k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      if (lane == 0) red[warp][j * 9 + k] = v;
+    }
+  __syncthreads();
+  if (tx < 36) {
+    float v = 0.0f;
+#pragma unroll
+    for (int w8 = 0; w8 < 8; ++w8) v += red[w8][tx];
+    atomicAdd(dw + c0 * 9 + tx, v);
+  }
 }
 
-// colT[k][m] (k = ci*9 + tap, as k_im2colT) from a channels-last BF16 map x[n][h][w][CIN]:
+// colT[k][m] (k = ci*9 + tap, the order of the weights) from a channels-last BF16 map x[n][h][w][CIN]:
 // a thread takes one pixel m, reads the CIN channels of each tap's source pixel with 16-byte
 // loads and writes them to CIN rows of colT, so both the reads and the writes of neighbouring
 // threads (neighbouring m) are contiguous.
@@ -916,55 +979,73 @@ __global__ void __launch_bounds__(256) k_transpose(const bf16* __restrict__ in, 
 
 // Gradient through the pooling and the ReLU: the argmax position of each pooled cell gets
 // dP if its activation is positive, the other three positions zero. A thread owns one pooled
-// pixel and 8 channels c0 .. c0 + 7 (blockIdx.y), the lanes of a warp consecutive pixels of
-// one image row (w / 2 is a multiple of 32): it writes dyT[c][m] as two 4-byte pairs per
+// pixel and 16 channels c0 .. c0 + 15 (blockIdx.y), the lanes of a warp consecutive pixels of
+// one image row (w / 2 is a multiple of 32). CL: dP and the pooled map are channels-last BF16
+// [pix][CN] (conv1's and conv2's pooled maps, whose gradient the next layer's input-gradient
+// convolution writes), read as 16-byte vectors; else (conv3) dP is FP32 and the pooled map
+// BF16, both in fc1's row layout [b][(c, y2, x2)]. Writes dyT[c][m] as two 4-byte pairs per
 // channel (upper and lower row), coalesced along the row, and, when dy is set, the
 // channels-last dy[m][CN] of its four pixels as 16-byte stores. The bias gradient
 // db[c] = sum over m of dY[c][m] (the BF16 values) is reduced over the CTA and added
 // atomically.
-template <int CN>
-__global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, int dp_chan_major,
-                                                const uint8_t* __restrict__ am, const bf16* __restrict__ pooled, int n,
-                                                int h, int w, bf16* __restrict__ dyT, bf16* __restrict__ dy,
-                                                float* __restrict__ db) {
-  __shared__ float red[8][8];
+template <int CN, bool CL>
+__global__ void __launch_bounds__(256) k_unpool(const void* __restrict__ dpv, const uint32_t* __restrict__ am,
+                                                const bf16* __restrict__ pooled, int n, int h, int w,
+                                                bf16* __restrict__ dyT, bf16* __restrict__ dy, float* __restrict__ db) {
+  __shared__ float red[8][16];
   // pooled pixel counts and map sizes stay below 2^31 (the workspace is sized for them)
   const int h2 = h / 2, w2 = w / 2;
   const int npix = n * h2 * w2;
   const long long mtot = static_cast<long long>(n) * h * w;
-  const int pix = blockIdx.x * 256 + threadIdx.x, c0 = blockIdx.y * 8;
+  const int pix = blockIdx.x * 256 + threadIdx.x, c0 = blockIdx.y * 16;
   const bool valid = pix < npix;
   const int x2 = pix % w2, r = pix / w2;
   const int y2 = r % h2, b = r / h2;
   const long long m00 = (static_cast<long long>(b) * h + 2 * y2) * w + 2 * x2;
-  float bsum[8];
-  uint32_t d0[4], d1[4], d2[4], d3[4];  // dy of the four pixels q (channel pairs)
+  // the 16 gradients (as BF16) and the 16 pooled activations of the pixel
+  uint32_t gw[8], pw[8];
+  uint32_t code = 0;
+  if (valid) {
+    code = am[static_cast<long long>(blockIdx.y) * npix + pix];
+    if constexpr (CL) {
+      const uint4* gs = reinterpret_cast<const uint4*>(static_cast<const bf16*>(dpv) + static_cast<long long>(pix) * CN + c0);
+      const uint4* ps = reinterpret_cast<const uint4*>(pooled + static_cast<long long>(pix) * CN + c0);
+      const uint4 g0 = gs[0], g1 = gs[1], p0 = ps[0], p1 = ps[1];
+      gw[0] = g0.x; gw[1] = g0.y; gw[2] = g0.z; gw[3] = g0.w; gw[4] = g1.x; gw[5] = g1.y; gw[6] = g1.z; gw[7] = g1.w;
+      pw[0] = p0.x; pw[1] = p0.y; pw[2] = p0.z; pw[3] = p0.w; pw[4] = p1.x; pw[5] = p1.y; pw[6] = p1.z; pw[7] = p1.w;
+    } else {
+      const float* dpf = static_cast<const float*>(dpv);
+      const long long f0 = static_cast<long long>(b) * CN * h2 * w2 + (static_cast<long long>(c0) * h2 + y2) * w2 + x2;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int c = c0 + j;
-    float g = 0.0f;
-    int a = 0;
-    bool live = false;
-    if (valid) {
-      const long long pc = static_cast<long long>(c) * npix + pix;  // channel-major pooled index
-      // the activation at the argmax is the pooled value (channels-last when the gradient is
-      // channel-major, fc1's rows [b][(c, y2, x2)] otherwise)
-      const long long fi = static_cast<long long>(b) * CN * h2 * w2 + (static_cast<long long>(c) * h2 + y2) * w2 + x2;
-      g = dp_chan_major ? dp[pc] : dp[fi];
-      a = am[pc];
-      const long long pi = dp_chan_major ? static_cast<long long>(pix) * CN + c : fi;
-      live = __bfloat162float(pooled[pi]) > 0.0f;
+      for (int q = 0; q < 16; q += 2) {
+        const long long fa = f0 + static_cast<long long>(q) * h2 * w2, fb = fa + static_cast<long long>(h2) * w2;
+        const __nv_bfloat162 gp = __floats2bfloat162_rn(dpf[fa], dpf[fb]);
+        gw[q >> 1] = *reinterpret_cast<const uint32_t*>(&gp);
+        pw[q >> 1] = static_cast<uint32_t>(__bfloat16_as_ushort(pooled[fa])) |
+                     (static_cast<uint32_t>(__bfloat16_as_ushort(pooled[fb])) << 16);
+      }
     }
-    const bf16 bv = __float2bfloat16_rn(live ? g : 0.0f);
-    const uint32_t u = __bfloat16_as_ushort(bv);
-    bsum[j] = __bfloat162float(bv);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) gw[q] = pw[q] = 0u;
+  }
+  float bsum[16];
+  uint32_t d0[8], d1[8], d2[8], d3[8];  // dy of the four pixels (channel pairs)
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int a = (code >> (2 * j)) & 3;
+    const uint32_t graw = (gw[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+    const uint32_t praw = (pw[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+    const bool live = __bfloat162float(__ushort_as_bfloat16(static_cast<unsigned short>(praw))) > 0.0f;
+    const uint32_t u = live ? graw : 0u;
+    bsum[j] = __bfloat162float(__ushort_as_bfloat16(static_cast<unsigned short>(u)));
     const uint32_t top = a == 0 ? u : (a == 1 ? (u << 16) : 0u);
     const uint32_t bot = a == 2 ? u : (a == 3 ? (u << 16) : 0u);
     if (valid) {
+      const int c = c0 + j;
       *reinterpret_cast<uint32_t*>(dyT + static_cast<long long>(c) * mtot + m00) = top;
       *reinterpret_cast<uint32_t*>(dyT + static_cast<long long>(c) * mtot + m00 + w) = bot;
     }
-    // channel j of pixel q: half j & 1 of word j / 2
     const int sh = (j & 1) * 16;
     const uint32_t e0 = (a == 0 ? u : 0u) << sh, e1 = (a == 1 ? u : 0u) << sh;
     const uint32_t e2 = (a == 2 ? u : 0u) << sh, e3 = (a == 3 ? u : 0u) << sh;
@@ -975,22 +1056,25 @@ __global__ void __launch_bounds__(256) k_unpool(const float* __restrict__ dp, in
     }
   }
   if (dy && valid) {
-    bf16* base = dy + m00 * CN + c0;
-    *reinterpret_cast<uint4*>(base) = make_uint4(d0[0], d0[1], d0[2], d0[3]);
-    *reinterpret_cast<uint4*>(base + CN) = make_uint4(d1[0], d1[1], d1[2], d1[3]);
-    *reinterpret_cast<uint4*>(base + static_cast<long long>(w) * CN) = make_uint4(d2[0], d2[1], d2[2], d2[3]);
-    *reinterpret_cast<uint4*>(base + static_cast<long long>(w + 1) * CN) = make_uint4(d3[0], d3[1], d3[2], d3[3]);
+    uint4* q0 = reinterpret_cast<uint4*>(dy + m00 * CN + c0);
+    uint4* q1 = reinterpret_cast<uint4*>(dy + (m00 + 1) * CN + c0);
+    uint4* q2 = reinterpret_cast<uint4*>(dy + (m00 + w) * CN + c0);
+    uint4* q3 = reinterpret_cast<uint4*>(dy + (m00 + w + 1) * CN + c0);
+    q0[0] = make_uint4(d0[0], d0[1], d0[2], d0[3]); q0[1] = make_uint4(d0[4], d0[5], d0[6], d0[7]);
+    q1[0] = make_uint4(d1[0], d1[1], d1[2], d1[3]); q1[1] = make_uint4(d1[4], d1[5], d1[6], d1[7]);
+    q2[0] = make_uint4(d2[0], d2[1], d2[2], d2[3]); q2[1] = make_uint4(d2[4], d2[5], d2[6], d2[7]);
+    q3[0] = make_uint4(d3[0], d3[1], d3[2], d3[3]); q3[1] = make_uint4(d3[4], d3[5], d3[6], d3[7]);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < 16; ++j) {
     float v = bsum[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     if (lane == 0) red[warp][j] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 8) {
+  if (threadIdx.x < 16) {
     float v = 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) v += red[k][threadIdx.x];
@@ -1255,13 +1339,13 @@ cudaError_t persistent_grid(K kern, int smem, int threads, int tmem_cols, int it
 
 // Forward 3x3 convolution and 2x2 max pooling of a channels-last [n][h][w][cin] BF16 map
 // with k_conv_halo: pooled output channels-last [(b, y2, x2)][cout] (pool_cl) or
-// [b][(c, y2, x2)], with am set (training) also the argmax of every pooled cell. With dxT set
-// instead: the plain convolution (no bias, ReLU or pooling) into dxT[cout][(b, y, x)] FP32,
+// [b][(c, y2, x2)], with am set (training) also the argmax of every pooled cell. With dx set
+// instead: the plain convolution (no bias, ReLU or pooling) into dx[(b, y, x)][cout] BF16,
 // which with dY as x and the flipped kernel is a layer's input gradient. Weights wb[cout][kp]
 // BF16, tap-major K.
 int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int kp, int cout, const float* bias,
-              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches, uint8_t* am = nullptr,
-              float* dxT = nullptr) {
+              bf16* pool, int pool_cl, uint32_t* err, cudaStream_t s, int64_t* launches, uint32_t* am = nullptr,
+              bf16* dx = nullptr) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
   const cuuint64_t dims[4] = {static_cast<cuuint64_t>(cin), static_cast<cuuint64_t>(w), static_cast<cuuint64_t>(h),
@@ -1276,7 +1360,7 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, dxT, pool, pool_cl, am};
+  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl, am, dx};
   const int items = n * (h / 2);
   auto go = [&](auto kern, int npl, int cw) {
     // stages x planes x 4 rows x (w + 2) pixels x 16 bytes, then the weights
@@ -1290,7 +1374,7 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
   };
   cudaError_t e;
   if (h % 2 != 0) return SND_ERR_UNSUPPORTED;
-  if (dxT) {
+  if (dx) {
     if (cin == 32 && cout == 16 && w == 128) {
       e = go(k_conv_halo<32, 16, 128, false, true>, 4, 16);
     } else if (cin == 64 && cout == 32 && w == 64) {
@@ -1311,7 +1395,7 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
 
 // conv1 of FP32 snippets x[n][64][256] on the tensor cores (k_conv1_tc) with its pooling,
 // channels-last [(b, y2, x2)][16]; with am set (training) also the argmax of every pooled cell.
-int conv1_tc(const float* x, int n, const float* w, const float* bias, bf16* out, uint8_t* am, uint32_t* err,
+int conv1_tc(const float* x, int n, const float* w, const float* bias, bf16* out, uint32_t* am, uint32_t* err,
              cudaStream_t s, int64_t* launches) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(x) & 15u)) return SND_ERR_UNSUPPORTED;
@@ -1386,12 +1470,12 @@ void layout(Sifter& f) {
     f.o.wb[l] = take(2ull * c.cout * c.kp);
     f.o.wT[l] = take(2ull * c.cin * ((9 * c.cout + kBK - 1) / kBK * kBK));
     f.o.p[l] = take(2ull * c.cout * m / 4);
-    f.o.am[l] = take(1ull * c.cout * m / 4);
+    f.o.am[l] = take(4ull * (c.cout / 16) * (m / 4));
     if (f.training) {
       f.o.dy[l] = take(l > 0 ? 2ull * m * c.cout : 0);
       f.o.dyT[l] = take(2ull * c.cout * m);
-      f.o.colT[l] = take(2ull * c.kc * m);
-      f.o.dp[l] = take(l < 2 ? 4ull * c.cout * m / 4 : 0);
+      f.o.colT[l] = take(l > 0 ? 2ull * c.kc * m : 0);
+      f.o.dp[l] = take(l < 2 ? 2ull * c.cout * m / 4 : 0);
     }
   }
   f.o.wf1b = take(2ull * kHid * kFeat);
@@ -1460,9 +1544,9 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
   // every convolution runs with its 2x2 max pooling in the epilogue; a sifter with training
   // state also keeps the argmax of every pooled cell (and fc1's input rows transposed), which
   // is all the backward pass needs of the forward activations
-  uint8_t* am[3] = {nullptr, nullptr, nullptr};
+  uint32_t* am[3] = {nullptr, nullptr, nullptr};
   if (f.training)
-    for (int l = 0; l < 3; ++l) am[l] = at<uint8_t>(f, f.o.am[l]);
+    for (int l = 0; l < 3; ++l) am[l] = at<uint32_t>(f, f.o.am[l]);
   {
     const int rc = conv1_tc(x, n, P + kOffW[0], P + kOffB[0], at<bf16>(f, f.o.p[0]), am[0], err, s, &f.launches);
     if (rc) return rc;
@@ -1514,34 +1598,35 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
   for (int l = 2; l >= 0; --l) {
     const ConvL& c = kConv[l];
     const long long m = 1LL * n * c.h * c.w;
-    const float* dp = (l == 2) ? at<float>(f, f.o.dp3) : at<float>(f, f.o.dp[l]);
     bf16* dyT = at<bf16>(f, f.o.dyT[l]);
     bf16* dy = l > 0 ? at<bf16>(f, f.o.dy[l]) : nullptr;
     {
       // the routed gradient and, fused, the bias gradient
-      const dim3 ub(static_cast<unsigned>((m / 4 + 255) / 256), static_cast<unsigned>(c.cout / 8));
-      const uint8_t* am = at<uint8_t>(f, f.o.am[l]);
+      const dim3 ub(static_cast<unsigned>((m / 4 + 255) / 256), static_cast<unsigned>(c.cout / 16));
+      const uint32_t* am = at<uint32_t>(f, f.o.am[l]);
       const bf16* yl = l == 2 ? at<bf16>(f, f.o.p3) : at<bf16>(f, f.o.p[l]);  // the pooled map
       float* db = G + kOffB[l];
-      if (c.cout == 16) {
-        k_unpool<16><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, db);
-      } else if (c.cout == 32) {
-        k_unpool<32><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, db);
+      if (l == 0) {
+        k_unpool<16, true><<<ub, 256, 0, s>>>(at<bf16>(f, f.o.dp[l]), am, yl, n, c.h, c.w, dyT, dy, db);
+      } else if (l == 1) {
+        k_unpool<32, true><<<ub, 256, 0, s>>>(at<bf16>(f, f.o.dp[l]), am, yl, n, c.h, c.w, dyT, dy, db);
       } else {
-        k_unpool<64><<<ub, 256, 0, s>>>(dp, l < 2 ? 1 : 0, am, yl, n, c.h, c.w, dyT, dy, db);
+        k_unpool<64, false><<<ub, 256, 0, s>>>(at<float>(f, f.o.dp3), am, yl, n, c.h, c.w, dyT, dy, db);
       }
     }
     f.launches++;
     // weight gradient
-    bf16* colT = at<bf16>(f, f.o.colT[l]);
     if (l == 0) {
-      k_im2colT<float><<<grid_for(m), 256, 0, s>>>(x, n, c.h, c.w, c.kc, colT);
-    } else if (c.cin == 16) {
+      static_assert(kW == 256 && kH + 2 <= 256, "k_dw1 geometry");
+      k_dw1<<<dim3(static_cast<unsigned>(n), 4), 256, 0, s>>>(x, n, dyT, G + kOffW[0]);
+      f.launches++;
+      break;
+    }
+    bf16* colT = at<bf16>(f, f.o.colT[l]);
+    if (c.cin == 16) {
       k_im2colT_nhwc<16><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
-    } else if (c.cin == 32) {
-      k_im2colT_nhwc<32><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
     } else {
-      k_im2colT<bf16><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, c.kc, colT);
+      k_im2colT_nhwc<32><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
     }
     f.launches++;
     const int ktiles = static_cast<int>((m + kBK - 1) / kBK);
@@ -1550,11 +1635,10 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
     Epi ew{nullptr, 0, G + kOffW[l], 0, 0, 1, c.kc};
     int rc = gemm(dyT, m, colT, m, c.cout, c.kc, m, ew, splits, err, s, &f.launches);
     if (rc) return rc;
-    if (l == 0) break;
     // input gradient, straight into the previous pooled map's gradient dP[cin][m]: the
     // convolution of dY with the flipped kernel, on the halo kernel
     rc = conv_halo(dy, n, c.h, c.w, c.cout, at<bf16>(f, f.o.wT[l]), (9 * c.cout + kBK - 1) / kBK * kBK, c.cin, nullptr,
-                   nullptr, 0, err, s, &f.launches, nullptr, at<float>(f, f.o.dp[l - 1]));
+                   nullptr, 0, err, s, &f.launches, nullptr, at<bf16>(f, f.o.dp[l - 1]));
     if (rc) return rc;
   }
   return cudaGetLastError() == cudaSuccess ? SND_OK : SND_ERR_CUDA;
