@@ -11,7 +11,7 @@
 // conv2 and conv3 run with their pooling as k_conv_halo (TMA-loaded input rows, each tap a
 // descriptor view into them; in training the epilogue also keeps the argmax of every pooled
 // cell); their input gradients run on the same kernel (the convolution of dY with the flipped
-// kernel, FP32 output);
+// kernel, BF16 channels-last output);
 // fc1 and every backward GEMM are C = A B^T with both operands K-major BF16 (k_gemm): TMA
 // (128-byte swizzle) fills a 4-stage shared-memory ring, one thread issues tcgen05.mma
 // (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator, and four warps read it
@@ -19,10 +19,11 @@
 // store, or FP32 atomic add for split-K). conv1 (one input channel) runs as k_conv1_tc.
 // The pooled maps that feed conv2 and conv3 and the output gradients dY that feed the input
 // gradients are channels-last ([b][h][w][c]); gradients routed through the pooling are also
-// kept channel-major (dY^T[c][m], m = (b, h, w)) for the weight gradients, whose patch rows
-// colT[k][m] have k tap-major ((ky*3 + kx)*cin + ci), zero-padded to a multiple of 64.
+// kept channel-major (dY^T[c][m], m = (b, h, w)) for the weight gradients, which read the
+// patches of conv2's and conv3's inputs as 9 TMA boxes a K step from three horizontally
+// shifted channel-major copies of the input (k_shift3); conv1's is a direct reduction.
 //   forward conv:   pool(relu(x (x) W + b))                               (k_conv_halo)
-//   weight grad:    dW[cout][k] += dY^T[cout][m] . colT[k][m]            (k_gemm, split-K, atomic)
+//   weight grad:    dW[cout][k] += dY^T[cout][m] . patch[m][k]           (k_gemm, 9 tap boxes, split-K)
 //   input grad:     dX^T[cin][m] = dY (x) flipped W                        (k_conv_halo, DX)
 // Every mbarrier wait is bounded (about 2 s of clock); a wait that gives up sets a device
 // error word that the host turns into SND_ERR_TIMEOUT, and the kernel still frees its TMEM.
@@ -75,6 +76,16 @@ struct Epi {
   long long ldo;
 };
 
+// Weight-gradient mode of k_gemm: K runs over the pixels m = (b, y, x) of an h x w map. The B
+// tile of N-tile j is one TMA box of S[kx][ci][b][y'][x] = map[b][y'][x + kx - 1][ci] (zero
+// outside): 64 pixels x rows y - 1 .. y + 1 x channels 16 j .. 16 j + 15 x kx = 0..2, i.e. 144
+// rows r = kx * 48 + ci * 3 + ky, weight column (16 j + ci) * 9 + 3 ky + kx. The A box holds
+// the arows output-channel rows of dY^T only (the MMA's other rows read stale shared memory
+// and their accumulators are never stored).
+struct Wg {
+  int h, w, arows;
+};
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -118,6 +129,14 @@ __device__ __forceinline__ void tma_load_2d_rows(uint32_t dst, const CUtensorMap
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
       : "memory");
 }
 
@@ -187,12 +206,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // t = blockIdx.x, + gridDim.x, ... (blockIdx.z = K split); the accumulator is double
 // buffered in TMEM (2 x BN columns), so the epilogue of tile j overlaps the MMAs of tile
 // j + 1, and the shared-memory stage ring runs across tiles.
-template <int BN>
+template <int BN, bool WG = false>
 __global__ void __launch_bounds__(192, 1)
     k_gemm(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, int M, int N, int ktiles,
-           int kt_per_split, Epi epi, uint32_t* err) {
+           int kt_per_split, Epi epi, uint32_t* err, Wg wg) {
   constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
-  constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
+  // TMEM: two accumulator buffers of BN columns, allocated as a power of two (at least 32)
+  constexpr uint32_t kCols = 2 * BN <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512)));
+  static_assert(!WG || BN == 144, "weight-gradient tile: 9 taps x 16 channels");
   extern __shared__ uint8_t gsm_raw[];
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_slot;
@@ -244,9 +265,19 @@ __global__ void __launch_bounds__(192, 1)
               break;
             }
             const uint32_t fb = smem_u32(&bar_full[s]);
-            mbar_expect_tx(fb, kABytes + kBBytes);
-            tma_load_2d(sA + s * kABytes, &ma, fb, (kt0 + i) * kBK, m0);
-            tma_load_2d(sB + s * kBBytes, &mb, fb, (kt0 + i) * kBK, n0);
+            if constexpr (WG) {
+              // K step = 64 pixels of one image row (64 divides w)
+              mbar_expect_tx(fb, static_cast<uint32_t>(wg.arows) * kBK * 2 + kBBytes);
+              tma_load_2d(sA + s * kABytes, &ma, fb, (kt0 + i) * kBK, m0);
+              const int px = (kt0 + i) * kBK;
+              const int x0 = px % wg.w, r = px / wg.w;
+              const int y = r % wg.h, b = r / wg.h;
+              tma_load_5d(sB + s * kBBytes, &mb, fb, x0, y - 1, b, (n0 / BN) * 16, 0);
+            } else {
+              mbar_expect_tx(fb, kABytes + kBBytes);
+              tma_load_2d(sA + s * kABytes, &ma, fb, (kt0 + i) * kBK, m0);
+              tma_load_2d(sB + s * kBBytes, &mb, fb, (kt0 + i) * kBK, n0);
+            }
           }
         }
       }
@@ -311,8 +342,12 @@ __global__ void __launch_bounds__(192, 1)
             float x = v[q];
             if (epi.bias) x += epi.bias[n];
             if (epi.relu) x = fmaxf(x, 0.0f);
-            const long long idx = epi.transposed ? static_cast<long long>(n) * epi.ldo + row
-                                                 : static_cast<long long>(row) * epi.ldo + n;
+            long long idx = epi.transposed ? static_cast<long long>(n) * epi.ldo + row
+                                           : static_cast<long long>(row) * epi.ldo + n;
+            if constexpr (WG) {
+              const int r = c + q, kx = r / 48, ci = (n0 / BN) * 16 + (r % 48) / 3, ky = r % 3;
+              idx = static_cast<long long>(row) * epi.ldo + ci * 9 + 3 * ky + kx;
+            }
             if (epi.atomic) {
               atomicAdd(static_cast<float*>(epi.out) + idx, x);
             } else if (epi.out_bf16) {
@@ -926,36 +961,41 @@ __global__ void __launch_bounds__(256) k_dw1(const float* __restrict__ x, int n,
   }
 }
 
-// colT[k][m] (k = ci*9 + tap, the order of the weights) from a channels-last BF16 map x[n][h][w][CIN]:
-// a thread takes one pixel m, reads the CIN channels of each tap's source pixel with 16-byte
-// loads and writes them to CIN rows of colT, so both the reads and the writes of neighbouring
-// threads (neighbouring m) are contiguous.
+// The three horizontally shifted channel-major copies of a channels-last BF16 map
+// x[n][h][w][CIN] that the weight-gradient GEMM reads: S[kx][ci][(b, y, xx)] =
+// x[b][y][xx + kx - 1][ci], zero where xx + kx - 1 is outside the row. A thread takes 8
+// consecutive pixels of one row and one 32-bit word (2 channels) of them, the lanes of a
+// warp the words of consecutive pixel groups (coalesced loads): it loads that word of the 10
+// pixels it needs and writes 2 x 3 rows of 8 values (16 bytes each).
 template <int CIN>
-__global__ void __launch_bounds__(256) k_im2colT_nhwc(const bf16* __restrict__ x, int n, int h, int w,
-                                                      bf16* __restrict__ colT) {
-  // a thread takes one pixel m (decoded once, in 32 bits: map sizes stay below 2^31) and all
-  // nine taps; the writes run along m for every (ci, tap)
-  const int hw = h * w;
-  const int mtot = n * hw;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < mtot; m += gridDim.x * blockDim.x) {
-    const int b = m / hw;
-    const int yx = m - b * hw;
-    const int yy = yx / w, xx = yx - yy * w;
+__global__ void __launch_bounds__(256) k_shift3(const bf16* __restrict__ x, int n, int h, int w, bf16* __restrict__ S) {
+  constexpr int NW = CIN / 2;  // 32-bit words per pixel
+  const long long m = static_cast<long long>(n) * h * w;
+  const long long total = m / 8 * NW;  // w is a multiple of 8
+  const uint32_t* xw = reinterpret_cast<const uint32_t*>(x);
+  for (long long id = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; id < total;
+       id += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long gi = id / NW;
+    const int q = static_cast<int>(id - gi * NW);
+    const long long p0 = gi * 8;  // first pixel (b, y, x0)
+    const int x0 = static_cast<int>(p0 % w);
+    uint32_t wv[10];  // word q of pixels x0 - 1 .. x0 + 8
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
-      uint4 v[CIN / 8];
-      if (sy >= 0 && sy < h && sx >= 0 && sx < w) {
-        const uint4* src = reinterpret_cast<const uint4*>(x + (static_cast<long long>(b) * hw + sy * w + sx) * CIN);
+    for (int k = 0; k < 10; ++k) {
+      const int xx = x0 - 1 + k;
+      wv[k] = (xx >= 0 && xx < w) ? xw[(p0 - 1 + k) * NW + q] : 0u;
+    }
 #pragma unroll
-        for (int q = 0; q < CIN / 8; ++q) v[q] = __ldg(src + q);
-      } else {
+    for (int hf = 0; hf < 2; ++hf) {
+      const uint32_t sel = hf ? 0x7632u : 0x5410u;  // channel 2 q + hf: the high or low halves
 #pragma unroll
-        for (int q = 0; q < CIN / 8; ++q) v[q] = make_uint4(0u, 0u, 0u, 0u);
+      for (int kx = 0; kx < 3; ++kx) {
+        uint32_t o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o[e] = __byte_perm(wv[kx + 2 * e], wv[kx + 2 * e + 1], sel);
+        *reinterpret_cast<uint4*>(S + (static_cast<long long>(kx) * CIN + 2 * q + hf) * m + p0) =
+            make_uint4(o[0], o[1], o[2], o[3]);
       }
-      const bf16* vb = reinterpret_cast<const bf16*>(v);
-#pragma unroll
-      for (int ci = 0; ci < CIN; ++ci) colT[static_cast<long long>(ci * 9 + tap) * mtot + m] = vb[ci];
     }
   }
 }
@@ -1271,11 +1311,11 @@ bool make_map(CUtensorMap* m, const void* base, long long kext, long long rows, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, bool WG = false>
 cudaError_t launch_gemm_bn(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int ktiles, int splits,
-                           const Epi& epi, uint32_t* err, cudaStream_t s) {
+                           const Epi& epi, uint32_t* err, cudaStream_t s, Wg wg = Wg{0, 0, 0}) {
   const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   // CTAs: every output tile gets its own, and K is split (at most `splits` ways, at least 8 K
   // steps a split) so that tiles x splits fill the GPU once (shared memory bounds the CTAs per
@@ -1289,7 +1329,7 @@ cudaError_t launch_gemm_bn(const CUtensorMap& ma, const CUtensorMap& mb, int M, 
   const int per = (ktiles + nsplit - 1) / nsplit;
   const int nz = (ktiles + per - 1) / per;
   dim3 grid(static_cast<unsigned>(std::min(tiles, std::max<long long>(1, slots / nz))), 1, nz);
-  k_gemm<BN><<<grid, 192, smem, s>>>(ma, mb, M, N, ktiles, per, epi, err);
+  k_gemm<BN, WG><<<grid, 192, smem, s>>>(ma, mb, M, N, ktiles, per, epi, err, wg);
   return cudaGetLastError();
 }
 
@@ -1312,6 +1352,34 @@ int gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int 
   }
   if (launches) *launches += 1;
   return e == cudaSuccess ? SND_OK : SND_ERR_CUDA;
+}
+
+// Weight gradient of a 3x3 convolution, dW[cout][ci * 9 + tap] += sum over pixels m of
+// dY^T[cout][m] * x[m + tap offset][ci], with k_gemm in weight-gradient mode: A = dY^T (K-major
+// over the n * h * w pixels), B from the three horizontally shifted channel-major copies of
+// the input map S[3][cin][n][h][w] (k_shift3). cin a multiple of 16, w a multiple of 64.
+int gemm_wg(const bf16* dyT, int cout, const bf16* S, int n, int h, int w, int cin, float* dw, uint32_t* err,
+            cudaStream_t s, int64_t* launches) {
+  EncodeTiledFn fn = encode_fn();
+  const long long m = 1LL * n * h * w;
+  if (!fn || cin % 16 != 0 || w % kBK != 0 || (reinterpret_cast<uintptr_t>(S) & 15u)) return SND_ERR_UNSUPPORTED;
+  CUtensorMap ma, mb;
+  if (cout > kBM || cout % 8 != 0 || !make_map(&ma, dyT, m, cout, m, cout)) return SND_ERR_UNSUPPORTED;
+  const cuuint64_t dims[5] = {static_cast<cuuint64_t>(w), static_cast<cuuint64_t>(h), static_cast<cuuint64_t>(n),
+                              static_cast<cuuint64_t>(cin), 3};
+  const cuuint64_t strides[4] = {static_cast<cuuint64_t>(w) * 2, static_cast<cuuint64_t>(h) * w * 2,
+                                 static_cast<cuuint64_t>(m) * 2, static_cast<cuuint64_t>(cin) * m * 2};
+  const cuuint32_t box[5] = {static_cast<cuuint32_t>(kBK), 3, 1, 16, 3};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (fn(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(S), dims, strides, box, estr,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return SND_ERR_UNSUPPORTED;
+  Epi e{nullptr, 0, dw, 0, 0, 1, 9LL * cin};
+  const int ktiles = static_cast<int>(m / kBK);
+  const cudaError_t ce = launch_gemm_bn<144, true>(ma, mb, cout, 9 * cin, ktiles, ktiles, e, err, s, Wg{h, w, cout});
+  if (launches) *launches += 1;
+  return ce == cudaSuccess ? SND_OK : SND_ERR_CUDA;
 }
 
 // Persistent grid of a kernel with `smem` bytes of dynamic shared memory, `threads` per CTA
@@ -1440,7 +1508,7 @@ struct Sifter {
   cudaStream_t last = nullptr;
   struct {
     size_t params, grads, m1, m2, err, loss, wb[3], wT[3], wf1b, wf1T, p[3], am[3], p3, p3T, hf,
-        logits, dh, dhT, dp3, dy[3], dyT[3], colT[3], dp[3];
+        logits, dh, dhT, dp3, dy[3], dyT[3], s3[3], dp[3];
   } o{};
 };
 
@@ -1474,7 +1542,7 @@ void layout(Sifter& f) {
     if (f.training) {
       f.o.dy[l] = take(l > 0 ? 2ull * m * c.cout : 0);
       f.o.dyT[l] = take(2ull * c.cout * m);
-      f.o.colT[l] = take(l > 0 ? 2ull * c.kc * m : 0);
+      f.o.s3[l] = take(l > 0 ? 2ull * 3 * c.cin * m : 0);  // the shifted copies of the layer's input
       f.o.dp[l] = take(l < 2 ? 2ull * c.cout * m / 4 : 0);
     }
   }
@@ -1622,18 +1690,17 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
       f.launches++;
       break;
     }
-    bf16* colT = at<bf16>(f, f.o.colT[l]);
-    if (c.cin == 16) {
-      k_im2colT_nhwc<16><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
-    } else {
-      k_im2colT_nhwc<32><<<grid_for(m), 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, colT);
+    bf16* S = at<bf16>(f, f.o.s3[l]);
+    {
+      const unsigned sg = static_cast<unsigned>(std::min<long long>((m / 8 * (c.cin / 2) + 255) / 256, 152LL * 8));
+      if (c.cin == 16) {
+        k_shift3<16><<<sg, 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, S);
+      } else {
+        k_shift3<32><<<sg, 256, 0, s>>>(at<bf16>(f, f.o.p[l - 1]), n, c.h, c.w, S);
+      }
+      f.launches++;
     }
-    f.launches++;
-    const int ktiles = static_cast<int>((m + kBK - 1) / kBK);
-    const int ntile = (c.kc + (c.kc <= 32 ? 32 : 64) - 1) / (c.kc <= 32 ? 32 : 64);
-    const int splits = std::max(1, std::min(ktiles, 2 * 152 / std::max(1, ntile)));
-    Epi ew{nullptr, 0, G + kOffW[l], 0, 0, 1, c.kc};
-    int rc = gemm(dyT, m, colT, m, c.cout, c.kc, m, ew, splits, err, s, &f.launches);
+    int rc = gemm_wg(dyT, c.cout, S, n, c.h, c.w, c.cin, G + kOffW[l], err, s, &f.launches);
     if (rc) return rc;
     // input gradient, straight into the previous pooled map's gradient dP[cin][m]: the
     // convolution of dY with the flipped kernel, on the halo kernel
