@@ -915,11 +915,19 @@ __global__ void __launch_bounds__(256) k_dw1(const float* __restrict__ x, int n,
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[j][k] = 0.0f;
   const bf16* dyb = dyT + static_cast<long long>(c0) * mtot + static_cast<long long>(b) * kH * kW + 8 * lane;
+  // the gradients of the warp's next row are loaded while the current row is summed
+  uint4 gn[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) gn[j] = *reinterpret_cast<const uint4*>(dyb + j * mtot + warp * kW);
 #pragma unroll 1
   for (int y = warp; y < kH; y += 8) {
     uint4 gq[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) gq[j] = *reinterpret_cast<const uint4*>(dyb + j * mtot + y * kW);
+    for (int j = 0; j < 4; ++j) gq[j] = gn[j];
+    if (y + 8 < kH) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) gn[j] = *reinterpret_cast<const uint4*>(dyb + j * mtot + (y + 8) * kW);
+    }
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky) {
       // pixels 8 lane - 1 .. 8 lane + 8 of input row y + ky - 1 (staged row y + ky)
@@ -1632,13 +1640,15 @@ int forward(Sifter& f, const float* x, int n, cudaStream_t s) {
                                                                              at<bf16>(f, f.o.p3T), f.bm);
     f.launches++;
   }
-  // fc1 pre-activation (bias and ReLU are applied where it is read, in k_head), K split
-  // over CTAs: only ceil(n / 128) output tiles exist
+  // fc1 pre-activation (bias and ReLU are applied where it is read, in k_head), computed as
+  // its transpose hf^T[hid][b] = Wf1 . F^T and stored transposed into hf[b][hid] (the lanes
+  // of an epilogue warp hold consecutive hid: coalesced); K split over CTAs: only
+  // ceil(n / 128) output tiles exist
   if (cudaMemsetAsync(at<float>(f, f.o.hf), 0, 4ull * n * kHid, s) != cudaSuccess) return SND_ERR_CUDA;
-  Epi e{nullptr, 0, at<float>(f, f.o.hf), 0, 0, 1, kHid};
-  const int mtiles = (n + kBM - 1) / kBM;
-  const int splits = std::max(1, std::min(kFeat / kBK, 2 * 152 / mtiles));
-  return gemm(at<bf16>(f, f.o.p3), kFeat, at<bf16>(f, f.o.wf1b), kFeat, n, kHid, kFeat, e, splits, err, s,
+  Epi e{nullptr, 0, at<float>(f, f.o.hf), 0, 1, 1, kHid};
+  const int ntiles = (n + kBM - 1) / kBM;
+  const int splits = std::max(1, std::min(kFeat / kBK, 2 * 152 / ntiles));
+  return gemm(at<bf16>(f, f.o.wf1b), kFeat, at<bf16>(f, f.o.p3), kFeat, kHid, n, kFeat, e, splits, err, s,
               &f.launches);
 }
 
@@ -1653,14 +1663,16 @@ int backward(Sifter& f, const float* x, const float* y, int n, cudaStream_t s) {
   k_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(at<float>(f, f.o.hf), P, n, y, at<float>(f, f.o.logits), G,
                                                at<float>(f, f.o.loss), at<bf16>(f, f.o.dh), at<bf16>(f, f.o.dhT), f.bm);
   f.launches++;
-  // fc1: dWf1 = dH^T . F ; dF = dH . Wf1
+  // fc1: dWf1 = dH^T . F ; dF = dH . Wf1, each computed as its transpose (M = the 16384
+  // features) and stored transposed, so the lanes of an epilogue warp write consecutive
+  // features (coalesced)
   {
-    Epi e{nullptr, 0, G + kOffWf1, 0, 0, 0, kFeat};
+    Epi e{nullptr, 0, G + kOffWf1, 0, 1, 0, kFeat};
     // K = n valid columns of rows pitched by the batch capacity (the rest reads as zero)
-    int rc = gemm(at<bf16>(f, f.o.dhT), f.bm, at<bf16>(f, f.o.p3T), f.bm, kHid, kFeat, n, e, 1, err, s, &f.launches);
+    int rc = gemm(at<bf16>(f, f.o.p3T), f.bm, at<bf16>(f, f.o.dhT), f.bm, kFeat, kHid, n, e, 1, err, s, &f.launches);
     if (rc) return rc;
-    Epi e2{nullptr, 0, at<float>(f, f.o.dp3), 0, 0, 0, kFeat};
-    rc = gemm(at<bf16>(f, f.o.dh), kHid, at<bf16>(f, f.o.wf1T), kHid, n, kFeat, kHid, e2, 1, err, s, &f.launches);
+    Epi e2{nullptr, 0, at<float>(f, f.o.dp3), 0, 1, 0, kFeat};
+    rc = gemm(at<bf16>(f, f.o.wf1T), kHid, at<bf16>(f, f.o.dh), kHid, kFeat, n, kHid, e2, 1, err, s, &f.launches);
     if (rc) return rc;
   }
   for (int l = 2; l >= 0; --l) {
