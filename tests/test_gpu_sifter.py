@@ -138,10 +138,11 @@ def test_logits_and_gradients_match_oracle():
 
 
 def test_inference_sifter_matches_training_path():
-    """A sifter built without training state runs conv1 and its pooling as one fused kernel
-    (no unpooled map, no argmax). With the same parameters its logits equal those of a
-    training-capable sifter (separate conv1 and pooling kernels): both take the same roundings
-    in the same order, and only the split-K FP32 atomics of fc1 may reorder the last bits."""
+    """A sifter built without training state runs the inference variants of the convolution
+    kernels (no argmax, no transposed fc1 rows). With the same parameters its logits equal
+    those of a training-capable sifter, whose training variants also write the argmax of
+    every pooled cell: both take the same roundings in the same order, and only the split-K
+    FP32 atomics of fc1 may reorder the last bits."""
     rng = np.random.default_rng(21)
     theta = osf.init_params(9).astype(np.float32)
     x = rng.normal(size=(70, 64, 256)).astype(np.float32)  # not a multiple of 64
