@@ -372,15 +372,11 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// Arguments of k_conv_halo (the input map itself comes as a TMA tensor map)
 struct ConvArgs {
-  const bf16* x;    // input activations, channels-last [n][h][w][ldx] (channels 0..cin-1 used)
-  int n, h, w, cin, kc, ktiles;
-  const float* bias;
-  bf16* yT;         // unused
-  int cout;
-  int ldx;          // elements per input pixel
-  float* yTf;       // unused
-  // k_conv_halo: the 2x2 max pooling of the activations. pool_cl: pooled map channels-last
+  int n, h;          // snippets, image rows (the kernel's W is a template argument)
+  const float* bias;  // [cout]; unused in DX mode
+  // the 2x2 max pooling of the activations. pool_cl: pooled map channels-last
   // p[(b, y2, x2)][cout]; else p[b][(c, y2, x2)] (fc1's input rows)
   bf16* p;
   int pool_cl;
@@ -1436,7 +1432,7 @@ int conv_halo(const bf16* x, int n, int h, int w, int cin, const bf16* wb, int k
          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return SND_ERR_UNSUPPORTED;
-  ConvArgs a{x, n, h, w, cin, 9 * cin, kp / kBK, bias, nullptr, cout, cin, nullptr, pool, pool_cl, am, dx};
+  ConvArgs a{n, h, bias, pool, pool_cl, am, dx};
   const int items = n * (h / 2);
   auto go = [&](auto kern, int npl, int cw) {
     // stages x planes x 4 rows x (w + 2) pixels x 16 bytes, then the weights
