@@ -20,14 +20,16 @@ namespace snd {
 namespace {
 
 constexpr int kHistRowsPerBlock = 2048;
+constexpr int kHistWarps = 32;  // warps of a histogram CTA, each over every kHistWarps-th row
 
-// CTA (bx, by) of the histogram: 32 channels x kHistRowsPerBlock samples
+// CTA (bx, by) of the histogram: 32 channels x kHistRowsPerBlock samples, kHistWarps warps
 __device__ __forceinline__ void hist_cta(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
                                          uint32_t* __restrict__ hist, int bx, int by) {
+  constexpr int NT = 32 * kHistWarps;
   __shared__ uint32_t h[256][32];
   const int lane = threadIdx.x, wy = threadIdx.y;
   const int tid = wy * 32 + lane;
-  for (int i = tid; i < 256 * 32; i += 256) (&h[0][0])[i] = 0;
+  for (int i = tid; i < 256 * 32; i += NT) (&h[0][0])[i] = 0;
   __syncthreads();
   const int c = bx * 32 + lane;
   const int r0 = by * kHistRowsPerBlock;
@@ -35,17 +37,17 @@ __device__ __forceinline__ void hist_cta(const uint8_t* __restrict__ chunk, int 
   if (c < nchan) {
     // eight rows' loads in flight per lane before their counts are added
     int r = r0 + wy;
-    for (; r + 56 < r1; r += 64) {
+    for (; r + 7 * kHistWarps < r1; r += 8 * kHistWarps) {
       uint32_t v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = __ldg(chunk + static_cast<size_t>(r + 8 * k) * nchan + c);
+      for (int k = 0; k < 8; ++k) v[k] = __ldg(chunk + static_cast<size_t>(r + kHistWarps * k) * nchan + c);
 #pragma unroll
       for (int k = 0; k < 8; ++k) atomicAdd(&h[v[k]][lane], 1u);
     }
-    for (; r < r1; r += 8) atomicAdd(&h[__ldg(chunk + static_cast<size_t>(r) * nchan + c)][lane], 1u);
+    for (; r < r1; r += kHistWarps) atomicAdd(&h[__ldg(chunk + static_cast<size_t>(r) * nchan + c)][lane], 1u);
   }
   __syncthreads();
-  for (int i = tid; i < 256 * 32; i += 256) {
+  for (int i = tid; i < 256 * 32; i += NT) {
     const int v = i >> 5, l = i & 31;
     const int cc = bx * 32 + l;
     const uint32_t n = h[v][l];
@@ -53,7 +55,7 @@ __device__ __forceinline__ void hist_cta(const uint8_t* __restrict__ chunk, int 
   }
 }
 
-__global__ void __launch_bounds__(256) k_hist(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
+__global__ void __launch_bounds__(32 * kHistWarps) k_hist(const uint8_t* __restrict__ chunk, int nsamp, int nchan,
                                               uint32_t* __restrict__ hist) {
   hist_cta(chunk, nsamp, nchan, hist, blockIdx.x, blockIdx.y);
 }
@@ -290,7 +292,7 @@ __device__ __forceinline__ int beam_of(const int* first, int n, int i) {
   return lo;
 }
 
-__global__ void __launch_bounds__(256) k_hist_multi(const __grid_constant__ EncMulti m) {
+__global__ void __launch_bounds__(32 * kHistWarps) k_hist_multi(const __grid_constant__ EncMulti m) {
   const int i = static_cast<int>(blockIdx.x);
   const int b = beam_of(m.first_h, m.nbeams, i);
   const EncBeam& e = m.beam[b];
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(256) k_pack32_multi(const __grid_constant__ En
 
 cudaError_t launch_encode(const Plan& p, const uint8_t* d_chunk, int nsamp, cudaStream_t s) {
   const DevPtrs& dp = p.dp;
-  dim3 hb(32, 8), hg((p.nchan + 31) / 32, (nsamp + kHistRowsPerBlock - 1) / kHistRowsPerBlock);
+  dim3 hb(32, kHistWarps), hg((p.nchan + 31) / 32, (nsamp + kHistRowsPerBlock - 1) / kHistRowsPerBlock);
   k_hist<<<hg, hb, 0, s>>>(d_chunk, nsamp, p.nchan, dp.hist);
   const bool z = p.mode == SND_MODE_ZFLOAT;
   k_levels<<<(p.nchan * 32 + 255) / 256, 256, 0, s>>>(dp.hist, p.nchan, nsamp, p.enc_theta, dp.levels,
@@ -369,7 +371,7 @@ cudaError_t launch_encode_batch(const Plan* const* plans, const uint8_t* const* 
   const Plan* owner = nullptr;
   auto flush = [&]() -> cudaError_t {
     if (m.nbeams == 0) return cudaSuccess;
-    k_hist_multi<<<nh, dim3(32, 8), 0, s>>>(m);
+    k_hist_multi<<<nh, dim3(32, kHistWarps), 0, s>>>(m);
     k_levels_multi<<<nl, 256, 0, s>>>(m);
     k_pack32_multi<<<np, 256, 0, s>>>(m);
     owner->launches += 3;
